@@ -1,0 +1,441 @@
+"""FP64 CPU oracle for the batched DDF query path — TEST INFRASTRUCTURE ONLY.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this module. The product path (the CUDA library and
+its Python binding) never does, and this module never imports the product:
+the two share nothing but the seeded input generators.
+
+Every function is the plain definition, evaluated in float64 on the float32
+inputs (rays, weights) promoted to double. A matrix product (numpy ``@``) is
+the only library step used on the network path.
+
+What the paper fixes and what this module reads into it:
+  * Sec. 3.1, Eq. (1): f(x, d) = (t, xi); t is the distance to the first
+    surface along d, xi the probability that the ray hits at all.
+  * Sec. 4.3 and Table 2: the first DDF uses a sinusoidal encoding with a
+    wide ReLU MLP. Reading: raw (x, d) first, then for each of the six
+    coordinates, for k = 0..L-1, sin(pi 2^k e) then cos(pi 2^k e).
+  * The two outputs: t = softplus(z0), xi = sigmoid(z1); a ray counts as a
+    hit when z1 > 0.
+  * Sec. 3.2 and 3.4: an L1 term on distance clamped at the box scale plus
+    a cross-entropy term on the hit weighted 0.3, trained with Adam.
+    Reading: the L1 term averages over hit rays only, the cross-entropy
+    over all rays; Adam with (0.9, 0.999, 1e-8) and bias correction.
+  * Sec. 3.3: a shadow ray is occluded when it hits within the light
+    distance; ambient occlusion averages the hit flag over hemisphere
+    directions.
+  * Sec. 3.2: supervision from an exact ray cast of the geometry; here the
+    geometry is a union of spheres and boxes with closed-form intersections.
+  * Sec. 4.4: sphere tracing an SDF is the sequential baseline.
+
+Reduced-precision modes emulate where the GPU path rounds (bf16 operands,
+or e4m3 operands with per-output-channel weight scales and per-tensor
+power-of-two activation scales) while every sum stays in float64; the
+rounding functions are written from the number formats' definitions.
+
+Parity status: every function here is pinned by ``tests/test_oracle_*.py``
+(closed forms, hand-computed networks, finite differences, brute force, and
+library casts for the rounding functions). The paper's own timing and
+accuracy tables need its datasets and weights and are not reproduced.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+F64 = np.float64
+
+# ----------------------------------------------------------------- encoding
+
+
+def encode(o: np.ndarray, d: np.ndarray, octaves: int) -> np.ndarray:
+    """Sinusoidal positional encoding of a ray (Sec. 4.3, Table 2).
+
+    o, d: [n,3]. Returns [n, 6 + 12*octaves] float64: o, d, then per
+    coordinate c (ox, oy, oz, dx, dy, dz) and band k: sin(pi 2^k e_c),
+    cos(pi 2^k e_c).
+    """
+    e = np.concatenate([np.asarray(o, F64), np.asarray(d, F64)], axis=1)
+    n = e.shape[0]
+    out = np.empty((n, 6 + 12 * octaves), dtype=F64)
+    out[:, :6] = e
+    col = 6
+    for c in range(6):
+        for k in range(octaves):
+            arg = np.pi * np.ldexp(e[:, c], k)
+            out[:, col] = np.sin(arg)
+            out[:, col + 1] = np.cos(arg)
+            col += 2
+    return out
+
+
+def encode_points(p: np.ndarray, octaves: int) -> np.ndarray:
+    """3D Fourier encoding of a point for the SDF baseline (Sec. 4.4):
+    p, then per coordinate and band sin(pi 2^k p_c), cos(pi 2^k p_c)."""
+    p = np.asarray(p, F64)
+    n = p.shape[0]
+    out = np.empty((n, 3 + 6 * octaves), dtype=F64)
+    out[:, :3] = p
+    col = 3
+    for c in range(3):
+        for k in range(octaves):
+            arg = np.pi * np.ldexp(p[:, c], k)
+            out[:, col] = np.sin(arg)
+            out[:, col + 1] = np.cos(arg)
+            col += 2
+    return out
+
+
+# ------------------------------------------------------- number formats
+
+
+def round_bf16(x) -> np.ndarray:
+    """Round to the nearest bfloat16 (8 significant bits, binary32 exponent
+    range), ties to even. Values are returned as float64."""
+    x = np.asarray(x, F64)
+    m, e = np.frexp(x)                       # x = m 2^e, 0.5 <= |m| < 1
+    e = np.maximum(e, -125)                  # below 2^-126 the spacing is fixed (subnormals)
+    q = np.ldexp(np.rint(np.ldexp(x, 8 - e)), e - 8)
+    return np.where(x == 0, x, q)
+
+
+E4M3_MAX = 448.0
+
+
+def round_e4m3(x) -> np.ndarray:
+    """Round to the nearest OCP FP8 E4M3 value (4 significant bits, exponent
+    bias 7, smallest normal 2^-6, subnormal spacing 2^-9, largest finite
+    448), ties to even, saturating to +-448. Returned as float64."""
+    x = np.asarray(x, F64)
+    m, e = np.frexp(x)
+    e = np.maximum(e, -5)                    # 2^-6 = 0.5 * 2^-5: subnormal range below
+    q = np.ldexp(np.rint(np.ldexp(x, 4 - e)), e - 4)
+    q = np.clip(q, -E4M3_MAX, E4M3_MAX)
+    return np.where(x == 0, x, q)
+
+
+def round_f32(x) -> np.ndarray:
+    return np.asarray(x, F64).astype(np.float32).astype(F64)
+
+
+# ------------------------------------------------------------- network
+
+
+def softplus(z):
+    z = np.asarray(z, F64)
+    return np.maximum(z, 0.0) + np.log1p(np.exp(-np.abs(z)))
+
+
+def sigmoid(z):
+    z = np.asarray(z, F64)
+    ez = np.exp(-np.abs(z))
+    return np.where(z >= 0, 1.0 / (1.0 + ez), ez / (1.0 + ez))
+
+
+def split_blob(blob, dims):
+    """[(W[out,in], b[out])] from the flat blob; dims = [(out, in), ...]."""
+    blob = np.asarray(blob)
+    out, off = [], 0
+    for fo, fi in dims:
+        w = blob[off:off + fo * fi].reshape(fo, fi).astype(F64)
+        off += fo * fi
+        b = blob[off:off + fo].astype(F64)
+        off += fo
+        out.append((w, b))
+    if off != blob.size:
+        raise ValueError(f"blob has {blob.size} floats, layers need {off}")
+    return out
+
+
+def ddf_dims(octaves: int, width: int, hidden: int):
+    d_in = 6 + 12 * octaves
+    return [(width, d_in)] + [(width, width)] * (hidden - 1) + [(2, width)]
+
+
+def fp8_weight_scales(w: np.ndarray) -> np.ndarray:
+    """Per-output-channel e4m3 scale s_n = amax_n / 448, rounded to float32."""
+    amax = np.max(np.abs(np.asarray(w, F64)), axis=1)
+    s = round_f32(amax / E4M3_MAX)
+    return np.where(s > 0, s, 1.0)
+
+
+def fp8_quantise_weights(w: np.ndarray):
+    """(codes, scales): codes = e4m3(float32(w / s_n)) with the division done
+    in float32, as float64 values."""
+    s = fp8_weight_scales(w)
+    q = (np.asarray(w, np.float32) / s.astype(np.float32)[:, None]).astype(F64)
+    return round_e4m3(q), s
+
+
+def pow2_scale(amax: float) -> float:
+    """Smallest power of two s with amax / s <= 448 (1.0 when amax is 0)."""
+    if amax <= 0:
+        return 1.0
+    return float(2.0 ** np.ceil(np.log2(amax / E4M3_MAX)))
+
+
+def mlp_forward(x0, layers, precision: str = "exact", act_scales=None, keep=False):
+    """ReLU MLP trunk + linear 2-output head (Sec. 3.1), from an encoded input.
+
+    precision:
+      "exact": every operation in float64.
+      "bf16":  the encoded input, hidden weights and every hidden activation
+               except the last are rounded to bfloat16 before they enter a
+               product; sums, bias, ReLU stay float64; the head uses float32
+               weights on the unrounded last activation.
+      "fp8":   layer 1 as in "bf16"; layers 2..H take e4m3 activation codes
+               a_q = e4m3(h / s_l) (s_l from act_scales, one per layer input)
+               and e4m3 weight codes with per-output-channel scales s_n; the
+               pre-activation is (sum a_q w_q) * s_l * s_n + b.
+    Returns z [n,2] (and the list of pre-activations and activations if keep).
+    """
+    hidden = layers[:-1]
+    wo, bo = layers[-1]
+    h = np.asarray(x0, F64)
+    pres, acts = [], [h]
+    H = len(hidden)
+    for l, (w, b) in enumerate(hidden):
+        if precision == "exact":
+            pre = h @ w.T + b
+        elif precision == "bf16" or (precision == "fp8" and l == 0):
+            pre = round_bf16(h) @ round_bf16(w).T + b
+        elif precision == "fp8":
+            s_in = act_scales[l - 1]
+            a_q = round_e4m3(h / s_in)
+            w_q, s_w = fp8_quantise_weights(w)
+            pre = (a_q @ w_q.T) * (s_in * s_w)[None, :] + b
+        else:
+            raise ValueError(precision)
+        h = np.maximum(pre, 0.0)
+        if precision == "bf16" and l < H - 1:
+            h = round_bf16(h)
+        if keep:
+            pres.append(pre)
+            acts.append(h)
+    z = h @ wo.T + bo
+    if keep:
+        return z, pres, acts
+    return z
+
+
+def ddf_forward(o, d, blob, octaves: int, width: int, hidden: int,
+                precision: str = "exact", act_scales=None):
+    """DDF query f(x, d) = (t, xi) of Sec. 3.1, Eq. (1): encode, MLP, heads.
+
+    Returns dict(t, vis, z) with t = softplus(z0), vis = sigmoid(z1)."""
+    layers = split_blob(blob, ddf_dims(octaves, width, hidden))
+    z = mlp_forward(encode(o, d, octaves), layers, precision, act_scales)
+    return {"t": softplus(z[:, 0]), "vis": sigmoid(z[:, 1]), "z": z}
+
+
+def calibrate_act_scales(o, d, blob, octaves, width, hidden):
+    """Per-tensor power-of-two scales for the e4m3 inputs of layers 2..H:
+    s_l = pow2_scale(max |h_l|) over a calibration batch, with h_l taken from
+    the exact forward pass."""
+    layers = split_blob(blob, ddf_dims(octaves, width, hidden))
+    _, _, acts = mlp_forward(encode(o, d, octaves), layers, "exact", keep=True)
+    return [pow2_scale(float(np.max(np.abs(a)))) for a in acts[1:hidden]]
+
+
+# ------------------------------------------------------ loss / gradients
+
+LOSS_CLAMP = 4.0
+LOSS_CE_WEIGHT = 0.3
+
+
+def loss_and_dz(z, t_target, hit_target, clamp=LOSS_CLAMP, lam=LOSS_CE_WEIGHT):
+    """Distillation loss of Sec. 3.2/3.4 and its gradient w.r.t. z.
+
+    L = (1/max(1,N_hit)) sum_{hit} |min(t_hat, c) - min(t*, c)|
+        + lam (1/B) sum_i [softplus(z1) - y z1]
+    with t_hat = softplus(z0). dL/dz0 uses d min(t,c)/dt = 1[t <= c] and
+    sign(0) = 0; dL/dz1 = lam (sigmoid(z1) - y) / B.
+    """
+    z = np.asarray(z, F64)
+    y = np.asarray(hit_target).astype(F64)
+    tt = np.asarray(t_target, F64)
+    B = z.shape[0]
+    nh = max(1.0, float(y.sum()))
+    th = softplus(z[:, 0])
+    diff = np.minimum(th, clamp) - np.minimum(tt, clamp)
+    l1 = np.sum(y * np.abs(diff)) / nh
+    ce = np.sum(softplus(z[:, 1]) - y * z[:, 1]) / B
+    L = l1 + lam * ce
+    dz = np.zeros_like(z)
+    dz[:, 0] = y * np.sign(diff) * (th <= clamp) * sigmoid(z[:, 0]) / nh
+    dz[:, 1] = lam * (sigmoid(z[:, 1]) - y) / B
+    return L, dz
+
+
+def mlp_backward(x0, layers, dz, precision="exact"):
+    """Gradient of sum(dz * z) w.r.t. every weight and bias (reverse-mode
+    chain rule through the linear layers and ReLUs; ReLU'(0) = 0).
+    Returns a list [(dW, db)] matching ``layers``."""
+    z, pres, acts = mlp_forward(x0, layers, precision, keep=True)
+    grads = [None] * len(layers)
+    wo, _ = layers[-1]
+    dz = np.asarray(dz, F64)
+    grads[-1] = (dz.T @ acts[-1], dz.sum(axis=0))
+    dh = dz @ wo
+    for l in range(len(layers) - 2, -1, -1):
+        w, _ = layers[l]
+        dpre = dh * (pres[l] > 0)
+        grads[l] = (dpre.T @ acts[l], dpre.sum(axis=0))
+        dh = dpre @ w
+    return grads
+
+
+def ddf_loss_grad(o, d, blob, octaves, width, hidden, t_target, hit_target):
+    """Loss and flat gradient blob (same layout as the weight blob)."""
+    layers = split_blob(blob, ddf_dims(octaves, width, hidden))
+    x0 = encode(o, d, octaves)
+    z = mlp_forward(x0, layers)
+    L, dz = loss_and_dz(z, t_target, hit_target)
+    grads = mlp_backward(x0, layers, dz)
+    flat = np.concatenate([np.concatenate([g.reshape(-1), gb]) for g, gb in grads])
+    return L, flat
+
+
+def adam_step(w, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba), bias-corrected, no weight decay.
+    step counts from 1. Returns (w, m, v)."""
+    w, g, m, v = (np.asarray(a, F64) for a in (w, g, m, v))
+    m = b1 * m + (1 - b1) * g
+    v = b2 * v + (1 - b2) * g * g
+    mh = m / (1 - b1 ** step)
+    vh = v / (1 - b2 ** step)
+    return w - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+# ------------------------------------------------------- analytic scene
+
+
+def cast_spheres(o, d, centers, radii):
+    """Nearest positive root of |o + t d - c| = r per ray and sphere, min over
+    spheres; inf where none. Tangent rays (zero discriminant) hit."""
+    o = np.asarray(o, F64)
+    d = np.asarray(d, F64)
+    best = np.full(o.shape[0], np.inf)
+    a = np.sum(d * d, axis=1)
+    for c, r in zip(np.asarray(centers, F64), np.asarray(radii, F64)):
+        oc = o - c
+        b = np.sum(d * oc, axis=1)
+        q = np.sum(oc * oc, axis=1) - r * r
+        disc = b * b - a * q
+        ok = disc >= 0
+        sq = np.sqrt(np.where(ok, disc, 0.0))
+        h = -b - np.where(b >= 0, sq, -sq)          # no cancellation
+        with np.errstate(divide="ignore", invalid="ignore"):
+            r1 = np.where(h != 0, h / a, 0.0)
+            r2 = np.where(h != 0, q / h, 0.0)
+        lo = np.minimum(r1, r2)
+        hi = np.maximum(r1, r2)
+        t = np.where(lo > 0, lo, np.where(hi > 0, hi, np.inf))
+        best = np.where(ok, np.minimum(best, t), best)
+    return best
+
+
+def cast_boxes(o, d, lo, hi):
+    """Slab test per axis-aligned box: nearest positive crossing of the
+    surface, min over boxes; inf where none."""
+    o = np.asarray(o, F64)
+    d = np.asarray(d, F64)
+    n = o.shape[0]
+    best = np.full(n, np.inf)
+    for blo, bhi in zip(np.asarray(lo, F64), np.asarray(hi, F64)):
+        tn = np.full(n, -np.inf)
+        tf = np.full(n, np.inf)
+        miss = np.zeros(n, dtype=bool)
+        for i in range(3):
+            par = d[:, i] == 0
+            miss |= par & ((o[:, i] < blo[i]) | (o[:, i] > bhi[i]))
+            with np.errstate(divide="ignore", invalid="ignore"):
+                ta = (blo[i] - o[:, i]) / d[:, i]
+                tb = (bhi[i] - o[:, i]) / d[:, i]
+            tn = np.where(par, tn, np.maximum(tn, np.minimum(ta, tb)))
+            tf = np.where(par, tf, np.minimum(tf, np.maximum(ta, tb)))
+        hit = (~miss) & (tn <= tf) & (tf > 0)
+        t = np.where(tn > 0, tn, tf)
+        best = np.where(hit, np.minimum(best, t), best)
+    return best
+
+
+def cast_scene(scene, o, d):
+    """Exact first-hit distance against the union of spheres and boxes
+    (the exact-cast supervision of Sec. 3.2, with analytic primitives in
+    place of a mesh). Returns (t, hit) with t = inf on a miss."""
+    t = np.minimum(cast_spheres(o, d, scene.centers, scene.radii),
+                   cast_boxes(o, d, scene.box_lo, scene.box_hi))
+    return t, np.isfinite(t)
+
+
+def union_sdf(scene, p):
+    """Signed distance to the union: min over spheres |p-c|-r and boxes
+    (|q|_+ + min(max_i q_i, 0) with q = |p - centre| - half-extent)."""
+    p = np.asarray(p, F64)
+    s = np.full(p.shape[0], np.inf)
+    for c, r in zip(scene.centers, scene.radii):
+        s = np.minimum(s, np.linalg.norm(p - c, axis=1) - r)
+    for lo, hi in zip(scene.box_lo, scene.box_hi):
+        q = np.abs(p - 0.5 * (lo + hi)) - 0.5 * (hi - lo)
+        out = np.linalg.norm(np.maximum(q, 0.0), axis=1)
+        s = np.minimum(s, out + np.minimum(np.max(q, axis=1), 0.0))
+    return s
+
+
+def sphere_trace(sdf, o, d, max_steps=128, eps=1e-3, t_max=4.0):
+    """Sphere tracing (Sec. 4.4): t = 0; repeat up to max_steps: s = sdf(o +
+    t d); stop with a hit when s < eps, else t += s; stop with a miss when
+    t > t_max. Returns (t, hit, steps) where steps counts SDF evaluations."""
+    o = np.asarray(o, F64)
+    d = np.asarray(d, F64)
+    n = o.shape[0]
+    t = np.zeros(n)
+    hit = np.zeros(n, dtype=bool)
+    steps = np.zeros(n, dtype=np.int64)
+    active = np.ones(n, dtype=bool)
+    for _ in range(max_steps):
+        if not active.any():
+            break
+        idx = np.nonzero(active)[0]
+        s = sdf(o[idx] + t[idx, None] * d[idx])
+        steps[idx] += 1
+        conv = s < eps
+        hit[idx[conv]] = True
+        go = idx[~conv]
+        t[go] += s[~conv]
+        active[idx[conv]] = False
+        active[go[t[go] > t_max]] = False
+    return t, hit, steps
+
+
+def sdf_mlp(p, blob, octaves, width, hidden, precision="exact"):
+    """SDF baseline network: Fourier-encoded point -> ReLU MLP -> 1 output."""
+    d_in = 3 + 6 * octaves
+    dims = [(width, d_in)] + [(width, width)] * (hidden - 1) + [(1, width)]
+    layers = split_blob(blob, dims)
+    return mlp_forward(encode_points(p, octaves), layers, precision)[:, 0]
+
+
+# ----------------------------------------------------------- queries
+
+
+def shadow(t, z1, o, light):
+    """Sec. 3.3: occluded iff the field reports a hit (z1 > 0) closer than
+    the light."""
+    dist = np.linalg.norm(np.asarray(light, F64)[None, :] - np.asarray(o, F64), axis=1)
+    return (np.asarray(z1) > 0) & (np.asarray(t, F64) < dist)
+
+
+def ambient_occlusion(hit, vis, offsets):
+    """Sec. 3.3: per shading point, 1 - mean hit flag over its rays (hard),
+    and 1 - mean visibility (soft). Empty sets give 1."""
+    offsets = np.asarray(offsets, np.int64)
+    n = offsets.size - 1
+    hard = np.ones(n)
+    soft = np.ones(n)
+    for p in range(n):
+        a, b = offsets[p], offsets[p + 1]
+        if b > a:
+            hard[p] = 1.0 - np.mean(np.asarray(hit[a:b], F64))
+            soft[p] = 1.0 - np.mean(np.asarray(vis[a:b], F64))
+    return hard, soft

@@ -1,0 +1,291 @@
+"""Seeded synthetic inputs for the DDF query path.
+
+This module is shared by the FP64 oracle (``oracle/``) and by the GPU path's
+tests and benchmark. It holds random numbers and workload recipes only: ray
+batches, analytic scenes, surface sample points, Xavier-initialised weight
+blobs and ragged ambient-occlusion direction sets. None of the DDF's own
+arithmetic (encoding, MLP, heads, loss, ray casting) lives here.
+
+Random source: SplitMix64 (Steele, Lea, Flood, "Fast splittable pseudorandom
+number generators", OOPSLA 2014), used counter-style: output i of stream s is
+the SplitMix64 finaliser applied to ``key(seed, s) + (i + 1) * GAMMA``, which
+equals the i-th output of the sequential generator started at that key.
+Uniform doubles take the top 53 bits. Everything is generated in float64 and
+rounded once to float32 where the product consumes float32.
+
+The workloads follow the paper's query kinds (Sec. 3.3: primary, shadow,
+ambient-occlusion and bounce rays) at the sizes used for measurement:
+  * ``uniform_rays``: origins uniform in [-1,1]^3, directions uniform on S^2.
+  * ``shadow_rays``: points on an analytic sphere scene, offset along the
+    normal by 1e-3, aimed at a point light.
+  * ``ao_rays``: per shading point a random count in [4, 64] of
+    cosine-weighted hemisphere directions, flattened with CSR offsets.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+# stream ids: one per independent random quantity
+S_ORIGIN, S_DIR, S_WEIGHTS, S_SCENE, S_POINTS, S_COUNTS, S_HEMI, S_TARGET = range(1, 9)
+
+
+def _mix(z: np.ndarray) -> np.ndarray:
+    z = (z ^ (z >> np.uint64(30))) * _M1
+    z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def splitmix64(seed: int, stream: int, n: int, offset: int = 0) -> np.ndarray:
+    """Outputs offset..offset+n-1 of SplitMix64 stream ``stream`` (uint64)."""
+    with np.errstate(over="ignore"):
+        key = _mix(np.array([(seed * 0x1000003 + stream) & 0xFFFFFFFFFFFFFFFF],
+                            dtype=np.uint64))[0]
+        i = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+        return _mix(key + i * GAMMA)
+
+
+def uniform(seed: int, stream: int, n: int, lo=0.0, hi=1.0, offset: int = 0) -> np.ndarray:
+    """n doubles uniform in [lo, hi)."""
+    u = (splitmix64(seed, stream, n, offset) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    return lo + (hi - lo) * u
+
+
+def gaussian(seed: int, stream: int, n: int, offset: int = 0) -> np.ndarray:
+    """n standard normals by Box-Muller on pairs of uniforms."""
+    u = uniform(seed, stream, 2 * n, offset=2 * offset)
+    u1 = 1.0 - u[0::2]  # (0, 1]
+    u2 = u[1::2]
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+
+
+def unit_vectors(seed: int, stream: int, n: int, offset: int = 0) -> np.ndarray:
+    """n directions uniform on S^2 (normalised Gaussian triples), float64 [n,3]."""
+    g = gaussian(seed, stream, 3 * n, offset=3 * offset).reshape(n, 3)
+    nrm = np.linalg.norm(g, axis=1, keepdims=True)
+    nrm[nrm == 0] = 1.0
+    return g / nrm
+
+
+@dataclass
+class Rays:
+    """Ray batch as a structure of arrays (float32, contiguous)."""
+    ox: np.ndarray
+    oy: np.ndarray
+    oz: np.ndarray
+    dx: np.ndarray
+    dy: np.ndarray
+    dz: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return int(self.ox.shape[0])
+
+    def soa(self):
+        return [self.ox, self.oy, self.oz, self.dx, self.dy, self.dz]
+
+    def origins(self) -> np.ndarray:
+        return np.stack([self.ox, self.oy, self.oz], axis=1)
+
+    def dirs(self) -> np.ndarray:
+        return np.stack([self.dx, self.dy, self.dz], axis=1)
+
+    def slice(self, a: int, b: int) -> "Rays":
+        return Rays(*[x[a:b].copy() for x in self.soa()])
+
+    @staticmethod
+    def from_arrays(o: np.ndarray, d: np.ndarray) -> "Rays":
+        o = np.asarray(o, dtype=np.float64)
+        d = np.asarray(d, dtype=np.float64)
+        f = lambda a: np.ascontiguousarray(a.astype(np.float32))
+        return Rays(f(o[:, 0]), f(o[:, 1]), f(o[:, 2]), f(d[:, 0]), f(d[:, 1]), f(d[:, 2]))
+
+
+def uniform_rays(n: int, seed: int = 0) -> Rays:
+    """Origins uniform in [-1,1]^3, directions uniform on the sphere."""
+    o = uniform(seed, S_ORIGIN, 3 * n, -1.0, 1.0).reshape(n, 3)
+    d = unit_vectors(seed, S_DIR, n)
+    return Rays.from_arrays(o, d)
+
+
+# ---------------------------------------------------------------- networks
+
+@dataclass
+class NetShape:
+    """DDF network shape: sinusoidal encoding with ``octaves`` bands per
+    coordinate, ``hidden`` ReLU layers of ``width``, and a 2-output head."""
+    octaves: int
+    width: int
+    hidden: int
+
+    @property
+    def d_in(self) -> int:
+        return 6 + 12 * self.octaves
+
+    def layer_dims(self):
+        """(fan_out, fan_in) for every linear layer, the head last."""
+        dims = [(self.width, self.d_in)]
+        dims += [(self.width, self.width)] * (self.hidden - 1)
+        dims.append((2, self.width))
+        return dims
+
+    @property
+    def n_params(self) -> int:
+        return sum(o * i + o for o, i in self.layer_dims())
+
+
+def xavier_blob(shape: NetShape, seed: int = 0) -> np.ndarray:
+    """Float32 weight blob, Xavier-uniform W and U(+-1/sqrt(fan_in)) biases.
+
+    Layout: for each layer in order, W[out][in] row-major then b[out]; the
+    2-row head comes last (row 0 drives the distance, row 1 the visibility).
+    """
+    parts = []
+    off = 0
+    for fo, fi in shape.layer_dims():
+        a = np.sqrt(6.0 / (fi + fo))
+        w = uniform(seed, S_WEIGHTS, fo * fi, -a, a, offset=off)
+        off += fo * fi
+        bb = 1.0 / np.sqrt(fi)
+        b = uniform(seed, S_WEIGHTS, fo, -bb, bb, offset=off)
+        off += fo
+        parts += [w, b]
+    return np.ascontiguousarray(np.concatenate(parts).astype(np.float32))
+
+
+def split_blob(shape: NetShape, blob: np.ndarray):
+    """[(W[out,in], b[out]), ...] views of a weight blob, head last."""
+    out = []
+    off = 0
+    for fo, fi in shape.layer_dims():
+        w = blob[off:off + fo * fi].reshape(fo, fi)
+        off += fo * fi
+        b = blob[off:off + fo]
+        off += fo
+        out.append((w, b))
+    if off != blob.size:
+        raise ValueError(f"blob has {blob.size} floats, shape needs {off}")
+    return out
+
+
+# ---------------------------------------------------------------- scenes
+
+@dataclass
+class Scene:
+    """Union of spheres (centre, radius) and axis-aligned boxes (lo, hi)."""
+    centers: np.ndarray  # [S,3] float64
+    radii: np.ndarray    # [S]
+    box_lo: np.ndarray   # [B,3]
+    box_hi: np.ndarray   # [B,3]
+
+    def packed(self) -> np.ndarray:
+        """Float32 [S*4 + B*6]: (cx,cy,cz,r) per sphere, then (lo,hi) per box."""
+        s = np.concatenate([self.centers, self.radii[:, None]], axis=1).reshape(-1)
+        b = np.concatenate([self.box_lo, self.box_hi], axis=1).reshape(-1)
+        return np.ascontiguousarray(np.concatenate([s, b]).astype(np.float32))
+
+    def as_float32(self) -> "Scene":
+        """The scene with every number rounded to float32 (what a GPU reads)."""
+        r = lambda a: a.astype(np.float32).astype(np.float64)
+        return Scene(r(self.centers), r(self.radii), r(self.box_lo), r(self.box_hi))
+
+
+def random_scene(n_spheres: int, n_boxes: int, seed: int = 0) -> Scene:
+    """Sphere centres U[-1,1]^3, radii U[0.05,0.3]; box centres U[-1,1]^3 with
+    half-extents U[0.05,0.3] per axis, clipped to [-1,1]^3."""
+    u = uniform(seed, S_SCENE, 4 * n_spheres + 6 * n_boxes)
+    c = -1.0 + 2.0 * u[:3 * n_spheres].reshape(n_spheres, 3)
+    r = 0.05 + 0.25 * u[3 * n_spheres:4 * n_spheres]
+    ub = u[4 * n_spheres:].reshape(n_boxes, 6)
+    bc = -1.0 + 2.0 * ub[:, :3]
+    he = 0.05 + 0.25 * ub[:, 3:]
+    lo = np.clip(bc - he, -1.0, 1.0)
+    hi = np.clip(bc + he, -1.0, 1.0)
+    return Scene(c, r, lo, hi).as_float32()
+
+
+def surface_points(scene: Scene, n: int, seed: int = 0):
+    """n points uniform on the union's sphere surfaces (sphere chosen by area),
+    dropping points that lie inside another sphere. Returns (p, normal), float64."""
+    S = scene.radii.shape[0]
+    area = scene.radii ** 2
+    cdf = np.cumsum(area) / area.sum()
+    got_p, got_n, have, off = [], [], 0, 0
+    while have < n:
+        m = int((n - have) * 1.3) + 1024
+        u = uniform(seed, S_POINTS, m, offset=off)
+        idx = np.minimum(np.searchsorted(cdf, u, side="right"), S - 1)
+        nrm = unit_vectors(seed, S_POINTS + 100, m, offset=off)
+        off += m
+        p = scene.centers[idx] + scene.radii[idx, None] * nrm
+        inside = np.zeros(m, dtype=bool)
+        for j in range(S):
+            dj = np.linalg.norm(p - scene.centers[j], axis=1)
+            inside |= (dj < scene.radii[j]) & (idx != j)
+        keep = ~inside
+        got_p.append(p[keep])
+        got_n.append(nrm[keep])
+        have += int(keep.sum())
+    return np.concatenate(got_p)[:n], np.concatenate(got_n)[:n]
+
+
+def shadow_rays(scene: Scene, n: int, light=(3.0, 3.0, 3.0), seed: int = 0, eps: float = 1e-3) -> Rays:
+    """Shadow rays: surface point offset by eps along its normal, aimed at the light."""
+    p, nrm = surface_points(scene, n, seed)
+    o = p + eps * nrm
+    d = np.asarray(light, dtype=np.float64)[None, :] - o
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return Rays.from_arrays(o, d)
+
+
+def _frame(nrm: np.ndarray):
+    """Orthonormal tangent frame (t, b) around each unit normal."""
+    a = np.where(np.abs(nrm[:, :1]) > 0.9, np.array([[0.0, 1.0, 0.0]]), np.array([[1.0, 0.0, 0.0]]))
+    t = np.cross(a, nrm)
+    t /= np.linalg.norm(t, axis=1, keepdims=True)
+    b = np.cross(nrm, t)
+    return t, b
+
+
+def cosine_directions(nrm: np.ndarray, seed: int, stream: int, offset: int = 0) -> np.ndarray:
+    """One cosine-weighted hemisphere direction per normal (Malley's method:
+    uniform disk sample lifted onto the hemisphere)."""
+    m = nrm.shape[0]
+    u = uniform(seed, stream, 2 * m, offset=2 * offset).reshape(m, 2)
+    r = np.sqrt(u[:, 0])
+    phi = 2.0 * np.pi * u[:, 1]
+    x, y = r * np.cos(phi), r * np.sin(phi)
+    z = np.sqrt(np.maximum(0.0, 1.0 - u[:, 0]))
+    t, b = _frame(nrm)
+    d = x[:, None] * t + y[:, None] * b + z[:, None] * nrm
+    return d / np.linalg.norm(d, axis=1, keepdims=True)
+
+
+def bounce_rays(scene: Scene, n: int, seed: int = 0, eps: float = 1e-3) -> Rays:
+    """One-bounce GI rays: surface point offset along the normal, one
+    cosine-weighted direction about the normal."""
+    p, nrm = surface_points(scene, n, seed)
+    o = p + eps * nrm
+    d = cosine_directions(nrm, seed, S_HEMI)
+    return Rays.from_arrays(o, d)
+
+
+def ao_rays(scene: Scene, n_points: int, seed: int = 0, lo: int = 4, hi: int = 64, eps: float = 1e-3):
+    """Ragged ambient-occlusion batch. Returns (rays, offsets int32[n_points+1]).
+    Point p owns rays offsets[p]..offsets[p+1]-1; counts are uniform in [lo, hi]."""
+    p, nrm = surface_points(scene, n_points, seed)
+    counts = lo + np.floor(uniform(seed, S_COUNTS, n_points) * (hi - lo + 1)).astype(np.int64)
+    counts = np.minimum(counts, hi)
+    offsets = np.zeros(n_points + 1, dtype=np.int64)
+    np.cumsum(counts, out=offsets[1:])
+    owner = np.repeat(np.arange(n_points), counts)
+    o = p[owner] + eps * nrm[owner]
+    d = cosine_directions(nrm[owner], seed, S_HEMI)
+    if offsets[-1] >= 2 ** 31:
+        raise ValueError("ragged batch exceeds int32 offsets")
+    return Rays.from_arrays(o, d), offsets.astype(np.int32)
