@@ -1,0 +1,160 @@
+/*
+ * ddf.h -- C ABI of the GB300 Directed Distance Field query library (libddf.so).
+ *
+ * The library evaluates a Directed Distance Field f(x, d) = (t, xi)
+ * (Sec. 3.1, Eq. 1): for a ray with origin x and unit direction d, t is the
+ * distance to the first surface along d and xi the probability that the ray
+ * hits anything. The field is the "first DDF" of Sec. 4.3 / Table 2: a
+ * sinusoidal encoding of (x, d) followed by a wide ReLU MLP; the two outputs
+ * are t = softplus(z0) and xi = sigmoid(z1), and a ray counts as a hit when
+ * z1 > 0. Every query is one network evaluation (Sec. 3.3).
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns a ddf_status and never aborts the process. Arguments
+ *    are checked before anything is launched; on failure nothing is launched
+ *    and ddf_last_error() describes the problem.
+ *  - Ray batches are a structure of arrays: rays[0..5] point to n float32
+ *    values each (ox, oy, oz, dx, dy, dz), 4-byte aligned, caller-owned.
+ *    Directions are used as given (no renormalisation).
+ *  - "device" pointers are CUDA device (or managed) memory on the handle's
+ *    device; "host" pointers are ordinary host memory. Calls that take a
+ *    stream are asynchronous with respect to the host: results are valid once
+ *    the stream has reached the call; the caller keeps inputs alive until then.
+ *  - stream is a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream. One handle must not be used from two host threads at once, and
+ *    two in-flight calls on different streams must not share one handle (they
+ *    share its workspace).
+ *  - The library owns the weights, their reduced-precision copies, the
+ *    workspace and any CUDA graphs; ddf_destroy frees all of it.
+ *  - Device kernels bound every wait; a wait that runs out makes the kernel
+ *    give up cleanly (no trap, the context stays usable) and sets a bit in the
+ *    handle's device status word, which ddf_check_status reads and clears.
+ *    Results of a launch that gave up are undefined.
+ */
+#ifndef DDF_H_
+#define DDF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ddf_s* ddf_handle;
+
+typedef enum {
+  DDF_OK = 0,
+  DDF_ERR_INVALID_ARG = 1,  /* null pointer, bad size, bad alignment, bad config */
+  DDF_ERR_CUDA = 2,         /* a CUDA runtime call failed (message in ddf_last_error) */
+  DDF_ERR_OOM = 3,          /* device or pinned allocation failed */
+  DDF_ERR_BAD_WEIGHTS = 4,  /* blob size mismatch, non-finite values, no weights loaded */
+  DDF_ERR_UNSUPPORTED = 5,  /* valid request this build does not support (e.g. width) */
+  DDF_ERR_TIMEOUT = 6       /* a device-side bounded wait ran out (see header notes) */
+} ddf_status;
+
+typedef enum {
+  DDF_FP32 = 0,      /* plain FP32 on CUDA cores (no TF32) */
+  DDF_BF16 = 1,      /* bf16 operands, FP32 accumulation on tcgen05 tensor cores */
+  DDF_FP8_E4M3 = 2   /* e4m3 operands (layers 2..H), FP32 accumulation on tcgen05 */
+} ddf_precision;
+
+/* Network shape and precision (Sec. 4.3: sinusoidal encoding + wide MLP).
+ *   octaves        L >= 0 bands per coordinate; encoded width D_in = 6 + 12 L
+ *                  laid out as [ox,oy,oz,dx,dy,dz, then for each coordinate c
+ *                  and band k: sin(pi 2^k e_c), cos(pi 2^k e_c)], L <= 16
+ *   width          hidden width W; tensor-core precisions need W % 128 == 0
+ *   hidden_layers  H >= 1 ReLU layers (D_in -> W, then H-1 times W -> W)
+ *   precision      a ddf_precision value
+ *   device         CUDA device ordinal the handle lives on */
+typedef struct {
+  int32_t octaves;
+  int32_t width;
+  int32_t hidden_layers;
+  int32_t precision;
+  int32_t device;
+} ddf_config;
+
+/* Number of floats in the weight blob of cfg (0 if cfg is invalid).
+ * Blob layout: for each layer in order, W[out][in] row-major then b[out];
+ * layers are D_in->W, (H-1) x W->W, then the head W->2 whose row 0 feeds
+ * t = softplus(z0) and row 1 feeds xi = sigmoid(z1). */
+size_t ddf_param_count(const ddf_config* cfg);
+
+/* Creates a handle on cfg->device. *out receives the handle (NULL on error).
+ * Allocates only small bookkeeping; weights arrive with ddf_load_weights. */
+ddf_status ddf_create(const ddf_config* cfg, ddf_handle* out);
+
+/* Frees everything the handle owns (synchronises its device first).
+ * Passing NULL is a no-op returning DDF_OK. */
+ddf_status ddf_destroy(ddf_handle h);
+
+/* Message of the last failing call on this host thread ("" if none).
+ * The string stays valid until the next call on the same thread. */
+const char* ddf_last_error(void);
+
+/* Copies n_floats = ddf_param_count() FP32 master weights from host memory,
+ * then derives the precision-specific device copies (bf16 casts, or e4m3
+ * codes with per-output-channel scales s_n = amax_n / 448). Synchronous.
+ * DDF_ERR_BAD_WEIGHTS on a size mismatch or a non-finite value. */
+ddf_status ddf_load_weights(ddf_handle h, const float* host_blob, size_t n_floats);
+
+/* Copies the current FP32 master weights (after any training steps) into
+ * host_blob (n_floats = ddf_param_count()). Synchronous: a checkpoint. */
+ddf_status ddf_get_weights(ddf_handle h, float* host_blob, size_t n_floats);
+
+/* FP8 only: per-tensor activation scales s_1..s_{H-1} for the e4m3 inputs of
+ * layers 2..H (n = H-1 host floats, each a positive power of two). Layer l+1
+ * reads the code e4m3(h_l / s_l). Required before an FP8 query. */
+ddf_status ddf_set_act_scales(ddf_handle h, const float* host_scales, int32_t n);
+
+/* One DDF evaluation per ray (Sec. 3.3, primary and bounce rays):
+ * out_t[i] = softplus(z0), out_vis[i] = sigmoid(z1) for ray i, i < n.
+ * rays: 6 device pointers (SoA, see above); out_t, out_vis: n device floats.
+ * n == 0 is a no-op. Asynchronous on stream. */
+ddf_status ddf_query_rays(ddf_handle h, const float* const rays[6], int64_t n,
+                          float* out_t, float* out_vis, void* stream);
+
+/* Shadow query (Sec. 3.3): as ddf_query_rays, plus out_occluded[i] = 1 when
+ * the field reports a hit (z1 > 0) closer than the light, i.e.
+ * t < |light - origin_i|, else 0. light: 3 host floats. out_occluded: n
+ * device bytes. Asynchronous on stream. */
+ddf_status ddf_query_shadow(ddf_handle h, const float* const rays[6], int64_t n,
+                            const float light[3], float* out_t, float* out_vis,
+                            uint8_t* out_occluded, void* stream);
+
+/* Same as ddf_query_rays with every buffer in HOST memory: the library copies
+ * the rays in, evaluates them and copies t and vis back, overlapping the copies
+ * of one chunk with the evaluation of the next on its own streams. Returns
+ * once the results are in out_t / out_vis (synchronous). Page-locked host
+ * buffers give the fastest copies; pageable ones work. */
+ddf_status ddf_query_rays_host(ddf_handle h, const float* const rays[6], int64_t n,
+                               float* out_t, float* out_vis);
+
+/* Device status word of the handle: bit 0 = a pipeline wait timed out,
+ * bit 1 = a scheduler wait timed out. Synchronises the device, stores the
+ * word in *out and clears it. */
+ddf_status ddf_check_status(ddf_handle h, uint32_t* out);
+
+/* Wait limit, in nanoseconds, for every device-side wait of later launches
+ * (default 2e9). Setting 0 makes any wait that does not succeed at once give
+ * up, which exercises the timeout path without faulting the device. */
+ddf_status ddf_set_timeout_ns(ddf_handle h, uint64_t ns);
+
+/* Rays per internal chunk of a query (default 1,048,576; minimum 128). Sets
+ * the workspace size: about chunk * (4 W + D_in) bytes at bf16/fp8 and twice
+ * that at FP32. */
+ddf_status ddf_set_chunk_rays(ddf_handle h, int64_t chunk);
+
+/* Kernel timing. When on, the library brackets every launch with CUDA events
+ * on the launching stream, grouped by kernel class:
+ *   0 encode, 1 hidden-layer GEMM, 2 head/finish, 3 other.
+ * ddf_profile_read synchronises, then stores per class the summed device time
+ * in milliseconds (ms[4]) and launch counts (launches[4]), and resets them. */
+ddf_status ddf_profile_enable(ddf_handle h, int32_t on);
+ddf_status ddf_profile_read(ddf_handle h, double ms[4], int64_t launches[4]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDF_H_ */

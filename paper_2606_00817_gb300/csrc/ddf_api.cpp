@@ -1,0 +1,697 @@
+// ddf_api.cpp -- the C ABI of libddf.so (declared in include/ddf.h).
+//
+// Host-side runtime of the DDF query path: argument checking, weight upload
+// and derivation of the per-precision device copies, workspace management,
+// TMA tensor-map construction, the per-chunk launch sequence
+//   encode -> H dense layers -> heads
+// (one network evaluation per ray, Sec. 3.3), the pipelined host-buffer
+// query, device status words and per-kernel-class event timing.
+#include "ddf.h"
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ddf_status fail(ddf_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+ddf_status cuda_fail(cudaError_t e, const char* what) {
+  const ddf_status s = (e == cudaErrorMemoryAllocation) ? DDF_ERR_OOM : DDF_ERR_CUDA;
+  return fail(s, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define DDF_CK(call)                                   \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Restores the caller's current device when it goes out of scope.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (fn == nullptr) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Row-major [rows x inner] matrix of 1- or 2-byte elements, 128-byte-swizzled
+// boxes of [box_rows x (128 bytes)].
+bool make_tmap(CUtensorMap* m, const void* base, bool one_byte, uint64_t inner, uint64_t rows,
+               uint64_t row_bytes, uint32_t box_rows) {
+  auto fn = get_encode_fn();
+  if (fn == nullptr) return false;
+  const cuuint64_t dims[2] = {inner, rows};
+  const cuuint64_t strides[1] = {row_bytes};
+  const cuuint32_t box[2] = {one_byte ? 128u : 64u, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(m, one_byte ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                        2, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+constexpr int kProfClasses = 4;
+enum ProfClass { kProfEncode = 0, kProfGemm = 1, kProfHead = 2, kProfOther = 3 };
+
+}  // namespace
+
+struct ddf_s {
+  ddf_config cfg{};
+  int d_in = 0;
+  int kp32 = 0;  // padded encoded width, FP32 rows (multiple of 8)
+  int kp16 = 0;  // padded encoded width, bf16 rows (multiple of 8 -> 16-byte rows)
+  int bn = 0;    // tensor-core N tile
+  int num_sms = 0;
+  bool loaded = false;
+  bool scales_set = false;
+  uint64_t timeout_ns = 2000000000ull;
+  int64_t chunk = 1 << 20;
+
+  std::vector<void*> owned;  // device allocations freed by ddf_destroy
+  float* d_blob = nullptr;   // FP32 master weights
+  std::vector<float*> wf;    // FP32: padded W per hidden layer
+  std::vector<float*> bias;  // per hidden layer [W]
+  std::vector<__nv_bfloat16*> wb;  // bf16 W (all layers for BF16, layer 1 for FP8)
+  std::vector<uint8_t*> wq;        // FP8: e4m3 codes for layers 2..H
+  std::vector<float*> wscale;      // FP8: per-output-channel scales
+  std::vector<float*> colscale;    // FP8: s_{l-1} * wscale_l
+  std::vector<float> act_scales;
+  std::vector<CUtensorMap> tmB;
+  float* head_w = nullptr;  // [2 x W]
+  float* head_b = nullptr;  // [2]
+
+  int64_t ws_rows = 0;
+  void* ws_enc = nullptr;
+  void* ws_act[2] = {nullptr, nullptr};
+  float2* ws_part = nullptr;
+
+  uint32_t* status_dev = nullptr;
+
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  struct Rec {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+
+  // host-buffer pipeline
+  cudaStream_t s_copy = nullptr, s_comp = nullptr;
+  float* hp_rays[2][6] = {};
+  float* hp_t[2] = {};
+  float* hp_v[2] = {};
+  int64_t hp_rows = 0;
+  cudaEvent_t ev_in[2] = {}, ev_comp[2] = {};
+};
+
+namespace {
+
+ddf_status dev_alloc(ddf_s* h, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(DDF_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
+                                 cudaGetErrorString(e));
+  }
+  h->owned.push_back(*p);
+  return DDF_OK;
+}
+
+void dev_free(ddf_s* h, void* p) {
+  if (p == nullptr) return;
+  auto it = std::find(h->owned.begin(), h->owned.end(), p);
+  if (it != h->owned.end()) h->owned.erase(it);
+  cudaFree(p);
+}
+
+bool valid_config(const ddf_config* c, std::string* why) {
+  if (c == nullptr) return *why = "config is NULL", false;
+  if (c->octaves < 0 || c->octaves > 16) return *why = "octaves must be in [0, 16]", false;
+  if (c->width < 8 || c->width > 8192 || c->width % 8 != 0)
+    return *why = "width must be a multiple of 8 in [8, 8192]", false;
+  if (c->hidden_layers < 1 || c->hidden_layers > 64)
+    return *why = "hidden_layers must be in [1, 64]", false;
+  if (c->precision < DDF_FP32 || c->precision > DDF_FP8_E4M3)
+    return *why = "unknown precision", false;
+  if (c->device < 0) return *why = "device must be >= 0", false;
+  return true;
+}
+
+size_t param_count(const ddf_config& c) {
+  const size_t d_in = 6 + 12 * static_cast<size_t>(c.octaves);
+  const size_t W = c.width;
+  return d_in * W + W + (c.hidden_layers - 1) * (W * W + W) + 2 * W + 2;
+}
+
+cudaEvent_t prof_event(ddf_s* h) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    h->ev_pool.push_back(e);
+  }
+  return h->ev_pool[h->ev_used++];
+}
+
+struct ProfScope {
+  ddf_s* h;
+  int cls;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  ProfScope(ddf_s* h_, int cls_, cudaStream_t s_) : h(h_), cls(cls_), s(s_) {
+    if (h->prof && (a = prof_event(h)) != nullptr) cudaEventRecord(a, s);
+  }
+  ~ProfScope() {
+    if (a == nullptr) return;
+    cudaEvent_t b = prof_event(h);
+    if (b == nullptr) return;
+    cudaEventRecord(b, s);
+    h->recs.push_back({cls, a, b});
+  }
+};
+
+ddf_status ensure_workspace(ddf_s* h, int64_t rows) {
+  if (rows <= h->ws_rows) return DDF_OK;
+  dev_free(h, h->ws_enc);
+  dev_free(h, h->ws_act[0]);
+  dev_free(h, h->ws_act[1]);
+  dev_free(h, h->ws_part);
+  h->ws_enc = h->ws_act[0] = h->ws_act[1] = nullptr;
+  h->ws_part = nullptr;
+  h->ws_rows = 0;
+  const int W = h->cfg.width;
+  const bool f32 = h->cfg.precision == DDF_FP32;
+  const size_t act_elem = f32 ? 4 : (h->cfg.precision == DDF_BF16 ? 2 : 1);
+  const size_t enc_bytes = static_cast<size_t>(rows) * (f32 ? h->kp32 * 4 : h->kp16 * 2);
+  ddf_status st;
+  if ((st = dev_alloc(h, &h->ws_enc, enc_bytes)) != DDF_OK) return st;
+  for (int i = 0; i < 2; ++i)
+    if ((st = dev_alloc(h, &h->ws_act[i], static_cast<size_t>(rows) * W * act_elem)) != DDF_OK)
+      return st;
+  if (!f32) {
+    void* p;
+    if ((st = dev_alloc(h, &p, static_cast<size_t>(rows) * (W / h->bn) * sizeof(float2))) != DDF_OK)
+      return st;
+    h->ws_part = static_cast<float2*>(p);
+  }
+  h->ws_rows = rows;
+  return DDF_OK;
+}
+
+ddf::RaySoA shift_rays(ddf::RaySoA r, int64_t off) {
+  for (int c = 0; c < 6; ++c) r.p[c] += off;
+  return r;
+}
+
+ddf::HeadOut shift_out(ddf::HeadOut o, int64_t off) {
+  o.t += off;
+  o.vis += off;
+  if (o.occluded) o.occluded += off;
+  o.rays = shift_rays(o.rays, off);
+  return o;
+}
+
+ddf_status forward_f32(ddf_s* h, ddf::RaySoA rays, int m, ddf::HeadOut out, cudaStream_t st) {
+  const int W = h->cfg.width;
+  {
+    ProfScope ps(h, kProfEncode, st);
+    DDF_CK(ddf::launch_encode_f32(rays, m, h->cfg.octaves, h->kp32, static_cast<float*>(h->ws_enc), st));
+  }
+  const float* A = static_cast<const float*>(h->ws_enc);
+  int K = h->kp32;
+  for (int l = 0; l < h->cfg.hidden_layers; ++l) {
+    float* C = static_cast<float*>(h->ws_act[l & 1]);
+    ProfScope ps(h, kProfGemm, st);
+    DDF_CK(ddf::launch_sgemm_relu(A, h->wf[l], h->bias[l], C, m, W, K, st));
+    A = C;
+    K = W;
+  }
+  ProfScope ps(h, kProfHead, st);
+  DDF_CK(ddf::launch_head_f32(A, m, W, h->head_w, h->head_b, out, st));
+  return DDF_OK;
+}
+
+ddf_status forward_tc(ddf_s* h, ddf::RaySoA rays, int m, ddf::HeadOut out, cudaStream_t st) {
+  const int W = h->cfg.width;
+  const int H = h->cfg.hidden_layers;
+  const bool fp8 = h->cfg.precision == DDF_FP8_E4M3;
+  {
+    ProfScope ps(h, kProfEncode, st);
+    DDF_CK(ddf::launch_encode_bf16(rays, m, h->cfg.octaves, h->kp16,
+                                   static_cast<__nv_bfloat16*>(h->ws_enc), st));
+  }
+  for (int l = 0; l < H; ++l) {
+    const bool in_fp8 = fp8 && l > 0;
+    const bool last = l == H - 1;
+    const bool out_fp8 = fp8 && !last;
+    const void* a_base = l == 0 ? h->ws_enc : h->ws_act[(l - 1) & 1];
+    const int K = l == 0 ? h->kp16 : W;
+    const uint64_t row_bytes = static_cast<uint64_t>(K) * (in_fp8 ? 1 : 2);
+    CUtensorMap tmA;
+    if (!make_tmap(&tmA, a_base, in_fp8, K, m, row_bytes, 128))
+      return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for an activation map");
+    ddf::TcGemmParams p{};
+    p.M = m;
+    p.N = W;
+    p.K = K;
+    p.bias = h->bias[l];
+    p.col_scale = in_fp8 ? h->colscale[l] : nullptr;
+    p.out_scale = out_fp8 ? 1.0f / h->act_scales[l] : 1.0f;
+    p.out = last ? nullptr : h->ws_act[l & 1];
+    p.ldo = W;
+    p.head_w = h->head_w;
+    p.head_part = h->ws_part;
+    p.mode = last ? 1 : 0;
+    p.status = h->status_dev;
+    p.timeout_ns = h->timeout_ns;
+    const int64_t tiles = ((m + 127) / 128) * static_cast<int64_t>(W / h->bn);
+    const int grid = static_cast<int>(std::min<int64_t>(tiles, h->num_sms));
+    ProfScope ps(h, kProfGemm, st);
+    DDF_CK(ddf::launch_tc_gemm(h->bn, in_fp8, out_fp8, tmA, h->tmB[l], p, grid, st));
+  }
+  ProfScope ps(h, kProfHead, st);
+  DDF_CK(ddf::launch_finish_heads(h->ws_part, W / h->bn, m, h->head_b, out, st));
+  return DDF_OK;
+}
+
+ddf_status check_rays(const float* const rays[6], int64_t n) {
+  if (n < 0) return fail(DDF_ERR_INVALID_ARG, "n must be >= 0");
+  if (n > 0 && rays == nullptr) return fail(DDF_ERR_INVALID_ARG, "rays is NULL");
+  for (int c = 0; n > 0 && c < 6; ++c) {
+    if (rays[c] == nullptr) return fail(DDF_ERR_INVALID_ARG, "a ray array pointer is NULL");
+    if (reinterpret_cast<uintptr_t>(rays[c]) % 4 != 0)
+      return fail(DDF_ERR_INVALID_ARG, "ray arrays must be 4-byte aligned");
+  }
+  return DDF_OK;
+}
+
+ddf_status check_ready(ddf_s* h) {
+  if (h == nullptr) return fail(DDF_ERR_INVALID_ARG, "handle is NULL");
+  if (!h->loaded) return fail(DDF_ERR_BAD_WEIGHTS, "no weights loaded");
+  if (h->cfg.precision == DDF_FP8_E4M3 && h->cfg.hidden_layers > 1 && !h->scales_set)
+    return fail(DDF_ERR_INVALID_ARG, "FP8 needs activation scales (ddf_set_act_scales)");
+  return DDF_OK;
+}
+
+ddf_status run_query(ddf_s* h, const float* const rays[6], int64_t n, ddf::HeadOut out,
+                     cudaStream_t st) {
+  const int64_t rows = std::min<int64_t>(n, h->chunk);
+  ddf_status s = ensure_workspace(h, rows);
+  if (s != DDF_OK) return s;
+  ddf::RaySoA r;
+  for (int c = 0; c < 6; ++c) r.p[c] = rays[c];
+  out.rays = r;
+  for (int64_t off = 0; off < n; off += h->chunk) {
+    const int m = static_cast<int>(std::min<int64_t>(h->chunk, n - off));
+    const ddf::RaySoA rc = shift_rays(r, off);
+    const ddf::HeadOut oc = shift_out(out, off);
+    s = h->cfg.precision == DDF_FP32 ? forward_f32(h, rc, m, oc, st) : forward_tc(h, rc, m, oc, st);
+    if (s != DDF_OK) return s;
+  }
+  return DDF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ddf_param_count(const ddf_config* cfg) {
+  std::string why;
+  return valid_config(cfg, &why) ? param_count(*cfg) : 0;
+}
+
+const char* ddf_last_error(void) { return g_last_error.c_str(); }
+
+ddf_status ddf_create(const ddf_config* cfg, ddf_handle* out) {
+  if (out == nullptr) return fail(DDF_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  std::string why;
+  if (!valid_config(cfg, &why)) return fail(DDF_ERR_INVALID_ARG, why);
+  if (cfg->precision != DDF_FP32 && cfg->width % 128 != 0)
+    return fail(DDF_ERR_UNSUPPORTED, "tensor-core precisions need width % 128 == 0");
+  int ndev = 0;
+  DDF_CK(cudaGetDeviceCount(&ndev));
+  if (cfg->device >= ndev) return fail(DDF_ERR_INVALID_ARG, "device ordinal out of range");
+  DeviceGuard g(cfg->device);
+  if (!g.ok) return fail(DDF_ERR_CUDA, "cudaSetDevice failed");
+  if (cfg->precision != DDF_FP32) {
+    int major = 0, minor = 0;
+    DDF_CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, cfg->device));
+    DDF_CK(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, cfg->device));
+    if (major != 10 || minor != 3)
+      return fail(DDF_ERR_UNSUPPORTED, "tensor-core precisions are built for sm_103a only");
+    if (get_encode_fn() == nullptr)
+      return fail(DDF_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available");
+  }
+  ddf_s* h = new ddf_s();
+  h->cfg = *cfg;
+  h->d_in = 6 + 12 * cfg->octaves;
+  h->kp32 = static_cast<int>(round_up(h->d_in, 8));
+  h->kp16 = static_cast<int>(round_up(h->d_in, 8));
+  h->bn = (cfg->width % 256 == 0) ? 256 : 128;
+  cudaError_t e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, cfg->device);
+  void* p = nullptr;
+  if (e != cudaSuccess || dev_alloc(h, &p, sizeof(uint32_t)) != DDF_OK) {
+    delete h;
+    return e != cudaSuccess ? cuda_fail(e, "cudaDeviceGetAttribute") : DDF_ERR_OOM;
+  }
+  h->status_dev = static_cast<uint32_t*>(p);
+  if ((e = cudaMemset(h->status_dev, 0, sizeof(uint32_t))) != cudaSuccess) {
+    ddf_destroy(h);
+    return cuda_fail(e, "cudaMemset");
+  }
+  *out = h;
+  return DDF_OK;
+}
+
+ddf_status ddf_destroy(ddf_handle h) {
+  if (h == nullptr) return DDF_OK;
+  DeviceGuard g(h->cfg.device);
+  cudaDeviceSynchronize();
+  for (void* p : h->owned) cudaFree(p);
+  for (auto& e : h->ev_pool) cudaEventDestroy(e);
+  for (int b = 0; b < 2; ++b) {
+    for (int c = 0; c < 6; ++c)
+      if (h->hp_rays[b][c]) cudaFree(h->hp_rays[b][c]);
+    if (h->hp_t[b]) cudaFree(h->hp_t[b]);
+    if (h->hp_v[b]) cudaFree(h->hp_v[b]);
+    if (h->ev_in[b]) cudaEventDestroy(h->ev_in[b]);
+    if (h->ev_comp[b]) cudaEventDestroy(h->ev_comp[b]);
+  }
+  if (h->s_copy) cudaStreamDestroy(h->s_copy);
+  if (h->s_comp) cudaStreamDestroy(h->s_comp);
+  delete h;
+  return DDF_OK;
+}
+
+ddf_status ddf_load_weights(ddf_handle h, const float* host_blob, size_t n_floats) {
+  if (h == nullptr || host_blob == nullptr) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+  const size_t need = param_count(h->cfg);
+  if (n_floats != need)
+    return fail(DDF_ERR_BAD_WEIGHTS, "blob has " + std::to_string(n_floats) + " floats, config needs " +
+                                         std::to_string(need));
+  for (size_t i = 0; i < n_floats; ++i)
+    if (!std::isfinite(host_blob[i]))
+      return fail(DDF_ERR_BAD_WEIGHTS, "non-finite weight at index " + std::to_string(i));
+  DeviceGuard g(h->cfg.device);
+  const int W = h->cfg.width, H = h->cfg.hidden_layers;
+  const int prec = h->cfg.precision;
+  cudaStream_t st = nullptr;
+  ddf_status s;
+  if (h->d_blob == nullptr) {
+    void* p;
+    if ((s = dev_alloc(h, &p, need * sizeof(float))) != DDF_OK) return s;
+    h->d_blob = static_cast<float*>(p);
+    h->wf.assign(H, nullptr);
+    h->bias.assign(H, nullptr);
+    h->wb.assign(H, nullptr);
+    h->wq.assign(H, nullptr);
+    h->wscale.assign(H, nullptr);
+    h->colscale.assign(H, nullptr);
+    h->tmB.assign(H, CUtensorMap{});
+    for (int l = 0; l < H; ++l) {
+      const int K = l == 0 ? h->d_in : W;
+      if ((s = dev_alloc(h, &p, W * sizeof(float))) != DDF_OK) return s;
+      h->bias[l] = static_cast<float*>(p);
+      if (prec == DDF_FP32) {
+        const int kp = l == 0 ? h->kp32 : W;
+        if ((s = dev_alloc(h, &p, static_cast<size_t>(W) * kp * sizeof(float))) != DDF_OK) return s;
+        h->wf[l] = static_cast<float*>(p);
+      } else if (prec == DDF_BF16 || l == 0) {
+        const int kp = l == 0 ? h->kp16 : W;
+        if ((s = dev_alloc(h, &p, static_cast<size_t>(W) * kp * 2)) != DDF_OK) return s;
+        h->wb[l] = static_cast<__nv_bfloat16*>(p);
+        if (!make_tmap(&h->tmB[l], h->wb[l], false, kp, W, static_cast<uint64_t>(kp) * 2, h->bn))
+          return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for a weight map");
+      } else {
+        if ((s = dev_alloc(h, &p, static_cast<size_t>(W) * W)) != DDF_OK) return s;
+        h->wq[l] = static_cast<uint8_t*>(p);
+        if ((s = dev_alloc(h, &p, W * sizeof(float))) != DDF_OK) return s;
+        h->wscale[l] = static_cast<float*>(p);
+        if ((s = dev_alloc(h, &p, W * sizeof(float))) != DDF_OK) return s;
+        h->colscale[l] = static_cast<float*>(p);
+        if (!make_tmap(&h->tmB[l], h->wq[l], true, W, W, W, h->bn))
+          return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for a weight map");
+      }
+      (void)K;
+    }
+    if ((s = dev_alloc(h, &p, 2 * W * sizeof(float))) != DDF_OK) return s;
+    h->head_w = static_cast<float*>(p);
+    if ((s = dev_alloc(h, &p, 4 * sizeof(float))) != DDF_OK) return s;
+    h->head_b = static_cast<float*>(p);
+  }
+  DDF_CK(cudaMemcpy(h->d_blob, host_blob, need * sizeof(float), cudaMemcpyHostToDevice));
+  size_t off = 0;
+  for (int l = 0; l < H; ++l) {
+    const int K = l == 0 ? h->d_in : W;
+    const float* w = h->d_blob + off;
+    off += static_cast<size_t>(W) * K;
+    DDF_CK(cudaMemcpy(h->bias[l], h->d_blob + off, W * sizeof(float), cudaMemcpyDeviceToDevice));
+    off += W;
+    if (prec == DDF_FP32) {
+      DDF_CK(ddf::launch_pack_f32(w, W, K, l == 0 ? h->kp32 : W, h->wf[l], st));
+    } else if (prec == DDF_BF16 || l == 0) {
+      DDF_CK(ddf::launch_pack_bf16(w, W, K, l == 0 ? h->kp16 : W, h->wb[l], st));
+    } else {
+      DDF_CK(ddf::launch_quant_e4m3(w, W, K, W, h->wq[l], h->wscale[l], st));
+    }
+  }
+  DDF_CK(cudaMemcpy(h->head_w, h->d_blob + off, 2 * W * sizeof(float), cudaMemcpyDeviceToDevice));
+  off += 2 * W;
+  DDF_CK(cudaMemcpy(h->head_b, h->d_blob + off, 2 * sizeof(float), cudaMemcpyDeviceToDevice));
+  if (prec == DDF_FP8_E4M3 && h->scales_set) {
+    for (int l = 1; l < H; ++l)
+      DDF_CK(ddf::launch_scale_vec(h->wscale[l], h->act_scales[l - 1], W, h->colscale[l], st));
+  }
+  DDF_CK(cudaDeviceSynchronize());
+  h->loaded = true;
+  return DDF_OK;
+}
+
+ddf_status ddf_get_weights(ddf_handle h, float* host_blob, size_t n_floats) {
+  if (h == nullptr || host_blob == nullptr) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+  if (!h->loaded) return fail(DDF_ERR_BAD_WEIGHTS, "no weights loaded");
+  if (n_floats != param_count(h->cfg)) return fail(DDF_ERR_INVALID_ARG, "wrong blob size");
+  DeviceGuard g(h->cfg.device);
+  DDF_CK(cudaDeviceSynchronize());
+  DDF_CK(cudaMemcpy(host_blob, h->d_blob, n_floats * sizeof(float), cudaMemcpyDeviceToHost));
+  return DDF_OK;
+}
+
+ddf_status ddf_set_act_scales(ddf_handle h, const float* host_scales, int32_t n) {
+  if (h == nullptr) return fail(DDF_ERR_INVALID_ARG, "handle is NULL");
+  if (h->cfg.precision != DDF_FP8_E4M3)
+    return fail(DDF_ERR_INVALID_ARG, "activation scales apply to FP8 handles only");
+  if (n != h->cfg.hidden_layers - 1) return fail(DDF_ERR_INVALID_ARG, "need hidden_layers - 1 scales");
+  if (n > 0 && host_scales == nullptr) return fail(DDF_ERR_INVALID_ARG, "scales is NULL");
+  for (int i = 0; i < n; ++i) {
+    int ex;
+    const float m = std::frexp(host_scales[i], &ex);
+    if (!(host_scales[i] > 0.f) || !std::isfinite(host_scales[i]) || m != 0.5f)
+      return fail(DDF_ERR_INVALID_ARG, "activation scales must be positive powers of two");
+  }
+  h->act_scales.assign(host_scales, host_scales + n);
+  h->scales_set = true;
+  if (h->loaded) {
+    DeviceGuard g(h->cfg.device);
+    for (int l = 1; l < h->cfg.hidden_layers; ++l)
+      DDF_CK(ddf::launch_scale_vec(h->wscale[l], h->act_scales[l - 1], h->cfg.width, h->colscale[l],
+                                   nullptr));
+    DDF_CK(cudaDeviceSynchronize());
+  }
+  return DDF_OK;
+}
+
+ddf_status ddf_query_rays(ddf_handle h, const float* const rays[6], int64_t n, float* out_t,
+                          float* out_vis, void* stream) {
+  ddf_status s = check_ready(h);
+  if (s != DDF_OK) return s;
+  if ((s = check_rays(rays, n)) != DDF_OK) return s;
+  if (n > 0 && (out_t == nullptr || out_vis == nullptr))
+    return fail(DDF_ERR_INVALID_ARG, "output pointer is NULL");
+  if (n == 0) return DDF_OK;
+  DeviceGuard g(h->cfg.device);
+  ddf::HeadOut o{};
+  o.t = out_t;
+  o.vis = out_vis;
+  return run_query(h, rays, n, o, static_cast<cudaStream_t>(stream));
+}
+
+ddf_status ddf_query_shadow(ddf_handle h, const float* const rays[6], int64_t n,
+                            const float light[3], float* out_t, float* out_vis,
+                            uint8_t* out_occluded, void* stream) {
+  ddf_status s = check_ready(h);
+  if (s != DDF_OK) return s;
+  if ((s = check_rays(rays, n)) != DDF_OK) return s;
+  if (light == nullptr) return fail(DDF_ERR_INVALID_ARG, "light is NULL");
+  if (n > 0 && (out_t == nullptr || out_vis == nullptr || out_occluded == nullptr))
+    return fail(DDF_ERR_INVALID_ARG, "output pointer is NULL");
+  if (n == 0) return DDF_OK;
+  DeviceGuard g(h->cfg.device);
+  ddf::HeadOut o{};
+  o.t = out_t;
+  o.vis = out_vis;
+  o.occluded = out_occluded;
+  for (int i = 0; i < 3; ++i) o.light[i] = light[i];
+  return run_query(h, rays, n, o, static_cast<cudaStream_t>(stream));
+}
+
+ddf_status ddf_query_rays_host(ddf_handle h, const float* const rays[6], int64_t n, float* out_t,
+                               float* out_vis) {
+  ddf_status s = check_ready(h);
+  if (s != DDF_OK) return s;
+  if ((s = check_rays(rays, n)) != DDF_OK) return s;
+  if (n > 0 && (out_t == nullptr || out_vis == nullptr))
+    return fail(DDF_ERR_INVALID_ARG, "output pointer is NULL");
+  if (n == 0) return DDF_OK;
+  DeviceGuard g(h->cfg.device);
+  const int64_t C = std::min<int64_t>(h->chunk, n);
+  if (h->s_copy == nullptr) {
+    DDF_CK(cudaStreamCreateWithFlags(&h->s_copy, cudaStreamNonBlocking));
+    DDF_CK(cudaStreamCreateWithFlags(&h->s_comp, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+      DDF_CK(cudaEventCreateWithFlags(&h->ev_in[b], cudaEventDisableTiming));
+      DDF_CK(cudaEventCreateWithFlags(&h->ev_comp[b], cudaEventDisableTiming));
+    }
+  }
+  if (h->hp_rows < C) {
+    for (int b = 0; b < 2; ++b) {
+      for (int c = 0; c < 6; ++c) {
+        cudaFree(h->hp_rays[b][c]);
+        h->hp_rays[b][c] = nullptr;
+      }
+      cudaFree(h->hp_t[b]);
+      cudaFree(h->hp_v[b]);
+      h->hp_t[b] = h->hp_v[b] = nullptr;
+    }
+    h->hp_rows = 0;
+    for (int b = 0; b < 2; ++b) {
+      for (int c = 0; c < 6; ++c) DDF_CK(cudaMalloc(&h->hp_rays[b][c], C * sizeof(float)));
+      DDF_CK(cudaMalloc(&h->hp_t[b], C * sizeof(float)));
+      DDF_CK(cudaMalloc(&h->hp_v[b], C * sizeof(float)));
+    }
+    h->hp_rows = C;
+  }
+  if ((s = ensure_workspace(h, C)) != DDF_OK) return s;
+  const int64_t nchunks = (n + C - 1) / C;
+  auto copy_in = [&](int64_t i) -> ddf_status {
+    const int b = static_cast<int>(i & 1);
+    const int64_t off = i * C, m = std::min<int64_t>(C, n - off);
+    for (int c = 0; c < 6; ++c)
+      DDF_CK(cudaMemcpyAsync(h->hp_rays[b][c], rays[c] + off, m * sizeof(float),
+                             cudaMemcpyHostToDevice, h->s_copy));
+    DDF_CK(cudaEventRecord(h->ev_in[b], h->s_copy));
+    return DDF_OK;
+  };
+  if ((s = copy_in(0)) != DDF_OK) return s;
+  for (int64_t i = 0; i < nchunks; ++i) {
+    const int b = static_cast<int>(i & 1);
+    const int64_t off = i * C, m = std::min<int64_t>(C, n - off);
+    if (i + 1 < nchunks && (s = copy_in(i + 1)) != DDF_OK) return s;
+    DDF_CK(cudaStreamWaitEvent(h->s_comp, h->ev_in[b], 0));
+    ddf::HeadOut o{};
+    o.t = h->hp_t[b];
+    o.vis = h->hp_v[b];
+    const float* rp[6];
+    for (int c = 0; c < 6; ++c) rp[c] = h->hp_rays[b][c];
+    if ((s = run_query(h, rp, m, o, h->s_comp)) != DDF_OK) return s;
+    DDF_CK(cudaEventRecord(h->ev_comp[b], h->s_comp));
+    DDF_CK(cudaStreamWaitEvent(h->s_copy, h->ev_comp[b], 0));
+    DDF_CK(cudaMemcpyAsync(out_t + off, h->hp_t[b], m * sizeof(float), cudaMemcpyDeviceToHost,
+                           h->s_copy));
+    DDF_CK(cudaMemcpyAsync(out_vis + off, h->hp_v[b], m * sizeof(float), cudaMemcpyDeviceToHost,
+                           h->s_copy));
+  }
+  DDF_CK(cudaStreamSynchronize(h->s_copy));
+  DDF_CK(cudaStreamSynchronize(h->s_comp));
+  return DDF_OK;
+}
+
+ddf_status ddf_check_status(ddf_handle h, uint32_t* out) {
+  if (h == nullptr || out == nullptr) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard g(h->cfg.device);
+  DDF_CK(cudaDeviceSynchronize());
+  DDF_CK(cudaMemcpy(out, h->status_dev, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  DDF_CK(cudaMemset(h->status_dev, 0, sizeof(uint32_t)));
+  return DDF_OK;
+}
+
+ddf_status ddf_set_timeout_ns(ddf_handle h, uint64_t ns) {
+  if (h == nullptr) return fail(DDF_ERR_INVALID_ARG, "handle is NULL");
+  h->timeout_ns = ns;
+  return DDF_OK;
+}
+
+ddf_status ddf_set_chunk_rays(ddf_handle h, int64_t chunk) {
+  if (h == nullptr) return fail(DDF_ERR_INVALID_ARG, "handle is NULL");
+  if (chunk < 128 || chunk > (int64_t{1} << 30))
+    return fail(DDF_ERR_INVALID_ARG, "chunk must be in [128, 2^30]");
+  h->chunk = chunk;
+  return DDF_OK;
+}
+
+ddf_status ddf_profile_enable(ddf_handle h, int32_t on) {
+  if (h == nullptr) return fail(DDF_ERR_INVALID_ARG, "handle is NULL");
+  h->prof = on != 0;
+  return DDF_OK;
+}
+
+ddf_status ddf_profile_read(ddf_handle h, double ms[4], int64_t launches[4]) {
+  if (h == nullptr || ms == nullptr || launches == nullptr)
+    return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard g(h->cfg.device);
+  DDF_CK(cudaDeviceSynchronize());
+  for (int c = 0; c < kProfClasses; ++c) {
+    ms[c] = 0.0;
+    launches[c] = 0;
+  }
+  for (const auto& r : h->recs) {
+    float t = 0.f;
+    DDF_CK(cudaEventElapsedTime(&t, r.a, r.b));
+    ms[r.cls] += t;
+    launches[r.cls] += 1;
+  }
+  h->recs.clear();
+  h->ev_used = 0;
+  return DDF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,78 @@
+// kernels.h -- host-side launchers of the DDF device kernels (internal to
+// libddf.so; the public interface is include/ddf.h).
+#pragma once
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace ddf {
+
+// Structure-of-arrays ray pointers (ox, oy, oz, dx, dy, dz).
+struct RaySoA {
+  const float* p[6];
+};
+
+// One dense layer y = act(scale_n * (A W^T)_n + b_n) on the tcgen05 tensor cores.
+// A: [M x K] activations (bf16 or e4m3 codes), W: [N x K], both K-major and
+// read through TMA tensor maps. mode 0 stores ReLU(y) * out_scale as the next
+// layer's activation; mode 1 (the last hidden layer) instead folds ReLU(y)
+// into the 2-row FP32 head and writes one (z0, z1) partial per N-block and row.
+struct TcGemmParams {
+  int M, N, K;
+  const float* bias;       // [N]
+  const float* col_scale;  // [N] or nullptr (e4m3 inputs: s_in * s_w[n])
+  float out_scale;         // multiplier before the e4m3 output cast (1/s_out)
+  void* out;               // mode 0: [M x ldo] bf16 or e4m3 codes
+  int ldo;                 // elements
+  const float* head_w;     // mode 1: [2 x N] FP32
+  float2* head_part;       // mode 1: [N/BN x M]
+  int mode;
+  uint32_t* status;        // device status word (timeouts)
+  uint64_t timeout_ns;
+};
+
+// in_fp8: operands are e4m3 codes (kind::f8f6f4) instead of bf16 (kind::f16).
+// out_fp8: mode-0 output is e4m3 codes instead of bf16. bn: 128 or 256.
+cudaError_t launch_tc_gemm(int bn, bool in_fp8, bool out_fp8, const CUtensorMap& tmA,
+                           const CUtensorMap& tmB, const TcGemmParams& p, int grid,
+                           cudaStream_t s);
+int tc_gemm_smem_bytes(int bn, bool in_fp8);
+
+// Sinusoidal encoding of M rays into a row-major [M x ld] matrix (ld >= 6+12L,
+// columns past 6+12L are zero).
+cudaError_t launch_encode_bf16(RaySoA rays, int64_t M, int L, int ld, __nv_bfloat16* out,
+                               cudaStream_t s);
+cudaError_t launch_encode_f32(RaySoA rays, int64_t M, int L, int ld, float* out, cudaStream_t s);
+
+// FP32 CUDA-core layer: C[M x N] = ReLU(A[M x K] W[N x K]^T + b), K % 8 == 0.
+cudaError_t launch_sgemm_relu(const float* A, const float* W, const float* b, float* C, int M,
+                              int N, int K, cudaStream_t s);
+
+// Heads: z = Wo h + bo, t = softplus(z0), vis = sigmoid(z1), optional shadow.
+struct HeadOut {
+  float* t;
+  float* vis;
+  uint8_t* occluded;  // nullptr unless a shadow query
+  float light[3];
+  RaySoA rays;        // origins for the shadow distance
+};
+// From FP32 activations H [M x W] (FP32 path).
+cudaError_t launch_head_f32(const float* H, int M, int W, const float* wo, const float* bo,
+                            HeadOut o, cudaStream_t s);
+// From per-N-block partial dot products [nblk x M] (tensor-core path).
+cudaError_t launch_finish_heads(const float2* part, int nblk, int M, const float* bo, HeadOut o,
+                                cudaStream_t s);
+
+// Weight preparation (load time).
+// dst[N x ldd] = src[N x K] zero-padded to ldd columns.
+cudaError_t launch_pack_f32(const float* src, int N, int K, int ldd, float* dst, cudaStream_t s);
+cudaError_t launch_pack_bf16(const float* src, int N, int K, int ldd, __nv_bfloat16* dst,
+                             cudaStream_t s);
+// Per-output-channel e4m3: scale[n] = amax_n / 448, codes = e4m3(src / scale[n]).
+cudaError_t launch_quant_e4m3(const float* src, int N, int K, int ldd, uint8_t* dst, float* scale,
+                              cudaStream_t s);
+// out[n] = a * v[n]
+cudaError_t launch_scale_vec(const float* v, float a, int n, float* out, cudaStream_t s);
+
+}  // namespace ddf

@@ -1,0 +1,329 @@
+// tc_gemm.cu -- one dense DDF layer on the sm_103a tensor cores.
+//
+// The hidden layers of the DDF MLP (Sec. 3.1 / Sec. 4.3: a wide ReLU MLP on the
+// encoded ray) are the whole cost of a query at width 1280. Each layer is a
+// GEMM  Y[M x N] = A[M x K] W[N x K]^T  over a chunk of M rays, followed by
+// bias + ReLU. This kernel is persistent (one CTA per SM) and warp-specialised:
+//   warp 0      TMA producer: 128-byte-swizzled A and W tiles into a ring of
+//               shared-memory stages (mbarrier full/empty handshake)
+//   warp 1      allocates TMEM; one thread issues tcgen05.mma (M=128, N=BN,
+//               K=16 bf16 / 32 e4m3 per instruction) into a double-buffered
+//               FP32 accumulator in TMEM, so the epilogue of tile i overlaps the
+//               MMAs of tile i+1
+//   warps 2-5   epilogue: tcgen05.ld of the accumulator (thread = ray row),
+//               scale, bias, ReLU, then either the next layer's activation
+//               (bf16 or e4m3, vectorised stores) or, for the last hidden layer,
+//               the two FP32 head dot products (one partial per N-block).
+// Tiles are ordered N-fastest so the N/BN CTAs that share an A row-block run
+// at the same time and A is read from HBM about once. Every wait is bounded
+// (globaltimer); a timeout raises a CTA abort flag and a status bit, the
+// producer drains its in-flight copies and the MMA thread its in-flight MMAs
+// before TMEM is released.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "kernels.h"
+#include "ptx_sm103.cuh"
+
+namespace ddf {
+
+namespace {
+
+constexpr uint64_t kDrainTimeoutNs = 1000000000ull;  // 1 s for drains at teardown
+
+template <int BN, bool IN_FP8>
+struct TcShape {
+  static constexpr int BM = 128;
+  static constexpr int ROW_BYTES = 128;                 // one 128-byte swizzle row along K
+  static constexpr int BK = IN_FP8 ? 128 : 64;          // K elements per stage
+  static constexpr int A_BYTES = BM * ROW_BYTES;        // 16 KB
+  static constexpr int B_BYTES = BN * ROW_BYTES;        // 16 or 32 KB
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int STAGES = (BN == 256) ? 4 : 6;
+  static constexpr int TMEM_COLS = 2 * BN;              // two FP32 accumulators
+  static constexpr int NUM_BARS = 2 * STAGES + 5;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + NUM_BARS * 8 + 16 + 1024;
+  static_assert(TMEM_COLS == 256 || TMEM_COLS == 512, "TMEM allocation must be a power of two");
+};
+
+__device__ __forceinline__ void raise_abort(volatile int* abort_flag, uint32_t* status) {
+  *abort_flag = 1;
+  atomicOr(status, kStatusPipelineTimeout);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
+  const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+  const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+  return (lo & 0xFFFFu) | (hi << 16);
+}
+
+template <int BN, bool IN_FP8, bool OUT_FP8>
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const TcGemmParams p) {
+  using S = TcShape<BN, IN_FP8>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + S::STAGES * S::A_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::STAGES * S::STAGE_BYTES);
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (S::STAGES + s); };
+  auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * S::STAGES + b); };
+  auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * S::STAGES + 2 + b); };
+  const uint32_t mdone_bar = bar0 + 8u * (2 * S::STAGES + 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + S::NUM_BARS);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S::STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull_bar(b), 1);
+      mbar_init(tempty_bar(b), 4);  // one arrival per epilogue warp
+    }
+    mbar_init(mdone_bar, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmB);
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), S::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  const int num_m = (p.M + S::BM - 1) / S::BM;
+  const int num_n = p.N / BN;
+  const int num_kb = (p.K + S::BK - 1) / S::BK;
+  const int num_tiles = num_m * num_n;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------------------------------------------------- producer
+    int it = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+      const int m0 = (tile / num_n) * S::BM;
+      const int n0 = (tile % num_n) * BN;
+      for (int kb = 0; kb < num_kb; ++kb, ++it) {
+        const int s = it % S::STAGES;
+        const uint32_t ph = (it / S::STAGES) & 1;
+        if (!mbar_wait_bounded(empty_bar(s), ph ^ 1u, abort_flag, p.timeout_ns)) {
+          ok = false;
+          break;
+        }
+        mbar_arrive_expect_tx(full_bar(s), S::STAGE_BYTES);
+        tma_load_2d(smem_u32(sA + s * S::A_BYTES), &tmA, kb * S::BK, m0, full_bar(s));
+        tma_load_2d(smem_u32(sB + s * S::B_BYTES), &tmB, kb * S::BK, n0, full_bar(s));
+      }
+    }
+    if (!ok) {
+      raise_abort(abort_flag, p.status);
+      // let every copy still in flight land before the CTA may exit
+      const int first = it > S::STAGES ? it - S::STAGES : 0;
+      for (int j = first; j < it; ++j)
+        mbar_wait_bounded(full_bar(j % S::STAGES), (j / S::STAGES) & 1, nullptr, kDrainTimeoutNs);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------------------------------------------------- MMA issuer
+    constexpr uint32_t idesc = mma_idesc(IN_FP8 ? 0u : 1u, BN, S::BM);
+    int it = 0, local = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x, ++local) {
+      const int b = local & 1;
+      const uint32_t aph = (local >> 1) & 1;
+      if (!mbar_wait_bounded(tempty_bar(b), aph ^ 1u, abort_flag, p.timeout_ns)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(b * BN);
+      for (int kb = 0; kb < num_kb; ++kb, ++it) {
+        const int s = it % S::STAGES;
+        const uint32_t ph = (it / S::STAGES) & 1;
+        if (!mbar_wait_bounded(full_bar(s), ph, abort_flag, p.timeout_ns)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(sA + s * S::A_BYTES);
+        const uint32_t b0 = smem_u32(sB + s * S::B_BYTES);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {  // 4 x 32 bytes of K per 128-byte row
+          const uint64_t ad = sw128_kmajor_desc(a0 + 32u * j);
+          const uint64_t bd = sw128_kmajor_desc(b0 + 32u * j);
+          const uint32_t acc = (kb | j) != 0 ? 1u : 0u;
+          if constexpr (IN_FP8)
+            tc_mma_f8(d_tmem, ad, bd, idesc, acc);
+          else
+            tc_mma_f16(d_tmem, ad, bd, idesc, acc);
+        }
+        tc_commit(empty_bar(s));  // stage s is free once these MMAs finish
+      }
+      if (!ok) break;
+      tc_commit(tfull_bar(b));  // accumulator b is complete
+    }
+    if (!ok) raise_abort(abort_flag, p.status);
+    tc_commit(mdone_bar);  // every MMA above has finished once this arrives
+    mbar_wait_bounded(mdone_bar, 0, nullptr, kDrainTimeoutNs);
+  } else if (warp >= 2) {
+    // ---------------------------------------------------------- epilogue
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int r_local = q * 32 + lane;
+    int local = 0;
+    for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++local) {
+      const int b = local & 1;
+      const uint32_t aph = (local >> 1) & 1;
+      bool ok = mbar_wait_bounded(tfull_bar(b), aph, abort_flag, p.timeout_ns);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        if (lane == 0) raise_abort(abort_flag, p.status);
+        break;
+      }
+      tc_fence_after();
+      const int m_blk = tile / num_n;
+      const int n_blk = tile % num_n;
+      const int row = m_blk * S::BM + r_local;
+      const bool row_ok = row < p.M;
+      const int n0 = n_blk * BN;
+      const uint32_t tbase = tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
+                             static_cast<uint32_t>(b * BN);
+      float h0 = 0.f, h1 = 0.f;
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        uint32_t v[32];
+        tmem_ld32(tbase + 32u * c, v);
+        tmem_wait_ld();
+        const int nc = n0 + 32 * c;
+        float x[32];
+        const float4* b4 = reinterpret_cast<const float4*>(p.bias + nc);
+#pragma unroll
+        for (int j4 = 0; j4 < 8; ++j4) {
+          const float4 bb = __ldg(b4 + j4);
+          float4 cs = make_float4(1.f, 1.f, 1.f, 1.f);
+          if (p.col_scale != nullptr) cs = __ldg(reinterpret_cast<const float4*>(p.col_scale + nc) + j4);
+          x[4 * j4 + 0] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 0]), cs.x, bb.x), 0.f);
+          x[4 * j4 + 1] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 1]), cs.y, bb.y), 0.f);
+          x[4 * j4 + 2] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 2]), cs.z, bb.z), 0.f);
+          x[4 * j4 + 3] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 3]), cs.w, bb.w), 0.f);
+        }
+        if (p.mode == 0) {
+          if (row_ok) {
+            if constexpr (OUT_FP8) {
+              uint8_t* dst = static_cast<uint8_t*>(p.out) + static_cast<size_t>(row) * p.ldo + nc;
+              const float os = p.out_scale;
+              uint4 w0, w1;
+              w0.x = pack_e4m3x4(x[0] * os, x[1] * os, x[2] * os, x[3] * os);
+              w0.y = pack_e4m3x4(x[4] * os, x[5] * os, x[6] * os, x[7] * os);
+              w0.z = pack_e4m3x4(x[8] * os, x[9] * os, x[10] * os, x[11] * os);
+              w0.w = pack_e4m3x4(x[12] * os, x[13] * os, x[14] * os, x[15] * os);
+              w1.x = pack_e4m3x4(x[16] * os, x[17] * os, x[18] * os, x[19] * os);
+              w1.y = pack_e4m3x4(x[20] * os, x[21] * os, x[22] * os, x[23] * os);
+              w1.z = pack_e4m3x4(x[24] * os, x[25] * os, x[26] * os, x[27] * os);
+              w1.w = pack_e4m3x4(x[28] * os, x[29] * os, x[30] * os, x[31] * os);
+              reinterpret_cast<uint4*>(dst)[0] = w0;
+              reinterpret_cast<uint4*>(dst)[1] = w1;
+            } else {
+              __nv_bfloat16* dst =
+                  static_cast<__nv_bfloat16*>(p.out) + static_cast<size_t>(row) * p.ldo + nc;
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                uint4 w;
+                w.x = pack_bf16x2(x[8 * k + 0], x[8 * k + 1]);
+                w.y = pack_bf16x2(x[8 * k + 2], x[8 * k + 3]);
+                w.z = pack_bf16x2(x[8 * k + 4], x[8 * k + 5]);
+                w.w = pack_bf16x2(x[8 * k + 6], x[8 * k + 7]);
+                reinterpret_cast<uint4*>(dst)[k] = w;
+              }
+            }
+          }
+        } else {
+          const float4* w0 = reinterpret_cast<const float4*>(p.head_w + nc);
+          const float4* w1 = reinterpret_cast<const float4*>(p.head_w + p.N + nc);
+#pragma unroll
+          for (int j4 = 0; j4 < 8; ++j4) {
+            const float4 a = __ldg(w0 + j4);
+            const float4 bb = __ldg(w1 + j4);
+            h0 = fmaf(x[4 * j4 + 0], a.x, h0);
+            h0 = fmaf(x[4 * j4 + 1], a.y, h0);
+            h0 = fmaf(x[4 * j4 + 2], a.z, h0);
+            h0 = fmaf(x[4 * j4 + 3], a.w, h0);
+            h1 = fmaf(x[4 * j4 + 0], bb.x, h1);
+            h1 = fmaf(x[4 * j4 + 1], bb.y, h1);
+            h1 = fmaf(x[4 * j4 + 2], bb.z, h1);
+            h1 = fmaf(x[4 * j4 + 3], bb.w, h1);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty_bar(b));
+      if (p.mode != 0 && row_ok)
+        p.head_part[static_cast<size_t>(n_blk) * p.M + row] = make_float2(h0, h1);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem_base, S::TMEM_COLS);
+  }
+}
+
+template <int BN, bool IN_FP8, bool OUT_FP8>
+cudaError_t launch_one(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcGemmParams& p,
+                       int grid, cudaStream_t s) {
+  using S = TcShape<BN, IN_FP8>;
+  auto kern = tc_gemm_kernel<BN, IN_FP8, OUT_FP8>;
+  // applies to the current device; cheap enough to repeat on every launch
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, 192, S::SMEM_BYTES, s>>>(tmA, tmB, p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int tc_gemm_smem_bytes(int bn, bool in_fp8) {
+  if (bn == 256) return in_fp8 ? TcShape<256, true>::SMEM_BYTES : TcShape<256, false>::SMEM_BYTES;
+  return in_fp8 ? TcShape<128, true>::SMEM_BYTES : TcShape<128, false>::SMEM_BYTES;
+}
+
+cudaError_t launch_tc_gemm(int bn, bool in_fp8, bool out_fp8, const CUtensorMap& tmA,
+                           const CUtensorMap& tmB, const TcGemmParams& p, int grid,
+                           cudaStream_t s) {
+  if (bn == 256) {
+    if (in_fp8) return out_fp8 ? launch_one<256, true, true>(tmA, tmB, p, grid, s)
+                               : launch_one<256, true, false>(tmA, tmB, p, grid, s);
+    return out_fp8 ? launch_one<256, false, true>(tmA, tmB, p, grid, s)
+                   : launch_one<256, false, false>(tmA, tmB, p, grid, s);
+  }
+  if (bn == 128) {
+    if (in_fp8) return out_fp8 ? launch_one<128, true, true>(tmA, tmB, p, grid, s)
+                               : launch_one<128, true, false>(tmA, tmB, p, grid, s);
+    return out_fp8 ? launch_one<128, false, true>(tmA, tmB, p, grid, s)
+                   : launch_one<128, false, false>(tmA, tmB, p, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace ddf

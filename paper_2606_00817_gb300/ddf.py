@@ -1,0 +1,260 @@
+"""ctypes binding of libddf.so, the C ABI in include/ddf.h.
+
+Functions named ``ddf_*`` mirror the C entry points one to one and only
+marshal arguments (torch tensors or integer addresses become pointers, numpy
+arrays become host pointers). ``DDF`` is a small convenience wrapper that
+allocates outputs as torch tensors. Every step of the query runs in the CUDA
+library; if the library is missing this module raises instead of computing
+anything itself.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libddf.so")
+
+DDF_FP32, DDF_BF16, DDF_FP8_E4M3 = 0, 1, 2
+PRECISIONS = {"fp32": DDF_FP32, "bf16": DDF_BF16, "fp8": DDF_FP8_E4M3}
+STATUS = {0: "DDF_OK", 1: "DDF_ERR_INVALID_ARG", 2: "DDF_ERR_CUDA", 3: "DDF_ERR_OOM",
+          4: "DDF_ERR_BAD_WEIGHTS", 5: "DDF_ERR_UNSUPPORTED", 6: "DDF_ERR_TIMEOUT"}
+PROFILE_CLASSES = ("encode", "gemm", "head", "other")
+
+# every entry point of include/ddf.h: name -> (restype, argtypes)
+_vp, _i32, _i64, _u64, _sz = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_size_t
+_RAYS = C.POINTER(C.c_void_p)
+
+
+class Config(C.Structure):
+    _fields_ = [("octaves", C.c_int32), ("width", C.c_int32), ("hidden_layers", C.c_int32),
+                ("precision", C.c_int32), ("device", C.c_int32)]
+
+
+SIGNATURES = {
+    "ddf_param_count": (_sz, [C.POINTER(Config)]),
+    "ddf_create": (C.c_int, [C.POINTER(Config), C.POINTER(_vp)]),
+    "ddf_destroy": (C.c_int, [_vp]),
+    "ddf_last_error": (C.c_char_p, []),
+    "ddf_load_weights": (C.c_int, [_vp, _vp, _sz]),
+    "ddf_get_weights": (C.c_int, [_vp, _vp, _sz]),
+    "ddf_set_act_scales": (C.c_int, [_vp, _vp, _i32]),
+    "ddf_query_rays": (C.c_int, [_vp, _RAYS, _i64, _vp, _vp, _vp]),
+    "ddf_query_shadow": (C.c_int, [_vp, _RAYS, _i64, _vp, _vp, _vp, _vp, _vp]),
+    "ddf_query_rays_host": (C.c_int, [_vp, _RAYS, _i64, _vp, _vp]),
+    "ddf_check_status": (C.c_int, [_vp, C.POINTER(C.c_uint32)]),
+    "ddf_set_timeout_ns": (C.c_int, [_vp, _u64]),
+    "ddf_set_chunk_rays": (C.c_int, [_vp, _i64]),
+    "ddf_profile_enable": (C.c_int, [_vp, _i32]),
+    "ddf_profile_read": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+}
+
+_LIB = None
+
+
+class DDFError(RuntimeError):
+    def __init__(self, fn, status, msg):
+        super().__init__(f"{fn} -> {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib():
+    """Loads libddf.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "paper_2606_00817_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _call(name, *args):
+    st = getattr(lib(), name)(*args)
+    if st != 0:
+        raise DDFError(name, st, lib().ddf_last_error().decode())
+
+
+def _ptr(x):
+    """Address of a torch tensor / numpy array / integer / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy buffers must be contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _rays(rays):
+    if len(rays) != 6:
+        raise ValueError("rays must hold 6 arrays (ox, oy, oz, dx, dy, dz)")
+    arr = (C.c_void_p * 6)(*[_ptr(r) for r in rays])
+    return C.cast(arr, _RAYS), arr
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def make_config(octaves, width, hidden_layers, precision="bf16", device=0) -> Config:
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return Config(int(octaves), int(width), int(hidden_layers), p, int(device))
+
+
+# ----------------------------------------------------------- 1:1 entry points
+
+def ddf_param_count(cfg: Config) -> int:
+    return int(lib().ddf_param_count(C.byref(cfg)))
+
+
+def ddf_create(cfg: Config) -> int:
+    h = C.c_void_p()
+    _call("ddf_create", C.byref(cfg), C.byref(h))
+    return h.value
+
+
+def ddf_destroy(h) -> None:
+    _call("ddf_destroy", h)
+
+
+def ddf_last_error() -> str:
+    return lib().ddf_last_error().decode()
+
+
+def ddf_load_weights(h, blob: np.ndarray) -> None:
+    blob = np.ascontiguousarray(blob, dtype=np.float32)
+    _call("ddf_load_weights", h, blob.ctypes.data, blob.size)
+
+
+def ddf_get_weights(h, n: int) -> np.ndarray:
+    out = np.empty(n, np.float32)
+    _call("ddf_get_weights", h, out.ctypes.data, n)
+    return out
+
+
+def ddf_set_act_scales(h, scales) -> None:
+    s = np.ascontiguousarray(scales, dtype=np.float32)
+    _call("ddf_set_act_scales", h, s.ctypes.data if s.size else None, s.size)
+
+
+def ddf_query_rays(h, rays, n, out_t, out_vis, stream=None) -> None:
+    rp, keep = _rays(rays)
+    _call("ddf_query_rays", h, rp, int(n), _ptr(out_t), _ptr(out_vis), _stream(stream))
+
+
+def ddf_query_shadow(h, rays, n, light, out_t, out_vis, out_occluded, stream=None) -> None:
+    rp, keep = _rays(rays)
+    lt = (C.c_float * 3)(*[float(v) for v in light])
+    _call("ddf_query_shadow", h, rp, int(n), C.addressof(lt), _ptr(out_t), _ptr(out_vis),
+          _ptr(out_occluded), _stream(stream))
+
+
+def ddf_query_rays_host(h, rays, n, out_t, out_vis) -> None:
+    rp, keep = _rays(rays)
+    _call("ddf_query_rays_host", h, rp, int(n), _ptr(out_t), _ptr(out_vis))
+
+
+def ddf_check_status(h) -> int:
+    v = C.c_uint32()
+    _call("ddf_check_status", h, C.byref(v))
+    return int(v.value)
+
+
+def ddf_set_timeout_ns(h, ns: int) -> None:
+    _call("ddf_set_timeout_ns", h, int(ns))
+
+
+def ddf_set_chunk_rays(h, chunk: int) -> None:
+    _call("ddf_set_chunk_rays", h, int(chunk))
+
+
+def ddf_profile_enable(h, on: bool) -> None:
+    _call("ddf_profile_enable", h, 1 if on else 0)
+
+
+def ddf_profile_read(h):
+    ms = (C.c_double * 4)()
+    n = (C.c_int64 * 4)()
+    _call("ddf_profile_read", h, ms, n)
+    return {k: (ms[i], n[i]) for i, k in enumerate(PROFILE_CLASSES)}
+
+
+# ----------------------------------------------------------- convenience
+
+class DDF:
+    """Owns one library handle; queries take and return torch CUDA tensors."""
+
+    def __init__(self, octaves, width, hidden_layers, precision="bf16", device=0):
+        self.cfg = make_config(octaves, width, hidden_layers, precision, device)
+        self.device = device
+        self.h = ddf_create(self.cfg)
+        self.n_params = ddf_param_count(self.cfg)
+
+    def close(self):
+        if self.h:
+            ddf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, blob, act_scales=None):
+        ddf_load_weights(self.h, blob)
+        if act_scales is not None:
+            ddf_set_act_scales(self.h, act_scales)
+
+    def _check(self, rays):
+        import torch
+        for r in rays:
+            if not (r.is_cuda and r.dtype == torch.float32 and r.is_contiguous()):
+                raise ValueError("rays must be contiguous float32 CUDA tensors")
+        n = rays[0].numel()
+        if any(r.numel() != n for r in rays):
+            raise ValueError("ray arrays differ in length")
+        return n
+
+    def query(self, rays, stream=None):
+        import torch
+        n = self._check(rays)
+        t = torch.empty(n, dtype=torch.float32, device=rays[0].device)
+        v = torch.empty_like(t)
+        ddf_query_rays(self.h, rays, n, t, v, stream or torch.cuda.current_stream(rays[0].device))
+        return t, v
+
+    def shadow(self, rays, light, stream=None):
+        import torch
+        n = self._check(rays)
+        t = torch.empty(n, dtype=torch.float32, device=rays[0].device)
+        v = torch.empty_like(t)
+        occ = torch.empty(n, dtype=torch.uint8, device=rays[0].device)
+        ddf_query_shadow(self.h, rays, n, light, t, v, occ,
+                         stream or torch.cuda.current_stream(rays[0].device))
+        return t, v, occ
+
+    def query_host(self, rays_np, out_t=None, out_vis=None):
+        n = int(rays_np[0].shape[0])
+        out_t = np.empty(n, np.float32) if out_t is None else out_t
+        out_vis = np.empty(n, np.float32) if out_vis is None else out_vis
+        ddf_query_rays_host(self.h, rays_np, n, out_t, out_vis)
+        return out_t, out_vis

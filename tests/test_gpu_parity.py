@@ -1,0 +1,211 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Bounds (|t_gpu - t_ref| and |vis_gpu - vis_ref|, relative to max(1, |ref|)):
+  * FP32 path vs the exact oracle: 1e-4 on every ray.
+  * bf16 / e4m3 paths vs the oracle emulating the same roundings: the two
+    differ only by FP32 accumulation order, which can move an activation across
+    a rounding boundary (one bf16 ulp = 2^-8 relative, one e4m3 ulp = 2^-3);
+    bounds max 2e-3 / mean 2e-4 (bf16) and max 1e-2 / mean 1e-3 (e4m3).
+  * bf16 / e4m3 paths vs the exact oracle: mean |dt| <= 5e-3, max <= 5e-2
+    (bf16) and mean <= 2e-2, max <= 0.2 (e4m3).
+"""
+import numpy as np
+import pytest
+
+from oracle import ddf_oracle as O
+from paper_2606_00817_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+SMALL = (6, 128, 4)      # 78 -> 128 x4 -> 2
+PAPER = (10, 1280, 8)    # 126 -> 1280 x8 -> 2
+LIGHT = (3.0, 3.0, 3.0)
+BOUNDS = {"bf16": (2e-3, 2e-4), "fp8": (1e-2, 1e-3)}
+EXACT_BOUNDS = {"bf16": (5e-2, 5e-3), "fp8": (0.2, 2e-2)}
+
+
+@pytest.fixture(scope="module")
+def torch_cuda(cuda_lib):
+    import torch
+    return torch
+
+
+def _dev(torch, rays):
+    return [torch.from_numpy(a).cuda() for a in rays.soa()]
+
+
+def _make(net, prec, blob, scales=None, chunk=None):
+    from paper_2606_00817_gb300 import ddf
+    m = ddf.DDF(*net, precision=prec)
+    m.load(blob, scales if prec == "fp8" else None)
+    if chunk:
+        ddf.ddf_set_chunk_rays(m.h, chunk)
+    return m
+
+
+def _query(torch, m, rays):
+    t, v = m.query(_dev(torch, rays))
+    torch.cuda.synchronize()
+    return t.cpu().numpy().astype(np.float64), v.cpu().numpy().astype(np.float64)
+
+
+def _rel(a, b):
+    return np.abs(a - b) / np.maximum(1.0, np.abs(b))
+
+
+def _oracle(rays, blob, net, prec, scales=None):
+    return O.ddf_forward(rays.origins(), rays.dirs(), blob, *net, precision=prec, act_scales=scales)
+
+
+def _check_reduced(t, v, rays, blob, net, prec, scales):
+    emu = _oracle(rays, blob, net, prec, scales)
+    mx, mean = BOUNDS[prec]
+    for g, r in ((t, emu["t"]), (v, emu["vis"])):
+        e = _rel(g, r)
+        assert e.max() <= mx and e.mean() <= mean, (prec, e.max(), e.mean())
+    ex = _oracle(rays, blob, net, "exact")
+    dt = np.abs(t - ex["t"])
+    mx, mean = EXACT_BOUNDS[prec]
+    assert dt.max() <= mx and dt.mean() <= mean, (prec, dt.max(), dt.mean())
+
+
+def _scales(blob, net, seed=99):
+    cal = I.uniform_rays(512, seed=seed)
+    return O.calibrate_act_scales(cal.origins(), cal.dirs(), blob, *net)
+
+
+@pytest.mark.parametrize("n", [1, 127, 129, 16384])
+def test_fp32_small_net_matches_exact_oracle(torch_cuda, n):
+    blob = I.xavier_blob(I.NetShape(*SMALL))
+    rays = I.uniform_rays(n, seed=1)
+    t, v = _query(torch_cuda, _make(SMALL, "fp32", blob), rays)
+    ex = _oracle(rays, blob, SMALL, "exact")
+    assert _rel(t, ex["t"]).max() <= 1e-4
+    assert _rel(v, ex["vis"]).max() <= 1e-4
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+@pytest.mark.parametrize("n", [1, 127, 129, 16384])
+def test_reduced_small_net_matches_emulating_oracle(torch_cuda, prec, n):
+    blob = I.xavier_blob(I.NetShape(*SMALL))
+    sc = _scales(blob, SMALL)
+    rays = I.uniform_rays(n, seed=2)
+    t, v = _query(torch_cuda, _make(SMALL, prec, blob, sc), rays)
+    _check_reduced(t, v, rays, blob, SMALL, prec, sc)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8"])
+def test_paper_sized_net(torch_cuda, prec):
+    blob = I.xavier_blob(I.NetShape(*PAPER))
+    scene = I.random_scene(64, 0, seed=0)
+    rays = I.shadow_rays(scene, 1037, LIGHT, seed=3)   # 8 full row tiles + a ragged one
+    sc = _scales(blob, PAPER)
+    t, v = _query(torch_cuda, _make(PAPER, prec, blob, sc), rays)
+    if prec == "fp32":
+        ex = _oracle(rays, blob, PAPER, "exact")
+        assert _rel(t, ex["t"]).max() <= 1e-4
+        assert _rel(v, ex["vis"]).max() <= 1e-4
+    else:
+        _check_reduced(t, v, rays, blob, PAPER, prec, sc)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_chunking_does_not_change_results(torch_cuda, prec):
+    blob = I.xavier_blob(I.NetShape(*SMALL))
+    rays = I.uniform_rays(1000, seed=4)
+    a = _query(torch_cuda, _make(SMALL, prec, blob), rays)
+    b = _query(torch_cuda, _make(SMALL, prec, blob, chunk=128), rays)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_shadow_decisions_match_oracle(torch_cuda):
+    torch = torch_cuda
+    blob = I.xavier_blob(I.NetShape(*SMALL))
+    scene = I.random_scene(64, 0, seed=0)
+    rays = I.shadow_rays(scene, 3000, LIGHT, seed=5)
+    m = _make(SMALL, "bf16", blob)
+    t, v, occ = m.shadow(_dev(torch, rays), LIGHT)
+    torch.cuda.synchronize()
+    emu = _oracle(rays, blob, SMALL, "bf16")
+    ref = O.shadow(emu["t"], emu["z"][:, 1], rays.origins(), LIGHT)
+    dist = np.linalg.norm(np.array(LIGHT) - rays.origins().astype(np.float64), axis=1)
+    clear = (np.abs(emu["z"][:, 1]) > 1e-3) & (np.abs(emu["t"] - dist) > 1e-3)
+    assert clear.mean() > 0.9
+    assert np.array_equal(occ.cpu().numpy().astype(bool)[clear], ref[clear])
+
+
+def test_host_buffer_query_matches_device_query(torch_cuda):
+    from paper_2606_00817_gb300 import ddf
+    blob = I.xavier_blob(I.NetShape(*SMALL))
+    rays = I.uniform_rays(5000, seed=6)
+    m = _make(SMALL, "bf16", blob, chunk=1024)
+    t_d, v_d = _query(torch_cuda, m, rays)
+    t_h, v_h = m.query_host(rays.soa())
+    assert np.array_equal(t_h.astype(np.float64), t_d) and np.array_equal(v_h.astype(np.float64), v_d)
+    assert ddf.ddf_check_status(m.h) == 0
+
+
+def test_weights_round_trip_and_argument_errors(torch_cuda):
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    blob = I.xavier_blob(I.NetShape(*SMALL))
+    m = _make(SMALL, "bf16", blob)
+    assert np.array_equal(ddf.ddf_get_weights(m.h, blob.size), blob)
+    with pytest.raises(ddf.DDFError) as e:
+        ddf.ddf_load_weights(m.h, blob[:-1])
+    assert e.value.status == 4
+    bad = blob.copy()
+    bad[5] = np.nan
+    with pytest.raises(ddf.DDFError):
+        ddf.ddf_load_weights(m.h, bad)
+    rays = _dev(torch, I.uniform_rays(4))
+    with pytest.raises(ddf.DDFError) as e:
+        ddf.ddf_query_rays(m.h, rays, 4, None, None)
+    assert e.value.status == 1
+    ddf.ddf_query_rays(m.h, rays, 0, None, None)  # empty batch: no-op
+    f8 = ddf.DDF(*SMALL, precision="fp8")
+    f8.load(blob)
+    with pytest.raises(ddf.DDFError):
+        f8.query(rays)                            # e4m3 needs activation scales
+    with pytest.raises(ddf.DDFError):
+        ddf.ddf_set_act_scales(f8.h, [0.3, 0.5, 0.25])   # not powers of two
+    with pytest.raises(ddf.DDFError) as e:
+        ddf.DDF(6, 96, 4, precision="bf16")        # tensor cores need width % 128 == 0
+    assert e.value.status == 5
+
+
+def test_timeout_path_gives_up_cleanly_and_recovers(torch_cuda):
+    """A zero wait limit makes the pipelined kernel give up at its first wait
+    that is not already satisfied: the status word reports it, nothing traps,
+    and the next launch with the normal limit is correct."""
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    blob = I.xavier_blob(I.NetShape(*SMALL))
+    rays = I.uniform_rays(65536, seed=7)
+    m = _make(SMALL, "bf16", blob)
+    ddf.ddf_set_timeout_ns(m.h, 0)
+    m.query(_dev(torch, rays))
+    assert ddf.ddf_check_status(m.h) & 1
+    ddf.ddf_set_timeout_ns(m.h, 2_000_000_000)
+    t, v = _query(torch, m, rays.slice(0, 2048))
+    assert ddf.ddf_check_status(m.h) == 0
+    _check_reduced(t, v, rays.slice(0, 2048), blob, SMALL, "bf16", None)
+
+
+def test_full_size_shadow_workload_sampled(torch_cuda):
+    """The 4,194,304-ray shadow workload on the 8x1280 field, in the launch
+    configuration the benchmark times; 256 sampled rays against the oracle."""
+    torch = torch_cuda
+    blob = I.xavier_blob(I.NetShape(*PAPER))
+    scene = I.random_scene(64, 0, seed=0)
+    rays = I.shadow_rays(scene, 4_194_304, LIGHT, seed=0)
+    m = _make(PAPER, "bf16", blob)
+    t, v, occ = m.shadow(_dev(torch, rays), LIGHT)
+    torch.cuda.synchronize()
+    t = t.cpu().numpy().astype(np.float64)
+    v = v.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(t)) and np.all(np.isfinite(v))
+    idx = np.sort(np.random.default_rng(0).choice(rays.n, 256, replace=False))
+    idx = np.concatenate([idx, [0, rays.n - 1]])
+    sub = I.Rays(*[a[idx] for a in rays.soa()])
+    _check_reduced(t[idx], v[idx], sub, blob, PAPER, "bf16", None)
