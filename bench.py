@@ -1,0 +1,347 @@
+"""DDF query benchmark: rays/s of the bf16 tensor-core path on the paper-sized
+field over 4,194,304 synthetic shadow rays, next to the plain FP32 path on the
+same GPU, with accuracy against the FP64 oracle and the oracle's own CPU rate.
+
+Workload: field = sinusoidal encoding with 10 bands (126 inputs) + 8 ReLU
+layers of width 1280 + 2-output head (11,642,882 parameters, Xavier-uniform
+weights, seed 0); rays = points on a 64-sphere analytic scene (seed 0) offset
+1e-3 along the normal, aimed at a point light at (3,3,3). One step = one DDF
+evaluation of every ray plus the shadow decision (Sec. 3.3).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank evaluates its own 4,194,304 rays (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2606_00817_gb300 import inputs as I  # noqa: E402
+
+NET = (10, 1280, 8)
+LIGHT = (3.0, 3.0, 3.0)
+METRIC = "DDF rays/sec (BF16/FP8 vs plain FP32, same GPU) at stated |dt|; tensor-pipe %"
+WORKLOAD = ("shadow rays: 4,194,304 rays from a 64-sphere analytic scene toward a point light "
+            "at (3,3,3); DDF 126 -> 1280x8 -> 2 (L=10, ~11.6M params, Xavier)")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp8", "fp32"])
+    ap.add_argument("--rays", type=int, default=4_194_304)
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP32 comparison run")
+    ap.add_argument("--oracle-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.f.flush()
+
+    def summary(self):
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    rows.append((float(p[1]), float(p[2]), float(p[3]) if p[3] not in ("[N/A]", "N/A") else 0.0,
+                                 p[5], p[6], p[7], p[8]))
+                except ValueError:
+                    continue
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [r for r in rows if r[2] > 200.0] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in load for n, v in zip(names, r[3:]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(load), "power_w_max": max(r[2] for r in rows), "reasons": reasons}
+
+
+# ------------------------------------------------------------- oracle leg
+
+def oracle_sample(rays, blob, seconds):
+    """Times the FP64 oracle on a bounded prefix of the workload; returns
+    (rays/s, n, exact outputs)."""
+    from oracle import ddf_oracle as O
+    probe = rays.slice(0, 256)
+    t0 = time.perf_counter()
+    O.ddf_forward(probe.origins(), probe.dirs(), blob, *NET)
+    dt = time.perf_counter() - t0
+    n = int(min(rays.n, 65536, max(512, seconds / max(dt, 1e-6) * 256)))
+    n -= n % 256
+    sub = rays.slice(0, n)
+    t0 = time.perf_counter()
+    ref = O.ddf_forward(sub.origins(), sub.dirs(), blob, *NET)
+    el = time.perf_counter() - t0
+    return n / el, n, el, ref
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import ddf_oracle as O
+    blob = I.xavier_blob(I.NetShape(*NET))
+    scene = I.random_scene(64, 0, seed=0)
+    per_step = 4096
+    need = per_step * (args.steps + args.warmup)
+    rays = I.shadow_rays(scene, need, LIGHT, seed=0)
+    times = []
+    for i in range(args.warmup + args.steps):
+        sub = rays.slice(i * per_step, (i + 1) * per_step)
+        t0 = time.perf_counter()
+        out = O.ddf_forward(sub.origins(), sub.dirs(), blob, *NET)
+        O.shadow(out["t"], out["z"][:, 1], sub.origins(), LIGHT)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = per_step * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "rays_per_step": per_step, "impl": "FP64 CPU oracle (numpy)"},
+        "cpu_baseline": {"value": value, "unit": "rays/s", "cores": cores(), "kind": "oracle",
+                         "sample": f"{per_step} rays per step of the same shadow workload"},
+        "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- GPU leg
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    from paper_2606_00817_gb300 import ddf
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    R = args.rays
+    blob = I.xavier_blob(I.NetShape(*NET))
+    scene = I.random_scene(64, 0, seed=0)
+    rays = I.shadow_rays(scene, R, LIGHT, seed=rank)
+    d_rays = [torch.from_numpy(a).to(dev) for a in rays.soa()]
+    t = torch.empty(R, dtype=torch.float32, device=dev)
+    vis = torch.empty_like(t)
+    occ = torch.empty(R, dtype=torch.uint8, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    stream = torch.cuda.current_stream(dev)
+
+    m = ddf.DDF(*NET, precision=args.precision, device=local)
+    if args.precision == "fp8":
+        raise SystemExit("fp8 headline needs activation-scale calibration; use bf16")
+    m.load(blob)
+
+    def step():
+        ddf.ddf_query_shadow(m.h, d_rays, R, LIGHT, t, vis, occ, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES", "").replace(",", "").isdigit() else local
+    ddf.ddf_profile_enable(m.h, True)
+    ddf.ddf_profile_read(m.h)
+    with ClockSampler(gpu_index) as clk:
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()                  # L2 flush between steps, outside the step events
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    prof = ddf.ddf_profile_read(m.h)
+    ddf.ddf_profile_enable(m.h, False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if ws > 1:
+        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+        dist.barrier()
+    value = R * ws * args.steps / (total_ms / 1e3)
+    status = ddf.ddf_check_status(m.h)
+
+    # roofline of the dominant kernel (the tensor-core layer GEMM)
+    L_, W_, H_ = NET
+    d_in = 6 + 12 * L_
+    gemm_flops_step = 2.0 * R * (d_in * W_ + (H_ - 1) * W_ * W_)
+    g_ms, g_n = prof["gemm"]
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    peak = peaks.get("bf16_tflops_sustained")
+    peak_src = "measured (bf16_tflops_sustained)"
+    if peak is None:
+        peak, peak_src = 1700.0, "fallback (1.7 PFLOP/s sustained)"
+    achieved = gemm_flops_step * args.steps / (g_ms / 1e3) / 1e12 if g_ms > 0 else None
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "kernel": "tc_gemm_kernel (bf16 layer GEMM, all 8 layers)",
+                "flops_per_launch": gemm_flops_step * args.steps / g_n if g_n else None,
+                "avg_launch_ms": g_ms / g_n if g_n else None, "peak_source": peak_src,
+                "kernel_time_share": g_ms / sum(v[0] for v in prof.values())}
+    launches = int(sum(v[1] for v in prof.values()))
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    h_rays = [torch.from_numpy(a).pin_memory() for a in rays.soa()]
+    h_t = torch.empty(R, dtype=torch.float32).pin_memory()
+    h_v = torch.empty(R, dtype=torch.float32).pin_memory()
+    h_o = torch.empty(R, dtype=torch.uint8).pin_memory()
+    ddf.ddf_query_shadow_host(m.h, h_rays, R, LIGHT, h_t, h_v, h_o)
+    e2e_steps = max(3, min(args.steps, 5))
+    if ws > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ddf.ddf_query_shadow_host(m.h, h_rays, R, LIGHT, h_t, h_v, h_o)
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = {"value": R * ws * e2e_steps / e2e_s, "unit": "rays/s",
+           "h2d_bytes_per_step": 24 * R, "d2h_bytes_per_step": 9 * R,
+           "api": "ddf_query_shadow_host (pinned host buffers, copies overlapped with compute)"}
+
+    compare = {}
+    if not args.no_compare and args.precision != "fp32":
+        f32 = ddf.DDF(*NET, precision="fp32", device=local)
+        f32.load(blob)
+        t32 = torch.empty_like(t)
+        v32 = torch.empty_like(t)
+        ddf.ddf_query_rays(f32.h, d_rays, R, t32, v32, stream)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ddf.ddf_query_rays(f32.h, d_rays, R, t32, v32, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        f32_ms = a.elapsed_time(b)
+        compare = {"fp32_rays_per_s": R / (f32_ms / 1e3), "fp32_ms_per_step": f32_ms,
+                   "speedup_vs_fp32": (R / (f32_ms / 1e3)) and value / ws / (R / (f32_ms / 1e3)),
+                   "bf16_vs_fp32_max_abs_dt": float((t - t32).abs().max().item())}
+        f32.close()
+
+    # CPU baseline (the FP64 oracle on a bounded prefix) + accuracy of the GPU outputs on it
+    cpu = None
+    acc = None
+    if rank == 0:
+        o_rate, o_n, o_el, ref = oracle_sample(rays, blob, args.oracle_seconds)
+        gt = t[:o_n].double().cpu().numpy()
+        gv = vis[:o_n].double().cpu().numpy()
+        dt = np.abs(gt - ref["t"])
+        z1 = ref["z"][:, 1]
+        flip = float(np.mean((gv > 0.5) != (z1 > 0)))
+        acc = {"rays_checked": o_n, "max_abs_dt": float(dt.max()), "mean_abs_dt": float(dt.mean()),
+               "max_abs_dvis": float(np.abs(gv - ref["vis"]).max()), "flip_rate": flip,
+               "near_tie_frac": float(np.mean(np.abs(z1) < 1e-3)),
+               "bounds": {"mean_abs_dt": 5e-3, "max_abs_dt": 5e-2, "flip_rate": 5e-3},
+               "reference": "FP64 oracle, exact arithmetic"}
+        cpu = {"value": o_rate, "unit": "rays/s", "cores": cores(), "kind": "oracle",
+               "sample": f"first {o_n} rays of the same workload ({o_el:.1f} s, numpy FP64)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rays_per_gpu": R, "precision": args.precision,
+                       "parallelism": f"rays sharded, {ws} GPU(s), no data-path collective",
+                       "l2": "512 MiB buffer written between timed steps (L2 flush)",
+                       "timing": "CUDA events per step on the launching stream",
+                       "wall_s_timed_region": wall},
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(), "e2e": e2e,
+            "gpu_launches": launches, "accuracy": acc, "compare": compare,
+            "kernel_ms_by_class": {k: v[0] for k, v in prof.items()},
+            "device_status": status,
+        }
+        print(json.dumps(line), flush=True)
+    m.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

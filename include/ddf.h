@@ -131,6 +131,13 @@ ddf_status ddf_query_shadow(ddf_handle h, const float* const rays[6], int64_t n,
 ddf_status ddf_query_rays_host(ddf_handle h, const float* const rays[6], int64_t n,
                                float* out_t, float* out_vis);
 
+/* Shadow query with every buffer in HOST memory (light: 3 host floats,
+ * out_occluded: n host bytes); pipelined and synchronous like
+ * ddf_query_rays_host. */
+ddf_status ddf_query_shadow_host(ddf_handle h, const float* const rays[6], int64_t n,
+                                 const float light[3], float* out_t, float* out_vis,
+                                 uint8_t* out_occluded);
+
 /* Device status word of the handle: bit 0 = a pipeline wait timed out,
  * bit 1 = a scheduler wait timed out. Synchronises the device, stores the
  * word in *out and clears it. */

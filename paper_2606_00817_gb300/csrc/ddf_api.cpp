@@ -137,6 +137,7 @@ struct ddf_s {
   float* hp_rays[2][6] = {};
   float* hp_t[2] = {};
   float* hp_v[2] = {};
+  uint8_t* hp_occ[2] = {};
   int64_t hp_rows = 0;
   cudaEvent_t ev_in[2] = {}, ev_comp[2] = {};
 };
@@ -413,6 +414,7 @@ ddf_status ddf_destroy(ddf_handle h) {
       if (h->hp_rays[b][c]) cudaFree(h->hp_rays[b][c]);
     if (h->hp_t[b]) cudaFree(h->hp_t[b]);
     if (h->hp_v[b]) cudaFree(h->hp_v[b]);
+    if (h->hp_occ[b]) cudaFree(h->hp_occ[b]);
     if (h->ev_in[b]) cudaEventDestroy(h->ev_in[b]);
     if (h->ev_comp[b]) cudaEventDestroy(h->ev_comp[b]);
   }
@@ -574,15 +576,13 @@ ddf_status ddf_query_shadow(ddf_handle h, const float* const rays[6], int64_t n,
   return run_query(h, rays, n, o, static_cast<cudaStream_t>(stream));
 }
 
-ddf_status ddf_query_rays_host(ddf_handle h, const float* const rays[6], int64_t n, float* out_t,
-                               float* out_vis) {
-  ddf_status s = check_ready(h);
-  if (s != DDF_OK) return s;
-  if ((s = check_rays(rays, n)) != DDF_OK) return s;
-  if (n > 0 && (out_t == nullptr || out_vis == nullptr))
-    return fail(DDF_ERR_INVALID_ARG, "output pointer is NULL");
-  if (n == 0) return DDF_OK;
-  DeviceGuard g(h->cfg.device);
+namespace {
+
+// Host-buffer pipeline: chunk i's rays are copied in on a copy stream while
+// chunk i-1 is evaluated on a compute stream; results go back on the copy
+// stream once the compute stream has finished the chunk.
+ddf_status host_pipeline(ddf_s* h, const float* const rays[6], int64_t n, const float* light,
+                         float* out_t, float* out_vis, uint8_t* out_occ) {
   const int64_t C = std::min<int64_t>(h->chunk, n);
   if (h->s_copy == nullptr) {
     DDF_CK(cudaStreamCreateWithFlags(&h->s_copy, cudaStreamNonBlocking));
@@ -600,17 +600,21 @@ ddf_status ddf_query_rays_host(ddf_handle h, const float* const rays[6], int64_t
       }
       cudaFree(h->hp_t[b]);
       cudaFree(h->hp_v[b]);
+      cudaFree(h->hp_occ[b]);
       h->hp_t[b] = h->hp_v[b] = nullptr;
+      h->hp_occ[b] = nullptr;
     }
     h->hp_rows = 0;
     for (int b = 0; b < 2; ++b) {
       for (int c = 0; c < 6; ++c) DDF_CK(cudaMalloc(&h->hp_rays[b][c], C * sizeof(float)));
       DDF_CK(cudaMalloc(&h->hp_t[b], C * sizeof(float)));
       DDF_CK(cudaMalloc(&h->hp_v[b], C * sizeof(float)));
+      DDF_CK(cudaMalloc(&h->hp_occ[b], C));
     }
     h->hp_rows = C;
   }
-  if ((s = ensure_workspace(h, C)) != DDF_OK) return s;
+  ddf_status s = ensure_workspace(h, C);
+  if (s != DDF_OK) return s;
   const int64_t nchunks = (n + C - 1) / C;
   auto copy_in = [&](int64_t i) -> ddf_status {
     const int b = static_cast<int>(i & 1);
@@ -630,6 +634,10 @@ ddf_status ddf_query_rays_host(ddf_handle h, const float* const rays[6], int64_t
     ddf::HeadOut o{};
     o.t = h->hp_t[b];
     o.vis = h->hp_v[b];
+    if (light != nullptr) {
+      o.occluded = h->hp_occ[b];
+      for (int k = 0; k < 3; ++k) o.light[k] = light[k];
+    }
     const float* rp[6];
     for (int c = 0; c < 6; ++c) rp[c] = h->hp_rays[b][c];
     if ((s = run_query(h, rp, m, o, h->s_comp)) != DDF_OK) return s;
@@ -639,10 +647,40 @@ ddf_status ddf_query_rays_host(ddf_handle h, const float* const rays[6], int64_t
                            h->s_copy));
     DDF_CK(cudaMemcpyAsync(out_vis + off, h->hp_v[b], m * sizeof(float), cudaMemcpyDeviceToHost,
                            h->s_copy));
+    if (light != nullptr)
+      DDF_CK(cudaMemcpyAsync(out_occ + off, h->hp_occ[b], m, cudaMemcpyDeviceToHost, h->s_copy));
   }
   DDF_CK(cudaStreamSynchronize(h->s_copy));
   DDF_CK(cudaStreamSynchronize(h->s_comp));
   return DDF_OK;
+}
+
+}  // namespace
+
+ddf_status ddf_query_rays_host(ddf_handle h, const float* const rays[6], int64_t n, float* out_t,
+                               float* out_vis) {
+  ddf_status s = check_ready(h);
+  if (s != DDF_OK) return s;
+  if ((s = check_rays(rays, n)) != DDF_OK) return s;
+  if (n > 0 && (out_t == nullptr || out_vis == nullptr))
+    return fail(DDF_ERR_INVALID_ARG, "output pointer is NULL");
+  if (n == 0) return DDF_OK;
+  DeviceGuard g(h->cfg.device);
+  return host_pipeline(h, rays, n, nullptr, out_t, out_vis, nullptr);
+}
+
+ddf_status ddf_query_shadow_host(ddf_handle h, const float* const rays[6], int64_t n,
+                                 const float light[3], float* out_t, float* out_vis,
+                                 uint8_t* out_occluded) {
+  ddf_status s = check_ready(h);
+  if (s != DDF_OK) return s;
+  if ((s = check_rays(rays, n)) != DDF_OK) return s;
+  if (light == nullptr) return fail(DDF_ERR_INVALID_ARG, "light is NULL");
+  if (n > 0 && (out_t == nullptr || out_vis == nullptr || out_occluded == nullptr))
+    return fail(DDF_ERR_INVALID_ARG, "output pointer is NULL");
+  if (n == 0) return DDF_OK;
+  DeviceGuard g(h->cfg.device);
+  return host_pipeline(h, rays, n, light, out_t, out_vis, out_occluded);
 }
 
 ddf_status ddf_check_status(ddf_handle h, uint32_t* out) {
