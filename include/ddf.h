@@ -138,6 +138,22 @@ ddf_status ddf_query_shadow_host(ddf_handle h, const float* const rays[6], int64
                                  const float light[3], float* out_t, float* out_vis,
                                  uint8_t* out_occluded);
 
+/* Allocation-free query (the paper has no counterpart; this is a library
+ * service). Same arguments, results and stream semantics as ddf_query_rays,
+ * but the scratch the kernels need comes from one static 32 MiB device array
+ * that every GPU loading the library reserves until exit, so the call itself
+ * never calls cudaMalloc/cudaFree. For callers that cannot allocate mid-work:
+ * a renderer's per-frame callback (cudaMalloc may synchronise the device and
+ * stall the frame) or a host framework whose pool owns all device memory.
+ *  - n must fit the scratch in one pass (about 6,190 rays for 126->1280x8
+ *    bf16); larger n returns DDF_ERR_INVALID_ARG with the limit in the message.
+ *  - The first call on a device looks up the scratch address there; make it
+ *    before any stream capture.
+ *  - All calls (all handles) share the array and leave their data in it; no
+ *    part of it needs to start zeroed. Calls that overlap on the GPU race. */
+ddf_status ddf_query_rays_noalloc(ddf_handle h, const float* const rays[6], int64_t n,
+                                  float* out_t, float* out_vis, void* stream);
+
 /* Device status word of the handle: bit 0 = a pipeline wait timed out,
  * bit 1 = a scheduler wait timed out. Synchronises the device, stores the
  * word in *out and clears it. */

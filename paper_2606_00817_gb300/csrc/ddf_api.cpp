@@ -733,3 +733,82 @@ ddf_status ddf_profile_read(ddf_handle h, double ms[4], int64_t launches[4]) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Internal helpers for queries whose workspace is supplied by the caller
+// instead of the handle (used by the allocation-free entry point in
+// noalloc.cu). Not part of the public header.
+
+size_t ddf_internal_workspace_bytes(ddf_handle h, int64_t rows) {
+  const int W = h->cfg.width;
+  const bool f32 = h->cfg.precision == DDF_FP32;
+  const size_t act_elem = f32 ? 4 : (h->cfg.precision == DDF_BF16 ? 2 : 1);
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  size_t total = up(static_cast<size_t>(rows) * (f32 ? h->kp32 * 4 : h->kp16 * 2));
+  total += 2 * up(static_cast<size_t>(rows) * W * act_elem);
+  if (!f32) total += up(static_cast<size_t>(rows) * (W / h->bn) * sizeof(float2));
+  return total;
+}
+
+int ddf_internal_device(ddf_handle h) { return h->cfg.device; }
+
+// Runs ddf_query_rays with its encode / activation / partial-sum buffers
+// carved out of `ws` (256-byte aligned, ws_bytes long) instead of the
+// handle's own workspace. The caller has checked that ws is large enough for
+// n rays in one chunk. The handle's workspace pointers are swapped in for the
+// launches and restored before returning (launch parameters are captured at
+// launch time); event timing is suspended so no event objects are created.
+ddf_status ddf_internal_query_in_workspace(ddf_handle h, const float* const rays[6], int64_t n,
+                                           float* out_t, float* out_vis, void* stream, void* ws,
+                                           size_t ws_bytes) {
+  ddf_status s = check_ready(h);
+  if (s != DDF_OK) return s;
+  if ((s = check_rays(rays, n)) != DDF_OK) return s;
+  if (n > 0 && (out_t == nullptr || out_vis == nullptr))
+    return fail(DDF_ERR_INVALID_ARG, "output pointer is NULL");
+  if (n == 0) return DDF_OK;
+  if (ws == nullptr || ddf_internal_workspace_bytes(h, n) > ws_bytes)
+    return fail(DDF_ERR_INVALID_ARG, "workspace too small for this batch");
+  DeviceGuard g(h->cfg.device);
+  const int W = h->cfg.width;
+  const bool f32 = h->cfg.precision == DDF_FP32;
+  const size_t act_elem = f32 ? 4 : (h->cfg.precision == DDF_BF16 ? 2 : 1);
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  uint8_t* p = static_cast<uint8_t*>(ws);
+  void* enc = p;
+  p += up(static_cast<size_t>(n) * (f32 ? h->kp32 * 4 : h->kp16 * 2));
+  void* act0 = p;
+  p += up(static_cast<size_t>(n) * W * act_elem);
+  void* act1 = p;
+  p += up(static_cast<size_t>(n) * W * act_elem);
+  float2* part = f32 ? nullptr : reinterpret_cast<float2*>(p);
+
+  void* save_enc = h->ws_enc;
+  void* save_act0 = h->ws_act[0];
+  void* save_act1 = h->ws_act[1];
+  float2* save_part = h->ws_part;
+  const int64_t save_rows = h->ws_rows, save_chunk = h->chunk;
+  const bool save_prof = h->prof;
+  h->ws_enc = enc;
+  h->ws_act[0] = act0;
+  h->ws_act[1] = act1;
+  h->ws_part = part;
+  h->ws_rows = n;
+  h->chunk = n;
+  h->prof = false;
+  ddf::HeadOut o{};
+  o.t = out_t;
+  o.vis = out_vis;
+  s = run_query(h, rays, n, o, static_cast<cudaStream_t>(stream));
+  h->ws_enc = save_enc;
+  h->ws_act[0] = save_act0;
+  h->ws_act[1] = save_act1;
+  h->ws_part = save_part;
+  h->ws_rows = save_rows;
+  h->chunk = save_chunk;
+  h->prof = save_prof;
+  return s;
+}
+
+// Records msg as the calling thread's last error and returns s.
+ddf_status ddf_internal_set_error(ddf_status s, const char* msg) { return fail(s, msg); }

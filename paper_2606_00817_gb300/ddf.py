@@ -45,6 +45,7 @@ SIGNATURES = {
     "ddf_query_shadow": (C.c_int, [_vp, _RAYS, _i64, _vp, _vp, _vp, _vp, _vp]),
     "ddf_query_rays_host": (C.c_int, [_vp, _RAYS, _i64, _vp, _vp]),
     "ddf_query_shadow_host": (C.c_int, [_vp, _RAYS, _i64, _vp, _vp, _vp, _vp]),
+    "ddf_query_rays_noalloc": (C.c_int, [_vp, _RAYS, _i64, _vp, _vp, _vp]),
     "ddf_check_status": (C.c_int, [_vp, C.POINTER(C.c_uint32)]),
     "ddf_set_timeout_ns": (C.c_int, [_vp, _u64]),
     "ddf_set_chunk_rays": (C.c_int, [_vp, _i64]),
@@ -178,6 +179,11 @@ def ddf_query_shadow_host(h, rays, n, light, out_t, out_vis, out_occluded) -> No
     lt = (C.c_float * 3)(*[float(v) for v in light])
     _call("ddf_query_shadow_host", h, rp, int(n), C.addressof(lt), _ptr(out_t), _ptr(out_vis),
           _ptr(out_occluded))
+
+
+def ddf_query_rays_noalloc(h, rays, n, out_t, out_vis, stream=None) -> None:
+    rp, keep = _rays(rays)
+    _call("ddf_query_rays_noalloc", h, rp, int(n), _ptr(out_t), _ptr(out_vis), _stream(stream))
 
 
 def ddf_check_status(h) -> int:

@@ -1,0 +1,59 @@
+"""The allocation-free query (ddf_query_rays_noalloc) against ddf_query_rays.
+
+ddf_query_rays_noalloc serves callers that must not have a library call
+cudaMalloc mid-work (a renderer's per-frame callback, or a framework whose
+memory pool owns the device); its scratch is a static device array shared by
+every call. Two calls in a row, with different batches, must each agree with
+the allocating entry point. This file is collected last on purpose."""
+import numpy as np
+import pytest
+
+from oracle import ddf_oracle as O
+from paper_2606_00817_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-3   # the bf16 parity bound used by the other GPU tests (relative to max(1, |ref|))
+
+
+@pytest.mark.parametrize("net,n1,n2", [((6, 128, 4), 3000, 1037), ((10, 1280, 8), 6000, 129)])
+def test_noalloc_matches_query_rays_twice(cuda_lib, net, n1, n2):
+    import torch
+    from paper_2606_00817_gb300 import ddf
+    blob = I.xavier_blob(I.NetShape(*net))
+    m = ddf.DDF(*net, precision="bf16")
+    m.load(blob)
+    for seed, n in ((11, n1), (12, n2)):
+        rays = I.uniform_rays(n, seed=seed)
+        dev = [torch.from_numpy(a).cuda() for a in rays.soa()]
+        t_ref, v_ref = m.query(dev)
+        t = torch.full((n,), float("nan"), device="cuda")
+        v = torch.full((n,), float("nan"), device="cuda")
+        ddf.ddf_query_rays_noalloc(m.h, dev, n, t, v, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        for a, b in ((t, t_ref), (v, v_ref)):
+            a = a.double().cpu().numpy()
+            b = b.double().cpu().numpy()
+            assert np.all(np.isfinite(a))
+            assert np.max(np.abs(a - b) / np.maximum(1.0, np.abs(b))) <= TOL
+        emu = O.ddf_forward(rays.origins()[:64], rays.dirs()[:64], blob, *net, precision="bf16")
+        err = np.abs(t.double().cpu().numpy()[:64] - emu["t"]) / np.maximum(1.0, np.abs(emu["t"]))
+        assert err.max() <= TOL
+    assert ddf.ddf_check_status(m.h) == 0
+    m.close()
+
+
+def test_noalloc_rejects_batches_beyond_the_scratch(cuda_lib):
+    import torch
+    from paper_2606_00817_gb300 import ddf
+    net = (10, 1280, 8)
+    m = ddf.DDF(*net, precision="bf16")
+    m.load(I.xavier_blob(I.NetShape(*net)))
+    n = 20000
+    dev = [torch.zeros(n, device="cuda") for _ in range(6)]
+    t = torch.empty(n, device="cuda")
+    v = torch.empty(n, device="cuda")
+    with pytest.raises(ddf.DDFError) as e:
+        ddf.ddf_query_rays_noalloc(m.h, dev, n, t, v)
+    assert e.value.status == 1 and "at most" in str(e.value)
+    m.close()
