@@ -96,7 +96,8 @@ struct ddf_s {
   int d_in = 0;
   int kp32 = 0;  // padded encoded width, FP32 rows (multiple of 8)
   int kp16 = 0;  // padded encoded width, bf16 rows (multiple of 8 -> 16-byte rows)
-  int bn = 0;    // tensor-core N tile
+  int bn = 0;    // tensor-core N tile (= tile.bn)
+  ddf::TcTile tile{256, 4};
   int num_sms = 0;
   bool loaded = false;
   bool scales_set = false;
@@ -209,6 +210,9 @@ struct ProfScope {
   }
 };
 
+// Most head partials any tile writes per row: N/128 blocks x 2 epilogue halves.
+int max_partials(int W) { return (W / 128) * 2; }
+
 ddf_status ensure_workspace(ddf_s* h, int64_t rows) {
   if (rows <= h->ws_rows) return DDF_OK;
   dev_free(h, h->ws_enc);
@@ -229,7 +233,7 @@ ddf_status ensure_workspace(ddf_s* h, int64_t rows) {
       return st;
   if (!f32) {
     void* p;
-    if ((st = dev_alloc(h, &p, static_cast<size_t>(rows) * (W / h->bn) * sizeof(float2))) != DDF_OK)
+    if ((st = dev_alloc(h, &p, static_cast<size_t>(rows) * max_partials(W) * sizeof(float2))) != DDF_OK)
       return st;
     h->ws_part = static_cast<float2*>(p);
   }
@@ -303,13 +307,30 @@ ddf_status forward_tc(ddf_s* h, ddf::RaySoA rays, int m, ddf::HeadOut out, cudaS
     p.mode = last ? 1 : 0;
     p.status = h->status_dev;
     p.timeout_ns = h->timeout_ns;
-    const int64_t tiles = ((m + 127) / 128) * static_cast<int64_t>(W / h->bn);
+    const int64_t tiles = ((m + 127) / 128) * static_cast<int64_t>(W / h->tile.bn);
     const int grid = static_cast<int>(std::min<int64_t>(tiles, h->num_sms));
     ProfScope ps(h, kProfGemm, st);
-    DDF_CK(ddf::launch_tc_gemm(h->bn, in_fp8, out_fp8, tmA, h->tmB[l], p, grid, st));
+    DDF_CK(ddf::launch_tc_gemm(h->tile, in_fp8, out_fp8, tmA, h->tmB[l], p, grid, st));
   }
   ProfScope ps(h, kProfHead, st);
-  DDF_CK(ddf::launch_finish_heads(h->ws_part, W / h->bn, m, h->head_b, out, st));
+  const int nparts = (W / h->tile.bn) * (h->tile.epi_warps / 4);
+  DDF_CK(ddf::launch_finish_heads(h->ws_part, nparts, m, h->head_b, out, st));
+  return DDF_OK;
+}
+
+// (Re)builds the TMA maps of the weight matrices for the current N tile.
+ddf_status build_weight_maps(ddf_s* h) {
+  const int W = h->cfg.width;
+  for (int l = 0; l < h->cfg.hidden_layers; ++l) {
+    bool ok = true;
+    if (h->wb[l] != nullptr) {
+      const int kp = l == 0 ? h->kp16 : W;
+      ok = make_tmap(&h->tmB[l], h->wb[l], false, kp, W, static_cast<uint64_t>(kp) * 2, h->tile.bn);
+    } else if (h->wq[l] != nullptr) {
+      ok = make_tmap(&h->tmB[l], h->wq[l], true, W, W, W, h->tile.bn);
+    }
+    if (!ok) return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for a weight map");
+  }
   return DDF_OK;
 }
 
@@ -388,6 +409,7 @@ ddf_status ddf_create(const ddf_config* cfg, ddf_handle* out) {
   h->kp32 = static_cast<int>(round_up(h->d_in, 8));
   h->kp16 = static_cast<int>(round_up(h->d_in, 8));
   h->bn = (cfg->width % 256 == 0) ? 256 : 128;
+  h->tile = ddf::TcTile{h->bn, 4};
   cudaError_t e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, cfg->device);
   void* p = nullptr;
   if (e != cudaSuccess || dev_alloc(h, &p, sizeof(uint32_t)) != DDF_OK) {
@@ -461,7 +483,7 @@ ddf_status ddf_load_weights(ddf_handle h, const float* host_blob, size_t n_float
         const int kp = l == 0 ? h->kp16 : W;
         if ((s = dev_alloc(h, &p, static_cast<size_t>(W) * kp * 2)) != DDF_OK) return s;
         h->wb[l] = static_cast<__nv_bfloat16*>(p);
-        if (!make_tmap(&h->tmB[l], h->wb[l], false, kp, W, static_cast<uint64_t>(kp) * 2, h->bn))
+        if (!make_tmap(&h->tmB[l], h->wb[l], false, kp, W, static_cast<uint64_t>(kp) * 2, h->tile.bn))
           return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for a weight map");
       } else {
         if ((s = dev_alloc(h, &p, static_cast<size_t>(W) * W)) != DDF_OK) return s;
@@ -470,7 +492,7 @@ ddf_status ddf_load_weights(ddf_handle h, const float* host_blob, size_t n_float
         h->wscale[l] = static_cast<float*>(p);
         if ((s = dev_alloc(h, &p, W * sizeof(float))) != DDF_OK) return s;
         h->colscale[l] = static_cast<float*>(p);
-        if (!make_tmap(&h->tmB[l], h->wq[l], true, W, W, W, h->bn))
+        if (!make_tmap(&h->tmB[l], h->wq[l], true, W, W, W, h->tile.bn))
           return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for a weight map");
       }
       (void)K;
@@ -732,6 +754,104 @@ ddf_status ddf_profile_read(ddf_handle h, double ms[4], int64_t launches[4]) {
   return DDF_OK;
 }
 
+
+ddf_status ddf_set_tile(ddf_handle h, int32_t bn, int32_t epi_warps) {
+  if (h == nullptr) return fail(DDF_ERR_INVALID_ARG, "handle is NULL");
+  if ((bn != 128 && bn != 256) || (epi_warps != 4 && epi_warps != 8))
+    return fail(DDF_ERR_INVALID_ARG, "bn must be 128 or 256 and epi_warps 4 or 8");
+  if (h->cfg.width % bn != 0) return fail(DDF_ERR_UNSUPPORTED, "width is not a multiple of bn");
+  h->tile = ddf::TcTile{bn, epi_warps};
+  h->bn = bn;
+  if (h->loaded && h->cfg.precision != DDF_FP32) {
+    DeviceGuard g(h->cfg.device);
+    DDF_CK(cudaDeviceSynchronize());  // launches in flight keep their own copies of the maps
+    return build_weight_maps(h);
+  }
+  return DDF_OK;
+}
+
+ddf_status ddf_get_tile(ddf_handle h, int32_t* bn, int32_t* epi_warps) {
+  if (h == nullptr || bn == nullptr || epi_warps == nullptr)
+    return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+  *bn = h->tile.bn;
+  *epi_warps = h->tile.epi_warps;
+  return DDF_OK;
+}
+
+ddf_status ddf_autotune(ddf_handle h, const float* const rays[6], int64_t n, void* stream,
+                        double* ms_out, int32_t n_out) {
+  ddf_status s = check_ready(h);
+  if (s != DDF_OK) return s;
+  if ((s = check_rays(rays, n)) != DDF_OK) return s;
+  if (n <= 0 || n > (int64_t{1} << 24)) return fail(DDF_ERR_INVALID_ARG, "tune on 1 .. 2^24 rays");
+  if (ms_out != nullptr && n_out < 4) return fail(DDF_ERR_INVALID_ARG, "ms_out needs 4 entries");
+  if (ms_out != nullptr)
+    for (int i = 0; i < 4; ++i) ms_out[i] = -1.0;
+  if (h->cfg.precision == DDF_FP32) return DDF_OK;  // one FP32 kernel shape, nothing to choose
+  DeviceGuard g(h->cfg.device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const ddf::TcTile cands[4] = {{256, 4}, {256, 8}, {128, 4}, {128, 8}};
+  float* buf = nullptr;
+  DDF_CK(cudaMalloc(&buf, 4 * n * sizeof(float)));
+  std::vector<float> ref_t(n), ref_v(n), got_t(n), got_v(n);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const ddf::TcTile keep = h->tile;
+  const bool keep_prof = h->prof;
+  h->prof = false;
+  double best = 1e30;
+  ddf::TcTile best_tile = keep;
+  bool have_ref = false;
+  ddf_status result = DDF_OK;
+  for (int c = 0; c < 4 && result == DDF_OK; ++c) {
+    if (h->cfg.width % cands[c].bn != 0) continue;
+    if ((result = ddf_set_tile(h, cands[c].bn, cands[c].epi_warps)) != DDF_OK) break;
+    ddf::HeadOut o{};
+    o.t = buf + (have_ref ? 2 * n : 0);
+    o.vis = o.t + n;
+    if ((result = run_query(h, rays, n, o, st)) != DDF_OK) break;
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+      result = fail(DDF_ERR_CUDA, "autotune: candidate launch failed");
+      break;
+    }
+    std::vector<float>& tt = have_ref ? got_t : ref_t;
+    std::vector<float>& vv = have_ref ? got_v : ref_v;
+    cudaMemcpy(tt.data(), o.t, n * sizeof(float), cudaMemcpyDeviceToHost);
+    cudaMemcpy(vv.data(), o.vis, n * sizeof(float), cudaMemcpyDeviceToHost);
+    if (have_ref) {  // every candidate must agree with the first before it may be timed
+      double worst = 0.0;
+      for (int64_t i = 0; i < n; ++i) {
+        worst = std::max(worst, std::fabs(double(got_t[i]) - ref_t[i]) / std::max(1.0, std::fabs(double(ref_t[i]))));
+        worst = std::max(worst, std::fabs(double(got_v[i]) - ref_v[i]) / std::max(1.0, std::fabs(double(ref_v[i]))));
+      }
+      if (!(worst <= 1e-3)) continue;
+    }
+    have_ref = true;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3; ++r) run_query(h, rays, n, o, st);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double per = ms / 3.0;
+    if (ms_out != nullptr) ms_out[c] = per;
+    if (per < best) {
+      best = per;
+      best_tile = cands[c];
+    }
+  }
+  h->prof = keep_prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (result != DDF_OK) {
+    ddf_set_tile(h, keep.bn, keep.epi_warps);
+    return result;
+  }
+  return ddf_set_tile(h, best_tile.bn, best_tile.epi_warps);
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
@@ -746,7 +866,7 @@ size_t ddf_internal_workspace_bytes(ddf_handle h, int64_t rows) {
   auto up = [](size_t b) { return (b + 255) / 256 * 256; };
   size_t total = up(static_cast<size_t>(rows) * (f32 ? h->kp32 * 4 : h->kp16 * 2));
   total += 2 * up(static_cast<size_t>(rows) * W * act_elem);
-  if (!f32) total += up(static_cast<size_t>(rows) * (W / h->bn) * sizeof(float2));
+  if (!f32) total += up(static_cast<size_t>(rows) * max_partials(W) * sizeof(float2));
   return total;
 }
 

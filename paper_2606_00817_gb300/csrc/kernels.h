@@ -26,15 +26,24 @@ struct TcGemmParams {
   void* out;               // mode 0: [M x ldo] bf16 or e4m3 codes
   int ldo;                 // elements
   const float* head_w;     // mode 1: [2 x N] FP32
-  float2* head_part;       // mode 1: [N/BN x M]
+  float2* head_part;       // mode 1: [(N/BN) * (epi_warps/4) x M]
   int mode;
   uint32_t* status;        // device status word (timeouts)
   uint64_t timeout_ns;
 };
 
+// Tile configuration of the tensor-core layer: N tile (128 or 256) and the
+// number of epilogue warps (4, or 8 = two warps per TMEM lane quarter, each
+// draining half of the columns). Mode 1 writes (N/bn) * (epi_warps/4) partials
+// per row.
+struct TcTile {
+  int bn;
+  int epi_warps;
+};
+
 // in_fp8: operands are e4m3 codes (kind::f8f6f4) instead of bf16 (kind::f16).
-// out_fp8: mode-0 output is e4m3 codes instead of bf16. bn: 128 or 256.
-cudaError_t launch_tc_gemm(int bn, bool in_fp8, bool out_fp8, const CUtensorMap& tmA,
+// out_fp8: mode-0 output is e4m3 codes instead of bf16.
+cudaError_t launch_tc_gemm(const TcTile& tile, bool in_fp8, bool out_fp8, const CUtensorMap& tmA,
                            const CUtensorMap& tmB, const TcGemmParams& p, int grid,
                            cudaStream_t s);
 int tc_gemm_smem_bytes(int bn, bool in_fp8);

@@ -62,8 +62,8 @@ __device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float
   return (lo & 0xFFFFu) | (hi << 16);
 }
 
-template <int BN, bool IN_FP8, bool OUT_FP8>
-__global__ void __launch_bounds__(192, 1)
+template <int BN, bool IN_FP8, bool OUT_FP8, int EPI>
+__global__ void __launch_bounds__(64 + 32 * EPI, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcGemmParams p) {
   using S = TcShape<BN, IN_FP8>;
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull_bar(b), 1);
-      mbar_init(tempty_bar(b), 4);  // one arrival per epilogue warp
+      mbar_init(tempty_bar(b), EPI);  // one arrival per epilogue warp
     }
     mbar_init(mdone_bar, 1);
     *abort_flag = 0;
@@ -185,6 +185,9 @@ __global__ void __launch_bounds__(192, 1)
   } else if (warp >= 2) {
     // ---------------------------------------------------------- epilogue
     const int q = warp & 3;  // TMEM lane quarter this warp may access
+    // with 8 epilogue warps, two warps share a lane quarter and split the columns
+    constexpr int kChunks = BN / 32 / (EPI / 4);
+    const int half = (warp - 2) / 4;
     const int r_local = q * 32 + lane;
     int local = 0;
     for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++local) {
@@ -206,7 +209,7 @@ __global__ void __launch_bounds__(192, 1)
                              static_cast<uint32_t>(b * BN);
       float h0 = 0.f, h1 = 0.f;
 #pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
+      for (int c = half * kChunks; c < (half + 1) * kChunks; ++c) {
         uint32_t v[32];
         tmem_ld32(tbase + 32u * c, v);
         tmem_wait_ld();
@@ -275,7 +278,8 @@ __global__ void __launch_bounds__(192, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty_bar(b));
       if (p.mode != 0 && row_ok)
-        p.head_part[static_cast<size_t>(n_blk) * p.M + row] = make_float2(h0, h1);
+        p.head_part[(static_cast<size_t>(n_blk) * (EPI / 4) + half) * p.M + row] =
+            make_float2(h0, h1);
     }
   }
 
@@ -288,17 +292,26 @@ __global__ void __launch_bounds__(192, 1)
   }
 }
 
-template <int BN, bool IN_FP8, bool OUT_FP8>
+template <int BN, bool IN_FP8, bool OUT_FP8, int EPI>
 cudaError_t launch_one(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcGemmParams& p,
                        int grid, cudaStream_t s) {
   using S = TcShape<BN, IN_FP8>;
-  auto kern = tc_gemm_kernel<BN, IN_FP8, OUT_FP8>;
+  auto kern = tc_gemm_kernel<BN, IN_FP8, OUT_FP8, EPI>;
   // applies to the current device; cheap enough to repeat on every launch
   cudaError_t e =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  kern<<<grid, 192, S::SMEM_BYTES, s>>>(tmA, tmB, p);
+  kern<<<grid, 64 + 32 * EPI, S::SMEM_BYTES, s>>>(tmA, tmB, p);
   return cudaGetLastError();
+}
+
+template <int BN, int EPI>
+cudaError_t launch_bn(bool in_fp8, bool out_fp8, const CUtensorMap& tmA, const CUtensorMap& tmB,
+                      const TcGemmParams& p, int grid, cudaStream_t s) {
+  if (in_fp8) return out_fp8 ? launch_one<BN, true, true, EPI>(tmA, tmB, p, grid, s)
+                             : launch_one<BN, true, false, EPI>(tmA, tmB, p, grid, s);
+  return out_fp8 ? launch_one<BN, false, true, EPI>(tmA, tmB, p, grid, s)
+                 : launch_one<BN, false, false, EPI>(tmA, tmB, p, grid, s);
 }
 
 }  // namespace
@@ -308,21 +321,13 @@ int tc_gemm_smem_bytes(int bn, bool in_fp8) {
   return in_fp8 ? TcShape<128, true>::SMEM_BYTES : TcShape<128, false>::SMEM_BYTES;
 }
 
-cudaError_t launch_tc_gemm(int bn, bool in_fp8, bool out_fp8, const CUtensorMap& tmA,
+cudaError_t launch_tc_gemm(const TcTile& tile, bool in_fp8, bool out_fp8, const CUtensorMap& tmA,
                            const CUtensorMap& tmB, const TcGemmParams& p, int grid,
                            cudaStream_t s) {
-  if (bn == 256) {
-    if (in_fp8) return out_fp8 ? launch_one<256, true, true>(tmA, tmB, p, grid, s)
-                               : launch_one<256, true, false>(tmA, tmB, p, grid, s);
-    return out_fp8 ? launch_one<256, false, true>(tmA, tmB, p, grid, s)
-                   : launch_one<256, false, false>(tmA, tmB, p, grid, s);
-  }
-  if (bn == 128) {
-    if (in_fp8) return out_fp8 ? launch_one<128, true, true>(tmA, tmB, p, grid, s)
-                               : launch_one<128, true, false>(tmA, tmB, p, grid, s);
-    return out_fp8 ? launch_one<128, false, true>(tmA, tmB, p, grid, s)
-                   : launch_one<128, false, false>(tmA, tmB, p, grid, s);
-  }
+  if (tile.bn == 256 && tile.epi_warps == 4) return launch_bn<256, 4>(in_fp8, out_fp8, tmA, tmB, p, grid, s);
+  if (tile.bn == 256 && tile.epi_warps == 8) return launch_bn<256, 8>(in_fp8, out_fp8, tmA, tmB, p, grid, s);
+  if (tile.bn == 128 && tile.epi_warps == 4) return launch_bn<128, 4>(in_fp8, out_fp8, tmA, tmB, p, grid, s);
+  if (tile.bn == 128 && tile.epi_warps == 8) return launch_bn<128, 8>(in_fp8, out_fp8, tmA, tmB, p, grid, s);
   return cudaErrorInvalidValue;
 }
 

@@ -209,3 +209,32 @@ def test_full_size_shadow_workload_sampled(torch_cuda):
     idx = np.concatenate([idx, [0, rays.n - 1]])
     sub = I.Rays(*[a[idx] for a in rays.soa()])
     _check_reduced(t[idx], v[idx], sub, blob, PAPER, "bf16", None)
+
+
+@pytest.mark.parametrize("tile", [(256, 4), (256, 8), (128, 4), (128, 8)])
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_every_tile_matches_oracle(torch_cuda, tile, prec):
+    from paper_2606_00817_gb300 import ddf
+    blob = I.xavier_blob(I.NetShape(*PAPER))
+    sc = _scales(blob, PAPER)
+    rays = I.uniform_rays(777, seed=8)
+    m = _make(PAPER, prec, blob, sc)
+    ddf.ddf_set_tile(m.h, *tile)
+    assert ddf.ddf_get_tile(m.h) == tile
+    t, v = _query(torch_cuda, m, rays)
+    _check_reduced(t, v, rays, blob, PAPER, prec, sc)
+
+
+def test_small_width_tiles_and_autotune(torch_cuda):
+    from paper_2606_00817_gb300 import ddf
+    blob = I.xavier_blob(I.NetShape(*SMALL))
+    rays = I.uniform_rays(4099, seed=9)
+    m = _make(SMALL, "bf16", blob)
+    with pytest.raises(ddf.DDFError):
+        ddf.ddf_set_tile(m.h, 256, 4)          # width 128 has no 256-wide N tile
+    ms = ddf.ddf_autotune(m.h, _dev(torch_cuda, rays), rays.n)
+    assert ms[(256, 4)] is None and ms[(256, 8)] is None
+    assert ms[(128, 4)] > 0 and ms[(128, 8)] > 0
+    assert ddf.ddf_get_tile(m.h) in ((128, 4), (128, 8))
+    t, v = _query(torch_cuda, m, rays)
+    _check_reduced(t, v, rays, blob, SMALL, "bf16", None)
