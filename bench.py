@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--rays", type=int, default=4_194_304)
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32 comparison run")
     ap.add_argument("--oracle-seconds", type=float, default=12.0)
-    ap.add_argument("--tile", default="auto", help="auto (autotune) or BNxEPI, e.g. 256x8")
+    ap.add_argument("--tile", default="auto", help="auto (autotune) or BNxEPI[pair], e.g. 256x8, 256x4pair")
     return ap.parse_args()
 
 
@@ -206,11 +206,12 @@ def main():
     tune_ms = None
     if args.tile == "auto":
         nt = min(R, 1 << 20)
-        tune_ms = {f"{k[0]}x{k[1]}": v for k, v in
+        tune_ms = {f"{k[0]}x{k[1]}{'pair' if k[2] else ''}": v for k, v in
                    ddf.ddf_autotune(m.h, [r[:nt] for r in d_rays], nt, stream).items()}
     else:
-        bn, ew = (int(x) for x in args.tile.split("x"))
-        ddf.ddf_set_tile(m.h, bn, ew)
+        pair = args.tile.endswith("pair")
+        bn, ew = (int(x) for x in args.tile.replace("pair", "").split("x"))
+        ddf.ddf_set_tile(m.h, bn, ew, int(pair))
     tile = ddf.ddf_get_tile(m.h)
 
     def step():
@@ -342,7 +343,8 @@ def main():
                        "l2": "512 MiB buffer written between timed steps (L2 flush)",
                        "timing": "CUDA events per step on the launching stream",
                        "wall_s_timed_region": wall,
-                       "tile": {"bn": tile[0], "epi_warps": tile[1], "autotune_ms_1M_rays": tune_ms}},
+                       "tile": {"bn": tile[0], "epi_warps": tile[1], "cta_pair": tile[2],
+                                "autotune_ms_1M_rays": tune_ms}},
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(), "e2e": e2e,
             "gpu_launches": launches, "accuracy": acc, "compare": compare,
             "kernel_ms_by_class": {k: v[0] for k, v in prof.items()},

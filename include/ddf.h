@@ -171,20 +171,22 @@ ddf_status ddf_set_chunk_rays(ddf_handle h, int64_t chunk);
 
 /* Tensor-core tile of the layer kernel: bn = N tile (128 or 256; 256 needs
  * width % 256 == 0), epi_warps = epilogue warps draining the TMEM accumulator
- * (4, or 8 = two per lane quarter). Results agree across tiles to FP32
- * rounding of the head sums. Default: bn 256 where possible, 4 warps.
- * ddf_set_tile synchronises the device when weights are loaded. */
-ddf_status ddf_set_tile(ddf_handle h, int32_t bn, int32_t epi_warps);
-ddf_status ddf_get_tile(ddf_handle h, int32_t* bn, int32_t* epi_warps);
+ * (4, or 8 = two per lane quarter), cta_pair = 1 for the 256 x 256 tile that a
+ * cluster of two CTAs computes with one pair MMA (needs bn 256, 4 warps).
+ * Results agree across tiles up to FP32 rounding of the head sums. Default:
+ * bn 256 where possible, 4 warps, no pair. ddf_set_tile synchronises the
+ * device when weights are loaded. */
+ddf_status ddf_set_tile(ddf_handle h, int32_t bn, int32_t epi_warps, int32_t cta_pair);
+ddf_status ddf_get_tile(ddf_handle h, int32_t* bn, int32_t* epi_warps, int32_t* cta_pair);
 
 /* Autotuner: runs every supported tile on n rays (device SoA, 1 <= n <= 2^24)
  * on stream, rejects any candidate whose t or vis differ from the first
  * candidate's by more than 1e-3 (relative to max(1, |ref|)), times each
  * passing candidate over 3 queries with CUDA events and keeps the fastest.
- * ms_out (nullable, n_out >= 4) receives per-candidate ms for the order
- * (256,4), (256,8), (128,4), (128,8); -1 marks skipped or rejected ones.
- * Synchronous; allocates 16 n bytes of device memory while it runs. A no-op on
- * FP32 handles. */
+ * ms_out (nullable, n_out >= 5) receives per-candidate ms for the order
+ * (256,4), (256,8), (128,4), (128,8), (256,4,pair); -1 marks skipped or
+ * rejected ones. Synchronous; allocates 16 n bytes of device memory while it
+ * runs. A no-op on FP32 handles. */
 ddf_status ddf_autotune(ddf_handle h, const float* const rays[6], int64_t n, void* stream,
                         double* ms_out, int32_t n_out);
 

@@ -98,6 +98,7 @@ struct ddf_s {
   int kp16 = 0;  // padded encoded width, bf16 rows (multiple of 8 -> 16-byte rows)
   int bn = 0;    // tensor-core N tile (= tile.bn)
   ddf::TcTile tile{256, 4};
+  int pair_clusters = 0;  // co-resident clusters of the CTA-pair kernel
   int num_sms = 0;
   bool loaded = false;
   bool scales_set = false;
@@ -307,13 +308,19 @@ ddf_status forward_tc(ddf_s* h, ddf::RaySoA rays, int m, ddf::HeadOut out, cudaS
     p.mode = last ? 1 : 0;
     p.status = h->status_dev;
     p.timeout_ns = h->timeout_ns;
-    const int64_t tiles = ((m + 127) / 128) * static_cast<int64_t>(W / h->tile.bn);
-    const int grid = static_cast<int>(std::min<int64_t>(tiles, h->num_sms));
     ProfScope ps(h, kProfGemm, st);
-    DDF_CK(ddf::launch_tc_gemm(h->tile, in_fp8, out_fp8, tmA, h->tmB[l], p, grid, st));
+    if (h->tile.pair) {
+      const int64_t tiles = ((m + 255) / 256) * static_cast<int64_t>(W / 256);
+      const int clusters = static_cast<int>(std::min<int64_t>(tiles, h->pair_clusters));
+      DDF_CK(ddf::launch_tc_gemm_pair(in_fp8, out_fp8, tmA, h->tmB[l], p, clusters, st));
+    } else {
+      const int64_t tiles = ((m + 127) / 128) * static_cast<int64_t>(W / h->tile.bn);
+      const int grid = static_cast<int>(std::min<int64_t>(tiles, h->num_sms));
+      DDF_CK(ddf::launch_tc_gemm(h->tile, in_fp8, out_fp8, tmA, h->tmB[l], p, grid, st));
+    }
   }
   ProfScope ps(h, kProfHead, st);
-  const int nparts = (W / h->tile.bn) * (h->tile.epi_warps / 4);
+  const int nparts = h->tile.pair ? W / 256 : (W / h->tile.bn) * (h->tile.epi_warps / 4);
   DDF_CK(ddf::launch_finish_heads(h->ws_part, nparts, m, h->head_b, out, st));
   return DDF_OK;
 }
@@ -321,13 +328,14 @@ ddf_status forward_tc(ddf_s* h, ddf::RaySoA rays, int m, ddf::HeadOut out, cudaS
 // (Re)builds the TMA maps of the weight matrices for the current N tile.
 ddf_status build_weight_maps(ddf_s* h) {
   const int W = h->cfg.width;
+  const uint32_t box_rows = h->tile.pair ? 128u : static_cast<uint32_t>(h->tile.bn);
   for (int l = 0; l < h->cfg.hidden_layers; ++l) {
     bool ok = true;
     if (h->wb[l] != nullptr) {
       const int kp = l == 0 ? h->kp16 : W;
-      ok = make_tmap(&h->tmB[l], h->wb[l], false, kp, W, static_cast<uint64_t>(kp) * 2, h->tile.bn);
+      ok = make_tmap(&h->tmB[l], h->wb[l], false, kp, W, static_cast<uint64_t>(kp) * 2, box_rows);
     } else if (h->wq[l] != nullptr) {
-      ok = make_tmap(&h->tmB[l], h->wq[l], true, W, W, W, h->tile.bn);
+      ok = make_tmap(&h->tmB[l], h->wq[l], true, W, W, W, box_rows);
     }
     if (!ok) return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for a weight map");
   }
@@ -410,6 +418,9 @@ ddf_status ddf_create(const ddf_config* cfg, ddf_handle* out) {
   h->kp16 = static_cast<int>(round_up(h->d_in, 8));
   h->bn = (cfg->width % 256 == 0) ? 256 : 128;
   h->tile = ddf::TcTile{h->bn, 4};
+  if (cfg->precision != DDF_FP32 && cfg->width % 256 == 0)
+    h->pair_clusters = std::min(ddf::tc_gemm_pair_max_clusters(false),
+                                ddf::tc_gemm_pair_max_clusters(true));
   cudaError_t e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, cfg->device);
   void* p = nullptr;
   if (e != cudaSuccess || dev_alloc(h, &p, sizeof(uint32_t)) != DDF_OK) {
@@ -755,12 +766,16 @@ ddf_status ddf_profile_read(ddf_handle h, double ms[4], int64_t launches[4]) {
 }
 
 
-ddf_status ddf_set_tile(ddf_handle h, int32_t bn, int32_t epi_warps) {
+ddf_status ddf_set_tile(ddf_handle h, int32_t bn, int32_t epi_warps, int32_t cta_pair) {
   if (h == nullptr) return fail(DDF_ERR_INVALID_ARG, "handle is NULL");
   if ((bn != 128 && bn != 256) || (epi_warps != 4 && epi_warps != 8))
     return fail(DDF_ERR_INVALID_ARG, "bn must be 128 or 256 and epi_warps 4 or 8");
   if (h->cfg.width % bn != 0) return fail(DDF_ERR_UNSUPPORTED, "width is not a multiple of bn");
-  h->tile = ddf::TcTile{bn, epi_warps};
+  if (cta_pair != 0 && (bn != 256 || epi_warps != 4))
+    return fail(DDF_ERR_INVALID_ARG, "the CTA-pair tile is bn 256 with 4 epilogue warps");
+  if (cta_pair != 0 && h->pair_clusters <= 0)
+    return fail(DDF_ERR_UNSUPPORTED, "CTA-pair clusters do not fit on this device");
+  h->tile = ddf::TcTile{bn, epi_warps, cta_pair != 0};
   h->bn = bn;
   if (h->loaded && h->cfg.precision != DDF_FP32) {
     DeviceGuard g(h->cfg.device);
@@ -770,11 +785,12 @@ ddf_status ddf_set_tile(ddf_handle h, int32_t bn, int32_t epi_warps) {
   return DDF_OK;
 }
 
-ddf_status ddf_get_tile(ddf_handle h, int32_t* bn, int32_t* epi_warps) {
-  if (h == nullptr || bn == nullptr || epi_warps == nullptr)
+ddf_status ddf_get_tile(ddf_handle h, int32_t* bn, int32_t* epi_warps, int32_t* cta_pair) {
+  if (h == nullptr || bn == nullptr || epi_warps == nullptr || cta_pair == nullptr)
     return fail(DDF_ERR_INVALID_ARG, "NULL argument");
   *bn = h->tile.bn;
   *epi_warps = h->tile.epi_warps;
+  *cta_pair = h->tile.pair ? 1 : 0;
   return DDF_OK;
 }
 
@@ -784,13 +800,13 @@ ddf_status ddf_autotune(ddf_handle h, const float* const rays[6], int64_t n, voi
   if (s != DDF_OK) return s;
   if ((s = check_rays(rays, n)) != DDF_OK) return s;
   if (n <= 0 || n > (int64_t{1} << 24)) return fail(DDF_ERR_INVALID_ARG, "tune on 1 .. 2^24 rays");
-  if (ms_out != nullptr && n_out < 4) return fail(DDF_ERR_INVALID_ARG, "ms_out needs 4 entries");
+  if (ms_out != nullptr && n_out < 5) return fail(DDF_ERR_INVALID_ARG, "ms_out needs 5 entries");
   if (ms_out != nullptr)
-    for (int i = 0; i < 4; ++i) ms_out[i] = -1.0;
+    for (int i = 0; i < 5; ++i) ms_out[i] = -1.0;
   if (h->cfg.precision == DDF_FP32) return DDF_OK;  // one FP32 kernel shape, nothing to choose
   DeviceGuard g(h->cfg.device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const ddf::TcTile cands[4] = {{256, 4}, {256, 8}, {128, 4}, {128, 8}};
+  const ddf::TcTile cands[5] = {{256, 4}, {256, 8}, {128, 4}, {128, 8}, {256, 4, true}};
   float* buf = nullptr;
   DDF_CK(cudaMalloc(&buf, 4 * n * sizeof(float)));
   std::vector<float> ref_t(n), ref_v(n), got_t(n), got_v(n);
@@ -804,9 +820,10 @@ ddf_status ddf_autotune(ddf_handle h, const float* const rays[6], int64_t n, voi
   ddf::TcTile best_tile = keep;
   bool have_ref = false;
   ddf_status result = DDF_OK;
-  for (int c = 0; c < 4 && result == DDF_OK; ++c) {
+  for (int c = 0; c < 5 && result == DDF_OK; ++c) {
     if (h->cfg.width % cands[c].bn != 0) continue;
-    if ((result = ddf_set_tile(h, cands[c].bn, cands[c].epi_warps)) != DDF_OK) break;
+    if (cands[c].pair && h->pair_clusters <= 0) continue;
+    if ((result = ddf_set_tile(h, cands[c].bn, cands[c].epi_warps, cands[c].pair)) != DDF_OK) break;
     ddf::HeadOut o{};
     o.t = buf + (have_ref ? 2 * n : 0);
     o.vis = o.t + n;
@@ -846,10 +863,10 @@ ddf_status ddf_autotune(ddf_handle h, const float* const rays[6], int64_t n, voi
   cudaEventDestroy(e1);
   cudaFree(buf);
   if (result != DDF_OK) {
-    ddf_set_tile(h, keep.bn, keep.epi_warps);
+    ddf_set_tile(h, keep.bn, keep.epi_warps, keep.pair);
     return result;
   }
-  return ddf_set_tile(h, best_tile.bn, best_tile.epi_warps);
+  return ddf_set_tile(h, best_tile.bn, best_tile.epi_warps, best_tile.pair);
 }
 
 }  // extern "C"

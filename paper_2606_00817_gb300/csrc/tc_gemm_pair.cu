@@ -1,0 +1,369 @@
+// tc_gemm_pair.cu -- one dense DDF layer on a pair of SMs (tcgen05 cta_group::2).
+//
+// Same layer as tc_gemm.cu (Y = act(A W^T * scale + b), Sec. 3.1 / Sec. 4.3),
+// but each 256 x 256 output tile is computed by a cluster of two CTAs that
+// share one MMA: CTA r of the pair loads rows [128 r, 128 r + 128) of the A
+// tile and rows [128 r, 128 r + 128) of the W tile into its own shared memory,
+// and the leader CTA (rank 0) issues tcgen05.mma.cta_group::2 with M = 256,
+// N = 256, which reads A and W from both CTAs and leaves the 128 x 256
+// accumulator of each CTA's rows in that CTA's TMEM. Per SM this halves the
+// shared-memory operand traffic of the 128 x 256 single-CTA tile (each SM now
+// stages 32 KB instead of 48 KB per 64-wide K step for the same MMA work).
+//
+// Synchronisation:
+//   full[s]     (leader) both CTAs' TMA copies of stage s land here; the
+//               leader's producer arms it with the bytes of both halves
+//   empty[s]    (each CTA) the leader's commit multicasts "stage s consumed"
+//   tfull[b]    (each CTA) the leader's commit multicasts "accumulator b ready"
+//   tempty[b]   (leader) 4 epilogue warps of each CTA arrive: "b drained"
+// Every wait is bounded. A timeout raises the abort flag of both CTAs and a
+// status bit. At teardown both producers publish how many stages they issued;
+// after a cluster barrier the one that issued fewer copies the missing stage
+// halves (in-bounds dummy loads) so that every armed barrier phase completes,
+// the leader waits for those phases, and a second cluster barrier precedes
+// the collective TMEM release.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "kernels.h"
+#include "ptx_sm103.cuh"
+
+namespace ddf {
+
+namespace {
+
+constexpr uint64_t kPairDrainNs = 1000000000ull;
+
+template <bool IN_FP8>
+struct PairShape {
+  static constexpr int BM = 256;                 // output rows per pair tile
+  static constexpr int BN = 256;                 // output columns per pair tile
+  static constexpr int HALF = 128;               // rows of A and of W per CTA
+  static constexpr int ROW_BYTES = 128;
+  static constexpr int BK = IN_FP8 ? 128 : 64;   // K elements per stage
+  static constexpr int A_BYTES = HALF * ROW_BYTES;
+  static constexpr int B_BYTES = HALF * ROW_BYTES;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;  // per CTA
+  static constexpr int STAGES = 6;
+  static constexpr int TMEM_COLS = 512;
+  static constexpr int NUM_BARS = 2 * STAGES + 5;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + NUM_BARS * 8 + 32 + 1024;
+};
+
+__device__ __forceinline__ uint32_t pack_bf16x2_p(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ uint32_t pack_e4m3x4_p(float a, float b, float c, float d) {
+  const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+  const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+  return (lo & 0xFFFFu) | (hi << 16);
+}
+
+template <bool IN_FP8, bool OUT_FP8>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
+    tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
+                        const __grid_constant__ CUtensorMap tmB, const TcGemmParams p) {
+  using S = PairShape<IN_FP8>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + S::STAGES * S::A_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::STAGES * S::STAGE_BYTES);
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (S::STAGES + s); };
+  auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * S::STAGES + b); };
+  auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * S::STAGES + 2 + b); };
+  const uint32_t mdone_bar = bar0 + 8u * (2 * S::STAGES + 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + S::NUM_BARS);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile uint32_t* issued = reinterpret_cast<volatile uint32_t*>(tmem_slot + 2);  // [2]
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_ctarank();  // 0: leader, issues the MMAs
+  const int pair = blockIdx.x >> 1;
+  const int npairs = gridDim.x >> 1;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S::STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull_bar(b), 1);
+      mbar_init(tempty_bar(b), 8);  // 4 epilogue warps in each CTA
+    }
+    mbar_init(mdone_bar, 1);
+    *abort_flag = 0;
+    issued[0] = 0;
+    issued[1] = 0;
+    fence_mbar_init();
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmB);
+  }
+  if (warp == 1) {
+    tmem_alloc_pair(smem_u32(tmem_slot), S::TMEM_COLS);  // collective with the peer's warp 1
+    tmem_relinquish_pair();
+  }
+  tc_fence_before();
+  cluster_sync_all();  // barriers of both CTAs initialised, TMEM allocated
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  const uint32_t full_leader0 = map_to_cta(full_bar(0), 0);
+  const uint32_t abort_peer = map_to_cta(smem_u32(const_cast<int*>(abort_flag)), rank ^ 1u);
+  auto raise_abort = [&]() {
+    *abort_flag = 1;
+    st_cluster_u32(abort_peer, 1u);
+    atomicOr(p.status, kStatusPipelineTimeout);
+  };
+
+  const int num_m = (p.M + S::BM - 1) / S::BM;
+  const int num_n = p.N / S::BN;
+  const int num_kb = (p.K + S::BK - 1) / S::BK;
+  const int num_tiles = num_m * num_n;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------------------------------------------------- producer
+    uint32_t it = 0;
+    bool ok = true;
+    for (int tile = pair; tile < num_tiles && ok; tile += npairs) {
+      const int m0 = (tile / num_n) * S::BM + static_cast<int>(rank) * S::HALF;
+      const int nb = (tile % num_n) * S::BN + static_cast<int>(rank) * S::HALF;
+      for (int kb = 0; kb < num_kb; ++kb, ++it) {
+        const int s = it % S::STAGES;
+        const uint32_t ph = (it / S::STAGES) & 1;
+        if (!mbar_wait_bounded(empty_bar(s), ph ^ 1u, abort_flag, p.timeout_ns)) {
+          ok = false;
+          break;
+        }
+        if (rank == 0) mbar_arrive_expect_tx(full_bar(s), 2 * S::STAGE_BYTES);
+        tma_load_2d_pair(smem_u32(sA + s * S::A_BYTES), &tmA, kb * S::BK, m0, full_leader0 + 8u * s);
+        tma_load_2d_pair(smem_u32(sB + s * S::B_BYTES), &tmB, kb * S::BK, nb, full_leader0 + 8u * s);
+      }
+    }
+    if (!ok) raise_abort();
+    const uint32_t slot = smem_u32(const_cast<uint32_t*>(issued)) + 4u * rank;
+    st_cluster_u32(map_to_cta(slot, 0), it);
+    st_cluster_u32(map_to_cta(slot, 1), it);
+  } else if (warp == 1 && lane == 0 && rank == 0) {
+    // ---------------------------------------------------------- MMA issuer (leader)
+    constexpr uint32_t idesc = mma_idesc(IN_FP8 ? 0u : 1u, S::BN, S::BM);
+    int it = 0, local = 0;
+    bool ok = true;
+    for (int tile = pair; tile < num_tiles && ok; tile += npairs, ++local) {
+      const int b = local & 1;
+      const uint32_t aph = (local >> 1) & 1;
+      if (!mbar_wait_bounded(tempty_bar(b), aph ^ 1u, abort_flag, p.timeout_ns)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(b * S::BN);
+      for (int kb = 0; kb < num_kb; ++kb, ++it) {
+        const int s = it % S::STAGES;
+        const uint32_t ph = (it / S::STAGES) & 1;
+        if (!mbar_wait_bounded(full_bar(s), ph, abort_flag, p.timeout_ns)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(sA + s * S::A_BYTES);
+        const uint32_t b0 = smem_u32(sB + s * S::B_BYTES);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint64_t ad = sw128_kmajor_desc(a0 + 32u * j);
+          const uint64_t bd = sw128_kmajor_desc(b0 + 32u * j);
+          const uint32_t acc = (kb | j) != 0 ? 1u : 0u;
+          if constexpr (IN_FP8)
+            tc_mma_pair_f8(d_tmem, ad, bd, idesc, acc);
+          else
+            tc_mma_pair_f16(d_tmem, ad, bd, idesc, acc);
+        }
+        tc_commit_pair_multicast(empty_bar(s), 0x3);  // stage s free in both CTAs
+      }
+      if (!ok) break;
+      tc_commit_pair_multicast(tfull_bar(b), 0x3);  // accumulator b ready in both CTAs
+    }
+    if (!ok) raise_abort();
+    tc_commit_pair(mdone_bar);
+    mbar_wait_bounded(mdone_bar, 0, nullptr, kPairDrainNs);
+  } else if (warp >= 2) {
+    // ---------------------------------------------------------- epilogue (both CTAs)
+    const int q = warp & 3;
+    const int r_local = q * 32 + lane;
+    const uint32_t tempty_leader0 = map_to_cta(tempty_bar(0), 0);
+    int local = 0;
+    for (int tile = pair; tile < num_tiles; tile += npairs, ++local) {
+      const int b = local & 1;
+      const uint32_t aph = (local >> 1) & 1;
+      bool ok = mbar_wait_bounded(tfull_bar(b), aph, abort_flag, p.timeout_ns);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        if (lane == 0) raise_abort();
+        break;
+      }
+      tc_fence_after();
+      const int m_blk = tile / num_n;
+      const int n_blk = tile % num_n;
+      const int row = m_blk * S::BM + static_cast<int>(rank) * S::HALF + r_local;
+      const bool row_ok = row < p.M;
+      const int n0 = n_blk * S::BN;
+      const uint32_t tbase = tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
+                             static_cast<uint32_t>(b * S::BN);
+      float h0 = 0.f, h1 = 0.f;
+#pragma unroll 1
+      for (int c = 0; c < S::BN / 32; ++c) {
+        uint32_t v[32];
+        tmem_ld32(tbase + 32u * c, v);
+        tmem_wait_ld();
+        const int nc = n0 + 32 * c;
+        float x[32];
+        const float4* b4 = reinterpret_cast<const float4*>(p.bias + nc);
+#pragma unroll
+        for (int j4 = 0; j4 < 8; ++j4) {
+          const float4 bb = __ldg(b4 + j4);
+          float4 cs = make_float4(1.f, 1.f, 1.f, 1.f);
+          if (p.col_scale != nullptr) cs = __ldg(reinterpret_cast<const float4*>(p.col_scale + nc) + j4);
+          x[4 * j4 + 0] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 0]), cs.x, bb.x), 0.f);
+          x[4 * j4 + 1] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 1]), cs.y, bb.y), 0.f);
+          x[4 * j4 + 2] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 2]), cs.z, bb.z), 0.f);
+          x[4 * j4 + 3] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 3]), cs.w, bb.w), 0.f);
+        }
+        if (p.mode == 0) {
+          if (row_ok) {
+            if constexpr (OUT_FP8) {
+              uint8_t* dst = static_cast<uint8_t*>(p.out) + static_cast<size_t>(row) * p.ldo + nc;
+              const float os = p.out_scale;
+              uint4 w0, w1;
+              w0.x = pack_e4m3x4_p(x[0] * os, x[1] * os, x[2] * os, x[3] * os);
+              w0.y = pack_e4m3x4_p(x[4] * os, x[5] * os, x[6] * os, x[7] * os);
+              w0.z = pack_e4m3x4_p(x[8] * os, x[9] * os, x[10] * os, x[11] * os);
+              w0.w = pack_e4m3x4_p(x[12] * os, x[13] * os, x[14] * os, x[15] * os);
+              w1.x = pack_e4m3x4_p(x[16] * os, x[17] * os, x[18] * os, x[19] * os);
+              w1.y = pack_e4m3x4_p(x[20] * os, x[21] * os, x[22] * os, x[23] * os);
+              w1.z = pack_e4m3x4_p(x[24] * os, x[25] * os, x[26] * os, x[27] * os);
+              w1.w = pack_e4m3x4_p(x[28] * os, x[29] * os, x[30] * os, x[31] * os);
+              reinterpret_cast<uint4*>(dst)[0] = w0;
+              reinterpret_cast<uint4*>(dst)[1] = w1;
+            } else {
+              __nv_bfloat16* dst =
+                  static_cast<__nv_bfloat16*>(p.out) + static_cast<size_t>(row) * p.ldo + nc;
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                uint4 w;
+                w.x = pack_bf16x2_p(x[8 * k + 0], x[8 * k + 1]);
+                w.y = pack_bf16x2_p(x[8 * k + 2], x[8 * k + 3]);
+                w.z = pack_bf16x2_p(x[8 * k + 4], x[8 * k + 5]);
+                w.w = pack_bf16x2_p(x[8 * k + 6], x[8 * k + 7]);
+                reinterpret_cast<uint4*>(dst)[k] = w;
+              }
+            }
+          }
+        } else {
+          const float4* w0 = reinterpret_cast<const float4*>(p.head_w + nc);
+          const float4* w1 = reinterpret_cast<const float4*>(p.head_w + p.N + nc);
+#pragma unroll
+          for (int j4 = 0; j4 < 8; ++j4) {
+            const float4 a = __ldg(w0 + j4);
+            const float4 bb = __ldg(w1 + j4);
+            h0 = fmaf(x[4 * j4 + 0], a.x, h0);
+            h0 = fmaf(x[4 * j4 + 1], a.y, h0);
+            h0 = fmaf(x[4 * j4 + 2], a.z, h0);
+            h0 = fmaf(x[4 * j4 + 3], a.w, h0);
+            h1 = fmaf(x[4 * j4 + 0], bb.x, h1);
+            h1 = fmaf(x[4 * j4 + 1], bb.y, h1);
+            h1 = fmaf(x[4 * j4 + 2], bb.z, h1);
+            h1 = fmaf(x[4 * j4 + 3], bb.w, h1);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(tempty_leader0 + 8u * b);
+      if (p.mode != 0 && row_ok)
+        p.head_part[static_cast<size_t>(n_blk) * p.M + row] = make_float2(h0, h1);
+    }
+  }
+
+  // ---------------------------------------------------------- teardown
+  tc_fence_before();
+  cluster_sync_all();  // #1: no role issues anything new; issue counts published
+  if (warp == 0 && lane == 0) {
+    const uint32_t mine = issued[rank], other = issued[rank ^ 1u];
+    // Copy this CTA's half of any stage the other producer issued and this one
+    // did not (only after an abort), so every armed full[] phase can complete.
+    for (uint32_t j = mine; j < other; ++j) {
+      const int s = j % S::STAGES;
+      if (rank == 0) mbar_arrive_expect_tx(full_bar(s), 2 * S::STAGE_BYTES);
+      tma_load_2d_pair(smem_u32(sA + s * S::A_BYTES), &tmA, 0, 0, full_leader0 + 8u * s);
+      tma_load_2d_pair(smem_u32(sB + s * S::B_BYTES), &tmB, 0, 0, full_leader0 + 8u * s);
+    }
+    if (rank == 0) {
+      const uint32_t jmax = mine > other ? mine : other;
+      const uint32_t jlo = jmax > static_cast<uint32_t>(S::STAGES) ? jmax - S::STAGES : 0u;
+      for (uint32_t j = jlo; j < jmax; ++j)
+        mbar_wait_bounded(full_bar(j % S::STAGES), (j / S::STAGES) & 1, nullptr, kPairDrainNs);
+    }
+  }
+  tc_fence_before();
+  cluster_sync_all();  // #2: every copy landed, every MMA finished
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc_pair(tmem_base, S::TMEM_COLS);
+  }
+}
+
+template <bool IN_FP8, bool OUT_FP8>
+cudaError_t launch_pair_one(const CUtensorMap& tmA, const CUtensorMap& tmB,
+                            const TcGemmParams& p, int grid, cudaStream_t s) {
+  using S = PairShape<IN_FP8>;
+  auto kern = tc_gemm_pair_kernel<IN_FP8, OUT_FP8>;
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, 192, S::SMEM_BYTES, s>>>(tmA, tmB, p);
+  return cudaGetLastError();
+}
+
+template <bool IN_FP8, bool OUT_FP8>
+int max_pairs_for() {
+  using S = PairShape<IN_FP8>;
+  auto kern = tc_gemm_pair_kernel<IN_FP8, OUT_FP8>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_BYTES) !=
+      cudaSuccess)
+    return 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2, 1, 1);
+  cfg.blockDim = dim3(192, 1, 1);
+  cfg.dynamicSmemBytes = S::SMEM_BYTES;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+}  // namespace
+
+int tc_gemm_pair_max_clusters(bool in_fp8) {
+  return in_fp8 ? max_pairs_for<true, false>() : max_pairs_for<false, false>();
+}
+
+cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, const CUtensorMap& tmA,
+                                const CUtensorMap& tmB, const TcGemmParams& p, int clusters,
+                                cudaStream_t s) {
+  const int grid = 2 * clusters;
+  if (in_fp8) return out_fp8 ? launch_pair_one<true, true>(tmA, tmB, p, grid, s)
+                             : launch_pair_one<true, false>(tmA, tmB, p, grid, s);
+  return out_fp8 ? launch_pair_one<false, true>(tmA, tmB, p, grid, s)
+                 : launch_pair_one<false, false>(tmA, tmB, p, grid, s);
+}
+
+}  // namespace ddf

@@ -49,8 +49,9 @@ SIGNATURES = {
     "ddf_check_status": (C.c_int, [_vp, C.POINTER(C.c_uint32)]),
     "ddf_set_timeout_ns": (C.c_int, [_vp, _u64]),
     "ddf_set_chunk_rays": (C.c_int, [_vp, _i64]),
-    "ddf_set_tile": (C.c_int, [_vp, _i32, _i32]),
-    "ddf_get_tile": (C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "ddf_set_tile": (C.c_int, [_vp, _i32, _i32, _i32]),
+    "ddf_get_tile": (C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                               C.POINTER(C.c_int32)]),
     "ddf_autotune": (C.c_int, [_vp, _RAYS, _i64, _vp, C.POINTER(C.c_double), _i32]),
     "ddf_profile_enable": (C.c_int, [_vp, _i32]),
     "ddf_profile_read": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
@@ -203,24 +204,25 @@ def ddf_set_chunk_rays(h, chunk: int) -> None:
     _call("ddf_set_chunk_rays", h, int(chunk))
 
 
-def ddf_set_tile(h, bn: int, epi_warps: int) -> None:
-    _call("ddf_set_tile", h, int(bn), int(epi_warps))
+def ddf_set_tile(h, bn: int, epi_warps: int, cta_pair: int = 0) -> None:
+    _call("ddf_set_tile", h, int(bn), int(epi_warps), int(cta_pair))
 
 
 def ddf_get_tile(h):
-    bn, ew = C.c_int32(), C.c_int32()
-    _call("ddf_get_tile", h, C.byref(bn), C.byref(ew))
-    return bn.value, ew.value
+    """(bn, epi_warps, cta_pair)"""
+    bn, ew, pr = C.c_int32(), C.c_int32(), C.c_int32()
+    _call("ddf_get_tile", h, C.byref(bn), C.byref(ew), C.byref(pr))
+    return bn.value, ew.value, pr.value
 
 
-TILE_CANDIDATES = ((256, 4), (256, 8), (128, 4), (128, 8))
+TILE_CANDIDATES = ((256, 4, 0), (256, 8, 0), (128, 4, 0), (128, 8, 0), (256, 4, 1))
 
 
 def ddf_autotune(h, rays, n, stream=None):
-    """Returns {(bn, epi_warps): ms or None} and leaves the fastest tile set."""
+    """Returns {(bn, epi_warps, cta_pair): ms or None}; leaves the fastest tile set."""
     rp, keep = _rays(rays)
-    ms = (C.c_double * 4)()
-    _call("ddf_autotune", h, rp, int(n), _stream(stream), ms, 4)
+    ms = (C.c_double * 5)()
+    _call("ddf_autotune", h, rp, int(n), _stream(stream), ms, 5)
     return {c: (ms[i] if ms[i] >= 0 else None) for i, c in enumerate(TILE_CANDIDATES)}
 
 
