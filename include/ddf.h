@@ -64,6 +64,7 @@ typedef enum {
  *                  laid out as [ox,oy,oz,dx,dy,dz, then for each coordinate c
  *                  and band k: sin(pi 2^k e_c), cos(pi 2^k e_c)], L <= 16
  *   width          hidden width W; tensor-core precisions need W % 128 == 0
+ *                  and W <= 2048
  *   hidden_layers  H >= 1 ReLU layers (D_in -> W, then H-1 times W -> W)
  *   precision      a ddf_precision value
  *   device         CUDA device ordinal the handle lives on */
@@ -192,7 +193,7 @@ ddf_status ddf_autotune(ddf_handle h, const float* const rays[6], int64_t n, voi
 
 /* Kernel timing. When on, the library brackets every launch with CUDA events
  * on the launching stream, grouped by kernel class:
- *   0 encode, 1 hidden-layer GEMM, 2 head/finish, 3 other.
+ *   0 encode, 1 hidden-layer GEMM (layers 2..H), 2 head/finish, 3 first-layer GEMM.
  * ddf_profile_read synchronises, then stores per class the summed device time
  * in milliseconds (ms[4]) and launch counts (launches[4]), and resets them. */
 ddf_status ddf_profile_enable(ddf_handle h, int32_t on);

@@ -87,7 +87,7 @@ bool make_tmap(CUtensorMap* m, const void* base, bool one_byte, uint64_t inner, 
 }
 
 constexpr int kProfClasses = 4;
-enum ProfClass { kProfEncode = 0, kProfGemm = 1, kProfHead = 2, kProfOther = 3 };
+enum ProfClass { kProfEncode = 0, kProfGemm = 1, kProfHead = 2, kProfFirst = 3 };
 
 }  // namespace
 
@@ -265,7 +265,7 @@ ddf_status forward_f32(ddf_s* h, ddf::RaySoA rays, int m, ddf::HeadOut out, cuda
   int K = h->kp32;
   for (int l = 0; l < h->cfg.hidden_layers; ++l) {
     float* C = static_cast<float*>(h->ws_act[l & 1]);
-    ProfScope ps(h, kProfGemm, st);
+    ProfScope ps(h, l == 0 ? kProfFirst : kProfGemm, st);
     DDF_CK(ddf::launch_sgemm_relu(A, h->wf[l], h->bias[l], C, m, W, K, st));
     A = C;
     K = W;
@@ -308,7 +308,7 @@ ddf_status forward_tc(ddf_s* h, ddf::RaySoA rays, int m, ddf::HeadOut out, cudaS
     p.mode = last ? 1 : 0;
     p.status = h->status_dev;
     p.timeout_ns = h->timeout_ns;
-    ProfScope ps(h, kProfGemm, st);
+    ProfScope ps(h, l == 0 ? kProfFirst : kProfGemm, st);
     if (h->tile.pair) {
       const int64_t tiles = ((m + 255) / 256) * static_cast<int64_t>(W / 256);
       const int clusters = static_cast<int>(std::min<int64_t>(tiles, h->pair_clusters));
@@ -397,6 +397,8 @@ ddf_status ddf_create(const ddf_config* cfg, ddf_handle* out) {
   if (!valid_config(cfg, &why)) return fail(DDF_ERR_INVALID_ARG, why);
   if (cfg->precision != DDF_FP32 && cfg->width % 128 != 0)
     return fail(DDF_ERR_UNSUPPORTED, "tensor-core precisions need width % 128 == 0");
+  if (cfg->precision != DDF_FP32 && cfg->width > 2048)
+    return fail(DDF_ERR_UNSUPPORTED, "tensor-core precisions support width <= 2048");
   int ndev = 0;
   DDF_CK(cudaGetDeviceCount(&ndev));
   if (cfg->device >= ndev) return fail(DDF_ERR_INVALID_ARG, "device ordinal out of range");

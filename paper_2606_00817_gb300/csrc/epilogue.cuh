@@ -1,0 +1,153 @@
+// epilogue.cuh -- the accumulator epilogue shared by the tensor-core layer
+// kernels (tc_gemm.cu, tc_gemm_pair.cu).
+//
+// One thread owns one row of a 128-lane TMEM accumulator. For the columns
+// [32 c_begin, 32 c_end) of its tile it computes x = ReLU(acc * scale + bias)
+// and either stores x (bf16, or e4m3 after out_scale) as the next layer's
+// activation or folds x into the two FP32 head dot products. The per-column
+// vectors are read from shared memory (staged once per CTA), and the TMEM load
+// of chunk c+1 is issued before chunk c is processed so the load latency
+// overlaps the arithmetic and the stores.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "kernels.h"
+#include "ptx_sm103.cuh"
+
+namespace ddf {
+
+// Column vectors of one layer staged in shared memory.
+struct EpiVectors {
+  const float* bias;   // [N]
+  const float* scale;  // [N] or nullptr
+  const float* hw0;    // [N] or nullptr (mode 1)
+  const float* hw1;    // [N] or nullptr (mode 1)
+};
+
+// Widest layer whose vectors the tensor-core kernels stage (4 x 2048 floats
+// fit next to 192 KB of pipeline stages within the 227 KB per CTA).
+constexpr int kMaxStagedColumns = 2048;
+
+// Bytes of shared memory the staged vectors of an N-column layer need.
+__host__ __device__ constexpr int epi_vector_bytes(int n) { return 4 * n * 4; }
+
+// Cooperative copy of the layer's vectors into shared memory (all threads).
+__device__ __forceinline__ EpiVectors stage_epi_vectors(const TcGemmParams& p, float* smem) {
+  const int n = p.N;
+  float* sb = smem;
+  float* ss = smem + n;
+  float* s0 = smem + 2 * n;
+  float* s1 = smem + 3 * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    sb[i] = p.bias[i];
+    if (p.col_scale != nullptr) ss[i] = p.col_scale[i];
+    if (p.mode != 0) {
+      s0[i] = p.head_w[i];
+      s1[i] = p.head_w[n + i];
+    }
+  }
+  return EpiVectors{sb, p.col_scale != nullptr ? ss : nullptr, p.mode != 0 ? s0 : nullptr,
+                    p.mode != 0 ? s1 : nullptr};
+}
+
+__device__ __forceinline__ uint32_t epi_pack_bf16x2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ uint32_t epi_pack_e4m3x4(float a, float b, float c, float d) {
+  const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+  const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+  return (lo & 0xFFFFu) | (hi << 16);
+}
+
+// Processes the 32 accumulator values v of columns [nc, nc + 32) of `row`.
+template <bool OUT_FP8>
+__device__ __forceinline__ void epi_chunk(const TcGemmParams& p, const EpiVectors& ev,
+                                          const uint32_t (&v)[32], int row, bool row_ok, int nc,
+                                          float& h0, float& h1) {
+  float x[32];
+  const float4* b4 = reinterpret_cast<const float4*>(ev.bias + nc);
+#pragma unroll
+  for (int j4 = 0; j4 < 8; ++j4) {
+    const float4 bb = b4[j4];
+    float4 cs = make_float4(1.f, 1.f, 1.f, 1.f);
+    if (ev.scale != nullptr) cs = reinterpret_cast<const float4*>(ev.scale + nc)[j4];
+    x[4 * j4 + 0] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 0]), cs.x, bb.x), 0.f);
+    x[4 * j4 + 1] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 1]), cs.y, bb.y), 0.f);
+    x[4 * j4 + 2] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 2]), cs.z, bb.z), 0.f);
+    x[4 * j4 + 3] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 3]), cs.w, bb.w), 0.f);
+  }
+  if (p.mode == 0) {
+    if (!row_ok) return;
+    if constexpr (OUT_FP8) {
+      uint8_t* dst = static_cast<uint8_t*>(p.out) + static_cast<size_t>(row) * p.ldo + nc;
+      const float os = p.out_scale;
+      uint4 w0, w1;
+      w0.x = epi_pack_e4m3x4(x[0] * os, x[1] * os, x[2] * os, x[3] * os);
+      w0.y = epi_pack_e4m3x4(x[4] * os, x[5] * os, x[6] * os, x[7] * os);
+      w0.z = epi_pack_e4m3x4(x[8] * os, x[9] * os, x[10] * os, x[11] * os);
+      w0.w = epi_pack_e4m3x4(x[12] * os, x[13] * os, x[14] * os, x[15] * os);
+      w1.x = epi_pack_e4m3x4(x[16] * os, x[17] * os, x[18] * os, x[19] * os);
+      w1.y = epi_pack_e4m3x4(x[20] * os, x[21] * os, x[22] * os, x[23] * os);
+      w1.z = epi_pack_e4m3x4(x[24] * os, x[25] * os, x[26] * os, x[27] * os);
+      w1.w = epi_pack_e4m3x4(x[28] * os, x[29] * os, x[30] * os, x[31] * os);
+      reinterpret_cast<uint4*>(dst)[0] = w0;
+      reinterpret_cast<uint4*>(dst)[1] = w1;
+    } else {
+      __nv_bfloat16* dst =
+          static_cast<__nv_bfloat16*>(p.out) + static_cast<size_t>(row) * p.ldo + nc;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        uint4 w;
+        w.x = epi_pack_bf16x2(x[8 * k + 0], x[8 * k + 1]);
+        w.y = epi_pack_bf16x2(x[8 * k + 2], x[8 * k + 3]);
+        w.z = epi_pack_bf16x2(x[8 * k + 4], x[8 * k + 5]);
+        w.w = epi_pack_bf16x2(x[8 * k + 6], x[8 * k + 7]);
+        reinterpret_cast<uint4*>(dst)[k] = w;
+      }
+    }
+  } else {
+    const float4* w0 = reinterpret_cast<const float4*>(ev.hw0 + nc);
+    const float4* w1 = reinterpret_cast<const float4*>(ev.hw1 + nc);
+#pragma unroll
+    for (int j4 = 0; j4 < 8; ++j4) {
+      const float4 a = w0[j4];
+      const float4 bb = w1[j4];
+      h0 = fmaf(x[4 * j4 + 0], a.x, h0);
+      h0 = fmaf(x[4 * j4 + 1], a.y, h0);
+      h0 = fmaf(x[4 * j4 + 2], a.z, h0);
+      h0 = fmaf(x[4 * j4 + 3], a.w, h0);
+      h1 = fmaf(x[4 * j4 + 0], bb.x, h1);
+      h1 = fmaf(x[4 * j4 + 1], bb.y, h1);
+      h1 = fmaf(x[4 * j4 + 2], bb.z, h1);
+      h1 = fmaf(x[4 * j4 + 3], bb.w, h1);
+    }
+  }
+}
+
+// Drains chunks [c_begin, c_end) of this thread's TMEM row (tbase = lane
+// quarter + accumulator column base), columns n0 + 32 c.
+template <bool OUT_FP8>
+__device__ __forceinline__ void epi_row(const TcGemmParams& p, const EpiVectors& ev,
+                                        uint32_t tbase, int row, bool row_ok, int n0, int c_begin,
+                                        int c_end, float& h0, float& h1) {
+  uint32_t va[32], vb[32];
+  tmem_ld32(tbase + 32u * c_begin, va);
+  tmem_wait_ld_regs(va);
+#pragma unroll 1
+  for (int c = c_begin; c < c_end; c += 2) {
+    const bool next = c + 1 < c_end;
+    if (next) tmem_ld32(tbase + 32u * (c + 1), vb);  // in flight during chunk c
+    epi_chunk<OUT_FP8>(p, ev, va, row, row_ok, n0 + 32 * c, h0, h1);
+    if (!next) break;
+    tmem_wait_ld_regs(vb);
+    const bool next2 = c + 2 < c_end;
+    if (next2) tmem_ld32(tbase + 32u * (c + 2), va);  // in flight during chunk c+1
+    epi_chunk<OUT_FP8>(p, ev, vb, row, row_ok, n0 + 32 * (c + 1), h0, h1);
+    if (next2) tmem_wait_ld_regs(va);
+  }
+}
+
+}  // namespace ddf

@@ -23,6 +23,25 @@ __device__ __forceinline__ __nv_bfloat16 to_out<__nv_bfloat16>(float v) {
   return __float2bfloat16_rn(v);
 }
 
+// 8 consecutive floats from shared memory to 8 consecutive outputs (16-byte
+// aligned destination).
+__device__ __forceinline__ void store8(__nv_bfloat16* dst, const float* src) {
+  uint4 w;
+  __nv_bfloat162 a = __floats2bfloat162_rn(src[0], src[1]);
+  __nv_bfloat162 b = __floats2bfloat162_rn(src[2], src[3]);
+  __nv_bfloat162 c = __floats2bfloat162_rn(src[4], src[5]);
+  __nv_bfloat162 d = __floats2bfloat162_rn(src[6], src[7]);
+  w.x = *reinterpret_cast<uint32_t*>(&a);
+  w.y = *reinterpret_cast<uint32_t*>(&b);
+  w.z = *reinterpret_cast<uint32_t*>(&c);
+  w.w = *reinterpret_cast<uint32_t*>(&d);
+  *reinterpret_cast<uint4*>(dst) = w;
+}
+__device__ __forceinline__ void store8(float* dst, const float* src) {
+  reinterpret_cast<float4*>(dst)[0] = make_float4(src[0], src[1], src[2], src[3]);
+  reinterpret_cast<float4*>(dst)[1] = make_float4(src[4], src[5], src[6], src[7]);
+}
+
 constexpr int kEncRays = 64;  // rays per block of the encoder
 
 // One block encodes kEncRays rays: each thread builds its ray's row in shared
@@ -57,12 +76,16 @@ __global__ void __launch_bounds__(kEncRays) encode_kernel(RaySoA rays, int64_t M
     for (; col < ld; ++col) row[col] = 0.f;
   }
   __syncthreads();
-  const int total = rows * ld;
+  // The block's rows are contiguous in global memory: write them 8 elements
+  // (16 bytes of bf16, 32 bytes of FP32) per thread step, consecutive threads
+  // on consecutive chunks. ld is a multiple of 8.
+  const int per_row = ld / 8;
+  const int total = rows * per_row;
   T* dst = out + r0 * ld;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int r = idx / ld;
-    const int c = idx - r * ld;
-    dst[idx] = to_out<T>(enc_smem[r * sld + c]);
+    const int r = idx / per_row;
+    const int c = (idx - r * per_row) * 8;
+    store8(dst + static_cast<int64_t>(r) * ld + c, enc_smem + r * sld + c);
   }
 }
 

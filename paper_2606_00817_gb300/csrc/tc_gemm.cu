@@ -23,6 +23,7 @@
 #include <cuda_fp8.h>
 
 #include "kernels.h"
+#include "epilogue.cuh"
 #include "ptx_sm103.cuh"
 
 namespace ddf {
@@ -42,24 +43,17 @@ struct TcShape {
   static constexpr int STAGES = (BN == 256) ? 4 : 6;
   static constexpr int TMEM_COLS = 2 * BN;              // two FP32 accumulators
   static constexpr int NUM_BARS = 2 * STAGES + 5;
-  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + NUM_BARS * 8 + 16 + 1024;
+  static constexpr int CTRL_BYTES = 256;  // barriers, TMEM slot, abort flag
+  static constexpr int VEC_OFFSET = STAGES * STAGE_BYTES + CTRL_BYTES;
+  // plus epi_vector_bytes(N) for the staged per-column vectors
+  static constexpr int SMEM_BYTES = VEC_OFFSET + 1024;
+  static_assert(NUM_BARS * 8 + 8 <= CTRL_BYTES, "control block overflow");
   static_assert(TMEM_COLS == 256 || TMEM_COLS == 512, "TMEM allocation must be a power of two");
 };
 
 __device__ __forceinline__ void raise_abort(volatile int* abort_flag, uint32_t* status) {
   *abort_flag = 1;
   atomicOr(status, kStatusPipelineTimeout);
-}
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<uint32_t*>(&v);
-}
-
-__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
-  const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
-  const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
-  return (lo & 0xFFFFu) | (hi << 16);
 }
 
 template <int BN, bool IN_FP8, bool OUT_FP8, int EPI>
@@ -104,6 +98,7 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
     tmem_alloc(smem_u32(tmem_slot), S::TMEM_COLS);
     tmem_relinquish();
   }
+  const EpiVectors ev = stage_epi_vectors(p, reinterpret_cast<float*>(smem + S::VEC_OFFSET));
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -208,72 +203,8 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
       const uint32_t tbase = tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
                              static_cast<uint32_t>(b * BN);
       float h0 = 0.f, h1 = 0.f;
-#pragma unroll 1
-      for (int c = half * kChunks; c < (half + 1) * kChunks; ++c) {
-        uint32_t v[32];
-        tmem_ld32(tbase + 32u * c, v);
-        tmem_wait_ld();
-        const int nc = n0 + 32 * c;
-        float x[32];
-        const float4* b4 = reinterpret_cast<const float4*>(p.bias + nc);
-#pragma unroll
-        for (int j4 = 0; j4 < 8; ++j4) {
-          const float4 bb = __ldg(b4 + j4);
-          float4 cs = make_float4(1.f, 1.f, 1.f, 1.f);
-          if (p.col_scale != nullptr) cs = __ldg(reinterpret_cast<const float4*>(p.col_scale + nc) + j4);
-          x[4 * j4 + 0] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 0]), cs.x, bb.x), 0.f);
-          x[4 * j4 + 1] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 1]), cs.y, bb.y), 0.f);
-          x[4 * j4 + 2] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 2]), cs.z, bb.z), 0.f);
-          x[4 * j4 + 3] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 3]), cs.w, bb.w), 0.f);
-        }
-        if (p.mode == 0) {
-          if (row_ok) {
-            if constexpr (OUT_FP8) {
-              uint8_t* dst = static_cast<uint8_t*>(p.out) + static_cast<size_t>(row) * p.ldo + nc;
-              const float os = p.out_scale;
-              uint4 w0, w1;
-              w0.x = pack_e4m3x4(x[0] * os, x[1] * os, x[2] * os, x[3] * os);
-              w0.y = pack_e4m3x4(x[4] * os, x[5] * os, x[6] * os, x[7] * os);
-              w0.z = pack_e4m3x4(x[8] * os, x[9] * os, x[10] * os, x[11] * os);
-              w0.w = pack_e4m3x4(x[12] * os, x[13] * os, x[14] * os, x[15] * os);
-              w1.x = pack_e4m3x4(x[16] * os, x[17] * os, x[18] * os, x[19] * os);
-              w1.y = pack_e4m3x4(x[20] * os, x[21] * os, x[22] * os, x[23] * os);
-              w1.z = pack_e4m3x4(x[24] * os, x[25] * os, x[26] * os, x[27] * os);
-              w1.w = pack_e4m3x4(x[28] * os, x[29] * os, x[30] * os, x[31] * os);
-              reinterpret_cast<uint4*>(dst)[0] = w0;
-              reinterpret_cast<uint4*>(dst)[1] = w1;
-            } else {
-              __nv_bfloat16* dst =
-                  static_cast<__nv_bfloat16*>(p.out) + static_cast<size_t>(row) * p.ldo + nc;
-#pragma unroll
-              for (int k = 0; k < 4; ++k) {
-                uint4 w;
-                w.x = pack_bf16x2(x[8 * k + 0], x[8 * k + 1]);
-                w.y = pack_bf16x2(x[8 * k + 2], x[8 * k + 3]);
-                w.z = pack_bf16x2(x[8 * k + 4], x[8 * k + 5]);
-                w.w = pack_bf16x2(x[8 * k + 6], x[8 * k + 7]);
-                reinterpret_cast<uint4*>(dst)[k] = w;
-              }
-            }
-          }
-        } else {
-          const float4* w0 = reinterpret_cast<const float4*>(p.head_w + nc);
-          const float4* w1 = reinterpret_cast<const float4*>(p.head_w + p.N + nc);
-#pragma unroll
-          for (int j4 = 0; j4 < 8; ++j4) {
-            const float4 a = __ldg(w0 + j4);
-            const float4 bb = __ldg(w1 + j4);
-            h0 = fmaf(x[4 * j4 + 0], a.x, h0);
-            h0 = fmaf(x[4 * j4 + 1], a.y, h0);
-            h0 = fmaf(x[4 * j4 + 2], a.z, h0);
-            h0 = fmaf(x[4 * j4 + 3], a.w, h0);
-            h1 = fmaf(x[4 * j4 + 0], bb.x, h1);
-            h1 = fmaf(x[4 * j4 + 1], bb.y, h1);
-            h1 = fmaf(x[4 * j4 + 2], bb.z, h1);
-            h1 = fmaf(x[4 * j4 + 3], bb.w, h1);
-          }
-        }
-      }
+      epi_row<OUT_FP8>(p, ev, tbase, row, row_ok, n0, half * kChunks, (half + 1) * kChunks, h0,
+                       h1);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty_bar(b));
@@ -298,10 +229,10 @@ cudaError_t launch_one(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcG
   using S = TcShape<BN, IN_FP8>;
   auto kern = tc_gemm_kernel<BN, IN_FP8, OUT_FP8, EPI>;
   // applies to the current device; cheap enough to repeat on every launch
-  cudaError_t e =
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_BYTES);
+  const int smem = S::SMEM_BYTES + epi_vector_bytes(p.N);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, 64 + 32 * EPI, S::SMEM_BYTES, s>>>(tmA, tmB, p);
+  kern<<<grid, 64 + 32 * EPI, smem, s>>>(tmA, tmB, p);
   return cudaGetLastError();
 }
 

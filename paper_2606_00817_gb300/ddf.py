@@ -21,7 +21,7 @@ DDF_FP32, DDF_BF16, DDF_FP8_E4M3 = 0, 1, 2
 PRECISIONS = {"fp32": DDF_FP32, "bf16": DDF_BF16, "fp8": DDF_FP8_E4M3}
 STATUS = {0: "DDF_OK", 1: "DDF_ERR_INVALID_ARG", 2: "DDF_ERR_CUDA", 3: "DDF_ERR_OOM",
           4: "DDF_ERR_BAD_WEIGHTS", 5: "DDF_ERR_UNSUPPORTED", 6: "DDF_ERR_TIMEOUT"}
-PROFILE_CLASSES = ("encode", "gemm", "head", "other")
+PROFILE_CLASSES = ("encode", "gemm", "head", "gemm_first")
 
 # every entry point of include/ddf.h: name -> (restype, argtypes)
 _vp, _i32, _i64, _u64, _sz = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_size_t
