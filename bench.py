@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--rays", type=int, default=4_194_304)
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32 comparison run")
     ap.add_argument("--oracle-seconds", type=float, default=12.0)
-    ap.add_argument("--tile", default="auto", help="auto (autotune) or BNxEPI[pair], e.g. 256x8, 256x4pair")
+    ap.add_argument("--tile", default="auto", help="auto (autotune) or BNxEPI[pair][staged], e.g. 256x8, 256x4pairstaged")
     return ap.parse_args()
 
 
@@ -204,15 +204,19 @@ def main():
         raise SystemExit("fp8 headline needs activation-scale calibration; use bf16")
     m.load(blob)
     tune_ms = None
+    fmt = lambda k: f"{k[0]}x{k[1]}{'pair' if k[2] else ''}{'staged' if k[3] else ''}"
     if args.tile == "auto":
         nt = min(R, 1 << 20)
-        tune_ms = {f"{k[0]}x{k[1]}{'pair' if k[2] else ''}": v for k, v in
-                   ddf.ddf_autotune(m.h, [r[:nt] for r in d_rays], nt, stream).items()}
+        p1, p2 = ddf.ddf_autotune(m.h, [r[:nt] for r in d_rays], nt, stream)
+        tune_ms = {"all_layers": {fmt(k): v for k, v in p1.items()},
+                   "first_layer": {fmt(k): v for k, v in p2.items()}}
     else:
-        pair = args.tile.endswith("pair")
-        bn, ew = (int(x) for x in args.tile.replace("pair", "").split("x"))
-        ddf.ddf_set_tile(m.h, bn, ew, int(pair))
-    tile = ddf.ddf_get_tile(m.h)
+        spec = args.tile
+        t4 = (256 if spec.startswith("256") else 128, 8 if "x8" in spec else 4,
+              int("pair" in spec), int("staged" in spec))
+        ddf.ddf_set_tile(m.h, t4, 0)
+        ddf.ddf_set_tile(m.h, t4, 1)
+    tile = {"hidden": fmt(ddf.ddf_get_tile(m.h, 0)), "first": fmt(ddf.ddf_get_tile(m.h, 1))}
 
     def step():
         ddf.ddf_query_shadow(m.h, d_rays, R, LIGHT, t, vis, occ, stream)
@@ -348,8 +352,7 @@ def main():
                        "l2": "512 MiB buffer written between timed steps (L2 flush)",
                        "timing": "CUDA events per step on the launching stream",
                        "wall_s_timed_region": wall,
-                       "tile": {"bn": tile[0], "epi_warps": tile[1], "cta_pair": tile[2],
-                                "autotune_ms_1M_rays": tune_ms}},
+                       "tile": {**tile, "autotune_ms_1M_rays": tune_ms}},
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(), "e2e": e2e,
             "gpu_launches": launches, "accuracy": acc, "compare": compare,
             "kernel_ms_by_class": {k: v[0] for k, v in prof.items()},

@@ -170,24 +170,38 @@ ddf_status ddf_set_timeout_ns(ddf_handle h, uint64_t ns);
  * that at FP32. */
 ddf_status ddf_set_chunk_rays(ddf_handle h, int64_t chunk);
 
-/* Tensor-core tile of the layer kernel: bn = N tile (128 or 256; 256 needs
- * width % 256 == 0), epi_warps = epilogue warps draining the TMEM accumulator
- * (4, or 8 = two per lane quarter), cta_pair = 1 for the 256 x 256 tile that a
- * cluster of two CTAs computes with one pair MMA (needs bn 256, 4 warps).
- * Results agree across tiles up to FP32 rounding of the head sums. Default:
- * bn 256 where possible, 4 warps, no pair. ddf_set_tile synchronises the
- * device when weights are loaded. */
-ddf_status ddf_set_tile(ddf_handle h, int32_t bn, int32_t epi_warps, int32_t cta_pair);
-ddf_status ddf_get_tile(ddf_handle h, int32_t* bn, int32_t* epi_warps, int32_t* cta_pair);
+/* Tensor-core tile of the layer kernel.
+ *   bn         N tile, 128 or 256 (256 needs width % 256 == 0)
+ *   epi_warps  epilogue warps draining the TMEM accumulator: 4, or 8 (two per
+ *              TMEM lane quarter, each draining half the columns)
+ *   cta_pair   1: the 256 x 256 tile a cluster of two CTAs computes with one
+ *              pair MMA (needs bn 256, epi_warps 4)
+ *   staged     1: pair tile only; activations leave through shared memory as
+ *              whole 128-byte lines instead of per-thread 16-byte pieces */
+typedef struct {
+  int32_t bn;
+  int32_t epi_warps;
+  int32_t cta_pair;
+  int32_t staged;
+} ddf_tile;
 
-/* Autotuner: runs every supported tile on n rays (device SoA, 1 <= n <= 2^24)
- * on stream, rejects any candidate whose t or vis differ from the first
- * candidate's by more than 1e-3 (relative to max(1, |ref|)), times each
- * passing candidate over 3 queries with CUDA events and keeps the fastest.
- * ms_out (nullable, n_out >= 5) receives per-candidate ms for the order
- * (256,4), (256,8), (128,4), (128,8), (256,4,pair); -1 marks skipped or
- * rejected ones. Synchronous; allocates 16 n bytes of device memory while it
- * runs. A no-op on FP32 handles. */
+/* Tile of layer 1 (which = 1) or of layers 2..H (which = 0). Results agree
+ * across tiles up to FP32 rounding of the head sums. Default: bn 256 where
+ * possible, 4 warps, no pair, not staged, for both. Synchronises the device
+ * when weights are loaded. */
+ddf_status ddf_set_tile(ddf_handle h, int32_t which, const ddf_tile* tile);
+ddf_status ddf_get_tile(ddf_handle h, int32_t which, ddf_tile* tile);
+
+/* Autotuner over the 6 candidate tiles {256,4,0,0}, {256,8,0,0}, {128,4,0,0},
+ * {128,8,0,0}, {256,4,1,0}, {256,4,1,1} on n rays (device SoA,
+ * 1 <= n <= 2^24) on stream. Phase 1 uses one candidate for every layer and
+ * keeps the fastest for layers 2..H; phase 2 keeps that and tries each
+ * candidate for layer 1. Every configuration must give t and vis within 1e-3
+ * (relative to max(1, |ref|)) of the first configuration tried before it is
+ * timed (3 queries, CUDA events). ms_out (nullable, n_out >= 12) receives the
+ * per-query ms of phase 1 in [0..5] and phase 2 in [6..11], -1 where a
+ * candidate was skipped or rejected. Synchronous; allocates 16 n bytes of
+ * device memory while it runs. A no-op on FP32 handles. */
 ddf_status ddf_autotune(ddf_handle h, const float* const rays[6], int64_t n, void* stream,
                         double* ms_out, int32_t n_out);
 

@@ -97,7 +97,8 @@ struct ddf_s {
   int kp32 = 0;  // padded encoded width, FP32 rows (multiple of 8)
   int kp16 = 0;  // padded encoded width, bf16 rows (multiple of 8 -> 16-byte rows)
   int bn = 0;    // tensor-core N tile (= tile.bn)
-  ddf::TcTile tile{256, 4};
+  ddf::TcTile tile{256, 4};        // layers 2..H
+  ddf::TcTile tile_first{256, 4};  // layer 1
   int pair_clusters = 0;  // co-resident clusters of the CTA-pair kernel
   int num_sms = 0;
   bool loaded = false;
@@ -309,18 +310,20 @@ ddf_status forward_tc(ddf_s* h, ddf::RaySoA rays, int m, ddf::HeadOut out, cudaS
     p.status = h->status_dev;
     p.timeout_ns = h->timeout_ns;
     ProfScope ps(h, l == 0 ? kProfFirst : kProfGemm, st);
-    if (h->tile.pair) {
+    const ddf::TcTile& t = l == 0 ? h->tile_first : h->tile;
+    if (t.pair) {
       const int64_t tiles = ((m + 255) / 256) * static_cast<int64_t>(W / 256);
       const int clusters = static_cast<int>(std::min<int64_t>(tiles, h->pair_clusters));
-      DDF_CK(ddf::launch_tc_gemm_pair(in_fp8, out_fp8, tmA, h->tmB[l], p, clusters, st));
+      DDF_CK(ddf::launch_tc_gemm_pair(in_fp8, out_fp8, t.staged, tmA, h->tmB[l], p, clusters, st));
     } else {
-      const int64_t tiles = ((m + 127) / 128) * static_cast<int64_t>(W / h->tile.bn);
+      const int64_t tiles = ((m + 127) / 128) * static_cast<int64_t>(W / t.bn);
       const int grid = static_cast<int>(std::min<int64_t>(tiles, h->num_sms));
-      DDF_CK(ddf::launch_tc_gemm(h->tile, in_fp8, out_fp8, tmA, h->tmB[l], p, grid, st));
+      DDF_CK(ddf::launch_tc_gemm(t, in_fp8, out_fp8, tmA, h->tmB[l], p, grid, st));
     }
   }
   ProfScope ps(h, kProfHead, st);
-  const int nparts = h->tile.pair ? W / 256 : (W / h->tile.bn) * (h->tile.epi_warps / 4);
+  const ddf::TcTile& tl = H == 1 ? h->tile_first : h->tile;  // the last layer writes the partials
+  const int nparts = tl.pair ? W / 256 : (W / tl.bn) * (tl.epi_warps / 4);
   DDF_CK(ddf::launch_finish_heads(h->ws_part, nparts, m, h->head_b, out, st));
   return DDF_OK;
 }
@@ -328,8 +331,9 @@ ddf_status forward_tc(ddf_s* h, ddf::RaySoA rays, int m, ddf::HeadOut out, cudaS
 // (Re)builds the TMA maps of the weight matrices for the current N tile.
 ddf_status build_weight_maps(ddf_s* h) {
   const int W = h->cfg.width;
-  const uint32_t box_rows = h->tile.pair ? 128u : static_cast<uint32_t>(h->tile.bn);
   for (int l = 0; l < h->cfg.hidden_layers; ++l) {
+    const ddf::TcTile& t = l == 0 ? h->tile_first : h->tile;
+    const uint32_t box_rows = t.pair ? 128u : static_cast<uint32_t>(t.bn);
     bool ok = true;
     if (h->wb[l] != nullptr) {
       const int kp = l == 0 ? h->kp16 : W;
@@ -420,6 +424,7 @@ ddf_status ddf_create(const ddf_config* cfg, ddf_handle* out) {
   h->kp16 = static_cast<int>(round_up(h->d_in, 8));
   h->bn = (cfg->width % 256 == 0) ? 256 : 128;
   h->tile = ddf::TcTile{h->bn, 4};
+  h->tile_first = h->tile;
   if (cfg->precision != DDF_FP32 && cfg->width % 256 == 0)
     h->pair_clusters = std::min(ddf::tc_gemm_pair_max_clusters(false),
                                 ddf::tc_gemm_pair_max_clusters(true));
@@ -496,7 +501,8 @@ ddf_status ddf_load_weights(ddf_handle h, const float* host_blob, size_t n_float
         const int kp = l == 0 ? h->kp16 : W;
         if ((s = dev_alloc(h, &p, static_cast<size_t>(W) * kp * 2)) != DDF_OK) return s;
         h->wb[l] = static_cast<__nv_bfloat16*>(p);
-        if (!make_tmap(&h->tmB[l], h->wb[l], false, kp, W, static_cast<uint64_t>(kp) * 2, h->tile.bn))
+        if (!make_tmap(&h->tmB[l], h->wb[l], false, kp, W, static_cast<uint64_t>(kp) * 2,
+                       (l == 0 ? h->tile_first : h->tile).pair ? 128u : (l == 0 ? h->tile_first : h->tile).bn))
           return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for a weight map");
       } else {
         if ((s = dev_alloc(h, &p, static_cast<size_t>(W) * W)) != DDF_OK) return s;
@@ -505,7 +511,7 @@ ddf_status ddf_load_weights(ddf_handle h, const float* host_blob, size_t n_float
         h->wscale[l] = static_cast<float*>(p);
         if ((s = dev_alloc(h, &p, W * sizeof(float))) != DDF_OK) return s;
         h->colscale[l] = static_cast<float*>(p);
-        if (!make_tmap(&h->tmB[l], h->wq[l], true, W, W, W, h->tile.bn))
+        if (!make_tmap(&h->tmB[l], h->wq[l], true, W, W, W, h->tile.pair ? 128u : h->tile.bn))
           return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for a weight map");
       }
       (void)K;
@@ -768,17 +774,22 @@ ddf_status ddf_profile_read(ddf_handle h, double ms[4], int64_t launches[4]) {
 }
 
 
-ddf_status ddf_set_tile(ddf_handle h, int32_t bn, int32_t epi_warps, int32_t cta_pair) {
-  if (h == nullptr) return fail(DDF_ERR_INVALID_ARG, "handle is NULL");
-  if ((bn != 128 && bn != 256) || (epi_warps != 4 && epi_warps != 8))
+ddf_status ddf_set_tile(ddf_handle h, int32_t which, const ddf_tile* tile) {
+  if (h == nullptr || tile == nullptr) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+  if (which != 0 && which != 1) return fail(DDF_ERR_INVALID_ARG, "which must be 0 or 1");
+  const int bn = tile->bn, ew = tile->epi_warps;
+  if ((bn != 128 && bn != 256) || (ew != 4 && ew != 8))
     return fail(DDF_ERR_INVALID_ARG, "bn must be 128 or 256 and epi_warps 4 or 8");
   if (h->cfg.width % bn != 0) return fail(DDF_ERR_UNSUPPORTED, "width is not a multiple of bn");
-  if (cta_pair != 0 && (bn != 256 || epi_warps != 4))
+  if (tile->cta_pair != 0 && (bn != 256 || ew != 4))
     return fail(DDF_ERR_INVALID_ARG, "the CTA-pair tile is bn 256 with 4 epilogue warps");
-  if (cta_pair != 0 && h->pair_clusters <= 0)
+  if (tile->staged != 0 && tile->cta_pair == 0)
+    return fail(DDF_ERR_INVALID_ARG, "staged stores exist for the CTA-pair tile only");
+  if (tile->cta_pair != 0 && h->pair_clusters <= 0)
     return fail(DDF_ERR_UNSUPPORTED, "CTA-pair clusters do not fit on this device");
-  h->tile = ddf::TcTile{bn, epi_warps, cta_pair != 0};
-  h->bn = bn;
+  (which == 1 ? h->tile_first : h->tile) =
+      ddf::TcTile{bn, ew, tile->cta_pair != 0, tile->staged != 0};
+  h->bn = h->tile.bn;
   if (h->loaded && h->cfg.precision != DDF_FP32) {
     DeviceGuard g(h->cfg.device);
     DDF_CK(cudaDeviceSynchronize());  // launches in flight keep their own copies of the maps
@@ -787,14 +798,28 @@ ddf_status ddf_set_tile(ddf_handle h, int32_t bn, int32_t epi_warps, int32_t cta
   return DDF_OK;
 }
 
-ddf_status ddf_get_tile(ddf_handle h, int32_t* bn, int32_t* epi_warps, int32_t* cta_pair) {
-  if (h == nullptr || bn == nullptr || epi_warps == nullptr || cta_pair == nullptr)
-    return fail(DDF_ERR_INVALID_ARG, "NULL argument");
-  *bn = h->tile.bn;
-  *epi_warps = h->tile.epi_warps;
-  *cta_pair = h->tile.pair ? 1 : 0;
+ddf_status ddf_get_tile(ddf_handle h, int32_t which, ddf_tile* tile) {
+  if (h == nullptr || tile == nullptr) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+  if (which != 0 && which != 1) return fail(DDF_ERR_INVALID_ARG, "which must be 0 or 1");
+  const ddf::TcTile& t = which == 1 ? h->tile_first : h->tile;
+  tile->bn = t.bn;
+  tile->epi_warps = t.epi_warps;
+  tile->cta_pair = t.pair ? 1 : 0;
+  tile->staged = t.staged ? 1 : 0;
   return DDF_OK;
 }
+
+namespace {
+
+constexpr int kTileCands = 6;
+const ddf_tile kCands[kTileCands] = {{256, 4, 0, 0}, {256, 8, 0, 0}, {128, 4, 0, 0},
+                                     {128, 8, 0, 0}, {256, 4, 1, 0}, {256, 4, 1, 1}};
+
+bool cand_ok(ddf_s* h, const ddf_tile& c) {
+  return h->cfg.width % c.bn == 0 && (c.cta_pair == 0 || h->pair_clusters > 0);
+}
+
+}  // namespace
 
 ddf_status ddf_autotune(ddf_handle h, const float* const rays[6], int64_t n, void* stream,
                         double* ms_out, int32_t n_out) {
@@ -802,73 +827,93 @@ ddf_status ddf_autotune(ddf_handle h, const float* const rays[6], int64_t n, voi
   if (s != DDF_OK) return s;
   if ((s = check_rays(rays, n)) != DDF_OK) return s;
   if (n <= 0 || n > (int64_t{1} << 24)) return fail(DDF_ERR_INVALID_ARG, "tune on 1 .. 2^24 rays");
-  if (ms_out != nullptr && n_out < 5) return fail(DDF_ERR_INVALID_ARG, "ms_out needs 5 entries");
+  if (ms_out != nullptr && n_out < 2 * kTileCands)
+    return fail(DDF_ERR_INVALID_ARG, "ms_out needs 12 entries");
   if (ms_out != nullptr)
-    for (int i = 0; i < 5; ++i) ms_out[i] = -1.0;
+    for (int i = 0; i < 2 * kTileCands; ++i) ms_out[i] = -1.0;
   if (h->cfg.precision == DDF_FP32) return DDF_OK;  // one FP32 kernel shape, nothing to choose
   DeviceGuard g(h->cfg.device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const ddf::TcTile cands[5] = {{256, 4}, {256, 8}, {128, 4}, {128, 8}, {256, 4, true}};
   float* buf = nullptr;
   DDF_CK(cudaMalloc(&buf, 4 * n * sizeof(float)));
   std::vector<float> ref_t(n), ref_v(n), got_t(n), got_v(n);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const ddf::TcTile keep = h->tile;
+  ddf_tile keep_h, keep_f;
+  ddf_get_tile(h, 0, &keep_h);
+  ddf_get_tile(h, 1, &keep_f);
   const bool keep_prof = h->prof;
   h->prof = false;
-  double best = 1e30;
-  ddf::TcTile best_tile = keep;
   bool have_ref = false;
   ddf_status result = DDF_OK;
-  for (int c = 0; c < 5 && result == DDF_OK; ++c) {
-    if (h->cfg.width % cands[c].bn != 0) continue;
-    if (cands[c].pair && h->pair_clusters <= 0) continue;
-    if ((result = ddf_set_tile(h, cands[c].bn, cands[c].epi_warps, cands[c].pair)) != DDF_OK) break;
+  // Runs the query with the current tiles; checks it against the reference
+  // (the first configuration run) and returns its time, or -1 if rejected.
+  auto trial = [&](double* ms) -> ddf_status {
+    *ms = -1.0;
     ddf::HeadOut o{};
     o.t = buf + (have_ref ? 2 * n : 0);
     o.vis = o.t + n;
-    if ((result = run_query(h, rays, n, o, st)) != DDF_OK) break;
-    if (cudaStreamSynchronize(st) != cudaSuccess) {
-      result = fail(DDF_ERR_CUDA, "autotune: candidate launch failed");
-      break;
-    }
+    ddf_status r = run_query(h, rays, n, o, st);
+    if (r != DDF_OK) return r;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return fail(DDF_ERR_CUDA, "autotune: launch failed");
     std::vector<float>& tt = have_ref ? got_t : ref_t;
     std::vector<float>& vv = have_ref ? got_v : ref_v;
     cudaMemcpy(tt.data(), o.t, n * sizeof(float), cudaMemcpyDeviceToHost);
     cudaMemcpy(vv.data(), o.vis, n * sizeof(float), cudaMemcpyDeviceToHost);
-    if (have_ref) {  // every candidate must agree with the first before it may be timed
+    if (have_ref) {
       double worst = 0.0;
       for (int64_t i = 0; i < n; ++i) {
         worst = std::max(worst, std::fabs(double(got_t[i]) - ref_t[i]) / std::max(1.0, std::fabs(double(ref_t[i]))));
         worst = std::max(worst, std::fabs(double(got_v[i]) - ref_v[i]) / std::max(1.0, std::fabs(double(ref_v[i]))));
       }
-      if (!(worst <= 1e-3)) continue;
+      if (!(worst <= 1e-3)) return DDF_OK;  // rejected
     }
     have_ref = true;
     cudaEventRecord(e0, st);
-    for (int r = 0; r < 3; ++r) run_query(h, rays, n, o, st);
+    for (int k = 0; k < 3; ++k) run_query(h, rays, n, o, st);
     cudaEventRecord(e1, st);
     cudaEventSynchronize(e1);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    const double per = ms / 3.0;
-    if (ms_out != nullptr) ms_out[c] = per;
-    if (per < best) {
-      best = per;
-      best_tile = cands[c];
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    *ms = t / 3.0;
+    return DDF_OK;
+  };
+  // phase 1: one tile for every layer; phase 2: the first layer's own tile
+  int best_h = -1, best_f = -1;
+  double tbest = 1e30;
+  for (int c = 0; c < kTileCands && result == DDF_OK; ++c) {
+    if (!cand_ok(h, kCands[c])) continue;
+    if ((result = ddf_set_tile(h, 0, &kCands[c])) != DDF_OK) break;
+    if ((result = ddf_set_tile(h, 1, &kCands[c])) != DDF_OK) break;
+    double ms;
+    if ((result = trial(&ms)) != DDF_OK) break;
+    if (ms_out != nullptr) ms_out[c] = ms;
+    if (ms > 0 && ms < tbest) tbest = ms, best_h = c;
+  }
+  if (result == DDF_OK && best_h >= 0) {
+    result = ddf_set_tile(h, 0, &kCands[best_h]);
+    tbest = 1e30;
+    for (int c = 0; c < kTileCands && result == DDF_OK; ++c) {
+      if (!cand_ok(h, kCands[c])) continue;
+      if ((result = ddf_set_tile(h, 1, &kCands[c])) != DDF_OK) break;
+      double ms;
+      if ((result = trial(&ms)) != DDF_OK) break;
+      if (ms_out != nullptr) ms_out[kTileCands + c] = ms;
+      if (ms > 0 && ms < tbest) tbest = ms, best_f = c;
     }
   }
   h->prof = keep_prof;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(buf);
-  if (result != DDF_OK) {
-    ddf_set_tile(h, keep.bn, keep.epi_warps, keep.pair);
-    return result;
+  if (result != DDF_OK || best_h < 0 || best_f < 0) {
+    ddf_set_tile(h, 0, &keep_h);
+    ddf_set_tile(h, 1, &keep_f);
+    return result != DDF_OK ? result : fail(DDF_ERR_CUDA, "autotune: no candidate passed");
   }
-  return ddf_set_tile(h, best_tile.bn, best_tile.epi_warps, best_tile.pair);
+  ddf_status r = ddf_set_tile(h, 0, &kCands[best_h]);
+  return r != DDF_OK ? r : ddf_set_tile(h, 1, &kCands[best_f]);
 }
 
 }  // extern "C"

@@ -150,4 +150,107 @@ __device__ __forceinline__ void epi_row(const TcGemmParams& p, const EpiVectors&
   }
 }
 
+// ---------------------------------------------------------------------------
+// Staged stores (mode 0): instead of every thread storing 16-byte pieces of
+// its own row (32 rows per warp instruction, half-filled sectors), a warp
+// packs 128 bytes of each of its 32 rows into a 4 KB shared buffer and then
+// writes whole 128-byte lines, 4 rows per instruction. Pieces are placed at
+// 16-byte slot (piece ^ (row & 7)) of their row so both the row-wise packing
+// and the line-wise copy-out touch all eight bank groups.
+
+constexpr int kStageBytesPerWarp = 32 * 128;
+
+// Packs chunk c (32 columns) into the staging row of this lane.
+template <bool OUT_FP8>
+__device__ __forceinline__ void epi_chunk_stage(const TcGemmParams& p, const EpiVectors& ev,
+                                                const uint32_t (&v)[32], int nc, int c,
+                                                uint8_t* stage, int lane) {
+  float x[32];
+  const float4* b4 = reinterpret_cast<const float4*>(ev.bias + nc);
+#pragma unroll
+  for (int j4 = 0; j4 < 8; ++j4) {
+    const float4 bb = b4[j4];
+    float4 cs = make_float4(1.f, 1.f, 1.f, 1.f);
+    if (ev.scale != nullptr) cs = reinterpret_cast<const float4*>(ev.scale + nc)[j4];
+    x[4 * j4 + 0] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 0]), cs.x, bb.x), 0.f);
+    x[4 * j4 + 1] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 1]), cs.y, bb.y), 0.f);
+    x[4 * j4 + 2] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 2]), cs.z, bb.z), 0.f);
+    x[4 * j4 + 3] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 3]), cs.w, bb.w), 0.f);
+  }
+  uint8_t* row = stage + lane * 128;
+  const int sw = lane & 7;
+  if constexpr (OUT_FP8) {
+    const float os = p.out_scale;
+    const int piece0 = 2 * (c & 3);  // 4 chunks of 32 bytes per 128-byte row
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      uint4 w;
+      w.x = epi_pack_e4m3x4(x[16 * k + 0] * os, x[16 * k + 1] * os, x[16 * k + 2] * os, x[16 * k + 3] * os);
+      w.y = epi_pack_e4m3x4(x[16 * k + 4] * os, x[16 * k + 5] * os, x[16 * k + 6] * os, x[16 * k + 7] * os);
+      w.z = epi_pack_e4m3x4(x[16 * k + 8] * os, x[16 * k + 9] * os, x[16 * k + 10] * os, x[16 * k + 11] * os);
+      w.w = epi_pack_e4m3x4(x[16 * k + 12] * os, x[16 * k + 13] * os, x[16 * k + 14] * os, x[16 * k + 15] * os);
+      *reinterpret_cast<uint4*>(row + (((piece0 + k) ^ sw) << 4)) = w;
+    }
+  } else {
+    const int piece0 = 4 * (c & 1);  // 2 chunks of 64 bytes per 128-byte row
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      uint4 w;
+      w.x = epi_pack_bf16x2(x[8 * k + 0], x[8 * k + 1]);
+      w.y = epi_pack_bf16x2(x[8 * k + 2], x[8 * k + 3]);
+      w.z = epi_pack_bf16x2(x[8 * k + 4], x[8 * k + 5]);
+      w.w = epi_pack_bf16x2(x[8 * k + 6], x[8 * k + 7]);
+      *reinterpret_cast<uint4*>(row + (((piece0 + k) ^ sw) << 4)) = w;
+    }
+  }
+}
+
+// Writes the warp's 32 staged rows (128 bytes each) to out rows
+// warp_row0 .. warp_row0 + 31 (those < M) at byte column col_bytes.
+__device__ __forceinline__ void epi_flush_stage(const TcGemmParams& p, const uint8_t* stage,
+                                                int warp_row0, size_t row_bytes, size_t col_bytes,
+                                                int lane) {
+  __syncwarp();
+  const int k = lane & 7;
+  uint8_t* out = static_cast<uint8_t*>(p.out) + col_bytes + (k << 4);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = 4 * i + (lane >> 3);
+    const uint4 w = *reinterpret_cast<const uint4*>(stage + r * 128 + ((k ^ (r & 7)) << 4));
+    const int row = warp_row0 + r;
+    if (row < p.M) *reinterpret_cast<uint4*>(out + static_cast<size_t>(row) * row_bytes) = w;
+  }
+  __syncwarp();
+}
+
+// Mode-0 drain of chunks [c_begin, c_end) through the warp's staging buffer
+// (c_begin and c_end multiples of the chunks per 128-byte row).
+template <bool OUT_FP8>
+__device__ __forceinline__ void epi_row_staged(const TcGemmParams& p, const EpiVectors& ev,
+                                               uint32_t tbase, int warp_row0, int n0, int c_begin,
+                                               int c_end, uint8_t* stage, int lane) {
+  constexpr int kGroup = OUT_FP8 ? 4 : 2;  // chunks per 128 bytes of a row
+  constexpr int kElem = OUT_FP8 ? 1 : 2;
+  const size_t row_bytes = static_cast<size_t>(p.ldo) * kElem;
+  uint32_t va[32], vb[32];
+  tmem_ld32(tbase + 32u * c_begin, va);
+  tmem_wait_ld_regs(va);
+#pragma unroll 1
+  for (int c = c_begin; c < c_end; c += 2) {
+    // chunks c (in va) and c + 1 (loaded into vb meanwhile); c_end - c_begin is even
+    tmem_ld32(tbase + 32u * (c + 1), vb);
+    epi_chunk_stage<OUT_FP8>(p, ev, va, n0 + 32 * c, c, stage, lane);
+    tmem_wait_ld_regs(vb);
+    const bool next2 = c + 2 < c_end;
+    if (next2) tmem_ld32(tbase + 32u * (c + 2), va);
+    epi_chunk_stage<OUT_FP8>(p, ev, vb, n0 + 32 * (c + 1), c + 1, stage, lane);
+    if (((c + 2 - c_begin) % kGroup) == 0) {
+      const int g0 = c + 2 - kGroup;  // first chunk of the staged group
+      epi_flush_stage(p, stage, warp_row0, row_bytes,
+                      static_cast<size_t>(n0 + 32 * g0) * kElem, lane);
+    }
+    if (next2) tmem_wait_ld_regs(va);
+  }
+}
+
 }  // namespace ddf

@@ -39,7 +39,8 @@ struct TcGemmParams {
 struct TcTile {
   int bn;
   int epi_warps;
-  bool pair = false;  // 256 x 256 tile on a 2-CTA cluster (tc_gemm_pair.cu; bn 256, 4 warps)
+  bool pair = false;    // 256 x 256 tile on a 2-CTA cluster (tc_gemm_pair.cu; bn 256, 4 warps)
+  bool staged = false;  // pair tile only: outputs staged through shared memory
 };
 
 // in_fp8: operands are e4m3 codes (kind::f8f6f4) instead of bf16 (kind::f16).
@@ -51,7 +52,7 @@ int tc_gemm_smem_bytes(int bn, bool in_fp8);
 
 // CTA-pair variant: clusters of 2 CTAs, 256 x 256 output tiles, persistent
 // over `clusters` clusters. Mode 1 writes N/256 partials per row.
-cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, const CUtensorMap& tmA,
+cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, bool staged, const CUtensorMap& tmA,
                                 const CUtensorMap& tmB, const TcGemmParams& p, int clusters,
                                 cudaStream_t s);
 // Clusters of the pair kernel that fit on the current device at once.

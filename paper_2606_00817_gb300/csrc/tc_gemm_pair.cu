@@ -35,7 +35,9 @@ namespace {
 
 constexpr uint64_t kPairDrainNs = 1000000000ull;
 
-template <bool IN_FP8>
+// STAGED: mode-0 outputs go through per-warp shared staging buffers
+// (epi_row_staged); one pipeline stage fewer leaves room for them.
+template <bool IN_FP8, bool STAGED>
 struct PairShape {
   static constexpr int BM = 256;                 // output rows per pair tile
   static constexpr int BN = 256;                 // output columns per pair tile
@@ -45,7 +47,8 @@ struct PairShape {
   static constexpr int A_BYTES = HALF * ROW_BYTES;
   static constexpr int B_BYTES = HALF * ROW_BYTES;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;  // per CTA
-  static constexpr int STAGES = 6;
+  static constexpr int STAGES = STAGED ? 5 : 6;
+  static constexpr int OUT_STAGE_BYTES = STAGED ? 4 * kStageBytesPerWarp : 0;
   static constexpr int TMEM_COLS = 512;
   static constexpr int NUM_BARS = 2 * STAGES + 5;
   static constexpr int CTRL_BYTES = 256;  // barriers, TMEM slot, abort flag, issue counts
@@ -55,11 +58,11 @@ struct PairShape {
   static_assert(NUM_BARS * 8 + 16 <= CTRL_BYTES, "control block overflow");
 };
 
-template <bool IN_FP8, bool OUT_FP8>
+template <bool IN_FP8, bool OUT_FP8, bool STAGED>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                         const __grid_constant__ CUtensorMap tmB, const TcGemmParams p) {
-  using S = PairShape<IN_FP8>;
+  using S = PairShape<IN_FP8, STAGED>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -211,7 +214,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
       const uint32_t tbase = tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
                              static_cast<uint32_t>(b * S::BN);
       float h0 = 0.f, h1 = 0.f;
-      epi_row<OUT_FP8>(p, ev, tbase, row, row_ok, n0, 0, S::BN / 32, h0, h1);
+      if (STAGED && p.mode == 0) {
+        uint8_t* stage = smem + S::VEC_OFFSET + epi_vector_bytes(p.N) + q * kStageBytesPerWarp;
+        epi_row_staged<OUT_FP8>(p, ev, tbase, row - lane, n0, 0, S::BN / 32, stage, lane);
+      } else {
+        epi_row<OUT_FP8>(p, ev, tbase, row, row_ok, n0, 0, S::BN / 32, h0, h1);
+      }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(tempty_leader0 + 8u * b);
@@ -249,23 +257,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
   }
 }
 
-template <bool IN_FP8, bool OUT_FP8>
+template <bool IN_FP8, bool OUT_FP8, bool STAGED>
 cudaError_t launch_pair_one(const CUtensorMap& tmA, const CUtensorMap& tmB,
                             const TcGemmParams& p, int grid, cudaStream_t s) {
-  using S = PairShape<IN_FP8>;
-  auto kern = tc_gemm_pair_kernel<IN_FP8, OUT_FP8>;
-  const int smem = S::SMEM_BYTES + epi_vector_bytes(p.N);
+  using S = PairShape<IN_FP8, STAGED>;
+  auto kern = tc_gemm_pair_kernel<IN_FP8, OUT_FP8, STAGED>;
+  const int smem = S::SMEM_BYTES + epi_vector_bytes(p.N) + S::OUT_STAGE_BYTES;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, 192, smem, s>>>(tmA, tmB, p);
   return cudaGetLastError();
 }
 
-template <bool IN_FP8, bool OUT_FP8>
+template <bool IN_FP8, bool STAGED>
 int max_pairs_for() {
-  using S = PairShape<IN_FP8>;
-  auto kern = tc_gemm_pair_kernel<IN_FP8, OUT_FP8>;
-  const int smem = S::SMEM_BYTES + epi_vector_bytes(kMaxStagedColumns);
+  using S = PairShape<IN_FP8, STAGED>;
+  auto kern = tc_gemm_pair_kernel<IN_FP8, false, STAGED>;
+  const int smem = S::SMEM_BYTES + epi_vector_bytes(kMaxStagedColumns) + S::OUT_STAGE_BYTES;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
     return 0;
   cudaLaunchConfig_t cfg = {};
@@ -280,20 +288,29 @@ int max_pairs_for() {
   return n;
 }
 
+template <bool IN_FP8, bool STAGED>
+cudaError_t launch_pair_io(bool out_fp8, const CUtensorMap& tmA, const CUtensorMap& tmB,
+                           const TcGemmParams& p, int grid, cudaStream_t s) {
+  return out_fp8 ? launch_pair_one<IN_FP8, true, STAGED>(tmA, tmB, p, grid, s)
+                 : launch_pair_one<IN_FP8, false, STAGED>(tmA, tmB, p, grid, s);
+}
+
 }  // namespace
 
 int tc_gemm_pair_max_clusters(bool in_fp8) {
-  return in_fp8 ? max_pairs_for<true, false>() : max_pairs_for<false, false>();
+  const int a = in_fp8 ? max_pairs_for<true, false>() : max_pairs_for<false, false>();
+  const int b = in_fp8 ? max_pairs_for<true, true>() : max_pairs_for<false, true>();
+  return a < b ? a : b;
 }
 
-cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, const CUtensorMap& tmA,
+cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, bool staged, const CUtensorMap& tmA,
                                 const CUtensorMap& tmB, const TcGemmParams& p, int clusters,
                                 cudaStream_t s) {
   const int grid = 2 * clusters;
-  if (in_fp8) return out_fp8 ? launch_pair_one<true, true>(tmA, tmB, p, grid, s)
-                             : launch_pair_one<true, false>(tmA, tmB, p, grid, s);
-  return out_fp8 ? launch_pair_one<false, true>(tmA, tmB, p, grid, s)
-                 : launch_pair_one<false, false>(tmA, tmB, p, grid, s);
+  if (in_fp8) return staged ? launch_pair_io<true, true>(out_fp8, tmA, tmB, p, grid, s)
+                            : launch_pair_io<true, false>(out_fp8, tmA, tmB, p, grid, s);
+  return staged ? launch_pair_io<false, true>(out_fp8, tmA, tmB, p, grid, s)
+                : launch_pair_io<false, false>(out_fp8, tmA, tmB, p, grid, s);
 }
 
 }  // namespace ddf

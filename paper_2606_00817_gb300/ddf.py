@@ -28,6 +28,11 @@ _vp, _i32, _i64, _u64, _sz = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_s
 _RAYS = C.POINTER(C.c_void_p)
 
 
+class Tile(C.Structure):
+    _fields_ = [("bn", C.c_int32), ("epi_warps", C.c_int32), ("cta_pair", C.c_int32),
+                ("staged", C.c_int32)]
+
+
 class Config(C.Structure):
     _fields_ = [("octaves", C.c_int32), ("width", C.c_int32), ("hidden_layers", C.c_int32),
                 ("precision", C.c_int32), ("device", C.c_int32)]
@@ -49,9 +54,8 @@ SIGNATURES = {
     "ddf_check_status": (C.c_int, [_vp, C.POINTER(C.c_uint32)]),
     "ddf_set_timeout_ns": (C.c_int, [_vp, _u64]),
     "ddf_set_chunk_rays": (C.c_int, [_vp, _i64]),
-    "ddf_set_tile": (C.c_int, [_vp, _i32, _i32, _i32]),
-    "ddf_get_tile": (C.c_int, [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
-                               C.POINTER(C.c_int32)]),
+    "ddf_set_tile": (C.c_int, [_vp, _i32, C.POINTER(Tile)]),
+    "ddf_get_tile": (C.c_int, [_vp, _i32, C.POINTER(Tile)]),
     "ddf_autotune": (C.c_int, [_vp, _RAYS, _i64, _vp, C.POINTER(C.c_double), _i32]),
     "ddf_profile_enable": (C.c_int, [_vp, _i32]),
     "ddf_profile_read": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
@@ -204,26 +208,31 @@ def ddf_set_chunk_rays(h, chunk: int) -> None:
     _call("ddf_set_chunk_rays", h, int(chunk))
 
 
-def ddf_set_tile(h, bn: int, epi_warps: int, cta_pair: int = 0) -> None:
-    _call("ddf_set_tile", h, int(bn), int(epi_warps), int(cta_pair))
+def ddf_set_tile(h, tile, which: int = 0) -> None:
+    """tile = (bn, epi_warps, cta_pair, staged); which 0 = layers 2..H, 1 = layer 1."""
+    _call("ddf_set_tile", h, int(which), C.byref(Tile(*[int(x) for x in tile])))
 
 
-def ddf_get_tile(h):
-    """(bn, epi_warps, cta_pair)"""
-    bn, ew, pr = C.c_int32(), C.c_int32(), C.c_int32()
-    _call("ddf_get_tile", h, C.byref(bn), C.byref(ew), C.byref(pr))
-    return bn.value, ew.value, pr.value
+def ddf_get_tile(h, which: int = 0):
+    t = Tile()
+    _call("ddf_get_tile", h, int(which), C.byref(t))
+    return (t.bn, t.epi_warps, t.cta_pair, t.staged)
 
 
-TILE_CANDIDATES = ((256, 4, 0), (256, 8, 0), (128, 4, 0), (128, 8, 0), (256, 4, 1))
+TILE_CANDIDATES = ((256, 4, 0, 0), (256, 8, 0, 0), (128, 4, 0, 0), (128, 8, 0, 0),
+                   (256, 4, 1, 0), (256, 4, 1, 1))
 
 
 def ddf_autotune(h, rays, n, stream=None):
-    """Returns {(bn, epi_warps, cta_pair): ms or None}; leaves the fastest tile set."""
+    """Returns ({tile: ms or None} for phase 1 (all layers), the same for
+    phase 2 (layer 1 only)); leaves the fastest tiles set."""
     rp, keep = _rays(rays)
-    ms = (C.c_double * 5)()
-    _call("ddf_autotune", h, rp, int(n), _stream(stream), ms, 5)
-    return {c: (ms[i] if ms[i] >= 0 else None) for i, c in enumerate(TILE_CANDIDATES)}
+    ms = (C.c_double * 12)()
+    _call("ddf_autotune", h, rp, int(n), _stream(stream), ms, 12)
+    k = len(TILE_CANDIDATES)
+    p1 = {c: (ms[i] if ms[i] >= 0 else None) for i, c in enumerate(TILE_CANDIDATES)}
+    p2 = {c: (ms[k + i] if ms[k + i] >= 0 else None) for i, c in enumerate(TILE_CANDIDATES)}
+    return p1, p2
 
 
 def ddf_profile_enable(h, on: bool) -> None:

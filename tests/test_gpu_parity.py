@@ -211,7 +211,8 @@ def test_full_size_shadow_workload_sampled(torch_cuda):
     _check_reduced(t[idx], v[idx], sub, blob, PAPER, "bf16", None)
 
 
-@pytest.mark.parametrize("tile", [(256, 4, 0), (256, 8, 0), (128, 4, 0), (128, 8, 0), (256, 4, 1)])
+@pytest.mark.parametrize("tile", [(256, 4, 0, 0), (256, 8, 0, 0), (128, 4, 0, 0), (128, 8, 0, 0),
+                                  (256, 4, 1, 0), (256, 4, 1, 1)])
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
 def test_every_tile_matches_oracle(torch_cuda, tile, prec):
     from paper_2606_00817_gb300 import ddf
@@ -219,24 +220,28 @@ def test_every_tile_matches_oracle(torch_cuda, tile, prec):
     sc = _scales(blob, PAPER)
     rays = I.uniform_rays(777, seed=8)          # 3 pair row-tiles + a ragged one
     m = _make(PAPER, prec, blob, sc)
-    ddf.ddf_set_tile(m.h, *tile)
-    assert ddf.ddf_get_tile(m.h) == tile
+    ddf.ddf_set_tile(m.h, tile, which=0)
+    ddf.ddf_set_tile(m.h, tile, which=1)
+    assert ddf.ddf_get_tile(m.h, 0) == tile and ddf.ddf_get_tile(m.h, 1) == tile
     t, v = _query(torch_cuda, m, rays)
     _check_reduced(t, v, rays, blob, PAPER, prec, sc)
     assert ddf.ddf_check_status(m.h) == 0
 
 
 def test_pair_tile_on_a_full_chunk(torch_cuda):
-    """The CTA-pair tile over 300,001 rays (1172 pair row-tiles, more than one
-    per cluster, and a ragged last tile), sampled against the oracle."""
+    """The staged CTA-pair tile over 300,001 rays (1172 pair row-tiles, more
+    than one per cluster, and a ragged last tile), sampled against the oracle
+    and against the default tile."""
     from paper_2606_00817_gb300 import ddf
     blob = I.xavier_blob(I.NetShape(*PAPER))
     rays = I.uniform_rays(300_001, seed=10)
     m = _make(PAPER, "bf16", blob)
-    ddf.ddf_set_tile(m.h, 256, 4, 1)
+    for which in (0, 1):
+        ddf.ddf_set_tile(m.h, (256, 4, 1, 1), which)
     t, v = _query(torch_cuda, m, rays)
     assert ddf.ddf_check_status(m.h) == 0
-    ddf.ddf_set_tile(m.h, 256, 4, 0)
+    for which in (0, 1):
+        ddf.ddf_set_tile(m.h, (256, 4, 0, 0), which)
     t1, v1 = _query(torch_cuda, m, rays)
     assert np.max(np.abs(t - t1)) <= 1e-5 and np.max(np.abs(v - v1)) <= 1e-5
     idx = np.concatenate([np.arange(0, 100), np.arange(rays.n - 100, rays.n)])
@@ -250,10 +255,12 @@ def test_small_width_tiles_and_autotune(torch_cuda):
     rays = I.uniform_rays(4099, seed=9)
     m = _make(SMALL, "bf16", blob)
     with pytest.raises(ddf.DDFError):
-        ddf.ddf_set_tile(m.h, 256, 4)          # width 128 has no 256-wide N tile
-    ms = ddf.ddf_autotune(m.h, _dev(torch_cuda, rays), rays.n)
-    assert ms[(256, 4, 0)] is None and ms[(256, 8, 0)] is None and ms[(256, 4, 1)] is None
-    assert ms[(128, 4, 0)] > 0 and ms[(128, 8, 0)] > 0
-    assert ddf.ddf_get_tile(m.h) in ((128, 4, 0), (128, 8, 0))
+        ddf.ddf_set_tile(m.h, (256, 4, 0, 0))  # width 128 has no 256-wide N tile
+    p1, p2 = ddf.ddf_autotune(m.h, _dev(torch_cuda, rays), rays.n)
+    for ms in (p1, p2):
+        assert all(ms[c] is None for c in ms if c[0] == 256)
+        assert ms[(128, 4, 0, 0)] > 0 and ms[(128, 8, 0, 0)] > 0
+    assert ddf.ddf_get_tile(m.h, 0) in ((128, 4, 0, 0), (128, 8, 0, 0))
+    assert ddf.ddf_get_tile(m.h, 1) in ((128, 4, 0, 0), (128, 8, 0, 0))
     t, v = _query(torch_cuda, m, rays)
     _check_reduced(t, v, rays, blob, SMALL, "bf16", None)
