@@ -155,6 +155,38 @@ ddf_status ddf_query_shadow_host(ddf_handle h, const float* const rays[6], int64
 ddf_status ddf_query_rays_noalloc(ddf_handle h, const float* const rays[6], int64_t n,
                                   float* out_t, float* out_vis, void* stream);
 
+/* Ragged ambient occlusion (Sec. 3.3: evaluate the field along a set of
+ * hemisphere directions and average the hit flag). Point p owns the rays
+ * offsets[p] .. offsets[p+1]-1 of the n_rays-ray batch (SoA as above);
+ * offsets: n_points + 1 device int32, non-decreasing, offsets[0] = 0,
+ * offsets[n_points] = n_rays (n_rays < 2^31). Writes
+ *   out_hard[p] = 1 - (number of rays with z1 > 0) / count
+ *   out_soft[p] = 1 - (sum of vis) / count        (out_soft nullable)
+ * and 1 for points with no rays. Device pointers, asynchronous on stream.
+ * Keeps a per-ray scratch of 5 bytes x n_rays inside the handle. */
+ddf_status ddf_query_ao(ddf_handle h, const float* const rays[6], int64_t n_rays,
+                        const int32_t* offsets, int64_t n_points, float* out_hard,
+                        float* out_soft, void* stream);
+
+/* Graph mode. When on, ddf_query_rays, ddf_query_shadow and ddf_query_ao
+ * record their whole launch sequence (all chunks and layers) into a CUDA
+ * graph the first time they see a given set of pointers, sizes and light,
+ * and afterwards replay that graph with one cudaGraphLaunch on the caller's
+ * stream; the data behind the pointers may change between calls. Up to 8
+ * graphs are cached per handle; changing tiles, chunk size, timeout or
+ * activation scales, or growing a workspace, drops them. Turning the mode off
+ * drops them too. */
+ddf_status ddf_set_graph_mode(ddf_handle h, int32_t on);
+
+/* FP8 handles: calibrates the per-tensor activation scales on n rays (device
+ * SoA; a representative batch). Runs layers 1..H-1 in bf16 on the same weights,
+ * records amax_l = max over the batch of the layer-l output h_l (after ReLU),
+ * and sets s_l = the smallest power of two with amax_l / s_l <= 448, as
+ * ddf_set_act_scales would. amax_out and scales_out (nullable, H-1 host
+ * floats) receive both. Synchronous; allocates 4 (H-1) bytes while it runs. */
+ddf_status ddf_calibrate_fp8(ddf_handle h, const float* const rays[6], int64_t n, float* amax_out,
+                             float* scales_out, void* stream);
+
 /* Device status word of the handle: bit 0 = a pipeline wait timed out,
  * bit 1 = a scheduler wait timed out. Synchronises the device, stores the
  * word in *out and clears it. */

@@ -116,6 +116,20 @@ struct ddf_s {
   std::vector<float*> colscale;    // FP8: s_{l-1} * wscale_l
   std::vector<float> act_scales;
   std::vector<CUtensorMap> tmB;
+  std::vector<__nv_bfloat16*> wcal;  // FP8: bf16 copies of layers 2..H for calibration
+  std::vector<CUtensorMap> tmBcal;   // FP8: maps of the bf16 weights, calibration tile
+
+  // CUDA-graph replay of queries (ddf_set_graph_mode)
+  bool graph_mode = false;
+  cudaStream_t s_graph = nullptr;
+  struct GraphEntry {
+    std::vector<uint64_t> key;
+    cudaGraphExec_t exec;
+  };
+  std::vector<GraphEntry> graphs;
+  float* ao_vis = nullptr;    // AO: per-ray visibility and hit flags
+  uint8_t* ao_hit = nullptr;
+  int64_t ao_rows = 0;
   float* head_w = nullptr;  // [2 x W]
   float* head_b = nullptr;  // [2]
 
@@ -215,8 +229,11 @@ struct ProfScope {
 // Most head partials any tile writes per row: N/128 blocks x 2 epilogue halves.
 int max_partials(int W) { return (W / 128) * 2; }
 
+void clear_graphs(ddf_s* h);
+
 ddf_status ensure_workspace(ddf_s* h, int64_t rows) {
   if (rows <= h->ws_rows) return DDF_OK;
+  clear_graphs(h);  // cached graphs point at the old buffers
   dev_free(h, h->ws_enc);
   dev_free(h, h->ws_act[0]);
   dev_free(h, h->ws_act[1]);
@@ -226,7 +243,9 @@ ddf_status ensure_workspace(ddf_s* h, int64_t rows) {
   h->ws_rows = 0;
   const int W = h->cfg.width;
   const bool f32 = h->cfg.precision == DDF_FP32;
-  const size_t act_elem = f32 ? 4 : (h->cfg.precision == DDF_BF16 ? 2 : 1);
+  // e4m3 activations need 1 byte, but the calibration pass of an FP8 handle
+  // runs the layers in bf16 through the same buffers
+  const size_t act_elem = f32 ? 4 : 2;
   const size_t enc_bytes = static_cast<size_t>(rows) * (f32 ? h->kp32 * 4 : h->kp16 * 2);
   ddf_status st;
   if ((st = dev_alloc(h, &h->ws_enc, enc_bytes)) != DDF_OK) return st;
@@ -248,10 +267,12 @@ ddf::RaySoA shift_rays(ddf::RaySoA r, int64_t off) {
   return r;
 }
 
+// Advances every output that is present (null outputs stay null).
 ddf::HeadOut shift_out(ddf::HeadOut o, int64_t off) {
-  o.t += off;
-  o.vis += off;
-  if (o.occluded) o.occluded += off;
+  if (o.t != nullptr) o.t += off;
+  if (o.vis != nullptr) o.vis += off;
+  if (o.hit != nullptr) o.hit += off;
+  if (o.occluded != nullptr) o.occluded += off;
   o.rays = shift_rays(o.rays, off);
   return o;
 }
@@ -383,6 +404,115 @@ ddf_status run_query(ddf_s* h, const float* const rays[6], int64_t n, ddf::HeadO
   return DDF_OK;
 }
 
+void clear_graphs(ddf_s* h) {
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+}
+
+// Identity of a query for the graph cache: everything its launches bake in.
+std::vector<uint64_t> query_key(int kind, const float* const rays[6], int64_t n,
+                                std::initializer_list<const void*> ptrs, const float* light,
+                                int64_t extra) {
+  std::vector<uint64_t> k{static_cast<uint64_t>(kind), static_cast<uint64_t>(n),
+                          static_cast<uint64_t>(extra)};
+  for (int c = 0; c < 6; ++c) k.push_back(reinterpret_cast<uintptr_t>(rays[c]));
+  for (const void* p : ptrs) k.push_back(reinterpret_cast<uintptr_t>(p));
+  for (int c = 0; light != nullptr && c < 3; ++c) {
+    uint32_t bits;
+    std::memcpy(&bits, &light[c], 4);
+    k.push_back(bits);
+  }
+  return k;
+}
+
+// Enqueues a query on st: directly, or in graph mode by replaying the CUDA
+// graph captured (on a private stream) the first time this key was seen.
+// Workspaces must already be large enough: nothing is allocated while capturing.
+template <class F>
+ddf_status enqueue(ddf_s* h, const std::vector<uint64_t>& key, cudaStream_t st, F body) {
+  if (!h->graph_mode) return body(st);
+  for (auto& g : h->graphs) {
+    if (g.key == key) {
+      DDF_CK(cudaGraphLaunch(g.exec, st));
+      return DDF_OK;
+    }
+  }
+  if (h->s_graph == nullptr) DDF_CK(cudaStreamCreateWithFlags(&h->s_graph, cudaStreamNonBlocking));
+  const bool keep_prof = h->prof;
+  h->prof = false;
+  DDF_CK(cudaStreamBeginCapture(h->s_graph, cudaStreamCaptureModeRelaxed));
+  const ddf_status s = body(h->s_graph);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->s_graph, &graph);
+  h->prof = keep_prof;
+  if (s != DDF_OK) {
+    if (graph != nullptr) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  if (h->graphs.size() >= 8) {
+    cudaGraphExecDestroy(h->graphs.front().exec);
+    h->graphs.erase(h->graphs.begin());
+  }
+  h->graphs.push_back({key, exec});
+  DDF_CK(cudaGraphLaunch(exec, st));
+  return DDF_OK;
+}
+
+ddf_status ensure_ao_buffers(ddf_s* h, int64_t rows) {
+  if (rows <= h->ao_rows) return DDF_OK;
+  clear_graphs(h);  // cached graphs may point at the old buffers
+  dev_free(h, h->ao_vis);
+  dev_free(h, h->ao_hit);
+  h->ao_vis = nullptr;
+  h->ao_hit = nullptr;
+  h->ao_rows = 0;
+  void* p;
+  ddf_status s;
+  if ((s = dev_alloc(h, &p, rows * sizeof(float))) != DDF_OK) return s;
+  h->ao_vis = static_cast<float*>(p);
+  if ((s = dev_alloc(h, &p, rows)) != DDF_OK) return s;
+  h->ao_hit = static_cast<uint8_t*>(p);
+  h->ao_rows = rows;
+  return DDF_OK;
+}
+
+// Layers 1..H-1 in bf16 on the calibration weights, recording max |h_l| of
+// every hidden activation that feeds an e4m3 layer into amax[l].
+ddf_status calibrate_chunk(ddf_s* h, ddf::RaySoA rays, int m, float* amax, cudaStream_t st) {
+  const int W = h->cfg.width;
+  DDF_CK(ddf::launch_encode_bf16(rays, m, h->cfg.octaves, h->kp16,
+                                 static_cast<__nv_bfloat16*>(h->ws_enc), st));
+  const ddf::TcTile tile{h->bn, 4};
+  for (int l = 0; l + 1 < h->cfg.hidden_layers; ++l) {
+    const void* a_base = l == 0 ? h->ws_enc : h->ws_act[(l - 1) & 1];
+    const int K = l == 0 ? h->kp16 : W;
+    CUtensorMap tmA;
+    if (!make_tmap(&tmA, a_base, false, K, m, static_cast<uint64_t>(K) * 2, 128))
+      return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for an activation map");
+    ddf::TcGemmParams p{};
+    p.M = m;
+    p.N = W;
+    p.K = K;
+    p.bias = h->bias[l];
+    p.out_scale = 1.0f;
+    p.out = h->ws_act[l & 1];
+    p.ldo = W;
+    p.mode = 0;
+    p.status = h->status_dev;
+    p.timeout_ns = h->timeout_ns;
+    p.amax = amax + l;
+    const int64_t tiles = ((m + 127) / 128) * static_cast<int64_t>(W / tile.bn);
+    const int grid = static_cast<int>(std::min<int64_t>(tiles, h->num_sms));
+    DDF_CK(ddf::launch_tc_gemm(tile, false, false, tmA, h->tmBcal[l], p, grid, st));
+  }
+  return DDF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -460,6 +590,8 @@ ddf_status ddf_destroy(ddf_handle h) {
   }
   if (h->s_copy) cudaStreamDestroy(h->s_copy);
   if (h->s_comp) cudaStreamDestroy(h->s_comp);
+  clear_graphs(h);
+  if (h->s_graph) cudaStreamDestroy(h->s_graph);
   delete h;
   return DDF_OK;
 }
@@ -488,7 +620,9 @@ ddf_status ddf_load_weights(ddf_handle h, const float* host_blob, size_t n_float
     h->wq.assign(H, nullptr);
     h->wscale.assign(H, nullptr);
     h->colscale.assign(H, nullptr);
+    h->wcal.assign(H, nullptr);
     h->tmB.assign(H, CUtensorMap{});
+    h->tmBcal.assign(H, CUtensorMap{});
     for (int l = 0; l < H; ++l) {
       const int K = l == 0 ? h->d_in : W;
       if ((s = dev_alloc(h, &p, W * sizeof(float))) != DDF_OK) return s;
@@ -513,8 +647,19 @@ ddf_status ddf_load_weights(ddf_handle h, const float* host_blob, size_t n_float
         h->colscale[l] = static_cast<float*>(p);
         if (!make_tmap(&h->tmB[l], h->wq[l], true, W, W, W, h->tile.pair ? 128u : h->tile.bn))
           return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for a weight map");
+        // bf16 copy for the activation-scale calibration pass
+        if ((s = dev_alloc(h, &p, static_cast<size_t>(W) * W * 2)) != DDF_OK) return s;
+        h->wcal[l] = static_cast<__nv_bfloat16*>(p);
       }
       (void)K;
+    }
+    if (prec == DDF_FP8_E4M3) {
+      for (int l = 0; l < H; ++l) {
+        const int kp = l == 0 ? h->kp16 : W;
+        const __nv_bfloat16* w = l == 0 ? h->wb[0] : h->wcal[l];
+        if (!make_tmap(&h->tmBcal[l], w, false, kp, W, static_cast<uint64_t>(kp) * 2, h->bn))
+          return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for a weight map");
+      }
     }
     if ((s = dev_alloc(h, &p, 2 * W * sizeof(float))) != DDF_OK) return s;
     h->head_w = static_cast<float*>(p);
@@ -535,6 +680,7 @@ ddf_status ddf_load_weights(ddf_handle h, const float* host_blob, size_t n_float
       DDF_CK(ddf::launch_pack_bf16(w, W, K, l == 0 ? h->kp16 : W, h->wb[l], st));
     } else {
       DDF_CK(ddf::launch_quant_e4m3(w, W, K, W, h->wq[l], h->wscale[l], st));
+      DDF_CK(ddf::launch_pack_bf16(w, W, K, W, h->wcal[l], st));
     }
   }
   DDF_CK(cudaMemcpy(h->head_w, h->d_blob + off, 2 * W * sizeof(float), cudaMemcpyDeviceToDevice));
@@ -571,6 +717,7 @@ ddf_status ddf_set_act_scales(ddf_handle h, const float* host_scales, int32_t n)
     if (!(host_scales[i] > 0.f) || !std::isfinite(host_scales[i]) || m != 0.5f)
       return fail(DDF_ERR_INVALID_ARG, "activation scales must be positive powers of two");
   }
+  clear_graphs(h);  // the output scales are launch parameters
   h->act_scales.assign(host_scales, host_scales + n);
   h->scales_set = true;
   if (h->loaded) {
@@ -592,10 +739,13 @@ ddf_status ddf_query_rays(ddf_handle h, const float* const rays[6], int64_t n, f
     return fail(DDF_ERR_INVALID_ARG, "output pointer is NULL");
   if (n == 0) return DDF_OK;
   DeviceGuard g(h->cfg.device);
+  if ((s = ensure_workspace(h, std::min<int64_t>(n, h->chunk))) != DDF_OK) return s;
   ddf::HeadOut o{};
   o.t = out_t;
   o.vis = out_vis;
-  return run_query(h, rays, n, o, static_cast<cudaStream_t>(stream));
+  return enqueue(h, query_key(0, rays, n, {out_t, out_vis}, nullptr, 0),
+                 static_cast<cudaStream_t>(stream),
+                 [&](cudaStream_t st) { return run_query(h, rays, n, o, st); });
 }
 
 ddf_status ddf_query_shadow(ddf_handle h, const float* const rays[6], int64_t n,
@@ -609,12 +759,92 @@ ddf_status ddf_query_shadow(ddf_handle h, const float* const rays[6], int64_t n,
     return fail(DDF_ERR_INVALID_ARG, "output pointer is NULL");
   if (n == 0) return DDF_OK;
   DeviceGuard g(h->cfg.device);
+  if ((s = ensure_workspace(h, std::min<int64_t>(n, h->chunk))) != DDF_OK) return s;
   ddf::HeadOut o{};
   o.t = out_t;
   o.vis = out_vis;
   o.occluded = out_occluded;
   for (int i = 0; i < 3; ++i) o.light[i] = light[i];
-  return run_query(h, rays, n, o, static_cast<cudaStream_t>(stream));
+  return enqueue(h, query_key(1, rays, n, {out_t, out_vis, out_occluded}, light, 0),
+                 static_cast<cudaStream_t>(stream),
+                 [&](cudaStream_t st) { return run_query(h, rays, n, o, st); });
+}
+
+ddf_status ddf_query_ao(ddf_handle h, const float* const rays[6], int64_t n_rays,
+                        const int32_t* offsets, int64_t n_points, float* out_hard,
+                        float* out_soft, void* stream) {
+  ddf_status s = check_ready(h);
+  if (s != DDF_OK) return s;
+  if ((s = check_rays(rays, n_rays)) != DDF_OK) return s;
+  if (n_points < 0) return fail(DDF_ERR_INVALID_ARG, "n_points must be >= 0");
+  if (n_points > 0 && (offsets == nullptr || out_hard == nullptr))
+    return fail(DDF_ERR_INVALID_ARG, "offsets or out_hard is NULL");
+  if (n_rays >= (int64_t{1} << 31)) return fail(DDF_ERR_INVALID_ARG, "n_rays must fit int32 offsets");
+  if (n_points == 0) return DDF_OK;
+  DeviceGuard g(h->cfg.device);
+  if ((s = ensure_workspace(h, std::max<int64_t>(1, std::min<int64_t>(n_rays, h->chunk)))) != DDF_OK)
+    return s;
+  if ((s = ensure_ao_buffers(h, std::max<int64_t>(1, n_rays))) != DDF_OK) return s;
+  ddf::HeadOut o{};
+  o.vis = h->ao_vis;
+  o.hit = h->ao_hit;
+  return enqueue(h, query_key(2, rays, n_rays, {offsets, out_hard, out_soft}, nullptr, n_points),
+                 static_cast<cudaStream_t>(stream), [&](cudaStream_t st) {
+                   ddf_status r = n_rays > 0 ? run_query(h, rays, n_rays, o, st) : DDF_OK;
+                   if (r != DDF_OK) return r;
+                   DDF_CK(ddf::launch_ao_reduce(h->ao_hit, h->ao_vis, offsets, n_points, out_hard,
+                                                out_soft, st));
+                   return DDF_OK;
+                 });
+}
+
+ddf_status ddf_set_graph_mode(ddf_handle h, int32_t on) {
+  if (h == nullptr) return fail(DDF_ERR_INVALID_ARG, "handle is NULL");
+  DeviceGuard g(h->cfg.device);
+  if (!on) clear_graphs(h);
+  h->graph_mode = on != 0;
+  return DDF_OK;
+}
+
+ddf_status ddf_calibrate_fp8(ddf_handle h, const float* const rays[6], int64_t n, float* amax_out,
+                             float* scales_out, void* stream) {
+  if (h == nullptr) return fail(DDF_ERR_INVALID_ARG, "handle is NULL");
+  if (h->cfg.precision != DDF_FP8_E4M3) return fail(DDF_ERR_INVALID_ARG, "not an FP8 handle");
+  if (!h->loaded) return fail(DDF_ERR_BAD_WEIGHTS, "no weights loaded");
+  ddf_status s = check_rays(rays, n);
+  if (s != DDF_OK) return s;
+  if (n <= 0) return fail(DDF_ERR_INVALID_ARG, "calibration needs at least one ray");
+  const int nl = h->cfg.hidden_layers - 1;
+  if (nl == 0) return DDF_OK;
+  DeviceGuard g(h->cfg.device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((s = ensure_workspace(h, std::min<int64_t>(n, h->chunk))) != DDF_OK) return s;
+  float* amax = nullptr;
+  DDF_CK(cudaMalloc(&amax, nl * sizeof(float)));
+  cudaMemsetAsync(amax, 0, nl * sizeof(float), st);
+  ddf::RaySoA r;
+  for (int c = 0; c < 6; ++c) r.p[c] = rays[c];
+  for (int64_t off = 0; off < n && s == DDF_OK; off += h->chunk) {
+    const int m = static_cast<int>(std::min<int64_t>(h->chunk, n - off));
+    s = calibrate_chunk(h, shift_rays(r, off), m, amax, st);
+  }
+  std::vector<float> a(nl);
+  const cudaError_t e1 = cudaStreamSynchronize(st);
+  const cudaError_t e2 = cudaMemcpy(a.data(), amax, nl * sizeof(float), cudaMemcpyDeviceToHost);
+  cudaFree(amax);
+  if (s != DDF_OK) return s;
+  if (e1 != cudaSuccess || e2 != cudaSuccess) return cuda_fail(e1 != cudaSuccess ? e1 : e2, "calibration");
+  std::vector<float> sc(nl);
+  for (int l = 0; l < nl; ++l) {
+    // smallest power of two s with amax / s <= 448
+    double q = static_cast<double>(a[l]) / 448.0;
+    int ex = 0;
+    const double m = std::frexp(q, &ex);  // q = m 2^ex, m in [0.5, 1)
+    sc[l] = a[l] > 0.f ? static_cast<float>(std::ldexp(1.0, m == 0.5 ? ex - 1 : ex)) : 1.0f;
+    if (amax_out != nullptr) amax_out[l] = a[l];
+    if (scales_out != nullptr) scales_out[l] = sc[l];
+  }
+  return ddf_set_act_scales(h, sc.data(), nl);
 }
 
 namespace {
@@ -735,6 +965,7 @@ ddf_status ddf_check_status(ddf_handle h, uint32_t* out) {
 
 ddf_status ddf_set_timeout_ns(ddf_handle h, uint64_t ns) {
   if (h == nullptr) return fail(DDF_ERR_INVALID_ARG, "handle is NULL");
+  clear_graphs(h);
   h->timeout_ns = ns;
   return DDF_OK;
 }
@@ -743,6 +974,7 @@ ddf_status ddf_set_chunk_rays(ddf_handle h, int64_t chunk) {
   if (h == nullptr) return fail(DDF_ERR_INVALID_ARG, "handle is NULL");
   if (chunk < 128 || chunk > (int64_t{1} << 30))
     return fail(DDF_ERR_INVALID_ARG, "chunk must be in [128, 2^30]");
+  clear_graphs(h);
   h->chunk = chunk;
   return DDF_OK;
 }
@@ -787,6 +1019,7 @@ ddf_status ddf_set_tile(ddf_handle h, int32_t which, const ddf_tile* tile) {
     return fail(DDF_ERR_INVALID_ARG, "staged stores exist for the CTA-pair tile only");
   if (tile->cta_pair != 0 && h->pair_clusters <= 0)
     return fail(DDF_ERR_UNSUPPORTED, "CTA-pair clusters do not fit on this device");
+  clear_graphs(h);  // weight maps and launch shapes change
   (which == 1 ? h->tile_first : h->tile) =
       ddf::TcTile{bn, ew, tile->cta_pair != 0, tile->staged != 0};
   h->bn = h->tile.bn;

@@ -80,6 +80,17 @@ __device__ __forceinline__ void epi_chunk(const TcGemmParams& p, const EpiVector
     x[4 * j4 + 3] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 3]), cs.w, bb.w), 0.f);
   }
   if (p.mode == 0) {
+    if (p.amax != nullptr) {  // calibration: the warp's largest output of valid rows
+      float m = 0.f;
+      if (row_ok) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) m = fmaxf(m, x[j]);
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+      // x >= 0 after ReLU, so the float order equals the int order of its bits
+      if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(p.amax), __float_as_int(m));
+    }
     if (!row_ok) return;
     if constexpr (OUT_FP8) {
       uint8_t* dst = static_cast<uint8_t*>(p.out) + static_cast<size_t>(row) * p.ldo + nc;

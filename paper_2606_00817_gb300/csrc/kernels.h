@@ -30,6 +30,8 @@ struct TcGemmParams {
   int mode;
   uint32_t* status;        // device status word (timeouts)
   uint64_t timeout_ns;
+  float* amax;             // mode 0, nullable: running max of the layer's outputs
+                           // (rows < M), for activation-scale calibration
 };
 
 // Tile configuration of the tensor-core layer: N tile (128 or 256) and the
@@ -70,8 +72,9 @@ cudaError_t launch_sgemm_relu(const float* A, const float* W, const float* b, fl
 
 // Heads: z = Wo h + bo, t = softplus(z0), vis = sigmoid(z1), optional shadow.
 struct HeadOut {
-  float* t;
-  float* vis;
+  float* t;           // nullable
+  float* vis;         // nullable
+  uint8_t* hit;       // nullable: 1 where z1 > 0
   uint8_t* occluded;  // nullptr unless a shadow query
   float light[3];
   RaySoA rays;        // origins for the shadow distance
@@ -82,6 +85,11 @@ cudaError_t launch_head_f32(const float* H, int M, int W, const float* wo, const
 // From per-N-block partial dot products [nblk x M] (tensor-core path).
 cudaError_t launch_finish_heads(const float2* part, int nblk, int M, const float* bo, HeadOut o,
                                 cudaStream_t s);
+
+// Ambient occlusion (Sec. 3.3): for point p with rays [offsets[p], offsets[p+1])
+// hard[p] = 1 - mean(hit), soft[p] = 1 - mean(vis); empty sets give 1.
+cudaError_t launch_ao_reduce(const uint8_t* hit, const float* vis, const int32_t* offsets,
+                             int64_t n_points, float* hard, float* soft, cudaStream_t s);
 
 // Weight preparation (load time).
 // dst[N x ldd] = src[N x K] zero-padded to ldd columns.

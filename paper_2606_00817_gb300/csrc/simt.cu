@@ -201,8 +201,9 @@ __device__ __forceinline__ float sigmoid_f(float z) {
 
 __device__ __forceinline__ void write_heads(const HeadOut& o, int64_t i, float z0, float z1) {
   const float t = softplus_f(z0);
-  o.t[i] = t;
-  o.vis[i] = sigmoid_f(z1);
+  if (o.t != nullptr) o.t[i] = t;
+  if (o.vis != nullptr) o.vis[i] = sigmoid_f(z1);
+  if (o.hit != nullptr) o.hit[i] = z1 > 0.f ? 1 : 0;
   if (o.occluded != nullptr) {
     const float dx = o.light[0] - o.rays.p[0][i];
     const float dy = o.light[1] - o.rays.p[1][i];
@@ -288,6 +289,32 @@ __global__ void quant_e4m3_kernel(const float* __restrict__ src, int N, int K, i
   }
 }
 
+// One warp per shading point: sums its contiguous ray segment in a fixed order.
+__global__ void ao_reduce_kernel(const uint8_t* __restrict__ hit, const float* __restrict__ vis,
+                                 const int32_t* __restrict__ offsets, int64_t n_points,
+                                 float* __restrict__ hard, float* __restrict__ soft) {
+  const int64_t p = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (p >= n_points) return;
+  const int32_t a = offsets[p], b = offsets[p + 1];
+  int nh = 0;
+  float sv = 0.f;
+  for (int32_t i = a + lane; i < b; i += 32) {
+    nh += hit[i];
+    sv += vis[i];
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    nh += __shfl_xor_sync(0xffffffffu, nh, off);
+    sv += __shfl_xor_sync(0xffffffffu, sv, off);
+  }
+  if (lane == 0) {
+    const int n = b - a;
+    hard[p] = n > 0 ? 1.f - static_cast<float>(nh) / static_cast<float>(n) : 1.f;
+    if (soft != nullptr) soft[p] = n > 0 ? 1.f - sv / static_cast<float>(n) : 1.f;
+  }
+}
+
 __global__ void scale_vec_kernel(const float* __restrict__ v, float a, int n, float* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = a * v[i];
@@ -345,6 +372,16 @@ cudaError_t launch_pack_bf16(const float* src, int N, int K, int ldd, __nv_bfloa
 cudaError_t launch_quant_e4m3(const float* src, int N, int K, int ldd, uint8_t* dst, float* scale,
                               cudaStream_t s) {
   quant_e4m3_kernel<<<N, 256, 0, s>>>(src, N, K, ldd, dst, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ao_reduce(const uint8_t* hit, const float* vis, const int32_t* offsets,
+                             int64_t n_points, float* hard, float* soft, cudaStream_t s) {
+  if (n_points <= 0) return cudaSuccess;
+  const int warps = 8;
+  const int64_t blocks = (n_points + warps - 1) / warps;
+  ao_reduce_kernel<<<static_cast<unsigned>(blocks), 32 * warps, 0, s>>>(hit, vis, offsets,
+                                                                       n_points, hard, soft);
   return cudaGetLastError();
 }
 

@@ -51,6 +51,9 @@ SIGNATURES = {
     "ddf_query_rays_host": (C.c_int, [_vp, _RAYS, _i64, _vp, _vp]),
     "ddf_query_shadow_host": (C.c_int, [_vp, _RAYS, _i64, _vp, _vp, _vp, _vp]),
     "ddf_query_rays_noalloc": (C.c_int, [_vp, _RAYS, _i64, _vp, _vp, _vp]),
+    "ddf_query_ao": (C.c_int, [_vp, _RAYS, _i64, _vp, _i64, _vp, _vp, _vp]),
+    "ddf_set_graph_mode": (C.c_int, [_vp, _i32]),
+    "ddf_calibrate_fp8": (C.c_int, [_vp, _RAYS, _i64, _vp, _vp, _vp]),
     "ddf_check_status": (C.c_int, [_vp, C.POINTER(C.c_uint32)]),
     "ddf_set_timeout_ns": (C.c_int, [_vp, _u64]),
     "ddf_set_chunk_rays": (C.c_int, [_vp, _i64]),
@@ -138,6 +141,7 @@ def ddf_param_count(cfg: Config) -> int:
 def ddf_create(cfg: Config) -> int:
     h = C.c_void_p()
     _call("ddf_create", C.byref(cfg), C.byref(h))
+    _HIDDEN[h.value] = cfg.hidden_layers
     return h.value
 
 
@@ -192,6 +196,33 @@ def ddf_query_shadow_host(h, rays, n, light, out_t, out_vis, out_occluded) -> No
 def ddf_query_rays_noalloc(h, rays, n, out_t, out_vis, stream=None) -> None:
     rp, keep = _rays(rays)
     _call("ddf_query_rays_noalloc", h, rp, int(n), _ptr(out_t), _ptr(out_vis), _stream(stream))
+
+
+def ddf_query_ao(h, rays, n_rays, offsets, n_points, out_hard, out_soft=None, stream=None) -> None:
+    rp, keep = _rays(rays)
+    _call("ddf_query_ao", h, rp, int(n_rays), _ptr(offsets), int(n_points), _ptr(out_hard),
+          _ptr(out_soft), _stream(stream))
+
+
+def ddf_set_graph_mode(h, on: bool) -> None:
+    _call("ddf_set_graph_mode", h, 1 if on else 0)
+
+
+def ddf_calibrate_fp8(h, rays, n, stream=None):
+    """Returns (amax, scales), H-1 floats each, and sets the scales."""
+    rp, keep = _rays(rays)
+    nl = max(0, lib_hidden_layers(h) - 1)
+    amax = np.zeros(max(nl, 1), np.float32)
+    sc = np.zeros(max(nl, 1), np.float32)
+    _call("ddf_calibrate_fp8", h, rp, int(n), amax.ctypes.data, sc.ctypes.data, _stream(stream))
+    return amax[:nl], sc[:nl]
+
+
+_HIDDEN = {}
+
+
+def lib_hidden_layers(h) -> int:
+    return _HIDDEN[h]
 
 
 def ddf_check_status(h) -> int:
