@@ -305,6 +305,7 @@ def main():
            "api": "ddf_query_shadow_host (pinned host buffers, copies overlapped with compute)"}
 
     compare = {}
+    fp8_out = None
     if not args.no_compare and args.precision != "fp32":
         f32 = ddf.DDF(*NET, precision="fp32", device=local)
         f32.load(blob)
@@ -322,6 +323,33 @@ def main():
                    "speedup_vs_fp32": (R / (f32_ms / 1e3)) and value / ws / (R / (f32_ms / 1e3)),
                    "bf16_vs_fp32_max_abs_dt": float((t - t32).abs().max().item())}
         f32.close()
+        # e4m3 path on the same rays: scales from the library's own calibration
+        # pass on the first 65,536 rays, tiles autotuned, 3 timed steps
+        f8 = ddf.DDF(*NET, precision="fp8", device=local)
+        f8.load(blob)
+        nc = min(R, 65536)
+        _, f8_scales = ddf.ddf_calibrate_fp8(f8.h, [r[:nc] for r in d_rays], nc, stream)
+        nt = min(R, 1 << 20)
+        ddf.ddf_autotune(f8.h, [r[:nt] for r in d_rays], nt, stream)
+        t8, v8 = torch.empty_like(t), torch.empty_like(t)
+        o8 = torch.empty_like(occ)
+        for _ in range(2):
+            ddf.ddf_query_shadow(f8.h, d_rays, R, LIGHT, t8, v8, o8, stream)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(3):
+            ddf.ddf_query_shadow(f8.h, d_rays, R, LIGHT, t8, v8, o8, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        f8_ms = a.elapsed_time(b) / 3
+        compare.update({"fp8_rays_per_s": R / (f8_ms / 1e3), "fp8_ms_per_step": f8_ms,
+                        "fp8_speedup_vs_fp32": f32_ms / f8_ms,
+                        "fp8_act_scales": [float(x) for x in f8_scales],
+                        "fp8_tile": {"hidden": ddf.ddf_get_tile(f8.h, 0),
+                                     "first": ddf.ddf_get_tile(f8.h, 1)},
+                        "fp8_vs_bf16_max_abs_dt": float((t8 - t).abs().max().item())})
+        fp8_out = (t8, v8)
+        f8.close()
 
     # CPU baseline (the FP64 oracle on a bounded prefix) + accuracy of the GPU outputs on it
     cpu = None
@@ -338,6 +366,13 @@ def main():
                "near_tie_frac": float(np.mean(np.abs(z1) < 1e-3)),
                "bounds": {"mean_abs_dt": 5e-3, "max_abs_dt": 5e-2, "flip_rate": 5e-3},
                "reference": "FP64 oracle, exact arithmetic"}
+        if fp8_out is not None:
+            t8n = fp8_out[0][:o_n].double().cpu().numpy()
+            v8n = fp8_out[1][:o_n].double().cpu().numpy()
+            d8 = np.abs(t8n - ref["t"])
+            acc["fp8"] = {"max_abs_dt": float(d8.max()), "mean_abs_dt": float(d8.mean()),
+                          "flip_rate": float(np.mean((v8n > 0.5) != (z1 > 0))),
+                          "bounds": {"mean_abs_dt": 2e-2, "max_abs_dt": 0.2, "flip_rate": 2e-2}}
         cpu = {"value": o_rate, "unit": "rays/s", "cores": cores(), "kind": "oracle",
                "sample": f"first {o_n} rays of the same workload ({o_el:.1f} s, numpy FP64)"}
 

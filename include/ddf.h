@@ -187,6 +187,48 @@ ddf_status ddf_set_graph_mode(ddf_handle h, int32_t on);
 ddf_status ddf_calibrate_fp8(ddf_handle h, const float* const rays[6], int64_t n, float* amax_out,
                              float* scales_out, void* stream);
 
+/* ---- distillation (Sec. 3.2 / 3.4), bf16 handles only ----
+ * One batch of rays with targets: t_target (device float[batch], the exact
+ * first-hit distance; ignored where hit_target is 0, may be +inf there) and
+ * hit_target (device uint8[batch], 1 = the ray hits the scene). The loss is
+ *   L = (1/max(1, N_hit)) sum_{hit} |min(t, 4) - min(t*, 4)|
+ *       + 0.3 (1/B) sum_i [softplus(z1) - y z1],     t = softplus(z0),
+ * computed from bf16 activations and FP32 head/loss arithmetic; gradients
+ * use bf16 operands with FP32 accumulation. batch: positive multiple of 8,
+ * below 2^31. out_loss: device float, nullable. Asynchronous on stream; the
+ * handle keeps every activation (8 + 4 W + ... bytes per ray and layer). */
+
+/* Gradient of the batch loss w.r.t. every weight and bias, kept in the
+ * handle (read it with ddf_get_grad); the weights do not change. */
+ddf_status ddf_compute_grad(ddf_handle h, const float* const rays[6], const float* t_target,
+                            const uint8_t* hit_target, int64_t batch, float* out_loss,
+                            void* stream);
+
+/* ddf_compute_grad, then one Adam step (beta 0.9 / 0.999, eps 1e-8,
+ * bias-corrected, no weight decay; lr > 0) on the FP32 master weights, after
+ * which every query on the handle uses the new weights. */
+ddf_status ddf_train_step(ddf_handle h, const float* const rays[6], const float* t_target,
+                          const uint8_t* hit_target, int64_t batch, float lr, float* out_loss,
+                          void* stream);
+
+/* Copies the last computed gradient (weight-blob layout, ddf_param_count
+ * floats) to host memory. Synchronous. */
+ddf_status ddf_get_grad(ddf_handle h, float* host_grad, size_t n_floats);
+
+/* Zeroes the Adam moments and step count. */
+ddf_status ddf_reset_optimizer(ddf_handle h);
+
+/* Exact first-hit distance of n rays against a union of spheres and
+ * axis-aligned boxes (the exact-cast supervision of Sec. 3.2 with analytic
+ * primitives): spheres = n_spheres x (cx, cy, cz, r), boxes = n_boxes x
+ * (lox, loy, loz, hix, hiy, hiz), device floats, at most 1024 of each. For
+ * each ray the smallest positive root over all primitives (surfaces, not
+ * CSG; tangent rays hit; slabs are closed): out_t (device float[n], +inf on a
+ * miss) and out_hit (device uint8[n]). No handle needed. Asynchronous. */
+ddf_status ddf_cast_scene(const float* spheres, int32_t n_spheres, const float* boxes,
+                          int32_t n_boxes, const float* const rays[6], int64_t n, float* out_t,
+                          uint8_t* out_hit, void* stream);
+
 /* Device status word of the handle: bit 0 = a pipeline wait timed out,
  * bit 1 = a scheduler wait timed out. Synchronises the device, stores the
  * word in *out and clears it. */

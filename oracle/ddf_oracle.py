@@ -295,6 +295,35 @@ def ddf_loss_grad(o, d, blob, octaves, width, hidden, t_target, hit_target):
     return L, flat
 
 
+def train_grad(o, d, blob, octaves, width, hidden, t_target, hit_target, precision="bf16"):
+    """Loss and flat gradient of one distillation batch (Sec. 3.2 / 3.4), with
+    the roundings of the bf16 training step emulated (precision="bf16"):
+    the encoding, every hidden weight matrix, every hidden activation (the last
+    one too, which then feeds the FP32 head) and every back-propagated
+    pre-activation gradient are rounded to bf16; sums are float64; the head,
+    the loss and dL/dz stay unrounded. precision="exact" rounds nothing and
+    equals ddf_loss_grad. Returns (L, flat gradient in the weight-blob layout)."""
+    rnd = round_bf16 if precision == "bf16" else (lambda a: np.asarray(a, F64))
+    layers = split_blob(blob, ddf_dims(octaves, width, hidden))
+    hid, (wo, bo) = layers[:-1], layers[-1]
+    x = rnd(encode(o, d, octaves))
+    acts = [x]
+    for w, b in hid:
+        x = rnd(np.maximum(x @ rnd(w).T + b, 0.0))
+        acts.append(x)
+    z = x @ wo.T + bo
+    L, dz = loss_and_dz(z, t_target, hit_target)
+    grads = [None] * len(layers)
+    grads[-1] = (dz.T @ acts[-1], dz.sum(axis=0))
+    dpre = rnd((dz @ wo) * (acts[-1] > 0))
+    for l in range(len(hid) - 1, -1, -1):
+        grads[l] = (dpre.T @ acts[l], dpre.sum(axis=0))
+        if l > 0:
+            dpre = rnd((dpre @ rnd(hid[l][0])) * (acts[l] > 0))
+    flat = np.concatenate([np.concatenate([g.reshape(-1), gb]) for g, gb in grads])
+    return L, flat
+
+
 def adam_step(w, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
     """One Adam update (Kingma & Ba), bias-corrected, no weight decay.
     step counts from 1. Returns (w, m, v)."""

@@ -19,9 +19,10 @@
 #include <string>
 #include <vector>
 
+#include "handle.h"
 #include "kernels.h"
 
-namespace {
+namespace ddfi {
 
 thread_local std::string g_last_error;
 
@@ -35,26 +36,9 @@ ddf_status cuda_fail(cudaError_t e, const char* what) {
   return fail(s, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-#define DDF_CK(call)                                   \
-  do {                                                 \
-    cudaError_t e_ = (call);                           \
-    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
-  } while (0)
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
-// Restores the caller's current device when it goes out of scope.
-struct DeviceGuard {
-  int prev = -1;
-  bool ok = false;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    ok = cudaSetDevice(dev) == cudaSuccess;
-  }
-  ~DeviceGuard() {
-    if (prev >= 0) cudaSetDevice(prev);
-  }
-};
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -86,80 +70,11 @@ bool make_tmap(CUtensorMap* m, const void* base, bool one_byte, uint64_t inner, 
   return r == CUDA_SUCCESS;
 }
 
-constexpr int kProfClasses = 4;
-enum ProfClass { kProfEncode = 0, kProfGemm = 1, kProfHead = 2, kProfFirst = 3 };
 
-}  // namespace
+}  // namespace ddfi
 
-struct ddf_s {
-  ddf_config cfg{};
-  int d_in = 0;
-  int kp32 = 0;  // padded encoded width, FP32 rows (multiple of 8)
-  int kp16 = 0;  // padded encoded width, bf16 rows (multiple of 8 -> 16-byte rows)
-  int bn = 0;    // tensor-core N tile (= tile.bn)
-  ddf::TcTile tile{256, 4};        // layers 2..H
-  ddf::TcTile tile_first{256, 4};  // layer 1
-  int pair_clusters = 0;  // co-resident clusters of the CTA-pair kernel
-  int num_sms = 0;
-  bool loaded = false;
-  bool scales_set = false;
-  uint64_t timeout_ns = 2000000000ull;
-  int64_t chunk = 1 << 20;
 
-  std::vector<void*> owned;  // device allocations freed by ddf_destroy
-  float* d_blob = nullptr;   // FP32 master weights
-  std::vector<float*> wf;    // FP32: padded W per hidden layer
-  std::vector<float*> bias;  // per hidden layer [W]
-  std::vector<__nv_bfloat16*> wb;  // bf16 W (all layers for BF16, layer 1 for FP8)
-  std::vector<uint8_t*> wq;        // FP8: e4m3 codes for layers 2..H
-  std::vector<float*> wscale;      // FP8: per-output-channel scales
-  std::vector<float*> colscale;    // FP8: s_{l-1} * wscale_l
-  std::vector<float> act_scales;
-  std::vector<CUtensorMap> tmB;
-  std::vector<__nv_bfloat16*> wcal;  // FP8: bf16 copies of layers 2..H for calibration
-  std::vector<CUtensorMap> tmBcal;   // FP8: maps of the bf16 weights, calibration tile
-
-  // CUDA-graph replay of queries (ddf_set_graph_mode)
-  bool graph_mode = false;
-  cudaStream_t s_graph = nullptr;
-  struct GraphEntry {
-    std::vector<uint64_t> key;
-    cudaGraphExec_t exec;
-  };
-  std::vector<GraphEntry> graphs;
-  float* ao_vis = nullptr;    // AO: per-ray visibility and hit flags
-  uint8_t* ao_hit = nullptr;
-  int64_t ao_rows = 0;
-  float* head_w = nullptr;  // [2 x W]
-  float* head_b = nullptr;  // [2]
-
-  int64_t ws_rows = 0;
-  void* ws_enc = nullptr;
-  void* ws_act[2] = {nullptr, nullptr};
-  float2* ws_part = nullptr;
-
-  uint32_t* status_dev = nullptr;
-
-  bool prof = false;
-  std::vector<cudaEvent_t> ev_pool;
-  size_t ev_used = 0;
-  struct Rec {
-    int cls;
-    cudaEvent_t a, b;
-  };
-  std::vector<Rec> recs;
-
-  // host-buffer pipeline
-  cudaStream_t s_copy = nullptr, s_comp = nullptr;
-  float* hp_rays[2][6] = {};
-  float* hp_t[2] = {};
-  float* hp_v[2] = {};
-  uint8_t* hp_occ[2] = {};
-  int64_t hp_rows = 0;
-  cudaEvent_t ev_in[2] = {}, ev_comp[2] = {};
-};
-
-namespace {
+namespace ddfi {
 
 ddf_status dev_alloc(ddf_s* h, void** p, size_t bytes) {
   *p = nullptr;
@@ -209,22 +124,6 @@ cudaEvent_t prof_event(ddf_s* h) {
   return h->ev_pool[h->ev_used++];
 }
 
-struct ProfScope {
-  ddf_s* h;
-  int cls;
-  cudaStream_t s;
-  cudaEvent_t a = nullptr;
-  ProfScope(ddf_s* h_, int cls_, cudaStream_t s_) : h(h_), cls(cls_), s(s_) {
-    if (h->prof && (a = prof_event(h)) != nullptr) cudaEventRecord(a, s);
-  }
-  ~ProfScope() {
-    if (a == nullptr) return;
-    cudaEvent_t b = prof_event(h);
-    if (b == nullptr) return;
-    cudaEventRecord(b, s);
-    h->recs.push_back({cls, a, b});
-  }
-};
 
 // Most head partials any tile writes per row: N/128 blocks x 2 epilogue halves.
 int max_partials(int W) { return (W / 128) * 2; }
@@ -513,7 +412,9 @@ ddf_status calibrate_chunk(ddf_s* h, ddf::RaySoA rays, int m, float* amax, cudaS
   return DDF_OK;
 }
 
-}  // namespace
+}  // namespace ddfi
+
+using namespace ddfi;
 
 extern "C" {
 
@@ -847,7 +748,7 @@ ddf_status ddf_calibrate_fp8(ddf_handle h, const float* const rays[6], int64_t n
   return ddf_set_act_scales(h, sc.data(), nl);
 }
 
-namespace {
+namespace ddfi {
 
 // Host-buffer pipeline: chunk i's rays are copied in on a copy stream while
 // chunk i-1 is evaluated on a compute stream; results go back on the copy
@@ -926,7 +827,7 @@ ddf_status host_pipeline(ddf_s* h, const float* const rays[6], int64_t n, const 
   return DDF_OK;
 }
 
-}  // namespace
+}  // namespace ddfi
 
 ddf_status ddf_query_rays_host(ddf_handle h, const float* const rays[6], int64_t n, float* out_t,
                                float* out_vis) {
@@ -1042,7 +943,7 @@ ddf_status ddf_get_tile(ddf_handle h, int32_t which, ddf_tile* tile) {
   return DDF_OK;
 }
 
-namespace {
+namespace ddfi {
 
 constexpr int kTileCands = 6;
 const ddf_tile kCands[kTileCands] = {{256, 4, 0, 0}, {256, 8, 0, 0}, {128, 4, 0, 0},
@@ -1052,7 +953,7 @@ bool cand_ok(ddf_s* h, const ddf_tile& c) {
   return h->cfg.width % c.bn == 0 && (c.cta_pair == 0 || h->pair_clusters > 0);
 }
 
-}  // namespace
+}  // namespace ddfi
 
 ddf_status ddf_autotune(ddf_handle h, const float* const rays[6], int64_t n, void* stream,
                         double* ms_out, int32_t n_out) {

@@ -40,15 +40,15 @@ __device__ __forceinline__ EpiVectors stage_epi_vectors(const TcGemmParams& p, f
   float* s0 = smem + 2 * n;
   float* s1 = smem + 3 * n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    sb[i] = p.bias[i];
+    if (p.bias != nullptr) sb[i] = p.bias[i];
     if (p.col_scale != nullptr) ss[i] = p.col_scale[i];
-    if (p.mode != 0) {
+    if (p.mode == 1) {  // only the last query layer folds the head
       s0[i] = p.head_w[i];
       s1[i] = p.head_w[n + i];
     }
   }
-  return EpiVectors{sb, p.col_scale != nullptr ? ss : nullptr, p.mode != 0 ? s0 : nullptr,
-                    p.mode != 0 ? s1 : nullptr};
+  return EpiVectors{sb, p.col_scale != nullptr ? ss : nullptr, p.mode == 1 ? s0 : nullptr,
+                    p.mode == 1 ? s1 : nullptr};
 }
 
 __device__ __forceinline__ uint32_t epi_pack_bf16x2(float lo, float hi) {
@@ -158,6 +158,54 @@ __device__ __forceinline__ void epi_row(const TcGemmParams& p, const EpiVectors&
     if (next2) tmem_ld32(tbase + 32u * (c + 2), va);  // in flight during chunk c+1
     epi_chunk<OUT_FP8>(p, ev, vb, row, row_ok, n0 + 32 * (c + 1), h0, h1);
     if (next2) tmem_wait_ld_regs(va);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Training epilogues (no bias, scale or ReLU), one 32-column chunk at a time:
+//   mode 2 (input gradient): x = acc where mask[row][col] > 0, else 0; bf16 to
+//          p.out [M x ldo]. mask is the bf16 activation [M x ldm] whose ReLU
+//          the gradient passes back through.
+//   mode 3 (weight gradient, split-K): acc as FP32 to
+//          p.out_f32 + split * split_stride, row-major [M x ldo].
+__device__ __forceinline__ void epi_row_train(const TcGemmParams& p, uint32_t tbase, int row,
+                                              bool row_ok, int n0, int c_begin, int c_end,
+                                              int split) {
+  uint32_t v[32];
+#pragma unroll 1
+  for (int c = c_begin; c < c_end; ++c) {
+    tmem_ld32(tbase + 32u * c, v);
+    tmem_wait_ld_regs(v);
+    if (!row_ok) continue;
+    const int nc = n0 + 32 * c;
+    if (p.mode == 2) {
+      const uint4* mk = reinterpret_cast<const uint4*>(
+          static_cast<const __nv_bfloat16*>(p.mask) + static_cast<size_t>(row) * p.ldm + nc);
+      uint4* dst = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(p.out) +
+                                            static_cast<size_t>(row) * p.ldo + nc);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint4 m4 = mk[k];
+        const uint32_t mw[4] = {m4.x, m4.y, m4.z, m4.w};
+        uint32_t ow[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          // a bf16 activation is > 0 iff its sign bit is clear and it is not zero
+          const uint32_t lo = mw[q] & 0xFFFFu, hi = mw[q] >> 16;
+          const float x0 = (lo != 0 && (lo & 0x8000u) == 0) ? __uint_as_float(v[8 * k + 2 * q]) : 0.f;
+          const float x1 = (hi != 0 && (hi & 0x8000u) == 0) ? __uint_as_float(v[8 * k + 2 * q + 1]) : 0.f;
+          ow[q] = epi_pack_bf16x2(x0, x1);
+        }
+        dst[k] = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+      }
+    } else {
+      float4* dst = reinterpret_cast<float4*>(p.out_f32 + static_cast<size_t>(split) * p.split_stride +
+                                              static_cast<size_t>(row) * p.ldo + nc);
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        dst[k] = make_float4(__uint_as_float(v[4 * k]), __uint_as_float(v[4 * k + 1]),
+                             __uint_as_float(v[4 * k + 2]), __uint_as_float(v[4 * k + 3]));
+    }
   }
 }
 

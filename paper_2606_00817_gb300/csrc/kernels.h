@@ -32,6 +32,14 @@ struct TcGemmParams {
   uint64_t timeout_ns;
   float* amax;             // mode 0, nullable: running max of the layer's outputs
                            // (rows < M), for activation-scale calibration
+  // training modes (1-CTA kernel only):
+  //   mode 2: out = bf16(acc masked by mask > 0), mask bf16 [M x ldm]
+  //   mode 3: out_f32[split][M x ldo] = acc, k_splits splits of the K range
+  const void* mask;
+  int ldm;
+  int k_splits;
+  size_t split_stride;     // elements between split outputs
+  float* out_f32;
 };
 
 // Tile configuration of the tensor-core layer: N tile (128 or 256) and the
@@ -90,6 +98,38 @@ cudaError_t launch_finish_heads(const float2* part, int nblk, int M, const float
 // hard[p] = 1 - mean(hit), soft[p] = 1 - mean(vis); empty sets give 1.
 cudaError_t launch_ao_reduce(const uint8_t* hit, const float* vis, const int32_t* offsets,
                              int64_t n_points, float* hard, float* soft, cudaStream_t s);
+
+// ---- distillation step (train.cu) ----
+cudaError_t launch_transpose_bf16(const __nv_bfloat16* src, int R, int C, int lds,
+                                  __nv_bfloat16* dst, int ldd, cudaStream_t s);
+// z[r] = (Wo h_r + bo) from bf16 rows H [M x W]
+cudaError_t launch_head_train(const __nv_bfloat16* H, int M, int W, const float* wo,
+                              const float* bo, float2* z, cudaStream_t s);
+// Loss of Sec. 3.2 / 3.4 and dL/dz: L1 on min(softplus(z0), clamp) against
+// min(t*, clamp) over hit rays / max(1, N_hit), plus lam x BCE(z1, y) / B.
+// part: ceil(B/256) floats of scratch; loss_out nullable (device scalar).
+cudaError_t launch_loss(const float2* z, const float* t_tgt, const uint8_t* y, int64_t B,
+                        unsigned* nhit, float clamp, float lam, float2* dz, float* part,
+                        float* loss_out, cudaStream_t s);
+cudaError_t launch_head_backward(const float2* dz, const __nv_bfloat16* H, int M, int W,
+                                 const float* wo, __nv_bfloat16* dpre, cudaStream_t s);
+// part [splits x 2 x W]: row-split partials of dz^T H
+cudaError_t launch_head_grad(const float2* dz, const __nv_bfloat16* H, int M, int W, int splits,
+                             float* part, cudaStream_t s);
+// part [splits x N]: row-split partial column sums
+cudaError_t launch_colsum_bf16(const __nv_bfloat16* X, int M, int N, int ld, int splits,
+                               float* part, cudaStream_t s);
+cudaError_t launch_colsum_f32(const float* X, int M, int N, int ld, int splits, float* part,
+                              cudaStream_t s);
+cudaError_t launch_splitk_reduce(const float* part, int S, int rows, int ldp, int64_t split_stride,
+                                 int cols_out, float* out, int ldo, cudaStream_t s);
+cudaError_t launch_adam(float* w, const float* g, float* m, float* v, int64_t n, float lr,
+                        float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s);
+// dst [K x N] = bf16(src [N x K])^T
+cudaError_t launch_pack_bf16_t(const float* src, int N, int K, __nv_bfloat16* dst, cudaStream_t s);
+cudaError_t launch_cast_scene(const float* spheres, int ns, const float* boxes, int nb,
+                              RaySoA rays, int64_t n, float* t_out, uint8_t* hit_out,
+                              cudaStream_t s);
 
 // Weight preparation (load time).
 // dst[N x ldd] = src[N x K] zero-padded to ldd columns.

@@ -107,16 +107,28 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
   const int num_m = (p.M + S::BM - 1) / S::BM;
   const int num_n = p.N / BN;
   const int num_kb = (p.K + S::BK - 1) / S::BK;
-  const int num_tiles = num_m * num_n;
+  // split-K (mode 3): tile = (split, m block, n block); split s covers the
+  // k-blocks [s kb_per, (s+1) kb_per) (the launcher makes every split non-empty)
+  const int splits = p.k_splits > 1 ? p.k_splits : 1;
+  const int kb_per = num_kb / splits;
+  const int num_tiles = splits * num_m * num_n;
+  auto decode = [&](int tile, int& split, int& m_blk, int& n_blk) {
+    split = tile / (num_m * num_n);
+    const int r = tile - split * num_m * num_n;
+    m_blk = r / num_n;
+    n_blk = r - m_blk * num_n;
+  };
 
   if (warp == 0 && lane == 0) {
     // ---------------------------------------------------------- producer
     int it = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
-      const int m0 = (tile / num_n) * S::BM;
-      const int n0 = (tile % num_n) * BN;
-      for (int kb = 0; kb < num_kb; ++kb, ++it) {
+      int split, m_blk, n_blk;
+      decode(tile, split, m_blk, n_blk);
+      const int m0 = m_blk * S::BM;
+      const int n0 = n_blk * BN;
+      for (int kb = split * kb_per; kb < (split + 1) * kb_per; ++kb, ++it) {
         const int s = it % S::STAGES;
         const uint32_t ph = (it / S::STAGES) & 1;
         if (!mbar_wait_bounded(empty_bar(s), ph ^ 1u, abort_flag, p.timeout_ns)) {
@@ -149,7 +161,8 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
       }
       tc_fence_after();
       const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(b * BN);
-      for (int kb = 0; kb < num_kb; ++kb, ++it) {
+      const int kb0 = (tile / (num_m * num_n)) * kb_per;
+      for (int kb = kb0; kb < kb0 + kb_per; ++kb, ++it) {
         const int s = it % S::STAGES;
         const uint32_t ph = (it / S::STAGES) & 1;
         if (!mbar_wait_bounded(full_bar(s), ph, abort_flag, p.timeout_ns)) {
@@ -163,7 +176,7 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
         for (int j = 0; j < 4; ++j) {  // 4 x 32 bytes of K per 128-byte row
           const uint64_t ad = sw128_kmajor_desc(a0 + 32u * j);
           const uint64_t bd = sw128_kmajor_desc(b0 + 32u * j);
-          const uint32_t acc = (kb | j) != 0 ? 1u : 0u;
+          const uint32_t acc = (kb != kb0 || j != 0) ? 1u : 0u;
           if constexpr (IN_FP8)
             tc_mma_f8(d_tmem, ad, bd, idesc, acc);
           else
@@ -195,20 +208,23 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
         break;
       }
       tc_fence_after();
-      const int m_blk = tile / num_n;
-      const int n_blk = tile % num_n;
+      int split, m_blk, n_blk;
+      decode(tile, split, m_blk, n_blk);
       const int row = m_blk * S::BM + r_local;
       const bool row_ok = row < p.M;
       const int n0 = n_blk * BN;
       const uint32_t tbase = tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
                              static_cast<uint32_t>(b * BN);
       float h0 = 0.f, h1 = 0.f;
-      epi_row<OUT_FP8>(p, ev, tbase, row, row_ok, n0, half * kChunks, (half + 1) * kChunks, h0,
-                       h1);
+      if (p.mode >= 2)
+        epi_row_train(p, tbase, row, row_ok, n0, half * kChunks, (half + 1) * kChunks, split);
+      else
+        epi_row<OUT_FP8>(p, ev, tbase, row, row_ok, n0, half * kChunks, (half + 1) * kChunks, h0,
+                         h1);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty_bar(b));
-      if (p.mode != 0 && row_ok)
+      if (p.mode == 1 && row_ok)
         p.head_part[(static_cast<size_t>(n_blk) * (EPI / 4) + half) * p.M + row] =
             make_float2(h0, h1);
     }
@@ -229,6 +245,7 @@ cudaError_t launch_one(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcG
   using S = TcShape<BN, IN_FP8>;
   auto kern = tc_gemm_kernel<BN, IN_FP8, OUT_FP8, EPI>;
   // applies to the current device; cheap enough to repeat on every launch
+  if (p.k_splits > 1 && ((p.K + S::BK - 1) / S::BK) % p.k_splits != 0) return cudaErrorInvalidValue;
   const int smem = S::SMEM_BYTES + epi_vector_bytes(p.N);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;

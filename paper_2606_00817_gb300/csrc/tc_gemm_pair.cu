@@ -223,7 +223,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(tempty_leader0 + 8u * b);
-      if (p.mode != 0 && row_ok)
+      if (p.mode == 1 && row_ok)
         p.head_part[static_cast<size_t>(n_blk) * p.M + row] = make_float2(h0, h1);
     }
   }
@@ -306,6 +306,7 @@ int tc_gemm_pair_max_clusters(bool in_fp8) {
 cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, bool staged, const CUtensorMap& tmA,
                                 const CUtensorMap& tmB, const TcGemmParams& p, int clusters,
                                 cudaStream_t s) {
+  if (p.mode > 1) return cudaErrorInvalidValue;  // training modes run on the 1-CTA kernel
   const int grid = 2 * clusters;
   if (in_fp8) return staged ? launch_pair_io<true, true>(out_fp8, tmA, tmB, p, grid, s)
                             : launch_pair_io<true, false>(out_fp8, tmA, tmB, p, grid, s);

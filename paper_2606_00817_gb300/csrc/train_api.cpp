@@ -1,0 +1,347 @@
+// train_api.cpp -- C ABI of the distillation step (declared in include/ddf.h).
+//
+// One step of Sec. 3.2 / 3.4 on a bf16 handle: forward through the encoder
+// and the tensor-core layers keeping every bf16 activation, the FP32 head,
+// the clamped-L1 + 0.3 x cross-entropy loss and dL/dz, then back through the
+// head and every layer:
+//   dW_l = dpre_l^T A_l   (tensor cores, split-K over the batch, FP32 partials
+//                          reduced in a fixed order)
+//   db_l = column sums of dpre_l
+//   dpre_{l-1} = (dpre_l W_l) masked by h_{l-1} > 0   (tensor cores, bf16)
+// and, for ddf_train_step, Adam on the FP32 master weights followed by a
+// refresh of the bf16 copies the queries use. The exact analytic ray caster
+// that produces distillation targets lives here too (ddf_cast_scene).
+#include <algorithm>
+#include <cmath>
+
+#include "handle.h"
+#include "kernels.h"
+
+using namespace ddfi;
+
+namespace {
+
+constexpr int kColSplits = 64;  // row splits of the column sums
+constexpr float kClamp = 4.0f;  // L1 clamp ("box scale")
+constexpr float kLambda = 0.3f; // cross-entropy weight
+constexpr float kB1 = 0.9f, kB2 = 0.999f, kEps = 1e-8f;
+
+struct BlobOffsets {
+  std::vector<size_t> w, b;
+  size_t wo = 0, bo = 0;
+};
+
+BlobOffsets blob_offsets(const ddf_s* h) {
+  BlobOffsets o;
+  const size_t W = h->cfg.width;
+  size_t off = 0;
+  for (int l = 0; l < h->cfg.hidden_layers; ++l) {
+    const size_t K = l == 0 ? h->d_in : W;
+    o.w.push_back(off);
+    off += W * K;
+    o.b.push_back(off);
+    off += W;
+  }
+  o.wo = off;
+  o.bo = off + 2 * W;
+  return o;
+}
+
+size_t n_params(const ddf_s* h) { return blob_offsets(h).bo + 2; }
+
+ddf_status train_alloc(ddf_s* h, void** p, size_t bytes) { return dev_alloc(h, p, bytes); }
+
+// Writes the bf16 query copies (W_l, and W_l^T for l >= 1), the biases and
+// the head from the FP32 master blob.
+ddf_status refresh_weights(ddf_s* h, cudaStream_t st) {
+  const int W = h->cfg.width;
+  const BlobOffsets o = blob_offsets(h);
+  for (int l = 0; l < h->cfg.hidden_layers; ++l) {
+    const int K = l == 0 ? h->d_in : W;
+    DDF_CK(ddf::launch_pack_bf16(h->d_blob + o.w[l], W, K, l == 0 ? h->kp16 : W, h->wb[l], st));
+    DDF_CK(cudaMemcpyAsync(h->bias[l], h->d_blob + o.b[l], W * sizeof(float),
+                           cudaMemcpyDeviceToDevice, st));
+    if (l > 0) DDF_CK(ddf::launch_pack_bf16_t(h->d_blob + o.w[l], W, W, h->wt[l], st));
+  }
+  DDF_CK(cudaMemcpyAsync(h->head_w, h->d_blob + o.wo, 2 * W * sizeof(float),
+                         cudaMemcpyDeviceToDevice, st));
+  DDF_CK(cudaMemcpyAsync(h->head_b, h->d_blob + o.bo, 2 * sizeof(float), cudaMemcpyDeviceToDevice,
+                         st));
+  return DDF_OK;
+}
+
+ddf_status ensure_train(ddf_s* h, int64_t B) {
+  const int W = h->cfg.width, H = h->cfg.hidden_layers;
+  ddf_status s;
+  void* p;
+  if (h->grad == nullptr) {
+    const size_t np = n_params(h);
+    if ((s = train_alloc(h, &p, np * sizeof(float))) != DDF_OK) return s;
+    h->grad = static_cast<float*>(p);
+    if ((s = train_alloc(h, &p, np * sizeof(float))) != DDF_OK) return s;
+    h->adam_m = static_cast<float*>(p);
+    if ((s = train_alloc(h, &p, np * sizeof(float))) != DDF_OK) return s;
+    h->adam_v = static_cast<float*>(p);
+    DDF_CK(cudaMemset(h->adam_m, 0, np * sizeof(float)));
+    DDF_CK(cudaMemset(h->adam_v, 0, np * sizeof(float)));
+    h->adam_step = 0;
+    h->wt.assign(H, nullptr);
+    h->tmBtr.assign(H, CUtensorMap{});
+    h->tmWT.assign(H, CUtensorMap{});
+    for (int l = 0; l < H; ++l) {
+      const int kp = l == 0 ? h->kp16 : W;
+      if (!make_tmap(&h->tmBtr[l], h->wb[l], false, kp, W, static_cast<uint64_t>(kp) * 2, h->bn))
+        return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for a weight map");
+      if (l == 0) continue;
+      if ((s = train_alloc(h, &p, static_cast<size_t>(W) * W * 2)) != DDF_OK) return s;
+      h->wt[l] = static_cast<__nv_bfloat16*>(p);
+      if (!make_tmap(&h->tmWT[l], h->wt[l], false, W, W, static_cast<uint64_t>(W) * 2, h->bn))
+        return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for a weight map");
+    }
+    const int nmax = std::max(W, 128);
+    if ((s = train_alloc(h, &p, 4 * static_cast<size_t>(W) * nmax * sizeof(float))) != DDF_OK) return s;
+    h->tr_part = static_cast<float*>(p);
+    if ((s = train_alloc(h, &p, kColSplits * 2 * static_cast<size_t>(W) * sizeof(float))) != DDF_OK)
+      return s;
+    h->tr_cpart = static_cast<float*>(p);
+    if ((s = train_alloc(h, &p, sizeof(unsigned))) != DDF_OK) return s;
+    h->tr_nhit = static_cast<unsigned*>(p);
+    if ((s = refresh_weights(h, nullptr)) != DDF_OK) return s;
+    DDF_CK(cudaDeviceSynchronize());
+  }
+  if (B > h->tr_rows) {
+    dev_free(h, h->tr_enc);
+    for (void* q : h->tr_h) dev_free(h, q);
+    dev_free(h, h->tr_dpre[0]);
+    dev_free(h, h->tr_dpre[1]);
+    dev_free(h, h->tr_t1);
+    dev_free(h, h->tr_t2);
+    dev_free(h, h->tr_z);
+    dev_free(h, h->tr_dz);
+    dev_free(h, h->tr_lpart);
+    h->tr_h.assign(H, nullptr);
+    h->tr_rows = 0;
+    const size_t act = static_cast<size_t>(B) * W * 2;
+    if ((s = train_alloc(h, &h->tr_enc, static_cast<size_t>(B) * h->kp16 * 2)) != DDF_OK) return s;
+    for (int l = 0; l < H; ++l)
+      if ((s = train_alloc(h, &h->tr_h[l], act)) != DDF_OK) return s;
+    for (int i = 0; i < 2; ++i)
+      if ((s = train_alloc(h, &h->tr_dpre[i], act)) != DDF_OK) return s;
+    if ((s = train_alloc(h, &h->tr_t1, act)) != DDF_OK) return s;
+    if ((s = train_alloc(h, &h->tr_t2, static_cast<size_t>(B) * std::max(W, 128) * 2)) != DDF_OK)
+      return s;
+    if ((s = train_alloc(h, &p, B * sizeof(float2))) != DDF_OK) return s;
+    h->tr_z = static_cast<float2*>(p);
+    if ((s = train_alloc(h, &p, B * sizeof(float2))) != DDF_OK) return s;
+    h->tr_dz = static_cast<float2*>(p);
+    if ((s = train_alloc(h, &p, ((B + 255) / 256) * sizeof(float))) != DDF_OK) return s;
+    h->tr_lpart = static_cast<float*>(p);
+    h->tr_rows = B;
+  }
+  return DDF_OK;
+}
+
+// One tensor-core GEMM C = A B^T with A [M x K] and B [N x K] bf16 K-major.
+ddf_status tc_gemm(ddf_s* h, const void* A, int M, int K, const CUtensorMap& tmB, int bn,
+                   ddf::TcGemmParams p, cudaStream_t st) {
+  CUtensorMap tmA;
+  if (!make_tmap(&tmA, A, false, K, M, static_cast<uint64_t>(K) * 2, 128))
+    return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for an activation map");
+  p.M = M;
+  p.K = K;
+  p.status = h->status_dev;
+  p.timeout_ns = h->timeout_ns;
+  const int splits = p.k_splits > 1 ? p.k_splits : 1;
+  const int64_t tiles = splits * ((M + 127) / 128) * static_cast<int64_t>(p.N / bn);
+  const int grid = static_cast<int>(std::min<int64_t>(tiles, h->num_sms));
+  DDF_CK(ddf::launch_tc_gemm(ddf::TcTile{bn, 4}, false, false, tmA, tmB, p, grid, st));
+  return DDF_OK;
+}
+
+ddf_status check_train_args(ddf_s* h, const float* const rays[6], const float* t_target,
+                            const uint8_t* hit_target, int64_t batch) {
+  if (h == nullptr) return fail(DDF_ERR_INVALID_ARG, "handle is NULL");
+  if (!h->loaded) return fail(DDF_ERR_BAD_WEIGHTS, "no weights loaded");
+  if (h->cfg.precision != DDF_BF16)
+    return fail(DDF_ERR_UNSUPPORTED, "training runs on bf16 handles");
+  if (batch < 8 || batch % 8 != 0 || batch >= (int64_t{1} << 31))
+    return fail(DDF_ERR_INVALID_ARG, "batch must be a positive multiple of 8 below 2^31");
+  ddf_status s = check_rays(rays, batch);
+  if (s != DDF_OK) return s;
+  if (t_target == nullptr || hit_target == nullptr)
+    return fail(DDF_ERR_INVALID_ARG, "targets are NULL");
+  return DDF_OK;
+}
+
+ddf_status compute_grad(ddf_s* h, const float* const rays[6], const float* t_tgt,
+                        const uint8_t* y, int64_t B64, float* loss_out, cudaStream_t st) {
+  const int W = h->cfg.width, H = h->cfg.hidden_layers;
+  const int B = static_cast<int>(B64);
+  const BlobOffsets o = blob_offsets(h);
+  ddf::RaySoA r;
+  for (int c = 0; c < 6; ++c) r.p[c] = rays[c];
+  auto bf = [](void* q) { return static_cast<__nv_bfloat16*>(q); };
+
+  // ---- forward, keeping every activation
+  {
+    ProfScope ps(h, kProfEncode, st);
+    DDF_CK(ddf::launch_encode_bf16(r, B, h->cfg.octaves, h->kp16, bf(h->tr_enc), st));
+  }
+  for (int l = 0; l < H; ++l) {
+    ddf::TcGemmParams p{};
+    p.N = W;
+    p.bias = h->bias[l];
+    p.out_scale = 1.0f;
+    p.out = h->tr_h[l];
+    p.ldo = W;
+    p.mode = 0;
+    ProfScope ps(h, l == 0 ? kProfFirst : kProfGemm, st);
+    ddf_status s = tc_gemm(h, l == 0 ? h->tr_enc : h->tr_h[l - 1], B, l == 0 ? h->kp16 : W,
+                           h->tmBtr[l], h->bn, p, st);
+    if (s != DDF_OK) return s;
+  }
+  DDF_CK(ddf::launch_head_train(bf(h->tr_h[H - 1]), B, W, h->head_w, h->head_b, h->tr_z, st));
+  DDF_CK(ddf::launch_loss(h->tr_z, t_tgt, y, B, h->tr_nhit, kClamp, kLambda, h->tr_dz, h->tr_lpart,
+                          loss_out, st));
+
+  // ---- head: dW_o = dz^T h_H, db_o = sum dz, dpre_H = (dz W_o) where h_H > 0
+  DDF_CK(ddf::launch_head_grad(h->tr_dz, bf(h->tr_h[H - 1]), B, W, kColSplits, h->tr_cpart, st));
+  DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart, kColSplits, 2, W, 2 * W, W, h->grad + o.wo, W, st));
+  DDF_CK(ddf::launch_colsum_f32(reinterpret_cast<const float*>(h->tr_dz), B, 2, 2, kColSplits,
+                                h->tr_cpart, st));
+  DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart, kColSplits, 1, 2, 2, 2, h->grad + o.bo, 2, st));
+  DDF_CK(ddf::launch_head_backward(h->tr_dz, bf(h->tr_h[H - 1]), B, W, h->head_w,
+                                   bf(h->tr_dpre[0]), st));
+
+  // ---- layers, last to first
+  int cur = 0;
+  const int num_kb = (B + 63) / 64;
+  const int splits = num_kb % 4 == 0 ? 4 : (num_kb % 2 == 0 ? 2 : 1);
+  for (int l = H - 1; l >= 0; --l) {
+    const int K = l == 0 ? h->d_in : W;        // columns of W_l in the blob
+    const int Kst = l == 0 ? h->kp16 : W;      // stored width of the layer input
+    const int N = l == 0 ? static_cast<int>(round_up(h->kp16, 128)) : W;  // GEMM N
+    const int bnw = N % 256 == 0 ? 256 : 128;
+    const void* A_in = l == 0 ? h->tr_enc : h->tr_h[l - 1];
+    DDF_CK(ddf::launch_transpose_bf16(bf(h->tr_dpre[cur]), B, W, W, bf(h->tr_t1), B, st));
+    DDF_CK(ddf::launch_transpose_bf16(static_cast<const __nv_bfloat16*>(A_in), B, Kst, Kst,
+                                      bf(h->tr_t2), B, st));
+    // dW_l [W x N] = dpre^T (as [W x B]) times A_in (as [N x B])^T, split over B
+    CUtensorMap tmT2;
+    if (!make_tmap(&tmT2, h->tr_t2, false, B, N, static_cast<uint64_t>(B) * 2, bnw))
+      return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for a gradient map");
+    ddf::TcGemmParams p{};
+    p.N = N;
+    p.mode = 3;
+    p.out_f32 = h->tr_part;
+    p.ldo = N;
+    p.k_splits = splits;
+    p.split_stride = static_cast<size_t>(W) * N;
+    {
+      ProfScope ps(h, kProfGemm, st);
+      ddf_status s = tc_gemm(h, h->tr_t1, W, B, tmT2, bnw, p, st);
+      if (s != DDF_OK) return s;
+    }
+    DDF_CK(ddf::launch_splitk_reduce(h->tr_part, splits, W, N, static_cast<int64_t>(W) * N, K,
+                                     h->grad + o.w[l], K, st));
+    DDF_CK(ddf::launch_colsum_bf16(bf(h->tr_dpre[cur]), B, W, W, kColSplits, h->tr_cpart, st));
+    DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart, kColSplits, 1, W, W, W, h->grad + o.b[l], W, st));
+    if (l == 0) break;
+    // dpre_{l-1} [B x W] = (dpre_l [B x W]) (W_l^T [W x W])^T masked by h_{l-1} > 0
+    ddf::TcGemmParams q{};
+    q.N = W;
+    q.mode = 2;
+    q.out = h->tr_dpre[cur ^ 1];
+    q.ldo = W;
+    q.mask = h->tr_h[l - 1];
+    q.ldm = W;
+    {
+      ProfScope ps(h, kProfGemm, st);
+      ddf_status s = tc_gemm(h, h->tr_dpre[cur], B, W, h->tmWT[l], h->bn, q, st);
+      if (s != DDF_OK) return s;
+    }
+    cur ^= 1;
+  }
+  h->grad_valid = true;
+  return DDF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ddf_status ddf_compute_grad(ddf_handle h, const float* const rays[6], const float* t_target,
+                            const uint8_t* hit_target, int64_t batch, float* out_loss,
+                            void* stream) {
+  ddf_status s = check_train_args(h, rays, t_target, hit_target, batch);
+  if (s != DDF_OK) return s;
+  DeviceGuard g(h->cfg.device);
+  if ((s = ensure_train(h, batch)) != DDF_OK) return s;
+  return compute_grad(h, rays, t_target, hit_target, batch, out_loss,
+                      static_cast<cudaStream_t>(stream));
+}
+
+ddf_status ddf_train_step(ddf_handle h, const float* const rays[6], const float* t_target,
+                          const uint8_t* hit_target, int64_t batch, float lr, float* out_loss,
+                          void* stream) {
+  ddf_status s = check_train_args(h, rays, t_target, hit_target, batch);
+  if (s != DDF_OK) return s;
+  if (!(lr > 0.f) || !std::isfinite(lr)) return fail(DDF_ERR_INVALID_ARG, "lr must be positive");
+  DeviceGuard g(h->cfg.device);
+  if ((s = ensure_train(h, batch)) != DDF_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((s = compute_grad(h, rays, t_target, hit_target, batch, out_loss, st)) != DDF_OK) return s;
+  ++h->adam_step;
+  const double t = static_cast<double>(h->adam_step);
+  const float bc1 = static_cast<float>(1.0 - std::pow(0.9, t));
+  const float bc2 = static_cast<float>(1.0 - std::pow(0.999, t));
+  {
+    ProfScope ps(h, kProfHead, st);
+    DDF_CK(ddf::launch_adam(h->d_blob, h->grad, h->adam_m, h->adam_v,
+                            static_cast<int64_t>(n_params(h)), lr, kB1, kB2, kEps, bc1, bc2, st));
+    if ((s = refresh_weights(h, st)) != DDF_OK) return s;
+  }
+  return DDF_OK;
+}
+
+ddf_status ddf_get_grad(ddf_handle h, float* host_grad, size_t n_floats) {
+  if (h == nullptr || host_grad == nullptr) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+  if (!h->grad_valid) return fail(DDF_ERR_INVALID_ARG, "no gradient computed yet");
+  if (n_floats != n_params(h)) return fail(DDF_ERR_INVALID_ARG, "wrong blob size");
+  DeviceGuard g(h->cfg.device);
+  DDF_CK(cudaDeviceSynchronize());
+  DDF_CK(cudaMemcpy(host_grad, h->grad, n_floats * sizeof(float), cudaMemcpyDeviceToHost));
+  return DDF_OK;
+}
+
+ddf_status ddf_reset_optimizer(ddf_handle h) {
+  if (h == nullptr) return fail(DDF_ERR_INVALID_ARG, "handle is NULL");
+  if (h->adam_m == nullptr) return DDF_OK;
+  DeviceGuard g(h->cfg.device);
+  const size_t np = n_params(h);
+  DDF_CK(cudaDeviceSynchronize());
+  DDF_CK(cudaMemset(h->adam_m, 0, np * sizeof(float)));
+  DDF_CK(cudaMemset(h->adam_v, 0, np * sizeof(float)));
+  h->adam_step = 0;
+  return DDF_OK;
+}
+
+ddf_status ddf_cast_scene(const float* spheres, int32_t n_spheres, const float* boxes,
+                          int32_t n_boxes, const float* const rays[6], int64_t n, float* out_t,
+                          uint8_t* out_hit, void* stream) {
+  if (n_spheres < 0 || n_boxes < 0 || n_spheres > 1024 || n_boxes > 1024)
+    return fail(DDF_ERR_INVALID_ARG, "0..1024 spheres and 0..1024 boxes");
+  if ((n_spheres > 0 && spheres == nullptr) || (n_boxes > 0 && boxes == nullptr))
+    return fail(DDF_ERR_INVALID_ARG, "primitive array is NULL");
+  ddf_status s = check_rays(rays, n);
+  if (s != DDF_OK) return s;
+  if (n > 0 && (out_t == nullptr || out_hit == nullptr))
+    return fail(DDF_ERR_INVALID_ARG, "output pointer is NULL");
+  ddf::RaySoA r;
+  for (int c = 0; c < 6; ++c) r.p[c] = n > 0 ? rays[c] : nullptr;
+  DDF_CK(ddf::launch_cast_scene(spheres, n_spheres, boxes, n_boxes, r, n, out_t, out_hit,
+                                static_cast<cudaStream_t>(stream)));
+  return DDF_OK;
+}
+
+}  // extern "C"

@@ -54,6 +54,11 @@ SIGNATURES = {
     "ddf_query_ao": (C.c_int, [_vp, _RAYS, _i64, _vp, _i64, _vp, _vp, _vp]),
     "ddf_set_graph_mode": (C.c_int, [_vp, _i32]),
     "ddf_calibrate_fp8": (C.c_int, [_vp, _RAYS, _i64, _vp, _vp, _vp]),
+    "ddf_compute_grad": (C.c_int, [_vp, _RAYS, _vp, _vp, _i64, _vp, _vp]),
+    "ddf_train_step": (C.c_int, [_vp, _RAYS, _vp, _vp, _i64, C.c_float, _vp, _vp]),
+    "ddf_get_grad": (C.c_int, [_vp, _vp, _sz]),
+    "ddf_reset_optimizer": (C.c_int, [_vp]),
+    "ddf_cast_scene": (C.c_int, [_vp, _i32, _vp, _i32, _RAYS, _i64, _vp, _vp, _vp]),
     "ddf_check_status": (C.c_int, [_vp, C.POINTER(C.c_uint32)]),
     "ddf_set_timeout_ns": (C.c_int, [_vp, _u64]),
     "ddf_set_chunk_rays": (C.c_int, [_vp, _i64]),
@@ -216,6 +221,34 @@ def ddf_calibrate_fp8(h, rays, n, stream=None):
     sc = np.zeros(max(nl, 1), np.float32)
     _call("ddf_calibrate_fp8", h, rp, int(n), amax.ctypes.data, sc.ctypes.data, _stream(stream))
     return amax[:nl], sc[:nl]
+
+
+def ddf_compute_grad(h, rays, t_target, hit_target, batch, out_loss=None, stream=None) -> None:
+    rp, keep = _rays(rays)
+    _call("ddf_compute_grad", h, rp, _ptr(t_target), _ptr(hit_target), int(batch), _ptr(out_loss),
+          _stream(stream))
+
+
+def ddf_train_step(h, rays, t_target, hit_target, batch, lr, out_loss=None, stream=None) -> None:
+    rp, keep = _rays(rays)
+    _call("ddf_train_step", h, rp, _ptr(t_target), _ptr(hit_target), int(batch), float(lr),
+          _ptr(out_loss), _stream(stream))
+
+
+def ddf_get_grad(h, n: int) -> np.ndarray:
+    out = np.empty(n, np.float32)
+    _call("ddf_get_grad", h, out.ctypes.data, n)
+    return out
+
+
+def ddf_reset_optimizer(h) -> None:
+    _call("ddf_reset_optimizer", h)
+
+
+def ddf_cast_scene(spheres, n_spheres, boxes, n_boxes, rays, n, out_t, out_hit, stream=None) -> None:
+    rp, keep = _rays(rays)
+    _call("ddf_cast_scene", _ptr(spheres), int(n_spheres), _ptr(boxes), int(n_boxes), rp, int(n),
+          _ptr(out_t), _ptr(out_hit), _stream(stream))
 
 
 _HIDDEN = {}

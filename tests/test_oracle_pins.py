@@ -424,3 +424,21 @@ def test_shadow_and_ao_hand_values():
     hard, soft = O.ambient_occlusion(hit, vis, [0, 2, 2, 6])
     assert np.allclose(hard, [0.5, 1.0, 0.25])
     assert np.allclose(soft, [0.5, 1.0, 1 - 2.3 / 4])
+
+
+def test_train_grad_reduces_to_pinned_gradient():
+    """With rounding off, the training-step gradient is the exact gradient that
+    central differences pin above; with bf16 rounding it stays close."""
+    shape = I.NetShape(2, 16, 3)
+    rng = np.random.default_rng(8)
+    blob = (rng.standard_normal(shape.n_params) * 0.5)
+    r = I.uniform_rays(64, seed=9)
+    tt = rng.uniform(0.2, 3.0, 64)
+    y = rng.integers(0, 2, 64)
+    L0, g0 = O.ddf_loss_grad(r.origins(), r.dirs(), blob, 2, 16, 3, tt, y)
+    L1, g1 = O.train_grad(r.origins(), r.dirs(), blob, 2, 16, 3, tt, y, precision="exact")
+    assert L1 == pytest.approx(L0, rel=1e-14)
+    assert np.allclose(g1, g0, rtol=1e-12, atol=1e-15)
+    L2, g2 = O.train_grad(r.origins(), r.dirs(), blob, 2, 16, 3, tt, y, precision="bf16")
+    assert abs(L2 - L0) < 2e-2 * abs(L0)
+    assert np.linalg.norm(g2 - g0) < 5e-2 * np.linalg.norm(g0)
