@@ -67,13 +67,21 @@ typedef enum {
  *                  and W <= 2048
  *   hidden_layers  H >= 1 ReLU layers (D_in -> W, then H-1 times W -> W)
  *   precision      a ddf_precision value
- *   device         CUDA device ordinal the handle lives on */
+ *   device         CUDA device ordinal the handle lives on
+ *   kind           DDF_KIND_RAY: the directed distance field of a ray (as
+ *                  above, 2 outputs); DDF_KIND_SDF: a signed distance field of
+ *                  a point p (the sphere-tracing baseline of Sec. 4.4): input
+ *                  [px,py,pz, per coordinate and band sin(pi 2^k p_c),
+ *                  cos(pi 2^k p_c)] (D_in = 3 + 6 L), one raw output; bf16 only */
+typedef enum { DDF_KIND_RAY = 0, DDF_KIND_SDF = 1 } ddf_kind;
+
 typedef struct {
   int32_t octaves;
   int32_t width;
   int32_t hidden_layers;
   int32_t precision;
   int32_t device;
+  int32_t kind;
 } ddf_config;
 
 /* Number of floats in the weight blob of cfg (0 if cfg is invalid).
@@ -228,6 +236,41 @@ ddf_status ddf_reset_optimizer(ddf_handle h);
 ddf_status ddf_cast_scene(const float* spheres, int32_t n_spheres, const float* boxes,
                           int32_t n_boxes, const float* const rays[6], int64_t n, float* out_t,
                           uint8_t* out_hit, void* stream);
+
+/* ---- SDF fields (kind DDF_KIND_SDF): the sphere-tracing baseline ----
+ * Blob layout as for ray fields but with a 1-row head (W weights, 1 bias);
+ * the output is the raw value s = z0. Ray-field entry points reject SDF
+ * handles and the other way round. */
+
+/* out_s[i] = SDF(p_i) for n points (points: 3 device float arrays). Async. */
+ddf_status ddf_sdf_eval(ddf_handle h, const float* const points[3], int64_t n, float* out_s,
+                        void* stream);
+
+/* Sphere tracing (Sec. 4.4): per ray t = 0, then up to max_steps times
+ * s = SDF(o + t d); s < eps: hit at t; else t += s, and the ray stops as a
+ * miss once t > t_max. Every step is one full network evaluation of the rays
+ * still active, compacted on the device (no host round trip). Writes out_t
+ * (device float[n]: t at the hit, else where the ray stopped), out_hit
+ * (device uint8[n]) and out_steps (device int32[n], nullable: evaluations
+ * used). n <= the chunk size (ddf_set_chunk_rays). Asynchronous. */
+ddf_status ddf_sphere_trace(ddf_handle h, const float* const rays[6], int64_t n, int32_t max_steps,
+                            float eps, float t_max, float* out_t, uint8_t* out_hit,
+                            int32_t* out_steps, void* stream);
+
+/* SDF regression (distils the baseline network): L = mean |s(p) - s*| over
+ * the batch (points: 3 device float arrays, s_target: device float[batch]);
+ * gradient into the handle (ddf_get_grad) or followed by one Adam step. Same
+ * batch rules and optimiser as ddf_compute_grad / ddf_train_step. */
+ddf_status ddf_sdf_compute_grad(ddf_handle h, const float* const points[3], const float* s_target,
+                                int64_t batch, float* out_loss, void* stream);
+ddf_status ddf_sdf_train_step(ddf_handle h, const float* const points[3], const float* s_target,
+                              int64_t batch, float lr, float* out_loss, void* stream);
+
+/* Closed-form signed distance to a union of spheres and boxes (same
+ * primitive arrays as ddf_cast_scene) at n points; no handle. Async. */
+ddf_status ddf_union_sdf(const float* spheres, int32_t n_spheres, const float* boxes,
+                         int32_t n_boxes, const float* const points[3], int64_t n, float* out_s,
+                         void* stream);
 
 /* Device status word of the handle: bit 0 = a pipeline wait timed out,
  * bit 1 = a scheduler wait timed out. Synchronises the device, stores the

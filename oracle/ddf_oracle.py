@@ -324,6 +324,38 @@ def train_grad(o, d, blob, octaves, width, hidden, t_target, hit_target, precisi
     return L, flat
 
 
+def sdf_train_grad(p, blob, octaves, width, hidden, s_target, precision="bf16"):
+    """SDF regression for the sphere-tracing baseline (Sec. 4.4 compares the
+    DDF with tracing an SDF network): L = mean |s(p) - s*| with s the raw
+    1-output network on the Fourier-encoded point. Roundings as in
+    train_grad; dL/ds = sign(s - s*) / B (sign(0) = 0). Returns (L, flat
+    gradient in the SDF blob layout)."""
+    rnd = round_bf16 if precision == "bf16" else (lambda a: np.asarray(a, F64))
+    d_in = 3 + 6 * octaves
+    dims = [(width, d_in)] + [(width, width)] * (hidden - 1) + [(1, width)]
+    layers = split_blob(blob, dims)
+    hid, (wo, bo) = layers[:-1], layers[-1]
+    x = rnd(encode_points(p, octaves))
+    acts = [x]
+    for w, b in hid:
+        x = rnd(np.maximum(x @ rnd(w).T + b, 0.0))
+        acts.append(x)
+    s = (x @ wo.T + bo)[:, 0]
+    B = s.shape[0]
+    diff = s - np.asarray(s_target, F64)
+    L = np.sum(np.abs(diff)) / B
+    ds = (np.sign(diff) / B)[:, None]
+    grads = [None] * len(layers)
+    grads[-1] = (ds.T @ acts[-1], ds.sum(axis=0))
+    dpre = rnd((ds @ wo) * (acts[-1] > 0))
+    for l in range(len(hid) - 1, -1, -1):
+        grads[l] = (dpre.T @ acts[l], dpre.sum(axis=0))
+        if l > 0:
+            dpre = rnd((dpre @ rnd(hid[l][0])) * (acts[l] > 0))
+    flat = np.concatenate([np.concatenate([g.reshape(-1), gb]) for g, gb in grads])
+    return L, flat
+
+
 def adam_step(w, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
     """One Adam update (Kingma & Ba), bias-corrected, no weight decay.
     step counts from 1. Returns (w, m, v)."""

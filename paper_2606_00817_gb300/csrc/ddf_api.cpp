@@ -106,13 +106,24 @@ bool valid_config(const ddf_config* c, std::string* why) {
   if (c->precision < DDF_FP32 || c->precision > DDF_FP8_E4M3)
     return *why = "unknown precision", false;
   if (c->device < 0) return *why = "device must be >= 0", false;
+  if (c->kind != DDF_KIND_RAY && c->kind != DDF_KIND_SDF) return *why = "unknown kind", false;
+  if (c->kind == DDF_KIND_SDF && c->precision != DDF_BF16)
+    return *why = "SDF fields run in bf16 only", false;
   return true;
 }
 
+size_t input_width(const ddf_config& c) {
+  return c.kind == DDF_KIND_SDF ? 3 + 6 * static_cast<size_t>(c.octaves)
+                                : 6 + 12 * static_cast<size_t>(c.octaves);
+}
+
+size_t head_rows(const ddf_config& c) { return c.kind == DDF_KIND_SDF ? 1 : 2; }
+
 size_t param_count(const ddf_config& c) {
-  const size_t d_in = 6 + 12 * static_cast<size_t>(c.octaves);
+  const size_t d_in = input_width(c);
   const size_t W = c.width;
-  return d_in * W + W + (c.hidden_layers - 1) * (W * W + W) + 2 * W + 2;
+  const size_t hr = head_rows(c);
+  return d_in * W + W + (c.hidden_layers - 1) * (W * W + W) + hr * W + hr;
 }
 
 cudaEvent_t prof_event(ddf_s* h) {
@@ -171,6 +182,7 @@ ddf::HeadOut shift_out(ddf::HeadOut o, int64_t off) {
   if (o.t != nullptr) o.t += off;
   if (o.vis != nullptr) o.vis += off;
   if (o.hit != nullptr) o.hit += off;
+  if (o.z0 != nullptr) o.z0 += off;
   if (o.occluded != nullptr) o.occluded += off;
   o.rays = shift_rays(o.rays, off);
   return o;
@@ -202,8 +214,12 @@ ddf_status forward_tc(ddf_s* h, ddf::RaySoA rays, int m, ddf::HeadOut out, cudaS
   const bool fp8 = h->cfg.precision == DDF_FP8_E4M3;
   {
     ProfScope ps(h, kProfEncode, st);
-    DDF_CK(ddf::launch_encode_bf16(rays, m, h->cfg.octaves, h->kp16,
-                                   static_cast<__nv_bfloat16*>(h->ws_enc), st));
+    if (h->cfg.kind == DDF_KIND_SDF)  // points in rays.p[0..2]
+      DDF_CK(ddf::launch_encode_points_bf16(rays.p[0], rays.p[1], rays.p[2], m, h->cfg.octaves,
+                                            h->kp16, static_cast<__nv_bfloat16*>(h->ws_enc), st));
+    else
+      DDF_CK(ddf::launch_encode_bf16(rays, m, h->cfg.octaves, h->kp16,
+                                     static_cast<__nv_bfloat16*>(h->ws_enc), st));
   }
   for (int l = 0; l < H; ++l) {
     const bool in_fp8 = fp8 && l > 0;
@@ -277,9 +293,13 @@ ddf_status check_rays(const float* const rays[6], int64_t n) {
   return DDF_OK;
 }
 
-ddf_status check_ready(ddf_s* h) {
+// Ready for a query of the given field kind (ray queries by default).
+ddf_status check_ready(ddf_s* h, int kind = DDF_KIND_RAY) {
   if (h == nullptr) return fail(DDF_ERR_INVALID_ARG, "handle is NULL");
   if (!h->loaded) return fail(DDF_ERR_BAD_WEIGHTS, "no weights loaded");
+  if (h->cfg.kind != kind)
+    return fail(DDF_ERR_INVALID_ARG, kind == DDF_KIND_RAY ? "not a ray (DDF) field"
+                                                          : "not an SDF field");
   if (h->cfg.precision == DDF_FP8_E4M3 && h->cfg.hidden_layers > 1 && !h->scales_set)
     return fail(DDF_ERR_INVALID_ARG, "FP8 needs activation scales (ddf_set_act_scales)");
   return DDF_OK;
@@ -412,11 +432,130 @@ ddf_status calibrate_chunk(ddf_s* h, ddf::RaySoA rays, int m, float* amax, cudaS
   return DDF_OK;
 }
 
+ddf_status ensure_plain_maps(ddf_s* h) {
+  const int W = h->cfg.width, H = h->cfg.hidden_layers;
+  if (static_cast<int>(h->tmBtr.size()) == H) return DDF_OK;
+  std::vector<CUtensorMap> maps(H);
+  for (int l = 0; l < H; ++l) {
+    const int kp = l == 0 ? h->kp16 : W;
+    if (h->wb[l] == nullptr) return fail(DDF_ERR_UNSUPPORTED, "no bf16 weights for this layer");
+    if (!make_tmap(&maps[l], h->wb[l], false, kp, W, static_cast<uint64_t>(kp) * 2, h->bn))
+      return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for a weight map");
+  }
+  h->tmBtr = maps;
+  return DDF_OK;
+}
+
+ddf_status ensure_trace_buffers(ddf_s* h, int64_t rows) {
+  if (rows <= h->trc_rows) return DDF_OK;
+  dev_free(h, h->trc_idx[0]);
+  dev_free(h, h->trc_idx[1]);
+  dev_free(h, h->trc_steps);
+  h->trc_idx[0] = h->trc_idx[1] = h->trc_steps = nullptr;
+  h->trc_rows = 0;
+  void* p;
+  ddf_status s;
+  for (int i = 0; i < 2; ++i) {
+    if ((s = dev_alloc(h, &p, rows * sizeof(int))) != DDF_OK) return s;
+    h->trc_idx[i] = static_cast<int*>(p);
+  }
+  if ((s = dev_alloc(h, &p, rows * sizeof(int))) != DDF_OK) return s;
+  h->trc_steps = static_cast<int*>(p);
+  if (h->trc_count == nullptr) {
+    if ((s = dev_alloc(h, &p, 2 * sizeof(int))) != DDF_OK) return s;
+    h->trc_count = static_cast<int*>(p);
+  }
+  h->trc_rows = rows;
+  return DDF_OK;
+}
+
 }  // namespace ddfi
 
 using namespace ddfi;
 
 extern "C" {
+
+ddf_status ddf_sdf_eval(ddf_handle h, const float* const points[3], int64_t n, float* out_s,
+                        void* stream) {
+  ddf_status s = check_ready(h, DDF_KIND_SDF);
+  if (s != DDF_OK) return s;
+  if (n < 0) return fail(DDF_ERR_INVALID_ARG, "n must be >= 0");
+  if (n == 0) return DDF_OK;
+  if (points == nullptr || points[0] == nullptr || points[1] == nullptr || points[2] == nullptr ||
+      out_s == nullptr)
+    return fail(DDF_ERR_INVALID_ARG, "a pointer is NULL");
+  DeviceGuard g(h->cfg.device);
+  const float* as_rays[6] = {points[0], points[1], points[2], points[0], points[1], points[2]};
+  ddf::HeadOut o{};
+  o.z0 = out_s;
+  return run_query(h, as_rays, n, o, static_cast<cudaStream_t>(stream));
+}
+
+ddf_status ddf_sphere_trace(ddf_handle h, const float* const rays[6], int64_t n, int32_t max_steps,
+                            float eps, float t_max, float* out_t, uint8_t* out_hit,
+                            int32_t* out_steps, void* stream) {
+  ddf_status s = check_ready(h, DDF_KIND_SDF);
+  if (s != DDF_OK) return s;
+  if ((s = check_rays(rays, n)) != DDF_OK) return s;
+  if (n == 0) return DDF_OK;
+  if (n > h->chunk) return fail(DDF_ERR_INVALID_ARG, "trace at most chunk_rays rays per call");
+  if (max_steps < 1 || !(eps > 0.f) || !(t_max > 0.f))
+    return fail(DDF_ERR_INVALID_ARG, "max_steps >= 1, eps > 0 and t_max > 0 required");
+  if (out_t == nullptr || out_hit == nullptr) return fail(DDF_ERR_INVALID_ARG, "output is NULL");
+  DeviceGuard g(h->cfg.device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int W = h->cfg.width, H = h->cfg.hidden_layers, cap = static_cast<int>(n);
+  if ((s = ensure_workspace(h, cap)) != DDF_OK) return s;
+  if ((s = ensure_trace_buffers(h, cap)) != DDF_OK) return s;
+  if ((s = ensure_plain_maps(h)) != DDF_OK) return s;
+  int* steps = out_steps != nullptr ? out_steps : h->trc_steps;
+  ddf::RaySoA r;
+  for (int c = 0; c < 6; ++c) r.p[c] = rays[c];
+  const ddf::TcTile tile{h->bn, 4};
+  const int64_t max_tiles = ((cap + 127) / 128) * static_cast<int64_t>(W / tile.bn);
+  const int grid = static_cast<int>(std::min<int64_t>(max_tiles, h->num_sms));
+  DDF_CK(ddf::launch_trace_init(cap, h->trc_idx[0], h->trc_count, out_t, steps, out_hit, st));
+  for (int it = 0; it < max_steps; ++it) {
+    int* cin = h->trc_count + (it & 1);
+    int* cout = h->trc_count + ((it + 1) & 1);
+    const int* iin = h->trc_idx[it & 1];
+    int* iout = h->trc_idx[(it + 1) & 1];
+    DDF_CK(cudaMemsetAsync(cout, 0, sizeof(int), st));
+    {
+      ProfScope ps(h, kProfEncode, st);
+      DDF_CK(ddf::launch_trace_encode(r, out_t, iin, cin, cap, h->cfg.octaves, h->kp16,
+                                      static_cast<__nv_bfloat16*>(h->ws_enc), st));
+    }
+    for (int l = 0; l < H; ++l) {
+      const bool last = l == H - 1;
+      const void* a_base = l == 0 ? h->ws_enc : h->ws_act[(l - 1) & 1];
+      const int K = l == 0 ? h->kp16 : W;
+      CUtensorMap tmA;
+      if (!make_tmap(&tmA, a_base, false, K, cap, static_cast<uint64_t>(K) * 2, 128))
+        return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for an activation map");
+      ddf::TcGemmParams p{};
+      p.M = cap;
+      p.m_dev = cin;
+      p.N = W;
+      p.K = K;
+      p.bias = h->bias[l];
+      p.out_scale = 1.0f;
+      p.out = last ? nullptr : h->ws_act[l & 1];
+      p.ldo = W;
+      p.head_w = h->head_w;
+      p.head_part = h->ws_part;
+      p.mode = last ? 1 : 0;
+      p.status = h->status_dev;
+      p.timeout_ns = h->timeout_ns;
+      ProfScope ps(h, l == 0 ? kProfFirst : kProfGemm, st);
+      DDF_CK(ddf::launch_tc_gemm(tile, false, false, tmA, h->tmBtr[l], p, grid, st));
+    }
+    ProfScope ps(h, kProfHead, st);
+    DDF_CK(ddf::launch_trace_update(h->ws_part, W / tile.bn, cap, cin, iin, h->head_b, eps, t_max,
+                                    max_steps, out_t, steps, out_hit, iout, cout, st));
+  }
+  return DDF_OK;
+}
 
 size_t ddf_param_count(const ddf_config* cfg) {
   std::string why;
@@ -450,7 +589,7 @@ ddf_status ddf_create(const ddf_config* cfg, ddf_handle* out) {
   }
   ddf_s* h = new ddf_s();
   h->cfg = *cfg;
-  h->d_in = 6 + 12 * cfg->octaves;
+  h->d_in = static_cast<int>(input_width(*cfg));
   h->kp32 = static_cast<int>(round_up(h->d_in, 8));
   h->kp16 = static_cast<int>(round_up(h->d_in, 8));
   h->bn = (cfg->width % 256 == 0) ? 256 : 128;
@@ -584,9 +723,14 @@ ddf_status ddf_load_weights(ddf_handle h, const float* host_blob, size_t n_float
       DDF_CK(ddf::launch_pack_bf16(w, W, K, W, h->wcal[l], st));
     }
   }
-  DDF_CK(cudaMemcpy(h->head_w, h->d_blob + off, 2 * W * sizeof(float), cudaMemcpyDeviceToDevice));
-  off += 2 * W;
-  DDF_CK(cudaMemcpy(h->head_b, h->d_blob + off, 2 * sizeof(float), cudaMemcpyDeviceToDevice));
+  // head rows: (t, vis) for a ray field; the SDF field has one row, and the
+  // second row of the device head stays zero
+  const int hr = static_cast<int>(head_rows(h->cfg));
+  DDF_CK(cudaMemset(h->head_w, 0, 2 * W * sizeof(float)));
+  DDF_CK(cudaMemset(h->head_b, 0, 2 * sizeof(float)));
+  DDF_CK(cudaMemcpy(h->head_w, h->d_blob + off, hr * W * sizeof(float), cudaMemcpyDeviceToDevice));
+  off += hr * W;
+  DDF_CK(cudaMemcpy(h->head_b, h->d_blob + off, hr * sizeof(float), cudaMemcpyDeviceToDevice));
   if (prec == DDF_FP8_E4M3 && h->scales_set) {
     for (int l = 1; l < H; ++l)
       DDF_CK(ddf::launch_scale_vec(h->wscale[l], h->act_scales[l - 1], W, h->colscale[l], st));

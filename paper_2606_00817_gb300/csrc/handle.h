@@ -99,8 +99,14 @@ struct ddf_s {
   int64_t adam_step = 0;
   bool grad_valid = false;
   std::vector<__nv_bfloat16*> wt;         // layers 2..H: bf16 W^T [K x W] for input gradients
-  std::vector<CUtensorMap> tmBtr;         // forward weight maps for the training tile
+  std::vector<CUtensorMap> tmBtr;         // weight maps for the plain 1-CTA tile {bn, 4}
   std::vector<CUtensorMap> tmWT;          // maps of wt
+
+  // sphere tracing (SDF fields)
+  int* trc_idx[2] = {nullptr, nullptr};   // active-ray lists
+  int* trc_count = nullptr;               // [2] active counts
+  int* trc_steps = nullptr;               // per-ray evaluations
+  int64_t trc_rows = 0;
 };
 
 namespace ddfi {
@@ -158,6 +164,8 @@ ddf_status check_rays(const float* const rays[6], int64_t n);
 ddf_status ensure_workspace(ddf_s* h, int64_t rows);
 void clear_graphs(ddf_s* h);
 ddf::RaySoA shift_rays(ddf::RaySoA r, int64_t off);
+// Builds h->tmBtr (bf16 weight maps for the plain 1-CTA tile) once.
+ddf_status ensure_plain_maps(ddf_s* h);
 int64_t round_up(int64_t x, int64_t m);
 
 }  // namespace ddfi

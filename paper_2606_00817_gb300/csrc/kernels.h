@@ -40,7 +40,38 @@ struct TcGemmParams {
   int k_splits;
   size_t split_stride;     // elements between split outputs
   float* out_f32;
+  // 1-CTA kernel, nullable: device int holding the number of rows to compute
+  // (at most M; M remains the row stride of the head partials)
+  const int* m_dev;
 };
+
+// ---- sphere tracing of an SDF field (trace.cu) ----
+// 3D Fourier encoding of points p [M x ld] bf16: p, then per coordinate and
+// band sin(pi 2^k p_c), cos(pi 2^k p_c); zero padding to ld.
+cudaError_t launch_encode_points_bf16(const float* px, const float* py, const float* pz, int64_t M,
+                                      int L, int ld, __nv_bfloat16* out, cudaStream_t s);
+// Same for the active rays of a trace: row j encodes o_i + t_i d_i with
+// i = idx[j], for j < *count (rows up to cap written, extra rows untouched).
+cudaError_t launch_trace_encode(RaySoA rays, const float* t, const int* idx, const int* count,
+                                int cap, int L, int ld, __nv_bfloat16* out, cudaStream_t s);
+// idx = 0..n-1, count = n, t = 0, steps = 0, hit = 0
+cudaError_t launch_trace_init(int n, int* idx, int* count, float* t, int* steps, uint8_t* hit,
+                              cudaStream_t s);
+// One sphere-tracing step for the active rays: s = sum of nparts head
+// partials [nparts x cap] + head_b[0]; steps += 1; s < eps -> hit; else
+// t += s and the ray stays active (appended to idx_out / count_out) unless
+// t > t_max or it has used max_steps evaluations.
+cudaError_t launch_trace_update(const float2* part, int nparts, int cap, const int* count_in,
+                                const int* idx_in, const float* head_b, float eps, float t_max,
+                                int max_steps, float* t, int* steps, uint8_t* hit, int* idx_out,
+                                int* count_out, cudaStream_t s);
+// Closed-form signed distance to a union of spheres and boxes at n points.
+cudaError_t launch_union_sdf(const float* spheres, int ns, const float* boxes, int nb,
+                             const float* px, const float* py, const float* pz, int64_t n,
+                             float* out, cudaStream_t s);
+// SDF regression loss: L = mean |z0 - s*|, dz = (sign(z0 - s*) / B, 0).
+cudaError_t launch_sdf_loss(const float2* z, const float* s_tgt, int64_t B, float2* dz,
+                            float* part, float* loss_out, cudaStream_t s);
 
 // Tile configuration of the tensor-core layer: N tile (128 or 256) and the
 // number of epilogue warps (4, or 8 = two warps per TMEM lane quarter, each
@@ -83,6 +114,7 @@ struct HeadOut {
   float* t;           // nullable
   float* vis;         // nullable
   uint8_t* hit;       // nullable: 1 where z1 > 0
+  float* z0;          // nullable: raw z0 (the value of an SDF field)
   uint8_t* occluded;  // nullptr unless a shadow query
   float light[3];
   RaySoA rays;        // origins for the shadow distance

@@ -204,6 +204,7 @@ __device__ __forceinline__ void write_heads(const HeadOut& o, int64_t i, float z
   if (o.t != nullptr) o.t[i] = t;
   if (o.vis != nullptr) o.vis[i] = sigmoid_f(z1);
   if (o.hit != nullptr) o.hit[i] = z1 > 0.f ? 1 : 0;
+  if (o.z0 != nullptr) o.z0[i] = z0;
   if (o.occluded != nullptr) {
     const float dx = o.light[0] - o.rays.p[0][i];
     const float dy = o.light[1] - o.rays.p[1][i];

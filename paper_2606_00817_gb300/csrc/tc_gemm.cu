@@ -104,7 +104,11 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  const int num_m = (p.M + S::BM - 1) / S::BM;
+  // rows this launch computes: p.M, or fewer when a device-side count
+  // (written by an earlier kernel of the stream) is given; p.M stays the row
+  // stride of the head partials
+  const int m_rows = p.m_dev != nullptr ? min(*p.m_dev, p.M) : p.M;
+  const int num_m = (m_rows + S::BM - 1) / S::BM;
   const int num_n = p.N / BN;
   const int num_kb = (p.K + S::BK - 1) / S::BK;
   // split-K (mode 3): tile = (split, m block, n block); split s covers the
@@ -211,7 +215,7 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
       int split, m_blk, n_blk;
       decode(tile, split, m_blk, n_blk);
       const int row = m_blk * S::BM + r_local;
-      const bool row_ok = row < p.M;
+      const bool row_ok = row < m_rows;
       const int n0 = n_blk * BN;
       const uint32_t tbase = tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
                              static_cast<uint32_t>(b * BN);

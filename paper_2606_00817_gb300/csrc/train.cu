@@ -110,6 +110,29 @@ __global__ void loss_dz_kernel(const float2* __restrict__ z, const float* __rest
   }
 }
 
+// SDF regression: per point |z0 - s*| / B and dz = (sign(z0 - s*) / B, 0).
+__global__ void sdf_loss_kernel(const float2* __restrict__ z, const float* __restrict__ s_tgt,
+                                int64_t B, float2* __restrict__ dz, float* __restrict__ part) {
+  __shared__ float red[32];
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  float l = 0.f;
+  if (i < B) {
+    const float diff = z[i].x - s_tgt[i];
+    l = fabsf(diff) / static_cast<float>(B);
+    const float sg = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
+    dz[i] = make_float2(sg / static_cast<float>(B), 0.f);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < (blockDim.x >> 5); ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+
 __global__ void sum_partials_kernel(const float* __restrict__ part, int n, float* __restrict__ out) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     float t = 0.f;
@@ -292,6 +315,14 @@ cudaError_t launch_loss(const float2* z, const float* t_tgt, const uint8_t* y, i
   count_hits_kernel<<<256, 256, 0, s>>>(y, B, nhit);
   const int blocks = static_cast<int>((B + 255) / 256);
   loss_dz_kernel<<<blocks, 256, 0, s>>>(z, t_tgt, y, B, nhit, clamp, lam, dz, part);
+  if (loss_out != nullptr) sum_partials_kernel<<<1, 32, 0, s>>>(part, blocks, loss_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sdf_loss(const float2* z, const float* s_tgt, int64_t B, float2* dz,
+                            float* part, float* loss_out, cudaStream_t s) {
+  const int blocks = static_cast<int>((B + 255) / 256);
+  sdf_loss_kernel<<<blocks, 256, 0, s>>>(z, s_tgt, B, dz, part);
   if (loss_out != nullptr) sum_partials_kernel<<<1, 32, 0, s>>>(part, blocks, loss_out);
   return cudaGetLastError();
 }

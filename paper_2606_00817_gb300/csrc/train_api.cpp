@@ -26,6 +26,9 @@ constexpr float kClamp = 4.0f;  // L1 clamp ("box scale")
 constexpr float kLambda = 0.3f; // cross-entropy weight
 constexpr float kB1 = 0.9f, kB2 = 0.999f, kEps = 1e-8f;
 
+// (t, vis) head rows of a ray field; one row (the distance) for an SDF field
+size_t head_rows(const ddf_s* h) { return h->cfg.kind == DDF_KIND_SDF ? 1 : 2; }
+
 struct BlobOffsets {
   std::vector<size_t> w, b;
   size_t wo = 0, bo = 0;
@@ -43,11 +46,11 @@ BlobOffsets blob_offsets(const ddf_s* h) {
     off += W;
   }
   o.wo = off;
-  o.bo = off + 2 * W;
+  o.bo = off + head_rows(h) * W;
   return o;
 }
 
-size_t n_params(const ddf_s* h) { return blob_offsets(h).bo + 2; }
+size_t n_params(const ddf_s* h) { return blob_offsets(h).bo + head_rows(h); }
 
 ddf_status train_alloc(ddf_s* h, void** p, size_t bytes) { return dev_alloc(h, p, bytes); }
 
@@ -63,9 +66,10 @@ ddf_status refresh_weights(ddf_s* h, cudaStream_t st) {
                            cudaMemcpyDeviceToDevice, st));
     if (l > 0) DDF_CK(ddf::launch_pack_bf16_t(h->d_blob + o.w[l], W, W, h->wt[l], st));
   }
-  DDF_CK(cudaMemcpyAsync(h->head_w, h->d_blob + o.wo, 2 * W * sizeof(float),
+  const size_t hr = head_rows(h);
+  DDF_CK(cudaMemcpyAsync(h->head_w, h->d_blob + o.wo, hr * W * sizeof(float),
                          cudaMemcpyDeviceToDevice, st));
-  DDF_CK(cudaMemcpyAsync(h->head_b, h->d_blob + o.bo, 2 * sizeof(float), cudaMemcpyDeviceToDevice,
+  DDF_CK(cudaMemcpyAsync(h->head_b, h->d_blob + o.bo, hr * sizeof(float), cudaMemcpyDeviceToDevice,
                          st));
   return DDF_OK;
 }
@@ -86,13 +90,9 @@ ddf_status ensure_train(ddf_s* h, int64_t B) {
     DDF_CK(cudaMemset(h->adam_v, 0, np * sizeof(float)));
     h->adam_step = 0;
     h->wt.assign(H, nullptr);
-    h->tmBtr.assign(H, CUtensorMap{});
     h->tmWT.assign(H, CUtensorMap{});
-    for (int l = 0; l < H; ++l) {
-      const int kp = l == 0 ? h->kp16 : W;
-      if (!make_tmap(&h->tmBtr[l], h->wb[l], false, kp, W, static_cast<uint64_t>(kp) * 2, h->bn))
-        return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for a weight map");
-      if (l == 0) continue;
+    if ((s = ensure_plain_maps(h)) != DDF_OK) return s;
+    for (int l = 1; l < H; ++l) {
       if ((s = train_alloc(h, &p, static_cast<size_t>(W) * W * 2)) != DDF_OK) return s;
       h->wt[l] = static_cast<__nv_bfloat16*>(p);
       if (!make_tmap(&h->tmWT[l], h->wt[l], false, W, W, static_cast<uint64_t>(W) * 2, h->bn))
@@ -159,8 +159,10 @@ ddf_status tc_gemm(ddf_s* h, const void* A, int M, int K, const CUtensorMap& tmB
 }
 
 ddf_status check_train_args(ddf_s* h, const float* const rays[6], const float* t_target,
-                            const uint8_t* hit_target, int64_t batch) {
+                            const uint8_t* hit_target, int64_t batch, int kind = DDF_KIND_RAY) {
   if (h == nullptr) return fail(DDF_ERR_INVALID_ARG, "handle is NULL");
+  if (h->cfg.kind != kind)
+    return fail(DDF_ERR_INVALID_ARG, kind == DDF_KIND_RAY ? "not a ray (DDF) field" : "not an SDF field");
   if (!h->loaded) return fail(DDF_ERR_BAD_WEIGHTS, "no weights loaded");
   if (h->cfg.precision != DDF_BF16)
     return fail(DDF_ERR_UNSUPPORTED, "training runs on bf16 handles");
@@ -168,13 +170,18 @@ ddf_status check_train_args(ddf_s* h, const float* const rays[6], const float* t
     return fail(DDF_ERR_INVALID_ARG, "batch must be a positive multiple of 8 below 2^31");
   ddf_status s = check_rays(rays, batch);
   if (s != DDF_OK) return s;
-  if (t_target == nullptr || hit_target == nullptr)
+  if (t_target == nullptr || (kind == DDF_KIND_RAY && hit_target == nullptr))
     return fail(DDF_ERR_INVALID_ARG, "targets are NULL");
   return DDF_OK;
 }
 
+// rays: 6 SoA arrays (ray field) or 3 point arrays (SDF field, in rays[0..2]);
+// t_tgt: first-hit distances (ray field) or signed distances (SDF field);
+// y: hit flags (ray field only).
 ddf_status compute_grad(ddf_s* h, const float* const rays[6], const float* t_tgt,
                         const uint8_t* y, int64_t B64, float* loss_out, cudaStream_t st) {
+  const bool sdf = h->cfg.kind == DDF_KIND_SDF;
+  const int hr = static_cast<int>(head_rows(h));
   const int W = h->cfg.width, H = h->cfg.hidden_layers;
   const int B = static_cast<int>(B64);
   const BlobOffsets o = blob_offsets(h);
@@ -185,7 +192,11 @@ ddf_status compute_grad(ddf_s* h, const float* const rays[6], const float* t_tgt
   // ---- forward, keeping every activation
   {
     ProfScope ps(h, kProfEncode, st);
-    DDF_CK(ddf::launch_encode_bf16(r, B, h->cfg.octaves, h->kp16, bf(h->tr_enc), st));
+    if (sdf)
+      DDF_CK(ddf::launch_encode_points_bf16(r.p[0], r.p[1], r.p[2], B, h->cfg.octaves, h->kp16,
+                                            bf(h->tr_enc), st));
+    else
+      DDF_CK(ddf::launch_encode_bf16(r, B, h->cfg.octaves, h->kp16, bf(h->tr_enc), st));
   }
   for (int l = 0; l < H; ++l) {
     ddf::TcGemmParams p{};
@@ -201,15 +212,18 @@ ddf_status compute_grad(ddf_s* h, const float* const rays[6], const float* t_tgt
     if (s != DDF_OK) return s;
   }
   DDF_CK(ddf::launch_head_train(bf(h->tr_h[H - 1]), B, W, h->head_w, h->head_b, h->tr_z, st));
-  DDF_CK(ddf::launch_loss(h->tr_z, t_tgt, y, B, h->tr_nhit, kClamp, kLambda, h->tr_dz, h->tr_lpart,
-                          loss_out, st));
+  if (sdf)
+    DDF_CK(ddf::launch_sdf_loss(h->tr_z, t_tgt, B, h->tr_dz, h->tr_lpart, loss_out, st));
+  else
+    DDF_CK(ddf::launch_loss(h->tr_z, t_tgt, y, B, h->tr_nhit, kClamp, kLambda, h->tr_dz,
+                            h->tr_lpart, loss_out, st));
 
   // ---- head: dW_o = dz^T h_H, db_o = sum dz, dpre_H = (dz W_o) where h_H > 0
   DDF_CK(ddf::launch_head_grad(h->tr_dz, bf(h->tr_h[H - 1]), B, W, kColSplits, h->tr_cpart, st));
-  DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart, kColSplits, 2, W, 2 * W, W, h->grad + o.wo, W, st));
+  DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart, kColSplits, hr, W, 2 * W, W, h->grad + o.wo, W, st));
   DDF_CK(ddf::launch_colsum_f32(reinterpret_cast<const float*>(h->tr_dz), B, 2, 2, kColSplits,
                                 h->tr_cpart, st));
-  DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart, kColSplits, 1, 2, 2, 2, h->grad + o.bo, 2, st));
+  DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart, kColSplits, 1, 2, 2, hr, h->grad + o.bo, hr, st));
   DDF_CK(ddf::launch_head_backward(h->tr_dz, bf(h->tr_h[H - 1]), B, W, h->head_w,
                                    bf(h->tr_dpre[0]), st));
 
@@ -266,6 +280,10 @@ ddf_status compute_grad(ddf_s* h, const float* const rays[6], const float* t_tgt
   return DDF_OK;
 }
 
+ddf_status train_step(ddf_s* h, const float* const rays[6], const float* t_target,
+                      const uint8_t* hit_target, int64_t batch, float lr, float* out_loss,
+                      cudaStream_t st);
+
 }  // namespace
 
 extern "C" {
@@ -286,10 +304,60 @@ ddf_status ddf_train_step(ddf_handle h, const float* const rays[6], const float*
                           void* stream) {
   ddf_status s = check_train_args(h, rays, t_target, hit_target, batch);
   if (s != DDF_OK) return s;
-  if (!(lr > 0.f) || !std::isfinite(lr)) return fail(DDF_ERR_INVALID_ARG, "lr must be positive");
+  return train_step(h, rays, t_target, hit_target, batch, lr, out_loss,
+                    static_cast<cudaStream_t>(stream));
+}
+
+ddf_status ddf_sdf_compute_grad(ddf_handle h, const float* const points[3], const float* s_target,
+                                int64_t batch, float* out_loss, void* stream) {
+  const float* p6[6] = {points ? points[0] : nullptr, points ? points[1] : nullptr,
+                        points ? points[2] : nullptr, points ? points[0] : nullptr,
+                        points ? points[1] : nullptr, points ? points[2] : nullptr};
+  ddf_status s = check_train_args(h, p6, s_target, nullptr, batch, DDF_KIND_SDF);
+  if (s != DDF_OK) return s;
   DeviceGuard g(h->cfg.device);
   if ((s = ensure_train(h, batch)) != DDF_OK) return s;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return compute_grad(h, p6, s_target, nullptr, batch, out_loss, static_cast<cudaStream_t>(stream));
+}
+
+ddf_status ddf_sdf_train_step(ddf_handle h, const float* const points[3], const float* s_target,
+                              int64_t batch, float lr, float* out_loss, void* stream) {
+  const float* p6[6] = {points ? points[0] : nullptr, points ? points[1] : nullptr,
+                        points ? points[2] : nullptr, points ? points[0] : nullptr,
+                        points ? points[1] : nullptr, points ? points[2] : nullptr};
+  ddf_status s = check_train_args(h, p6, s_target, nullptr, batch, DDF_KIND_SDF);
+  if (s != DDF_OK) return s;
+  return train_step(h, p6, s_target, nullptr, batch, lr, out_loss, static_cast<cudaStream_t>(stream));
+}
+
+ddf_status ddf_union_sdf(const float* spheres, int32_t n_spheres, const float* boxes,
+                         int32_t n_boxes, const float* const points[3], int64_t n, float* out_s,
+                         void* stream) {
+  if (n_spheres < 0 || n_boxes < 0) return fail(DDF_ERR_INVALID_ARG, "negative primitive count");
+  if ((n_spheres > 0 && spheres == nullptr) || (n_boxes > 0 && boxes == nullptr))
+    return fail(DDF_ERR_INVALID_ARG, "primitive array is NULL");
+  if (n < 0) return fail(DDF_ERR_INVALID_ARG, "n must be >= 0");
+  if (n > 0 && (points == nullptr || points[0] == nullptr || points[1] == nullptr ||
+                points[2] == nullptr || out_s == nullptr))
+    return fail(DDF_ERR_INVALID_ARG, "a pointer is NULL");
+  if (n == 0) return DDF_OK;
+  DDF_CK(ddf::launch_union_sdf(spheres, n_spheres, boxes, n_boxes, points[0], points[1], points[2],
+                               n, out_s, static_cast<cudaStream_t>(stream)));
+  return DDF_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Gradient, then Adam on the FP32 master weights and a refresh of the bf16 copies.
+ddf_status train_step(ddf_s* h, const float* const rays[6], const float* t_target,
+                      const uint8_t* hit_target, int64_t batch, float lr, float* out_loss,
+                      cudaStream_t st) {
+  if (!(lr > 0.f) || !std::isfinite(lr)) return fail(DDF_ERR_INVALID_ARG, "lr must be positive");
+  DeviceGuard g(h->cfg.device);
+  ddf_status s;
+  if ((s = ensure_train(h, batch)) != DDF_OK) return s;
   if ((s = compute_grad(h, rays, t_target, hit_target, batch, out_loss, st)) != DDF_OK) return s;
   ++h->adam_step;
   const double t = static_cast<double>(h->adam_step);
@@ -303,6 +371,10 @@ ddf_status ddf_train_step(ddf_handle h, const float* const rays[6], const float*
   }
   return DDF_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 ddf_status ddf_get_grad(ddf_handle h, float* host_grad, size_t n_floats) {
   if (h == nullptr || host_grad == nullptr) return fail(DDF_ERR_INVALID_ARG, "NULL argument");

@@ -33,9 +33,13 @@ class Tile(C.Structure):
                 ("staged", C.c_int32)]
 
 
+DDF_KIND_RAY, DDF_KIND_SDF = 0, 1
+KINDS = {"ray": DDF_KIND_RAY, "sdf": DDF_KIND_SDF}
+
+
 class Config(C.Structure):
     _fields_ = [("octaves", C.c_int32), ("width", C.c_int32), ("hidden_layers", C.c_int32),
-                ("precision", C.c_int32), ("device", C.c_int32)]
+                ("precision", C.c_int32), ("device", C.c_int32), ("kind", C.c_int32)]
 
 
 SIGNATURES = {
@@ -59,6 +63,12 @@ SIGNATURES = {
     "ddf_get_grad": (C.c_int, [_vp, _vp, _sz]),
     "ddf_reset_optimizer": (C.c_int, [_vp]),
     "ddf_cast_scene": (C.c_int, [_vp, _i32, _vp, _i32, _RAYS, _i64, _vp, _vp, _vp]),
+    "ddf_sdf_eval": (C.c_int, [_vp, _RAYS, _i64, _vp, _vp]),
+    "ddf_sphere_trace": (C.c_int, [_vp, _RAYS, _i64, _i32, C.c_float, C.c_float, _vp, _vp, _vp,
+                                   _vp]),
+    "ddf_sdf_compute_grad": (C.c_int, [_vp, _RAYS, _vp, _i64, _vp, _vp]),
+    "ddf_sdf_train_step": (C.c_int, [_vp, _RAYS, _vp, _i64, C.c_float, _vp, _vp]),
+    "ddf_union_sdf": (C.c_int, [_vp, _i32, _vp, _i32, _RAYS, _i64, _vp, _vp]),
     "ddf_check_status": (C.c_int, [_vp, C.POINTER(C.c_uint32)]),
     "ddf_set_timeout_ns": (C.c_int, [_vp, _u64]),
     "ddf_set_chunk_rays": (C.c_int, [_vp, _i64]),
@@ -124,6 +134,13 @@ def _rays(rays):
     return C.cast(arr, _RAYS), arr
 
 
+def _points(points):
+    if len(points) != 3:
+        raise ValueError("points must hold 3 arrays (x, y, z)")
+    arr = (C.c_void_p * 3)(*[_ptr(p) for p in points])
+    return C.cast(arr, _RAYS), arr
+
+
 def _stream(s):
     if s is None:
         return None
@@ -132,9 +149,10 @@ def _stream(s):
     return s.cuda_stream
 
 
-def make_config(octaves, width, hidden_layers, precision="bf16", device=0) -> Config:
+def make_config(octaves, width, hidden_layers, precision="bf16", device=0, kind="ray") -> Config:
     p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    return Config(int(octaves), int(width), int(hidden_layers), p, int(device))
+    k = KINDS[kind] if isinstance(kind, str) else int(kind)
+    return Config(int(octaves), int(width), int(hidden_layers), p, int(device), k)
 
 
 # ----------------------------------------------------------- 1:1 entry points
@@ -251,6 +269,35 @@ def ddf_cast_scene(spheres, n_spheres, boxes, n_boxes, rays, n, out_t, out_hit, 
           _ptr(out_t), _ptr(out_hit), _stream(stream))
 
 
+def ddf_sdf_eval(h, points, n, out_s, stream=None) -> None:
+    pp, keep = _points(points)
+    _call("ddf_sdf_eval", h, pp, int(n), _ptr(out_s), _stream(stream))
+
+
+def ddf_sphere_trace(h, rays, n, max_steps, eps, t_max, out_t, out_hit, out_steps=None,
+                     stream=None) -> None:
+    rp, keep = _rays(rays)
+    _call("ddf_sphere_trace", h, rp, int(n), int(max_steps), float(eps), float(t_max), _ptr(out_t),
+          _ptr(out_hit), _ptr(out_steps), _stream(stream))
+
+
+def ddf_sdf_compute_grad(h, points, s_target, batch, out_loss=None, stream=None) -> None:
+    pp, keep = _points(points)
+    _call("ddf_sdf_compute_grad", h, pp, _ptr(s_target), int(batch), _ptr(out_loss), _stream(stream))
+
+
+def ddf_sdf_train_step(h, points, s_target, batch, lr, out_loss=None, stream=None) -> None:
+    pp, keep = _points(points)
+    _call("ddf_sdf_train_step", h, pp, _ptr(s_target), int(batch), float(lr), _ptr(out_loss),
+          _stream(stream))
+
+
+def ddf_union_sdf(spheres, n_spheres, boxes, n_boxes, points, n, out_s, stream=None) -> None:
+    pp, keep = _points(points)
+    _call("ddf_union_sdf", _ptr(spheres), int(n_spheres), _ptr(boxes), int(n_boxes), pp, int(n),
+          _ptr(out_s), _stream(stream))
+
+
 _HIDDEN = {}
 
 
@@ -315,8 +362,8 @@ def ddf_profile_read(h):
 class DDF:
     """Owns one library handle; queries take and return torch CUDA tensors."""
 
-    def __init__(self, octaves, width, hidden_layers, precision="bf16", device=0):
-        self.cfg = make_config(octaves, width, hidden_layers, precision, device)
+    def __init__(self, octaves, width, hidden_layers, precision="bf16", device=0, kind="ray"):
+        self.cfg = make_config(octaves, width, hidden_layers, precision, device, kind)
         self.device = device
         self.h = ddf_create(self.cfg)
         self.n_params = ddf_param_count(self.cfg)

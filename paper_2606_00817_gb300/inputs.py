@@ -158,6 +158,33 @@ def xavier_blob(shape: NetShape, seed: int = 0) -> np.ndarray:
     return np.ascontiguousarray(np.concatenate(parts).astype(np.float32))
 
 
+def sdf_layer_dims(octaves: int, width: int, hidden: int):
+    """(fan_out, fan_in) of the SDF baseline network: Fourier-encoded point
+    (3 + 6 L inputs), hidden ReLU layers, a 1-output head."""
+    d_in = 3 + 6 * octaves
+    return [(width, d_in)] + [(width, width)] * (hidden - 1) + [(1, width)]
+
+
+def xavier_blob_dims(dims, seed: int = 0) -> np.ndarray:
+    """Float32 blob for arbitrary (fan_out, fan_in) layers, initialised as
+    xavier_blob does."""
+    parts = []
+    off = 0
+    for fo, fi in dims:
+        a = np.sqrt(6.0 / (fi + fo))
+        parts.append(uniform(seed, S_WEIGHTS, fo * fi, -a, a, offset=off))
+        off += fo * fi
+        bb = 1.0 / np.sqrt(fi)
+        parts.append(uniform(seed, S_WEIGHTS, fo, -bb, bb, offset=off))
+        off += fo
+    return np.ascontiguousarray(np.concatenate(parts).astype(np.float32))
+
+
+def uniform_points(n: int, lo: float = -1.2, hi: float = 1.2, seed: int = 0) -> np.ndarray:
+    """n points uniform in the cube [lo, hi]^3, float32 [n, 3]."""
+    return uniform(seed, S_TARGET, 3 * n, lo, hi).reshape(n, 3).astype(np.float32)
+
+
 def split_blob(shape: NetShape, blob: np.ndarray):
     """[(W[out,in], b[out]), ...] views of a weight blob, head last."""
     out = []

@@ -442,3 +442,25 @@ def test_train_grad_reduces_to_pinned_gradient():
     L2, g2 = O.train_grad(r.origins(), r.dirs(), blob, 2, 16, 3, tt, y, precision="bf16")
     assert abs(L2 - L0) < 2e-2 * abs(L0)
     assert np.linalg.norm(g2 - g0) < 5e-2 * np.linalg.norm(g0)
+
+
+def test_sdf_grad_matches_central_differences():
+    L, W, H = 1, 6, 2
+    n = (3 + 6 * L) * W + W + (H - 1) * (W * W + W) + W + 1
+    rng = np.random.default_rng(10)
+    blob = rng.standard_normal(n) * 0.6
+    p = rng.uniform(-1, 1, (24, 3))
+    s_t = rng.uniform(-0.5, 0.5, 24)
+    L0, g = O.sdf_train_grad(p, blob, L, W, H, s_t, precision="exact")
+    h = 1e-6
+    fd = np.empty(n)
+    for i in range(n):
+        bp = blob.copy(); bp[i] += h
+        bm = blob.copy(); bm[i] -= h
+        fd[i] = (O.sdf_train_grad(p, bp, L, W, H, s_t, "exact")[0]
+                 - O.sdf_train_grad(p, bm, L, W, H, s_t, "exact")[0]) / (2 * h)
+    err = np.abs(fd - g) / np.maximum(1e-6, np.abs(g))
+    assert np.median(err) < 1e-6 and np.mean(err < 1e-4) > 0.97
+    # the loss is the mean absolute error of the plain network
+    s = O.sdf_mlp(p, blob, L, W, H)
+    assert L0 == pytest.approx(np.mean(np.abs(s - s_t)), rel=1e-14)
