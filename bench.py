@@ -11,6 +11,18 @@ evaluation of every ray plus the shadow decision (Sec. 3.3).
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun every rank evaluates its own 4,194,304 rays (weak scaling, no
 collective on the data path); rank 0 prints one JSON line.
+
+The line's "workloads" object adds, on rank 0 and timed the same way (CUDA
+events on the launching stream, 3 timed repetitions after warm-up):
+  ao_fp8_graph   1024 x 1024 shading points with 4..64 cosine-weighted rays
+                 each (about 35.6M rays), e4m3 field with scales from the
+                 library's calibration pass, one graph replay per step
+  distillation   batch 65,536 rays, targets from the GPU analytic caster on
+                 32 spheres + 32 boxes, loss + backward + Adam, bf16
+  sphere_trace   an SDF network 63 -> 1280x8 -> 1 distilled for a few hundred
+                 steps from the 64-sphere scene's union SDF, traced on
+                 1,048,576 one-bounce rays (<= 128 steps, eps 1e-3), against
+                 one DDF pass over the same rays
 """
 from __future__ import annotations
 
@@ -48,6 +60,8 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32 comparison run")
     ap.add_argument("--oracle-seconds", type=float, default=12.0)
     ap.add_argument("--tile", default="auto", help="auto (autotune) or BNxEPI[pair][staged], e.g. 256x8, 256x4pairstaged")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the AO / distillation / sphere-tracing measurements")
     return ap.parse_args()
 
 
@@ -172,6 +186,150 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------- GPU leg
+
+def _time_ms(torch, stream, fn, reps=3, warm=1, flush=None):
+    """Mean device time of fn() over reps runs (CUDA events on `stream`),
+    after `warm` untimed runs; `flush` is written before each timed run."""
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / reps
+
+
+def _scene_buffers(torch, dev, scene):
+    sph = np.concatenate([scene.centers, scene.radii[:, None]], 1).astype(np.float32).ravel()
+    box = np.concatenate([scene.box_lo, scene.box_hi], 1).astype(np.float32).ravel()
+    return (torch.from_numpy(sph).to(dev), len(scene.radii),
+            torch.from_numpy(box).to(dev), len(scene.box_lo))
+
+
+def workloads(torch, ddf, dev, local, stream, flush, blob):
+    """The ragged AO, distillation and sphere-tracing measurements."""
+    out = {}
+    scene = I.random_scene(64, 0, seed=0)
+
+    # ragged AO, e4m3, graph replay
+    P = 1024 * 1024
+    rays, offsets = I.ao_rays(scene, P, seed=0)
+    d_rays = [torch.from_numpy(a).to(dev) for a in rays.soa()]
+    d_off = torch.from_numpy(offsets).to(dev)
+    del rays
+    hard = torch.empty(P, device=dev)
+    soft = torch.empty(P, device=dev)
+    f8 = ddf.DDF(*NET, precision="fp8", device=local)
+    f8.load(blob)
+    ddf.ddf_calibrate_fp8(f8.h, [r[:65536] for r in d_rays], 65536, stream)
+    nt = 1 << 20
+    ddf.ddf_autotune(f8.h, [r[:nt] for r in d_rays], nt, stream)
+    ddf.ddf_set_graph_mode(f8.h, True)
+    n_ao = int(offsets[-1])
+    ms = _time_ms(torch, stream, lambda: ddf.ddf_query_ao(f8.h, d_rays, n_ao, d_off, P, hard, soft,
+                                                          stream), warm=2)
+    out["ao_fp8_graph"] = {"rays": n_ao, "points": P, "ms_per_step": ms,
+                           "rays_per_s": n_ao / (ms / 1e3), "points_per_s": P / (ms / 1e3),
+                           "mean_soft_visibility": float(soft.mean().item()),
+                           "status": ddf.ddf_check_status(f8.h)}
+    f8.close()
+    del d_rays, d_off, hard, soft
+
+    # distillation steps: GPU caster targets + loss + backward + Adam
+    B = 65536
+    tscene = I.random_scene(32, 32, seed=0)
+    sph, ns, box, nb = _scene_buffers(torch, dev, tscene)
+    pool = [[torch.from_numpy(a).to(dev) for a in I.uniform_rays(B, seed=100 + k).soa()]
+            for k in range(8)]
+    tt = torch.empty(B, device=dev)
+    hit = torch.empty(B, dtype=torch.uint8, device=dev)
+    loss = torch.zeros(1, device=dev)
+    tr = ddf.DDF(*NET, precision="bf16", device=local)
+    tr.load(blob)
+    it = [0]
+
+    def train_step():
+        r = pool[it[0] % len(pool)]
+        it[0] += 1
+        ddf.ddf_cast_scene(sph, ns, box, nb, r, B, tt, hit, stream)
+        ddf.ddf_train_step(tr.h, r, tt, hit, B, 1e-3, loss, stream)
+
+    first = None
+    for _ in range(3):
+        train_step()
+        torch.cuda.synchronize()
+        first = first if first is not None else float(loss.item())
+    reps = 20
+    ms = _time_ms(torch, stream, lambda: [train_step() for _ in range(reps)], reps=1, warm=0) / reps
+    out["distillation"] = {"batch": B, "ms_per_step": ms, "steps_per_s": 1e3 / ms,
+                           "rays_per_s": B / (ms / 1e3),
+                           "tflops_6_b_params": 6.0 * B * I.NetShape(*NET).n_params / (ms / 1e3) / 1e12,
+                           "loss_first": first, "loss_after": float(loss.item()),
+                           "steps_taken": it[0], "status": ddf.ddf_check_status(tr.h)}
+    tr.close()
+    del pool
+
+    # sphere tracing an SDF network of the same size vs one DDF pass
+    SDF = (10, 1280, 8)
+    sblob = I.xavier_blob_dims(I.sdf_layer_dims(*SDF))
+    sm = ddf.DDF(*SDF, precision="bf16", device=local, kind="sdf")
+    sm.load(sblob)
+    sph, ns, box, nb = _scene_buffers(torch, dev, scene)
+    s_t = torch.empty(B, device=dev)
+    train_steps = 300
+    pts = [torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+           for a in I.uniform_points(B * 16, seed=7).T]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(train_steps):
+        lo = (k % 16) * B
+        pk = [c[lo:lo + B] for c in pts]
+        ddf.ddf_union_sdf(sph, ns, box, nb, pk, B, s_t, stream)
+        ddf.ddf_sdf_train_step(sm.h, pk, s_t, B, 1e-3 if k < 200 else 3e-4, loss, stream)
+    torch.cuda.synchronize()
+    sdf_train_s = time.perf_counter() - t0
+    sdf_loss = float(loss.item())
+    N = 1 << 20
+    br = I.bounce_rays(scene, N, seed=0)
+    d_br = [torch.from_numpy(a).to(dev) for a in br.soa()]
+    st = torch.empty(N, device=dev)
+    sh = torch.empty(N, dtype=torch.uint8, device=dev)
+    ss = torch.empty(N, dtype=torch.int32, device=dev)
+    trace_ms = _time_ms(torch, stream, lambda: ddf.ddf_sphere_trace(
+        sm.h, d_br, N, 128, 1e-3, 4.0, st, sh, ss, stream), flush=flush)
+    steps = ss.double()
+    dm = ddf.DDF(*NET, precision="bf16", device=local)
+    dm.load(blob)
+    nt = min(N, 1 << 20)
+    ddf.ddf_autotune(dm.h, d_br, nt, stream)
+    dt_ = torch.empty(N, device=dev)
+    dv = torch.empty(N, device=dev)
+    ddf_ms = _time_ms(torch, stream, lambda: ddf.ddf_query_rays(dm.h, d_br, N, dt_, dv, stream),
+                      flush=flush)
+    out["sphere_trace"] = {
+        "rays": N, "max_steps": 128, "eps": 1e-3, "t_max": 4.0,
+        "sdf_params": int(sblob.size), "ddf_params": int(blob.size),
+        "sdf_distill": {"steps": train_steps, "batch": B, "seconds": sdf_train_s,
+                        "final_loss": sdf_loss},
+        "trace_ms": trace_ms, "trace_rays_per_s": N / (trace_ms / 1e3),
+        "mean_steps": float(steps.mean().item()), "max_steps_taken": int(ss.max().item()),
+        "sdf_evals_per_s": float(steps.sum().item()) / (trace_ms / 1e3),
+        "hit_frac": float(sh.double().mean().item()),
+        "ddf_ms": ddf_ms, "ddf_rays_per_s": N / (ddf_ms / 1e3),
+        "ddf_speedup_vs_trace": trace_ms / ddf_ms,
+        "paper_speedup_context": "26-72x over sphere tracing, on the paper's own hardware",
+        "status": [ddf.ddf_check_status(sm.h), ddf.ddf_check_status(dm.h)]}
+    sm.close()
+    dm.close()
+    return out
+
 
 def main():
     args = parse()
@@ -351,6 +509,10 @@ def main():
         fp8_out = (t8, v8)
         f8.close()
 
+    extra = None
+    if rank == 0 and not args.no_workloads:
+        extra = workloads(torch, ddf, dev, local, stream, flush, blob)
+
     # CPU baseline (the FP64 oracle on a bounded prefix) + accuracy of the GPU outputs on it
     cpu = None
     acc = None
@@ -389,7 +551,7 @@ def main():
                        "wall_s_timed_region": wall,
                        "tile": {**tile, "autotune_ms_1M_rays": tune_ms}},
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(), "e2e": e2e,
-            "gpu_launches": launches, "accuracy": acc, "compare": compare,
+            "gpu_launches": launches, "accuracy": acc, "compare": compare, "workloads": extra,
             "kernel_ms_by_class": {k: v[0] for k, v in prof.items()},
             "device_status": status,
         }
