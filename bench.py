@@ -59,7 +59,8 @@ def parse():
     ap.add_argument("--rays", type=int, default=4_194_304)
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32 comparison run")
     ap.add_argument("--oracle-seconds", type=float, default=12.0)
-    ap.add_argument("--tile", default="auto", help="auto (autotune) or BNxEPI[pair][staged], e.g. 256x8, 256x4pairstaged")
+    ap.add_argument("--tile", default="auto", help="auto (autotune), or BNxEPI[pair][staged|fused] for every layer, or "
+                         "HIDDEN,FIRST, e.g. 256x4pairstaged,256x4fused")
     ap.add_argument("--no-workloads", action="store_true",
                     help="skip the AO / distillation / sphere-tracing measurements")
     return ap.parse_args()
@@ -320,6 +321,10 @@ def workloads(torch, ddf, dev, local, stream, flush, blob):
                         "final_loss": sdf_loss},
         "trace_ms": trace_ms, "trace_rays_per_s": N / (trace_ms / 1e3),
         "mean_steps": float(steps.mean().item()), "max_steps_taken": int(ss.max().item()),
+        "steps_histogram": {f"{lo}-{hi}": int(((ss >= lo) & (ss <= hi)).sum().item())
+                            for lo, hi in ((1, 1), (2, 2), (3, 4), (5, 8), (9, 16), (17, 32),
+                                           (33, 64), (65, 127), (128, 128))},
+        "trace_ms_per_sdf_eval_million": trace_ms / (float(steps.sum().item()) / 1e6),
         "sdf_evals_per_s": float(steps.sum().item()) / (trace_ms / 1e3),
         "hit_frac": float(sh.double().mean().item()),
         "ddf_ms": ddf_ms, "ddf_rays_per_s": N / (ddf_ms / 1e3),
@@ -362,18 +367,21 @@ def main():
         raise SystemExit("fp8 headline needs activation-scale calibration; use bf16")
     m.load(blob)
     tune_ms = None
-    fmt = lambda k: f"{k[0]}x{k[1]}{'pair' if k[2] else ''}{'staged' if k[3] else ''}"
+    fmt = lambda k: (f"{k[0]}x{k[1]}{'pair' if k[2] else ''}"
+                     f"{'fused' if len(k) > 4 and k[4] else ('staged' if k[3] else '')}")
     if args.tile == "auto":
         nt = min(R, 1 << 20)
         p1, p2 = ddf.ddf_autotune(m.h, [r[:nt] for r in d_rays], nt, stream)
         tune_ms = {"all_layers": {fmt(k): v for k, v in p1.items()},
                    "first_layer": {fmt(k): v for k, v in p2.items()}}
     else:
-        spec = args.tile
-        t4 = (256 if spec.startswith("256") else 128, 8 if "x8" in spec else 4,
-              int("pair" in spec), int("staged" in spec))
-        ddf.ddf_set_tile(m.h, t4, 0)
-        ddf.ddf_set_tile(m.h, t4, 1)
+        specs = args.tile.split(",")
+        for which in (0, 1):
+            spec = specs[min(which, len(specs) - 1)]
+            t4 = (256 if spec.startswith("256") else 128, 8 if "x8" in spec else 4,
+                  int("pair" in spec), int("staged" in spec or "fused" in spec),
+                  int("fused" in spec))
+            ddf.ddf_set_tile(m.h, t4, which)
     tile = {"hidden": fmt(ddf.ddf_get_tile(m.h, 0)), "first": fmt(ddf.ddf_get_tile(m.h, 1))}
 
     def step():
@@ -431,8 +439,19 @@ def main():
     if peak is None:
         peak, peak_src = 1700.0, "fallback (1.7 PFLOP/s sustained)"
     achieved = gemm_flops_step * args.steps / (g_ms / 1e3) / 1e12 if g_ms > 0 else None
+    # DRAM bytes per activation row of the CTA-pair staged bf16 kernel, from
+    # one ncu capture of a 262,144-row 1280x1280 launch (674.5 MB read +
+    # 633.4 MB written; profiles/tc_gemm_pair_bf16_shadow_4M.md); traffic grows
+    # with the rows, so a launch of R rows moves about R times this.
+    traffic = None
+    rows_per_launch = gemm_flops_step * args.steps / g_n / (2.0 * W_ * W_) if g_n else 0
+    if tile["hidden"] == "256x4pairstaged" and args.precision == "bf16":
+        traffic = rows_per_launch * (1307.9e6 / 262144)
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if achieved else None, "traffic": None,
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
+                "traffic_unit": "DRAM bytes per launch (ncu dram__bytes_read+write, scaled "
+                                "from a 262,144-row capture by rows per launch)",
+                "algorithmic_bytes_per_launch": rows_per_launch * 2 * 2 * W_ + 2 * W_ * W_,
                 "kernel": "tensor-core layer GEMM, hidden layers 2..8 (bf16, 1280x1280)",
                 "flops_per_launch": gemm_flops_step * args.steps / g_n if g_n else None,
                 "avg_launch_ms": g_ms / g_n if g_n else None, "peak_source": peak_src,

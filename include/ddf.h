@@ -293,13 +293,23 @@ ddf_status ddf_set_chunk_rays(ddf_handle h, int64_t chunk);
  *              TMEM lane quarter, each draining half the columns)
  *   cta_pair   1: the 256 x 256 tile a cluster of two CTAs computes with one
  *              pair MMA (needs bn 256, epi_warps 4)
- *   staged     1: pair tile only; activations leave through shared memory as
- *              whole 128-byte lines instead of per-thread 16-byte pieces */
+ *   staged     1: activations leave through shared memory as whole 128-byte
+ *              lines instead of per-thread 16-byte pieces (pair tile, or the
+ *              fused layer-1 tile)
+ *   fused_encode
+ *              1: layer 1 only (which = 1). The kernel builds the encoded
+ *              rays (Sec. 4.3) in shared memory from the ray arrays instead
+ *              of reading an encoded copy from device memory, and keeps each
+ *              128-ray block for all its column tiles. Needs bn 256, no pair,
+ *              staged 1, 6 + 12 octaves <= 128, width % 256 == 0, more than
+ *              one hidden layer and a ray (DDF) field. Results are bitwise
+ *              those of the unfused layer 1 with the same epilogue. */
 typedef struct {
   int32_t bn;
   int32_t epi_warps;
   int32_t cta_pair;
   int32_t staged;
+  int32_t fused_encode;
 } ddf_tile;
 
 /* Tile of layer 1 (which = 1) or of layers 2..H (which = 0). Results agree
@@ -309,16 +319,22 @@ typedef struct {
 ddf_status ddf_set_tile(ddf_handle h, int32_t which, const ddf_tile* tile);
 ddf_status ddf_get_tile(ddf_handle h, int32_t which, ddf_tile* tile);
 
-/* Autotuner over the 6 candidate tiles {256,4,0,0}, {256,8,0,0}, {128,4,0,0},
- * {128,8,0,0}, {256,4,1,0}, {256,4,1,1} on n rays (device SoA,
- * 1 <= n <= 2^24) on stream. Phase 1 uses one candidate for every layer and
- * keeps the fastest for layers 2..H; phase 2 keeps that and tries each
- * candidate for layer 1. Every configuration must give t and vis within 1e-3
- * (relative to max(1, |ref|)) of the first configuration tried before it is
- * timed (3 queries, CUDA events). ms_out (nullable, n_out >= 12) receives the
- * per-query ms of phase 1 in [0..5] and phase 2 in [6..11], -1 where a
- * candidate was skipped or rejected. Synchronous; allocates 16 n bytes of
- * device memory while it runs. A no-op on FP32 handles. */
+/* Autotuner over the 8 candidate tiles {256,4,0,0,0}, {256,8,0,0,0},
+ * {128,4,0,0,0}, {128,8,0,0,0}, {256,4,1,0,0}, {256,4,1,1,0},
+ * {256,4,0,1,1}, {256,8,0,1,1} on n rays (device SoA, 1 <= n <= 2^24) on
+ * stream. Phase 1 uses one of the first 6 for every layer and keeps the
+ * fastest for layers 2..H; phase 2 keeps that and tries all 8 for layer 1
+ * (the last two fuse the encoding into it). Every configuration must give t
+ * and vis within 1e-3 (relative to max(1, |ref|)) of the first configuration
+ * tried before it is timed. The passing candidates are then timed round-robin
+ * over 3 rounds, one query each, and keep their best round (so a clock that
+ * drifts under the power cap affects all alike): phase 1 times every launch
+ * of the query, phase 2 the encoding and layer-1 launches only (CUDA events
+ * around each launch). ms_out (nullable,
+ * n_out >= 16) receives the per-query ms of phase 1 in [0..7] (6, 7 unused)
+ * and of phase 2 in [8..15], -1 where a candidate was skipped or rejected.
+ * Synchronous; allocates 16 n bytes of device memory while it runs. A no-op
+ * on FP32 handles. */
 ddf_status ddf_autotune(ddf_handle h, const float* const rays[6], int64_t n, void* stream,
                         double* ms_out, int32_t n_out);
 

@@ -212,7 +212,9 @@ ddf_status forward_tc(ddf_s* h, ddf::RaySoA rays, int m, ddf::HeadOut out, cudaS
   const int W = h->cfg.width;
   const int H = h->cfg.hidden_layers;
   const bool fp8 = h->cfg.precision == DDF_FP8_E4M3;
-  {
+  // layer 1 may build the encoding itself (ddf_set_tile checked the shape)
+  const bool fused1 = h->tile_first.fused && h->cfg.kind == DDF_KIND_RAY;
+  if (!fused1) {
     ProfScope ps(h, kProfEncode, st);
     if (h->cfg.kind == DDF_KIND_SDF)  // points in rays.p[0..2]
       DDF_CK(ddf::launch_encode_points_bf16(rays.p[0], rays.p[1], rays.p[2], m, h->cfg.octaves,
@@ -227,10 +229,6 @@ ddf_status forward_tc(ddf_s* h, ddf::RaySoA rays, int m, ddf::HeadOut out, cudaS
     const bool out_fp8 = fp8 && !last;
     const void* a_base = l == 0 ? h->ws_enc : h->ws_act[(l - 1) & 1];
     const int K = l == 0 ? h->kp16 : W;
-    const uint64_t row_bytes = static_cast<uint64_t>(K) * (in_fp8 ? 1 : 2);
-    CUtensorMap tmA;
-    if (!make_tmap(&tmA, a_base, in_fp8, K, m, row_bytes, 128))
-      return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for an activation map");
     ddf::TcGemmParams p{};
     p.M = m;
     p.N = W;
@@ -247,6 +245,16 @@ ddf_status forward_tc(ddf_s* h, ddf::RaySoA rays, int m, ddf::HeadOut out, cudaS
     p.timeout_ns = h->timeout_ns;
     ProfScope ps(h, l == 0 ? kProfFirst : kProfGemm, st);
     const ddf::TcTile& t = l == 0 ? h->tile_first : h->tile;
+    if (l == 0 && fused1) {
+      const int grid = static_cast<int>(std::min<int64_t>((m + 127) / 128, h->num_sms));
+      DDF_CK(ddf::launch_tc_layer1(t.epi_warps, out_fp8, h->tmB[0], rays, h->cfg.octaves, p, grid,
+                                   st));
+      continue;
+    }
+    const uint64_t row_bytes = static_cast<uint64_t>(K) * (in_fp8 ? 1 : 2);
+    CUtensorMap tmA;
+    if (!make_tmap(&tmA, a_base, in_fp8, K, m, row_bytes, 128))
+      return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for an activation map");
     if (t.pair) {
       const int64_t tiles = ((m + 255) / 256) * static_cast<int64_t>(W / 256);
       const int clusters = static_cast<int>(std::min<int64_t>(tiles, h->pair_clusters));
@@ -1060,13 +1068,23 @@ ddf_status ddf_set_tile(ddf_handle h, int32_t which, const ddf_tile* tile) {
   if (h->cfg.width % bn != 0) return fail(DDF_ERR_UNSUPPORTED, "width is not a multiple of bn");
   if (tile->cta_pair != 0 && (bn != 256 || ew != 4))
     return fail(DDF_ERR_INVALID_ARG, "the CTA-pair tile is bn 256 with 4 epilogue warps");
-  if (tile->staged != 0 && tile->cta_pair == 0)
-    return fail(DDF_ERR_INVALID_ARG, "staged stores exist for the CTA-pair tile only");
+  if (tile->fused_encode != 0) {
+    if (which != 1) return fail(DDF_ERR_INVALID_ARG, "fused_encode is a layer-1 tile (which = 1)");
+    if (bn != 256 || tile->cta_pair != 0 || tile->staged == 0)
+      return fail(DDF_ERR_INVALID_ARG, "the fused layer-1 tile is bn 256, no pair, staged");
+    if (h->cfg.kind != DDF_KIND_RAY || h->cfg.hidden_layers < 2 ||
+        !ddf::tc_layer1_supported(h->cfg.octaves, h->cfg.width))
+      return fail(DDF_ERR_UNSUPPORTED,
+                  "fused_encode needs a ray field, >= 2 hidden layers, 6 + 12 octaves <= 128 "
+                  "and width % 256 == 0");
+  } else if (tile->staged != 0 && tile->cta_pair == 0) {
+    return fail(DDF_ERR_INVALID_ARG, "staged stores exist for the CTA-pair and fused tiles only");
+  }
   if (tile->cta_pair != 0 && h->pair_clusters <= 0)
     return fail(DDF_ERR_UNSUPPORTED, "CTA-pair clusters do not fit on this device");
   clear_graphs(h);  // weight maps and launch shapes change
   (which == 1 ? h->tile_first : h->tile) =
-      ddf::TcTile{bn, ew, tile->cta_pair != 0, tile->staged != 0};
+      ddf::TcTile{bn, ew, tile->cta_pair != 0, tile->staged != 0, tile->fused_encode != 0};
   h->bn = h->tile.bn;
   if (h->loaded && h->cfg.precision != DDF_FP32) {
     DeviceGuard g(h->cfg.device);
@@ -1084,16 +1102,24 @@ ddf_status ddf_get_tile(ddf_handle h, int32_t which, ddf_tile* tile) {
   tile->epi_warps = t.epi_warps;
   tile->cta_pair = t.pair ? 1 : 0;
   tile->staged = t.staged ? 1 : 0;
+  tile->fused_encode = t.fused ? 1 : 0;
   return DDF_OK;
 }
 
 namespace ddfi {
 
-constexpr int kTileCands = 6;
-const ddf_tile kCands[kTileCands] = {{256, 4, 0, 0}, {256, 8, 0, 0}, {128, 4, 0, 0},
-                                     {128, 8, 0, 0}, {256, 4, 1, 0}, {256, 4, 1, 1}};
+// the last kFusedCands candidates are layer-1 only (phase 2)
+constexpr int kTileCands = 8;
+constexpr int kFusedCands = 2;
+constexpr int kMsSlots = 2 * kTileCands;
+const ddf_tile kCands[kTileCands] = {{256, 4, 0, 0, 0}, {256, 8, 0, 0, 0}, {128, 4, 0, 0, 0},
+                                     {128, 8, 0, 0, 0}, {256, 4, 1, 0, 0}, {256, 4, 1, 1, 0},
+                                     {256, 4, 0, 1, 1}, {256, 8, 0, 1, 1}};
 
 bool cand_ok(ddf_s* h, const ddf_tile& c) {
+  if (c.fused_encode != 0)
+    return h->cfg.kind == DDF_KIND_RAY && h->cfg.hidden_layers >= 2 &&
+           ddf::tc_layer1_supported(h->cfg.octaves, h->cfg.width);
   return h->cfg.width % c.bn == 0 && (c.cta_pair == 0 || h->pair_clusters > 0);
 }
 
@@ -1105,19 +1131,16 @@ ddf_status ddf_autotune(ddf_handle h, const float* const rays[6], int64_t n, voi
   if (s != DDF_OK) return s;
   if ((s = check_rays(rays, n)) != DDF_OK) return s;
   if (n <= 0 || n > (int64_t{1} << 24)) return fail(DDF_ERR_INVALID_ARG, "tune on 1 .. 2^24 rays");
-  if (ms_out != nullptr && n_out < 2 * kTileCands)
-    return fail(DDF_ERR_INVALID_ARG, "ms_out needs 12 entries");
+  if (ms_out != nullptr && n_out < kMsSlots)
+    return fail(DDF_ERR_INVALID_ARG, "ms_out needs 16 entries");
   if (ms_out != nullptr)
-    for (int i = 0; i < 2 * kTileCands; ++i) ms_out[i] = -1.0;
+    for (int i = 0; i < kMsSlots; ++i) ms_out[i] = -1.0;
   if (h->cfg.precision == DDF_FP32) return DDF_OK;  // one FP32 kernel shape, nothing to choose
   DeviceGuard g(h->cfg.device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   float* buf = nullptr;
   DDF_CK(cudaMalloc(&buf, 4 * n * sizeof(float)));
   std::vector<float> ref_t(n), ref_v(n), got_t(n), got_v(n);
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
   ddf_tile keep_h, keep_f;
   ddf_get_tile(h, 0, &keep_h);
   ddf_get_tile(h, 1, &keep_f);
@@ -1125,10 +1148,10 @@ ddf_status ddf_autotune(ddf_handle h, const float* const rays[6], int64_t n, voi
   h->prof = false;
   bool have_ref = false;
   ddf_status result = DDF_OK;
-  // Runs the query with the current tiles; checks it against the reference
-  // (the first configuration run) and returns its time, or -1 if rejected.
-  auto trial = [&](double* ms) -> ddf_status {
-    *ms = -1.0;
+  // Runs the query once with the current tiles and checks it against the
+  // reference (the first configuration run); false if rejected.
+  auto check = [&](bool* ok) -> ddf_status {
+    *ok = false;
     ddf::HeadOut o{};
     o.t = buf + (have_ref ? 2 * n : 0);
     o.vis = o.t + n;
@@ -1148,42 +1171,82 @@ ddf_status ddf_autotune(ddf_handle h, const float* const rays[6], int64_t n, voi
       if (!(worst <= 1e-3)) return DDF_OK;  // rejected
     }
     have_ref = true;
-    cudaEventRecord(e0, st);
-    for (int k = 0; k < 3; ++k) run_query(h, rays, n, o, st);
-    cudaEventRecord(e1, st);
-    cudaEventSynchronize(e1);
-    float t = 0.f;
-    cudaEventElapsedTime(&t, e0, e1);
-    *ms = t / 3.0;
+    *ok = true;
     return DDF_OK;
   };
+  // Device time of one query with the current tiles, from the per-launch
+  // events of the profiling classes: every class (phase 1) or only the
+  // encoding and layer 1 (phase 2). The events used here are released again.
+  auto timed = [&](bool first_only, double* ms) -> ddf_status {
+    const size_t k0 = h->recs.size(), e0 = h->ev_used;
+    ddf::HeadOut o{};
+    o.t = buf + 2 * n;
+    o.vis = o.t + n;
+    h->prof = true;
+    ddf_status r = run_query(h, rays, n, o, st);
+    h->prof = false;
+    if (r == DDF_OK && cudaStreamSynchronize(st) != cudaSuccess)
+      r = fail(DDF_ERR_CUDA, "autotune: launch failed");
+    double sum = 0.0;
+    for (size_t i = k0; r == DDF_OK && i < h->recs.size(); ++i) {
+      const auto& rec = h->recs[i];
+      if (first_only && rec.cls != kProfEncode && rec.cls != kProfFirst) continue;
+      float t = 0.f;
+      cudaEventElapsedTime(&t, rec.a, rec.b);
+      sum += t;
+    }
+    h->recs.resize(k0);
+    h->ev_used = e0;
+    *ms = sum;
+    return r;
+  };
+  // Candidates are checked once, then timed round-robin; each keeps its best
+  // round, so a clock that drifts while the GPU warms up (power cap) affects
+  // every candidate alike instead of the ones tried last.
+  constexpr int kRounds = 3;
+  auto tune = [&](int which_set, int n_cands, bool first_only, double* best_ms) -> int {
+    std::vector<double> ms(n_cands, 1e30);
+    std::vector<char> ok(n_cands, 0);
+    for (int c = 0; c < n_cands && result == DDF_OK; ++c) {
+      if (!cand_ok(h, kCands[c])) continue;
+      if (which_set != 0 && (result = ddf_set_tile(h, 0, &kCands[c])) != DDF_OK) break;
+      if ((result = ddf_set_tile(h, 1, &kCands[c])) != DDF_OK) break;
+      bool pass = false;
+      if ((result = check(&pass)) != DDF_OK) break;
+      ok[c] = pass;
+    }
+    for (int round = 0; round < kRounds && result == DDF_OK; ++round) {
+      for (int c = 0; c < n_cands && result == DDF_OK; ++c) {
+        if (!ok[c]) continue;
+        if (which_set != 0 && (result = ddf_set_tile(h, 0, &kCands[c])) != DDF_OK) break;
+        if ((result = ddf_set_tile(h, 1, &kCands[c])) != DDF_OK) break;
+        double t = 0.0;
+        if ((result = timed(first_only, &t)) != DDF_OK) break;
+        ms[c] = std::min(ms[c], t);
+      }
+    }
+    int best = -1;
+    for (int c = 0; c < n_cands; ++c) {
+      if (!ok[c]) continue;
+      best_ms[c] = ms[c];
+      if (best < 0 || ms[c] < ms[best]) best = c;
+    }
+    return best;
+  };
   // phase 1: one tile for every layer; phase 2: the first layer's own tile
-  int best_h = -1, best_f = -1;
-  double tbest = 1e30;
-  for (int c = 0; c < kTileCands && result == DDF_OK; ++c) {
-    if (!cand_ok(h, kCands[c])) continue;
-    if ((result = ddf_set_tile(h, 0, &kCands[c])) != DDF_OK) break;
-    if ((result = ddf_set_tile(h, 1, &kCands[c])) != DDF_OK) break;
-    double ms;
-    if ((result = trial(&ms)) != DDF_OK) break;
-    if (ms_out != nullptr) ms_out[c] = ms;
-    if (ms > 0 && ms < tbest) tbest = ms, best_h = c;
-  }
+  double p1[kTileCands], p2[kTileCands];
+  for (int c = 0; c < kTileCands; ++c) p1[c] = p2[c] = -1.0;
+  const int best_h = tune(1, kTileCands - kFusedCands, false, p1);
+  int best_f = -1;
   if (result == DDF_OK && best_h >= 0) {
     result = ddf_set_tile(h, 0, &kCands[best_h]);
-    tbest = 1e30;
-    for (int c = 0; c < kTileCands && result == DDF_OK; ++c) {
-      if (!cand_ok(h, kCands[c])) continue;
-      if ((result = ddf_set_tile(h, 1, &kCands[c])) != DDF_OK) break;
-      double ms;
-      if ((result = trial(&ms)) != DDF_OK) break;
-      if (ms_out != nullptr) ms_out[kTileCands + c] = ms;
-      if (ms > 0 && ms < tbest) tbest = ms, best_f = c;
-    }
+    if (result == DDF_OK) best_f = tune(0, kTileCands, true, p2);
+  }
+  for (int c = 0; ms_out != nullptr && c < kTileCands; ++c) {
+    ms_out[c] = p1[c];
+    ms_out[kTileCands + c] = p2[c];
   }
   h->prof = keep_prof;
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   cudaFree(buf);
   if (result != DDF_OK || best_h < 0 || best_f < 0) {
     ddf_set_tile(h, 0, &keep_h);

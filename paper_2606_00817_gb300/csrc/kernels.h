@@ -81,8 +81,16 @@ struct TcTile {
   int bn;
   int epi_warps;
   bool pair = false;    // 256 x 256 tile on a 2-CTA cluster (tc_gemm_pair.cu; bn 256, 4 warps)
-  bool staged = false;  // pair tile only: outputs staged through shared memory
+  bool staged = false;  // pair tile, or the fused layer-1 tile: outputs staged through shared memory
+  bool fused = false;   // layer 1 only: the encoding is built in shared memory (tc_layer1.cu)
 };
+
+// Layer 1 with the ray encoding computed inside the kernel (tc_layer1.cu):
+// mode-0 output (bf16, or e4m3 after out_scale) of ReLU(enc(rays) W_1^T + b)
+// for p.M rays, N % 256 == 0, 6 + 12 L <= 128; p.K is not used.
+bool tc_layer1_supported(int L, int N);
+cudaError_t launch_tc_layer1(int epi_warps, bool out_fp8, const CUtensorMap& tmB, RaySoA rays,
+                             int L, const TcGemmParams& p, int grid, cudaStream_t s);
 
 // in_fp8: operands are e4m3 codes (kind::f8f6f4) instead of bf16 (kind::f16).
 // out_fp8: mode-0 output is e4m3 codes instead of bf16.

@@ -30,7 +30,7 @@ _RAYS = C.POINTER(C.c_void_p)
 
 class Tile(C.Structure):
     _fields_ = [("bn", C.c_int32), ("epi_warps", C.c_int32), ("cta_pair", C.c_int32),
-                ("staged", C.c_int32)]
+                ("staged", C.c_int32), ("fused_encode", C.c_int32)]
 
 
 DDF_KIND_RAY, DDF_KIND_SDF = 0, 1
@@ -320,28 +320,31 @@ def ddf_set_chunk_rays(h, chunk: int) -> None:
 
 
 def ddf_set_tile(h, tile, which: int = 0) -> None:
-    """tile = (bn, epi_warps, cta_pair, staged); which 0 = layers 2..H, 1 = layer 1."""
+    """tile = (bn, epi_warps, cta_pair, staged[, fused_encode]); which 0 =
+    layers 2..H, 1 = layer 1."""
     _call("ddf_set_tile", h, int(which), C.byref(Tile(*[int(x) for x in tile])))
 
 
 def ddf_get_tile(h, which: int = 0):
+    """(bn, epi_warps, cta_pair, staged, fused_encode)"""
     t = Tile()
     _call("ddf_get_tile", h, int(which), C.byref(t))
-    return (t.bn, t.epi_warps, t.cta_pair, t.staged)
+    return (t.bn, t.epi_warps, t.cta_pair, t.staged, t.fused_encode)
 
 
-TILE_CANDIDATES = ((256, 4, 0, 0), (256, 8, 0, 0), (128, 4, 0, 0), (128, 8, 0, 0),
-                   (256, 4, 1, 0), (256, 4, 1, 1))
+# the autotuner's candidates, in its order; the last two are layer-1 only
+TILE_CANDIDATES = ((256, 4, 0, 0, 0), (256, 8, 0, 0, 0), (128, 4, 0, 0, 0), (128, 8, 0, 0, 0),
+                   (256, 4, 1, 0, 0), (256, 4, 1, 1, 0), (256, 4, 0, 1, 1), (256, 8, 0, 1, 1))
 
 
 def ddf_autotune(h, rays, n, stream=None):
     """Returns ({tile: ms or None} for phase 1 (all layers), the same for
     phase 2 (layer 1 only)); leaves the fastest tiles set."""
     rp, keep = _rays(rays)
-    ms = (C.c_double * 12)()
-    _call("ddf_autotune", h, rp, int(n), _stream(stream), ms, 12)
     k = len(TILE_CANDIDATES)
-    p1 = {c: (ms[i] if ms[i] >= 0 else None) for i, c in enumerate(TILE_CANDIDATES)}
+    ms = (C.c_double * (2 * k))()
+    _call("ddf_autotune", h, rp, int(n), _stream(stream), ms, 2 * k)
+    p1 = {c: (ms[i] if ms[i] >= 0 else None) for i, c in enumerate(TILE_CANDIDATES) if not c[4]}
     p2 = {c: (ms[k + i] if ms[k + i] >= 0 else None) for i, c in enumerate(TILE_CANDIDATES)}
     return p1, p2
 

@@ -19,6 +19,7 @@ pytestmark = pytest.mark.gpu
 
 SMALL = (6, 128, 4)      # 78 -> 128 x4 -> 2
 PAPER = (10, 1280, 8)    # 126 -> 1280 x8 -> 2
+SMALL_256 = (6, 256, 3)  # 78 -> 256 x3 -> 2
 LIGHT = (3.0, 3.0, 3.0)
 BOUNDS = {"bf16": (2e-3, 2e-4), "fp8": (1e-2, 1e-3)}
 EXACT_BOUNDS = {"bf16": (5e-2, 5e-3), "fp8": (0.2, 2e-2)}
@@ -211,8 +212,8 @@ def test_full_size_shadow_workload_sampled(torch_cuda):
     _check_reduced(t[idx], v[idx], sub, blob, PAPER, "bf16", None)
 
 
-@pytest.mark.parametrize("tile", [(256, 4, 0, 0), (256, 8, 0, 0), (128, 4, 0, 0), (128, 8, 0, 0),
-                                  (256, 4, 1, 0), (256, 4, 1, 1)])
+@pytest.mark.parametrize("tile", [(256, 4, 0, 0, 0), (256, 8, 0, 0, 0), (128, 4, 0, 0, 0),
+                                  (128, 8, 0, 0, 0), (256, 4, 1, 0, 0), (256, 4, 1, 1, 0)])
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
 def test_every_tile_matches_oracle(torch_cuda, tile, prec):
     from paper_2606_00817_gb300 import ddf
@@ -226,6 +227,49 @@ def test_every_tile_matches_oracle(torch_cuda, tile, prec):
     t, v = _query(torch_cuda, m, rays)
     _check_reduced(t, v, rays, blob, PAPER, prec, sc)
     assert ddf.ddf_check_status(m.h) == 0
+
+
+@pytest.mark.parametrize("net,n", [(PAPER, 777), (PAPER, 300_001), (SMALL_256, 1029)])
+@pytest.mark.parametrize("epi", [4, 8])
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_fused_encode_layer1(torch_cuda, net, n, epi, prec):
+    """Layer 1 with the encoding built in shared memory (L = 10: K = 126 in two
+    64-wide slices; L = 6: K = 78, the second slice mostly padding): every
+    output equals the unfused layer 1's bit for bit (same rounding of the same
+    features, same epilogue), and sampled rays match the oracle. 777 rays: 7
+    row blocks, the last ragged; 300,001 rays: about 15 row blocks per CTA, so
+    both shared-memory A buffers are reused many times."""
+    from paper_2606_00817_gb300 import ddf
+    blob = I.xavier_blob(I.NetShape(*net))
+    sc = _scales(blob, net) if prec == "fp8" else None
+    rays = I.uniform_rays(n, seed=11)
+    m = _make(net, prec, blob, sc)
+    ddf.ddf_set_tile(m.h, (256, 4, 0, 0), which=1)
+    ref_t, ref_v = _query(torch_cuda, m, rays)
+    ddf.ddf_set_tile(m.h, (256, epi, 0, 1, 1), which=1)
+    assert ddf.ddf_get_tile(m.h, 1) == (256, epi, 0, 1, 1)
+    t, v = _query(torch_cuda, m, rays)
+    assert ddf.ddf_check_status(m.h) == 0
+    assert np.array_equal(t, ref_t) and np.array_equal(v, ref_v)
+    idx = np.unique(np.concatenate([np.arange(0, 64), np.arange(rays.n - 64, rays.n),
+                                    np.random.default_rng(4).choice(rays.n, 64, replace=False)]))
+    sub = I.Rays(*[a[idx] for a in rays.soa()])
+    _check_reduced(t[idx], v[idx], sub, blob, net, prec, sc)
+
+
+def test_fused_encode_rejected_where_unsupported(torch_cuda):
+    from paper_2606_00817_gb300 import ddf
+    m = _make(PAPER, "bf16", I.xavier_blob(I.NetShape(*PAPER)))
+    for tile, which in (((256, 4, 0, 1, 1), 0), ((256, 4, 1, 1, 1), 1), ((128, 4, 0, 1, 1), 1),
+                        ((256, 4, 0, 0, 1), 1)):
+        with pytest.raises(ddf.DDFError):
+            ddf.ddf_set_tile(m.h, tile, which)
+    m12 = _make((12, 256, 2), "bf16", I.xavier_blob(I.NetShape(12, 256, 2)))
+    with pytest.raises(ddf.DDFError):                       # 6 + 12 x 12 = 150 > 128
+        ddf.ddf_set_tile(m12.h, (256, 4, 0, 1, 1), 1)
+    m1 = _make((10, 256, 1), "bf16", I.xavier_blob(I.NetShape(10, 256, 1)))
+    with pytest.raises(ddf.DDFError):                       # layer 1 is also the head layer
+        ddf.ddf_set_tile(m1.h, (256, 4, 0, 1, 1), 1)
 
 
 def test_pair_tile_on_a_full_chunk(torch_cuda):
@@ -259,8 +303,8 @@ def test_small_width_tiles_and_autotune(torch_cuda):
     p1, p2 = ddf.ddf_autotune(m.h, _dev(torch_cuda, rays), rays.n)
     for ms in (p1, p2):
         assert all(ms[c] is None for c in ms if c[0] == 256)
-        assert ms[(128, 4, 0, 0)] > 0 and ms[(128, 8, 0, 0)] > 0
-    assert ddf.ddf_get_tile(m.h, 0) in ((128, 4, 0, 0), (128, 8, 0, 0))
-    assert ddf.ddf_get_tile(m.h, 1) in ((128, 4, 0, 0), (128, 8, 0, 0))
+        assert ms[(128, 4, 0, 0, 0)] > 0 and ms[(128, 8, 0, 0, 0)] > 0
+    assert ddf.ddf_get_tile(m.h, 0) in ((128, 4, 0, 0, 0), (128, 8, 0, 0, 0))
+    assert ddf.ddf_get_tile(m.h, 1) in ((128, 4, 0, 0, 0), (128, 8, 0, 0, 0))
     t, v = _query(torch_cuda, m, rays)
     _check_reduced(t, v, rays, blob, SMALL, "bf16", None)
