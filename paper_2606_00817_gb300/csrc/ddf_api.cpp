@@ -246,9 +246,12 @@ ddf_status forward_tc(ddf_s* h, ddf::RaySoA rays, int m, ddf::HeadOut out, cudaS
     ProfScope ps(h, l == 0 ? kProfFirst : kProfGemm, st);
     const ddf::TcTile& t = l == 0 ? h->tile_first : h->tile;
     if (l == 0 && fused1) {
+      CUtensorMap tmO;  // the layer's output, written by TMA stores of 32-row boxes
+      if (!make_tmap(&tmO, p.out, out_fp8, W, m, static_cast<uint64_t>(W) * (out_fp8 ? 1 : 2), 32))
+        return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for an output map");
       const int grid = static_cast<int>(std::min<int64_t>((m + 127) / 128, h->num_sms));
-      DDF_CK(ddf::launch_tc_layer1(t.epi_warps, out_fp8, h->tmB[0], rays, h->cfg.octaves, p, grid,
-                                   st));
+      DDF_CK(ddf::launch_tc_layer1(t.epi_warps, out_fp8, h->tmB[0], tmO, rays, h->cfg.octaves, p,
+                                   grid, st));
       continue;
     }
     const uint64_t row_bytes = static_cast<uint64_t>(K) * (in_fp8 ? 1 : 2);

@@ -87,10 +87,12 @@ struct TcTile {
 
 // Layer 1 with the ray encoding computed inside the kernel (tc_layer1.cu):
 // mode-0 output (bf16, or e4m3 after out_scale) of ReLU(enc(rays) W_1^T + b)
-// for p.M rays, N % 256 == 0, 6 + 12 L <= 128; p.K is not used.
+// for p.M rays, N % 256 == 0, 6 + 12 L <= 128; p.K is not used. tmO maps
+// p.out [M x N] with 128-byte-swizzled boxes of 128 bytes x 32 rows.
 bool tc_layer1_supported(int L, int N);
-cudaError_t launch_tc_layer1(int epi_warps, bool out_fp8, const CUtensorMap& tmB, RaySoA rays,
-                             int L, const TcGemmParams& p, int grid, cudaStream_t s);
+cudaError_t launch_tc_layer1(int epi_warps, bool out_fp8, const CUtensorMap& tmB,
+                             const CUtensorMap& tmO, RaySoA rays, int L, const TcGemmParams& p,
+                             int grid, cudaStream_t s);
 
 // in_fp8: operands are e4m3 codes (kind::f8f6f4) instead of bf16 (kind::f16).
 // out_fp8: mode-0 output is e4m3 codes instead of bf16.

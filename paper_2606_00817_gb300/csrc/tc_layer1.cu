@@ -7,13 +7,15 @@
 // memory from the ray SoA instead of reading it from an encoded copy in HBM,
 // and keeps it there for all W / 256 column tiles of its 128-ray row block.
 //   warp 0         TMA producer: 256 x 64 bf16 tiles of W_1 (128-byte
-//                  swizzle) into a 3-stage ring
+//                  swizzle) into a ring of 3 stages (2 with 8 epilogue warps)
 //   warp 1         TMEM owner; one thread issues tcgen05.mma (M 128, N 256,
 //                  K 16) into two 256-column FP32 accumulators
-//   warps 2..E+1   epilogue: bias + ReLU of the accumulator, rows staged
-//                  through shared memory and written as 128-byte lines
+//   warps 2..E+1   epilogue: bias + ReLU of the accumulator; each warp packs
+//                  32 rows x 128 bytes into a 128-byte-swizzled shared box
+//                  (two per warp) that a TMA tensor store writes out, so no
+//                  thread issues a global store
 //   last 4 warps   encoder: thread = ray; raw (o, d) then sin / cos of
-//                  pi 2^k e_c, written as bf16 pairs straight into the
+//                  pi 2^k e_c, written as 16-byte pieces straight into the
 //                  swizzled K-major layout tcgen05 reads (two buffers, so the
 //                  next row block is encoded while this one is multiplied)
 // Persistent: CTA b takes row blocks b, b + grid, ... Every wait is bounded.
@@ -29,6 +31,7 @@ namespace {
 
 constexpr uint64_t kL1DrainNs = 1000000000ull;
 
+template <int EPI>
 struct L1Shape {
   static constexpr int BM = 128;
   static constexpr int BN = 256;
@@ -36,36 +39,90 @@ struct L1Shape {
   static constexpr int ATOM = BM * 128;                 // one 64-element K slice of A: 16 KB
   static constexpr int A_BUF = KB_MAX * ATOM;           // 32 KB
   static constexpr int B_BYTES = BN * 128;              // 32 KB
-  static constexpr int STAGES = 3;
+  static constexpr int STAGES = EPI == 8 ? 2 : 3;       // W_1 ring
+  static constexpr int OUT_DEPTH = 2;                   // output boxes per epilogue warp
+  static constexpr int OUT_BOX = 32 * 128;              // 32 rows x 128 bytes
   static constexpr int B_OFF = 2 * A_BUF;
   static constexpr int CTRL_OFF = B_OFF + STAGES * B_BYTES;
   static constexpr int NUM_BARS = 2 * STAGES + 9;
   static constexpr int CTRL_BYTES = 256;
-  static constexpr int VEC_OFF = CTRL_OFF + CTRL_BYTES;
+  static constexpr int VEC_OFF = CTRL_OFF + CTRL_BYTES;  // bias [N] floats
   static constexpr int TMEM_COLS = 2 * BN;
   static_assert(NUM_BARS * 8 + 8 <= CTRL_BYTES, "control block overflow");
+  // output boxes start on a 1024-byte boundary (128-byte swizzle atom)
+  __host__ __device__ static constexpr int out_off(int n) { return (VEC_OFF + 4 * n + 1023) & ~1023; }
+  __host__ __device__ static constexpr int smem_bytes(int n) { return out_off(n) + EPI * OUT_DEPTH * OUT_BOX + 1024; }
 };
 
-// Shared memory of a launch: fixed part + per-column vectors + output staging.
-constexpr int l1_smem_bytes(int n, int epi) {
-  return L1Shape::VEC_OFF + epi_vector_bytes(n) + epi * kStageBytesPerWarp + 1024;
+// Byte offset of 16-byte piece q (bf16 elements 8q .. 8q+7) of row r inside a
+// K-major A buffer with 128-byte swizzle: 64-element slices of 16 KB, rows of
+// 128 bytes, piece q mod 8 of row r stored at piece (q mod 8) ^ (r mod 8).
+__device__ __forceinline__ uint32_t a_piece_offset(int r, int q) {
+  return static_cast<uint32_t>((q >> 3) * (128 * 128) + r * 128 + (((q & 7) ^ (r & 7)) << 4));
 }
 
-// Byte offset of 32-bit word w (bf16 elements 2w, 2w+1) of row r inside a
-// K-major A buffer with 128-byte swizzle: 64-element slices of 16 KB, rows of
-// 128 bytes, 16-byte piece c of row r stored at piece c ^ (r mod 8).
-__device__ __forceinline__ uint32_t a_word_offset(int r, int w) {
-  const int slice = w >> 5;
-  const int piece = (w & 31) >> 2;
-  return static_cast<uint32_t>(slice * L1Shape::ATOM + r * 128 + ((piece ^ (r & 7)) << 4) +
-                               ((w & 3) << 2));
+// (sin, cos)(pi 2^k e_c) as a bf16 pair for the next (c, k) of the encoding
+// order (coordinate-major, band-minor), then advances (c, k); zero once all
+// six coordinates are done (padding up to the MMA's K).
+__device__ __forceinline__ uint32_t next_pair(const float (&e)[6], int L, int& c, int& k) {
+  if (c >= 6) return 0u;
+  const float ec = c == 0 ? e[0] : c == 1 ? e[1] : c == 2 ? e[2] : c == 3 ? e[3] : c == 4 ? e[4] : e[5];
+  float sn, cs;
+  sincospif(ldexpf(ec, k), &sn, &cs);  // pi 2^k e, the 2^k scaling is exact
+  if (++k == L) {
+    k = 0;
+    ++c;
+  }
+  return epi_pack_bf16x2(sn, cs);
+}
+
+// Epilogue of one tile for one warp: chunks [c_begin, c_end) of its TMEM rows
+// (bias + ReLU, bf16 or e4m3), packed group by group (128 bytes of each row)
+// into the warp's output boxes and written by TMA stores at
+// (column n0 + 32 c, row row0). `issued` counts the warp's stores so far.
+template <bool OUT_FP8, int DEPTH>
+__device__ __forceinline__ void epi_tile_tma(const TcGemmParams& p, const EpiVectors& ev,
+                                             const CUtensorMap* tmO, uint32_t tbase, int row0,
+                                             int n0, int c_begin, int c_end, uint8_t* boxes,
+                                             int lane, uint32_t& issued) {
+  constexpr int kGroup = OUT_FP8 ? 4 : 2;  // 32-column chunks per 128-byte row piece
+  uint32_t va[32], vb[32];
+  uint8_t* box = boxes;
+  tmem_ld32(tbase + 32u * c_begin, va);
+  tmem_wait_ld_regs(va);
+#pragma unroll 1
+  for (int c = c_begin; c < c_end; c += 2) {
+    if (((c - c_begin) % kGroup) == 0) {  // a new group: take the next box once it is free
+      box = boxes + (issued % DEPTH) * (32 * 128);
+      if (lane == 0) bulk_wait_group_read<DEPTH - 1>();
+      __syncwarp();
+    }
+    tmem_ld32(tbase + 32u * (c + 1), vb);
+    epi_chunk_stage<OUT_FP8>(p, ev, va, n0 + 32 * c, c, box, lane);
+    tmem_wait_ld_regs(vb);
+    const bool next2 = c + 2 < c_end;
+    if (next2) tmem_ld32(tbase + 32u * (c + 2), va);
+    epi_chunk_stage<OUT_FP8>(p, ev, vb, n0 + 32 * (c + 1), c + 1, box, lane);
+    if (((c + 2 - c_begin) % kGroup) == 0) {
+      const int g0 = c + 2 - kGroup;  // first chunk of the finished group
+      fence_proxy_async_smem();       // the TMA store reads the box through the async proxy
+      __syncwarp();
+      if (lane == 0) {
+        // element coordinates: 32 columns per chunk; e4m3 elements are bytes
+        tma_store_2d(tmO, smem_u32(box), n0 + 32 * g0, row0);
+        bulk_commit_group();
+      }
+      ++issued;
+    }
+    if (next2) tmem_wait_ld_regs(va);
+  }
 }
 
 template <bool OUT_FP8, int EPI>
 __global__ void __launch_bounds__(64 + 32 * EPI + 128, 1)
-    tc_layer1_kernel(const __grid_constant__ CUtensorMap tmB, const RaySoA rays, const int L,
-                     const TcGemmParams p) {
-  using S = L1Shape;
+    tc_layer1_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmO,
+                     const RaySoA rays, const int L, const TcGemmParams p) {
+  using S = L1Shape<EPI>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -106,12 +163,16 @@ __global__ void __launch_bounds__(64 + 32 * EPI + 128, 1)
     *abort_flag = 0;
     fence_mbar_init();
     tma_prefetch_desc(&tmB);
+    tma_prefetch_desc(&tmO);
   }
   if (warp == 1) {
     tmem_alloc(smem_u32(tmem_slot), S::TMEM_COLS);
     tmem_relinquish();
   }
-  const EpiVectors ev = stage_epi_vectors(p, reinterpret_cast<float*>(smem + S::VEC_OFF));
+  // layer 1 has no column scale and no head: only the bias is staged
+  float* sbias = reinterpret_cast<float*>(smem + S::VEC_OFF);
+  for (int i = threadIdx.x; i < p.N; i += blockDim.x) sbias[i] = p.bias[i];
+  const EpiVectors ev{sbias, nullptr, nullptr, nullptr};
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -196,7 +257,8 @@ __global__ void __launch_bounds__(64 + 32 * EPI + 128, 1)
     const int q = warp & 3;  // TMEM lane quarter this warp may access
     constexpr int kChunks = S::BN / 32 / (EPI / 4);
     const int half = (warp - 2) / 4;
-    uint8_t* stage = smem + S::VEC_OFF + epi_vector_bytes(p.N) + (warp - 2) * kStageBytesPerWarp;
+    uint8_t* boxes = smem + S::out_off(p.N) + (warp - 2) * S::OUT_DEPTH * S::OUT_BOX;
+    uint32_t issued = 0;
     int local = 0;
     for (int mb = blockIdx.x; mb < num_m; mb += gridDim.x) {
       bool ok = true;
@@ -211,19 +273,23 @@ __global__ void __launch_bounds__(64 + 32 * EPI + 128, 1)
         tc_fence_after();
         const uint32_t tbase = tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
                                static_cast<uint32_t>(b * S::BN);
-        epi_row_staged<OUT_FP8>(p, ev, tbase, mb * S::BM + q * 32, nb * S::BN, half * kChunks,
-                                (half + 1) * kChunks, stage, lane);
+        epi_tile_tma<OUT_FP8, S::OUT_DEPTH>(p, ev, &tmO, tbase, mb * S::BM + q * 32, nb * S::BN,
+                                            half * kChunks, (half + 1) * kChunks, boxes, lane,
+                                            issued);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(tempty_bar(b));
       }
       if (!ok) break;
     }
+    // the boxes must stay untouched until every store has read them, and the
+    // outputs be written before the kernel ends
+    if (lane == 0) bulk_wait_group<0>();
+    __syncwarp();
   } else if (warp >= kEncWarp0) {
     // ---------------------------------------------------------- encoder
     const int r = threadIdx.x - 32 * kEncWarp0;  // row of the 128-ray block
-    const int used = 3 + 6 * L;                  // 32-bit words of features per row
-    const int words = 32 * kb_count;
+    const int pieces = 8 * kb_count;             // 16-byte pieces per row (8 bf16 each)
     int blk = 0;
     for (int mb = blockIdx.x; mb < num_m; mb += gridDim.x, ++blk) {
       const int a = blk & 1;
@@ -238,21 +304,22 @@ __global__ void __launch_bounds__(64 + 32 * EPI + 128, 1)
         break;
       }
       uint8_t* buf = sA + a * S::A_BUF;
-#pragma unroll
-      for (int w = 0; w < 3; ++w)
-        *reinterpret_cast<uint32_t*>(buf + a_word_offset(r, w)) =
-            epi_pack_bf16x2(e[2 * w], e[2 * w + 1]);
-      int w = 3;
-#pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        for (int k = 0; k < L; ++k, ++w) {
-          float sn, cs;
-          sincospif(ldexpf(e[c], k), &sn, &cs);  // pi 2^k e, the 2^k scaling is exact
-          *reinterpret_cast<uint32_t*>(buf + a_word_offset(r, w)) = epi_pack_bf16x2(sn, cs);
-        }
+      int c = 0, k = 0;
+      // piece 0: the raw ray (6 values) and the first (sin, cos) pair
+      uint4 pc;
+      pc.x = epi_pack_bf16x2(e[0], e[1]);
+      pc.y = epi_pack_bf16x2(e[2], e[3]);
+      pc.z = epi_pack_bf16x2(e[4], e[5]);
+      pc.w = next_pair(e, L, c, k);
+      *reinterpret_cast<uint4*>(buf + a_piece_offset(r, 0)) = pc;
+      for (int qp = 1; qp < pieces; ++qp) {
+        pc.x = next_pair(e, L, c, k);
+        pc.y = next_pair(e, L, c, k);
+        pc.z = next_pair(e, L, c, k);
+        pc.w = next_pair(e, L, c, k);
+        *reinterpret_cast<uint4*>(buf + a_piece_offset(r, qp)) = pc;
       }
-      for (w = used; w < words; ++w) *reinterpret_cast<uint32_t*>(buf + a_word_offset(r, w)) = 0u;
-      fence_proxy_async_smem();  // the MMAs read these words through the async proxy
+      fence_proxy_async_smem();  // the MMAs read these pieces through the async proxy
       __syncwarp();
       if (lane == 0) mbar_arrive(afull_bar(a));
     }
@@ -268,32 +335,34 @@ __global__ void __launch_bounds__(64 + 32 * EPI + 128, 1)
 }
 
 template <bool OUT_FP8, int EPI>
-cudaError_t launch_l1(const CUtensorMap& tmB, RaySoA rays, int L, const TcGemmParams& p, int grid,
-                      cudaStream_t s) {
+cudaError_t launch_l1(const CUtensorMap& tmB, const CUtensorMap& tmO, RaySoA rays, int L,
+                      const TcGemmParams& p, int grid, cudaStream_t s) {
   auto kern = tc_layer1_kernel<OUT_FP8, EPI>;
-  const int smem = l1_smem_bytes(p.N, EPI);
+  const int smem = L1Shape<EPI>::smem_bytes(p.N);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, 64 + 32 * EPI + 128, smem, s>>>(tmB, rays, L, p);
+  kern<<<grid, 64 + 32 * EPI + 128, smem, s>>>(tmB, tmO, rays, L, p);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 bool tc_layer1_supported(int L, int N) {
-  return L >= 1 && 6 + 12 * L <= 64 * L1Shape::KB_MAX && N % L1Shape::BN == 0 &&
-         N <= kMaxStagedColumns && l1_smem_bytes(N, 8) <= 232448;
+  return L >= 1 && 6 + 12 * L <= 64 * L1Shape<4>::KB_MAX && N % L1Shape<4>::BN == 0 &&
+         N <= kMaxStagedColumns && L1Shape<4>::smem_bytes(N) <= 232448 &&
+         L1Shape<8>::smem_bytes(N) <= 232448;
 }
 
-cudaError_t launch_tc_layer1(int epi_warps, bool out_fp8, const CUtensorMap& tmB, RaySoA rays,
-                             int L, const TcGemmParams& p, int grid, cudaStream_t s) {
+cudaError_t launch_tc_layer1(int epi_warps, bool out_fp8, const CUtensorMap& tmB,
+                             const CUtensorMap& tmO, RaySoA rays, int L, const TcGemmParams& p,
+                             int grid, cudaStream_t s) {
   if (!tc_layer1_supported(L, p.N) || p.mode != 0 || p.amax != nullptr || p.m_dev != nullptr ||
-      p.out == nullptr || p.M <= 0 || grid <= 0)
+      p.col_scale != nullptr || p.out == nullptr || p.bias == nullptr || p.M <= 0 || grid <= 0)
     return cudaErrorInvalidValue;
-  if (epi_warps == 4) return out_fp8 ? launch_l1<true, 4>(tmB, rays, L, p, grid, s)
-                                     : launch_l1<false, 4>(tmB, rays, L, p, grid, s);
-  if (epi_warps == 8) return out_fp8 ? launch_l1<true, 8>(tmB, rays, L, p, grid, s)
-                                     : launch_l1<false, 8>(tmB, rays, L, p, grid, s);
+  if (epi_warps == 4) return out_fp8 ? launch_l1<true, 4>(tmB, tmO, rays, L, p, grid, s)
+                                     : launch_l1<false, 4>(tmB, tmO, rays, L, p, grid, s);
+  if (epi_warps == 8) return out_fp8 ? launch_l1<true, 8>(tmB, tmO, rays, L, p, grid, s)
+                                     : launch_l1<false, 8>(tmB, tmO, rays, L, p, grid, s);
   return cudaErrorInvalidValue;
 }
 
