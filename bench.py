@@ -136,20 +136,22 @@ class ClockSampler:
 
 # ------------------------------------------------------------- oracle leg
 
-def oracle_sample(rays, blob, seconds):
-    """Times the FP64 oracle on a bounded prefix of the workload; returns
-    (rays/s, n, exact outputs)."""
+def oracle_sample(rays, blob, seconds, chunk=16384, cap=262144):
+    """Times the FP64 oracle on a bounded prefix of the workload: consecutive
+    chunks of `chunk` rays until `seconds` of CPU time have passed (at most
+    `cap` rays); returns (rays/s, n, elapsed s, exact outputs of the n rays)."""
     from oracle import ddf_oracle as O
-    probe = rays.slice(0, 256)
+    parts = []
+    n = 0
     t0 = time.perf_counter()
-    O.ddf_forward(probe.origins(), probe.dirs(), blob, *NET)
-    dt = time.perf_counter() - t0
-    n = int(min(rays.n, 65536, max(512, seconds / max(dt, 1e-6) * 256)))
-    n -= n % 256
-    sub = rays.slice(0, n)
-    t0 = time.perf_counter()
-    ref = O.ddf_forward(sub.origins(), sub.dirs(), blob, *NET)
+    while n < min(rays.n, cap):
+        sub = rays.slice(n, min(n + chunk, rays.n))
+        parts.append(O.ddf_forward(sub.origins(), sub.dirs(), blob, *NET))
+        n += sub.n
+        if time.perf_counter() - t0 >= seconds:
+            break
     el = time.perf_counter() - t0
+    ref = {k: np.concatenate([p[k] for p in parts]) for k in parts[0]}
     return n / el, n, el, ref
 
 

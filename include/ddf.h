@@ -219,6 +219,34 @@ ddf_status ddf_train_step(ddf_handle h, const float* const rays[6], const float*
                           const uint8_t* hit_target, int64_t batch, float lr, float* out_loss,
                           void* stream);
 
+/* The two halves of ddf_compute_grad, for a loss written elsewhere (the
+ * Python binding wraps them in a torch.autograd.Function):
+ * ddf_forward_train runs the training forward on a bf16 handle (same batch
+ * rules as ddf_compute_grad; inputs = 6 ray arrays, or 3 point arrays for an
+ * SDF field), keeps every activation in the handle and writes the head
+ * outputs before softplus / sigmoid to out_z (device float, batch x 2 row
+ * pairs (z0, z1) for a ray field, batch values for an SDF field).
+ * ddf_backward takes dL/dz in the same layout (device float) and computes
+ * the gradient of every weight and bias into the handle (ddf_get_grad,
+ * ddf_copy_grad). It needs the activations of a ddf_forward_train of the same
+ * batch with no training call, weight load or Adam step in between, and
+ * fails with DDF_ERR_INVALID_ARG otherwise. Both asynchronous on stream. */
+ddf_status ddf_forward_train(ddf_handle h, const float* const inputs[6], int64_t batch,
+                             float* out_z, void* stream);
+ddf_status ddf_backward(ddf_handle h, const float* dz, int64_t batch, void* stream);
+
+/* Copies the last computed gradient (blob layout) to device memory dev_grad
+ * (ddf_param_count floats). Asynchronous on stream. */
+ddf_status ddf_copy_grad(ddf_handle h, float* dev_grad, size_t n_floats, void* stream);
+
+/* Replaces the FP32 master weights of a loaded bf16 handle from a device blob
+ * (same layout and size as ddf_load_weights; values are not checked for
+ * finiteness) and refreshes the bf16 copies every query and training step
+ * uses. Asynchronous on stream; the blob may be reused once the stream has
+ * passed this call. */
+ddf_status ddf_load_weights_device(ddf_handle h, const float* dev_blob, size_t n_floats,
+                                   void* stream);
+
 /* Copies the last computed gradient (weight-blob layout, ddf_param_count
  * floats) to host memory. Synchronous. */
 ddf_status ddf_get_grad(ddf_handle h, float* host_grad, size_t n_floats);

@@ -729,6 +729,9 @@ ddf_status ddf_load_weights(ddf_handle h, const float* host_blob, size_t n_float
       DDF_CK(ddf::launch_pack_f32(w, W, K, l == 0 ? h->kp32 : W, h->wf[l], st));
     } else if (prec == DDF_BF16 || l == 0) {
       DDF_CK(ddf::launch_pack_bf16(w, W, K, l == 0 ? h->kp16 : W, h->wb[l], st));
+      // the transposed copies of a handle that has trained (input gradients)
+      if (prec == DDF_BF16 && l > 0 && static_cast<int>(h->wt.size()) > l && h->wt[l] != nullptr)
+        DDF_CK(ddf::launch_pack_bf16_t(w, W, W, h->wt[l], st));
     } else {
       DDF_CK(ddf::launch_quant_e4m3(w, W, K, W, h->wq[l], h->wscale[l], st));
       DDF_CK(ddf::launch_pack_bf16(w, W, K, W, h->wcal[l], st));
@@ -748,6 +751,7 @@ ddf_status ddf_load_weights(ddf_handle h, const float* host_blob, size_t n_float
   }
   DDF_CK(cudaDeviceSynchronize());
   h->loaded = true;
+  h->fwd_rows = 0;  // kept training activations belong to the old weights
   return DDF_OK;
 }
 

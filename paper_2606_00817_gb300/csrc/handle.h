@@ -98,6 +98,10 @@ struct ddf_s {
   float* adam_v = nullptr;
   int64_t adam_step = 0;
   bool grad_valid = false;
+  // rows of the last ddf_forward_train whose activations are still kept for
+  // ddf_backward (0: none; cleared by anything that changes weights or reuses
+  // the training buffers)
+  int64_t fwd_rows = 0;
   std::vector<__nv_bfloat16*> wt;         // layers 2..H: bf16 W^T [K x W] for input gradients
   std::vector<CUtensorMap> tmBtr;         // weight maps for the plain 1-CTA tile {bn, 4}
   std::vector<CUtensorMap> tmWT;          // maps of wt

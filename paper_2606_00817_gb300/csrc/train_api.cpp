@@ -64,7 +64,8 @@ ddf_status refresh_weights(ddf_s* h, cudaStream_t st) {
     DDF_CK(ddf::launch_pack_bf16(h->d_blob + o.w[l], W, K, l == 0 ? h->kp16 : W, h->wb[l], st));
     DDF_CK(cudaMemcpyAsync(h->bias[l], h->d_blob + o.b[l], W * sizeof(float),
                            cudaMemcpyDeviceToDevice, st));
-    if (l > 0) DDF_CK(ddf::launch_pack_bf16_t(h->d_blob + o.w[l], W, W, h->wt[l], st));
+    if (l > 0 && static_cast<int>(h->wt.size()) > l && h->wt[l] != nullptr)
+      DDF_CK(ddf::launch_pack_bf16_t(h->d_blob + o.w[l], W, W, h->wt[l], st));
   }
   const size_t hr = head_rows(h);
   DDF_CK(cudaMemcpyAsync(h->head_w, h->d_blob + o.wo, hr * W * sizeof(float),
@@ -110,6 +111,7 @@ ddf_status ensure_train(ddf_s* h, int64_t B) {
     DDF_CK(cudaDeviceSynchronize());
   }
   if (B > h->tr_rows) {
+    h->fwd_rows = 0;
     dev_free(h, h->tr_enc);
     for (void* q : h->tr_h) dev_free(h, q);
     dev_free(h, h->tr_dpre[0]);
@@ -175,21 +177,15 @@ ddf_status check_train_args(ddf_s* h, const float* const rays[6], const float* t
   return DDF_OK;
 }
 
-// rays: 6 SoA arrays (ray field) or 3 point arrays (SDF field, in rays[0..2]);
-// t_tgt: first-hit distances (ray field) or signed distances (SDF field);
-// y: hit flags (ray field only).
-ddf_status compute_grad(ddf_s* h, const float* const rays[6], const float* t_tgt,
-                        const uint8_t* y, int64_t B64, float* loss_out, cudaStream_t st) {
+// Forward keeping every activation: encoding, the tensor-core layers, the
+// FP32 head into h->tr_z (float2 per row; .y unused for an SDF field).
+// rays: 6 SoA arrays (ray field) or 3 point arrays (SDF field, in rays[0..2]).
+ddf_status forward_keep(ddf_s* h, const float* const rays[6], int B, cudaStream_t st) {
   const bool sdf = h->cfg.kind == DDF_KIND_SDF;
-  const int hr = static_cast<int>(head_rows(h));
   const int W = h->cfg.width, H = h->cfg.hidden_layers;
-  const int B = static_cast<int>(B64);
-  const BlobOffsets o = blob_offsets(h);
   ddf::RaySoA r;
   for (int c = 0; c < 6; ++c) r.p[c] = rays[c];
   auto bf = [](void* q) { return static_cast<__nv_bfloat16*>(q); };
-
-  // ---- forward, keeping every activation
   {
     ProfScope ps(h, kProfEncode, st);
     if (sdf)
@@ -212,11 +208,16 @@ ddf_status compute_grad(ddf_s* h, const float* const rays[6], const float* t_tgt
     if (s != DDF_OK) return s;
   }
   DDF_CK(ddf::launch_head_train(bf(h->tr_h[H - 1]), B, W, h->head_w, h->head_b, h->tr_z, st));
-  if (sdf)
-    DDF_CK(ddf::launch_sdf_loss(h->tr_z, t_tgt, B, h->tr_dz, h->tr_lpart, loss_out, st));
-  else
-    DDF_CK(ddf::launch_loss(h->tr_z, t_tgt, y, B, h->tr_nhit, kClamp, kLambda, h->tr_dz,
-                            h->tr_lpart, loss_out, st));
+  return DDF_OK;
+}
+
+// Backward from dL/dz in h->tr_dz through the head and every layer, using the
+// activations forward_keep left; the gradient goes to h->grad.
+ddf_status backward_from_dz(ddf_s* h, int B, cudaStream_t st) {
+  const int hr = static_cast<int>(head_rows(h));
+  const int W = h->cfg.width, H = h->cfg.hidden_layers;
+  const BlobOffsets o = blob_offsets(h);
+  auto bf = [](void* q) { return static_cast<__nv_bfloat16*>(q); };
 
   // ---- head: dW_o = dz^T h_H, db_o = sum dz, dpre_H = (dz W_o) where h_H > 0
   DDF_CK(ddf::launch_head_grad(h->tr_dz, bf(h->tr_h[H - 1]), B, W, kColSplits, h->tr_cpart, st));
@@ -278,6 +279,23 @@ ddf_status compute_grad(ddf_s* h, const float* const rays[6], const float* t_tgt
   }
   h->grad_valid = true;
   return DDF_OK;
+}
+
+// rays: 6 SoA arrays (ray field) or 3 point arrays (SDF field, in rays[0..2]);
+// t_tgt: first-hit distances (ray field) or signed distances (SDF field);
+// y: hit flags (ray field only).
+ddf_status compute_grad(ddf_s* h, const float* const rays[6], const float* t_tgt,
+                        const uint8_t* y, int64_t B64, float* loss_out, cudaStream_t st) {
+  const int B = static_cast<int>(B64);
+  h->fwd_rows = 0;  // the kept activations become this batch's
+  ddf_status s = forward_keep(h, rays, B, st);
+  if (s != DDF_OK) return s;
+  if (h->cfg.kind == DDF_KIND_SDF)
+    DDF_CK(ddf::launch_sdf_loss(h->tr_z, t_tgt, B, h->tr_dz, h->tr_lpart, loss_out, st));
+  else
+    DDF_CK(ddf::launch_loss(h->tr_z, t_tgt, y, B, h->tr_nhit, kClamp, kLambda, h->tr_dz,
+                            h->tr_lpart, loss_out, st));
+  return backward_from_dz(h, B, st);
 }
 
 ddf_status train_step(ddf_s* h, const float* const rays[6], const float* t_target,
@@ -365,6 +383,7 @@ ddf_status train_step(ddf_s* h, const float* const rays[6], const float* t_targe
   const float bc2 = static_cast<float>(1.0 - std::pow(0.999, t));
   {
     ProfScope ps(h, kProfHead, st);
+    h->fwd_rows = 0;  // the weights change
     DDF_CK(ddf::launch_adam(h->d_blob, h->grad, h->adam_m, h->adam_v,
                             static_cast<int64_t>(n_params(h)), lr, kB1, kB2, kEps, bc1, bc2, st));
     if ((s = refresh_weights(h, st)) != DDF_OK) return s;
@@ -375,6 +394,76 @@ ddf_status train_step(ddf_s* h, const float* const rays[6], const float* t_targe
 }  // namespace
 
 extern "C" {
+
+ddf_status ddf_forward_train(ddf_handle h, const float* const inputs[6], int64_t batch,
+                             float* out_z, void* stream) {
+  if (h == nullptr) return fail(DDF_ERR_INVALID_ARG, "handle is NULL");
+  const bool sdf = h->cfg.kind == DDF_KIND_SDF;
+  const float* p6[6] = {};
+  for (int c = 0; c < 6 && inputs != nullptr; ++c) p6[c] = inputs[sdf ? c % 3 : c];
+  // the target checks do not apply to a forward pass: pass a dummy target
+  const float dummy = 0.f;
+  const uint8_t ydummy = 0;
+  ddf_status s = check_train_args(h, p6, &dummy, &ydummy, batch, h->cfg.kind);
+  if (s != DDF_OK) return s;
+  if (out_z == nullptr) return fail(DDF_ERR_INVALID_ARG, "out_z is NULL");
+  DeviceGuard g(h->cfg.device);
+  if ((s = ensure_train(h, batch)) != DDF_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  h->fwd_rows = 0;
+  if ((s = forward_keep(h, p6, static_cast<int>(batch), st)) != DDF_OK) return s;
+  if (head_rows(h) == 2) {
+    DDF_CK(cudaMemcpyAsync(out_z, h->tr_z, batch * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+  } else {  // z0 of each float2 into a dense column
+    DDF_CK(cudaMemcpy2DAsync(out_z, sizeof(float), h->tr_z, sizeof(float2), sizeof(float),
+                             batch, cudaMemcpyDeviceToDevice, st));
+  }
+  h->fwd_rows = batch;
+  return DDF_OK;
+}
+
+ddf_status ddf_backward(ddf_handle h, const float* dz, int64_t batch, void* stream) {
+  if (h == nullptr || dz == nullptr) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+  if (h->fwd_rows == 0 || h->fwd_rows != batch)
+    return fail(DDF_ERR_INVALID_ARG,
+                "ddf_backward needs the activations of a ddf_forward_train of the same batch, "
+                "with no weight update or other training call in between");
+  DeviceGuard g(h->cfg.device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (head_rows(h) == 2) {
+    DDF_CK(cudaMemcpyAsync(h->tr_dz, dz, batch * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+  } else {  // (dz, 0) pairs: the unused second head row gets no gradient
+    DDF_CK(cudaMemsetAsync(h->tr_dz, 0, batch * sizeof(float2), st));
+    DDF_CK(cudaMemcpy2DAsync(h->tr_dz, sizeof(float2), dz, sizeof(float), sizeof(float), batch,
+                             cudaMemcpyDeviceToDevice, st));
+  }
+  return backward_from_dz(h, static_cast<int>(batch), st);
+}
+
+ddf_status ddf_copy_grad(ddf_handle h, float* dev_grad, size_t n_floats, void* stream) {
+  if (h == nullptr || dev_grad == nullptr) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+  if (!h->grad_valid) return fail(DDF_ERR_INVALID_ARG, "no gradient computed yet");
+  if (n_floats != n_params(h)) return fail(DDF_ERR_INVALID_ARG, "wrong blob size");
+  DeviceGuard g(h->cfg.device);
+  DDF_CK(cudaMemcpyAsync(dev_grad, h->grad, n_floats * sizeof(float), cudaMemcpyDeviceToDevice,
+                         static_cast<cudaStream_t>(stream)));
+  return DDF_OK;
+}
+
+ddf_status ddf_load_weights_device(ddf_handle h, const float* dev_blob, size_t n_floats,
+                                   void* stream) {
+  if (h == nullptr || dev_blob == nullptr) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+  if (!h->loaded) return fail(DDF_ERR_BAD_WEIGHTS, "load weights once with ddf_load_weights first");
+  if (h->cfg.precision != DDF_BF16)
+    return fail(DDF_ERR_UNSUPPORTED, "device weight updates run on bf16 handles");
+  if (n_floats != n_params(h)) return fail(DDF_ERR_BAD_WEIGHTS, "wrong blob size");
+  DeviceGuard g(h->cfg.device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  h->fwd_rows = 0;
+  DDF_CK(cudaMemcpyAsync(h->d_blob, dev_blob, n_floats * sizeof(float), cudaMemcpyDeviceToDevice,
+                         st));
+  return refresh_weights(h, st);
+}
 
 ddf_status ddf_get_grad(ddf_handle h, float* host_grad, size_t n_floats) {
   if (h == nullptr || host_grad == nullptr) return fail(DDF_ERR_INVALID_ARG, "NULL argument");

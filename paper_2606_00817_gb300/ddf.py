@@ -60,6 +60,10 @@ SIGNATURES = {
     "ddf_calibrate_fp8": (C.c_int, [_vp, _RAYS, _i64, _vp, _vp, _vp]),
     "ddf_compute_grad": (C.c_int, [_vp, _RAYS, _vp, _vp, _i64, _vp, _vp]),
     "ddf_train_step": (C.c_int, [_vp, _RAYS, _vp, _vp, _i64, C.c_float, _vp, _vp]),
+    "ddf_forward_train": (C.c_int, [_vp, _RAYS, _i64, _vp, _vp]),
+    "ddf_backward": (C.c_int, [_vp, _vp, _i64, _vp]),
+    "ddf_copy_grad": (C.c_int, [_vp, _vp, _sz, _vp]),
+    "ddf_load_weights_device": (C.c_int, [_vp, _vp, _sz, _vp]),
     "ddf_get_grad": (C.c_int, [_vp, _vp, _sz]),
     "ddf_reset_optimizer": (C.c_int, [_vp]),
     "ddf_cast_scene": (C.c_int, [_vp, _i32, _vp, _i32, _RAYS, _i64, _vp, _vp, _vp]),
@@ -253,6 +257,24 @@ def ddf_train_step(h, rays, t_target, hit_target, batch, lr, out_loss=None, stre
           _ptr(out_loss), _stream(stream))
 
 
+def ddf_forward_train(h, inputs, batch, out_z, stream=None) -> None:
+    """inputs: 6 ray arrays, or 3 point arrays for an SDF field."""
+    ip, keep = _rays(inputs) if len(inputs) == 6 else _points(inputs)
+    _call("ddf_forward_train", h, ip, int(batch), _ptr(out_z), _stream(stream))
+
+
+def ddf_backward(h, dz, batch, stream=None) -> None:
+    _call("ddf_backward", h, _ptr(dz), int(batch), _stream(stream))
+
+
+def ddf_copy_grad(h, out, stream=None) -> None:
+    _call("ddf_copy_grad", h, _ptr(out), int(out.numel()), _stream(stream))
+
+
+def ddf_load_weights_device(h, blob, stream=None) -> None:
+    _call("ddf_load_weights_device", h, _ptr(blob), int(blob.numel()), _stream(stream))
+
+
 def ddf_get_grad(h, n: int) -> np.ndarray:
     out = np.empty(n, np.float32)
     _call("ddf_get_grad", h, out.ctypes.data, n)
@@ -421,3 +443,54 @@ class DDF:
         out_vis = np.empty(n, np.float32) if out_vis is None else out_vis
         ddf_query_rays_host(self.h, rays_np, n, out_t, out_vis)
         return out_t, out_vis
+
+
+def _autograd_function():
+    import torch
+
+    class DDFFunction(torch.autograd.Function):
+        """z = f_theta(inputs) with theta a flat float32 CUDA tensor in the
+        weight-blob layout: the head outputs before softplus / sigmoid
+        (Sec. 3.1), [B, 2] for a ray field, [B] for an SDF field. Forward
+        and backward are the library's (ddf_forward_train / ddf_backward:
+        tensor-core layers, hand-written backward), so a loss written in
+        torch on z trains the field with any torch optimiser. theta is copied
+        into the handle on every forward; the activations of the latest
+        forward of a handle are the ones its backward uses."""
+
+        @staticmethod
+        def forward(ctx, theta, model, inputs):
+            stream = torch.cuda.current_stream(theta.device)
+            B = inputs[0].numel()
+            ddf_load_weights_device(model.h, theta.detach().contiguous(), stream)
+            hr = 1 if model.cfg.kind == DDF_KIND_SDF else 2
+            z = torch.empty((B, hr) if hr == 2 else (B,), dtype=torch.float32, device=theta.device)
+            ddf_forward_train(model.h, list(inputs), B, z, stream)
+            model._fwd_serial = getattr(model, "_fwd_serial", 0) + 1
+            ctx.model, ctx.batch, ctx.serial, ctx.n = model, B, model._fwd_serial, theta.numel()
+            return z
+
+        @staticmethod
+        def backward(ctx, dz):
+            if ctx.model._fwd_serial != ctx.serial:
+                raise RuntimeError("DDFFunction: another forward ran on this field since; "
+                                   "its activations are gone")
+            stream = torch.cuda.current_stream(dz.device)
+            ddf_backward(ctx.model.h, dz.contiguous().to(torch.float32), ctx.batch, stream)
+            g = torch.empty(ctx.n, dtype=torch.float32, device=dz.device)
+            ddf_copy_grad(ctx.model.h, g, stream)
+            return g, None, None
+
+    return DDFFunction
+
+
+def ddf_function():
+    """The torch.autograd.Function over ddf_forward_train / ddf_backward
+    (created on first use so that importing this module needs no torch)."""
+    global _DDF_FUNCTION
+    if _DDF_FUNCTION is None:
+        _DDF_FUNCTION = _autograd_function()
+    return _DDF_FUNCTION
+
+
+_DDF_FUNCTION = None

@@ -157,3 +157,138 @@ def test_full_size_distillation_lowers_the_loss(torch_cuda):
     w = ddf.ddf_get_weights(m.h, blob.size)
     assert np.all(np.isfinite(w)) and not np.array_equal(w, blob)
     assert ddf.ddf_check_status(m.h) == 0
+
+
+def _torch_loss(torch, z, tt, y):
+    """The distillation loss (Sec. 3.2 / 3.4) written with torch ops on the
+    head outputs: L1 between min(softplus(z0), 4) and min(t*, 4) over hit rays
+    / max(1, N_hit), plus 0.3 x BCE(z1, y) over all rays."""
+    F = torch.nn.functional
+    hit = y.bool()
+    l1 = (torch.clamp(F.softplus(z[:, 0]), max=4.0) - torch.clamp(tt, max=4.0)).abs()
+    n_hit = max(1, int(hit.sum().item()))
+    bce = F.binary_cross_entropy_with_logits(z[:, 1], y.float(), reduction="mean")
+    return l1[hit].sum() / n_hit + 0.3 * bce
+
+
+@pytest.mark.parametrize("net,B", [(SMALL, 4096), (PAPER, 4096)])
+def test_autograd_function_matches_oracle(torch_cuda, net, B):
+    """DDFFunction (library forward + hand-written backward) under a loss
+    written in torch: the gradient torch hands to the weights meets the
+    oracle bounds of test_gradient_matches_oracle and equals the fused
+    ddf_compute_grad gradient up to float32 rounding of dL/dz."""
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    blob = I.xavier_blob(I.NetShape(*net))
+    rays, tt, y = _batch(net, B, seed=42)
+    m = ddf.DDF(*net, precision="bf16")
+    m.load(blob)
+    theta = torch.nn.Parameter(torch.from_numpy(blob).cuda())
+    inputs = _dev(torch, rays.soa())
+    tt_d, y_d = torch.from_numpy(tt).cuda(), torch.from_numpy(y).cuda()
+    z = ddf.ddf_function().apply(theta, m, inputs)
+    assert z.shape == (B, 2)
+    loss = _torch_loss(torch, z, tt_d, y_d)
+    loss.backward()
+    g = theta.grad.double().cpu().numpy()
+    L_emu, g_emu = O.train_grad(rays.origins(), rays.dirs(), blob, *net, tt, y, precision="bf16")
+    _, g_ex = O.ddf_loss_grad(rays.origins(), rays.dirs(), blob, *net, tt, y)
+    assert abs(loss.item() - L_emu) <= 1e-4 * abs(L_emu)
+    for i, (a, b, c) in enumerate(zip(_blocks(g, net), _blocks(g_emu, net), _blocks(g_ex, net))):
+        noise = np.linalg.norm(b - c)
+        assert np.linalg.norm(a - b) <= 0.4 * noise + 1e-3 * np.linalg.norm(b), i
+        assert np.linalg.norm(a - c) <= 1.2 * noise + 1e-3 * np.linalg.norm(c), i
+    ddf.ddf_compute_grad(m.h, inputs, tt_d, y_d, B)
+    g_fused = ddf.ddf_get_grad(m.h, blob.size).astype(np.float64)
+    for a, b in zip(_blocks(g, net), _blocks(g_fused, net)):
+        assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(b)
+    assert ddf.ddf_check_status(m.h) == 0
+
+
+def test_autograd_function_with_torch_adam(torch_cuda):
+    """Three torch.optim.Adam steps through DDFFunction track three library
+    Adam steps (ddf_train_step) on the same batch: both apply
+    w -= lr m_hat / (sqrt(v_hat) + eps). The two gradients differ by bf16
+    rounding noise (the loss's float32 dL/dz differs in the last bits, and the
+    weights after each step do too), which Adam's normalisation passes on to
+    small-gradient parameters; so the weight updates are compared in norm:
+    within 5 % of each other (a sign, step or bias-correction error gives
+    30 % or more), and the loss falls."""
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    net, B, lr = SMALL, 4096, 1e-3
+    blob = I.xavier_blob(I.NetShape(*net))
+    rays, tt, y = _batch(net, B, seed=44)
+    inputs = _dev(torch, rays.soa())
+    tt_d, y_d = torch.from_numpy(tt).cuda(), torch.from_numpy(y).cuda()
+    m = ddf.DDF(*net, precision="bf16")
+    m.load(blob)
+    theta = torch.nn.Parameter(torch.from_numpy(blob).cuda())
+    opt = torch.optim.Adam([theta], lr=lr, betas=(0.9, 0.999), eps=1e-8)
+    losses = []
+    for _ in range(3):
+        opt.zero_grad()
+        loss = _torch_loss(torch, ddf.ddf_function().apply(theta, m, inputs), tt_d, y_d)
+        loss.backward()
+        opt.step()
+        losses.append(loss.item())
+    ref = ddf.DDF(*net, precision="bf16")
+    ref.load(blob)
+    for _ in range(3):
+        ddf.ddf_train_step(ref.h, inputs, tt_d, y_d, B, lr)
+    w0 = blob.astype(np.float64)
+    d_lib = ddf.ddf_get_weights(ref.h, blob.size).astype(np.float64) - w0
+    d_torch = theta.detach().double().cpu().numpy() - w0
+    assert np.linalg.norm(d_lib) > 10 * lr       # the steps moved the weights
+    assert np.linalg.norm(d_torch - d_lib) <= 0.05 * np.linalg.norm(d_lib)
+    assert losses[-1] < losses[0]
+
+
+def test_autograd_function_sdf_and_misuse(torch_cuda):
+    """DDFFunction on an SDF field (z = s, [B]) under an L1 regression loss in
+    torch matches the oracle's SDF gradient bounds; a backward whose
+    activations were replaced by a later forward, or after a weight update,
+    is refused."""
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    net, B = (4, 128, 3), 2048
+    blob = I.xavier_blob_dims(I.sdf_layer_dims(*net))
+    scene = I.random_scene(32, 32, seed=0)
+    p = I.uniform_points(B, seed=53)
+    s_t = O.union_sdf(scene, p.astype(np.float64)).astype(np.float32)
+    m = ddf.DDF(*net, precision="bf16", kind="sdf")
+    m.load(blob)
+    theta = torch.nn.Parameter(torch.from_numpy(blob).cuda())
+    pts = _dev(torch, p.T)
+    z = ddf.ddf_function().apply(theta, m, pts)
+    assert z.shape == (B,)
+    (z - torch.from_numpy(s_t).cuda()).abs().mean().backward()
+    g = theta.grad.double().cpu().numpy()
+    _, g_emu = O.sdf_train_grad(p.astype(np.float64), blob, *net, s_t, precision="bf16")
+    _, g_ex = O.sdf_train_grad(p.astype(np.float64), blob, *net, s_t, precision="exact")
+    off = 0
+    for fo, fi in I.sdf_layer_dims(*net):
+        for n in (fo * fi, fo):
+            a, b, c = g[off:off + n], g_emu[off:off + n], g_ex[off:off + n]
+            off += n
+            noise = np.linalg.norm(b - c)
+            assert np.linalg.norm(a - b) <= 0.4 * noise + 1e-3 * np.linalg.norm(b)
+            assert np.linalg.norm(a - c) <= 1.2 * noise + 1e-3 * np.linalg.norm(c)
+    # misuse: a second forward replaces the first one's activations
+    z1 = ddf.ddf_function().apply(theta, m, pts)
+    z2 = ddf.ddf_function().apply(theta, m, pts)
+    with pytest.raises(RuntimeError):
+        z1.sum().backward()
+    z2.sum().backward()                                   # the latest one is fine
+    # a weight update in between also drops the activations (C-level check)
+    dz = torch.ones(B, device="cuda")
+    out = torch.empty(B, device="cuda")
+    ddf.ddf_forward_train(m.h, pts, B, out)
+    ddf.ddf_sdf_train_step(m.h, pts, torch.from_numpy(s_t).cuda(), B, 1e-3)
+    with pytest.raises(ddf.DDFError):
+        ddf.ddf_backward(m.h, dz, B)
+    ddf.ddf_forward_train(m.h, pts, B, out)
+    with pytest.raises(ddf.DDFError):                     # batch mismatch
+        ddf.ddf_backward(m.h, dz, B - 8)
+    ddf.ddf_backward(m.h, dz, B)
+    assert ddf.ddf_check_status(m.h) == 0
