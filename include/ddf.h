@@ -280,7 +280,9 @@ ddf_status ddf_sdf_eval(ddf_handle h, const float* const points[3], int64_t n, f
  * still active, compacted on the device (no host round trip). Writes out_t
  * (device float[n]: t at the hit, else where the ray stopped), out_hit
  * (device uint8[n]) and out_steps (device int32[n], nullable: evaluations
- * used). n <= the chunk size (ddf_set_chunk_rays). Asynchronous. */
+ * used). n <= the chunk size (ddf_set_chunk_rays); max_steps >= 1, eps > 0
+ * and t_max >= 0 finite (t_max 0: a ray that does not hit at t = 0 is a miss
+ * after its first step). Asynchronous. */
 ddf_status ddf_sphere_trace(ddf_handle h, const float* const rays[6], int64_t n, int32_t max_steps,
                             float eps, float t_max, float* out_t, uint8_t* out_hit,
                             int32_t* out_steps, void* stream);

@@ -510,8 +510,9 @@ ddf_status ddf_sphere_trace(ddf_handle h, const float* const rays[6], int64_t n,
   if ((s = check_rays(rays, n)) != DDF_OK) return s;
   if (n == 0) return DDF_OK;
   if (n > h->chunk) return fail(DDF_ERR_INVALID_ARG, "trace at most chunk_rays rays per call");
-  if (max_steps < 1 || !(eps > 0.f) || !(t_max > 0.f))
-    return fail(DDF_ERR_INVALID_ARG, "max_steps >= 1, eps > 0 and t_max > 0 required");
+  if (max_steps < 1 || !(eps > 0.f) || !std::isfinite(eps) || !(t_max >= 0.f) ||
+      !std::isfinite(t_max))
+    return fail(DDF_ERR_INVALID_ARG, "max_steps >= 1, finite eps > 0 and finite t_max >= 0 required");
   if (out_t == nullptr || out_hit == nullptr) return fail(DDF_ERR_INVALID_ARG, "output is NULL");
   DeviceGuard g(h->cfg.device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
