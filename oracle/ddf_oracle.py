@@ -27,6 +27,7 @@ What the paper fixes and what this module reads into it:
   * Sec. 3.2: supervision from an exact ray cast of the geometry; here the
     geometry is a union of spheres and boxes with closed-form intersections.
   * Sec. 4.4: sphere tracing an SDF is the sequential baseline.
+  * Sec. 3.4: the hash-grid field (readings in its section below).
 
 Reduced-precision modes emulate where the GPU path rounds (bf16 operands,
 or e4m3 operands with per-output-channel weight scales and per-tensor
@@ -475,6 +476,123 @@ def sdf_mlp(p, blob, octaves, width, hidden, precision="exact"):
     dims = [(width, d_in)] + [(width, width)] * (hidden - 1) + [(1, width)]
     layers = split_blob(blob, dims)
     return mlp_forward(encode_points(p, octaves), layers, precision)[:, 0]
+
+
+# ------------------------------------------- hash-grid field (Sec. 3.4)
+#
+# The paper's final field encodes the point x with a multiresolution hash
+# grid (16 levels, 2 features per level, 2^19 entries per level, base
+# resolution 16, growth 1.5, over a box bounding the object), the direction
+# d with four sinusoidal bands, and reads the joined code with a two-layer
+# MLP of width 64. Readings where the paper is silent:
+#   * level resolution N_l = floor(16 * 1.5^l); a level is a grid of
+#     (N_l + 1)^3 vertices over the box [-1, 1]^3 (x clamped into it);
+#   * a level stores min(2^19, (N_l + 1)^3) entries: dense levels index a
+#     vertex (i, j, k) as i + (N+1) (j + (N+1) k), hashed levels with the
+#     spatial hash of the cited multiresolution-hash-encoding work,
+#     (i * 1 xor j * 2654435761 xor k * 805459861) mod 2^19;
+#   * trilinear interpolation of the 8 corner entries of the cell holding x
+#     (cell index clamped to N - 1 at the upper face);
+#   * code = [level 0 features, ..., level 15 features, d, then per
+#     coordinate of d and band k = 0..3: sin(pi 2^k d_c), cos(pi 2^k d_c)]
+#     (59 values), MLP 59 -> 64 -> 64 -> 2 with ReLU, heads as Sec. 3.1;
+#   * blob = the level tables in order (entry-major, features adjacent),
+#     then the MLP as split_blob lays it out.
+
+HG_LEVELS = 16
+HG_FEATURES = 2
+HG_LOG2_T = 19
+HG_BASE = 16
+HG_GROWTH = 1.5
+HG_DIR_BANDS = 4
+HG_PRIMES = (1, 2654435761, 805459861)
+
+
+def hashgrid_resolutions(levels=HG_LEVELS, base=HG_BASE, growth=HG_GROWTH):
+    """N_l = floor(base * growth^l) cells per axis for l = 0..levels-1."""
+    return [int(np.floor(base * growth ** l)) for l in range(levels)]
+
+
+def hashgrid_table_sizes(levels=HG_LEVELS, log2_t=HG_LOG2_T, base=HG_BASE, growth=HG_GROWTH):
+    """Entries per level: every vertex while they fit, else 2^log2_t."""
+    return [min(2 ** log2_t, (n + 1) ** 3) for n in hashgrid_resolutions(levels, base, growth)]
+
+
+def hashgrid_index(ijk, res, size, log2_t=HG_LOG2_T):
+    """Table row of integer vertices ijk [n, 3] on a level with res cells
+    per axis and `size` entries: dense row-major index if every vertex has
+    its own entry, else the spatial hash taken modulo 2^log2_t."""
+    ijk = np.asarray(ijk, np.int64)
+    if (res + 1) ** 3 <= size:
+        return ijk[:, 0] + (res + 1) * (ijk[:, 1] + (res + 1) * ijk[:, 2])
+    u = ijk.astype(np.uint64)
+    h = (u[:, 0] * np.uint64(HG_PRIMES[0])) ^ (u[:, 1] * np.uint64(HG_PRIMES[1])) \
+        ^ (u[:, 2] * np.uint64(HG_PRIMES[2]))
+    return (h & np.uint64((1 << log2_t) - 1)).astype(np.int64)
+
+
+def hashgrid_encode(x, tables, resolutions, log2_t=HG_LOG2_T, lo=-1.0, hi=1.0):
+    """Multiresolution hash encoding of points x [n, 3]: per level the
+    trilinear interpolation of the level table ([T_l, F]) over the 8 corners
+    of the cell holding x. Returns [n, levels * F] float64."""
+    x01 = np.clip((np.asarray(x, F64) - lo) / (hi - lo), 0.0, 1.0)
+    feats = []
+    for table, res in zip(tables, resolutions):
+        table = np.asarray(table, F64)
+        u = x01 * res
+        i0 = np.minimum(np.floor(u), res - 1).astype(np.int64)
+        w = u - i0
+        f = np.zeros((x01.shape[0], table.shape[1]))
+        for corner in range(8):
+            c = np.array([(corner >> a) & 1 for a in range(3)])
+            wt = np.prod(np.where(c[None, :] == 1, w, 1.0 - w), axis=1)
+            idx = hashgrid_index(i0 + c[None, :], res, table.shape[0], log2_t)
+            f += wt[:, None] * table[idx]
+        feats.append(f)
+    return np.concatenate(feats, axis=1)
+
+
+def encode_dir(d, bands=HG_DIR_BANDS):
+    """Sinusoidal encoding of a direction: d, then per coordinate c and band
+    k: sin(pi 2^k d_c), cos(pi 2^k d_c). Returns [n, 3 + 6 bands]."""
+    d = np.asarray(d, F64)
+    out = [d]
+    for c in range(3):
+        for k in range(bands):
+            arg = np.pi * np.ldexp(d[:, c], k)
+            out += [np.sin(arg)[:, None], np.cos(arg)[:, None]]
+    return np.concatenate(out, axis=1)
+
+
+def hashgrid_mlp_dims(width=64, hidden=2, bands=HG_DIR_BANDS):
+    d_in = HG_LEVELS * HG_FEATURES + 3 + 6 * bands
+    return [(width, d_in)] + [(width, width)] * (hidden - 1) + [(2, width)]
+
+
+def hashgrid_split(blob, width=64, hidden=2, bands=HG_DIR_BANDS):
+    """(level tables [T_l, F], MLP layers) from a hash-grid field blob."""
+    blob = np.asarray(blob)
+    tables, off = [], 0
+    for t in hashgrid_table_sizes():
+        tables.append(blob[off:off + t * HG_FEATURES].reshape(t, HG_FEATURES).astype(F64))
+        off += t * HG_FEATURES
+    return tables, split_blob(blob[off:], hashgrid_mlp_dims(width, hidden, bands))
+
+
+def hashgrid_forward(o, d, blob, width=64, hidden=2, bands=HG_DIR_BANDS, precision="exact"):
+    """Query of the hash-grid DDF: f(x, d) = (t, xi) from the joined code
+    [hash features of x, encoded d]. precision "bf16" rounds the table
+    entries to bfloat16 (interpolation stays float64) and runs the MLP as
+    mlp_forward's bf16 mode. Returns dict(t, vis, z)."""
+    tables, layers = hashgrid_split(blob, width, hidden, bands)
+    if precision == "bf16":
+        tables = [round_bf16(t) for t in tables]
+    elif precision != "exact":
+        raise ValueError(precision)
+    code = np.concatenate([hashgrid_encode(o, tables, hashgrid_resolutions()),
+                           encode_dir(d, bands)], axis=1)
+    z = mlp_forward(code, layers, precision)
+    return {"t": softplus(z[:, 0]), "vis": sigmoid(z[:, 1]), "z": z}
 
 
 # ----------------------------------------------------------- queries

@@ -1,0 +1,139 @@
+"""Pins of the oracle's hash-grid field (Sec. 3.4) against values that do not
+come from the oracle itself: the paper's layout figures, hand-computed spatial
+hashes, affine fields that trilinear interpolation must reproduce exactly,
+table entries at grid vertices, continuity across cell faces, clamping, and
+the direction encoding's special values."""
+import json
+import os
+
+import numpy as np
+
+from oracle import ddf_oracle as O
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _load(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+def test_layout_matches_the_paper():
+    g = _load("hashgrid_layout.json")
+    assert O.hashgrid_resolutions() == g["resolutions"]
+    assert O.hashgrid_table_sizes() == g["table_sizes"]
+    assert sum(O.hashgrid_table_sizes()) == g["table_entries"]
+    assert 2 * g["table_entries"] == g["table_params"]
+    assert sum(fo * fi + fo for fo, fi in O.hashgrid_mlp_dims()) == g["mlp_params"]
+    # "about 13M parameters", "52 MB" of float32
+    assert 12.5e6 < g["table_params"] < 13.5e6
+    assert 51e6 < 4 * (g["table_params"] + g["mlp_params"]) < 53e6
+
+
+def test_spatial_hash_hand_values():
+    g = _load("hashgrid_spatial_hash.json")
+    ijk = np.array([v["ijk"] for v in g["vertices"]])
+    got = O.hashgrid_index(ijk, res=81, size=1 << 19)       # level 4: hashed
+    assert got.tolist() == [v["hash"] for v in g["vertices"]]
+
+
+def test_dense_index_is_row_major():
+    res = 16
+    ijk = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [16, 16, 16]])
+    got = O.hashgrid_index(ijk, res, (res + 1) ** 3)
+    assert got.tolist() == [0, 1, 17, 289, 17 ** 3 - 1]
+
+
+def test_dense_levels_reproduce_affine_fields():
+    """Trilinear interpolation reproduces any affine function of position, so
+    tables holding a . v + b at every vertex v (normalised to [0, 1]^3) give
+    features a . x01 + b at every point: pins the corner enumeration, the
+    weights and the dense indexing together."""
+    rng = np.random.default_rng(0)
+    res = O.hashgrid_resolutions()[:4]
+    a = rng.normal(size=(2, 3))
+    b = rng.normal(size=2)
+    tables = []
+    for n in res:
+        g = np.arange(n + 1)
+        k, j, i = np.meshgrid(g, g, g, indexing="ij")          # row-major: i fastest
+        v = np.stack([i.ravel(), j.ravel(), k.ravel()], 1) / n
+        tables.append(v @ a.T + b)
+    x = rng.uniform(-1, 1, size=(500, 3))
+    x[:4] = [[-1, -1, -1], [1, 1, 1], [1, -1, 0.3], [0, 0, 0]]   # faces and corners
+    f = O.hashgrid_encode(x, tables, res)
+    want = ((x + 1) / 2) @ a.T + b
+    for lvl in range(4):
+        assert np.abs(f[:, 2 * lvl:2 * lvl + 2] - want).max() < 1e-12
+
+
+def test_hashed_level_vertices_read_their_entry():
+    """A point on a grid vertex of a hashed level reads exactly the entry the
+    hand-checked hash picks."""
+    g = _load("hashgrid_spatial_hash.json")
+    res = 81
+    table = np.random.default_rng(1).normal(size=(1 << 19, 2))
+    for v in g["vertices"]:
+        x = (np.array(v["ijk"], float) / res) * 2 - 1
+        f = O.hashgrid_encode(x[None, :], [table], [res])
+        assert np.array_equal(f[0], table[v["hash"]])
+
+
+def test_continuity_across_cell_faces_and_clamping():
+    res = [81, 7006]
+    rng = np.random.default_rng(2)
+    tables = [rng.normal(size=(1 << 19, 2)) for _ in res]
+    bound = 8 * np.abs(np.stack(tables)).max()   # |d feature / d x01| <= 2 N max|entry| x 4
+    for n in res:
+        face = (37 / n) * 2 - 1                                   # x on a cell face
+        base = np.array([[face, 0.123, -0.456]])
+        jumps = []
+        for eps in (1e-6, 1e-9):
+            lo = O.hashgrid_encode(base - [eps, 0, 0], tables, res)
+            hi = O.hashgrid_encode(base + [eps, 0, 0], tables, res)
+            jumps.append(np.abs(lo - hi).max())
+            assert jumps[-1] <= eps * max(res) * bound      # Lipschitz, no jump at the face
+        assert jumps[1] <= 2e-3 * jumps[0] + 1e-12          # shrinks with eps (linear)
+    inside = rng.uniform(-1, 1, size=(50, 3))
+    outside = inside.copy()
+    outside[:, 0] = np.where(inside[:, 0] > 0, 3.0, -3.0)
+    clamped = inside.copy()
+    clamped[:, 0] = np.where(inside[:, 0] > 0, 1.0, -1.0)
+    assert np.array_equal(O.hashgrid_encode(outside, tables, res),
+                          O.hashgrid_encode(clamped, tables, res))
+
+
+def test_direction_encoding_special_values():
+    d = np.array([[1.0, 0.0, 0.5]])
+    e = O.encode_dir(d, 4)
+    assert e.shape == (1, 27)
+    assert np.array_equal(e[0, :3], d[0])
+    sx, cx = e[0, 3:11:2], e[0, 4:12:2]          # coordinate x = 1, bands 0..3
+    assert np.allclose(sx, 0, atol=1e-15) and np.allclose(cx, [-1, 1, 1, 1])
+    sy, cy = e[0, 11:19:2], e[0, 12:20:2]        # coordinate y = 0
+    assert np.array_equal(sy, np.zeros(4)) and np.array_equal(cy, np.ones(4))
+    sz = e[0, 19:27:2]                           # z = 0.5: sin(pi/2) = 1, sin(pi) = 0, ...
+    assert np.allclose(sz, [1, 0, 0, 0], atol=1e-15)
+
+
+def test_forward_reads_the_code_in_order():
+    """An MLP that passes code entry j straight to z0 (ReLU-safe: positive
+    tables and directions) returns exactly that entry: level l feature f at
+    j = 2 l + f, then the direction encoding from j = 32."""
+    tables_sizes = O.hashgrid_table_sizes()
+    rng = np.random.default_rng(3)
+    tables = [rng.uniform(0.5, 1.5, size=(t, 2)) for t in tables_sizes]
+    o = rng.uniform(-1, 1, size=(20, 3))
+    d = np.abs(rng.normal(size=(20, 3)))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    code = np.concatenate([O.hashgrid_encode(o, tables, O.hashgrid_resolutions()),
+                           O.encode_dir(d)], axis=1)
+    for j in (0, 5, 31, 32, 34):
+        dims = O.hashgrid_mlp_dims()
+        w1 = np.zeros(dims[0]); w1[0, j] = 1.0
+        w2 = np.zeros(dims[1]); w2[0, 0] = 1.0
+        wo = np.zeros(dims[2]); wo[0, 0] = 1.0
+        mlp = [w1, np.zeros(64), w2, np.zeros(64), wo, np.zeros(2)]
+        blob = np.concatenate([t.ravel() for t in tables] + [m.ravel() for m in mlp])
+        z = O.hashgrid_forward(o, d, blob)["z"]
+        assert np.allclose(z[:, 0], code[:, j], rtol=1e-13, atol=0), j
