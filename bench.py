@@ -23,6 +23,8 @@ events on the launching stream, 3 timed repetitions after warm-up):
                  steps from the 64-sphere scene's union SDF, traced on
                  1,048,576 one-bounce rays (<= 128 steps, eps 1e-3), against
                  one DDF pass over the same rays
+  hashgrid       the paper's final field (hash grid + 2x64 MLP, 52 MB) on the
+                 same 4,194,304 shadow rays, bf16 and FP32
 """
 from __future__ import annotations
 
@@ -62,7 +64,9 @@ def parse():
     ap.add_argument("--tile", default="auto", help="auto (autotune), or BNxEPI[pair][staged|fused] for every layer, or "
                          "HIDDEN,FIRST, e.g. 256x4pairstaged,256x4fused")
     ap.add_argument("--no-workloads", action="store_true",
-                    help="skip the AO / distillation / sphere-tracing measurements")
+                    help="skip the AO / distillation / sphere-tracing / hash-grid measurements")
+    ap.add_argument("--workloads", default="ao,train,trace,hashgrid",
+                    help="comma list of the secondary measurements to run")
     return ap.parse_args()
 
 
@@ -216,11 +220,51 @@ def _scene_buffers(torch, dev, scene):
             torch.from_numpy(box).to(dev), len(scene.box_lo))
 
 
-def workloads(torch, ddf, dev, local, stream, flush, blob):
-    """The ragged AO, distillation and sphere-tracing measurements."""
+def hashgrid_workload(torch, ddf, dev, local, stream, flush, d_rays, R):
+    """The paper's final field (Sec. 3.4): hash grid (16 levels x 2 features,
+    2^19 entries, base 16, growth 1.5) + 4-band direction code + 59 -> 64 ->
+    64 -> 2 MLP, on the benchmark's shadow rays, bf16 and FP32."""
+    cfg = ddf.make_config(4, 64, 2, kind="hashgrid")
+    n = ddf.ddf_param_count(cfg)
+    mlp_dims = [(64, ddf.HASHGRID_CODE), (64, 64), (2, 64)]
+    hblob = I.hashgrid_blob(n, mlp_dims, seed=0)
+    res = {"params": int(n), "field_mb_fp32": 4 * n / 1e6, "rays": R}
+    t = torch.empty(R, device=dev)
+    v = torch.empty(R, device=dev)
+    occ = torch.empty(R, dtype=torch.uint8, device=dev)
+    for prec in ("bf16", "fp32"):
+        m = ddf.DDF(4, 64, 2, precision=prec, device=local, kind="hashgrid")
+        m.load(hblob)
+        ms = _time_ms(torch, stream, lambda: ddf.ddf_query_shadow(m.h, d_rays, R, LIGHT, t, v, occ,
+                                                                  stream),
+                      reps=5, warm=2, flush=flush)
+        res[prec] = {"ms_per_step": ms, "rays_per_s": R / (ms / 1e3),
+                     "status": ddf.ddf_check_status(m.h)}
+        m.close()
+    # gather traffic: 16 levels x 8 corners x one 4-byte bf16 entry pair per
+    # ray, plus 24 B of ray and 9 B of outputs; the 26 MB bf16 table stays in L2
+    per_ray = 16 * 8 * 4 + 24 + 9
+    res["bytes_per_ray_algorithmic"] = per_ray
+    res["achieved_gbs_algorithmic"] = per_ray * res["bf16"]["rays_per_s"] / 1e9
+    res["speedup_bf16_vs_fp32"] = res["fp32"]["ms_per_step"] / res["bf16"]["ms_per_step"]
+    return res
+
+
+def workloads(torch, ddf, dev, local, stream, flush, blob, which):
+    """The ragged AO, distillation and sphere-tracing measurements (those
+    named in `which`)."""
     out = {}
     scene = I.random_scene(64, 0, seed=0)
+    if "ao" in which:
+        out["ao_fp8_graph"] = _ao_workload(torch, ddf, dev, local, stream, blob, scene)
+    if "train" in which:
+        out["distillation"] = _train_workload(torch, ddf, dev, local, stream, blob)
+    if "trace" in which:
+        out["sphere_trace"] = _trace_workload(torch, ddf, dev, local, stream, flush, blob, scene)
+    return out
 
+
+def _ao_workload(torch, ddf, dev, local, stream, blob, scene):
     # ragged AO, e4m3, graph replay
     P = 1024 * 1024
     rays, offsets = I.ao_rays(scene, P, seed=0)
@@ -238,13 +282,15 @@ def workloads(torch, ddf, dev, local, stream, flush, blob):
     n_ao = int(offsets[-1])
     ms = _time_ms(torch, stream, lambda: ddf.ddf_query_ao(f8.h, d_rays, n_ao, d_off, P, hard, soft,
                                                           stream), warm=2)
-    out["ao_fp8_graph"] = {"rays": n_ao, "points": P, "ms_per_step": ms,
-                           "rays_per_s": n_ao / (ms / 1e3), "points_per_s": P / (ms / 1e3),
-                           "mean_soft_visibility": float(soft.mean().item()),
-                           "status": ddf.ddf_check_status(f8.h)}
+    res = {"rays": n_ao, "points": P, "ms_per_step": ms,
+           "rays_per_s": n_ao / (ms / 1e3), "points_per_s": P / (ms / 1e3),
+           "mean_soft_visibility": float(soft.mean().item()),
+           "status": ddf.ddf_check_status(f8.h)}
     f8.close()
-    del d_rays, d_off, hard, soft
+    return res
 
+
+def _train_workload(torch, ddf, dev, local, stream, blob):
     # distillation steps: GPU caster targets + loss + backward + Adam
     B = 65536
     tscene = I.random_scene(32, 32, seed=0)
@@ -271,15 +317,19 @@ def workloads(torch, ddf, dev, local, stream, flush, blob):
         first = first if first is not None else float(loss.item())
     reps = 20
     ms = _time_ms(torch, stream, lambda: [train_step() for _ in range(reps)], reps=1, warm=0) / reps
-    out["distillation"] = {"batch": B, "ms_per_step": ms, "steps_per_s": 1e3 / ms,
+    res = {"batch": B, "ms_per_step": ms, "steps_per_s": 1e3 / ms,
                            "rays_per_s": B / (ms / 1e3),
                            "tflops_6_b_params": 6.0 * B * I.NetShape(*NET).n_params / (ms / 1e3) / 1e12,
                            "loss_first": first, "loss_after": float(loss.item()),
                            "steps_taken": it[0], "status": ddf.ddf_check_status(tr.h)}
     tr.close()
-    del pool
+    return res
 
+
+def _trace_workload(torch, ddf, dev, local, stream, flush, blob, scene):
     # sphere tracing an SDF network of the same size vs one DDF pass
+    B = 65536
+    loss = torch.zeros(1, device=dev)
     SDF = (10, 1280, 8)
     sblob = I.xavier_blob_dims(I.sdf_layer_dims(*SDF))
     sm = ddf.DDF(*SDF, precision="bf16", device=local, kind="sdf")
@@ -316,7 +366,7 @@ def workloads(torch, ddf, dev, local, stream, flush, blob):
     dv = torch.empty(N, device=dev)
     ddf_ms = _time_ms(torch, stream, lambda: ddf.ddf_query_rays(dm.h, d_br, N, dt_, dv, stream),
                       flush=flush)
-    out["sphere_trace"] = {
+    res = {
         "rays": N, "max_steps": 128, "eps": 1e-3, "t_max": 4.0,
         "sdf_params": int(sblob.size), "ddf_params": int(blob.size),
         "sdf_distill": {"steps": train_steps, "batch": B, "seconds": sdf_train_s,
@@ -335,7 +385,7 @@ def workloads(torch, ddf, dev, local, stream, flush, blob):
         "status": [ddf.ddf_check_status(sm.h), ddf.ddf_check_status(dm.h)]}
     sm.close()
     dm.close()
-    return out
+    return res
 
 
 def main():
@@ -532,7 +582,10 @@ def main():
 
     extra = None
     if rank == 0 and not args.no_workloads:
-        extra = workloads(torch, ddf, dev, local, stream, flush, blob)
+        which = set(args.workloads.split(","))
+        extra = workloads(torch, ddf, dev, local, stream, flush, blob, which)
+        if "hashgrid" in which:
+            extra["hashgrid"] = hashgrid_workload(torch, ddf, dev, local, stream, flush, d_rays, R)
 
     # CPU baseline (the FP64 oracle on a bounded prefix) + accuracy of the GPU outputs on it
     cpu = None

@@ -72,8 +72,23 @@ typedef enum {
  *                  above, 2 outputs); DDF_KIND_SDF: a signed distance field of
  *                  a point p (the sphere-tracing baseline of Sec. 4.4): input
  *                  [px,py,pz, per coordinate and band sin(pi 2^k p_c),
- *                  cos(pi 2^k p_c)] (D_in = 3 + 6 L), one raw output; bf16 only */
-typedef enum { DDF_KIND_RAY = 0, DDF_KIND_SDF = 1 } ddf_kind;
+ *                  cos(pi 2^k p_c)] (D_in = 3 + 6 L), one raw output; bf16 only;
+ *                  DDF_KIND_HASHGRID: the paper's final field (Sec. 3.4), a
+ *                  ray field whose origin is encoded by a multiresolution hash
+ *                  grid (16 levels x 2 features, 2^19 entries per level, base
+ *                  resolution 16, growth 1.5, over the box [-1,1]^3, origins
+ *                  clamped into it) and whose direction by `octaves` = 4
+ *                  sinusoidal bands; code = [level 0..15 features, d, per
+ *                  coordinate and band sin, cos] (59 values); `width` = 64,
+ *                  1..4 hidden layers; bf16 (bf16 table and MLP on tensor
+ *                  cores, FP32 head) or FP32. Level l has N = floor(16 1.5^l)
+ *                  cells per axis; it stores every vertex (i + (N+1)(j +
+ *                  (N+1) k)) while (N+1)^3 <= 2^19, else 2^19 entries indexed
+ *                  by (i xor j * 2654435761 xor k * 805459861) mod 2^19; a
+ *                  point reads the trilinear interpolation of its cell's 8
+ *                  corners. Ray queries (ddf_query_*) accept it; tiles,
+ *                  FP8 and training do not. */
+typedef enum { DDF_KIND_RAY = 0, DDF_KIND_SDF = 1, DDF_KIND_HASHGRID = 2 } ddf_kind;
 
 typedef struct {
   int32_t octaves;
@@ -87,7 +102,10 @@ typedef struct {
 /* Number of floats in the weight blob of cfg (0 if cfg is invalid).
  * Blob layout: for each layer in order, W[out][in] row-major then b[out];
  * layers are D_in->W, (H-1) x W->W, then the head W->2 whose row 0 feeds
- * t = softplus(z0) and row 1 feeds xi = sigmoid(z1). */
+ * t = softplus(z0) and row 1 feeds xi = sigmoid(z1). A hash-grid field puts
+ * its level tables first (level 0..15, entry-major, the 2 features of an
+ * entry adjacent; 13,058,044 floats), then the MLP laid out as above with
+ * D_in = 59. */
 size_t ddf_param_count(const ddf_config* cfg);
 
 /* Creates a handle on cfg->device. *out receives the handle (NULL on error).

@@ -106,13 +106,20 @@ bool valid_config(const ddf_config* c, std::string* why) {
   if (c->precision < DDF_FP32 || c->precision > DDF_FP8_E4M3)
     return *why = "unknown precision", false;
   if (c->device < 0) return *why = "device must be >= 0", false;
-  if (c->kind != DDF_KIND_RAY && c->kind != DDF_KIND_SDF) return *why = "unknown kind", false;
+  if (c->kind != DDF_KIND_RAY && c->kind != DDF_KIND_SDF && c->kind != DDF_KIND_HASHGRID)
+    return *why = "unknown kind", false;
   if (c->kind == DDF_KIND_SDF && c->precision != DDF_BF16)
     return *why = "SDF fields run in bf16 only", false;
+  if (c->kind == DDF_KIND_HASHGRID) {
+    if (c->octaves != 4 || c->width != 64 || c->hidden_layers > 4)
+      return *why = "hash-grid fields: 4 direction bands, width 64, 1..4 hidden layers", false;
+    if (c->precision == DDF_FP8_E4M3) return *why = "hash-grid fields run in bf16 or FP32", false;
+  }
   return true;
 }
 
 size_t input_width(const ddf_config& c) {
+  if (c.kind == DDF_KIND_HASHGRID) return 59;  // 16 levels x 2 features + 27 direction values
   return c.kind == DDF_KIND_SDF ? 3 + 6 * static_cast<size_t>(c.octaves)
                                 : 6 + 12 * static_cast<size_t>(c.octaves);
 }
@@ -120,6 +127,7 @@ size_t input_width(const ddf_config& c) {
 size_t head_rows(const ddf_config& c) { return c.kind == DDF_KIND_SDF ? 1 : 2; }
 
 size_t param_count(const ddf_config& c) {
+  if (c.kind == DDF_KIND_HASHGRID) return hg_param_count(c);
   const size_t d_in = input_width(c);
   const size_t W = c.width;
   const size_t hr = head_rows(c);
@@ -142,7 +150,7 @@ int max_partials(int W) { return (W / 128) * 2; }
 void clear_graphs(ddf_s* h);
 
 ddf_status ensure_workspace(ddf_s* h, int64_t rows) {
-  if (rows <= h->ws_rows) return DDF_OK;
+  if (rows <= h->ws_rows || h->cfg.kind == DDF_KIND_HASHGRID) return DDF_OK;  // no workspace
   clear_graphs(h);  // cached graphs point at the old buffers
   dev_free(h, h->ws_enc);
   dev_free(h, h->ws_act[0]);
@@ -308,7 +316,9 @@ ddf_status check_rays(const float* const rays[6], int64_t n) {
 ddf_status check_ready(ddf_s* h, int kind = DDF_KIND_RAY) {
   if (h == nullptr) return fail(DDF_ERR_INVALID_ARG, "handle is NULL");
   if (!h->loaded) return fail(DDF_ERR_BAD_WEIGHTS, "no weights loaded");
-  if (h->cfg.kind != kind)
+  const bool match = h->cfg.kind == kind ||
+                     (kind == DDF_KIND_RAY && h->cfg.kind == DDF_KIND_HASHGRID);  // ray queries
+  if (!match)
     return fail(DDF_ERR_INVALID_ARG, kind == DDF_KIND_RAY ? "not a ray (DDF) field"
                                                           : "not an SDF field");
   if (h->cfg.precision == DDF_FP8_E4M3 && h->cfg.hidden_layers > 1 && !h->scales_set)
@@ -324,6 +334,7 @@ ddf_status run_query(ddf_s* h, const float* const rays[6], int64_t n, ddf::HeadO
   ddf::RaySoA r;
   for (int c = 0; c < 6; ++c) r.p[c] = rays[c];
   out.rays = r;
+  if (h->cfg.kind == DDF_KIND_HASHGRID) return hg_query(h, r, n, out, st);  // no chunks needed
   for (int64_t off = 0; off < n; off += h->chunk) {
     const int m = static_cast<int>(std::min<int64_t>(h->chunk, n - off));
     const ddf::RaySoA rc = shift_rays(r, off);
@@ -581,9 +592,10 @@ ddf_status ddf_create(const ddf_config* cfg, ddf_handle* out) {
   *out = nullptr;
   std::string why;
   if (!valid_config(cfg, &why)) return fail(DDF_ERR_INVALID_ARG, why);
-  if (cfg->precision != DDF_FP32 && cfg->width % 128 != 0)
+  const bool layered = cfg->kind != DDF_KIND_HASHGRID;
+  if (layered && cfg->precision != DDF_FP32 && cfg->width % 128 != 0)
     return fail(DDF_ERR_UNSUPPORTED, "tensor-core precisions need width % 128 == 0");
-  if (cfg->precision != DDF_FP32 && cfg->width > 2048)
+  if (layered && cfg->precision != DDF_FP32 && cfg->width > 2048)
     return fail(DDF_ERR_UNSUPPORTED, "tensor-core precisions support width <= 2048");
   int ndev = 0;
   DDF_CK(cudaGetDeviceCount(&ndev));
@@ -607,7 +619,7 @@ ddf_status ddf_create(const ddf_config* cfg, ddf_handle* out) {
   h->bn = (cfg->width % 256 == 0) ? 256 : 128;
   h->tile = ddf::TcTile{h->bn, 4};
   h->tile_first = h->tile;
-  if (cfg->precision != DDF_FP32 && cfg->width % 256 == 0)
+  if (layered && cfg->precision != DDF_FP32 && cfg->width % 256 == 0)
     h->pair_clusters = std::min(ddf::tc_gemm_pair_max_clusters(false),
                                 ddf::tc_gemm_pair_max_clusters(true));
   cudaError_t e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, cfg->device);
@@ -658,6 +670,11 @@ ddf_status ddf_load_weights(ddf_handle h, const float* host_blob, size_t n_float
     if (!std::isfinite(host_blob[i]))
       return fail(DDF_ERR_BAD_WEIGHTS, "non-finite weight at index " + std::to_string(i));
   DeviceGuard g(h->cfg.device);
+  if (h->cfg.kind == DDF_KIND_HASHGRID) {
+    const ddf_status r = hg_load(h, host_blob);
+    if (r == DDF_OK) h->loaded = true;
+    return r;
+  }
   const int W = h->cfg.width, H = h->cfg.hidden_layers;
   const int prec = h->cfg.precision;
   cudaStream_t st = nullptr;
@@ -1070,6 +1087,8 @@ ddf_status ddf_profile_read(ddf_handle h, double ms[4], int64_t launches[4]) {
 ddf_status ddf_set_tile(ddf_handle h, int32_t which, const ddf_tile* tile) {
   if (h == nullptr || tile == nullptr) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
   if (which != 0 && which != 1) return fail(DDF_ERR_INVALID_ARG, "which must be 0 or 1");
+  if (h->cfg.kind == DDF_KIND_HASHGRID)
+    return fail(DDF_ERR_UNSUPPORTED, "hash-grid fields have one kernel shape");
   const int bn = tile->bn, ew = tile->epi_warps;
   if ((bn != 128 && bn != 256) || (ew != 4 && ew != 8))
     return fail(DDF_ERR_INVALID_ARG, "bn must be 128 or 256 and epi_warps 4 or 8");
@@ -1143,7 +1162,8 @@ ddf_status ddf_autotune(ddf_handle h, const float* const rays[6], int64_t n, voi
     return fail(DDF_ERR_INVALID_ARG, "ms_out needs 16 entries");
   if (ms_out != nullptr)
     for (int i = 0; i < kMsSlots; ++i) ms_out[i] = -1.0;
-  if (h->cfg.precision == DDF_FP32) return DDF_OK;  // one FP32 kernel shape, nothing to choose
+  if (h->cfg.precision == DDF_FP32 || h->cfg.kind == DDF_KIND_HASHGRID)
+    return DDF_OK;  // one kernel shape, nothing to choose
   DeviceGuard g(h->cfg.device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   float* buf = nullptr;

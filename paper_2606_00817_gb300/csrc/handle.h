@@ -15,6 +15,15 @@
 
 struct ddf_s {
   ddf_config cfg{};
+  // hash-grid field (kind DDF_KIND_HASHGRID): level layout, the level tables
+  // (bf16x2 or float2 entries), the swizzled MLP operand images, FP32 biases
+  // and head, and the query grid (CTAs) of the tensor-core kernel
+  ddf::HashGridParams hg{};
+  int64_t hg_entries = 0;
+  void* hg_table = nullptr;
+  uint8_t* hg_img = nullptr;
+  float* hg_bias = nullptr;
+  int hg_grid = 0;
   int d_in = 0;
   int kp32 = 0;  // padded encoded width, FP32 rows (multiple of 8)
   int kp16 = 0;  // padded encoded width, bf16 rows (multiple of 8 -> 16-byte rows)
@@ -171,5 +180,12 @@ ddf::RaySoA shift_rays(ddf::RaySoA r, int64_t off);
 // Builds h->tmBtr (bf16 weight maps for the plain 1-CTA tile) once.
 ddf_status ensure_plain_maps(ddf_s* h);
 int64_t round_up(int64_t x, int64_t m);
+
+// hash-grid field (hashgrid_api.cpp)
+// Level layout; even_offsets pads each level to start on an even entry.
+ddf::HashGridParams hg_layout(int64_t* entries, bool even_offsets);
+size_t hg_param_count(const ddf_config& c);
+ddf_status hg_load(ddf_s* h, const float* host_blob);
+ddf_status hg_query(ddf_s* h, ddf::RaySoA rays, int64_t n, ddf::HeadOut out, cudaStream_t st);
 
 }  // namespace ddfi

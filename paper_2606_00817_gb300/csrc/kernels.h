@@ -136,6 +136,32 @@ cudaError_t launch_head_f32(const float* H, int M, int W, const float* wo, const
 cudaError_t launch_finish_heads(const float2* part, int nblk, int M, const float* bo, HeadOut o,
                                 cudaStream_t s);
 
+// ---- the hash-grid field (hashgrid.cu) ----
+// Level layout of the multiresolution hash grid (Sec. 3.4): per level the
+// cells per axis, whether every vertex has its own entry (dense row-major
+// index) or the spatial hash picks one (mod mask + 1), and the first entry.
+struct HashGridParams {
+  int res[16];
+  int dense[16];
+  uint32_t offset[16];
+  uint32_t mask;
+};
+// Tensor-core query: table = bf16x2 entries, w_img = H swizzled 64 x 64 bf16
+// operand images (layer 1 zero-padded from 59 inputs), bias [H x 64], head_w
+// [2 x 64], head_b [2] FP32. grid = CTAs (each loops over 128-ray tiles).
+cudaError_t launch_hashgrid_tc(const HashGridParams& g, const uint32_t* table,
+                               const uint8_t* w_img, const float* bias, const float* head_w,
+                               const float* head_b, int H, RaySoA rays, int64_t M, HeadOut out,
+                               uint32_t* status, uint64_t timeout_ns, int grid, cudaStream_t s);
+int hashgrid_tc_blocks_per_sm(int H);
+int hashgrid_smem_bytes(int H);
+// FP32 query: table = (f0, f1) float pairs, mlp = the blob's MLP part.
+cudaError_t launch_hashgrid_f32(const HashGridParams& g, const float2* table, const float* mlp,
+                                int H, RaySoA rays, int64_t M, HeadOut out, cudaStream_t s);
+cudaError_t launch_hg_pack_table(const float* src, int64_t n_entries, uint32_t* dst,
+                                 cudaStream_t s);
+cudaError_t launch_hg_pack_image(const float* w, int K, uint8_t* img, cudaStream_t s);
+
 // Ambient occlusion (Sec. 3.3): for point p with rays [offsets[p], offsets[p+1])
 // hard[p] = 1 - mean(hit), soft[p] = 1 - mean(vis); empty sets give 1.
 cudaError_t launch_ao_reduce(const uint8_t* hit, const float* vis, const int32_t* offsets,

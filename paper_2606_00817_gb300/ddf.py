@@ -33,8 +33,11 @@ class Tile(C.Structure):
                 ("staged", C.c_int32), ("fused_encode", C.c_int32)]
 
 
-DDF_KIND_RAY, DDF_KIND_SDF = 0, 1
-KINDS = {"ray": DDF_KIND_RAY, "sdf": DDF_KIND_SDF}
+DDF_KIND_RAY, DDF_KIND_SDF, DDF_KIND_HASHGRID = 0, 1, 2
+KINDS = {"ray": DDF_KIND_RAY, "sdf": DDF_KIND_SDF, "hashgrid": DDF_KIND_HASHGRID}
+# hash-grid field (Sec. 3.4): 4 direction bands, width 64; its MLP reads a
+# 59-value code (16 levels x 2 features + 27 direction values)
+HASHGRID_CODE = 59
 
 
 class Config(C.Structure):

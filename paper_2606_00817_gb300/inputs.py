@@ -33,6 +33,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 
 # stream ids: one per independent random quantity
 S_ORIGIN, S_DIR, S_WEIGHTS, S_SCENE, S_POINTS, S_COUNTS, S_HEMI, S_TARGET = range(1, 9)
+S_TABLE = 15
 
 
 def _mix(z: np.ndarray) -> np.ndarray:
@@ -178,6 +179,18 @@ def xavier_blob_dims(dims, seed: int = 0) -> np.ndarray:
         parts.append(uniform(seed, S_WEIGHTS, fo, -bb, bb, offset=off))
         off += fo
     return np.ascontiguousarray(np.concatenate(parts).astype(np.float32))
+
+
+def hashgrid_blob(n_params: int, mlp_dims, seed: int = 0, table_scale: float = 1.0) -> np.ndarray:
+    """Float32 blob of a hash-grid field: the level tables (everything before
+    the MLP) uniform in +-table_scale, then Xavier MLP layers with the given
+    (fan_out, fan_in) dims."""
+    mlp = xavier_blob_dims(mlp_dims, seed)
+    n_tab = n_params - mlp.size
+    if n_tab <= 0:
+        raise ValueError("n_params leaves no room for the tables")
+    tab = uniform(seed, S_TABLE, n_tab, -table_scale, table_scale)
+    return np.ascontiguousarray(np.concatenate([tab.astype(np.float32), mlp]))
 
 
 def uniform_points(n: int, lo: float = -1.2, hi: float = 1.2, seed: int = 0) -> np.ndarray:
