@@ -267,10 +267,11 @@ def loss_and_dz(z, t_target, hit_target, clamp=LOSS_CLAMP, lam=LOSS_CE_WEIGHT):
     return L, dz
 
 
-def mlp_backward(x0, layers, dz, precision="exact"):
+def mlp_backward(x0, layers, dz, precision="exact", return_dx=False):
     """Gradient of sum(dz * z) w.r.t. every weight and bias (reverse-mode
     chain rule through the linear layers and ReLUs; ReLU'(0) = 0).
-    Returns a list [(dW, db)] matching ``layers``."""
+    Returns a list [(dW, db)] matching ``layers`` (and the gradient w.r.t.
+    the input x0 if return_dx)."""
     z, pres, acts = mlp_forward(x0, layers, precision, keep=True)
     grads = [None] * len(layers)
     wo, _ = layers[-1]
@@ -282,6 +283,8 @@ def mlp_backward(x0, layers, dz, precision="exact"):
         dpre = dh * (pres[l] > 0)
         grads[l] = (dpre.T @ acts[l], dpre.sum(axis=0))
         dh = dpre @ w
+    if return_dx:
+        return grads, dh
     return grads
 
 
@@ -577,6 +580,58 @@ def hashgrid_split(blob, width=64, hidden=2, bands=HG_DIR_BANDS):
         tables.append(blob[off:off + t * HG_FEATURES].reshape(t, HG_FEATURES).astype(F64))
         off += t * HG_FEATURES
     return tables, split_blob(blob[off:], hashgrid_mlp_dims(width, hidden, bands))
+
+
+def hashgrid_encode_backward(x, dfeat, table_sizes, resolutions, log2_t=HG_LOG2_T, lo=-1.0,
+                             hi=1.0):
+    """Gradient of sum(dfeat * hashgrid_encode(x)) w.r.t. every level table:
+    each of a point's 8 corner entries receives its interpolation weight
+    times the point's feature gradient (summed over points sharing an entry).
+    dfeat [n, levels * F]. Returns [T_l, F] arrays."""
+    x01 = np.clip((np.asarray(x, F64) - lo) / (hi - lo), 0.0, 1.0)
+    dfeat = np.asarray(dfeat, F64)
+    out = []
+    for l, (size, res) in enumerate(zip(table_sizes, resolutions)):
+        g = np.zeros((size, HG_FEATURES))
+        u = x01 * res
+        i0 = np.minimum(np.floor(u), res - 1).astype(np.int64)
+        w = u - i0
+        df = dfeat[:, HG_FEATURES * l:HG_FEATURES * (l + 1)]
+        for corner in range(8):
+            c = np.array([(corner >> a) & 1 for a in range(3)])
+            wt = np.prod(np.where(c[None, :] == 1, w, 1.0 - w), axis=1)
+            idx = hashgrid_index(i0 + c[None, :], res, size, log2_t)
+            np.add.at(g, idx, wt[:, None] * df)
+        out.append(g)
+    return out
+
+
+def hashgrid_field_loss_grad(o, d, tables, resolutions, layers, t_target, hit_target,
+                             bands=HG_DIR_BANDS, log2_t=HG_LOG2_T):
+    """Distillation loss (loss_and_dz) of a hash-grid field given as level
+    tables, resolutions and MLP layers, and its gradient: the MLP by
+    mlp_backward, the tables by hashgrid_encode_backward of the code
+    gradient's hash-feature part. Everything in float64. Returns (L, [table
+    gradients], [(dW, db)])."""
+    code = np.concatenate([hashgrid_encode(o, tables, resolutions, log2_t),
+                           encode_dir(d, bands)], axis=1)
+    z = mlp_forward(code, layers)
+    L, dz = loss_and_dz(z, t_target, hit_target)
+    grads, dcode = mlp_backward(code, layers, dz, return_dx=True)
+    nf = len(tables) * HG_FEATURES
+    dtab = hashgrid_encode_backward(o, dcode[:, :nf], [t.shape[0] for t in tables], resolutions,
+                                    log2_t)
+    return L, dtab, grads
+
+
+def hashgrid_loss_grad(o, d, blob, t_target, hit_target, width=64, hidden=2, bands=HG_DIR_BANDS):
+    """hashgrid_field_loss_grad for a blob in the paper's layout; the
+    gradient comes back flat in the blob layout (tables, then the MLP)."""
+    tables, layers = hashgrid_split(blob, width, hidden, bands)
+    L, dtab, grads = hashgrid_field_loss_grad(o, d, tables, hashgrid_resolutions(), layers,
+                                              t_target, hit_target, bands)
+    flat = [t.ravel() for t in dtab] + [np.concatenate([g.ravel(), gb]) for g, gb in grads]
+    return L, np.concatenate(flat)
 
 
 def hashgrid_forward(o, d, blob, width=64, hidden=2, bands=HG_DIR_BANDS, precision="exact"):

@@ -137,3 +137,72 @@ def test_forward_reads_the_code_in_order():
         blob = np.concatenate([t.ravel() for t in tables] + [m.ravel() for m in mlp])
         z = O.hashgrid_forward(o, d, blob)["z"]
         assert np.allclose(z[:, 0], code[:, j], rtol=1e-13, atol=0), j
+
+
+def _tiny_field(rng):
+    """Two levels: a dense 3^3-vertex grid and a hashed one (res 5, 16
+    entries); MLP 4 + 27 -> 6 -> 6 -> 2."""
+    res = [2, 5]
+    sizes = [27, 16]
+    tables = [rng.normal(size=(s, 2)) for s in sizes]
+    dims = [(6, 4 + 27), (6, 6), (2, 6)]
+    layers = [(rng.normal(size=dims[i]) * 0.6, rng.normal(size=dims[i][0]) * 0.3)
+              for i in range(3)]
+    return res, tables, layers
+
+
+def test_hashgrid_gradient_matches_central_differences():
+    """Every table entry and every MLP parameter of a tiny field (a dense and
+    a hashed level, with collisions) against central differences of the
+    loss."""
+    rng = np.random.default_rng(11)
+    res, tables, layers = _tiny_field(rng)
+    n = 40
+    o = rng.uniform(-1.1, 1.1, size=(n, 3))
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    tt = rng.uniform(0.2, 3.0, n)
+    y = rng.integers(0, 2, n)
+    f = lambda tb, ly: O.hashgrid_field_loss_grad(o, d, tb, res, ly, tt, y, log2_t=4)
+    L0, dtab, grads = f(tables, layers)
+    h = 1e-6
+    got, fd = [], []
+    for l in range(2):
+        for i in range(tables[l].size):
+            tp = [t.copy() for t in tables]
+            tm = [t.copy() for t in tables]
+            tp[l].flat[i] += h
+            tm[l].flat[i] -= h
+            fd.append((f(tp, layers)[0] - f(tm, layers)[0]) / (2 * h))
+            got.append(dtab[l].flat[i])
+    for li in range(3):
+        for which in range(2):
+            arr = layers[li][which]
+            for i in range(arr.size):
+                lp = [(w.copy(), b.copy()) for w, b in layers]
+                lm = [(w.copy(), b.copy()) for w, b in layers]
+                lp[li][which].flat[i] += h
+                lm[li][which].flat[i] -= h
+                fd.append((f(tables, lp)[0] - f(tables, lm)[0]) / (2 * h))
+                got.append(grads[li][which].flat[i])
+    fd, got = np.array(fd), np.array(got)
+    err = np.abs(fd - got) / np.maximum(1e-6, np.abs(got))
+    assert np.median(err) < 1e-6
+    assert np.mean(err < 1e-4) > 0.98
+    assert np.count_nonzero(np.array(got[:27 * 2 + 16 * 2])) > 40   # the tables do get gradient
+
+
+def test_hashgrid_table_gradient_is_a_weighted_scatter():
+    """Feature gradient 1 on one point: its 8 corners of a dense level receive
+    exactly their trilinear weights (which sum to 1)."""
+    x = np.array([[0.1, -0.35, 0.62]])
+    res = [4]
+    dfeat = np.array([[1.0, 0.0]])
+    g = O.hashgrid_encode_backward(x, dfeat, [125], res)[0]
+    assert abs(g[:, 0].sum() - 1.0) < 1e-15 and np.count_nonzero(g[:, 0]) == 8
+    assert np.all(g[:, 1] == 0)
+    u = (x[0] + 1) / 2 * 4
+    i0 = np.floor(u).astype(int)
+    w = u - i0
+    corner = g[i0[0] + 5 * (i0[1] + 5 * i0[2]), 0]       # the (0,0,0) corner
+    assert abs(corner - (1 - w[0]) * (1 - w[1]) * (1 - w[2])) < 1e-15
