@@ -213,16 +213,22 @@ ddf_status ddf_set_graph_mode(ddf_handle h, int32_t on);
 ddf_status ddf_calibrate_fp8(ddf_handle h, const float* const rays[6], int64_t n, float* amax_out,
                              float* scales_out, void* stream);
 
-/* ---- distillation (Sec. 3.2 / 3.4), bf16 handles only ----
+/* ---- distillation (Sec. 3.2 / 3.4) ----
  * One batch of rays with targets: t_target (device float[batch], the exact
  * first-hit distance; ignored where hit_target is 0, may be +inf there) and
  * hit_target (device uint8[batch], 1 = the ray hits the scene). The loss is
  *   L = (1/max(1, N_hit)) sum_{hit} |min(t, 4) - min(t*, 4)|
- *       + 0.3 (1/B) sum_i [softplus(z1) - y z1],     t = softplus(z0),
- * computed from bf16 activations and FP32 head/loss arithmetic; gradients
- * use bf16 operands with FP32 accumulation. batch: positive multiple of 8,
- * below 2^31. out_loss: device float, nullable. Asynchronous on stream; the
- * handle keeps every activation (8 + 4 W + ... bytes per ray and layer). */
+ *       + 0.3 (1/B) sum_i [softplus(z1) - y z1],     t = softplus(z0).
+ * Sinusoidal ray fields (bf16 handles only): bf16 activations, FP32 head and
+ * loss, gradients from bf16 operands with FP32 accumulation; the handle keeps
+ * every activation (2 W bytes per ray and layer, plus the same again for the
+ * input gradients and transposes). Hash-grid fields (bf16 or FP32 handles):
+ * forward and backward in FP32 on the master weights; the level tables'
+ * gradient is a scatter of each ray's feature gradient into its 8 corner
+ * entries per level (atomic adds, so its last bits may vary from run to run);
+ * a bf16 handle's query copies are refreshed after each Adam step.
+ * batch: positive multiple of 8, below 2^31. out_loss: device float,
+ * nullable. Asynchronous on stream. */
 
 /* Gradient of the batch loss w.r.t. every weight and bias, kept in the
  * handle (read it with ddf_get_grad); the weights do not change. */

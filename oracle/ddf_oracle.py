@@ -495,7 +495,11 @@ def sdf_mlp(p, blob, octaves, width, hidden, precision="exact"):
 #     spatial hash of the cited multiresolution-hash-encoding work,
 #     (i * 1 xor j * 2654435761 xor k * 805459861) mod 2^19;
 #   * trilinear interpolation of the 8 corner entries of the cell holding x
-#     (cell index clamped to N - 1 at the upper face);
+#     (cell index clamped to N - 1 at the upper face); `positions="fp32"`
+#     takes the cell and in-cell coordinates from float32 arithmetic, as a
+#     float32 implementation picks them (at N = 7006 a float32 box
+#     coordinate moves u by up to 4e-4 of a cell, and with it every ReLU
+#     decision downstream of the features);
 #   * code = [level 0 features, ..., level 15 features, d, then per
 #     coordinate of d and band k = 0..3: sin(pi 2^k d_c), cos(pi 2^k d_c)]
 #     (59 values), MLP 59 -> 64 -> 64 -> 2 with ReLU, heads as Sec. 3.1;
@@ -534,18 +538,35 @@ def hashgrid_index(ijk, res, size, log2_t=HG_LOG2_T):
     return (h & np.uint64((1 << log2_t) - 1)).astype(np.int64)
 
 
-def hashgrid_encode(x, tables, resolutions, log2_t=HG_LOG2_T, lo=-1.0, hi=1.0):
+def hashgrid_cell(x, res, positions="exact", lo=-1.0, hi=1.0):
+    """Cell index i0 [n, 3] and in-cell coordinates w [n, 3] of points x on a
+    level with `res` cells per axis (x clamped into the box). positions
+    "fp32" takes the box coordinate (x + 1) / 2 and its product with res in
+    float32, as a float32 implementation does, so that both pick the same
+    cell and weights; "exact" computes in float64."""
+    if positions == "fp32":
+        f = np.float32
+        x01 = np.clip((np.asarray(x, f) + f(1.0)) * f(0.5), f(0.0), f(1.0))
+        u = (x01 * f(res)).astype(F64)
+    elif positions == "exact":
+        x01 = np.clip((np.asarray(x, F64) - lo) / (hi - lo), 0.0, 1.0)
+        u = x01 * res
+    else:
+        raise ValueError(positions)
+    i0 = np.minimum(np.floor(u), res - 1).astype(np.int64)
+    return i0, u - i0
+
+
+def hashgrid_encode(x, tables, resolutions, log2_t=HG_LOG2_T, lo=-1.0, hi=1.0,
+                    positions="exact"):
     """Multiresolution hash encoding of points x [n, 3]: per level the
     trilinear interpolation of the level table ([T_l, F]) over the 8 corners
     of the cell holding x. Returns [n, levels * F] float64."""
-    x01 = np.clip((np.asarray(x, F64) - lo) / (hi - lo), 0.0, 1.0)
     feats = []
     for table, res in zip(tables, resolutions):
         table = np.asarray(table, F64)
-        u = x01 * res
-        i0 = np.minimum(np.floor(u), res - 1).astype(np.int64)
-        w = u - i0
-        f = np.zeros((x01.shape[0], table.shape[1]))
+        i0, w = hashgrid_cell(x, res, positions, lo, hi)
+        f = np.zeros((i0.shape[0], table.shape[1]))
         for corner in range(8):
             c = np.array([(corner >> a) & 1 for a in range(3)])
             wt = np.prod(np.where(c[None, :] == 1, w, 1.0 - w), axis=1)
@@ -583,19 +604,16 @@ def hashgrid_split(blob, width=64, hidden=2, bands=HG_DIR_BANDS):
 
 
 def hashgrid_encode_backward(x, dfeat, table_sizes, resolutions, log2_t=HG_LOG2_T, lo=-1.0,
-                             hi=1.0):
+                             hi=1.0, positions="exact"):
     """Gradient of sum(dfeat * hashgrid_encode(x)) w.r.t. every level table:
     each of a point's 8 corner entries receives its interpolation weight
     times the point's feature gradient (summed over points sharing an entry).
     dfeat [n, levels * F]. Returns [T_l, F] arrays."""
-    x01 = np.clip((np.asarray(x, F64) - lo) / (hi - lo), 0.0, 1.0)
     dfeat = np.asarray(dfeat, F64)
     out = []
     for l, (size, res) in enumerate(zip(table_sizes, resolutions)):
         g = np.zeros((size, HG_FEATURES))
-        u = x01 * res
-        i0 = np.minimum(np.floor(u), res - 1).astype(np.int64)
-        w = u - i0
+        i0, w = hashgrid_cell(x, res, positions, lo, hi)
         df = dfeat[:, HG_FEATURES * l:HG_FEATURES * (l + 1)]
         for corner in range(8):
             c = np.array([(corner >> a) & 1 for a in range(3)])
@@ -607,34 +625,36 @@ def hashgrid_encode_backward(x, dfeat, table_sizes, resolutions, log2_t=HG_LOG2_
 
 
 def hashgrid_field_loss_grad(o, d, tables, resolutions, layers, t_target, hit_target,
-                             bands=HG_DIR_BANDS, log2_t=HG_LOG2_T):
+                             bands=HG_DIR_BANDS, log2_t=HG_LOG2_T, positions="exact"):
     """Distillation loss (loss_and_dz) of a hash-grid field given as level
     tables, resolutions and MLP layers, and its gradient: the MLP by
     mlp_backward, the tables by hashgrid_encode_backward of the code
     gradient's hash-feature part. Everything in float64. Returns (L, [table
     gradients], [(dW, db)])."""
-    code = np.concatenate([hashgrid_encode(o, tables, resolutions, log2_t),
+    code = np.concatenate([hashgrid_encode(o, tables, resolutions, log2_t, positions=positions),
                            encode_dir(d, bands)], axis=1)
     z = mlp_forward(code, layers)
     L, dz = loss_and_dz(z, t_target, hit_target)
     grads, dcode = mlp_backward(code, layers, dz, return_dx=True)
     nf = len(tables) * HG_FEATURES
     dtab = hashgrid_encode_backward(o, dcode[:, :nf], [t.shape[0] for t in tables], resolutions,
-                                    log2_t)
+                                    log2_t, positions=positions)
     return L, dtab, grads
 
 
-def hashgrid_loss_grad(o, d, blob, t_target, hit_target, width=64, hidden=2, bands=HG_DIR_BANDS):
+def hashgrid_loss_grad(o, d, blob, t_target, hit_target, width=64, hidden=2, bands=HG_DIR_BANDS,
+                       positions="exact"):
     """hashgrid_field_loss_grad for a blob in the paper's layout; the
     gradient comes back flat in the blob layout (tables, then the MLP)."""
     tables, layers = hashgrid_split(blob, width, hidden, bands)
     L, dtab, grads = hashgrid_field_loss_grad(o, d, tables, hashgrid_resolutions(), layers,
-                                              t_target, hit_target, bands)
+                                              t_target, hit_target, bands, positions=positions)
     flat = [t.ravel() for t in dtab] + [np.concatenate([g.ravel(), gb]) for g, gb in grads]
     return L, np.concatenate(flat)
 
 
-def hashgrid_forward(o, d, blob, width=64, hidden=2, bands=HG_DIR_BANDS, precision="exact"):
+def hashgrid_forward(o, d, blob, width=64, hidden=2, bands=HG_DIR_BANDS, precision="exact",
+                     positions="exact"):
     """Query of the hash-grid DDF: f(x, d) = (t, xi) from the joined code
     [hash features of x, encoded d]. precision "bf16" rounds the table
     entries to bfloat16 (interpolation stays float64) and runs the MLP as
@@ -644,7 +664,7 @@ def hashgrid_forward(o, d, blob, width=64, hidden=2, bands=HG_DIR_BANDS, precisi
         tables = [round_bf16(t) for t in tables]
     elif precision != "exact":
         raise ValueError(precision)
-    code = np.concatenate([hashgrid_encode(o, tables, hashgrid_resolutions()),
+    code = np.concatenate([hashgrid_encode(o, tables, hashgrid_resolutions(), positions=positions),
                            encode_dir(d, bands)], axis=1)
     z = mlp_forward(code, layers, precision)
     return {"t": softplus(z[:, 0]), "vis": sigmoid(z[:, 1]), "z": z}

@@ -24,6 +24,11 @@ struct ddf_s {
   uint8_t* hg_img = nullptr;
   float* hg_bias = nullptr;
   int hg_grid = 0;
+  ddf::HashGridParams hg_blob{};  // the master blob's (unpadded) level layout
+  int64_t hg_blob_entries = 0;
+  float* hg_code = nullptr;   // training: [B x 64] codes
+  float* hg_acts = nullptr;   // training: [H x B x 64] hidden activations
+  float* hg_dpre = nullptr;   // training: [H x B x 64] dL/d(pre-activation)
   int d_in = 0;
   int kp32 = 0;  // padded encoded width, FP32 rows (multiple of 8)
   int kp16 = 0;  // padded encoded width, bf16 rows (multiple of 8 -> 16-byte rows)
@@ -111,6 +116,7 @@ struct ddf_s {
   // ddf_backward (0: none; cleared by anything that changes weights or reuses
   // the training buffers)
   int64_t fwd_rows = 0;
+  ddf::RaySoA fwd_rays{};  // the inputs of that forward (a hash grid's backward re-reads them)
   std::vector<__nv_bfloat16*> wt;         // layers 2..H: bf16 W^T [K x W] for input gradients
   std::vector<CUtensorMap> tmBtr;         // weight maps for the plain 1-CTA tile {bn, 4}
   std::vector<CUtensorMap> tmWT;          // maps of wt
@@ -181,11 +187,27 @@ ddf::RaySoA shift_rays(ddf::RaySoA r, int64_t off);
 ddf_status ensure_plain_maps(ddf_s* h);
 int64_t round_up(int64_t x, int64_t m);
 
+// Distillation loss and optimiser constants (Sec. 3.2 / 3.4): L1 clamp at
+// the box scale, cross-entropy weight 0.3, Adam (0.9, 0.999, 1e-8).
+constexpr float kLossClamp = 4.0f;
+constexpr float kLossLambda = 0.3f;
+constexpr float kAdamB1 = 0.9f, kAdamB2 = 0.999f, kAdamEps = 1e-8f;
+
 // hash-grid field (hashgrid_api.cpp)
 // Level layout; even_offsets pads each level to start on an even entry.
 ddf::HashGridParams hg_layout(int64_t* entries, bool even_offsets);
 size_t hg_param_count(const ddf_config& c);
 ddf_status hg_load(ddf_s* h, const float* host_blob);
 ddf_status hg_query(ddf_s* h, ddf::RaySoA rays, int64_t n, ddf::HeadOut out, cudaStream_t st);
+// Training (FP32 on the master blob): forward keeping the code and every
+// activation (z into tr_z), backward from tr_dz into h->grad, and the whole
+// step (loss, gradient, optional Adam with lr > 0 and the bf16 refresh).
+ddf_status hg_forward_keep(ddf_s* h, ddf::RaySoA rays, int B, cudaStream_t st);
+ddf_status hg_backward(ddf_s* h, ddf::RaySoA rays, int B, cudaStream_t st);
+ddf_status hg_train(ddf_s* h, ddf::RaySoA rays, const float* t_target, const uint8_t* hit_target,
+                    int B, float lr, float* out_loss, cudaStream_t st);
+ddf_status hg_ensure_train(ddf_s* h, int64_t B);
+// Rewrites a bf16 field's query copies from the FP32 master blob (on st).
+ddf_status hg_refresh(ddf_s* h, cudaStream_t st);
 
 }  // namespace ddfi

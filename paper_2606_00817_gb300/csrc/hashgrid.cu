@@ -291,11 +291,14 @@ constexpr int kHgF32Rays = 64;  // rays per block
 constexpr int kHgLd = kHgW + 1; // per-thread row stride in shared memory
 
 // Thread = ray: code and activations in a per-thread shared-memory row,
-// weights broadcast from shared memory, FFMA only.
+// weights broadcast from shared memory, FFMA only. The training variant also
+// stores the code [B x 64], every hidden activation ([H x B x 64]) and z.
+template <bool TRAIN>
 __global__ void __launch_bounds__(kHgF32Rays)
     hashgrid_f32_kernel(const HashGridParams g, const float2* __restrict__ table,
                         const float* __restrict__ mlp, int H, RaySoA rays, int64_t M,
-                        HeadOut out) {
+                        HeadOut out, float* __restrict__ code_out, float* __restrict__ acts,
+                        float2* __restrict__ z_out) {
   extern __shared__ float fsm[];
   const int n_mlp = kHgW * kHgCode + kHgW + (H - 1) * (kHgW * kHgW + kHgW) + 2 * kHgW + 2;
   float* sw = fsm;
@@ -317,6 +320,9 @@ __global__ void __launch_bounds__(kHgF32Rays)
   hg_dir_code(rays.p[3][row], rays.p[4][row], rays.p[5][row], dcode);
 #pragma unroll
   for (int k = 0; k < 27; ++k) a[32 + k] = dcode[k];
+  if constexpr (TRAIN) {
+    for (int k = 0; k < kHgW; ++k) code_out[row * kHgW + k] = k < kHgCode ? a[k] : 0.f;
+  }
   const float* w = sw;
   int K = kHgCode;
   for (int l = 0; l < H; ++l) {
@@ -325,6 +331,10 @@ __global__ void __launch_bounds__(kHgF32Rays)
       float s = 0.f;
       for (int k = 0; k < K; ++k) s = fmaf(a[k], w[n * K + k], s);
       nb[n] = fmaxf(s + b[n], 0.f);
+    }
+    if constexpr (TRAIN) {
+      float* dst = acts + (static_cast<int64_t>(l) * M + row) * kHgW;
+      for (int n = 0; n < kHgW; ++n) dst[n] = nb[n];
     }
     float* t = a;
     a = nb;
@@ -337,7 +347,103 @@ __global__ void __launch_bounds__(kHgF32Rays)
     z0 = fmaf(a[k], w[k], z0);
     z1 = fmaf(a[k], w[kHgW + k], z1);
   }
-  write_heads(out, row, z0 + w[2 * kHgW], z1 + w[2 * kHgW + 1]);
+  z0 += w[2 * kHgW];
+  z1 += w[2 * kHgW + 1];
+  if constexpr (TRAIN) {
+    z_out[row] = make_float2(z0, z1);
+  } else {
+    write_heads(out, row, z0, z1);
+  }
+}
+
+// Backward of one ray (FP32): from dL/dz through the head and the hidden
+// layers (ReLU masks from the stored activations), storing every dL/dpre for
+// the weight gradients, then the hash features' gradient scattered into the
+// level tables' gradient (blob layout): each corner entry receives its
+// trilinear weight times the feature gradient (atomic adds; entries shared by
+// several rays or corners sum up).
+__global__ void __launch_bounds__(kHgF32Rays)
+    hg_train_bwd_kernel(const HashGridParams g, const float* __restrict__ mlp, int H, RaySoA rays,
+                        int64_t M, const float* __restrict__ acts, const float2* __restrict__ dz,
+                        float* __restrict__ dpre, float* __restrict__ grad_table) {
+  extern __shared__ float fsm[];
+  const int n_mlp = kHgW * kHgCode + kHgW + (H - 1) * (kHgW * kHgW + kHgW) + 2 * kHgW + 2;
+  float* sw = fsm;
+  float* bufA = fsm + ((n_mlp + 3) & ~3);
+  float* bufB = bufA + kHgF32Rays * kHgLd;
+  for (int i = threadIdx.x; i < n_mlp; i += blockDim.x) sw[i] = mlp[i];
+  __syncthreads();
+  const int64_t row = static_cast<int64_t>(blockIdx.x) * kHgF32Rays + threadIdx.x;
+  if (row >= M) return;
+  float* dh = bufA + threadIdx.x * kHgLd;
+  float* dn = bufB + threadIdx.x * kHgLd;
+  // weight offsets: layer l's W [64 x K_l] and b, then the head W_o [2 x 64], b_o
+  int woff[4];
+  int off = 0;
+  for (int l = 0; l < H; ++l) {
+    woff[l] = off;
+    off += kHgW * (l == 0 ? kHgCode : kHgW) + kHgW;
+  }
+  const float* wo = sw + off;
+  const float2 d = dz[row];
+  for (int k = 0; k < kHgW; ++k) dh[k] = d.x * wo[k] + d.y * wo[kHgW + k];
+  for (int l = H - 1; l >= 0; --l) {
+    const float* h = acts + (static_cast<int64_t>(l) * M + row) * kHgW;
+    float* dp = dpre + (static_cast<int64_t>(l) * M + row) * kHgW;
+    for (int k = 0; k < kHgW; ++k) {
+      const float v = h[k] > 0.f ? dh[k] : 0.f;
+      dh[k] = v;
+      dp[k] = v;
+    }
+    const int K = l == 0 ? 2 * 16 : kHgW;  // layer 1: only the hash features need a gradient
+    const int ldw = l == 0 ? kHgCode : kHgW;
+    const float* w = sw + woff[l];
+    for (int j = 0; j < K; ++j) {
+      float s = 0.f;
+      for (int n = 0; n < kHgW; ++n) s = fmaf(dh[n], w[n * ldw + j], s);
+      dn[j] = s;
+    }
+    float* t = dh;
+    dh = dn;
+    dn = t;
+  }
+  // dh now holds dL/d(hash features) [32]: scatter to the 8 corners per level
+  const float x = box01(rays.p[0][row]), y = box01(rays.p[1][row]), z = box01(rays.p[2][row]);
+  for (int l = 0; l < 16; ++l) {
+    const int n = g.res[l];
+    const float fn = static_cast<float>(n);
+    const float ux = x * fn, uy = y * fn, uz = z * fn;
+    const int ix = min(static_cast<int>(ux), n - 1);
+    const int iy = min(static_cast<int>(uy), n - 1);
+    const int iz = min(static_cast<int>(uz), n - 1);
+    const float wx = ux - static_cast<float>(ix);
+    const float wy = uy - static_cast<float>(iy);
+    const float wz = uz - static_cast<float>(iz);
+    const float g0 = dh[2 * l], g1 = dh[2 * l + 1];
+    for (int c = 0; c < 8; ++c) {
+      const float w = ((c & 1) ? wx : 1.f - wx) * (((c >> 1) & 1) ? wy : 1.f - wy) *
+                      ((c >> 2) ? wz : 1.f - wz);
+      const uint32_t e = g.offset[l] + hg_index(g, l, ix + (c & 1), iy + ((c >> 1) & 1), iz + (c >> 2));
+      atomicAdd(grad_table + 2 * static_cast<int64_t>(e), w * g0);
+      atomicAdd(grad_table + 2 * static_cast<int64_t>(e) + 1, w * g1);
+    }
+  }
+}
+
+// part[s][n][k] = sum over the rays of split s of P[r][n] * A[r][k], for the
+// weight gradient dW = P^T A of a layer (P = dL/dpre [B x ldp], A = the
+// layer input [B x lda]); deterministic: every partial in a fixed order.
+__global__ void hg_outer_kernel(const float* __restrict__ P, int ldp, const float* __restrict__ A,
+                                int lda, int na, int64_t B, int64_t per_split,
+                                float* __restrict__ part) {
+  const int n = blockIdx.x, sp = blockIdx.y, np = gridDim.x;
+  const int k = threadIdx.x;
+  if (k >= na) return;
+  const int64_t r0 = sp * per_split;
+  const int64_t r1 = r0 + per_split < B ? r0 + per_split : B;
+  float s = 0.f;
+  for (int64_t r = r0; r < r1; ++r) s = fmaf(P[r * ldp + n], A[r * lda + k], s);
+  part[(static_cast<int64_t>(sp) * np + n) * na + k] = s;
 }
 
 // ------------------------------------------------------------ packing
@@ -426,13 +532,61 @@ cudaError_t launch_hashgrid_f32(const HashGridParams& g, const float2* table, co
   if (H < 1 || H > 4) return cudaErrorInvalidValue;
   const int n_mlp = kHgW * kHgCode + kHgW + (H - 1) * (kHgW * kHgW + kHgW) + 2 * kHgW + 2;
   const size_t smem = (((n_mlp + 3) & ~3) + 2 * kHgF32Rays * kHgLd) * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(hashgrid_f32_kernel,
+  cudaError_t e = cudaFuncSetAttribute(hashgrid_f32_kernel<false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   const int64_t blocks = (M + kHgF32Rays - 1) / kHgF32Rays;
-  hashgrid_f32_kernel<<<static_cast<unsigned>(blocks), kHgF32Rays, smem, s>>>(g, table, mlp, H,
-                                                                               rays, M, out);
+  hashgrid_f32_kernel<false><<<static_cast<unsigned>(blocks), kHgF32Rays, smem, s>>>(
+      g, table, mlp, H, rays, M, out, nullptr, nullptr, nullptr);
+  return cudaGetLastError();
+}
+
+namespace {
+size_t hg_f32_smem(int H) {
+  const int n_mlp = kHgW * kHgCode + kHgW + (H - 1) * (kHgW * kHgW + kHgW) + 2 * kHgW + 2;
+  return (((n_mlp + 3) & ~3) + 2 * kHgF32Rays * kHgLd) * sizeof(float);
+}
+}  // namespace
+
+cudaError_t launch_hg_train_fwd(const HashGridParams& g, const float2* table, const float* mlp,
+                                int H, RaySoA rays, int64_t B, float* code, float* acts,
+                                float2* z, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  if (H < 1 || H > 4) return cudaErrorInvalidValue;
+  const size_t smem = hg_f32_smem(H);
+  cudaError_t e = cudaFuncSetAttribute(hashgrid_f32_kernel<true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = (B + kHgF32Rays - 1) / kHgF32Rays;
+  hashgrid_f32_kernel<true><<<static_cast<unsigned>(blocks), kHgF32Rays, smem, s>>>(
+      g, table, mlp, H, rays, B, HeadOut{}, code, acts, z);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hg_train_bwd(const HashGridParams& g, const float* mlp, int H, RaySoA rays,
+                                int64_t B, const float* acts, const float2* dz, float* dpre,
+                                float* grad_table, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  if (H < 1 || H > 4) return cudaErrorInvalidValue;
+  const size_t smem = hg_f32_smem(H);
+  cudaError_t e = cudaFuncSetAttribute(hg_train_bwd_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = (B + kHgF32Rays - 1) / kHgF32Rays;
+  hg_train_bwd_kernel<<<static_cast<unsigned>(blocks), kHgF32Rays, smem, s>>>(
+      g, mlp, H, rays, B, acts, dz, dpre, grad_table);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hg_outer(const float* P, int ldp, int np, const float* A, int lda, int na,
+                            int64_t B, int splits, float* part, cudaStream_t s) {
+  if (np < 1 || na < 1 || na > 1024 || splits < 1) return cudaErrorInvalidValue;
+  const int64_t per = (B + splits - 1) / splits;
+  hg_outer_kernel<<<dim3(np, splits), ((na + 31) / 32) * 32, 0, s>>>(P, ldp, A, lda, na, B, per,
+                                                                      part);
   return cudaGetLastError();
 }
 

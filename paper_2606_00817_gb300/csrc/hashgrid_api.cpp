@@ -53,6 +53,32 @@ size_t hg_param_count(const ddf_config& c) {
   return static_cast<size_t>(entries) * 2 + mlp_params(c);
 }
 
+// Writes the query copies of a bf16 field (padded bf16 table, swizzled MLP
+// operand images, FP32 biases and head) from the FP32 master blob, on st.
+ddf_status hg_refresh(ddf_s* h, cudaStream_t st) {
+  const int H = h->cfg.hidden_layers;
+  const float* tables = h->d_blob;
+  uint32_t* tab = static_cast<uint32_t*>(h->hg_table);
+  for (int l = 0; l < kLevels; ++l) {  // level by level into the padded layout
+    const int64_t end = l + 1 < kLevels ? h->hg_blob.offset[l + 1] : h->hg_blob_entries;
+    DDF_CK(ddf::launch_hg_pack_table(tables + 2 * static_cast<int64_t>(h->hg_blob.offset[l]),
+                                     end - h->hg_blob.offset[l], tab + h->hg.offset[l], st));
+  }
+  // MLP part: W_1 [64 x 59], b_1, (W_l [64 x 64], b_l) ..., W_o [2 x 64], b_o
+  const float* m = tables + 2 * h->hg_blob_entries;
+  int K = kCode;
+  for (int l = 0; l < H; ++l) {
+    DDF_CK(ddf::launch_hg_pack_image(m, K, h->hg_img + static_cast<size_t>(l) * kW * 128, st));
+    DDF_CK(cudaMemcpyAsync(h->hg_bias + l * kW, m + kW * K, kW * sizeof(float),
+                           cudaMemcpyDeviceToDevice, st));
+    m += kW * K + kW;
+    K = kW;
+  }
+  DDF_CK(cudaMemcpyAsync(h->hg_bias + H * kW, m, (2 * kW + 2) * sizeof(float),
+                         cudaMemcpyDeviceToDevice, st));  // head rows then head bias
+  return DDF_OK;
+}
+
 ddf_status hg_load(ddf_s* h, const float* host_blob) {
   const ddf_config& c = h->cfg;
   const int H = c.hidden_layers;
@@ -64,6 +90,7 @@ ddf_status hg_load(ddf_s* h, const float* host_blob) {
     // the FP32 path reads the blob's tables in place; the bf16 table starts
     // every level on an even entry (8-byte corner pairs)
     h->hg = hg_layout(&h->hg_entries, !f32);
+    h->hg_blob = hg_layout(&h->hg_blob_entries, false);
     if ((s = dev_alloc(h, &p, need * sizeof(float))) != DDF_OK) return s;
     h->d_blob = static_cast<float*>(p);
     if (!f32) {
@@ -81,30 +108,7 @@ ddf_status hg_load(ddf_s* h, const float* host_blob) {
     }
   }
   DDF_CK(cudaMemcpy(h->d_blob, host_blob, need * sizeof(float), cudaMemcpyHostToDevice));
-  if (!f32) {
-    cudaStream_t st = nullptr;
-    const float* tables = h->d_blob;
-    int64_t blob_entries = 0;
-    const ddf::HashGridParams dense = hg_layout(&blob_entries, false);
-    uint32_t* tab = static_cast<uint32_t*>(h->hg_table);
-    for (int l = 0; l < kLevels; ++l) {  // level by level into the padded layout
-      const int64_t end = l + 1 < kLevels ? dense.offset[l + 1] : blob_entries;
-      DDF_CK(ddf::launch_hg_pack_table(tables + 2 * static_cast<int64_t>(dense.offset[l]),
-                                       end - dense.offset[l], tab + h->hg.offset[l], st));
-    }
-    // MLP part: W_1 [64 x 59], b_1, (W_l [64 x 64], b_l) ..., W_o [2 x 64], b_o
-    const float* m = tables + 2 * blob_entries;
-    int K = kCode;
-    for (int l = 0; l < H; ++l) {
-      DDF_CK(ddf::launch_hg_pack_image(m, K, h->hg_img + static_cast<size_t>(l) * kW * 128, st));
-      DDF_CK(cudaMemcpy(h->hg_bias + l * kW, m + kW * K, kW * sizeof(float),
-                        cudaMemcpyDeviceToDevice));
-      m += kW * K + kW;
-      K = kW;
-    }
-    DDF_CK(cudaMemcpy(h->hg_bias + H * kW, m, (2 * kW + 2) * sizeof(float),
-                      cudaMemcpyDeviceToDevice));  // head rows then head bias
-  }
+  if (!f32 && (s = hg_refresh(h, nullptr)) != DDF_OK) return s;
   DDF_CK(cudaDeviceSynchronize());
   return DDF_OK;
 }
@@ -125,6 +129,140 @@ ddf_status hg_query(ddf_s* h, ddf::RaySoA rays, int64_t n, ddf::HeadOut out, cud
   DDF_CK(ddf::launch_hashgrid_tc(h->hg, static_cast<const uint32_t*>(h->hg_table), h->hg_img, vecs,
                                  vecs + H * kW, vecs + H * kW + 2 * kW, H, rays, n, out,
                                  h->status_dev, h->timeout_ns, grid, st));
+  return DDF_OK;
+}
+
+// ------------------------------------------------------------ training
+
+namespace {
+
+constexpr int kGradSplits = 64;  // ray splits of the weight-gradient sums
+
+struct MlpOffsets {
+  int64_t w[4], b[4], wo, bo;
+};
+
+MlpOffsets mlp_offsets(int H) {
+  MlpOffsets o{};
+  int64_t off = 0;
+  for (int l = 0; l < H; ++l) {
+    const int K = l == 0 ? kCode : kW;
+    o.w[l] = off;
+    off += static_cast<int64_t>(kW) * K;
+    o.b[l] = off;
+    off += kW;
+  }
+  o.wo = off;
+  o.bo = off + 2 * kW;
+  return o;
+}
+
+}  // namespace
+
+ddf_status hg_ensure_train(ddf_s* h, int64_t B) {
+  const int H = h->cfg.hidden_layers;
+  const size_t np = hg_param_count(h->cfg);
+  ddf_status s;
+  void* p = nullptr;
+  if (h->grad == nullptr) {
+    for (float** q : {&h->grad, &h->adam_m, &h->adam_v}) {
+      if ((s = dev_alloc(h, &p, np * sizeof(float))) != DDF_OK) return s;
+      *q = static_cast<float*>(p);
+    }
+    DDF_CK(cudaMemset(h->adam_m, 0, np * sizeof(float)));
+    DDF_CK(cudaMemset(h->adam_v, 0, np * sizeof(float)));
+    h->adam_step = 0;
+    if ((s = dev_alloc(h, &p, static_cast<size_t>(kGradSplits) * kW * kW * sizeof(float))) != DDF_OK)
+      return s;
+    h->tr_part = static_cast<float*>(p);
+    if ((s = dev_alloc(h, &p, static_cast<size_t>(kGradSplits) * kW * sizeof(float))) != DDF_OK)
+      return s;
+    h->tr_cpart = static_cast<float*>(p);
+    if ((s = dev_alloc(h, &p, sizeof(unsigned))) != DDF_OK) return s;
+    h->tr_nhit = static_cast<unsigned*>(p);
+  }
+  if (B > h->tr_rows) {
+    h->fwd_rows = 0;
+    for (void* q : {static_cast<void*>(h->hg_code), static_cast<void*>(h->hg_acts),
+                    static_cast<void*>(h->hg_dpre), static_cast<void*>(h->tr_z),
+                    static_cast<void*>(h->tr_dz), static_cast<void*>(h->tr_lpart)})
+      dev_free(h, q);
+    h->tr_rows = 0;
+    const size_t rows = static_cast<size_t>(B);
+    if ((s = dev_alloc(h, &p, rows * kW * sizeof(float))) != DDF_OK) return s;
+    h->hg_code = static_cast<float*>(p);
+    if ((s = dev_alloc(h, &p, static_cast<size_t>(H) * rows * kW * sizeof(float))) != DDF_OK) return s;
+    h->hg_acts = static_cast<float*>(p);
+    if ((s = dev_alloc(h, &p, static_cast<size_t>(H) * rows * kW * sizeof(float))) != DDF_OK) return s;
+    h->hg_dpre = static_cast<float*>(p);
+    if ((s = dev_alloc(h, &p, rows * sizeof(float2))) != DDF_OK) return s;
+    h->tr_z = static_cast<float2*>(p);
+    if ((s = dev_alloc(h, &p, rows * sizeof(float2))) != DDF_OK) return s;
+    h->tr_dz = static_cast<float2*>(p);
+    if ((s = dev_alloc(h, &p, ((rows + 255) / 256) * sizeof(float))) != DDF_OK) return s;
+    h->tr_lpart = static_cast<float*>(p);
+    h->tr_rows = B;
+  }
+  return DDF_OK;
+}
+
+ddf_status hg_forward_keep(ddf_s* h, ddf::RaySoA rays, int B, cudaStream_t st) {
+  const float2* table = static_cast<const float2*>(static_cast<void*>(h->d_blob));
+  DDF_CK(ddf::launch_hg_train_fwd(h->hg_blob, table, h->d_blob + 2 * h->hg_blob_entries,
+                                  h->cfg.hidden_layers, rays, B, h->hg_code, h->hg_acts, h->tr_z,
+                                  st));
+  return DDF_OK;
+}
+
+ddf_status hg_backward(ddf_s* h, ddf::RaySoA rays, int B, cudaStream_t st) {
+  const int H = h->cfg.hidden_layers;
+  const int64_t tab = 2 * h->hg_blob_entries;
+  const float* mlp = h->d_blob + tab;
+  float* gmlp = h->grad + tab;
+  const MlpOffsets o = mlp_offsets(H);
+  const int64_t act = static_cast<int64_t>(B) * kW;
+  // the table gradient is a sum of scattered contributions: start from zero
+  DDF_CK(cudaMemsetAsync(h->grad, 0, tab * sizeof(float), st));
+  DDF_CK(ddf::launch_hg_train_bwd(h->hg_blob, mlp, H, rays, B, h->hg_acts, h->tr_dz, h->hg_dpre,
+                                  h->grad, st));
+  for (int l = 0; l < H; ++l) {
+    const float* P = h->hg_dpre + l * act;
+    const float* A = l == 0 ? h->hg_code : h->hg_acts + (l - 1) * act;
+    const int K = l == 0 ? kCode : kW;
+    DDF_CK(ddf::launch_hg_outer(P, kW, kW, A, kW, K, B, kGradSplits, h->tr_part, st));
+    DDF_CK(ddf::launch_splitk_reduce(h->tr_part, kGradSplits, kW, K, static_cast<int64_t>(kW) * K, K,
+                                     gmlp + o.w[l], K, st));
+    DDF_CK(ddf::launch_colsum_f32(P, B, kW, kW, kGradSplits, h->tr_cpart, st));
+    DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart, kGradSplits, 1, kW, kW, kW, gmlp + o.b[l], kW, st));
+  }
+  const float* dz = reinterpret_cast<const float*>(h->tr_dz);
+  DDF_CK(ddf::launch_hg_outer(dz, 2, 2, h->hg_acts + (H - 1) * act, kW, kW, B, kGradSplits,
+                              h->tr_part, st));
+  DDF_CK(ddf::launch_splitk_reduce(h->tr_part, kGradSplits, 2, kW, 2 * kW, kW, gmlp + o.wo, kW, st));
+  DDF_CK(ddf::launch_colsum_f32(dz, B, 2, 2, kGradSplits, h->tr_cpart, st));
+  DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart, kGradSplits, 1, 2, 2, 2, gmlp + o.bo, 2, st));
+  h->grad_valid = true;
+  return DDF_OK;
+}
+
+ddf_status hg_train(ddf_s* h, ddf::RaySoA rays, const float* t_target, const uint8_t* hit_target,
+                    int B, float lr, float* out_loss, cudaStream_t st) {
+  ddf_status s;
+  h->fwd_rows = 0;
+  if ((s = hg_forward_keep(h, rays, B, st)) != DDF_OK) return s;
+  DDF_CK(ddf::launch_loss(h->tr_z, t_target, hit_target, B, h->tr_nhit, kLossClamp, kLossLambda,
+                          h->tr_dz, h->tr_lpart, out_loss, st));
+  if ((s = hg_backward(h, rays, B, st)) != DDF_OK) return s;
+  if (lr > 0.f) {
+    ++h->adam_step;
+    const double t = static_cast<double>(h->adam_step);
+    const float bc1 = static_cast<float>(1.0 - std::pow(0.9, t));
+    const float bc2 = static_cast<float>(1.0 - std::pow(0.999, t));
+    DDF_CK(ddf::launch_adam(h->d_blob, h->grad, h->adam_m, h->adam_v,
+                            static_cast<int64_t>(hg_param_count(h->cfg)), lr, kAdamB1, kAdamB2,
+                            kAdamEps, bc1, bc2, st));
+    if (h->cfg.precision != DDF_FP32 && (s = hg_refresh(h, st)) != DDF_OK) return s;
+  }
   return DDF_OK;
 }
 

@@ -22,9 +22,9 @@ using namespace ddfi;
 namespace {
 
 constexpr int kColSplits = 64;  // row splits of the column sums
-constexpr float kClamp = 4.0f;  // L1 clamp ("box scale")
-constexpr float kLambda = 0.3f; // cross-entropy weight
-constexpr float kB1 = 0.9f, kB2 = 0.999f, kEps = 1e-8f;
+constexpr float kClamp = kLossClamp;
+constexpr float kLambda = kLossLambda;
+constexpr float kB1 = kAdamB1, kB2 = kAdamB2, kEps = kAdamEps;
 
 // (t, vis) head rows of a ray field; one row (the distance) for an SDF field
 size_t head_rows(const ddf_s* h) { return h->cfg.kind == DDF_KIND_SDF ? 1 : 2; }
@@ -50,7 +50,12 @@ BlobOffsets blob_offsets(const ddf_s* h) {
   return o;
 }
 
-size_t n_params(const ddf_s* h) { return blob_offsets(h).bo + head_rows(h); }
+size_t n_params(const ddf_s* h) {
+  if (h->cfg.kind == DDF_KIND_HASHGRID) return hg_param_count(h->cfg);
+  return blob_offsets(h).bo + head_rows(h);
+}
+
+bool is_hashgrid(const ddf_s* h) { return h->cfg.kind == DDF_KIND_HASHGRID; }
 
 ddf_status train_alloc(ddf_s* h, void** p, size_t bytes) { return dev_alloc(h, p, bytes); }
 
@@ -163,10 +168,12 @@ ddf_status tc_gemm(ddf_s* h, const void* A, int M, int K, const CUtensorMap& tmB
 ddf_status check_train_args(ddf_s* h, const float* const rays[6], const float* t_target,
                             const uint8_t* hit_target, int64_t batch, int kind = DDF_KIND_RAY) {
   if (h == nullptr) return fail(DDF_ERR_INVALID_ARG, "handle is NULL");
-  if (h->cfg.kind != kind)
+  const bool hg = h->cfg.kind == DDF_KIND_HASHGRID &&
+                  (kind == DDF_KIND_RAY || kind == DDF_KIND_HASHGRID);  // a ray field too
+  if (h->cfg.kind != kind && !hg)
     return fail(DDF_ERR_INVALID_ARG, kind == DDF_KIND_RAY ? "not a ray (DDF) field" : "not an SDF field");
   if (!h->loaded) return fail(DDF_ERR_BAD_WEIGHTS, "no weights loaded");
-  if (h->cfg.precision != DDF_BF16)
+  if (h->cfg.precision != DDF_BF16 && !hg)
     return fail(DDF_ERR_UNSUPPORTED, "training runs on bf16 handles");
   if (batch < 8 || batch % 8 != 0 || batch >= (int64_t{1} << 31))
     return fail(DDF_ERR_INVALID_ARG, "batch must be a positive multiple of 8 below 2^31");
@@ -312,6 +319,13 @@ ddf_status ddf_compute_grad(ddf_handle h, const float* const rays[6], const floa
   ddf_status s = check_train_args(h, rays, t_target, hit_target, batch);
   if (s != DDF_OK) return s;
   DeviceGuard g(h->cfg.device);
+  if (is_hashgrid(h)) {
+    if ((s = hg_ensure_train(h, batch)) != DDF_OK) return s;
+    ddf::RaySoA r;
+    for (int c = 0; c < 6; ++c) r.p[c] = rays[c];
+    return hg_train(h, r, t_target, hit_target, static_cast<int>(batch), 0.f, out_loss,
+                    static_cast<cudaStream_t>(stream));
+  }
   if ((s = ensure_train(h, batch)) != DDF_OK) return s;
   return compute_grad(h, rays, t_target, hit_target, batch, out_loss,
                       static_cast<cudaStream_t>(stream));
@@ -375,6 +389,12 @@ ddf_status train_step(ddf_s* h, const float* const rays[6], const float* t_targe
   if (!(lr > 0.f) || !std::isfinite(lr)) return fail(DDF_ERR_INVALID_ARG, "lr must be positive");
   DeviceGuard g(h->cfg.device);
   ddf_status s;
+  if (is_hashgrid(h)) {
+    if ((s = hg_ensure_train(h, batch)) != DDF_OK) return s;
+    ddf::RaySoA r;
+    for (int c = 0; c < 6; ++c) r.p[c] = rays[c];
+    return hg_train(h, r, t_target, hit_target, static_cast<int>(batch), lr, out_loss, st);
+  }
   if ((s = ensure_train(h, batch)) != DDF_OK) return s;
   if ((s = compute_grad(h, rays, t_target, hit_target, batch, out_loss, st)) != DDF_OK) return s;
   ++h->adam_step;
@@ -408,16 +428,25 @@ ddf_status ddf_forward_train(ddf_handle h, const float* const inputs[6], int64_t
   if (s != DDF_OK) return s;
   if (out_z == nullptr) return fail(DDF_ERR_INVALID_ARG, "out_z is NULL");
   DeviceGuard g(h->cfg.device);
-  if ((s = ensure_train(h, batch)) != DDF_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  h->fwd_rows = 0;
-  if ((s = forward_keep(h, p6, static_cast<int>(batch), st)) != DDF_OK) return s;
+  if (is_hashgrid(h)) {
+    if ((s = hg_ensure_train(h, batch)) != DDF_OK) return s;
+    h->fwd_rows = 0;
+    ddf::RaySoA r;
+    for (int c = 0; c < 6; ++c) r.p[c] = p6[c];
+    if ((s = hg_forward_keep(h, r, static_cast<int>(batch), st)) != DDF_OK) return s;
+  } else {
+    if ((s = ensure_train(h, batch)) != DDF_OK) return s;
+    h->fwd_rows = 0;
+    if ((s = forward_keep(h, p6, static_cast<int>(batch), st)) != DDF_OK) return s;
+  }
   if (head_rows(h) == 2) {
     DDF_CK(cudaMemcpyAsync(out_z, h->tr_z, batch * sizeof(float2), cudaMemcpyDeviceToDevice, st));
   } else {  // z0 of each float2 into a dense column
     DDF_CK(cudaMemcpy2DAsync(out_z, sizeof(float), h->tr_z, sizeof(float2), sizeof(float),
                              batch, cudaMemcpyDeviceToDevice, st));
   }
+  for (int c = 0; c < 6; ++c) h->fwd_rays.p[c] = p6[c];  // the backward's table scatter re-reads them
   h->fwd_rows = batch;
   return DDF_OK;
 }
@@ -437,6 +466,7 @@ ddf_status ddf_backward(ddf_handle h, const float* dz, int64_t batch, void* stre
     DDF_CK(cudaMemcpy2DAsync(h->tr_dz, sizeof(float2), dz, sizeof(float), sizeof(float), batch,
                              cudaMemcpyDeviceToDevice, st));
   }
+  if (is_hashgrid(h)) return hg_backward(h, h->fwd_rays, static_cast<int>(batch), st);
   return backward_from_dz(h, static_cast<int>(batch), st);
 }
 
@@ -454,7 +484,7 @@ ddf_status ddf_load_weights_device(ddf_handle h, const float* dev_blob, size_t n
                                    void* stream) {
   if (h == nullptr || dev_blob == nullptr) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
   if (!h->loaded) return fail(DDF_ERR_BAD_WEIGHTS, "load weights once with ddf_load_weights first");
-  if (h->cfg.precision != DDF_BF16)
+  if (h->cfg.precision != DDF_BF16 && !is_hashgrid(h))
     return fail(DDF_ERR_UNSUPPORTED, "device weight updates run on bf16 handles");
   if (n_floats != n_params(h)) return fail(DDF_ERR_BAD_WEIGHTS, "wrong blob size");
   DeviceGuard g(h->cfg.device);
@@ -462,6 +492,7 @@ ddf_status ddf_load_weights_device(ddf_handle h, const float* dev_blob, size_t n
   h->fwd_rows = 0;
   DDF_CK(cudaMemcpyAsync(h->d_blob, dev_blob, n_floats * sizeof(float), cudaMemcpyDeviceToDevice,
                          st));
+  if (is_hashgrid(h)) return h->cfg.precision == DDF_FP32 ? DDF_OK : hg_refresh(h, st);
   return refresh_weights(h, st);
 }
 

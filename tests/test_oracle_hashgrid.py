@@ -206,3 +206,28 @@ def test_hashgrid_table_gradient_is_a_weighted_scatter():
     w = u - i0
     corner = g[i0[0] + 5 * (i0[1] + 5 * i0[2]), 0]       # the (0,0,0) corner
     assert abs(corner - (1 - w[0]) * (1 - w[1]) * (1 - w[2])) < 1e-15
+
+
+def test_fp32_positions_round_like_float32():
+    """The fp32 position mode picks the cell and in-cell coordinates from
+    float32 arithmetic: u = f32(f32(f32(x) + 1) * 0.5) * f32(N). At a
+    coordinate whose float32 box position rounds across a cell face, the two
+    modes pick different cells; everywhere the features stay within the
+    float32 position error (N x 2^-24 of a cell) of the exact ones."""
+    res = [7006]
+    # x such that (x + 1) / 2 * 7006 sits 1e-6 below the face at 3000 in float64
+    x_exact = (3000 - 1e-6) / 7006 * 2 - 1
+    x = np.array([[x_exact, 0.1, -0.2]], np.float32).astype(np.float64)
+    i_ex, w_ex = O.hashgrid_cell(x, 7006, "exact")
+    i_32, w_32 = O.hashgrid_cell(x, 7006, "fp32")
+    f = np.float32
+    u32 = f(f(f(x[0, 0]) + f(1)) * f(0.5)) * f(7006)
+    assert i_32[0, 0] == int(np.floor(u32)) and w_32[0, 0] == float(u32) - int(np.floor(u32))
+    rng = np.random.default_rng(4)
+    table = rng.normal(size=(1 << 19, 2))
+    pts = rng.uniform(-1, 1, size=(2000, 3)).astype(np.float32).astype(np.float64)
+    fe = O.hashgrid_encode(pts, [table], res)
+    f3 = O.hashgrid_encode(pts, [table], res, positions="fp32")
+    lip = 2 * 4 * np.abs(table).max()                       # per unit of u, 4 corners per axis
+    assert np.abs(fe - f3).max() <= lip * 7006 * 2.0 ** -23
+    assert np.abs(fe - f3).max() > 0                        # float32 positions do move features
