@@ -271,6 +271,34 @@ ddf_status ddf_copy_grad(ddf_handle h, float* dev_grad, size_t n_floats, void* s
 ddf_status ddf_load_weights_device(ddf_handle h, const float* dev_blob, size_t n_floats,
                                    void* stream);
 
+/* ---- the distillation schedule (Sec. 3.2 / 3.4) ----
+ * ddf_sample_rays: n training rays into rays_out (6 device float arrays): a
+ * fraction surface_frac anchored on the scene (a primitive chosen uniformly,
+ * a point on its surface offset 1e-3 along the normal, a direction uniform
+ * on the sphere: the "rays that start on the surface and point in all
+ * directions" of Sec. 3.2), the rest camera rays (origin uniform on a face
+ * of the box [-1,1]^3, aimed at a point uniform in [-0.9,0.9]^3). Counter-
+ * based SplitMix64: (seed, step, i) fixes ray i. Primitive arrays as
+ * ddf_cast_scene. Asynchronous.
+ * ddf_shift_rays: the ray-march shifted points of Sec. 3.2: every ray
+ * i in [first, n) with hit[i] moves forward by s = u t[i] (u uniform in
+ * [0, 1), from (seed, step, i)) and t[i] becomes t[i] - s. Asynchronous.
+ * ddf_distill: `steps` steps of `batch` rays on h (a ray or hash-grid field):
+ * sample (surface_frac surface-anchored), cast exact targets, shift the last
+ * round(shift_frac batch) rays, ddf_train_step with lr following a cosine
+ * from lr0 to 0.05 lr0 (Sec. 3.4: 3e-3, batch 16,384, 30 % shifted).
+ * losses: host float[steps] or NULL. Allocates its batch buffers for the
+ * call; synchronous. */
+ddf_status ddf_sample_rays(const float* spheres, int32_t n_spheres, const float* boxes,
+                           int32_t n_boxes, uint64_t seed, uint64_t step, int64_t n,
+                           float surface_frac, float* const rays_out[6], void* stream);
+ddf_status ddf_shift_rays(float* const rays[6], float* t, const uint8_t* hit, int64_t n,
+                          int64_t first, uint64_t seed, uint64_t step, void* stream);
+ddf_status ddf_distill(ddf_handle h, const float* spheres, int32_t n_spheres, const float* boxes,
+                       int32_t n_boxes, int64_t steps, int64_t batch, float lr0,
+                       float surface_frac, float shift_frac, uint64_t seed, float* losses,
+                       void* stream);
+
 /* Copies the last computed gradient (weight-blob layout, ddf_param_count
  * floats) to host memory. Synchronous. */
 ddf_status ddf_get_grad(ddf_handle h, float* host_grad, size_t n_floats);

@@ -1,0 +1,157 @@
+// distill.cu -- ray sampling for the distillation schedule (Sec. 3.2 / 3.4):
+// camera rays that view the object, rays anchored on its surface that point
+// in all directions, and the ray-march shifted copies that keep the field
+// consistent along a ray (a ray that hits at t, moved forward by s along
+// itself, hits at t - s).
+//
+// Random numbers come from a counter-based SplitMix64 (Steele, Lea and Flood's
+// 64-bit mixing function): draw j of ray i at step k is
+// mix(key(seed, k, i) + j), so any ray of any step can be regenerated alone.
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace ddf {
+
+namespace {
+
+__device__ __forceinline__ uint64_t sm64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  uint64_t z = x;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Uniform float in [0, 1) from the top 24 bits.
+__device__ __forceinline__ float u01(uint64_t key, int j) {
+  return static_cast<float>(sm64(key + static_cast<uint64_t>(j)) >> 40) * (1.0f / 16777216.0f);
+}
+
+__device__ __forceinline__ uint64_t ray_key(uint64_t seed, uint64_t step, int64_t i) {
+  return sm64(sm64(seed ^ 0x5DEECE66Dull) + step) ^ (static_cast<uint64_t>(i) * 0x2545F4914F6CDD1Dull);
+}
+
+// Unit vector uniform on the sphere from two uniforms.
+__device__ __forceinline__ void sphere_dir(float a, float b, float& x, float& y, float& z) {
+  z = 2.f * a - 1.f;
+  const float r = sqrtf(fmaxf(0.f, 1.f - z * z));
+  float s, c;
+  sincospif(2.f * b, &s, &c);
+  x = r * c;
+  y = r * s;
+}
+
+constexpr float kSurfaceOffset = 1e-3f;  // origins sit this far off the surface
+
+__global__ void sample_rays_kernel(const float* __restrict__ spheres, int ns,
+                                   const float* __restrict__ boxes, int nb, uint64_t seed,
+                                   uint64_t step, int64_t n, float surface_frac,
+                                   RayOut r) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t key = ray_key(seed, step, i);
+  float ox, oy, oz, dx, dy, dz;
+  if (u01(key, 0) < surface_frac && ns + nb > 0) {
+    // a surface point of a primitive chosen uniformly, its normal, and a
+    // direction uniform over the whole sphere
+    const int p = min(static_cast<int>(u01(key, 1) * static_cast<float>(ns + nb)), ns + nb - 1);
+    float px, py, pz, nx, ny, nz;
+    if (p < ns) {
+      const float* s = spheres + 4 * p;
+      sphere_dir(u01(key, 2), u01(key, 3), nx, ny, nz);
+      px = s[0] + s[3] * nx;
+      py = s[1] + s[3] * ny;
+      pz = s[2] + s[3] * nz;
+    } else {
+      const float* b = boxes + 6 * (p - ns);
+      const int face = min(static_cast<int>(u01(key, 2) * 6.f), 5);
+      const int axis = face >> 1;
+      const float sg = (face & 1) ? 1.f : -1.f;
+      const float a = u01(key, 3), c = u01(key, 4);
+      float q[3];
+      // the two in-face coordinates take a and c; the face's own axis its side
+      const int u = (axis + 1) % 3, v = (axis + 2) % 3;
+      q[u] = b[u] + a * (b[u + 3] - b[u]);
+      q[v] = b[v] + c * (b[v + 3] - b[v]);
+      q[axis] = sg > 0.f ? b[axis + 3] : b[axis];
+      float nrm[3] = {0.f, 0.f, 0.f};
+      nrm[axis] = sg;
+      px = q[0];
+      py = q[1];
+      pz = q[2];
+      nx = nrm[0];
+      ny = nrm[1];
+      nz = nrm[2];
+    }
+    ox = px + kSurfaceOffset * nx;
+    oy = py + kSurfaceOffset * ny;
+    oz = pz + kSurfaceOffset * nz;
+    sphere_dir(u01(key, 5), u01(key, 6), dx, dy, dz);
+  } else {
+    // a camera ray: origin uniform on a face of the box [-1, 1]^3, aimed at a
+    // point uniform in the inner box [-0.9, 0.9]^3
+    const int face = min(static_cast<int>(u01(key, 1) * 6.f), 5);
+    const int axis = face >> 1;
+    float o[3];
+    o[(axis + 1) % 3] = 2.f * u01(key, 2) - 1.f;
+    o[(axis + 2) % 3] = 2.f * u01(key, 3) - 1.f;
+    o[axis] = (face & 1) ? 1.f : -1.f;
+    const float tx = 1.8f * u01(key, 4) - 0.9f;
+    const float ty = 1.8f * u01(key, 5) - 0.9f;
+    const float tz = 1.8f * u01(key, 6) - 0.9f;
+    ox = o[0];
+    oy = o[1];
+    oz = o[2];
+    dx = tx - ox;
+    dy = ty - oy;
+    dz = tz - oz;
+    const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+    dx *= inv;
+    dy *= inv;
+    dz *= inv;
+  }
+  r.p[0][i] = ox;
+  r.p[1][i] = oy;
+  r.p[2][i] = oz;
+  r.p[3][i] = dx;
+  r.p[4][i] = dy;
+  r.p[5][i] = dz;
+}
+
+// Rays i >= first that hit move forward by s = u t along themselves; their
+// target becomes t - s (the first hit along the same line is unchanged).
+__global__ void shift_rays_kernel(RayOut r, float* __restrict__ t, const uint8_t* __restrict__ hit,
+                                  int64_t n, int64_t first, uint64_t seed, uint64_t step) {
+  const int64_t i = first + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n || hit[i] == 0) return;
+  const float ti = t[i];
+  if (!(ti < 1e30f)) return;
+  const float s = u01(ray_key(seed, step, i), 7) * ti;
+  r.p[0][i] += s * r.p[3][i];
+  r.p[1][i] += s * r.p[4][i];
+  r.p[2][i] += s * r.p[5][i];
+  t[i] = ti - s;
+}
+
+}  // namespace
+
+cudaError_t launch_sample_rays(const float* spheres, int ns, const float* boxes, int nb,
+                               uint64_t seed, uint64_t step, int64_t n, float surface_frac,
+                               RayOut r, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  sample_rays_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(
+      spheres, ns, boxes, nb, seed, step, n, surface_frac, r);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shift_rays(RayOut r, float* t, const uint8_t* hit, int64_t n, int64_t first,
+                              uint64_t seed, uint64_t step, cudaStream_t s) {
+  if (first >= n) return cudaSuccess;
+  const int64_t m = n - first;
+  shift_rays_kernel<<<static_cast<unsigned>((m + 255) / 256), 256, 0, s>>>(r, t, hit, n, first,
+                                                                            seed, step);
+  return cudaGetLastError();
+}
+
+}  // namespace ddf

@@ -12,6 +12,9 @@ namespace ddf {
 struct RaySoA {
   const float* p[6];
 };
+struct RayOut {
+  float* p[6];
+};
 
 // One dense layer y = act(scale_n * (A W^T)_n + b_n) on the tcgen05 tensor cores.
 // A: [M x K] activations (bf16 or e4m3 codes), W: [N x K], both K-major and
@@ -221,5 +224,18 @@ cudaError_t launch_quant_e4m3(const float* src, int N, int K, int ldd, uint8_t* 
                               cudaStream_t s);
 // out[n] = a * v[n]
 cudaError_t launch_scale_vec(const float* v, float a, int n, float* out, cudaStream_t s);
+
+// ---- distillation sampling (distill.cu) ----
+// n rays: a fraction surface_frac anchored on a primitive's surface (1e-3 off
+// it along the normal, direction uniform on the sphere), the rest camera rays
+// from a face of [-1,1]^3 toward a point of [-0.9,0.9]^3. Counter-based:
+// (seed, step, i) fixes ray i.
+cudaError_t launch_sample_rays(const float* spheres, int ns, const float* boxes, int nb,
+                               uint64_t seed, uint64_t step, int64_t n, float surface_frac,
+                               RayOut r, cudaStream_t s);
+// Rays first..n-1 that hit move forward by s = u t (u uniform in [0,1)) and
+// their target becomes t - s.
+cudaError_t launch_shift_rays(RayOut r, float* t, const uint8_t* hit, int64_t n, int64_t first,
+                              uint64_t seed, uint64_t step, cudaStream_t s);
 
 }  // namespace ddf

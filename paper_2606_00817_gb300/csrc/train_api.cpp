@@ -537,3 +537,93 @@ ddf_status ddf_cast_scene(const float* spheres, int32_t n_spheres, const float* 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// The distillation schedule (Sec. 3.2 / 3.4) on the device.
+
+extern "C" {
+
+ddf_status ddf_sample_rays(const float* spheres, int32_t n_spheres, const float* boxes,
+                           int32_t n_boxes, uint64_t seed, uint64_t step, int64_t n,
+                           float surface_frac, float* const rays_out[6], void* stream) {
+  if (n_spheres < 0 || n_boxes < 0 || n < 0) return fail(DDF_ERR_INVALID_ARG, "negative count");
+  if ((n_spheres > 0 && spheres == nullptr) || (n_boxes > 0 && boxes == nullptr))
+    return fail(DDF_ERR_INVALID_ARG, "primitive array is NULL");
+  if (!(surface_frac >= 0.f && surface_frac <= 1.f))
+    return fail(DDF_ERR_INVALID_ARG, "surface_frac must be in [0, 1]");
+  if (n == 0) return DDF_OK;
+  if (rays_out == nullptr) return fail(DDF_ERR_INVALID_ARG, "rays_out is NULL");
+  ddf::RayOut r;
+  for (int c = 0; c < 6; ++c) {
+    if (rays_out[c] == nullptr) return fail(DDF_ERR_INVALID_ARG, "a ray array is NULL");
+    r.p[c] = rays_out[c];
+  }
+  DDF_CK(ddf::launch_sample_rays(spheres, n_spheres, boxes, n_boxes, seed, step, n, surface_frac, r,
+                                 static_cast<cudaStream_t>(stream)));
+  return DDF_OK;
+}
+
+ddf_status ddf_shift_rays(float* const rays[6], float* t, const uint8_t* hit, int64_t n,
+                          int64_t first, uint64_t seed, uint64_t step, void* stream) {
+  if (n < 0 || first < 0) return fail(DDF_ERR_INVALID_ARG, "negative count");
+  if (first >= n) return DDF_OK;
+  if (rays == nullptr || t == nullptr || hit == nullptr)
+    return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+  ddf::RayOut r;
+  for (int c = 0; c < 6; ++c) {
+    if (rays[c] == nullptr) return fail(DDF_ERR_INVALID_ARG, "a ray array is NULL");
+    r.p[c] = rays[c];
+  }
+  DDF_CK(ddf::launch_shift_rays(r, t, hit, n, first, seed, step, static_cast<cudaStream_t>(stream)));
+  return DDF_OK;
+}
+
+ddf_status ddf_distill(ddf_handle h, const float* spheres, int32_t n_spheres, const float* boxes,
+                       int32_t n_boxes, int64_t steps, int64_t batch, float lr0,
+                       float surface_frac, float shift_frac, uint64_t seed, float* losses,
+                       void* stream) {
+  if (h == nullptr) return fail(DDF_ERR_INVALID_ARG, "handle is NULL");
+  if (steps < 1 || !(lr0 > 0.f) || !(shift_frac >= 0.f && shift_frac <= 1.f))
+    return fail(DDF_ERR_INVALID_ARG, "steps >= 1, lr0 > 0, shift_frac in [0, 1]");
+  if (n_spheres > 1024 || n_boxes > 1024)
+    return fail(DDF_ERR_INVALID_ARG, "at most 1024 spheres and 1024 boxes");
+  DeviceGuard g(h->cfg.device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float* buf = nullptr;  // 6 ray arrays, targets, per-step losses
+  uint8_t* hit = nullptr;
+  DDF_CK(cudaMalloc(&buf, (7 * batch + steps) * sizeof(float)));
+  if (cudaMalloc(&hit, batch) != cudaSuccess) {
+    cudaFree(buf);
+    return fail(DDF_ERR_OOM, "cudaMalloc of the hit flags failed");
+  }
+  float* rp[6];
+  for (int c = 0; c < 6; ++c) rp[c] = buf + c * batch;
+  float* t = buf + 6 * batch;
+  float* dev_loss = buf + 7 * batch;
+  const int64_t first = batch - static_cast<int64_t>(std::llround(shift_frac * batch));
+  ddf_status s = DDF_OK;
+  for (int64_t k = 0; k < steps && s == DDF_OK; ++k) {
+    // cosine decay from lr0 to 5 % of it
+    const double c = 0.5 * (1.0 + std::cos(3.14159265358979323846 * static_cast<double>(k) / steps));
+    const float lr = static_cast<float>(lr0 * (0.05 + 0.95 * c));
+    s = ddf_sample_rays(spheres, n_spheres, boxes, n_boxes, seed, static_cast<uint64_t>(k), batch,
+                        surface_frac, rp, st);
+    const float* const rc[6] = {rp[0], rp[1], rp[2], rp[3], rp[4], rp[5]};
+    if (s == DDF_OK) s = ddf_cast_scene(spheres, n_spheres, boxes, n_boxes, rc, batch, t, hit, st);
+    if (s == DDF_OK) s = ddf_shift_rays(rp, t, hit, batch, first, seed, static_cast<uint64_t>(k), st);
+    if (s == DDF_OK) s = ddf_train_step(h, rc, t, hit, batch, lr, dev_loss + k, st);
+  }
+  if (s == DDF_OK && losses != nullptr) {
+    const cudaError_t e = cudaMemcpyAsync(losses, dev_loss, steps * sizeof(float),
+                                          cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) s = cuda_fail(e, "cudaMemcpyAsync");
+  }
+  const cudaError_t e = cudaStreamSynchronize(st);
+  cudaFree(buf);
+  cudaFree(hit);
+  if (s == DDF_OK && e != cudaSuccess) s = cuda_fail(e, "cudaStreamSynchronize");
+  return s;
+}
+
+}  // extern "C"
+

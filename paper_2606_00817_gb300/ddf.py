@@ -67,6 +67,10 @@ SIGNATURES = {
     "ddf_backward": (C.c_int, [_vp, _vp, _i64, _vp]),
     "ddf_copy_grad": (C.c_int, [_vp, _vp, _sz, _vp]),
     "ddf_load_weights_device": (C.c_int, [_vp, _vp, _sz, _vp]),
+    "ddf_sample_rays": (C.c_int, [_vp, _i32, _vp, _i32, _u64, _u64, _i64, C.c_float, _RAYS, _vp]),
+    "ddf_shift_rays": (C.c_int, [_RAYS, _vp, _vp, _i64, _i64, _u64, _u64, _vp]),
+    "ddf_distill": (C.c_int, [_vp, _vp, _i32, _vp, _i32, _i64, _i64, C.c_float, C.c_float,
+                              C.c_float, _u64, _vp, _vp]),
     "ddf_get_grad": (C.c_int, [_vp, _vp, _sz]),
     "ddf_reset_optimizer": (C.c_int, [_vp]),
     "ddf_cast_scene": (C.c_int, [_vp, _i32, _vp, _i32, _RAYS, _i64, _vp, _vp, _vp]),
@@ -276,6 +280,29 @@ def ddf_copy_grad(h, out, stream=None) -> None:
 
 def ddf_load_weights_device(h, blob, stream=None) -> None:
     _call("ddf_load_weights_device", h, _ptr(blob), int(blob.numel()), _stream(stream))
+
+
+def ddf_sample_rays(spheres, n_spheres, boxes, n_boxes, seed, step, n, surface_frac, rays_out,
+                    stream=None) -> None:
+    rp, keep = _rays(rays_out)
+    _call("ddf_sample_rays", _ptr(spheres), int(n_spheres), _ptr(boxes), int(n_boxes), int(seed),
+          int(step), int(n), float(surface_frac), rp, _stream(stream))
+
+
+def ddf_shift_rays(rays, t, hit, n, first, seed, step, stream=None) -> None:
+    rp, keep = _rays(rays)
+    _call("ddf_shift_rays", rp, _ptr(t), _ptr(hit), int(n), int(first), int(seed), int(step),
+          _stream(stream))
+
+
+def ddf_distill(h, spheres, n_spheres, boxes, n_boxes, steps, batch, lr0, surface_frac=0.5,
+                shift_frac=0.3, seed=0, stream=None) -> np.ndarray:
+    """Runs the schedule; returns the per-step losses (host float32)."""
+    losses = np.zeros(int(steps), np.float32)
+    _call("ddf_distill", h, _ptr(spheres), int(n_spheres), _ptr(boxes), int(n_boxes), int(steps),
+          int(batch), float(lr0), float(surface_frac), float(shift_frac), int(seed),
+          losses.ctypes.data, _stream(stream))
+    return losses
 
 
 def ddf_get_grad(h, n: int) -> np.ndarray:

@@ -1,0 +1,157 @@
+"""GPU tests of the distillation schedule (Sec. 3.2 / 3.4): the training-ray
+sampler (camera rays, surface-anchored rays), the ray-march shifted points,
+and the whole schedule on a hash-grid and a sinusoidal field, with the
+learned field checked against exact casts of held-out rays."""
+import numpy as np
+import pytest
+
+from oracle import ddf_oracle as O
+from paper_2606_00817_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda(cuda_lib):
+    import torch
+    return torch
+
+
+def _scene(torch, ns=32, nb=32):
+    scene = I.random_scene(ns, nb, seed=0)
+    sph = torch.from_numpy(np.concatenate([scene.centers, scene.radii[:, None]], 1)
+                           .astype(np.float32).ravel()).cuda()
+    box = torch.from_numpy(np.concatenate([scene.box_lo, scene.box_hi], 1)
+                           .astype(np.float32).ravel()).cuda()
+    return scene, sph, box
+
+
+def _sample(torch, ddf, sph, box, n, seed, step, frac=0.5):
+    out = [torch.empty(n, device="cuda") for _ in range(6)]
+    ddf.ddf_sample_rays(sph, 32, box, 32, seed, step, n, frac, out)
+    torch.cuda.synchronize()
+    return out
+
+
+def _prim_dist(scene, p):
+    """|signed distance| to every primitive's own surface, [n, primitives]."""
+    ds = [np.abs(np.linalg.norm(p - c, axis=1) - r) for c, r in zip(scene.centers, scene.radii)]
+    for lo, hi in zip(scene.box_lo, scene.box_hi):
+        q = np.abs(p - 0.5 * (lo + hi)) - 0.5 * (hi - lo)
+        ds.append(np.abs(np.linalg.norm(np.maximum(q, 0), axis=1) + np.minimum(q.max(1), 0)))
+    return np.stack(ds, 1)
+
+
+def test_sampler_camera_and_surface_rays(torch_cuda):
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    scene, sph, box = _scene(torch)
+    n = 100_000
+    r = [a.double().cpu().numpy() for a in _sample(torch, ddf, sph, box, n, 7, 3)]
+    o, d = np.stack(r[:3], 1), np.stack(r[3:], 1)
+    assert np.abs(np.linalg.norm(d, axis=1) - 1).max() < 1e-5
+    cam = np.any(np.abs(o) == 1.0, axis=1) & np.all(np.abs(o) <= 1.0, axis=1)
+    surf = ~cam
+    assert 0.48 < surf.mean() < 0.52
+    # camera rays start on a face and point into the box
+    axis = np.argmax(np.abs(o[cam]), axis=1)
+    side = np.sign(o[cam][np.arange(cam.sum()), axis])
+    assert np.all(d[cam][np.arange(cam.sum()), axis] * side < 0)
+    # surface rays start 1e-3 off some primitive's surface
+    dist = _prim_dist(scene, o[surf][:5000])
+    assert np.all(np.abs(dist - 1e-3).min(axis=1) < 2e-5)
+    # their directions cover the whole sphere
+    assert abs(d[surf].mean(axis=0)).max() < 0.02
+    # counter-based: the same (seed, step) gives the same rays, another step others
+    r2 = _sample(torch, ddf, sph, box, n, 7, 3)
+    r3 = _sample(torch, ddf, sph, box, n, 7, 4)
+    assert all(np.array_equal(a, b.double().cpu().numpy()) for a, b in zip(r, r2))
+    assert not np.array_equal(r[0], r3[0].double().cpu().numpy())
+
+
+def test_shifted_rays_keep_their_hit(torch_cuda):
+    """A ray that hits at t, moved forward by s along itself, hits at t - s:
+    recasting the shifted rays gives back the shifted targets."""
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    scene, sph, box = _scene(torch)
+    n = 50_000
+    rays = _sample(torch, ddf, sph, box, n, 9, 0)
+    t = torch.empty(n, device="cuda")
+    hit = torch.empty(n, dtype=torch.uint8, device="cuda")
+    ddf.ddf_cast_scene(sph, 32, box, 32, rays, n, t, hit)
+    before = [a.clone() for a in rays]
+    first = n - 15_000
+    ddf.ddf_shift_rays(rays, t, hit, n, first, 9, 0)
+    t2 = torch.empty(n, device="cuda")
+    hit2 = torch.empty(n, dtype=torch.uint8, device="cuda")
+    ddf.ddf_cast_scene(sph, 32, box, 32, rays, n, t2, hit2)
+    torch.cuda.synchronize()
+    h = hit.cpu().numpy().astype(bool)
+    assert all(torch.equal(a[:first], b[:first]) for a, b in zip(rays, before))   # untouched head
+    moved = np.zeros(n, bool)
+    moved[first:] = h[first:]
+    o0 = np.stack([a.cpu().numpy() for a in before[:3]], 1)
+    o1 = np.stack([a.cpu().numpy() for a in rays[:3]], 1)
+    assert np.all(np.linalg.norm(o1 - o0, axis=1)[moved] > 0) or moved.sum() == 0
+    tt, tt2 = t.cpu().numpy(), t2.cpu().numpy()
+    h2 = hit2.cpu().numpy().astype(bool)
+    assert np.mean(h2[moved]) > 0.999
+    ok = moved & h2
+    # grazing hits are ill-conditioned: a float32-rounded origin moves them
+    err = np.abs(tt2[ok] - tt[ok]) / np.maximum(1.0, tt[ok])
+    assert np.mean(err <= 2e-4) > 0.999 and np.median(err) < 1e-6
+
+
+def _held_out(torch, ddf, sph, box, n=65536):
+    ev = _sample(torch, ddf, sph, box, n, 12345, 0)
+    tt = torch.empty(n, device="cuda")
+    hit = torch.empty(n, dtype=torch.uint8, device="cuda")
+    ddf.ddf_cast_scene(sph, 32, box, 32, ev, n, tt, hit)
+    torch.cuda.synchronize()
+    return ev, tt.cpu().numpy(), hit.cpu().numpy().astype(bool)
+
+
+def _quality(torch, m, ev, tr, hr):
+    t, v = m.query(ev)
+    torch.cuda.synchronize()
+    t, v = t.cpu().numpy(), v.cpu().numpy()
+    dt = np.abs(np.minimum(t, 4) - np.minimum(tr, 4))[hr]
+    return np.mean((v > 0.5) == hr), np.median(dt)
+
+
+def test_distill_hashgrid_field(torch_cuda):
+    """The paper's recipe (Sec. 3.4: hash grid + 2x64 MLP, Adam 3e-3 with a
+    cosine decay to 5 %, batch 16,384, 30 % shifted points) for 2,000 steps on
+    32 spheres + 32 boxes: the loss falls by more than half, and on held-out
+    rays the hit flag is right for more than 88 % and the median distance
+    error is below 0.08 (measured on GB300: 91 % and 0.047)."""
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    scene, sph, box = _scene(torch)
+    n = ddf.ddf_param_count(ddf.make_config(4, 64, 2, kind="hashgrid"))
+    blob = I.hashgrid_blob(n, O.hashgrid_mlp_dims(), seed=0, table_scale=1e-4)
+    m = ddf.DDF(4, 64, 2, precision="bf16", kind="hashgrid")
+    m.load(blob)
+    losses = ddf.ddf_distill(m.h, sph, 32, box, 32, 2000, 16384, 3e-3, 0.5, 0.3, seed=1)
+    assert np.all(np.isfinite(losses))
+    assert losses[-50:].mean() < 0.5 * losses[:5].mean()
+    acc, med = _quality(torch, m, *_held_out(torch, ddf, sph, box))
+    assert acc > 0.88 and med < 0.08, (acc, med)
+    assert ddf.ddf_check_status(m.h) == 0
+
+
+def test_distill_sinusoidal_field(torch_cuda):
+    """The same schedule on the small sinusoidal field (78 -> 128x4 -> 2,
+    bf16) for 300 steps: the loss falls and the held-out hit flag beats the
+    constant guess (measured on GB300: 83.9 % against 83.2 %)."""
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    scene, sph, box = _scene(torch)
+    m = ddf.DDF(6, 128, 4, precision="bf16")
+    m.load(I.xavier_blob(I.NetShape(6, 128, 4)))
+    losses = ddf.ddf_distill(m.h, sph, 32, box, 32, 300, 16384, 1e-3, 0.5, 0.3, seed=2)
+    assert losses[-20:].mean() < 0.7 * losses[:5].mean()
+    ev, tr, hr = _held_out(torch, ddf, sph, box)
+    acc, _ = _quality(torch, m, ev, tr, hr)
+    assert acc > max(hr.mean(), 1 - hr.mean()) + 0.003, acc
