@@ -28,6 +28,7 @@ What the paper fixes and what this module reads into it:
     geometry is a union of spheres and boxes with closed-form intersections.
   * Sec. 4.4: sphere tracing an SDF is the sequential baseline.
   * Sec. 3.4: the hash-grid field (readings in its section below).
+  * Sec. 3.3 / the application: shadow and AO images (readings below).
 
 Reduced-precision modes emulate where the GPU path rounds (bf16 operands,
 or e4m3 operands with per-output-channel weight scales and per-tensor
@@ -668,6 +669,138 @@ def hashgrid_forward(o, d, blob, width=64, hidden=2, bands=HG_DIR_BANDS, precisi
                            encode_dir(d, bands)], axis=1)
     z = mlp_forward(code, layers, precision)
     return {"t": softplus(z[:, 0]), "vis": sigmoid(z[:, 1]), "z": z}
+
+
+# ------------------------------------- shadow / AO images (Sec. 3.3, app.)
+#
+# The paper's application: per pixel of a camera image, a primary hit, then a
+# shadow ray toward a point light and hemisphere rays for ambient occlusion,
+# answered by the field. Readings (the paper gives no camera or sampler):
+#   * pinhole camera: forward f = (target - eye)/|.|, right r = f x up /|.|,
+#     u = r x f; pixel (x, y) (row 0 at the top) looks along
+#     f + sx r + sy u, sx = (2 (x + 0.5)/W - 1) tan(fov/2) W/H,
+#     sy = (1 - 2 (y + 0.5)/H) tan(fov/2);
+#   * primary hits exact (caster); shading normal = the outward normal of the
+#     primitive whose surface holds the hit point, flipped to face the eye;
+#     secondary origins 1e-3 off the surface along it;
+#   * shadow: occluded when the ray toward the light hits closer than the
+#     light; AO: 1 - mean hit flag over k cosine-weighted directions (Malley:
+#     r = sqrt(u1), phi = 2 pi u2, z = sqrt(1 - u1)) in the orthonormal basis
+#     of Duff et al. (2017) around the normal;
+#   * uniforms: SplitMix64 (Steele, Lea, Flood), u = (mix(key + m) >> 40) 2^-24
+#     with key = mix(mix(seed xor 0x5DEECE66D) + pixel) xor (sample x
+#     0x2545F4914F6CDD1D), m = 0, 1 for (u1, u2);
+#   * background pixels read -1 in both images.
+
+_U64 = np.uint64
+
+
+def splitmix64(x):
+    """SplitMix64 output for state x (the state is advanced by the golden
+    gamma first): uint64 in, uint64 out (wrapping arithmetic)."""
+    with np.errstate(over="ignore"):
+        z = np.asarray(x, _U64) + _U64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> _U64(30))) * _U64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> _U64(27))) * _U64(0x94D049BB133111EB)
+        return z ^ (z >> _U64(31))
+
+
+def gi_uniform(seed, pixel, sample, m):
+    """The m-th uniform of (pixel, sample): 24-bit, exact in float32."""
+    with np.errstate(over="ignore"):
+        key = splitmix64(splitmix64(_U64(seed) ^ _U64(0x5DEECE66D)) + np.asarray(pixel, _U64)) \
+            ^ (np.asarray(sample, _U64) * _U64(0x2545F4914F6CDD1D))
+        return (splitmix64(key + _U64(m)) >> _U64(40)).astype(F64) * 2.0 ** -24
+
+
+def camera_rays(eye, target, up, fov_y, width, height):
+    """Pixel-centre rays of a pinhole camera, pixel index y * width + x."""
+    eye = np.asarray(eye, F64)
+    f = np.asarray(target, F64) - eye
+    f /= np.linalg.norm(f)
+    r = np.cross(f, np.asarray(up, F64))
+    r /= np.linalg.norm(r)
+    u = np.cross(r, f)
+    th = np.tan(0.5 * fov_y)
+    y, x = np.mgrid[0:height, 0:width]
+    sx = (2 * (x.ravel() + 0.5) / width - 1) * th * width / height
+    sy = (1 - 2 * (y.ravel() + 0.5) / height) * th
+    d = f[None, :] + sx[:, None] * r[None, :] + sy[:, None] * u[None, :]
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return np.repeat(eye[None, :], width * height, axis=0), d
+
+
+def surface_normal(scene, p):
+    """Outward normal at points p on the scene's surfaces: of the primitive
+    whose surface lies nearest p (sphere: radial; box: the nearest face)."""
+    p = np.asarray(p, F64)
+    cand_d, cand_n = [], []
+    for c, r in zip(scene.centers, scene.radii):
+        v = p - c
+        dist = np.linalg.norm(v, axis=1)
+        cand_d.append(np.abs(dist - r))
+        cand_n.append(v / np.maximum(dist, 1e-300)[:, None])
+    for lo, hi in zip(scene.box_lo, scene.box_hi):
+        gaps = np.stack([np.abs(p - lo), np.abs(p - hi)], axis=2)       # [n, 3 axes, 2 sides]
+        inside = np.all((p >= lo - 1e-9) & (p <= hi + 1e-9), axis=1)
+        flat = gaps.reshape(p.shape[0], 6)
+        k = np.argmin(flat, axis=1)
+        face_gap = flat[np.arange(p.shape[0]), k]
+        # distance to the box surface (off-face points are farther than the gap)
+        out = np.linalg.norm(np.maximum(np.maximum(lo - p, p - hi), 0.0), axis=1)
+        cand_d.append(np.where(inside, face_gap, np.maximum(out, face_gap)))
+        n = np.zeros_like(p)
+        n[np.arange(p.shape[0]), k // 2] = np.where(k % 2 == 1, 1.0, -1.0)
+        cand_n.append(n)
+    j = np.argmin(np.stack(cand_d, 1), axis=1)
+    return np.stack(cand_n, 1)[np.arange(p.shape[0]), j]
+
+
+def onb(n):
+    """Orthonormal tangents (t1, t2) with t1 x t2 = n (Duff et al. 2017)."""
+    n = np.asarray(n, F64)
+    sgn = np.where(n[:, 2] >= 0, 1.0, -1.0)
+    a = -1.0 / (sgn + n[:, 2])
+    b = n[:, 0] * n[:, 1] * a
+    t1 = np.stack([1 + sgn * n[:, 0] ** 2 * a, sgn * b, -sgn * n[:, 0]], 1)
+    t2 = np.stack([b, sgn + n[:, 1] ** 2 * a, -n[:, 1]], 1)
+    return t1, t2
+
+
+def cosine_dirs(n, u1, u2):
+    """Malley's method: cosine-weighted directions about unit normals n."""
+    r = np.sqrt(u1)
+    phi = 2 * np.pi * u2
+    z = np.sqrt(np.maximum(0.0, 1 - u1))
+    t1, t2 = onb(n)
+    return (r * np.cos(phi))[:, None] * t1 + (r * np.sin(phi))[:, None] * t2 + z[:, None] * n
+
+
+def gi_images(scene, eye, target, up, fov_y, width, height, light, ao_samples, seed):
+    """Shadow (1 lit, 0 shadowed) and ambient-occlusion images of the scene
+    from exact casts; background -1. Returns (shadow, ao) [height, width]."""
+    o, d = camera_rays(eye, target, up, fov_y, width, height)
+    t, hit = cast_scene(scene, o, d)
+    npx = width * height
+    shadow = -np.ones(npx)
+    ao = -np.ones(npx)
+    idx = np.nonzero(hit)[0]
+    p = o[idx] + t[idx, None] * d[idx]
+    nrm = surface_normal(scene, p)
+    nrm = np.where(np.sum(nrm * d[idx], axis=1, keepdims=True) > 0, -nrm, nrm)
+    sp = p + 1e-3 * nrm
+    to_l = np.asarray(light, F64)[None, :] - sp
+    dist = np.linalg.norm(to_l, axis=1)
+    ts, hs = cast_scene(scene, sp, to_l / dist[:, None])
+    shadow[idx] = np.where(hs & (ts < dist), 0.0, 1.0)
+    hits = np.zeros(idx.size)
+    for j in range(ao_samples):
+        u1 = gi_uniform(seed, idx, j, 0)
+        u2 = gi_uniform(seed, idx, j, 1)
+        _, ha = cast_scene(scene, sp, cosine_dirs(nrm, u1, u2))
+        hits += ha
+    ao[idx] = 1.0 - hits / ao_samples
+    return shadow.reshape(height, width), ao.reshape(height, width)
 
 
 # ----------------------------------------------------------- queries

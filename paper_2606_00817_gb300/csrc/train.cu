@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 
 #include "kernels.h"
+#include "caster.cuh"
 
 namespace ddf {
 
@@ -237,11 +238,7 @@ __global__ void pack_bf16_t_kernel(const float* __restrict__ src, int N, int K,
   dst[idx] = __float2bfloat16_rn(src[static_cast<int64_t>(n) * K + k]);
 }
 
-// Exact first hit of each ray against spheres (cx,cy,cz,r) and boxes
-// (lo xyz, hi xyz): nearest positive root of each primitive, minimum over all
-// (surfaces, not CSG). Tangent rays hit; slabs are closed. Miss: t = +inf.
-constexpr int kMaxPrims = 1024;
-
+// Exact first hit of each ray (caster.cuh), primitives staged in shared memory.
 __global__ void cast_scene_kernel(const float* __restrict__ spheres, int ns,
                                   const float* __restrict__ boxes, int nb, RaySoA rays, int64_t n,
                                   float* __restrict__ t_out, uint8_t* __restrict__ hit_out) {
@@ -254,39 +251,7 @@ __global__ void cast_scene_kernel(const float* __restrict__ spheres, int ns,
   if (i >= n) return;
   const float o[3] = {rays.p[0][i], rays.p[1][i], rays.p[2][i]};
   const float d[3] = {rays.p[3][i], rays.p[4][i], rays.p[5][i]};
-  const float a = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-  float best = __int_as_float(0x7f800000);
-  for (int s = 0; s < ns; ++s) {
-    const float oc0 = o[0] - s_sph[4 * s], oc1 = o[1] - s_sph[4 * s + 1], oc2 = o[2] - s_sph[4 * s + 2];
-    const float r = s_sph[4 * s + 3];
-    const float b = d[0] * oc0 + d[1] * oc1 + d[2] * oc2;
-    const float q = oc0 * oc0 + oc1 * oc1 + oc2 * oc2 - r * r;
-    const float disc = b * b - a * q;
-    if (disc < 0.f) continue;
-    const float sq = sqrtf(disc);
-    const float hh = -b - (b >= 0.f ? sq : -sq);  // no cancellation
-    if (hh == 0.f) continue;
-    const float r1 = hh / a, r2 = q / hh;
-    const float lo = fminf(r1, r2), hi = fmaxf(r1, r2);
-    const float t = lo > 0.f ? lo : hi;
-    if (t > 0.f) best = fminf(best, t);
-  }
-  for (int bx = 0; bx < nb; ++bx) {
-    float tn = -__int_as_float(0x7f800000), tf = __int_as_float(0x7f800000);
-    bool miss = false;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const float lo = s_box[6 * bx + k], hi = s_box[6 * bx + 3 + k];
-      if (d[k] == 0.f) {
-        miss |= (o[k] < lo) || (o[k] > hi);
-      } else {
-        const float ta = (lo - o[k]) / d[k], tb = (hi - o[k]) / d[k];
-        tn = fmaxf(tn, fminf(ta, tb));
-        tf = fminf(tf, fmaxf(ta, tb));
-      }
-    }
-    if (!miss && tn <= tf && tf > 0.f) best = fminf(best, tn > 0.f ? tn : tf);
-  }
+  const float best = cast_one(o, d, s_sph, ns, s_box, nb, nullptr);
   t_out[i] = best;
   hit_out[i] = best < __int_as_float(0x7f800000) ? 1 : 0;
 }
