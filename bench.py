@@ -274,6 +274,34 @@ def hashgrid_workload(torch, ddf, dev, local, stream, flush, d_rays, R):
                       "held_out_median_abs_dt": float(np.median(dte)),
                       "held_out_mean_abs_dt": float(dte.mean()),
                       "status": ddf.ddf_check_status(m.h)}
+    # the application (Sec. 3.3): shadow and AO images, 512 x 512, 16 AO
+    # rays, secondary rays answered by the distilled field vs the exact caster
+    W = H = 512
+    k = 16
+    cam = (2.5, 1.8, -3.0, 0.0, 0.0, 0.0, 0.0, 1.0, 0.0, float(np.radians(50.0)))
+    imgs = {}
+    for name, hh_ in (("field", m.h), ("exact", None)):
+        sh_i = torch.empty(W * H, device=dev)
+        ao_i = torch.empty(W * H, device=dev)
+        ddf.ddf_render_gi(hh_, sph, ns, box, nb, cam, W, H, LIGHT, k, 5, sh_i, ao_i, stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ddf.ddf_render_gi(hh_, sph, ns, box, nb, cam, W, H, LIGHT, k, 5, sh_i, ao_i, stream)
+        imgs[name] = (time.perf_counter() - t0, sh_i.cpu().numpy(), ao_i.cpu().numpy())
+    fg = imgs["exact"][1] >= 0
+    psnr = lambda a, b, msk: float(10 * np.log10(1.0 / max(np.mean((a[msk] - b[msk]) ** 2), 1e-12)))
+    full = np.ones_like(fg)
+    res["gi"] = {"width": W, "height": H, "ao_rays_per_pixel": k,
+                 "foreground_frac": float(fg.mean()),
+                 "field_render_s": imgs["field"][0], "exact_render_s": imgs["exact"][0],
+                 "secondary_rays": int(W * H * (1 + k)),
+                 "shadow_psnr_foreground_db": psnr(imgs["field"][1], imgs["exact"][1], fg),
+                 "ao_psnr_foreground_db": psnr(imgs["field"][2], imgs["exact"][2], fg),
+                 "shadow_psnr_image_db": psnr(np.where(fg, imgs["field"][1], 1.0),
+                                              np.where(fg, imgs["exact"][1], 1.0), full),
+                 "ao_psnr_image_db": psnr(np.where(fg, imgs["field"][2], 1.0),
+                                          np.where(fg, imgs["exact"][2], 1.0), full),
+                 "paper_context": "shadow 30.3 dB, AO 21.3 dB over 142 scanned objects (Table e4)"}
     m.close()
     # gather traffic: 16 levels x 8 corners x one 4-byte bf16 entry pair per
     # ray, plus 24 B of ray and 9 B of outputs; the 26 MB bf16 table stays in L2

@@ -299,6 +299,26 @@ ddf_status ddf_distill(ddf_handle h, const float* spheres, int32_t n_spheres, co
                        float surface_frac, float shift_frac, uint64_t seed, float* losses,
                        void* stream);
 
+/* ---- shadow and ambient-occlusion images (the application, Sec. 3.3) ----
+ * For a pinhole camera (camera = eye[3], target[3], up[3], fov_y in radians;
+ * pixel (x, y), row 0 at the top, looks along f + sx r + sy u with
+ * sx = (2 (x + 0.5) / width - 1) tan(fov_y / 2) width / height,
+ * sy = (1 - 2 (y + 0.5) / height) tan(fov_y / 2), f = (target - eye)/|.|,
+ * r = f x up / |.|, u = r x f): the exact primary hit on the analytic scene,
+ * its shading point 1e-3 off the surface along the normal (facing the eye),
+ * one shadow ray toward `light` and `ao_samples` cosine-weighted hemisphere
+ * rays (Malley's method in the Duff et al. basis; uniforms from SplitMix64
+ * per (seed, pixel, sample)). The secondary rays are answered by the field h
+ * (occluded iff z1 > 0 and t below the light distance; a hemisphere ray
+ * counts when z1 > 0), or by the exact caster when h is NULL (the reference
+ * image). out_shadow (device float[height x width], nullable): 1 lit, 0 in
+ * shadow; out_ao (nullable): 1 - mean hit flag; background pixels -1.
+ * Allocates its ray buffers for the call; synchronous. */
+ddf_status ddf_render_gi(ddf_handle h, const float* spheres, int32_t n_spheres,
+                         const float* boxes, int32_t n_boxes, const float camera[10],
+                         int32_t width, int32_t height, const float light[3], int32_t ao_samples,
+                         uint64_t seed, float* out_shadow, float* out_ao, void* stream);
+
 /* Copies the last computed gradient (weight-blob layout, ddf_param_count
  * floats) to host memory. Synchronous. */
 ddf_status ddf_get_grad(ddf_handle h, float* host_grad, size_t n_floats);

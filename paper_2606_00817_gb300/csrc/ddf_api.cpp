@@ -1365,3 +1365,93 @@ ddf_status ddf_internal_query_in_workspace(ddf_handle h, const float* const rays
 
 // Records msg as the calling thread's last error and returns s.
 ddf_status ddf_internal_set_error(ddf_status s, const char* msg) { return fail(s, msg); }
+
+// ---------------------------------------------------------------------------
+// Shadow and AO images (the application of Sec. 3.3).
+
+extern "C" ddf_status ddf_render_gi(ddf_handle h, const float* spheres, int32_t n_spheres,
+                                    const float* boxes, int32_t n_boxes, const float camera[10],
+                                    int32_t width, int32_t height, const float light[3],
+                                    int32_t ao_samples, uint64_t seed, float* out_shadow,
+                                    float* out_ao, void* stream) {
+  if (camera == nullptr || light == nullptr) return fail(DDF_ERR_INVALID_ARG, "NULL camera or light");
+  if (width < 1 || height < 1 || static_cast<int64_t>(width) * height > (int64_t{1} << 26))
+    return fail(DDF_ERR_INVALID_ARG, "width, height >= 1 and at most 2^26 pixels");
+  const int k = out_ao != nullptr ? ao_samples : 0;
+  if (out_ao != nullptr && (ao_samples < 1 || ao_samples > 1024))
+    return fail(DDF_ERR_INVALID_ARG, "ao_samples must be in [1, 1024]");
+  if (n_spheres < 0 || n_boxes < 0 || n_spheres > 1024 || n_boxes > 1024)
+    return fail(DDF_ERR_INVALID_ARG, "0..1024 spheres and 0..1024 boxes");
+  if ((n_spheres > 0 && spheres == nullptr) || (n_boxes > 0 && boxes == nullptr))
+    return fail(DDF_ERR_INVALID_ARG, "primitive array is NULL");
+  ddf_status s = DDF_OK;
+  if (h != nullptr && (s = check_ready(h)) != DDF_OK) return s;
+  // camera basis in double, as the pinhole model defines it
+  double e[3], f[3], up[3];
+  for (int c = 0; c < 3; ++c) e[c] = camera[c], f[c] = camera[3 + c] - camera[c], up[c] = camera[6 + c];
+  const double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+  double r[3] = {f[1] * up[2] - f[2] * up[1], f[2] * up[0] - f[0] * up[2], f[0] * up[1] - f[1] * up[0]};
+  if (!(fl > 0.0)) return fail(DDF_ERR_INVALID_ARG, "eye and target coincide");
+  for (double& v : f) v /= fl;
+  r[0] = f[1] * up[2] - f[2] * up[1];
+  r[1] = f[2] * up[0] - f[0] * up[2];
+  r[2] = f[0] * up[1] - f[1] * up[0];
+  const double rl = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  if (!(rl > 0.0)) return fail(DDF_ERR_INVALID_ARG, "up is parallel to the view direction");
+  for (double& v : r) v /= rl;
+  const double u[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
+  ddf::GiCamera cam{};
+  for (int c = 0; c < 3; ++c) {
+    cam.eye[c] = static_cast<float>(e[c]);
+    cam.f[c] = static_cast<float>(f[c]);
+    cam.r[c] = static_cast<float>(r[c]);
+    cam.u[c] = static_cast<float>(u[c]);
+  }
+  cam.tan_half = static_cast<float>(std::tan(0.5 * camera[9]));
+  cam.width = width;
+  cam.height = height;
+  int dev = 0;
+  if (h != nullptr) dev = h->cfg.device;
+  else DDF_CK(cudaGetDevice(&dev));
+  DeviceGuard g(dev);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t npx = static_cast<int64_t>(width) * height;
+  const int64_t n2 = npx * (1 + k);
+  // shading points, normals, 6 ray arrays, t, hit flags
+  const size_t bytes = npx * sizeof(float4) + 3 * npx * sizeof(float) + 7 * n2 * sizeof(float) + n2;
+  uint8_t* buf = nullptr;
+  DDF_CK(cudaMalloc(&buf, bytes));
+  float4* sp = reinterpret_cast<float4*>(buf);
+  float* nrm = reinterpret_cast<float*>(sp + npx);
+  float* rp = nrm + 3 * npx;
+  float* t = rp + 6 * n2;
+  uint8_t* hit = reinterpret_cast<uint8_t*>(t + n2);
+  ddf::RayOut ro;
+  const float* rc[6];
+  for (int c = 0; c < 6; ++c) ro.p[c] = rp + c * n2, rc[c] = ro.p[c];
+  cudaError_t ce = ddf::launch_gi_primary(cam, spheres, n_spheres, boxes, n_boxes, sp, nrm, st);
+  if (ce == cudaSuccess) ce = ddf::launch_gi_rays(sp, nrm, npx, k, seed, light, ro, st);
+  if (ce != cudaSuccess) s = cuda_fail(ce, "gi ray generation");
+  if (s == DDF_OK) {
+    if (h != nullptr) {
+      ddf::HeadOut o{};
+      o.t = t;
+      o.hit = hit;
+      s = run_query(h, rc, n2, o, st);
+    } else {
+      ddf::RaySoA rs;
+      for (int c = 0; c < 6; ++c) rs.p[c] = rc[c];
+      ce = ddf::launch_cast_scene(spheres, n_spheres, boxes, n_boxes, rs, n2, t, hit, st);
+      if (ce != cudaSuccess) s = cuda_fail(ce, "cast");
+    }
+  }
+  if (s == DDF_OK) {
+    ce = ddf::launch_gi_compose(sp, npx, k, light, t, hit, out_shadow, out_ao, st);
+    if (ce != cudaSuccess) s = cuda_fail(ce, "gi compose");
+  }
+  ce = cudaStreamSynchronize(st);
+  cudaFree(buf);
+  if (s == DDF_OK && ce != cudaSuccess) s = cuda_fail(ce, "cudaStreamSynchronize");
+  return s;
+}
+

@@ -4,32 +4,22 @@
 // consistent along a ray (a ray that hits at t, moved forward by s along
 // itself, hits at t - s).
 //
-// Random numbers come from a counter-based SplitMix64 (Steele, Lea and Flood's
-// 64-bit mixing function): draw j of ray i at step k is
-// mix(key(seed, k, i) + j), so any ray of any step can be regenerated alone.
+// Random numbers come from the counter-based SplitMix64 of rng.cuh: draw j of
+// ray i at step k is mix(key(seed, k, i) + j), so any ray of any step can be
+// regenerated alone.
 #include <cstdint>
 
 #include "kernels.h"
+#include "rng.cuh"
 
 namespace ddf {
 
 namespace {
 
-__device__ __forceinline__ uint64_t sm64(uint64_t x) {
-  x += 0x9E3779B97F4A7C15ull;
-  uint64_t z = x;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
-// Uniform float in [0, 1) from the top 24 bits.
-__device__ __forceinline__ float u01(uint64_t key, int j) {
-  return static_cast<float>(sm64(key + static_cast<uint64_t>(j)) >> 40) * (1.0f / 16777216.0f);
-}
+__device__ __forceinline__ float u01(uint64_t key, int j) { return rng_u01(key, j); }
 
 __device__ __forceinline__ uint64_t ray_key(uint64_t seed, uint64_t step, int64_t i) {
-  return sm64(sm64(seed ^ 0x5DEECE66Dull) + step) ^ (static_cast<uint64_t>(i) * 0x2545F4914F6CDD1Dull);
+  return rng_key(seed, step, static_cast<uint64_t>(i));
 }
 
 // Unit vector uniform on the sphere from two uniforms.

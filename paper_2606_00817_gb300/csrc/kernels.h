@@ -238,4 +238,25 @@ cudaError_t launch_sample_rays(const float* spheres, int ns, const float* boxes,
 cudaError_t launch_shift_rays(RayOut r, float* t, const uint8_t* hit, int64_t n, int64_t first,
                               uint64_t seed, uint64_t step, cudaStream_t s);
 
+// ---- shadow / AO images (gi.cu) ----
+// Pinhole camera: eye, unit forward f, right r, up u, tan(fov_y / 2).
+struct GiCamera {
+  float eye[3], f[3], r[3], u[3];
+  float tan_half;
+  int width, height;
+};
+// Per pixel the exact primary hit: shading point (xyz, w = 1 hit / 0 none)
+// 1e-3 off the surface along the normal, and the normal [3 per pixel] facing
+// the eye.
+cudaError_t launch_gi_primary(const GiCamera& cam, const float* spheres, int ns, const float* boxes,
+                              int nb, float4* sp, float* nrm, cudaStream_t s);
+// (1 + k) rays per pixel: toward the light, then k cosine-weighted ones.
+cudaError_t launch_gi_rays(const float4* sp, const float* nrm, int64_t npx, int k, uint64_t seed,
+                           const float light[3], RayOut r, cudaStream_t s);
+// Images from the secondary rays' t and hit flags (background -1).
+cudaError_t launch_gi_compose(const float4* sp, int64_t npx, int k, const float light[3],
+                              const float* t, const uint8_t* hit, float* shadow, float* ao,
+                              cudaStream_t s);
+
 }  // namespace ddf
+

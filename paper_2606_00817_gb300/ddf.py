@@ -71,6 +71,8 @@ SIGNATURES = {
     "ddf_shift_rays": (C.c_int, [_RAYS, _vp, _vp, _i64, _i64, _u64, _u64, _vp]),
     "ddf_distill": (C.c_int, [_vp, _vp, _i32, _vp, _i32, _i64, _i64, C.c_float, C.c_float,
                               C.c_float, _u64, _vp, _vp]),
+    "ddf_render_gi": (C.c_int, [_vp, _vp, _i32, _vp, _i32, _vp, _i32, _i32, _vp, _i32, _u64, _vp,
+                                _vp, _vp]),
     "ddf_get_grad": (C.c_int, [_vp, _vp, _sz]),
     "ddf_reset_optimizer": (C.c_int, [_vp]),
     "ddf_cast_scene": (C.c_int, [_vp, _i32, _vp, _i32, _RAYS, _i64, _vp, _vp, _vp]),
@@ -303,6 +305,17 @@ def ddf_distill(h, spheres, n_spheres, boxes, n_boxes, steps, batch, lr0, surfac
           int(batch), float(lr0), float(surface_frac), float(shift_frac), int(seed),
           losses.ctypes.data, _stream(stream))
     return losses
+
+
+def ddf_render_gi(h, spheres, n_spheres, boxes, n_boxes, camera, width, height, light, ao_samples,
+                  seed, out_shadow, out_ao, stream=None) -> None:
+    """camera = (eye xyz, target xyz, up xyz, fov_y); h = None renders with
+    the exact caster."""
+    cam = (C.c_float * 10)(*[float(v) for v in camera])
+    lt = (C.c_float * 3)(*[float(v) for v in light])
+    _call("ddf_render_gi", h, _ptr(spheres), int(n_spheres), _ptr(boxes), int(n_boxes), cam,
+          int(width), int(height), lt, int(ao_samples), int(seed), _ptr(out_shadow), _ptr(out_ao),
+          _stream(stream))
 
 
 def ddf_get_grad(h, n: int) -> np.ndarray:

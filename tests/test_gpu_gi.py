@@ -1,0 +1,92 @@
+"""GPU tests of the application images (Sec. 3.3): shadow and ambient
+occlusion rendered with the exact caster match the oracle pixel by pixel (up
+to float32 decisions at silhouettes and grazing rays), and rendered with a
+distilled hash-grid field they approach the exact images (PSNR)."""
+import numpy as np
+import pytest
+
+from oracle import ddf_oracle as O
+from paper_2606_00817_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+CAM = (2.5, 1.8, -3.0, 0.0, 0.0, 0.0, 0.0, 1.0, 0.0, np.radians(50.0))
+LIGHT = (3.0, 3.0, 3.0)
+
+
+@pytest.fixture(scope="module")
+def torch_cuda(cuda_lib):
+    import torch
+    return torch
+
+
+def _scene(torch, ns=32, nb=32):
+    scene = I.random_scene(ns, nb, seed=0)
+    sph = torch.from_numpy(np.concatenate([scene.centers, scene.radii[:, None]], 1)
+                           .astype(np.float32).ravel()).cuda()
+    box = torch.from_numpy(np.concatenate([scene.box_lo, scene.box_hi], 1)
+                           .astype(np.float32).ravel()).cuda()
+    return scene, sph, box
+
+
+def _render(torch, ddf, h, sph, box, W, H, k, seed=5, cam=CAM):
+    sh = torch.empty(H * W, device="cuda")
+    ao = torch.empty(H * W, device="cuda")
+    ddf.ddf_render_gi(h, sph, 32, box, 32, cam, W, H, LIGHT, k, seed, sh, ao)
+    torch.cuda.synchronize()
+    return sh.cpu().numpy().reshape(H, W).astype(np.float64), ao.cpu().numpy().reshape(H, W).astype(np.float64)
+
+
+def test_exact_render_matches_oracle(torch_cuda):
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    scene, sph, box = _scene(torch)
+    W, H, k = 96, 72, 8
+    sh, ao = _render(torch, ddf, None, sph, box, W, H, k)
+    rs, ra = O.gi_images(scene, CAM[0:3], CAM[3:6], CAM[6:9], CAM[9], W, H, LIGHT, k, 5)
+    fg_g, fg_r = sh >= 0, rs >= 0
+    assert np.mean(fg_g == fg_r) >= 0.995 and 0.2 < fg_r.mean() < 0.95
+    both = fg_g & fg_r
+    assert np.mean(sh[both] == rs[both]) >= 0.99
+    assert 0.05 < np.mean(rs[both] == 0) < 0.95                 # shadows exist, not everywhere
+    assert np.mean(ao[both] == ra[both]) >= 0.97
+    assert np.abs(ao[both] - ra[both]).mean() <= 0.01
+    assert np.all(ao[~fg_g] == -1) and np.all(sh[~fg_g] == -1)
+
+
+def test_render_of_empty_view_is_background(torch_cuda):
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    _, sph, box = _scene(torch)
+    away = (0.0, 0.0, -3.0, 0.0, 0.0, -10.0, 0.0, 1.0, 0.0, np.radians(30.0))   # looking away
+    sh, ao = _render(torch, ddf, None, sph, box, 16, 8, 4, cam=away)
+    assert np.all(sh == -1) and np.all(ao == -1)
+
+
+def _psnr(a, b, mask):
+    mse = np.mean((a[mask] - b[mask]) ** 2)
+    return 10 * np.log10(1.0 / max(mse, 1e-12))
+
+
+def test_field_render_approaches_exact(torch_cuda):
+    """A hash-grid field distilled for 3,000 steps (the paper's recipe)
+    renders shadow and AO images whose PSNR against the exact images, over
+    foreground pixels, is above 10 dB and 14.5 dB (measured on GB300 at
+    128 x 96 with 16 AO rays on this 64-primitive scene: 11.1-11.4 and 16.2
+    dB at 3,000 steps, 12.3 and 19.0 dB at 30,000), and its images use the
+    exact primary hits (same foreground)."""
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    scene, sph, box = _scene(torch)
+    n = ddf.ddf_param_count(ddf.make_config(4, 64, 2, kind="hashgrid"))
+    m = ddf.DDF(4, 64, 2, precision="bf16", kind="hashgrid")
+    m.load(I.hashgrid_blob(n, O.hashgrid_mlp_dims(), seed=0, table_scale=1e-4))
+    ddf.ddf_distill(m.h, sph, 32, box, 32, 3000, 16384, 3e-3, 0.5, 0.3, seed=1)
+    W, H, k = 128, 96, 16
+    fs, fa = _render(torch, ddf, m.h, sph, box, W, H, k)
+    es, ea = _render(torch, ddf, None, sph, box, W, H, k)
+    fg = es >= 0
+    assert np.array_equal(fs >= 0, fg)
+    ps, pa = _psnr(fs, es, fg), _psnr(fa, ea, fg)
+    assert ps > 10.0 and pa > 14.5, (ps, pa)
+    assert ddf.ddf_check_status(m.h) == 0
