@@ -29,6 +29,7 @@ What the paper fixes and what this module reads into it:
   * Sec. 4.4: sphere tracing an SDF is the sequential baseline.
   * Sec. 3.4: the hash-grid field (readings in its section below).
   * Sec. 3.3 / the application: shadow and AO images (readings below).
+  * Sec. 3.2 / Sec. 4.2 (the supervision study): Gaussian-rendered depth.
 
 Reduced-precision modes emulate where the GPU path rounds (bf16 operands,
 or e4m3 operands with per-output-channel weight scales and per-tensor
@@ -801,6 +802,107 @@ def gi_images(scene, eye, target, up, fov_y, width, height, light, ao_samples, s
         hits += ha
     ao[idx] = 1.0 - hits / ao_samples
     return shadow.reshape(height, width), ao.reshape(height, width)
+
+
+# ----------------------- Gaussian-rendered depth (Sec. 3.2, Sec. 4.2)
+#
+# The supervision source the paper finds too blurry for thin parts: depth
+# rendered from the scene's 3D Gaussians. Definitions (the standard 3DGS
+# depth composite, restated; the paper cites it and gives no formula):
+#   * camera as camera_rays; view coordinates (x, y, z) of a point along
+#     (r, u, f); pixel coordinates px = (x/z) fx + (W - 1)/2,
+#     py = -(y/z) fy + (H - 1)/2 with fx = W / (2 tan(fov/2) W/H),
+#     fy = H / (2 tan(fov/2)), so pixel (i, j) is looked at by camera ray
+#     j W + i;
+#   * screen covariance S = J V C V^T J^T + 0.3 I (EWA splatting, 3DGS's
+#     low-pass), V = rows (r, u, f), J the Jacobian of (px, py) at the mean;
+#   * alpha_i = min(0.99, o_i exp(-q/2)), q = dp^T S^-1 dp; contributions with
+#     alpha < 1/255 are skipped; Gaussians with z <= 0.05 are culled;
+#   * front to back by mean depth z (ties by index): T starts at 1; each
+#     contribution adds T alpha t_i to D and T alpha to A, then T *= 1 - alpha;
+#     stop once T < 1e-4; t_i = z_i / (d . f) is the mean's depth as a
+#     distance along the pixel ray d;
+#   * output: t = D / A where A > 0 (inf otherwise), hit = A > 0.5.
+
+GS_LOWPASS = 0.3
+GS_ALPHA_MIN = 1.0 / 255.0
+GS_ALPHA_MAX = 0.99
+GS_T_MIN = 1e-4
+GS_NEAR = 0.05
+
+
+def gs_project(means, covs, eye, target, up, fov_y, width, height):
+    """Per Gaussian: pixel mean [n, 2], screen covariance [n, 2, 2], view
+    depth z [n]."""
+    eye = np.asarray(eye, F64)
+    f = np.asarray(target, F64) - eye
+    f /= np.linalg.norm(f)
+    r = np.cross(f, np.asarray(up, F64))
+    r /= np.linalg.norm(r)
+    u = np.cross(r, f)
+    V = np.stack([r, u, f])
+    th = np.tan(0.5 * fov_y)
+    fx = width / (2 * th * width / height)
+    fy = height / (2 * th)
+    v = (np.asarray(means, F64) - eye) @ V.T
+    x, y, z = v[:, 0], v[:, 1], v[:, 2]
+    px = x / z * fx + (width - 1) / 2
+    py = -y / z * fy + (height - 1) / 2
+    J = np.zeros((v.shape[0], 2, 3))
+    J[:, 0, 0] = fx / z
+    J[:, 0, 2] = -fx * x / z ** 2
+    J[:, 1, 1] = -fy / z
+    J[:, 1, 2] = fy * y / z ** 2
+    cv = np.einsum("ij,njk,lk->nil", V, np.asarray(covs, F64), V)
+    S = np.einsum("nij,njk,nlk->nil", J, cv, J) + GS_LOWPASS * np.eye(2)[None]
+    return np.stack([px, py], 1), S, z
+
+
+def gs_depth(means, covs, opacities, eye, target, up, fov_y, width, height, pixels=None):
+    """Expected distance and hit flag per pixel ([height, width] each) of a
+    Gaussian scene, by the composite above, every Gaussian against every
+    pixel (plain definition; small images only). covs: [n, 3, 3]. With
+    `pixels` (flat indices y * width + x) only those pixels, as flat arrays."""
+    mu2, S, z = gs_project(means, covs, eye, target, up, fov_y, width, height)
+    _, d = camera_rays(eye, target, up, fov_y, width, height)
+    f = np.asarray(target, F64) - np.asarray(eye, F64)
+    f /= np.linalg.norm(f)
+    yy, xx = np.mgrid[0:height, 0:width]
+    pix = np.stack([xx.ravel(), yy.ravel()], 1).astype(F64)
+    if pixels is not None:
+        pix, d = pix[pixels], d[pixels]
+    cosf = d @ f
+    keep = z > GS_NEAR
+    order = np.lexsort((np.arange(z.size), z))
+    order = order[keep[order]]
+    Sinv = np.linalg.inv(S[order])
+    op = np.asarray(opacities, F64)[order]
+    zz = z[order]
+    npx = pix.shape[0]
+    T = np.ones(npx)
+    D = np.zeros(npx)
+    A = np.zeros(npx)
+    done = np.zeros(npx, dtype=bool)
+    for g in range(order.size):
+        dp = pix - mu2[order[g]]
+        q = np.einsum("ni,ij,nj->n", dp, Sinv[g], dp)
+        alpha = np.minimum(GS_ALPHA_MAX, op[g] * np.exp(-0.5 * q))
+        use = (alpha >= GS_ALPHA_MIN) & ~done
+        w = np.where(use, T * alpha, 0.0)
+        D += w * (zz[g] / cosf)
+        A += w
+        T = np.where(use, T * (1 - alpha), T)
+        done |= T < GS_T_MIN
+    t = np.where(A > 0, D / np.where(A > 0, A, 1.0), np.inf)
+    if pixels is not None:
+        return t, A > 0.5
+    return t.reshape(height, width), (A > 0.5).reshape(height, width)
+
+
+def gs_cov_matrices(covs6):
+    """[n, 3, 3] covariances from rows (xx, xy, xz, yy, yz, zz)."""
+    c = np.asarray(covs6, F64)
+    return np.stack([c[:, [0, 1, 2]], c[:, [1, 3, 4]], c[:, [2, 4, 5]]], axis=1)
 
 
 # ----------------------------------------------------------- queries

@@ -1,0 +1,65 @@
+"""Pins of the oracle's Gaussian-rendered depth against closed forms: the
+projection of a point and of an isotropic Gaussian, the alpha profile of a
+single Gaussian, and the two-layer composite."""
+import numpy as np
+
+from oracle import ddf_oracle as O
+
+EYE, TGT, UP = [0.0, 0.0, -4.0], [0.0, 0.0, 0.0], [0.0, 1.0, 0.0]
+FOV = np.radians(40.0)
+
+
+def test_projection_matches_the_camera_rays():
+    """The pixel a point projects to is the pixel whose camera ray passes
+    through it."""
+    W, H = 9, 7
+    o, d = O.camera_rays(EYE, TGT, UP, FOV, W, H)
+    pts = o + 3.0 * d                                     # points on pixel rays
+    mu, S, z = O.gs_project(pts, np.zeros((W * H, 3, 3)), EYE, TGT, UP, FOV, W, H)
+    yy, xx = np.mgrid[0:H, 0:W]
+    assert np.allclose(mu[:, 0], xx.ravel(), atol=1e-9) and np.allclose(mu[:, 1], yy.ravel(), atol=1e-9)
+    assert np.allclose(S, O.GS_LOWPASS * np.eye(2)[None], atol=1e-12)   # zero covariance: low-pass only
+
+
+def test_isotropic_gaussian_footprint():
+    """An isotropic Gaussian (sigma) on the optical axis at depth zc projects
+    to variance (f sigma / zc)^2 + 0.3 on each screen axis, f in pixels."""
+    W = H = 64
+    sigma, zc = 0.1, 4.0
+    mu, S, z = O.gs_project(np.array([[0.0, 0.0, 0.0]]), (sigma ** 2 * np.eye(3))[None],
+                            EYE, TGT, UP, FOV, W, H)
+    fpx = H / (2 * np.tan(FOV / 2))
+    assert np.allclose(mu[0], [(W - 1) / 2, (H - 1) / 2]) and abs(z[0] - zc) < 1e-12
+    assert np.allclose(S[0], (fpx * sigma / zc) ** 2 * np.eye(2) + 0.3 * np.eye(2), rtol=1e-12)
+
+
+def test_single_gaussian_alpha_profile_and_depth():
+    """One Gaussian, opacity 0.8: every pixel it covers reports the mean's
+    depth as a distance along that pixel ray, and the hit flag follows
+    alpha = 0.8 exp(-q/2) > 0.5."""
+    W = H = 33
+    sigma = 0.15
+    t, hit = O.gs_depth(np.array([[0.0, 0.0, 0.0]]), (sigma ** 2 * np.eye(3))[None], [0.8],
+                        EYE, TGT, UP, FOV, W, H)
+    _, d = O.camera_rays(EYE, TGT, UP, FOV, W, H)
+    cosf = d[:, 2].reshape(H, W)
+    cover = np.isfinite(t)
+    assert np.allclose(t[cover], (4.0 / cosf)[cover], rtol=1e-12)
+    fpx = H / (2 * np.tan(FOV / 2))
+    var = (fpx * sigma / 4.0) ** 2 + 0.3
+    yy, xx = np.mgrid[0:H, 0:W]
+    q = ((xx - 16) ** 2 + (yy - 16) ** 2) / var
+    assert np.array_equal(hit, 0.8 * np.exp(-q / 2) > 0.5)
+
+
+def test_two_layer_composite():
+    """A near Gaussian of opacity a1 in front of a far one of opacity a2 (both
+    wide): at the centre pixel A = a1 + (1 - a1) a2 and the expected distance
+    is (a1 t1 + (1 - a1) a2 t2) / A."""
+    W = H = 5
+    covs = (0.5 ** 2 * np.eye(3))[None].repeat(2, 0)
+    a1, a2 = 0.3, 0.6
+    t, hit = O.gs_depth(np.array([[0, 0, -1.0], [0, 0, 1.0]]), covs, [a1, a2], EYE, TGT, UP, FOV, W, H)
+    q1 = 0.0      # the centre pixel sits on both means
+    A = a1 + (1 - a1) * a2
+    assert abs(t[2, 2] - (a1 * 3.0 + (1 - a1) * a2 * 5.0) / A) < 1e-12 and hit[2, 2] == (A > 0.5)
