@@ -319,6 +319,45 @@ ddf_status ddf_render_gi(ddf_handle h, const float* spheres, int32_t n_spheres,
                          int32_t width, int32_t height, const float light[3], int32_t ao_samples,
                          uint64_t seed, float* out_shadow, float* out_ao, void* stream);
 
+/* ---- Gaussian-rendered depth: the supervision source of Sec. 3.2 that the
+ * study of Sec. 4.2 finds too blurry for thin parts ----
+ * ddf_render_gs_depth: depth images of n 3D Gaussians (means: device float
+ * n x 3; covs: device float n x 6 = (xx, xy, xz, yy, yz, zz) of each
+ * world-space covariance; opacities: device float[n]) in n_views pinhole
+ * views (cameras: host float n_views x 10, each as for ddf_render_gi), by the
+ * 3DGS depth composite: screen covariance J V C V^T J^T + 0.3 I (EWA, V the
+ * view rotation, J the projection's Jacobian at the mean; square pixels, the
+ * pixel centres of ddf_render_gi); Gaussians with view depth z <= 0.05
+ * culled; per pixel front to back by z (equal z: lower index first)
+ * alpha = min(0.99, o exp(-q / 2)), q the Mahalanobis distance of the pixel
+ * centre in the screen covariance, contributions with alpha < 1/255 skipped,
+ * D += T alpha z, A += T alpha, T *= 1 - alpha from T = 1, stopping once
+ * T < 1e-4. Writes out_t (device float n_views x height x width, view-major,
+ * row 0 at the top): the expected distance along the pixel ray,
+ * (D / A) / (d . f), or +inf where A = 0; out_hit (device uint8, same
+ * layout): A > 0.5. n <= 2^31; at most 2^31 pixels over all views.
+ * Allocates its tile lists for the call; synchronous.
+ * ddf_camera_rays: the pixel-centre rays of the same views (origins = eye,
+ * unit directions) into 6 device float arrays of n_views x height x width
+ * rows, in the layout of out_t. Synchronous.
+ * ddf_distill_pool: like ddf_distill, but each step's batch is drawn with
+ * replacement from a fixed pool of supervised rays (pool: 6 device float
+ * arrays of n_pool rows; pool_t: device float[n_pool], read where pool_hit
+ * is set; pool_hit: device uint8[n_pool]): batch row i copies pool row
+ * floor(u n_pool), u 32 uniform bits of (seed, step, i); then the shift of
+ * ddf_shift_rays on the last round(shift_frac batch) rows and ddf_train_step
+ * with the cosine rate of ddf_distill. The pool is not modified.
+ * 1 <= n_pool <= 2^31. Synchronous. */
+ddf_status ddf_render_gs_depth(const float* means, const float* covs, const float* opacities,
+                               int64_t n, const float* cameras, int32_t n_views, int32_t width,
+                               int32_t height, float* out_t, uint8_t* out_hit, void* stream);
+ddf_status ddf_camera_rays(const float* cameras, int32_t n_views, int32_t width, int32_t height,
+                           float* const rays_out[6], void* stream);
+ddf_status ddf_distill_pool(ddf_handle h, const float* const pool[6], const float* pool_t,
+                            const uint8_t* pool_hit, int64_t n_pool, int64_t steps,
+                            int64_t batch, float lr0, float shift_frac, uint64_t seed,
+                            float* losses, void* stream);
+
 /* Copies the last computed gradient (weight-blob layout, ddf_param_count
  * floats) to host memory. Synchronous. */
 ddf_status ddf_get_grad(ddf_handle h, float* host_grad, size_t n_floats);

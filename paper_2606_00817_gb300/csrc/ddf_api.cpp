@@ -1369,6 +1369,39 @@ ddf_status ddf_internal_set_error(ddf_status s, const char* msg) { return fail(s
 // ---------------------------------------------------------------------------
 // Shadow and AO images (the application of Sec. 3.3).
 
+namespace ddfi {
+
+ddf_status camera_basis(const float camera[10], int32_t width, int32_t height,
+                        ddf::GiCamera* cam) {
+  // basis in double, as the pinhole model defines it
+  double e[3], f[3], up[3];
+  for (int c = 0; c < 3; ++c) e[c] = camera[c], f[c] = camera[3 + c] - camera[c], up[c] = camera[6 + c];
+  const double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+  if (!(fl > 0.0)) return fail(DDF_ERR_INVALID_ARG, "eye and target coincide");
+  for (double& v : f) v /= fl;
+  double r[3] = {f[1] * up[2] - f[2] * up[1], f[2] * up[0] - f[0] * up[2], f[0] * up[1] - f[1] * up[0]};
+  const double rl = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  if (!(rl > 0.0)) return fail(DDF_ERR_INVALID_ARG, "up is parallel to the view direction");
+  for (double& v : r) v /= rl;
+  const double u[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
+  const double th = std::tan(0.5 * static_cast<double>(camera[9]));
+  if (!(th > 0.0) || !std::isfinite(th) || !(camera[9] < 3.14159265358979323846))
+    return fail(DDF_ERR_INVALID_ARG, "fov_y must be in (0, pi)");
+  for (int c = 0; c < 3; ++c) {
+    if (!std::isfinite(e[c])) return fail(DDF_ERR_INVALID_ARG, "camera eye is not finite");
+    cam->eye[c] = static_cast<float>(e[c]);
+    cam->f[c] = static_cast<float>(f[c]);
+    cam->r[c] = static_cast<float>(r[c]);
+    cam->u[c] = static_cast<float>(u[c]);
+  }
+  cam->tan_half = static_cast<float>(th);
+  cam->width = width;
+  cam->height = height;
+  return DDF_OK;
+}
+
+}  // namespace ddfi
+
 extern "C" ddf_status ddf_render_gi(ddf_handle h, const float* spheres, int32_t n_spheres,
                                     const float* boxes, int32_t n_boxes, const float camera[10],
                                     int32_t width, int32_t height, const float light[3],
@@ -1386,30 +1419,8 @@ extern "C" ddf_status ddf_render_gi(ddf_handle h, const float* spheres, int32_t 
     return fail(DDF_ERR_INVALID_ARG, "primitive array is NULL");
   ddf_status s = DDF_OK;
   if (h != nullptr && (s = check_ready(h)) != DDF_OK) return s;
-  // camera basis in double, as the pinhole model defines it
-  double e[3], f[3], up[3];
-  for (int c = 0; c < 3; ++c) e[c] = camera[c], f[c] = camera[3 + c] - camera[c], up[c] = camera[6 + c];
-  const double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
-  double r[3] = {f[1] * up[2] - f[2] * up[1], f[2] * up[0] - f[0] * up[2], f[0] * up[1] - f[1] * up[0]};
-  if (!(fl > 0.0)) return fail(DDF_ERR_INVALID_ARG, "eye and target coincide");
-  for (double& v : f) v /= fl;
-  r[0] = f[1] * up[2] - f[2] * up[1];
-  r[1] = f[2] * up[0] - f[0] * up[2];
-  r[2] = f[0] * up[1] - f[1] * up[0];
-  const double rl = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-  if (!(rl > 0.0)) return fail(DDF_ERR_INVALID_ARG, "up is parallel to the view direction");
-  for (double& v : r) v /= rl;
-  const double u[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
   ddf::GiCamera cam{};
-  for (int c = 0; c < 3; ++c) {
-    cam.eye[c] = static_cast<float>(e[c]);
-    cam.f[c] = static_cast<float>(f[c]);
-    cam.r[c] = static_cast<float>(r[c]);
-    cam.u[c] = static_cast<float>(u[c]);
-  }
-  cam.tan_half = static_cast<float>(std::tan(0.5 * camera[9]));
-  cam.width = width;
-  cam.height = height;
+  if ((s = camera_basis(camera, width, height, &cam)) != DDF_OK) return s;
   int dev = 0;
   if (h != nullptr) dev = h->cfg.device;
   else DDF_CK(cudaGetDevice(&dev));

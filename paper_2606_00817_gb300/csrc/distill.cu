@@ -124,7 +124,31 @@ __global__ void shift_rays_kernel(RayOut r, float* __restrict__ t, const uint8_t
   t[i] = ti - s;
 }
 
+// Batch row i copies pool row floor(u n_pool), u = 32 bits of draw 8 of
+// (seed, step, i) (draw 7 is the shift's).
+__global__ void pool_gather_kernel(RaySoA pool, const float* __restrict__ pool_t,
+                                   const uint8_t* __restrict__ pool_hit, int64_t n_pool,
+                                   uint64_t seed, uint64_t step, int64_t n, RayOut r,
+                                   float* __restrict__ t, uint8_t* __restrict__ hit) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t u = sm64(ray_key(seed, step, i) + 8) >> 32;
+  const int64_t j = static_cast<int64_t>((u * static_cast<uint64_t>(n_pool)) >> 32);
+  for (int c = 0; c < 6; ++c) r.p[c][i] = pool.p[c][j];
+  t[i] = pool_t[j];
+  hit[i] = pool_hit[j];
+}
+
 }  // namespace
+
+cudaError_t launch_pool_gather(RaySoA pool, const float* pool_t, const uint8_t* pool_hit,
+                               int64_t n_pool, uint64_t seed, uint64_t step, int64_t n,
+                               RayOut r, float* t, uint8_t* hit, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  pool_gather_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(
+      pool, pool_t, pool_hit, n_pool, seed, step, n, r, t, hit);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_sample_rays(const float* spheres, int ns, const float* boxes, int nb,
                                uint64_t seed, uint64_t step, int64_t n, float surface_frac,

@@ -186,6 +186,9 @@ ddf::RaySoA shift_rays(ddf::RaySoA r, int64_t off);
 // Builds h->tmBtr (bf16 weight maps for the plain 1-CTA tile) once.
 ddf_status ensure_plain_maps(ddf_s* h);
 int64_t round_up(int64_t x, int64_t m);
+// Pinhole basis of a camera given as eye[3], target[3], up[3], fov_y.
+ddf_status camera_basis(const float camera[10], int32_t width, int32_t height,
+                        ddf::GiCamera* cam);
 
 // Distillation loss and optimiser constants (Sec. 3.2 / 3.4): L1 clamp at
 // the box scale, cross-entropy weight 0.3, Adam (0.9, 0.999, 1e-8).

@@ -258,5 +258,35 @@ cudaError_t launch_gi_compose(const float4* sp, int64_t npx, int k, const float 
                               const float* t, const uint8_t* hit, float* shadow, float* ao,
                               cudaStream_t s);
 
+// ---- Gaussian-rendered depth (gs.cu) ----
+// Tiles of 16 pixels along an image extent.
+int gs_tiles(int extent);
+// Per (view, Gaussian): screen record rec[2 j], rec[2 j + 1] (pixel mean,
+// depth, opacity; inverse screen covariance), tile rectangle rect[j] (empty:
+// z < x), and +1 on the count of each tile in it (count zeroed by the caller,
+// nv x ntx x nty entries, view-major).
+cudaError_t launch_gs_project(const float* means, const float* covs, const float* opac, int64_t n,
+                              const GiCamera* cams, int nv, int ntx, int nty, float4* rec,
+                              int4* rect, unsigned* count, cudaStream_t s);
+// Exclusive scan of n counts into off[0..n], off[n] the total (one block).
+cudaError_t launch_gs_scan(const unsigned* count, int64_t n, int64_t* off, cudaStream_t s);
+// Writes the depth-index keys into the tile lists (cursor zeroed by the caller).
+cudaError_t launch_gs_fill(const float4* rec, const int4* rect, int64_t n, int nv, int ntx,
+                           int nty, const int64_t* off, unsigned* cursor,
+                           unsigned long long* keys, cudaStream_t s);
+// Sorts each tile's list and composites it: out_t / out_hit [nv x H x W].
+cudaError_t launch_gs_render(const float4* rec, int64_t n, const GiCamera* cams, int nv, int ntx,
+                             int nty, const int64_t* off, const unsigned long long* keys,
+                             float* out_t, uint8_t* out_hit, cudaStream_t s);
+// Pixel-centre rays of nv views of npx pixels each (cams on the device).
+cudaError_t launch_camera_rays(const GiCamera* cams, int nv, int64_t npx, RayOut r, cudaStream_t s);
+
+// ---- training from a fixed pool of supervised rays (distill.cu) ----
+// Row i of the batch copies pool row floor(u n_pool), u a 32-bit uniform of
+// (seed, step, i).
+cudaError_t launch_pool_gather(RaySoA pool, const float* pool_t, const uint8_t* pool_hit,
+                               int64_t n_pool, uint64_t seed, uint64_t step, int64_t n,
+                               RayOut r, float* t, uint8_t* hit, cudaStream_t s);
+
 }  // namespace ddf
 

@@ -625,5 +625,59 @@ ddf_status ddf_distill(ddf_handle h, const float* spheres, int32_t n_spheres, co
   return s;
 }
 
+ddf_status ddf_distill_pool(ddf_handle h, const float* const pool[6], const float* pool_t,
+                            const uint8_t* pool_hit, int64_t n_pool, int64_t steps,
+                            int64_t batch, float lr0, float shift_frac, uint64_t seed,
+                            float* losses, void* stream) {
+  if (h == nullptr) return fail(DDF_ERR_INVALID_ARG, "handle is NULL");
+  if (steps < 1 || !(lr0 > 0.f) || !(shift_frac >= 0.f && shift_frac <= 1.f))
+    return fail(DDF_ERR_INVALID_ARG, "steps >= 1, lr0 > 0, shift_frac in [0, 1]");
+  if (n_pool < 1 || n_pool > (int64_t{1} << 31))
+    return fail(DDF_ERR_INVALID_ARG, "n_pool must be in [1, 2^31]");
+  if (pool == nullptr || pool_t == nullptr || pool_hit == nullptr)
+    return fail(DDF_ERR_INVALID_ARG, "pool arrays are NULL");
+  ddf::RaySoA ps;
+  for (int c = 0; c < 6; ++c) {
+    if (pool[c] == nullptr) return fail(DDF_ERR_INVALID_ARG, "a pool ray array is NULL");
+    ps.p[c] = pool[c];
+  }
+  if (batch < 1) return fail(DDF_ERR_INVALID_ARG, "batch must be >= 1");
+  DeviceGuard g(h->cfg.device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float* buf = nullptr;  // 6 ray arrays, targets, per-step losses
+  uint8_t* hit = nullptr;
+  DDF_CK(cudaMalloc(&buf, (7 * batch + steps) * sizeof(float)));
+  if (cudaMalloc(&hit, batch) != cudaSuccess) {
+    cudaFree(buf);
+    return fail(DDF_ERR_OOM, "cudaMalloc of the hit flags failed");
+  }
+  ddf::RayOut ro;
+  for (int c = 0; c < 6; ++c) ro.p[c] = buf + c * batch;
+  float* t = buf + 6 * batch;
+  float* dev_loss = buf + 7 * batch;
+  const int64_t first = batch - static_cast<int64_t>(std::llround(shift_frac * batch));
+  ddf_status s = DDF_OK;
+  for (int64_t k = 0; k < steps && s == DDF_OK; ++k) {
+    const double c = 0.5 * (1.0 + std::cos(3.14159265358979323846 * static_cast<double>(k) / steps));
+    const float lr = static_cast<float>(lr0 * (0.05 + 0.95 * c));
+    const cudaError_t e = ddf::launch_pool_gather(ps, pool_t, pool_hit, n_pool, seed,
+                                                  static_cast<uint64_t>(k), batch, ro, t, hit, st);
+    if (e != cudaSuccess) s = cuda_fail(e, "pool gather");
+    const float* const rc[6] = {ro.p[0], ro.p[1], ro.p[2], ro.p[3], ro.p[4], ro.p[5]};
+    if (s == DDF_OK) s = ddf_shift_rays(ro.p, t, hit, batch, first, seed, static_cast<uint64_t>(k), st);
+    if (s == DDF_OK) s = ddf_train_step(h, rc, t, hit, batch, lr, dev_loss + k, st);
+  }
+  if (s == DDF_OK && losses != nullptr) {
+    const cudaError_t e = cudaMemcpyAsync(losses, dev_loss, steps * sizeof(float),
+                                          cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) s = cuda_fail(e, "cudaMemcpyAsync");
+  }
+  const cudaError_t e = cudaStreamSynchronize(st);
+  cudaFree(buf);
+  cudaFree(hit);
+  if (s == DDF_OK && e != cudaSuccess) s = cuda_fail(e, "cudaStreamSynchronize");
+  return s;
+}
+
 }  // extern "C"
 

@@ -73,6 +73,10 @@ SIGNATURES = {
                               C.c_float, _u64, _vp, _vp]),
     "ddf_render_gi": (C.c_int, [_vp, _vp, _i32, _vp, _i32, _vp, _i32, _i32, _vp, _i32, _u64, _vp,
                                 _vp, _vp]),
+    "ddf_render_gs_depth": (C.c_int, [_vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _vp, _vp]),
+    "ddf_camera_rays": (C.c_int, [_vp, _i32, _i32, _i32, _RAYS, _vp]),
+    "ddf_distill_pool": (C.c_int, [_vp, _RAYS, _vp, _vp, _i64, _i64, _i64, C.c_float, C.c_float,
+                                   _u64, _vp, _vp]),
     "ddf_get_grad": (C.c_int, [_vp, _vp, _sz]),
     "ddf_reset_optimizer": (C.c_int, [_vp]),
     "ddf_cast_scene": (C.c_int, [_vp, _i32, _vp, _i32, _RAYS, _i64, _vp, _vp, _vp]),
@@ -316,6 +320,37 @@ def ddf_render_gi(h, spheres, n_spheres, boxes, n_boxes, camera, width, height, 
     _call("ddf_render_gi", h, _ptr(spheres), int(n_spheres), _ptr(boxes), int(n_boxes), cam,
           int(width), int(height), lt, int(ao_samples), int(seed), _ptr(out_shadow), _ptr(out_ao),
           _stream(stream))
+
+
+def _cameras(cameras):
+    cams = np.ascontiguousarray(np.asarray(cameras, np.float32).reshape(-1, 10))
+    return cams, cams.shape[0]
+
+
+def ddf_render_gs_depth(means, covs, opacities, n, cameras, width, height, out_t, out_hit,
+                        stream=None) -> None:
+    """cameras: [views, 10] rows (eye xyz, target xyz, up xyz, fov_y)."""
+    cams, nv = _cameras(cameras)
+    _call("ddf_render_gs_depth", _ptr(means), _ptr(covs), _ptr(opacities), int(n),
+          cams.ctypes.data, nv, int(width), int(height), _ptr(out_t), _ptr(out_hit),
+          _stream(stream))
+
+
+def ddf_camera_rays(cameras, width, height, rays_out, stream=None) -> None:
+    cams, nv = _cameras(cameras)
+    rp, keep = _rays(rays_out)
+    _call("ddf_camera_rays", cams.ctypes.data, nv, int(width), int(height), rp, _stream(stream))
+
+
+def ddf_distill_pool(h, pool, pool_t, pool_hit, n_pool, steps, batch, lr0, shift_frac=0.3, seed=0,
+                     stream=None) -> np.ndarray:
+    """Trains from a fixed pool of supervised rays; returns the per-step losses."""
+    rp, keep = _rays(pool)
+    losses = np.zeros(int(steps), np.float32)
+    _call("ddf_distill_pool", h, rp, _ptr(pool_t), _ptr(pool_hit), int(n_pool), int(steps),
+          int(batch), float(lr0), float(shift_frac), int(seed), losses.ctypes.data,
+          _stream(stream))
+    return losses
 
 
 def ddf_get_grad(h, n: int) -> np.ndarray:

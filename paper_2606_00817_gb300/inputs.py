@@ -20,6 +20,10 @@ ambient-occlusion and bounce rays) at the sizes used for measurement:
     normal by 1e-3, aimed at a point light.
   * ``ao_rays``: per shading point a random count in [4, 64] of
     cosine-weighted hemisphere directions, flattened with CSR offsets.
+
+For the supervision study (Sec. 4.2), a scene with thin parts (``table_scene``)
+and flat 3D Gaussians laid on its visible surfaces (``surface_gaussians``)
+stand in for a trained 3DGS scene; ``orbit_cameras`` places the views.
 """
 from __future__ import annotations
 
@@ -34,6 +38,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 # stream ids: one per independent random quantity
 S_ORIGIN, S_DIR, S_WEIGHTS, S_SCENE, S_POINTS, S_COUNTS, S_HEMI, S_TARGET = range(1, 9)
 S_TABLE = 15
+S_GAUSS, S_GAUSS_OPAC, S_VIEWS = 16, 17, 18
 
 
 def _mix(z: np.ndarray) -> np.ndarray:
@@ -329,3 +334,121 @@ def ao_rays(scene: Scene, n_points: int, seed: int = 0, lo: int = 4, hi: int = 6
     if offsets[-1] >= 2 ** 31:
         raise ValueError("ragged batch exceeds int32 offsets")
     return Rays.from_arrays(o, d), offsets.astype(np.int32)
+
+
+# ------------------------------------------------- supervision-study scene
+
+def table_scene():
+    """A table on a floor slab with a ball and a mug on top (boxes in
+    [-0.95, 0.95]^3): tabletop 1.4 x 0.06 x 1.0, four legs 0.04 x 0.90 x 0.04,
+    two cross bars 1.2 x 0.03 x 0.03, a mug (sphere r 0.15) with a handle of
+    three 0.03-thick bars, a ball (r 0.12). Returns (scene, thin) where thin
+    marks the boxes that are legs, bars or handle parts: a few pixels wide in
+    a 256-pixel view from 3 units away, the parts the study is about."""
+    boxes, thin = [], []
+
+    def box(lo, hi, is_thin):
+        boxes.append((lo, hi))
+        thin.append(is_thin)
+
+    box((-0.95, -0.86, -0.95), (0.95, -0.80, 0.95), False)          # floor
+    box((-0.70, 0.10, -0.50), (0.70, 0.16, 0.50), False)            # tabletop
+    for x in (-0.64, 0.60):
+        for z in (-0.44, 0.40):
+            box((x, -0.80, z), (x + 0.04, 0.10, z + 0.04), True)    # legs
+    for z in (-0.435, 0.405):
+        box((-0.60, -0.50, z), (0.60, -0.47, z + 0.03), True)       # cross bars
+    box((0.50, 0.22, -0.015), (0.53, 0.40, 0.015), True)            # handle
+    box((0.43, 0.37, -0.015), (0.53, 0.40, 0.015), True)
+    box((0.43, 0.22, -0.015), (0.53, 0.25, 0.015), True)
+    centers = np.array([[0.30, 0.31, 0.0], [-0.30, 0.28, 0.10]])
+    radii = np.array([0.15, 0.12])
+    lo = np.array([b[0] for b in boxes], dtype=np.float64)
+    hi = np.array([b[1] for b in boxes], dtype=np.float64)
+    return Scene(centers, radii, lo, hi).as_float32(), np.array(thin)
+
+
+def surface_gaussians(scene: Scene, n: int, sigma_t: float = 0.02, sigma_n: float = 0.002,
+                      opacity=(0.6, 1.0), seed: int = 0, coverage: bool = True):
+    """n flat 3D Gaussians on the union's outer surface, the shape a trained
+    3DGS scene takes on opaque surfaces: means uniform by area over sphere
+    surfaces and box faces (points strictly inside another primitive
+    dropped), covariance sigma_t^2 in the tangent plane and sigma_n^2 along
+    the normal, opacity uniform in the given range. With coverage, a
+    Gaussian on a part narrower than itself is softened the way a fit to
+    images softens it: its opacity is scaled by min(1, w / (sqrt(2 pi)
+    sigma_t)), w the face's narrower side (2 r on a sphere), so that its
+    alpha integrated across the part matches the part's width. Returns
+    float32 means [n, 3], covs [n, 6] = (xx, xy, xz, yy, yz, zz) and
+    opacities [n]."""
+    S, B = scene.radii.shape[0], scene.box_lo.shape[0]
+    ext = scene.box_hi - scene.box_lo
+    face_area = np.stack([ext[:, 1] * ext[:, 2], ext[:, 0] * ext[:, 2], ext[:, 0] * ext[:, 1]], 1)
+    area = np.concatenate([4 * np.pi * scene.radii ** 2, np.repeat(face_area, 2, axis=1).ravel()])
+    cdf = np.cumsum(area) / area.sum()
+    got_p, got_n, got_w, have, off = [], [], [], 0, 0
+    while have < n:
+        m = int((n - have) * 1.3) + 1024
+        u = uniform(seed, S_GAUSS, 3 * m, offset=3 * off).reshape(m, 3)
+        nrm_s = unit_vectors(seed, S_GAUSS + 100, m, offset=off)
+        off += m
+        k = np.minimum(np.searchsorted(cdf, u[:, 0], side="right"), area.size - 1)
+        p = np.zeros((m, 3))
+        nrm = np.zeros((m, 3))
+        own = np.full(m, -1)
+        width = np.zeros(m)
+        sph = k < S
+        p[sph] = scene.centers[k[sph]] + scene.radii[k[sph], None] * nrm_s[sph]
+        nrm[sph] = nrm_s[sph]
+        own[sph] = k[sph]
+        width[sph] = 2 * scene.radii[k[sph]]
+        for q in np.nonzero(~sph)[0]:
+            f = k[q] - S
+            b, face = f // 6, f % 6
+            axis, side = face // 2, face % 2
+            a1, a2 = (axis + 1) % 3, (axis + 2) % 3
+            p[q, a1] = scene.box_lo[b, a1] + u[q, 1] * ext[b, a1]
+            p[q, a2] = scene.box_lo[b, a2] + u[q, 2] * ext[b, a2]
+            p[q, axis] = scene.box_hi[b, axis] if side else scene.box_lo[b, axis]
+            nrm[q, axis] = 1.0 if side else -1.0
+            own[q] = S + b
+            width[q] = min(ext[b, a1], ext[b, a2])
+        inside = np.zeros(m, dtype=bool)
+        for j in range(S):
+            inside |= (np.linalg.norm(p - scene.centers[j], axis=1) < scene.radii[j] - 1e-6) & (own != j)
+        for j in range(B):
+            inside |= np.all((p > scene.box_lo[j] + 1e-6) & (p < scene.box_hi[j] - 1e-6), axis=1) \
+                & (own != S + j)
+        got_p.append(p[~inside])
+        got_n.append(nrm[~inside])
+        got_w.append(width[~inside])
+        have += int((~inside).sum())
+    p = np.concatenate(got_p)[:n]
+    nrm = np.concatenate(got_n)[:n]
+    width = np.concatenate(got_w)[:n]
+    t, b = _frame(nrm)
+    cov = sigma_t ** 2 * (t[:, :, None] * t[:, None, :] + b[:, :, None] * b[:, None, :]) \
+        + sigma_n ** 2 * nrm[:, :, None] * nrm[:, None, :]
+    covs = cov[:, [0, 0, 0, 1, 1, 2], [0, 1, 2, 1, 2, 2]]
+    op = uniform(seed, S_GAUSS_OPAC, n, opacity[0], opacity[1])
+    if coverage:
+        op = op * np.minimum(1.0, width / (np.sqrt(2 * np.pi) * sigma_t))
+    return p.astype(np.float32), covs.astype(np.float32), op.astype(np.float32)
+
+
+def orbit_cameras(n: int, radius: float = 3.0, target=(0.0, -0.2, 0.0), elev=(10.0, 55.0),
+                  fov_y_deg: float = 40.0, seed: int = 0, offset: int = 0) -> np.ndarray:
+    """n pinhole cameras [n, 10] (eye, target, up = +y, fov_y in radians) on a
+    sphere about target: azimuth uniform in [0, 360), elevation uniform in
+    elev degrees."""
+    u = uniform(seed, S_VIEWS, 2 * n, offset=2 * offset).reshape(n, 2)
+    az = 2 * np.pi * u[:, 0]
+    el = np.radians(elev[0] + (elev[1] - elev[0]) * u[:, 1])
+    tg = np.asarray(target, np.float64)
+    eye = tg + radius * np.stack([np.cos(el) * np.cos(az), np.sin(el), np.cos(el) * np.sin(az)], 1)
+    cams = np.zeros((n, 10))
+    cams[:, 0:3] = eye
+    cams[:, 3:6] = tg
+    cams[:, 7] = 1.0
+    cams[:, 9] = np.radians(fov_y_deg)
+    return cams.astype(np.float32)
