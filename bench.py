@@ -29,11 +29,13 @@ events on the launching stream, 3 timed repetitions after warm-up):
                  with held-out exact casts
   gs_supervision the supervision study (Sec. 4.2) on synthetic data: a table
                  scene with thin legs, bars and a mug handle; 60,000 flat
-                 surface Gaussians stand in for its 3DGS scene; 48 training
-                 views of 256 x 256 rendered to depth by the tile rasteriser
-                 and, on the same rays, cast exactly; one hash-grid field
-                 distilled from each source (3,000 steps of 16,384 rays) and
-                 compared on 8 held-out views with exact targets
+                 surface Gaussians stand in for its 3DGS scene; 1,024
+                 training views of 128 x 128 rendered to depth by the tile
+                 rasteriser and, on the same rays, cast exactly; one
+                 hash-grid field distilled from each source with the paper's
+                 schedule (30,000 steps of 16,384 rays) and compared on 8
+                 training and 8 held-out views with exact targets
+                 (--gs-config VIEWS,SIZE,STEPS,SIGMA changes the setting)
 """
 from __future__ import annotations
 
@@ -76,6 +78,8 @@ def parse():
                     help="skip the AO / distillation / sphere-tracing / hash-grid measurements")
     ap.add_argument("--workloads", default="ao,train,trace,hashgrid,gs",
                     help="comma list of the secondary measurements to run")
+    ap.add_argument("--gs-config", default="1024,128,30000,0.02",
+                    help="supervision study: training views, image size, steps, Gaussian sigma")
     return ap.parse_args()
 
 
@@ -347,23 +351,27 @@ def _chamfer(torch, P, Q, cap=20000, seed=0):
     return 0.5 * (one(P, Q) + one(Q, P))
 
 
-def gs_workload(torch, ddf, dev, local, stream):
+def gs_workload(torch, ddf, dev, local, stream, V=1024, W=128, steps=30000, n_gauss=60000,
+                sigma_t=0.02, held_out=8):
     """The supervision study (Sec. 4.2) on synthetic data: Gaussian-rendered
     depth vs exact casts as the targets of the same field, the same rays and
     the same schedule."""
     scene, thin = I.table_scene()
-    means, covs, opac = I.surface_gaussians(scene, 60000, sigma_t=0.02, sigma_n=0.002, seed=0)
+    means, covs, opac = I.surface_gaussians(scene, n_gauss, sigma_t=sigma_t, sigma_n=0.002, seed=0)
     sph, ns, box, nb = _scene_buffers(torch, dev, scene)
     sub = I.Scene(scene.centers[:0], scene.radii[:0], scene.box_lo[thin], scene.box_hi[thin])
     _, _, tbox, tnb = _scene_buffers(torch, dev, sub)
     dm, dc, do = (torch.from_numpy(a).to(dev) for a in (means, covs, opac))
-    W = 256
 
-    def views(cams):
+    def views(cams, t_eye=None):
+        """Camera rays moved to their entry into the field's box [-1, 1]^3
+        (t_eye, distances from the eye, shifted alike), exact targets and the
+        thin / near-thin ray classes."""
         V = cams.shape[0]
         n = V * W * W
         rays = [torch.empty(n, device=dev) for _ in range(6)]
         ddf.ddf_camera_rays(cams, W, W, rays, stream)
+        ddf.ddf_enter_box(rays, t_eye, None, n, 1.0, stream)
         t = torch.empty(n, device=dev)
         h = torch.empty(n, dtype=torch.uint8, device=dev)
         ddf.ddf_cast_scene(sph, ns, box, nb, rays, n, t, h, stream)
@@ -376,9 +384,7 @@ def gs_workload(torch, ddf, dev, local, stream):
         near_thin = _dilate(torch, on_thin, V, W, 3) & ~on_thin
         return rays, t, h, on_thin, near_thin
 
-    V = 48
     cams = I.orbit_cameras(V, seed=0)
-    rays, t_ex, h_ex, on_thin, near_thin = views(cams)
     n = V * W * W
     t_gs = torch.empty(n, device=dev)
     h_gs = torch.empty(n, dtype=torch.uint8, device=dev)
@@ -389,6 +395,7 @@ def gs_workload(torch, ddf, dev, local, stream):
     for _ in range(reps):
         ddf.ddf_render_gs_depth(dm, dc, do, len(opac), cams, W, W, t_gs, h_gs, stream)
     render_s = (time.perf_counter() - t0) / reps
+    rays, t_ex, h_ex, on_thin, near_thin = views(cams, t_gs)
 
     def compare(t_p, hit_p, t_r, hit_r, cls):
         """Hit agreement and |dt| where both hit, per ray class."""
@@ -404,17 +411,21 @@ def gs_workload(torch, ddf, dev, local, stream):
         return out
 
     allm = torch.ones_like(on_thin)
-    res = {"gaussians": len(opac), "sigma_tangent": 0.02, "sigma_normal": 0.002,
+    res = {"gaussians": len(opac), "sigma_tangent": sigma_t, "sigma_normal": 0.002,
            "train_views": V, "width": W, "height": W, "train_rays": n,
            "render_s": render_s, "render_pixels_per_s": n / render_s,
            "gs_depth_vs_exact_on_train_views": compare(
                t_gs, h_gs.bool(), t_ex, h_ex.bool(),
                {"all": allm, "thin": on_thin, "near_thin": near_thin})}
-    # held-out views and their classes
-    hcams = I.orbit_cameras(8, seed=0, offset=1000)
+    # evaluation sets: the first 8 training views (how well each field holds
+    # the geometry its supervision showed) and held-out views; exact targets
+    k = min(8, V) * W * W
+    sets = {"train_views": ([r[:k] for r in rays], t_ex[:k], h_ex[:k].bool(), on_thin[:k],
+                            near_thin[:k]),
+            "held_out": None}
+    hcams = I.orbit_cameras(held_out, seed=0, offset=1000)
     hrays, ht, hh, hthin, hnear = views(hcams)
-    hb = hh.bool()
-    pts_exact = torch.stack([hrays[c] + ht * hrays[3 + c] for c in range(3)], 1)[hb]
+    sets["held_out"] = (hrays, ht, hh.bool(), hthin, hnear)
     zone = lambda P: (P[:, 1] > -0.79) & (P[:, 1] < 0.09)      # legs and bars only
     fields = {}
     for name, (tt, hh_t) in (("gs_depth", (t_gs, h_gs)), ("exact", (t_ex, h_ex))):
@@ -422,24 +433,28 @@ def gs_workload(torch, ddf, dev, local, stream):
         m.load(I.hashgrid_blob(m.n_params, hashgrid_mlp_dims(ddf), seed=0, table_scale=1e-4))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        losses = ddf.ddf_distill_pool(m.h, rays, tt, hh_t, n, 3000, 16384, 3e-3, 0.3, seed=1,
+        losses = ddf.ddf_distill_pool(m.h, rays, tt, hh_t, n, steps, 16384, 3e-3, 0.3, seed=1,
                                       stream=stream)
         el = time.perf_counter() - t0
-        pt, pv = m.query(hrays, stream)
-        torch.cuda.synchronize()
-        ph = pv > 0.5
-        pts = torch.stack([hrays[c] + pt * hrays[3 + c] for c in range(3)], 1)[ph]
-        fields[name] = {
-            "train_seconds": el, "loss_first": float(losses[:5].mean()),
-            "loss_last": float(losses[-50:].mean()),
-            "held_out": compare(pt, ph, ht, hb, {"all": torch.ones_like(hb), "thin": hthin,
-                                                 "near_thin": hnear}),
-            "chamfer_all": _chamfer(torch, pts, pts_exact),
-            "chamfer_legs_zone": _chamfer(torch, pts[zone(pts)], pts_exact[zone(pts_exact)]),
-            "status": ddf.ddf_check_status(m.h)}
+        out = {"train_seconds": el, "loss_first": float(losses[:5].mean()),
+               "loss_last": float(losses[-50:].mean())}
+        for sname, (er, et, eh, ethin, enear) in sets.items():
+            pt, pv = m.query(er, stream)
+            torch.cuda.synchronize()
+            ph = pv > 0.5
+            pts = torch.stack([er[c] + pt * er[3 + c] for c in range(3)], 1)[ph]
+            ref = torch.stack([er[c] + et * er[3 + c] for c in range(3)], 1)[eh]
+            out[sname] = {
+                "rays": compare(pt, ph, et, eh, {"all": torch.ones_like(eh), "thin": ethin,
+                                                 "near_thin": enear}),
+                "chamfer_all": _chamfer(torch, pts, ref),
+                "chamfer_legs_zone": _chamfer(torch, pts[zone(pts)], ref[zone(ref)])}
+        out["status"] = ddf.ddf_check_status(m.h)
+        fields[name] = out
         m.close()
     res["fields"] = fields
-    res["held_out_views"] = 8
+    res["steps"] = steps
+    res["held_out_views"] = held_out
     res["paper_context"] = ("Chamfer over ten objects 0.082 (Gaussian depth) -> 0.065 (clean "
                             "distance); thin-part objects gain most (Sec. 4.2)")
     return res
@@ -782,7 +797,9 @@ def main():
         if "hashgrid" in which:
             extra["hashgrid"] = hashgrid_workload(torch, ddf, dev, local, stream, flush, d_rays, R)
         if "gs" in which:
-            extra["gs_supervision"] = gs_workload(torch, ddf, dev, local, stream)
+            gv, gw, gsteps, gsig = args.gs_config.split(",")
+            extra["gs_supervision"] = gs_workload(torch, ddf, dev, local, stream, V=int(gv),
+                                                  W=int(gw), steps=int(gsteps), sigma_t=float(gsig))
 
     # CPU baseline (the FP64 oracle on a bounded prefix) + accuracy of the GPU outputs on it
     cpu = None

@@ -348,6 +348,16 @@ ddf_status ddf_render_gi(ddf_handle h, const float* spheres, int32_t n_spheres,
  * ddf_shift_rays on the last round(shift_frac batch) rows and ddf_train_step
  * with the cosine rate of ddf_distill. The pool is not modified.
  * 1 <= n_pool <= 2^31. Synchronous. */
+/* ddf_enter_box: a field encodes ray origins inside the box [-1, 1]^3 (the
+ * box that bounds the normalised object, Sec. 3.4), so a ray from a camera
+ * outside it is first moved to where it enters the box: for n rays (6 device
+ * float arrays, updated in place) the slab-test entry distance e (0 when the
+ * origin is inside or the ray misses the box [-half_extent, half_extent]^3)
+ * moves the origin to o + e d; t (device float[n], nullable) becomes
+ * max(t - e, 0) where finite; out_t_in (device float[n], nullable) receives
+ * e. Asynchronous. */
+ddf_status ddf_enter_box(float* const rays[6], float* t, float* out_t_in, int64_t n,
+                         float half_extent, void* stream);
 ddf_status ddf_render_gs_depth(const float* means, const float* covs, const float* opacities,
                                int64_t n, const float* cameras, int32_t n_views, int32_t width,
                                int32_t height, float* out_t, uint8_t* out_hit, void* stream);

@@ -899,6 +899,23 @@ def gs_depth(means, covs, opacities, eye, target, up, fov_y, width, height, pixe
     return t.reshape(height, width), (A > 0.5).reshape(height, width)
 
 
+def enter_box(o, d, half=1.0):
+    """Entry of rays into the box [-half, half]^3 (the field's domain,
+    Sec. 3.4; slab test): returns (o + e d, e) with e the distance to the
+    entry point, 0 for an origin inside the box or a ray that misses it."""
+    o = np.asarray(o, F64)
+    d = np.asarray(d, F64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        a = (-half - o) / d
+        b = (half - o) / d
+    lo_t = np.where(d != 0, np.minimum(a, b), np.where(np.abs(o) <= half, -np.inf, np.inf))
+    hi_t = np.where(d != 0, np.maximum(a, b), np.where(np.abs(o) <= half, np.inf, -np.inf))
+    tn = np.maximum(lo_t.max(axis=1), 0.0)
+    tf = hi_t.min(axis=1)
+    e = np.where(tn <= tf, tn, 0.0)
+    return o + e[:, None] * d, e
+
+
 def gs_cov_matrices(covs6):
     """[n, 3, 3] covariances from rows (xx, xy, xz, yy, yz, zz)."""
     c = np.asarray(covs6, F64)

@@ -139,7 +139,43 @@ __global__ void pool_gather_kernel(RaySoA pool, const float* __restrict__ pool_t
   hit[i] = pool_hit[j];
 }
 
+// Moves ray i's origin forward to where it enters the box [-h, h]^3 (slab
+// test; unchanged when it starts inside or misses the box), stores that
+// distance in t_in[i] and subtracts it from a finite t[i] (not below 0).
+__global__ void enter_box_kernel(RayOut r, float* __restrict__ t, float* __restrict__ t_in,
+                                 int64_t n, float h) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float o[3] = {r.p[0][i], r.p[1][i], r.p[2][i]};
+  const float d[3] = {r.p[3][i], r.p[4][i], r.p[5][i]};
+  float tn = 0.f, tf = __int_as_float(0x7f800000);
+  bool miss = false;
+  for (int k = 0; k < 3; ++k) {
+    if (d[k] != 0.f) {
+      const float a = (-h - o[k]) / d[k], b = (h - o[k]) / d[k];
+      tn = fmaxf(tn, fminf(a, b));
+      tf = fminf(tf, fmaxf(a, b));
+    } else if (o[k] < -h || o[k] > h) {
+      miss = true;
+    }
+  }
+  const float e = (!miss && tn <= tf) ? tn : 0.f;
+  if (e > 0.f)
+    for (int k = 0; k < 3; ++k) r.p[k][i] = o[k] + e * d[k];
+  if (t != nullptr) {
+    const float ti = t[i];
+    if (ti < __int_as_float(0x7f800000)) t[i] = fmaxf(ti - e, 0.f);
+  }
+  if (t_in != nullptr) t_in[i] = e;
+}
+
 }  // namespace
+
+cudaError_t launch_enter_box(RayOut r, float* t, float* t_in, int64_t n, float h, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  enter_box_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(r, t, t_in, n, h);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_pool_gather(RaySoA pool, const float* pool_t, const uint8_t* pool_hit,
                                int64_t n_pool, uint64_t seed, uint64_t step, int64_t n,

@@ -3,6 +3,7 @@
 // workspace, and the launch sequence of gs.cu.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <vector>
 
@@ -108,6 +109,23 @@ ddf_status ddf_camera_rays(const float* cameras, int32_t n_views, int32_t width,
   if (e == cudaSuccess) e = e2;
   cudaFree(dcam);
   if (e != cudaSuccess) return cuda_fail(e, "camera rays");
+  return DDF_OK;
+}
+
+ddf_status ddf_enter_box(float* const rays[6], float* t, float* out_t_in, int64_t n,
+                         float half_extent, void* stream) {
+  if (rays == nullptr) return fail(DDF_ERR_INVALID_ARG, "rays is NULL");
+  if (n < 0) return fail(DDF_ERR_INVALID_ARG, "n must be >= 0");
+  if (!(half_extent > 0.f) || !std::isfinite(half_extent))
+    return fail(DDF_ERR_INVALID_ARG, "half_extent must be finite and > 0");
+  ddf::RayOut r;
+  for (int c = 0; c < 6; ++c) {
+    if (rays[c] == nullptr && n > 0) return fail(DDF_ERR_INVALID_ARG, "a ray array is NULL");
+    r.p[c] = rays[c];
+  }
+  const cudaError_t e =
+      ddf::launch_enter_box(r, t, out_t_in, n, half_extent, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "enter box");
   return DDF_OK;
 }
 

@@ -281,6 +281,10 @@ cudaError_t launch_gs_render(const float4* rec, int64_t n, const GiCamera* cams,
 // Pixel-centre rays of nv views of npx pixels each (cams on the device).
 cudaError_t launch_camera_rays(const GiCamera* cams, int nv, int64_t npx, RayOut r, cudaStream_t s);
 
+// Moves origins to their entry into [-h, h]^3; t (nullable) loses that
+// distance, t_in (nullable) receives it.
+cudaError_t launch_enter_box(RayOut r, float* t, float* t_in, int64_t n, float h, cudaStream_t s);
+
 // ---- training from a fixed pool of supervised rays (distill.cu) ----
 // Row i of the batch copies pool row floor(u n_pool), u a 32-bit uniform of
 // (seed, step, i).

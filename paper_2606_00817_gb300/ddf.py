@@ -75,6 +75,7 @@ SIGNATURES = {
                                 _vp, _vp]),
     "ddf_render_gs_depth": (C.c_int, [_vp, _vp, _vp, _i64, _vp, _i32, _i32, _i32, _vp, _vp, _vp]),
     "ddf_camera_rays": (C.c_int, [_vp, _i32, _i32, _i32, _RAYS, _vp]),
+    "ddf_enter_box": (C.c_int, [_RAYS, _vp, _vp, _i64, C.c_float, _vp]),
     "ddf_distill_pool": (C.c_int, [_vp, _RAYS, _vp, _vp, _i64, _i64, _i64, C.c_float, C.c_float,
                                    _u64, _vp, _vp]),
     "ddf_get_grad": (C.c_int, [_vp, _vp, _sz]),
@@ -340,6 +341,12 @@ def ddf_camera_rays(cameras, width, height, rays_out, stream=None) -> None:
     cams, nv = _cameras(cameras)
     rp, keep = _rays(rays_out)
     _call("ddf_camera_rays", cams.ctypes.data, nv, int(width), int(height), rp, _stream(stream))
+
+
+def ddf_enter_box(rays, t, out_t_in, n, half_extent=1.0, stream=None) -> None:
+    rp, keep = _rays(rays)
+    _call("ddf_enter_box", rp, _ptr(t), _ptr(out_t_in), int(n), float(half_extent),
+          _stream(stream))
 
 
 def ddf_distill_pool(h, pool, pool_t, pool_hit, n_pool, steps, batch, lr0, shift_frac=0.3, seed=0,

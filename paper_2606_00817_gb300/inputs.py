@@ -433,7 +433,7 @@ def surface_gaussians(scene: Scene, n: int, sigma_t: float = 0.02, sigma_n: floa
     op = uniform(seed, S_GAUSS_OPAC, n, opacity[0], opacity[1])
     if coverage:
         op = op * np.minimum(1.0, width / (np.sqrt(2 * np.pi) * sigma_t))
-    return p.astype(np.float32), covs.astype(np.float32), op.astype(np.float32)
+    return tuple(np.ascontiguousarray(a, dtype=np.float32) for a in (p, covs, op))
 
 
 def orbit_cameras(n: int, radius: float = 3.0, target=(0.0, -0.2, 0.0), elev=(10.0, 55.0),

@@ -85,6 +85,34 @@ def test_camera_rays_match_oracle(torch_cuda):
         assert np.allclose(got[v, :, 3:], d, atol=2e-6)
 
 
+def test_enter_box_matches_oracle(torch_cuda):
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    rng = np.random.default_rng(7)
+    n = 5000
+    o = rng.uniform(-4, 4, (n, 3))
+    d = rng.normal(size=(n, 3))
+    d[: n // 2] = rng.uniform(-1, 1, (n // 2, 3)) - o[: n // 2]
+    d[:10, 1] = 0.0                                   # axis-parallel components
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    o, d = o.astype(np.float32), d.astype(np.float32)
+    rays = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (*o.T, *d.T)]
+    t = torch.from_numpy(np.where(np.arange(n) % 3 == 0, np.inf, 10.0).astype(np.float32)).cuda()
+    t_in = torch.empty(n, device="cuda")
+    ddf.ddf_enter_box(rays, t, t_in, n, 1.0)
+    torch.cuda.synchronize()
+    ro, re = O.enter_box(o.astype(np.float64), d.astype(np.float64))
+    got = np.stack([r.cpu().numpy() for r in rays[:3]], 1)
+    assert np.allclose(got, ro, atol=2e-6)
+    assert np.allclose(t_in.cpu().numpy(), re, atol=2e-6)
+    tt = t.cpu().numpy()
+    fin = np.arange(n) % 3 != 0
+    assert np.all(np.isinf(tt[~fin])) and np.allclose(tt[fin], 10.0 - re[fin], atol=2e-6)
+    assert (re > 0).sum() > 1000
+    with pytest.raises(ddf.DDFError):
+        ddf.ddf_enter_box(rays, None, None, n, 0.0)
+
+
 def test_random_gaussians_match_oracle(torch_cuda):
     """3,000 overlapping Gaussians of random shape and opacity, two views of
     48 x 40 pixels (a ragged row of tiles), every pixel against the oracle."""
@@ -225,6 +253,7 @@ def test_distill_from_a_pool(torch_cuda):
     n = 8 * W * H
     rays = [torch.empty(n, device="cuda") for _ in range(6)]
     ddf.ddf_camera_rays(cams, W, H, rays)
+    ddf.ddf_enter_box(rays, None, None, n, 1.0)
     t = torch.empty(n, device="cuda")
     hit = torch.empty(n, dtype=torch.uint8, device="cuda")
     ddf.ddf_cast_scene(sph, len(scene.radii), box, len(scene.box_lo), rays, n, t, hit)

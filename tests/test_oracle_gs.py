@@ -4,6 +4,7 @@ single Gaussian, and the two-layer composite."""
 import numpy as np
 
 from oracle import ddf_oracle as O
+from paper_2606_00817_gb300 import inputs as I
 
 EYE, TGT, UP = [0.0, 0.0, -4.0], [0.0, 0.0, 0.0], [0.0, 1.0, 0.0]
 FOV = np.radians(40.0)
@@ -63,3 +64,39 @@ def test_two_layer_composite():
     q1 = 0.0      # the centre pixel sits on both means
     A = a1 + (1 - a1) * a2
     assert abs(t[2, 2] - (a1 * 3.0 + (1 - a1) * a2 * 5.0) / A) < 1e-12 and hit[2, 2] == (A > 0.5)
+
+
+def test_enter_box_invariants():
+    """Rays from outside that meet the box start on its surface afterwards and
+    keep their line (the first hit stays at the same point); rays that start
+    inside or miss are left alone."""
+    rng = np.random.default_rng(0)
+    n = 2000
+    o = rng.uniform(-4, 4, (n, 3))
+    d = rng.normal(size=(n, 3))
+    d[: n // 2] = rng.uniform(-1, 1, (n // 2, 3)) - o[: n // 2]     # half aimed into the box
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    o2, e = O.enter_box(o, d)
+    inside = np.all(np.abs(o) <= 1, axis=1)
+    assert np.all(e[inside] == 0) and np.array_equal(o2[inside], o[inside])
+    moved = e > 0
+    assert moved.sum() > 500 and (~moved & ~np.all(np.abs(o) <= 1, axis=1)).sum() > 500
+    assert np.allclose(np.abs(o2[moved]).max(axis=1), 1.0, atol=1e-12)
+    assert np.allclose(o2 - o, e[:, None] * d)
+    # brute force: march each moved ray finely, the first sample inside the box
+    # lies just past the entry distance
+    s = np.linspace(0, 12, 120001)
+    for i in np.nonzero(moved)[0][:50]:
+        p = o[i] + s[:, None] * d[i]
+        first = s[np.argmax(np.all(np.abs(p) <= 1, axis=1))]
+        assert 0 <= first - e[i] <= 1e-4 + 1e-12
+    # rays that miss: no sample of the line is inside
+    miss = ~inside & ~moved
+    for i in np.nonzero(miss)[0][:50]:
+        p = o[i] + s[:, None] * d[i]
+        assert not np.any(np.all(np.abs(p) < 1 - 1e-9, axis=1))
+    # exact hits are preserved: cast before and after
+    sc = I.Scene(np.zeros((1, 3)), np.array([0.5]), np.zeros((0, 3)), np.zeros((0, 3)))
+    t0, h0 = O.cast_scene(sc, o, d)
+    t1, h1 = O.cast_scene(sc, o2, d)
+    assert np.array_equal(h0, h1) and np.allclose(t1[h0], t0[h0] - e[h0])
