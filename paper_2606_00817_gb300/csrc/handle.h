@@ -99,8 +99,6 @@ struct ddf_s {
   void* tr_enc = nullptr;                 // [B x kp16] bf16
   std::vector<void*> tr_h;                // per layer [B x W] bf16 activations
   void* tr_dpre[2] = {nullptr, nullptr};  // [B x W] bf16 pre-activation gradients
-  void* tr_t1 = nullptr;                  // [W x B] bf16 (transposed gradient)
-  void* tr_t2 = nullptr;                  // [max(W, 128) x B] bf16 (transposed layer input)
   float* tr_part = nullptr;               // split-K partials of a weight gradient
   float* tr_cpart = nullptr;              // row-split partials of column sums
   float2* tr_z = nullptr;

@@ -46,6 +46,10 @@ struct TcGemmParams {
   // 1-CTA kernel, nullable: device int holding the number of rows to compute
   // (at most M; M remains the row stride of the head partials)
   const int* m_dev;
+  // 1-CTA kernel, bf16: both operands stored MN-major, A as [K x M] and B as
+  // [K x N] row-major (M / N index contiguous), their maps built with
+  // 64 x 64 boxes; lets dW = dZ^T X read dZ [B x W] and X [B x K] as stored
+  int mn_major;
 };
 
 // ---- sphere tracing of an SDF field (trace.cu) ----
@@ -183,8 +187,6 @@ cudaError_t launch_ao_reduce(const uint8_t* hit, const float* vis, const int32_t
                              int64_t n_points, float* hard, float* soft, cudaStream_t s);
 
 // ---- distillation step (train.cu) ----
-cudaError_t launch_transpose_bf16(const __nv_bfloat16* src, int R, int C, int lds,
-                                  __nv_bfloat16* dst, int ldd, cudaStream_t s);
 // z[r] = (Wo h_r + bo) from bf16 rows H [M x W]
 cudaError_t launch_head_train(const __nv_bfloat16* H, int M, int W, const float* wo,
                               const float* bo, float2* z, cudaStream_t s);

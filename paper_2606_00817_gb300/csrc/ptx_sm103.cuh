@@ -322,8 +322,24 @@ __device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t smem_addr) {
   return d;
 }
 
+// Shared-memory matrix descriptor for an MN-major bf16 operand: TMA boxes of
+// 64 M (or N) elements x K rows with 128-byte swizzling, so each K row is one
+// 128-byte line holding 64 consecutive M indices and 8 rows form a 1024-byte
+// atom. The leading-dimension offset steps to the next 64-wide box along M
+// (lbo bytes); the stride-dimension offset steps to the next 8 rows along K
+// (1024 B).
+__device__ __forceinline__ uint64_t sw128_mnmajor_desc(uint32_t smem_addr, uint32_t lbo) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((smem_addr >> 4) & 0x3FFFu);
+  d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
+  d |= static_cast<uint64_t>(1024u >> 4) << 32;
+  d |= static_cast<uint64_t>(1u) << 46;
+  d |= static_cast<uint64_t>(2u) << 61;
+  return d;
+}
+
 // Instruction descriptor for a dense M=128 MMA with FP32 accumulation and
-// both operands K-major.
+// both operands K-major (set bits 15 and 16 for MN-major A and B).
 //   bits 4-5 D format (1 = f32); bits 7-9 / 10-12 A / B format
 //   (kind::f16: 1 = bf16; kind::f8f6f4: 0 = e4m3); bit 15/16 A/B major (0 = K);
 //   bits 17-22 N >> 3; bits 24-28 M >> 4.

@@ -140,8 +140,20 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
           break;
         }
         mbar_arrive_expect_tx(full_bar(s), S::STAGE_BYTES);
-        tma_load_2d(smem_u32(sA + s * S::A_BYTES), &tmA, kb * S::BK, m0, full_bar(s));
-        tma_load_2d(smem_u32(sB + s * S::B_BYTES), &tmB, kb * S::BK, n0, full_bar(s));
+        if (!IN_FP8 && p.mn_major) {
+          // 64-wide boxes along M (N), each BK rows of K: 8 KB apiece
+#pragma unroll
+          for (int j = 0; j < S::BM / 64; ++j)
+            tma_load_2d(smem_u32(sA + s * S::A_BYTES + j * 64 * S::BK * 2), &tmA, m0 + 64 * j,
+                        kb * S::BK, full_bar(s));
+#pragma unroll
+          for (int j = 0; j < BN / 64; ++j)
+            tma_load_2d(smem_u32(sB + s * S::B_BYTES + j * 64 * S::BK * 2), &tmB, n0 + 64 * j,
+                        kb * S::BK, full_bar(s));
+        } else {
+          tma_load_2d(smem_u32(sA + s * S::A_BYTES), &tmA, kb * S::BK, m0, full_bar(s));
+          tma_load_2d(smem_u32(sB + s * S::B_BYTES), &tmB, kb * S::BK, n0, full_bar(s));
+        }
       }
     }
     if (!ok) {
@@ -153,7 +165,10 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------------------------------------------------- MMA issuer
-    constexpr uint32_t idesc = mma_idesc(IN_FP8 ? 0u : 1u, BN, S::BM);
+    constexpr uint32_t idesc_k = mma_idesc(IN_FP8 ? 0u : 1u, BN, S::BM);
+    const bool mn = !IN_FP8 && p.mn_major != 0;
+    const uint32_t idesc = mn ? (idesc_k | (1u << 15) | (1u << 16)) : idesc_k;
+    constexpr uint32_t kBoxBytes = 64 * S::BK * 2;  // one MN-major box (bf16)
     int it = 0, local = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x, ++local) {
@@ -177,9 +192,13 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
         const uint32_t a0 = smem_u32(sA + s * S::A_BYTES);
         const uint32_t b0 = smem_u32(sB + s * S::B_BYTES);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {  // 4 x 32 bytes of K per 128-byte row
-          const uint64_t ad = sw128_kmajor_desc(a0 + 32u * j);
-          const uint64_t bd = sw128_kmajor_desc(b0 + 32u * j);
+        for (int j = 0; j < 4; ++j) {
+          // K-major: 4 x 32 bytes of K per 128-byte row; MN-major: 4 x 16 K
+          // rows of 128 bytes (two 1024-byte atoms)
+          const uint64_t ad = mn ? sw128_mnmajor_desc(a0 + 2048u * j, kBoxBytes)
+                                 : sw128_kmajor_desc(a0 + 32u * j);
+          const uint64_t bd = mn ? sw128_mnmajor_desc(b0 + 2048u * j, kBoxBytes)
+                                 : sw128_kmajor_desc(b0 + 32u * j);
           const uint32_t acc = (kb != kb0 || j != 0) ? 1u : 0u;
           if constexpr (IN_FP8)
             tc_mma_f8(d_tmem, ad, bd, idesc, acc);
@@ -250,6 +269,7 @@ cudaError_t launch_one(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcG
   auto kern = tc_gemm_kernel<BN, IN_FP8, OUT_FP8, EPI>;
   // applies to the current device; cheap enough to repeat on every launch
   if (p.k_splits > 1 && ((p.K + S::BK - 1) / S::BK) % p.k_splits != 0) return cudaErrorInvalidValue;
+  if (p.mn_major && IN_FP8) return cudaErrorInvalidValue;
   const int smem = S::SMEM_BYTES + epi_vector_bytes(p.N);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;

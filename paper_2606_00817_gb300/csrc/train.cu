@@ -1,7 +1,8 @@
 // train.cu -- CUDA-core kernels of the distillation step (Sec. 3.2 / 3.4):
-// the FP32 head and its gradient, the clamped-L1 + cross-entropy loss, bf16
-// transposes for the weight-gradient GEMMs, column sums and split-K reduction,
-// Adam, transposed weight packing, and the exact ray caster against a union of
+// the FP32 head and its gradient, the clamped-L1 + cross-entropy loss, column
+// sums and split-K reduction, Adam, transposed weight packing (the weight
+// gradients themselves read their operands MN-major on the tensor cores, so
+// no activation is transposed), and the exact ray caster against a union of
 // spheres and boxes that supplies the distillation targets (Sec. 3.2, exact
 // cast supervision with analytic primitives in place of a mesh).
 #include <cuda_bf16.h>
@@ -17,23 +18,6 @@ __device__ __forceinline__ float softplus_t(float z) { return fmaxf(z, 0.f) + lo
 __device__ __forceinline__ float sigmoid_t(float z) {
   const float e = expf(-fabsf(z));
   return z >= 0.f ? 1.f / (1.f + e) : e / (1.f + e);
-}
-
-// dst[c][r] = src[r][c] for a bf16 [R x C] matrix (row strides lds, ldd).
-__global__ void transpose_bf16_kernel(const __nv_bfloat16* __restrict__ src, int R, int C, int lds,
-                                      __nv_bfloat16* __restrict__ dst, int ldd) {
-  __shared__ __nv_bfloat16 tile[32][34];
-  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const int r = r0 + i, c = c0 + threadIdx.x;
-    tile[i][threadIdx.x] = (r < R && c < C) ? src[static_cast<size_t>(r) * lds + c]
-                                            : __float2bfloat16_rn(0.f);
-  }
-  __syncthreads();
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const int c = c0 + i, r = r0 + threadIdx.x;
-    if (c < C && r < R) dst[static_cast<size_t>(c) * ldd + r] = tile[threadIdx.x][i];
-  }
 }
 
 // One warp per row: z = Wo h + bo from a bf16 activation row.
@@ -257,14 +241,6 @@ __global__ void cast_scene_kernel(const float* __restrict__ spheres, int ns,
 }
 
 }  // namespace
-
-cudaError_t launch_transpose_bf16(const __nv_bfloat16* src, int R, int C, int lds,
-                                  __nv_bfloat16* dst, int ldd, cudaStream_t s) {
-  if (R <= 0 || C <= 0) return cudaSuccess;
-  dim3 grid((C + 31) / 32, (R + 31) / 32);
-  transpose_bf16_kernel<<<grid, dim3(32, 8), 0, s>>>(src, R, C, lds, dst, ldd);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_head_train(const __nv_bfloat16* H, int M, int W, const float* wo,
                               const float* bo, float2* z, cudaStream_t s) {

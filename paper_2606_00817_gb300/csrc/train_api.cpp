@@ -121,8 +121,6 @@ ddf_status ensure_train(ddf_s* h, int64_t B) {
     for (void* q : h->tr_h) dev_free(h, q);
     dev_free(h, h->tr_dpre[0]);
     dev_free(h, h->tr_dpre[1]);
-    dev_free(h, h->tr_t1);
-    dev_free(h, h->tr_t2);
     dev_free(h, h->tr_z);
     dev_free(h, h->tr_dz);
     dev_free(h, h->tr_lpart);
@@ -134,9 +132,6 @@ ddf_status ensure_train(ddf_s* h, int64_t B) {
       if ((s = train_alloc(h, &h->tr_h[l], act)) != DDF_OK) return s;
     for (int i = 0; i < 2; ++i)
       if ((s = train_alloc(h, &h->tr_dpre[i], act)) != DDF_OK) return s;
-    if ((s = train_alloc(h, &h->tr_t1, act)) != DDF_OK) return s;
-    if ((s = train_alloc(h, &h->tr_t2, static_cast<size_t>(B) * std::max(W, 128) * 2)) != DDF_OK)
-      return s;
     if ((s = train_alloc(h, &p, B * sizeof(float2))) != DDF_OK) return s;
     h->tr_z = static_cast<float2*>(p);
     if ((s = train_alloc(h, &p, B * sizeof(float2))) != DDF_OK) return s;
@@ -245,24 +240,30 @@ ddf_status backward_from_dz(ddf_s* h, int B, cudaStream_t st) {
     const int N = l == 0 ? static_cast<int>(round_up(h->kp16, 128)) : W;  // GEMM N
     const int bnw = N % 256 == 0 ? 256 : 128;
     const void* A_in = l == 0 ? h->tr_enc : h->tr_h[l - 1];
-    DDF_CK(ddf::launch_transpose_bf16(bf(h->tr_dpre[cur]), B, W, W, bf(h->tr_t1), B, st));
-    DDF_CK(ddf::launch_transpose_bf16(static_cast<const __nv_bfloat16*>(A_in), B, Kst, Kst,
-                                      bf(h->tr_t2), B, st));
-    // dW_l [W x N] = dpre^T (as [W x B]) times A_in (as [N x B])^T, split over B
-    CUtensorMap tmT2;
-    if (!make_tmap(&tmT2, h->tr_t2, false, B, N, static_cast<uint64_t>(B) * 2, bnw))
+    // dW_l [W x N] = dpre^T A_in, the sum over the batch split in `splits`
+    // ranges: both operands are read as stored ([B x W] and [B x Kst],
+    // row-major), i.e. MN-major, so nothing is transposed
+    CUtensorMap tmD, tmX;
+    if (!make_tmap(&tmD, h->tr_dpre[cur], false, W, B, static_cast<uint64_t>(W) * 2, 64) ||
+        !make_tmap(&tmX, A_in, false, Kst, B, static_cast<uint64_t>(Kst) * 2, 64))
       return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for a gradient map");
     ddf::TcGemmParams p{};
+    p.M = W;
     p.N = N;
+    p.K = B;
     p.mode = 3;
+    p.mn_major = 1;
     p.out_f32 = h->tr_part;
     p.ldo = N;
     p.k_splits = splits;
     p.split_stride = static_cast<size_t>(W) * N;
+    p.status = h->status_dev;
+    p.timeout_ns = h->timeout_ns;
     {
       ProfScope ps(h, kProfGemm, st);
-      ddf_status s = tc_gemm(h, h->tr_t1, W, B, tmT2, bnw, p, st);
-      if (s != DDF_OK) return s;
+      const int64_t tiles = splits * ((W + 127) / 128) * static_cast<int64_t>(N / bnw);
+      const int grid = static_cast<int>(std::min<int64_t>(tiles, h->num_sms));
+      DDF_CK(ddf::launch_tc_gemm(ddf::TcTile{bnw, 4}, false, false, tmD, tmX, p, grid, st));
     }
     DDF_CK(ddf::launch_splitk_reduce(h->tr_part, splits, W, N, static_cast<int64_t>(W) * N, K,
                                      h->grad + o.w[l], K, st));
