@@ -118,6 +118,10 @@ struct ddf_s {
   std::vector<__nv_bfloat16*> wt;         // layers 2..H: bf16 W^T [K x W] for input gradients
   std::vector<CUtensorMap> tmBtr;         // weight maps for the plain 1-CTA tile {bn, 4}
   std::vector<CUtensorMap> tmWT;          // maps of wt
+  // CTA-pair training GEMMs (width a multiple of 256): weight maps with
+  // 128-row boxes, for the forward (W_l) and the input gradients (W_l^T)
+  bool tr_pair = false;
+  std::vector<CUtensorMap> tmBpair, tmWTpair;
 
   // sphere tracing (SDF fields)
   int* trc_idx[2] = {nullptr, nullptr};   // active-ray lists

@@ -109,7 +109,8 @@ cudaError_t launch_tc_gemm(const TcTile& tile, bool in_fp8, bool out_fp8, const 
 int tc_gemm_smem_bytes(int bn, bool in_fp8);
 
 // CTA-pair variant: clusters of 2 CTAs, 256 x 256 output tiles, persistent
-// over `clusters` clusters. Mode 1 writes N/256 partials per row.
+// over `clusters` clusters. Mode 1 writes N/256 partials per row; modes 2
+// and 3 (bf16) as the 1-CTA kernel, mode 3 with K-major or MN-major operands.
 cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, bool staged, const CUtensorMap& tmA,
                                 const CUtensorMap& tmB, const TcGemmParams& p, int clusters,
                                 cudaStream_t s);

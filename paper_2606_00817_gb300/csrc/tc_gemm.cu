@@ -112,9 +112,10 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
   const int num_n = p.N / BN;
   const int num_kb = (p.K + S::BK - 1) / S::BK;
   // split-K (mode 3): tile = (split, m block, n block); split s covers the
-  // k-blocks [s kb_per, (s+1) kb_per) (the launcher makes every split non-empty)
+  // k-blocks [s num_kb / splits, (s+1) num_kb / splits) (the launcher makes
+  // every split non-empty)
   const int splits = p.k_splits > 1 ? p.k_splits : 1;
-  const int kb_per = num_kb / splits;
+  auto kb_lo = [&](int split) { return static_cast<int>((static_cast<int64_t>(split) * num_kb) / splits); };
   const int num_tiles = splits * num_m * num_n;
   auto decode = [&](int tile, int& split, int& m_blk, int& n_blk) {
     split = tile / (num_m * num_n);
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
       decode(tile, split, m_blk, n_blk);
       const int m0 = m_blk * S::BM;
       const int n0 = n_blk * BN;
-      for (int kb = split * kb_per; kb < (split + 1) * kb_per; ++kb, ++it) {
+      for (int kb = kb_lo(split); kb < kb_lo(split + 1); ++kb, ++it) {
         const int s = it % S::STAGES;
         const uint32_t ph = (it / S::STAGES) & 1;
         if (!mbar_wait_bounded(empty_bar(s), ph ^ 1u, abort_flag, p.timeout_ns)) {
@@ -180,8 +181,9 @@ __global__ void __launch_bounds__(64 + 32 * EPI, 1)
       }
       tc_fence_after();
       const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(b * BN);
-      const int kb0 = (tile / (num_m * num_n)) * kb_per;
-      for (int kb = kb0; kb < kb0 + kb_per; ++kb, ++it) {
+      const int split = tile / (num_m * num_n);
+      const int kb0 = kb_lo(split), kb1 = kb_lo(split + 1);
+      for (int kb = kb0; kb < kb1; ++kb, ++it) {
         const int s = it % S::STAGES;
         const uint32_t ph = (it / S::STAGES) & 1;
         if (!mbar_wait_bounded(full_bar(s), ph, abort_flag, p.timeout_ns)) {
@@ -268,7 +270,7 @@ cudaError_t launch_one(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcG
   using S = TcShape<BN, IN_FP8>;
   auto kern = tc_gemm_kernel<BN, IN_FP8, OUT_FP8, EPI>;
   // applies to the current device; cheap enough to repeat on every launch
-  if (p.k_splits > 1 && ((p.K + S::BK - 1) / S::BK) % p.k_splits != 0) return cudaErrorInvalidValue;
+  if (p.k_splits > 1 && (p.K + S::BK - 1) / S::BK < p.k_splits) return cudaErrorInvalidValue;
   if (p.mn_major && IN_FP8) return cudaErrorInvalidValue;
   const int smem = S::SMEM_BYTES + epi_vector_bytes(p.N);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -1,6 +1,8 @@
 // tc_gemm_pair.cu -- one dense DDF layer on a pair of SMs (tcgen05 cta_group::2).
 //
-// Same layer as tc_gemm.cu (Y = act(A W^T * scale + b), Sec. 3.1 / Sec. 4.3),
+// Same layer as tc_gemm.cu (Y = act(A W^T * scale + b), Sec. 3.1 / Sec. 4.3,
+// and the training modes: masked input gradients, split-K weight gradients
+// with MN-major operands),
 // but each 256 x 256 output tile is computed by a cluster of two CTAs that
 // share one MMA: CTA r of the pair loads rows [128 r, 128 r + 128) of the A
 // tile and rows [128 r, 128 r + 128) of the W tile into its own shared memory,
@@ -58,7 +60,10 @@ struct PairShape {
   static_assert(NUM_BARS * 8 + 16 <= CTRL_BYTES, "control block overflow");
 };
 
-template <bool IN_FP8, bool OUT_FP8, bool STAGED>
+// TRAIN: the training modes (2, 3: masked input gradients, split-K weight
+// gradients with K-major or MN-major operands), bf16 only; the query
+// instantiations compile none of it.
+template <bool IN_FP8, bool OUT_FP8, bool STAGED, bool TRAIN>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                         const __grid_constant__ CUtensorMap tmB, const TcGemmParams p) {
@@ -123,16 +128,50 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
   const int num_m = (p.M + S::BM - 1) / S::BM;
   const int num_n = p.N / S::BN;
   const int num_kb = (p.K + S::BK - 1) / S::BK;
-  const int num_tiles = num_m * num_n;
+  // split-K (mode 3): tile = (split, m block, n block); split s covers the
+  // k-blocks [s num_kb / splits, (s+1) num_kb / splits)
+  const int splits = (TRAIN && p.k_splits > 1) ? p.k_splits : 1;
+  auto kb_lo = [&](int split) {
+    if constexpr (!TRAIN) return split * num_kb;
+    return static_cast<int>((static_cast<int64_t>(split) * num_kb) / splits);
+  };
+  const int num_tiles = splits * num_m * num_n;
+  auto decode = [&](int tile, int& split, int& m_blk, int& n_blk) {
+    split = tile / (num_m * num_n);
+    const int r = tile - split * num_m * num_n;
+    m_blk = r / num_n;
+    n_blk = r - m_blk * num_n;
+  };
+  // MN-major operands (bf16): A as [K x M], B as [K x N] row-major, loaded as
+  // 64-wide boxes of BK rows (8 KB each, two per operand half)
+  const bool mn = TRAIN && !IN_FP8 && p.mn_major != 0;
+  constexpr uint32_t kBoxBytes = 64 * S::BK * 2;
+  auto load_stage = [&](int s, int m0, int nb, int kb, uint32_t bar) {
+    if (mn) {
+#pragma unroll
+      for (int j = 0; j < S::HALF / 64; ++j) {
+        tma_load_2d_pair(smem_u32(sA + s * S::A_BYTES) + j * kBoxBytes, &tmA, m0 + 64 * j,
+                         kb * S::BK, bar);
+        tma_load_2d_pair(smem_u32(sB + s * S::B_BYTES) + j * kBoxBytes, &tmB, nb + 64 * j,
+                         kb * S::BK, bar);
+      }
+    } else {
+      tma_load_2d_pair(smem_u32(sA + s * S::A_BYTES), &tmA, kb * S::BK, m0, bar);
+      tma_load_2d_pair(smem_u32(sB + s * S::B_BYTES), &tmB, kb * S::BK, nb, bar);
+    }
+  };
 
   if (warp == 0 && lane == 0) {
     // ---------------------------------------------------------- producer
     uint32_t it = 0;
     bool ok = true;
     for (int tile = pair; tile < num_tiles && ok; tile += npairs) {
-      const int m0 = (tile / num_n) * S::BM + static_cast<int>(rank) * S::HALF;
-      const int nb = (tile % num_n) * S::BN + static_cast<int>(rank) * S::HALF;
-      for (int kb = 0; kb < num_kb; ++kb, ++it) {
+      int split, m_blk, n_blk;
+      decode(tile, split, m_blk, n_blk);
+      const int m0 = m_blk * S::BM + static_cast<int>(rank) * S::HALF;
+      const int nb = n_blk * S::BN + static_cast<int>(rank) * S::HALF;
+      const int kb1 = kb_lo(split + 1);
+      for (int kb = kb_lo(split); kb < kb1; ++kb, ++it) {
         const int s = it % S::STAGES;
         const uint32_t ph = (it / S::STAGES) & 1;
         if (!mbar_wait_bounded(empty_bar(s), ph ^ 1u, abort_flag, p.timeout_ns)) {
@@ -140,8 +179,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
           break;
         }
         if (rank == 0) mbar_arrive_expect_tx(full_bar(s), 2 * S::STAGE_BYTES);
-        tma_load_2d_pair(smem_u32(sA + s * S::A_BYTES), &tmA, kb * S::BK, m0, full_leader0 + 8u * s);
-        tma_load_2d_pair(smem_u32(sB + s * S::B_BYTES), &tmB, kb * S::BK, nb, full_leader0 + 8u * s);
+        load_stage(s, m0, nb, kb, full_leader0 + 8u * s);
       }
     }
     if (!ok) raise_abort();
@@ -150,7 +188,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     st_cluster_u32(map_to_cta(slot, 1), it);
   } else if (warp == 1 && lane == 0 && rank == 0) {
     // ---------------------------------------------------------- MMA issuer (leader)
-    constexpr uint32_t idesc = mma_idesc(IN_FP8 ? 0u : 1u, S::BN, S::BM);
+    constexpr uint32_t idesc_k = mma_idesc(IN_FP8 ? 0u : 1u, S::BN, S::BM);
+    const uint32_t idesc = mn ? (idesc_k | (1u << 15) | (1u << 16)) : idesc_k;
     int it = 0, local = 0;
     bool ok = true;
     for (int tile = pair; tile < num_tiles && ok; tile += npairs, ++local) {
@@ -162,7 +201,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
       }
       tc_fence_after();
       const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(b * S::BN);
-      for (int kb = 0; kb < num_kb; ++kb, ++it) {
+      const int split = tile / (num_m * num_n);
+      const int kb0 = kb_lo(split), kb1 = kb_lo(split + 1);
+      for (int kb = kb0; kb < kb1; ++kb, ++it) {
         const int s = it % S::STAGES;
         const uint32_t ph = (it / S::STAGES) & 1;
         if (!mbar_wait_bounded(full_bar(s), ph, abort_flag, p.timeout_ns)) {
@@ -174,9 +215,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
         const uint32_t b0 = smem_u32(sB + s * S::B_BYTES);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const uint64_t ad = sw128_kmajor_desc(a0 + 32u * j);
-          const uint64_t bd = sw128_kmajor_desc(b0 + 32u * j);
-          const uint32_t acc = (kb | j) != 0 ? 1u : 0u;
+          // K-major: 4 x 32 bytes of K per 128-byte row; MN-major: 4 x 16 K
+          // rows of 128 bytes
+          const uint64_t ad = mn ? sw128_mnmajor_desc(a0 + 2048u * j, kBoxBytes)
+                                 : sw128_kmajor_desc(a0 + 32u * j);
+          const uint64_t bd = mn ? sw128_mnmajor_desc(b0 + 2048u * j, kBoxBytes)
+                                 : sw128_kmajor_desc(b0 + 32u * j);
+          const uint32_t acc = (kb != kb0 || j != 0) ? 1u : 0u;
           if constexpr (IN_FP8)
             tc_mma_pair_f8(d_tmem, ad, bd, idesc, acc);
           else
@@ -206,15 +251,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
         break;
       }
       tc_fence_after();
-      const int m_blk = tile / num_n;
-      const int n_blk = tile % num_n;
+      int split, m_blk, n_blk;
+      decode(tile, split, m_blk, n_blk);
       const int row = m_blk * S::BM + static_cast<int>(rank) * S::HALF + r_local;
       const bool row_ok = row < p.M;
       const int n0 = n_blk * S::BN;
       const uint32_t tbase = tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
                              static_cast<uint32_t>(b * S::BN);
       float h0 = 0.f, h1 = 0.f;
-      if (STAGED && p.mode == 0) {
+      if constexpr (TRAIN) {
+        epi_row_train(p, tbase, row, row_ok, n0, 0, S::BN / 32, split);
+      } else if (STAGED && p.mode == 0) {
         uint8_t* stage = smem + S::VEC_OFFSET + epi_vector_bytes(p.N) + q * kStageBytesPerWarp;
         epi_row_staged<OUT_FP8>(p, ev, tbase, row - lane, n0, 0, S::BN / 32, stage, lane);
       } else {
@@ -238,8 +285,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     for (uint32_t j = mine; j < other; ++j) {
       const int s = j % S::STAGES;
       if (rank == 0) mbar_arrive_expect_tx(full_bar(s), 2 * S::STAGE_BYTES);
-      tma_load_2d_pair(smem_u32(sA + s * S::A_BYTES), &tmA, 0, 0, full_leader0 + 8u * s);
-      tma_load_2d_pair(smem_u32(sB + s * S::B_BYTES), &tmB, 0, 0, full_leader0 + 8u * s);
+      load_stage(s, 0, 0, 0, full_leader0 + 8u * s);
     }
     if (rank == 0) {
       const uint32_t jmax = mine > other ? mine : other;
@@ -257,11 +303,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
   }
 }
 
-template <bool IN_FP8, bool OUT_FP8, bool STAGED>
+template <bool IN_FP8, bool OUT_FP8, bool STAGED, bool TRAIN = false>
 cudaError_t launch_pair_one(const CUtensorMap& tmA, const CUtensorMap& tmB,
                             const TcGemmParams& p, int grid, cudaStream_t s) {
   using S = PairShape<IN_FP8, STAGED>;
-  auto kern = tc_gemm_pair_kernel<IN_FP8, OUT_FP8, STAGED>;
+  auto kern = tc_gemm_pair_kernel<IN_FP8, OUT_FP8, STAGED, TRAIN>;
   const int smem = S::SMEM_BYTES + epi_vector_bytes(p.N) + S::OUT_STAGE_BYTES;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
@@ -272,7 +318,7 @@ cudaError_t launch_pair_one(const CUtensorMap& tmA, const CUtensorMap& tmB,
 template <bool IN_FP8, bool STAGED>
 int max_pairs_for() {
   using S = PairShape<IN_FP8, STAGED>;
-  auto kern = tc_gemm_pair_kernel<IN_FP8, false, STAGED>;
+  auto kern = tc_gemm_pair_kernel<IN_FP8, false, STAGED, false>;
   const int smem = S::SMEM_BYTES + epi_vector_bytes(kMaxStagedColumns) + S::OUT_STAGE_BYTES;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
     return 0;
@@ -306,8 +352,12 @@ int tc_gemm_pair_max_clusters(bool in_fp8) {
 cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, bool staged, const CUtensorMap& tmA,
                                 const CUtensorMap& tmB, const TcGemmParams& p, int clusters,
                                 cudaStream_t s) {
-  if (p.mode > 1) return cudaErrorInvalidValue;  // training modes run on the 1-CTA kernel
+  if (p.mode == 3 && (p.k_splits > 1 ? p.k_splits : 1) > (p.K + 63) / 64)
+    return cudaErrorInvalidValue;  // every split needs a k-block
+  if (p.mn_major && (in_fp8 || p.mode != 3)) return cudaErrorInvalidValue;
+  if (p.mode >= 2 && (in_fp8 || out_fp8)) return cudaErrorInvalidValue;
   const int grid = 2 * clusters;
+  if (p.mode >= 2) return launch_pair_one<false, false, false, true>(tmA, tmB, p, grid, s);
   if (in_fp8) return staged ? launch_pair_io<true, true>(out_fp8, tmA, tmB, p, grid, s)
                             : launch_pair_io<true, false>(out_fp8, tmA, tmB, p, grid, s);
   return staged ? launch_pair_io<false, true>(out_fp8, tmA, tmB, p, grid, s)

@@ -21,7 +21,8 @@ using namespace ddfi;
 
 namespace {
 
-constexpr int kColSplits = 64;  // row splits of the column sums
+constexpr int kColSplits = 64;   // row splits of the column sums
+constexpr int kPartSplits = 16;  // most batch splits of a weight-gradient GEMM
 constexpr float kClamp = kLossClamp;
 constexpr float kLambda = kLossLambda;
 constexpr float kB1 = kAdamB1, kB2 = kAdamB2, kEps = kAdamEps;
@@ -98,14 +99,22 @@ ddf_status ensure_train(ddf_s* h, int64_t B) {
     h->wt.assign(H, nullptr);
     h->tmWT.assign(H, CUtensorMap{});
     if ((s = ensure_plain_maps(h)) != DDF_OK) return s;
+    h->tr_pair = W % 256 == 0 && h->pair_clusters > 0;
+    h->tmBpair.assign(H, CUtensorMap{});
+    h->tmWTpair.assign(H, CUtensorMap{});
     for (int l = 1; l < H; ++l) {
       if ((s = train_alloc(h, &p, static_cast<size_t>(W) * W * 2)) != DDF_OK) return s;
       h->wt[l] = static_cast<__nv_bfloat16*>(p);
       if (!make_tmap(&h->tmWT[l], h->wt[l], false, W, W, static_cast<uint64_t>(W) * 2, h->bn))
         return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for a weight map");
+      if (h->tr_pair &&
+          (!make_tmap(&h->tmWTpair[l], h->wt[l], false, W, W, static_cast<uint64_t>(W) * 2, 128) ||
+           !make_tmap(&h->tmBpair[l], h->wb[l], false, W, W, static_cast<uint64_t>(W) * 2, 128)))
+        return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for a weight map");
     }
     const int nmax = std::max(W, 128);
-    if ((s = train_alloc(h, &p, 4 * static_cast<size_t>(W) * nmax * sizeof(float))) != DDF_OK) return s;
+    if ((s = train_alloc(h, &p, kPartSplits * static_cast<size_t>(W) * nmax * sizeof(float))) != DDF_OK)
+      return s;
     h->tr_part = static_cast<float*>(p);
     if ((s = train_alloc(h, &p, kColSplits * 2 * static_cast<size_t>(W) * sizeof(float))) != DDF_OK)
       return s;
@@ -160,6 +169,23 @@ ddf_status tc_gemm(ddf_s* h, const void* A, int M, int K, const CUtensorMap& tmB
   return DDF_OK;
 }
 
+// The same on the CTA-pair kernel (W a multiple of 256; B-operand maps with
+// 128-row boxes); staged: mode-0 outputs leave through shared memory.
+ddf_status tc_gemm_pair(ddf_s* h, const void* A, int M, int K, const CUtensorMap& tmB, bool staged,
+                        ddf::TcGemmParams p, cudaStream_t st) {
+  CUtensorMap tmA;
+  if (!make_tmap(&tmA, A, false, K, M, static_cast<uint64_t>(K) * 2, 128))
+    return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for an activation map");
+  p.M = M;
+  p.K = K;
+  p.status = h->status_dev;
+  p.timeout_ns = h->timeout_ns;
+  const int64_t tiles = ((M + 255) / 256) * static_cast<int64_t>(p.N / 256);
+  const int clusters = static_cast<int>(std::min<int64_t>(tiles, h->pair_clusters));
+  DDF_CK(ddf::launch_tc_gemm_pair(false, false, staged, tmA, tmB, p, clusters, st));
+  return DDF_OK;
+}
+
 ddf_status check_train_args(ddf_s* h, const float* const rays[6], const float* t_target,
                             const uint8_t* hit_target, int64_t batch, int kind = DDF_KIND_RAY) {
   if (h == nullptr) return fail(DDF_ERR_INVALID_ARG, "handle is NULL");
@@ -205,8 +231,10 @@ ddf_status forward_keep(ddf_s* h, const float* const rays[6], int B, cudaStream_
     p.ldo = W;
     p.mode = 0;
     ProfScope ps(h, l == 0 ? kProfFirst : kProfGemm, st);
-    ddf_status s = tc_gemm(h, l == 0 ? h->tr_enc : h->tr_h[l - 1], B, l == 0 ? h->kp16 : W,
-                           h->tmBtr[l], h->bn, p, st);
+    ddf_status s = l > 0 && h->tr_pair
+                       ? tc_gemm_pair(h, h->tr_h[l - 1], B, W, h->tmBpair[l], true, p, st)
+                       : tc_gemm(h, l == 0 ? h->tr_enc : h->tr_h[l - 1], B, l == 0 ? h->kp16 : W,
+                                 h->tmBtr[l], h->bn, p, st);
     if (s != DDF_OK) return s;
   }
   DDF_CK(ddf::launch_head_train(bf(h->tr_h[H - 1]), B, W, h->head_w, h->head_b, h->tr_z, st));
@@ -233,12 +261,32 @@ ddf_status backward_from_dz(ddf_s* h, int B, cudaStream_t st) {
   // ---- layers, last to first
   int cur = 0;
   const int num_kb = (B + 63) / 64;
-  const int splits = num_kb % 4 == 0 ? 4 : (num_kb % 2 == 0 ? 2 : 1);
   for (int l = H - 1; l >= 0; --l) {
     const int K = l == 0 ? h->d_in : W;        // columns of W_l in the blob
     const int Kst = l == 0 ? h->kp16 : W;      // stored width of the layer input
     const int N = l == 0 ? static_cast<int>(round_up(h->kp16, 128)) : W;  // GEMM N
     const int bnw = N % 256 == 0 ? 256 : 128;
+    const bool pair = h->tr_pair && N % 256 == 0;
+    // split the batch so that the tiles fill the GPU evenly: the number of
+    // splits s minimises waves(s) / s (time per unit of work, waves = ceil(s
+    // tiles / CTAs or pairs)) with 2 % per split for the partials' traffic,
+    // within the partial buffer (kPartSplits W max(W, 128) floats) and at
+    // least one k-block per split
+    const int64_t tiles1 = pair ? static_cast<int64_t>((W + 255) / 256) * (N / 256)
+                                : static_cast<int64_t>((W + 127) / 128) * (N / bnw);
+    const int64_t slots = pair ? h->pair_clusters : h->num_sms;
+    const int64_t cap = std::min<int64_t>(
+        num_kb, (kPartSplits * static_cast<int64_t>(W) * std::max(W, 128)) / (static_cast<int64_t>(W) * N));
+    int splits = 1;
+    double best = 1e30;
+    for (int64_t c = 1; c <= cap; ++c) {
+      const double waves = static_cast<double>((c * tiles1 + slots - 1) / slots);
+      const double cost = waves / static_cast<double>(c) * (1.0 + 0.02 * static_cast<double>(c));
+      if (cost < best - 1e-12) {
+        best = cost;
+        splits = static_cast<int>(c);
+      }
+    }
     const void* A_in = l == 0 ? h->tr_enc : h->tr_h[l - 1];
     // dW_l [W x N] = dpre^T A_in, the sum over the batch split in `splits`
     // ranges: both operands are read as stored ([B x W] and [B x Kst],
@@ -261,9 +309,11 @@ ddf_status backward_from_dz(ddf_s* h, int B, cudaStream_t st) {
     p.timeout_ns = h->timeout_ns;
     {
       ProfScope ps(h, kProfGemm, st);
-      const int64_t tiles = splits * ((W + 127) / 128) * static_cast<int64_t>(N / bnw);
-      const int grid = static_cast<int>(std::min<int64_t>(tiles, h->num_sms));
-      DDF_CK(ddf::launch_tc_gemm(ddf::TcTile{bnw, 4}, false, false, tmD, tmX, p, grid, st));
+      const int grid = static_cast<int>(std::min<int64_t>(splits * tiles1, slots));
+      if (pair)
+        DDF_CK(ddf::launch_tc_gemm_pair(false, false, false, tmD, tmX, p, grid, st));
+      else
+        DDF_CK(ddf::launch_tc_gemm(ddf::TcTile{bnw, 4}, false, false, tmD, tmX, p, grid, st));
     }
     DDF_CK(ddf::launch_splitk_reduce(h->tr_part, splits, W, N, static_cast<int64_t>(W) * N, K,
                                      h->grad + o.w[l], K, st));
@@ -280,7 +330,8 @@ ddf_status backward_from_dz(ddf_s* h, int B, cudaStream_t st) {
     q.ldm = W;
     {
       ProfScope ps(h, kProfGemm, st);
-      ddf_status s = tc_gemm(h, h->tr_dpre[cur], B, W, h->tmWT[l], h->bn, q, st);
+      ddf_status s = h->tr_pair ? tc_gemm_pair(h, h->tr_dpre[cur], B, W, h->tmWTpair[l], false, q, st)
+                                : tc_gemm(h, h->tr_dpre[cur], B, W, h->tmWT[l], h->bn, q, st);
       if (s != DDF_OK) return s;
     }
     cur ^= 1;
