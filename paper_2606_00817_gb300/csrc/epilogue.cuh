@@ -312,4 +312,115 @@ __device__ __forceinline__ void epi_row_staged(const TcGemmParams& p, const EpiV
   }
 }
 
+// Training forward (mode 0, bf16, no column scale) through the warp's
+// staging buffer, as epi_row_staged, plus the layer's ReLU pattern: bit j of
+// relu_bits[row * ldb + column / 32] is set iff output column 32 (column / 32)
+// + j of the row is positive after rounding to bf16 (the test the input
+// gradients apply to this activation).
+__device__ __forceinline__ void epi_row_staged_bits(const TcGemmParams& p, const EpiVectors& ev,
+                                                    uint32_t tbase, int warp_row0, int n0,
+                                                    int c_begin, int c_end, uint8_t* stage,
+                                                    int lane) {
+  const size_t row_bytes = static_cast<size_t>(p.ldo) * 2;
+  const int row = warp_row0 + lane;
+  const int sw = lane & 7;
+  uint8_t* myrow = stage + lane * 128;
+  uint32_t va[32], vb[32];
+#pragma unroll 1
+  for (int c = c_begin; c < c_end; c += 2) {
+    tmem_ld32(tbase + 32u * c, va);
+    tmem_ld32(tbase + 32u * (c + 1), vb);
+    tmem_wait_ld_regs(va);
+    tmem_wait_ld_regs(vb);
+    uint32_t bits[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t* v = h == 0 ? va : vb;
+      const float* bias = ev.bias + n0 + 32 * (c + h);
+      uint32_t m = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        uint32_t ow[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = 8 * k + 2 * q;
+          ow[q] = epi_pack_bf16x2(fmaxf(__uint_as_float(v[j]) + bias[j], 0.f),
+                                  fmaxf(__uint_as_float(v[j + 1]) + bias[j + 1], 0.f));
+          m |= ((ow[q] & 0xFFFFu) != 0u ? 1u : 0u) << j;
+          m |= ((ow[q] >> 16) != 0u ? 1u : 0u) << (j + 1);
+        }
+        *reinterpret_cast<uint4*>(myrow + (((4 * h + k) ^ sw) << 4)) =
+            make_uint4(ow[0], ow[1], ow[2], ow[3]);
+      }
+      bits[h] = m;
+    }
+    if (row < p.M)
+      *reinterpret_cast<uint2*>(p.relu_bits + static_cast<size_t>(row) * p.ldb + n0 / 32 + c) =
+          make_uint2(bits[0], bits[1]);
+    epi_flush_stage(p, stage, warp_row0, row_bytes, static_cast<size_t>(n0 + 32 * c) * 2, lane);
+  }
+}
+
+// Input gradient (mode 2, bf16) through the warp's staging buffer: the
+// accumulator where the previous layer's ReLU pattern (relu_bits, as written
+// by epi_row_staged_bits) is set, else 0, leaving as 128-byte lines. With
+// p.col_part, lane l also sums columns 2l and 2l + 1 of each 64-column group
+// over the warp's 32 rows (the bias gradient's share of these rows) into
+// col_part[warp_row0 / 32][column].
+__device__ __forceinline__ void epi_row_masked_staged(const TcGemmParams& p, uint32_t tbase,
+                                                      int warp_row0, int n0, int c_begin,
+                                                      int c_end, uint8_t* stage, int lane) {
+  const size_t row_bytes = static_cast<size_t>(p.ldo) * 2;
+  const int row = warp_row0 + lane;
+  const int sw = lane & 7;
+  uint8_t* myrow = stage + lane * 128;
+  uint32_t va[32], vb[32];
+#pragma unroll 1
+  for (int c = c_begin; c < c_end; c += 2) {
+    tmem_ld32(tbase + 32u * c, va);
+    tmem_ld32(tbase + 32u * (c + 1), vb);
+    uint2 mb = make_uint2(0u, 0u);
+    if (row < p.M)
+      mb = *reinterpret_cast<const uint2*>(p.relu_bits + static_cast<size_t>(row) * p.ldb + n0 / 32 + c);
+    tmem_wait_ld_regs(va);
+    tmem_wait_ld_regs(vb);
+    __syncwarp();  // the previous group's flush has read the buffer
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t* v = h == 0 ? va : vb;
+      const uint32_t m = h == 0 ? mb.x : mb.y;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        uint32_t ow[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = 8 * k + 2 * q;
+          const float x0 = (m >> j) & 1u ? __uint_as_float(v[j]) : 0.f;
+          const float x1 = (m >> (j + 1)) & 1u ? __uint_as_float(v[j + 1]) : 0.f;
+          ow[q] = epi_pack_bf16x2(x0, x1);
+        }
+        *reinterpret_cast<uint4*>(myrow + (((4 * h + k) ^ sw) << 4)) =
+            make_uint4(ow[0], ow[1], ow[2], ow[3]);
+      }
+    }
+    if (p.col_part != nullptr) {
+      __syncwarp();
+      // lane l: columns 2l, 2l + 1 of the group = 4-byte word (l & 3) of
+      // 16-byte piece l >> 2 in every row
+      float s0 = 0.f, s1 = 0.f;
+      const int piece = lane >> 2, word = lane & 3;
+#pragma unroll 8
+      for (int r = 0; r < 32; ++r) {
+        const uint32_t w = *reinterpret_cast<const uint32_t*>(stage + r * 128 +
+                                                              ((piece ^ (r & 7)) << 4) + 4 * word);
+        s0 += __uint_as_float(w << 16);
+        s1 += __uint_as_float(w & 0xFFFF0000u);
+      }
+      *reinterpret_cast<float2*>(p.col_part + static_cast<size_t>(warp_row0 / 32) * p.ldo + n0 +
+                                 32 * c + 2 * lane) = make_float2(s0, s1);
+    }
+    epi_flush_stage(p, stage, warp_row0, row_bytes, static_cast<size_t>(n0 + 32 * c) * 2, lane);
+  }
+}
+
 }  // namespace ddf

@@ -105,6 +105,8 @@ struct ddf_s {
   float2* tr_dz = nullptr;
   unsigned* tr_nhit = nullptr;
   float* tr_lpart = nullptr;              // per-block loss partials
+  float* tr_colpart = nullptr;            // [B / 32 x W] column sums of an input gradient
+  std::vector<uint32_t*> tr_bits;         // layers 0..H-2: [B x W/32] ReLU patterns (pair path)
   float* grad = nullptr;                  // gradient blob (weight-blob layout)
   float* adam_m = nullptr;
   float* adam_v = nullptr;

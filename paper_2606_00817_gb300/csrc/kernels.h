@@ -50,6 +50,14 @@ struct TcGemmParams {
   // [K x N] row-major (M / N index contiguous), their maps built with
   // 64 x 64 boxes; lets dW = dZ^T X read dZ [B x W] and X [B x K] as stored
   int mn_major;
+  // training on the pair kernel: mode 0 writes the output's ReLU pattern
+  // (bit j of relu_bits[row * ldb + c]: column 32 c + j positive), mode 2
+  // applies the previous layer's pattern from relu_bits instead of reading
+  // `mask`, and writes per 32-row block column sums of its output into
+  // col_part [ceil(M / 32) x ldo] FP32 (nullable)
+  uint32_t* relu_bits;
+  int ldb;
+  float* col_part;
 };
 
 // ---- sphere tracing of an SDF field (trace.cu) ----

@@ -260,7 +260,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
                              static_cast<uint32_t>(b * S::BN);
       float h0 = 0.f, h1 = 0.f;
       if constexpr (TRAIN) {
-        epi_row_train(p, tbase, row, row_ok, n0, 0, S::BN / 32, split);
+        uint8_t* stage = smem + S::VEC_OFFSET + epi_vector_bytes(p.N) + q * kStageBytesPerWarp;
+        if (p.mode == 0)
+          epi_row_staged_bits(p, ev, tbase, row - lane, n0, 0, S::BN / 32, stage, lane);
+        else if (p.mode == 2)
+          epi_row_masked_staged(p, tbase, row - lane, n0, 0, S::BN / 32, stage, lane);
+        else
+          epi_row_train(p, tbase, row, row_ok, n0, 0, S::BN / 32, split);
       } else if (STAGED && p.mode == 0) {
         uint8_t* stage = smem + S::VEC_OFFSET + epi_vector_bytes(p.N) + q * kStageBytesPerWarp;
         epi_row_staged<OUT_FP8>(p, ev, tbase, row - lane, n0, 0, S::BN / 32, stage, lane);
@@ -356,8 +362,14 @@ cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, bool staged, const CU
     return cudaErrorInvalidValue;  // every split needs a k-block
   if (p.mn_major && (in_fp8 || p.mode != 3)) return cudaErrorInvalidValue;
   if (p.mode >= 2 && (in_fp8 || out_fp8)) return cudaErrorInvalidValue;
+  if ((p.mode == 2 || p.relu_bits != nullptr) &&
+      (p.relu_bits == nullptr || p.ldb < p.N / 32 || p.ldb % 2 != 0 || p.N % 64 != 0 || in_fp8 ||
+       out_fp8))
+    return cudaErrorInvalidValue;  // ReLU patterns: bf16, whole 64-column groups
   const int grid = 2 * clusters;
-  if (p.mode >= 2) return launch_pair_one<false, false, false, true>(tmA, tmB, p, grid, s);
+  // training modes, and the training forward that writes ReLU patterns
+  if (p.mode >= 2 || p.relu_bits != nullptr)
+    return launch_pair_one<false, false, true, true>(tmA, tmB, p, grid, s);
   if (in_fp8) return staged ? launch_pair_io<true, true>(out_fp8, tmA, tmB, p, grid, s)
                             : launch_pair_io<true, false>(out_fp8, tmA, tmB, p, grid, s);
   return staged ? launch_pair_io<false, true>(out_fp8, tmA, tmB, p, grid, s)

@@ -102,6 +102,9 @@ ddf_status ensure_train(ddf_s* h, int64_t B) {
     h->tr_pair = W % 256 == 0 && h->pair_clusters > 0;
     h->tmBpair.assign(H, CUtensorMap{});
     h->tmWTpair.assign(H, CUtensorMap{});
+    if (h->tr_pair &&
+        !make_tmap(&h->tmBpair[0], h->wb[0], false, h->kp16, W, static_cast<uint64_t>(h->kp16) * 2, 128))
+      return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for a weight map");
     for (int l = 1; l < H; ++l) {
       if ((s = train_alloc(h, &p, static_cast<size_t>(W) * W * 2)) != DDF_OK) return s;
       h->wt[l] = static_cast<__nv_bfloat16*>(p);
@@ -133,6 +136,10 @@ ddf_status ensure_train(ddf_s* h, int64_t B) {
     dev_free(h, h->tr_z);
     dev_free(h, h->tr_dz);
     dev_free(h, h->tr_lpart);
+    dev_free(h, h->tr_colpart);
+    h->tr_colpart = nullptr;
+    for (uint32_t* q : h->tr_bits) dev_free(h, q);
+    h->tr_bits.assign(H > 1 ? H - 1 : 0, nullptr);
     h->tr_h.assign(H, nullptr);
     h->tr_rows = 0;
     const size_t act = static_cast<size_t>(B) * W * 2;
@@ -147,6 +154,16 @@ ddf_status ensure_train(ddf_s* h, int64_t B) {
     h->tr_dz = static_cast<float2*>(p);
     if ((s = train_alloc(h, &p, ((B + 255) / 256) * sizeof(float))) != DDF_OK) return s;
     h->tr_lpart = static_cast<float*>(p);
+    if ((s = train_alloc(h, &p, static_cast<size_t>(round_up(B, 256) / 32) * W * sizeof(float))) !=
+        DDF_OK)
+      return s;
+    h->tr_colpart = static_cast<float*>(p);
+    if (h->tr_pair)
+      for (auto& q : h->tr_bits) {
+        if ((s = train_alloc(h, &p, static_cast<size_t>(B) * (W / 32) * sizeof(uint32_t))) != DDF_OK)
+          return s;
+        q = static_cast<uint32_t*>(p);
+      }
     h->tr_rows = B;
   }
   return DDF_OK;
@@ -231,10 +248,14 @@ ddf_status forward_keep(ddf_s* h, const float* const rays[6], int B, cudaStream_
     p.ldo = W;
     p.mode = 0;
     ProfScope ps(h, l == 0 ? kProfFirst : kProfGemm, st);
-    ddf_status s = l > 0 && h->tr_pair
-                       ? tc_gemm_pair(h, h->tr_h[l - 1], B, W, h->tmBpair[l], true, p, st)
-                       : tc_gemm(h, l == 0 ? h->tr_enc : h->tr_h[l - 1], B, l == 0 ? h->kp16 : W,
-                                 h->tmBtr[l], h->bn, p, st);
+    const void* A_in = l == 0 ? h->tr_enc : h->tr_h[l - 1];
+    const int K = l == 0 ? h->kp16 : W;
+    if (h->tr_pair && l < H - 1) {  // the input gradients will test this layer's ReLU pattern
+      p.relu_bits = h->tr_bits[l];
+      p.ldb = W / 32;
+    }
+    ddf_status s = h->tr_pair ? tc_gemm_pair(h, A_in, B, K, h->tmBpair[l], true, p, st)
+                              : tc_gemm(h, A_in, B, K, h->tmBtr[l], h->bn, p, st);
     if (s != DDF_OK) return s;
   }
   DDF_CK(ddf::launch_head_train(bf(h->tr_h[H - 1]), B, W, h->head_w, h->head_b, h->tr_z, st));
@@ -317,7 +338,14 @@ ddf_status backward_from_dz(ddf_s* h, int B, cudaStream_t st) {
     }
     DDF_CK(ddf::launch_splitk_reduce(h->tr_part, splits, W, N, static_cast<int64_t>(W) * N, K,
                                      h->grad + o.w[l], K, st));
-    DDF_CK(ddf::launch_colsum_bf16(bf(h->tr_dpre[cur]), B, W, W, kColSplits, h->tr_cpart, st));
+    // bias gradient: column sums of dpre_l, from the 32-row partials the
+    // pair kernel's input-gradient epilogue left (below, one layer up), or
+    // read from dpre_l itself (the top layer, or without the pair kernel)
+    const int nblk = static_cast<int>(round_up(B, 256) / 32);
+    if (h->tr_pair && l < H - 1)
+      DDF_CK(ddf::launch_colsum_f32(h->tr_colpart, nblk, W, W, kColSplits, h->tr_cpart, st));
+    else
+      DDF_CK(ddf::launch_colsum_bf16(bf(h->tr_dpre[cur]), B, W, W, kColSplits, h->tr_cpart, st));
     DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart, kColSplits, 1, W, W, W, h->grad + o.b[l], W, st));
     if (l == 0) break;
     // dpre_{l-1} [B x W] = (dpre_l [B x W]) (W_l^T [W x W])^T masked by h_{l-1} > 0
@@ -328,6 +356,11 @@ ddf_status backward_from_dz(ddf_s* h, int B, cudaStream_t st) {
     q.ldo = W;
     q.mask = h->tr_h[l - 1];
     q.ldm = W;
+    if (h->tr_pair) {
+      q.relu_bits = h->tr_bits[l - 1];
+      q.ldb = W / 32;
+      q.col_part = h->tr_colpart;
+    }
     {
       ProfScope ps(h, kProfGemm, st);
       ddf_status s = h->tr_pair ? tc_gemm_pair(h, h->tr_dpre[cur], B, W, h->tmWTpair[l], false, q, st)
