@@ -205,11 +205,12 @@ cudaError_t launch_head_train(const __nv_bfloat16* H, int M, int W, const float*
 cudaError_t launch_loss(const float2* z, const float* t_tgt, const uint8_t* y, int64_t B,
                         unsigned* nhit, float clamp, float lam, float2* dz, float* part,
                         float* loss_out, cudaStream_t s);
-cudaError_t launch_head_backward(const float2* dz, const __nv_bfloat16* H, int M, int W,
-                                 const float* wo, __nv_bfloat16* dpre, cudaStream_t s);
-// part [splits x 2 x W]: row-split partials of dz^T H
-cudaError_t launch_head_grad(const float2* dz, const __nv_bfloat16* H, int M, int W, int splits,
-                             float* part, cudaStream_t s);
+// One pass over H [M x W]: dpre = bf16((dz wo) where H > 0), and per split
+// of rows part [splits x 3 x W]: partials of dz0 H, dz1 H and of dpre's
+// column sums.
+cudaError_t launch_head_back_fused(const float2* dz, const __nv_bfloat16* H, int M, int W,
+                                  const float* wo, int splits, __nv_bfloat16* dpre, float* part,
+                                  cudaStream_t s);
 // part [splits x N]: row-split partial column sums
 cudaError_t launch_colsum_bf16(const __nv_bfloat16* X, int M, int N, int ld, int splits,
                                float* part, cudaStream_t s);

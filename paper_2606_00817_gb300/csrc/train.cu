@@ -126,43 +126,56 @@ __global__ void sum_partials_kernel(const float* __restrict__ part, int n, float
   }
 }
 
-// dpre = bf16((dz0 wo[0] + dz1 wo[1]) where h > 0), 8 columns per thread.
-__global__ void head_backward_kernel(const float2* __restrict__ dz, const __nv_bfloat16* __restrict__ H,
-                                     int M, int W, const float* __restrict__ wo,
-                                     __nv_bfloat16* __restrict__ dpre) {
-  const int per_row = W / 8;
-  const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= static_cast<int64_t>(M) * per_row) return;
-  const int64_t row = idx / per_row;
-  const int c = static_cast<int>(idx - row * per_row) * 8;
-  const float2 d = dz[row];
-  const uint4 hv = *reinterpret_cast<const uint4*>(H + row * W + c);
-  const __nv_bfloat16* hb = reinterpret_cast<const __nv_bfloat16*>(&hv);
-  __align__(16) __nv_bfloat16 out[8];
+// The head's backward in one pass over the last activation H [M x W] (bf16):
+// per row r, dpre = bf16((dz0 wo[0] + dz1 wo[1]) where H > 0); per split s of
+// rows (one block; thread t owns columns 8t .. 8t + 7) the partial sums
+// part[s][0][k] = sum dz0 H[r][k], part[s][1][k] = sum dz1 H[r][k] (the head
+// weights' gradient) and part[s][2][k] = sum dpre[r][k] (the last layer's
+// bias gradient), in row order.
+__global__ void head_back_fused_kernel(const float2* __restrict__ dz, const __nv_bfloat16* __restrict__ H,
+                                       int M, int W, const float* __restrict__ wo, int rows_per_split,
+                                       __nv_bfloat16* __restrict__ dpre, float* __restrict__ part) {
+  const int c = 8 * threadIdx.x;
+  if (c >= W) return;
+  const int s = blockIdx.x;
+  const int r0 = s * rows_per_split, r1 = min(M, r0 + rows_per_split);
+  float w0[8], w1[8], g0[8], g1[8], cs[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    const float g = d.x * wo[c + j] + d.y * wo[W + c + j];
-    out[j] = __float2bfloat16_rn(__bfloat162float(hb[j]) > 0.f ? g : 0.f);
+    w0[j] = wo[c + j];
+    w1[j] = wo[W + c + j];
+    g0[j] = g1[j] = cs[j] = 0.f;
   }
-  *reinterpret_cast<uint4*>(dpre + row * W + c) = *reinterpret_cast<const uint4*>(out);
-}
-
-// part[s][0][k] = sum over rows of split s of dz0 * H[r][k], part[s][1][k] of dz1 * H.
-__global__ void head_grad_kernel(const float2* __restrict__ dz, const __nv_bfloat16* __restrict__ H,
-                                 int M, int W, int rows_per_split, float* __restrict__ part) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = blockIdx.y;
-  if (k >= W) return;
-  const int r0 = s * rows_per_split, r1 = min(M, r0 + rows_per_split);
-  float a0 = 0.f, a1 = 0.f;
+#pragma unroll 4
   for (int r = r0; r < r1; ++r) {
-    const float x = __bfloat162float(H[static_cast<int64_t>(r) * W + k]);
     const float2 d = dz[r];
-    a0 = fmaf(d.x, x, a0);
-    a1 = fmaf(d.y, x, a1);
+    const uint4 hv = *reinterpret_cast<const uint4*>(H + static_cast<int64_t>(r) * W + c);
+    const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+    uint32_t ow[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float h0 = __uint_as_float(hw[q] << 16), h1 = __uint_as_float(hw[q] & 0xFFFF0000u);
+      const int j = 2 * q;
+      const float x0 = h0 > 0.f ? d.x * w0[j] + d.y * w1[j] : 0.f;
+      const float x1 = h1 > 0.f ? d.x * w0[j + 1] + d.y * w1[j + 1] : 0.f;
+      const __nv_bfloat162 o = __floats2bfloat162_rn(x0, x1);
+      ow[q] = *reinterpret_cast<const uint32_t*>(&o);
+      cs[j] += __low2float(o);
+      cs[j + 1] += __high2float(o);
+      g0[j] = fmaf(d.x, h0, g0[j]);
+      g1[j] = fmaf(d.y, h0, g1[j]);
+      g0[j + 1] = fmaf(d.x, h1, g0[j + 1]);
+      g1[j + 1] = fmaf(d.y, h1, g1[j + 1]);
+    }
+    *reinterpret_cast<uint4*>(dpre + static_cast<int64_t>(r) * W + c) = make_uint4(ow[0], ow[1], ow[2], ow[3]);
   }
-  part[(static_cast<size_t>(s) * 2 + 0) * W + k] = a0;
-  part[(static_cast<size_t>(s) * 2 + 1) * W + k] = a1;
+  float* ps = part + static_cast<size_t>(s) * 3 * W + c;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    ps[j] = g0[j];
+    ps[W + j] = g1[j];
+    ps[2 * W + j] = cs[j];
+  }
 }
 
 // part[s][k] = sum over rows of split s of X[r][k] (bf16 or FP32 input).
@@ -268,17 +281,13 @@ cudaError_t launch_sdf_loss(const float2* z, const float* s_tgt, int64_t B, floa
   return cudaGetLastError();
 }
 
-cudaError_t launch_head_backward(const float2* dz, const __nv_bfloat16* H, int M, int W,
-                                 const float* wo, __nv_bfloat16* dpre, cudaStream_t s) {
-  const int64_t total = static_cast<int64_t>(M) * (W / 8);
-  head_backward_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(dz, H, M, W, wo, dpre);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_head_grad(const float2* dz, const __nv_bfloat16* H, int M, int W, int splits,
-                             float* part, cudaStream_t s) {
+cudaError_t launch_head_back_fused(const float2* dz, const __nv_bfloat16* H, int M, int W,
+                                  const float* wo, int splits, __nv_bfloat16* dpre, float* part,
+                                  cudaStream_t s) {
+  if (W % 8 != 0 || W / 8 > 1024) return cudaErrorInvalidValue;
   const int rps = (M + splits - 1) / splits;
-  head_grad_kernel<<<dim3((W + 255) / 256, splits), 256, 0, s>>>(dz, H, M, W, rps, part);
+  const int threads = ((W / 8 + 31) / 32) * 32;
+  head_back_fused_kernel<<<splits, threads, 0, s>>>(dz, H, M, W, wo, rps, dpre, part);
   return cudaGetLastError();
 }
 

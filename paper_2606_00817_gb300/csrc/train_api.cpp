@@ -23,6 +23,7 @@ namespace {
 
 constexpr int kColSplits = 64;   // row splits of the column sums
 constexpr int kPartSplits = 16;  // most batch splits of a weight-gradient GEMM
+constexpr int kHeadSplits = 512; // row splits of the head's fused backward
 constexpr float kClamp = kLossClamp;
 constexpr float kLambda = kLossLambda;
 constexpr float kB1 = kAdamB1, kB2 = kAdamB2, kEps = kAdamEps;
@@ -119,9 +120,12 @@ ddf_status ensure_train(ddf_s* h, int64_t B) {
     if ((s = train_alloc(h, &p, kPartSplits * static_cast<size_t>(W) * nmax * sizeof(float))) != DDF_OK)
       return s;
     h->tr_part = static_cast<float*>(p);
-    if ((s = train_alloc(h, &p, kColSplits * 2 * static_cast<size_t>(W) * sizeof(float))) != DDF_OK)
+    if ((s = train_alloc(h, &p, kColSplits * 3 * static_cast<size_t>(W) * sizeof(float))) != DDF_OK)
       return s;
     h->tr_cpart = static_cast<float*>(p);
+    if ((s = train_alloc(h, &p, kHeadSplits * 3 * static_cast<size_t>(W) * sizeof(float))) != DDF_OK)
+      return s;
+    h->tr_hpart = static_cast<float*>(p);
     if ((s = train_alloc(h, &p, sizeof(unsigned))) != DDF_OK) return s;
     h->tr_nhit = static_cast<unsigned*>(p);
     if ((s = refresh_weights(h, nullptr)) != DDF_OK) return s;
@@ -271,13 +275,18 @@ ddf_status backward_from_dz(ddf_s* h, int B, cudaStream_t st) {
   auto bf = [](void* q) { return static_cast<__nv_bfloat16*>(q); };
 
   // ---- head: dW_o = dz^T h_H, db_o = sum dz, dpre_H = (dz W_o) where h_H > 0
-  DDF_CK(ddf::launch_head_grad(h->tr_dz, bf(h->tr_h[H - 1]), B, W, kColSplits, h->tr_cpart, st));
-  DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart, kColSplits, hr, W, 2 * W, W, h->grad + o.wo, W, st));
+  // and its column sums (the last layer's bias gradient), in one pass over
+  // h_H; the row-split partials reduce in two deterministic steps
+  const int hsplits = std::max(1, std::min(kHeadSplits, B / 64));
+  DDF_CK(ddf::launch_head_back_fused(h->tr_dz, bf(h->tr_h[H - 1]), B, W, h->head_w, hsplits,
+                                     bf(h->tr_dpre[0]), h->tr_hpart, st));
+  DDF_CK(ddf::launch_colsum_f32(h->tr_hpart, hsplits, 3 * W, 3 * W, kColSplits, h->tr_cpart, st));
+  DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart, kColSplits, hr, W, 3 * W, W, h->grad + o.wo, W, st));
+  DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart + 2 * W, kColSplits, 1, W, 3 * W, W,
+                                   h->grad + o.b[H - 1], W, st));
   DDF_CK(ddf::launch_colsum_f32(reinterpret_cast<const float*>(h->tr_dz), B, 2, 2, kColSplits,
                                 h->tr_cpart, st));
   DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart, kColSplits, 1, 2, 2, hr, h->grad + o.bo, hr, st));
-  DDF_CK(ddf::launch_head_backward(h->tr_dz, bf(h->tr_h[H - 1]), B, W, h->head_w,
-                                   bf(h->tr_dpre[0]), st));
 
   // ---- layers, last to first
   int cur = 0;
@@ -341,12 +350,15 @@ ddf_status backward_from_dz(ddf_s* h, int B, cudaStream_t st) {
     // bias gradient: column sums of dpre_l, from the 32-row partials the
     // pair kernel's input-gradient epilogue left (below, one layer up), or
     // read from dpre_l itself (the top layer, or without the pair kernel)
+    // (the top layer's came with the head's backward)
     const int nblk = static_cast<int>(round_up(B, 256) / 32);
-    if (h->tr_pair && l < H - 1)
-      DDF_CK(ddf::launch_colsum_f32(h->tr_colpart, nblk, W, W, kColSplits, h->tr_cpart, st));
-    else
-      DDF_CK(ddf::launch_colsum_bf16(bf(h->tr_dpre[cur]), B, W, W, kColSplits, h->tr_cpart, st));
-    DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart, kColSplits, 1, W, W, W, h->grad + o.b[l], W, st));
+    if (l < H - 1) {
+      if (h->tr_pair)
+        DDF_CK(ddf::launch_colsum_f32(h->tr_colpart, nblk, W, W, kColSplits, h->tr_cpart, st));
+      else
+        DDF_CK(ddf::launch_colsum_bf16(bf(h->tr_dpre[cur]), B, W, W, kColSplits, h->tr_cpart, st));
+      DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart, kColSplits, 1, W, W, W, h->grad + o.b[l], W, st));
+    }
     if (l == 0) break;
     // dpre_{l-1} [B x W] = (dpre_l [B x W]) (W_l^T [W x W])^T masked by h_{l-1} > 0
     ddf::TcGemmParams q{};
