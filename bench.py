@@ -78,6 +78,8 @@ def parse():
                     help="skip the AO / distillation / sphere-tracing / hash-grid measurements")
     ap.add_argument("--workloads", default="ao,train,trace,hashgrid,gs",
                     help="comma list of the secondary measurements to run")
+    ap.add_argument("--hg-steps", type=int, default=3000,
+                    help="distillation steps of the hash-grid workload")
     ap.add_argument("--gs-config", default="1024,128,30000,0.02",
                     help="supervision study: training views, image size, steps, Gaussian sigma")
     return ap.parse_args()
@@ -238,7 +240,7 @@ def hashgrid_mlp_dims(ddf):
     return [(64, ddf.HASHGRID_CODE), (64, 64), (2, 64)]
 
 
-def hashgrid_workload(torch, ddf, dev, local, stream, flush, d_rays, R):
+def hashgrid_workload(torch, ddf, dev, local, stream, flush, d_rays, R, steps=3000):
     """The paper's final field (Sec. 3.4): hash grid (16 levels x 2 features,
     2^19 entries, base 16, growth 1.5) + 4-band direction code + 59 -> 64 ->
     64 -> 2 MLP, on the benchmark's shadow rays, bf16 and FP32."""
@@ -266,7 +268,7 @@ def hashgrid_workload(torch, ddf, dev, local, stream, flush, d_rays, R):
     sph, ns, box, nb = _scene_buffers(torch, dev, tscene)
     m = ddf.DDF(4, 64, 2, precision="bf16", device=local, kind="hashgrid")
     m.load(I.hashgrid_blob(n, mlp_dims, seed=0, table_scale=1e-4))
-    steps, batch = 3000, 16384
+    batch = 16384
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     losses = ddf.ddf_distill(m.h, sph, ns, box, nb, steps, batch, 3e-3, 0.5, 0.3, seed=1,
@@ -795,7 +797,8 @@ def main():
         which = set(args.workloads.split(","))
         extra = workloads(torch, ddf, dev, local, stream, flush, blob, which)
         if "hashgrid" in which:
-            extra["hashgrid"] = hashgrid_workload(torch, ddf, dev, local, stream, flush, d_rays, R)
+            extra["hashgrid"] = hashgrid_workload(torch, ddf, dev, local, stream, flush, d_rays, R,
+                                                  steps=args.hg_steps)
         if "gs" in which:
             gv, gw, gsteps, gsig = args.gs_config.split(",")
             extra["gs_supervision"] = gs_workload(torch, ddf, dev, local, stream, V=int(gv),
