@@ -92,6 +92,29 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_rays(R, rank):
+    """This rank's shard: its own R shadow rays of the 64-sphere scene (seed =
+    rank), so N ranks evaluate N disjoint sets of the same distribution."""
+    scene = I.random_scene(64, 0, seed=0)
+    return I.shadow_rays(scene, R, LIGHT, seed=rank)
+
+
+def max_over_ranks(x, ws, device):
+    """x maximised over all ranks by one all-reduce (x itself when ws = 1)."""
+    if ws == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_rate(units_per_rank, ws, steps, seconds):
+    """Units all ranks processed per second of the slowest rank's time."""
+    return units_per_rank * ws * steps / seconds
+
+
 def cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -617,8 +640,7 @@ def main():
 
     R = args.rays
     blob = I.xavier_blob(I.NetShape(*NET))
-    scene = I.random_scene(64, 0, seed=0)
-    rays = I.shadow_rays(scene, R, LIGHT, seed=rank)
+    rays = rank_rays(R, rank)
     d_rays = [torch.from_numpy(a).to(dev) for a in rays.soa()]
     t = torch.empty(R, dtype=torch.float32, device=dev)
     vis = torch.empty_like(t)
@@ -675,13 +697,10 @@ def main():
     prof = ddf.ddf_profile_read(m.h)
     ddf.ddf_profile_enable(m.h, False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
+    total_ms = max_over_ranks(sum(step_ms), ws, dev)
     if ws > 1:
-        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
         dist.barrier()
-    value = R * ws * args.steps / (total_ms / 1e3)
+    value = whole_job_rate(R, ws, args.steps, total_ms / 1e3)
     status = ddf.ddf_check_status(m.h)
 
     # roofline of the dominant kernel: the tensor-core GEMM of the hidden
@@ -736,12 +755,8 @@ def main():
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         ddf.ddf_query_shadow_host(m.h, h_rays, R, LIGHT, h_t, h_v, h_o)
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = {"value": R * ws * e2e_steps / e2e_s, "unit": "rays/s",
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws, dev)
+    e2e = {"value": whole_job_rate(R, ws, e2e_steps, e2e_s), "unit": "rays/s",
            "h2d_bytes_per_step": 24 * R, "d2h_bytes_per_step": 9 * R,
            "api": "ddf_query_shadow_host (pinned host buffers, copies overlapped with compute)"}
 
