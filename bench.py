@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--oracle-seconds", type=float, default=12.0)
     ap.add_argument("--tile", default="auto", help="auto (autotune), or BNxEPI[pair][staged|fused] for every layer, or "
                          "HIDDEN,FIRST, e.g. 256x4pairstaged,256x4fused")
+    ap.add_argument("--fp8-tile", default="auto",
+                    help="tiles of the e4m3 comparison run: auto (autotune) or as --tile")
     ap.add_argument("--no-workloads", action="store_true",
                     help="skip the AO / distillation / sphere-tracing / hash-grid measurements")
     ap.add_argument("--workloads", default="ao,train,trace,hashgrid,gs",
@@ -90,6 +92,16 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def set_tiles(ddf, h, spec_str):
+    """Tiles from "HIDDEN[,FIRST]", each BNxEPI[pair][staged|fused]."""
+    specs = spec_str.split(",")
+    for which in (0, 1):
+        spec = specs[min(which, len(specs) - 1)]
+        t4 = (256 if spec.startswith("256") else 128, 8 if "x8" in spec else 4,
+              int("pair" in spec), int("staged" in spec or "fused" in spec), int("fused" in spec))
+        ddf.ddf_set_tile(h, t4, which)
 
 
 def rank_rays(R, rank):
@@ -661,13 +673,7 @@ def main():
         tune_ms = {"all_layers": {fmt(k): v for k, v in p1.items()},
                    "first_layer": {fmt(k): v for k, v in p2.items()}}
     else:
-        specs = args.tile.split(",")
-        for which in (0, 1):
-            spec = specs[min(which, len(specs) - 1)]
-            t4 = (256 if spec.startswith("256") else 128, 8 if "x8" in spec else 4,
-                  int("pair" in spec), int("staged" in spec or "fused" in spec),
-                  int("fused" in spec))
-            ddf.ddf_set_tile(m.h, t4, which)
+        set_tiles(ddf, m.h, args.tile)
     tile = {"hidden": fmt(ddf.ddf_get_tile(m.h, 0)), "first": fmt(ddf.ddf_get_tile(m.h, 1))}
 
     def step():
@@ -785,19 +791,36 @@ def main():
         f8.load(blob)
         nc = min(R, 65536)
         _, f8_scales = ddf.ddf_calibrate_fp8(f8.h, [r[:nc] for r in d_rays], nc, stream)
-        nt = min(R, 1 << 20)
-        ddf.ddf_autotune(f8.h, [r[:nt] for r in d_rays], nt, stream)
+        if args.fp8_tile == "auto":
+            nt = min(R, 1 << 20)
+            ddf.ddf_autotune(f8.h, [r[:nt] for r in d_rays], nt, stream)
+        else:
+            set_tiles(ddf, f8.h, args.fp8_tile)
         t8, v8 = torch.empty_like(t), torch.empty_like(t)
         o8 = torch.empty_like(occ)
         for _ in range(2):
             ddf.ddf_query_shadow(f8.h, d_rays, R, LIGHT, t8, v8, o8, stream)
         torch.cuda.synchronize()
+        ddf.ddf_profile_enable(f8.h, True)
+        ddf.ddf_profile_read(f8.h)
         a.record(stream)
         for _ in range(3):
             ddf.ddf_query_shadow(f8.h, d_rays, R, LIGHT, t8, v8, o8, stream)
         b.record(stream)
         torch.cuda.synchronize()
         f8_ms = a.elapsed_time(b) / 3
+        p8 = ddf.ddf_profile_read(f8.h)
+        ddf.ddf_profile_enable(f8.h, False)
+        # the e4m3 hidden-layer GEMMs against the e4m3 dense peak: the measured
+        # sustained bf16 peak times the nominal e4m3 / bf16 ratio (2)
+        g8_ms = p8["gemm"][0]
+        f8_ach = gemm_flops_step * 3 / (g8_ms / 1e3) / 1e12 if g8_ms > 0 else None
+        f8_peak = 2.0 * peak
+        compare["fp8_roofline"] = {
+            "bound": "tensor", "achieved": f8_ach, "peak": f8_peak, "unit": "TFLOP/s",
+            "frac": f8_ach / f8_peak if f8_ach else None,
+            "peak_source": "2 x " + peak_src, "gemm_ms_per_step": g8_ms / 3,
+            "kernel_time_share": g8_ms / sum(v[0] for v in p8.values()) if g8_ms > 0 else None}
         compare.update({"fp8_rays_per_s": R / (f8_ms / 1e3), "fp8_ms_per_step": f8_ms,
                         "fp8_speedup_vs_fp32": f32_ms / f8_ms,
                         "fp8_act_scales": [float(x) for x in f8_scales],

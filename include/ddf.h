@@ -443,7 +443,7 @@ ddf_status ddf_set_chunk_rays(ddf_handle h, int64_t chunk);
  *   epi_warps  epilogue warps draining the TMEM accumulator: 4, or 8 (two per
  *              TMEM lane quarter, each draining half the columns)
  *   cta_pair   1: the 256 x 256 tile a cluster of two CTAs computes with one
- *              pair MMA (needs bn 256, epi_warps 4)
+ *              pair MMA (needs bn 256)
  *   staged     1: activations leave through shared memory as whole 128-byte
  *              lines instead of per-thread 16-byte pieces (pair tile, or the
  *              fused layer-1 tile)
@@ -470,20 +470,20 @@ typedef struct {
 ddf_status ddf_set_tile(ddf_handle h, int32_t which, const ddf_tile* tile);
 ddf_status ddf_get_tile(ddf_handle h, int32_t which, ddf_tile* tile);
 
-/* Autotuner over the 8 candidate tiles {256,4,0,0,0}, {256,8,0,0,0},
+/* Autotuner over the 9 candidate tiles {256,4,0,0,0}, {256,8,0,0,0},
  * {128,4,0,0,0}, {128,8,0,0,0}, {256,4,1,0,0}, {256,4,1,1,0},
- * {256,4,0,1,1}, {256,8,0,1,1} on n rays (device SoA, 1 <= n <= 2^24) on
- * stream. Phase 1 uses one of the first 6 for every layer and keeps the
- * fastest for layers 2..H; phase 2 keeps that and tries all 8 for layer 1
- * (the last two fuse the encoding into it). Every configuration must give t
+ * {256,8,1,1,0}, {256,4,0,1,1}, {256,8,0,1,1} on n rays (device SoA,
+ * 1 <= n <= 2^24) on stream. Phase 1 uses one of the first 7 for every layer
+ * and keeps the fastest for layers 2..H; phase 2 keeps that and tries all 9
+ * for layer 1 (the last two fuse the encoding into it). Every configuration must give t
  * and vis within 1e-3 (relative to max(1, |ref|)) of the first configuration
  * tried before it is timed. The passing candidates are then timed round-robin
  * over 3 rounds, one query each, and keep their best round (so a clock that
  * drifts under the power cap affects all alike): phase 1 times every launch
  * of the query, phase 2 the encoding and layer-1 launches only (CUDA events
  * around each launch). ms_out (nullable,
- * n_out >= 16) receives the per-query ms of phase 1 in [0..7] (6, 7 unused)
- * and of phase 2 in [8..15], -1 where a candidate was skipped or rejected.
+ * n_out >= 18) receives the per-query ms of phase 1 in [0..8] (7, 8 unused)
+ * and of phase 2 in [9..17], -1 where a candidate was skipped or rejected.
  * Synchronous; allocates 16 n bytes of device memory while it runs. A no-op
  * on FP32 handles. */
 ddf_status ddf_autotune(ddf_handle h, const float* const rays[6], int64_t n, void* stream,

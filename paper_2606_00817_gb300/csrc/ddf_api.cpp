@@ -269,7 +269,8 @@ ddf_status forward_tc(ddf_s* h, ddf::RaySoA rays, int m, ddf::HeadOut out, cudaS
     if (t.pair) {
       const int64_t tiles = ((m + 255) / 256) * static_cast<int64_t>(W / 256);
       const int clusters = static_cast<int>(std::min<int64_t>(tiles, h->pair_clusters));
-      DDF_CK(ddf::launch_tc_gemm_pair(in_fp8, out_fp8, t.staged, tmA, h->tmB[l], p, clusters, st));
+      DDF_CK(ddf::launch_tc_gemm_pair(in_fp8, out_fp8, t.staged, t.epi_warps, tmA, h->tmB[l], p,
+                                      clusters, st));
     } else {
       const int64_t tiles = ((m + 127) / 128) * static_cast<int64_t>(W / t.bn);
       const int grid = static_cast<int>(std::min<int64_t>(tiles, h->num_sms));
@@ -278,7 +279,7 @@ ddf_status forward_tc(ddf_s* h, ddf::RaySoA rays, int m, ddf::HeadOut out, cudaS
   }
   ProfScope ps(h, kProfHead, st);
   const ddf::TcTile& tl = H == 1 ? h->tile_first : h->tile;  // the last layer writes the partials
-  const int nparts = tl.pair ? W / 256 : (W / tl.bn) * (tl.epi_warps / 4);
+  const int nparts = (tl.pair ? W / 256 : W / tl.bn) * (tl.epi_warps / 4);
   DDF_CK(ddf::launch_finish_heads(h->ws_part, nparts, m, h->head_b, out, st));
   return DDF_OK;
 }
@@ -1093,8 +1094,8 @@ ddf_status ddf_set_tile(ddf_handle h, int32_t which, const ddf_tile* tile) {
   if ((bn != 128 && bn != 256) || (ew != 4 && ew != 8))
     return fail(DDF_ERR_INVALID_ARG, "bn must be 128 or 256 and epi_warps 4 or 8");
   if (h->cfg.width % bn != 0) return fail(DDF_ERR_UNSUPPORTED, "width is not a multiple of bn");
-  if (tile->cta_pair != 0 && (bn != 256 || ew != 4))
-    return fail(DDF_ERR_INVALID_ARG, "the CTA-pair tile is bn 256 with 4 epilogue warps");
+  if (tile->cta_pair != 0 && bn != 256)
+    return fail(DDF_ERR_INVALID_ARG, "the CTA-pair tile is bn 256");
   if (tile->fused_encode != 0) {
     if (which != 1) return fail(DDF_ERR_INVALID_ARG, "fused_encode is a layer-1 tile (which = 1)");
     if (bn != 256 || tile->cta_pair != 0 || tile->staged == 0)
@@ -1136,12 +1137,12 @@ ddf_status ddf_get_tile(ddf_handle h, int32_t which, ddf_tile* tile) {
 namespace ddfi {
 
 // the last kFusedCands candidates are layer-1 only (phase 2)
-constexpr int kTileCands = 8;
+constexpr int kTileCands = 9;
 constexpr int kFusedCands = 2;
 constexpr int kMsSlots = 2 * kTileCands;
 const ddf_tile kCands[kTileCands] = {{256, 4, 0, 0, 0}, {256, 8, 0, 0, 0}, {128, 4, 0, 0, 0},
                                      {128, 8, 0, 0, 0}, {256, 4, 1, 0, 0}, {256, 4, 1, 1, 0},
-                                     {256, 4, 0, 1, 1}, {256, 8, 0, 1, 1}};
+                                     {256, 8, 1, 1, 0}, {256, 4, 0, 1, 1}, {256, 8, 0, 1, 1}};
 
 bool cand_ok(ddf_s* h, const ddf_tile& c) {
   if (c.fused_encode != 0)

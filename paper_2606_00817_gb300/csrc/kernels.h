@@ -117,11 +117,12 @@ cudaError_t launch_tc_gemm(const TcTile& tile, bool in_fp8, bool out_fp8, const 
 int tc_gemm_smem_bytes(int bn, bool in_fp8);
 
 // CTA-pair variant: clusters of 2 CTAs, 256 x 256 output tiles, persistent
-// over `clusters` clusters. Mode 1 writes N/256 partials per row; modes 2
+// over `clusters` clusters, 4 or 8 epilogue warps per CTA (training modes:
+// 4). Mode 1 writes (N/256) (epi_warps/4) partials per row; modes 2
 // and 3 (bf16) as the 1-CTA kernel, mode 3 with K-major or MN-major operands.
-cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, bool staged, const CUtensorMap& tmA,
-                                const CUtensorMap& tmB, const TcGemmParams& p, int clusters,
-                                cudaStream_t s);
+cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, bool staged, int epi_warps,
+                                const CUtensorMap& tmA, const CUtensorMap& tmB,
+                                const TcGemmParams& p, int clusters, cudaStream_t s);
 // Clusters of the pair kernel that fit on the current device at once.
 int tc_gemm_pair_max_clusters(bool in_fp8);
 

@@ -38,8 +38,10 @@ namespace {
 constexpr uint64_t kPairDrainNs = 1000000000ull;
 
 // STAGED: mode-0 outputs go through per-warp shared staging buffers
-// (epi_row_staged); one pipeline stage fewer leaves room for them.
-template <bool IN_FP8, bool STAGED>
+// (epi_row_staged); one pipeline stage fewer leaves room for them. EPI:
+// epilogue warps per CTA, 4 (one per TMEM lane quarter) or 8 (two per
+// quarter, each draining half of the tile's columns).
+template <bool IN_FP8, bool STAGED, int EPI = 4>
 struct PairShape {
   static constexpr int BM = 256;                 // output rows per pair tile
   static constexpr int BN = 256;                 // output columns per pair tile
@@ -50,7 +52,8 @@ struct PairShape {
   static constexpr int B_BYTES = HALF * ROW_BYTES;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;  // per CTA
   static constexpr int STAGES = STAGED ? 5 : 6;
-  static constexpr int OUT_STAGE_BYTES = STAGED ? 4 * kStageBytesPerWarp : 0;
+  static constexpr int OUT_STAGE_BYTES = STAGED ? EPI * kStageBytesPerWarp : 0;
+  static constexpr int THREADS = 64 + 32 * EPI;
   static constexpr int TMEM_COLS = 512;
   static constexpr int NUM_BARS = 2 * STAGES + 5;
   static constexpr int CTRL_BYTES = 256;  // barriers, TMEM slot, abort flag, issue counts
@@ -63,11 +66,11 @@ struct PairShape {
 // TRAIN: the training modes (2, 3: masked input gradients, split-K weight
 // gradients with K-major or MN-major operands), bf16 only; the query
 // instantiations compile none of it.
-template <bool IN_FP8, bool OUT_FP8, bool STAGED, bool TRAIN>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
+template <bool IN_FP8, bool OUT_FP8, bool STAGED, bool TRAIN, int EPI = 4>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * EPI, 1)
     tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                         const __grid_constant__ CUtensorMap tmB, const TcGemmParams p) {
-  using S = PairShape<IN_FP8, STAGED>;
+  using S = PairShape<IN_FP8, STAGED, EPI>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -97,7 +100,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull_bar(b), 1);
-      mbar_init(tempty_bar(b), 8);  // 4 epilogue warps in each CTA
+      mbar_init(tempty_bar(b), 2 * EPI);  // every epilogue warp of both CTAs
     }
     mbar_init(mdone_bar, 1);
     *abort_flag = 0;
@@ -237,7 +240,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
     mbar_wait_bounded(mdone_bar, 0, nullptr, kPairDrainNs);
   } else if (warp >= 2) {
     // ---------------------------------------------------------- epilogue (both CTAs)
-    const int q = warp & 3;
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int half = EPI == 4 ? 0 : (warp - 2) / 4;
+    constexpr int kChunks = S::BN / 32 / (EPI / 4);  // 32-column chunks per warp
+    const int c0 = half * kChunks, c1 = c0 + kChunks;
+    uint8_t* const stage_w = smem + S::VEC_OFFSET + epi_vector_bytes(p.N) + (warp - 2) * kStageBytesPerWarp;
     const int r_local = q * 32 + lane;
     const uint32_t tempty_leader0 = map_to_cta(tempty_bar(0), 0);
     int local = 0;
@@ -260,24 +267,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
                              static_cast<uint32_t>(b * S::BN);
       float h0 = 0.f, h1 = 0.f;
       if constexpr (TRAIN) {
-        uint8_t* stage = smem + S::VEC_OFFSET + epi_vector_bytes(p.N) + q * kStageBytesPerWarp;
         if (p.mode == 0)
-          epi_row_staged_bits(p, ev, tbase, row - lane, n0, 0, S::BN / 32, stage, lane);
+          epi_row_staged_bits(p, ev, tbase, row - lane, n0, c0, c1, stage_w, lane);
         else if (p.mode == 2)
-          epi_row_masked_staged(p, tbase, row - lane, n0, 0, S::BN / 32, stage, lane);
+          epi_row_masked_staged(p, tbase, row - lane, n0, c0, c1, stage_w, lane);
         else
-          epi_row_train(p, tbase, row, row_ok, n0, 0, S::BN / 32, split);
+          epi_row_train(p, tbase, row, row_ok, n0, c0, c1, split);
       } else if (STAGED && p.mode == 0) {
-        uint8_t* stage = smem + S::VEC_OFFSET + epi_vector_bytes(p.N) + q * kStageBytesPerWarp;
-        epi_row_staged<OUT_FP8>(p, ev, tbase, row - lane, n0, 0, S::BN / 32, stage, lane);
+        epi_row_staged<OUT_FP8>(p, ev, tbase, row - lane, n0, c0, c1, stage_w, lane);
       } else {
-        epi_row<OUT_FP8>(p, ev, tbase, row, row_ok, n0, 0, S::BN / 32, h0, h1);
+        epi_row<OUT_FP8>(p, ev, tbase, row, row_ok, n0, c0, c1, h0, h1);
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(tempty_leader0 + 8u * b);
       if (p.mode == 1 && row_ok)
-        p.head_part[static_cast<size_t>(n_blk) * p.M + row] = make_float2(h0, h1);
+        p.head_part[(static_cast<size_t>(n_blk) * (EPI / 4) + half) * p.M + row] =
+            make_float2(h0, h1);
     }
   }
 
@@ -309,28 +315,28 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
   }
 }
 
-template <bool IN_FP8, bool OUT_FP8, bool STAGED, bool TRAIN = false>
+template <bool IN_FP8, bool OUT_FP8, bool STAGED, bool TRAIN = false, int EPI = 4>
 cudaError_t launch_pair_one(const CUtensorMap& tmA, const CUtensorMap& tmB,
                             const TcGemmParams& p, int grid, cudaStream_t s) {
-  using S = PairShape<IN_FP8, STAGED>;
-  auto kern = tc_gemm_pair_kernel<IN_FP8, OUT_FP8, STAGED, TRAIN>;
+  using S = PairShape<IN_FP8, STAGED, EPI>;
+  auto kern = tc_gemm_pair_kernel<IN_FP8, OUT_FP8, STAGED, TRAIN, EPI>;
   const int smem = S::SMEM_BYTES + epi_vector_bytes(p.N) + S::OUT_STAGE_BYTES;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, 192, smem, s>>>(tmA, tmB, p);
+  kern<<<grid, S::THREADS, smem, s>>>(tmA, tmB, p);
   return cudaGetLastError();
 }
 
-template <bool IN_FP8, bool STAGED>
+template <bool IN_FP8, bool STAGED, int EPI>
 int max_pairs_for() {
-  using S = PairShape<IN_FP8, STAGED>;
-  auto kern = tc_gemm_pair_kernel<IN_FP8, false, STAGED, false>;
+  using S = PairShape<IN_FP8, STAGED, EPI>;
+  auto kern = tc_gemm_pair_kernel<IN_FP8, false, STAGED, false, EPI>;
   const int smem = S::SMEM_BYTES + epi_vector_bytes(kMaxStagedColumns) + S::OUT_STAGE_BYTES;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
     return 0;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(2, 1, 1);
-  cfg.blockDim = dim3(192, 1, 1);
+  cfg.blockDim = dim3(S::THREADS, 1, 1);
   cfg.dynamicSmemBytes = smem;
   int n = 0;
   if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
@@ -340,24 +346,38 @@ int max_pairs_for() {
   return n;
 }
 
-template <bool IN_FP8, bool STAGED>
+template <bool IN_FP8, bool STAGED, int EPI>
 cudaError_t launch_pair_io(bool out_fp8, const CUtensorMap& tmA, const CUtensorMap& tmB,
                            const TcGemmParams& p, int grid, cudaStream_t s) {
-  return out_fp8 ? launch_pair_one<IN_FP8, true, STAGED>(tmA, tmB, p, grid, s)
-                 : launch_pair_one<IN_FP8, false, STAGED>(tmA, tmB, p, grid, s);
+  return out_fp8 ? launch_pair_one<IN_FP8, true, STAGED, false, EPI>(tmA, tmB, p, grid, s)
+                 : launch_pair_one<IN_FP8, false, STAGED, false, EPI>(tmA, tmB, p, grid, s);
+}
+
+template <int EPI>
+cudaError_t launch_pair_epi(bool in_fp8, bool out_fp8, bool staged, const CUtensorMap& tmA,
+                            const CUtensorMap& tmB, const TcGemmParams& p, int grid,
+                            cudaStream_t s) {
+  if (in_fp8) return staged ? launch_pair_io<true, true, EPI>(out_fp8, tmA, tmB, p, grid, s)
+                            : launch_pair_io<true, false, EPI>(out_fp8, tmA, tmB, p, grid, s);
+  return staged ? launch_pair_io<false, true, EPI>(out_fp8, tmA, tmB, p, grid, s)
+                : launch_pair_io<false, false, EPI>(out_fp8, tmA, tmB, p, grid, s);
 }
 
 }  // namespace
 
 int tc_gemm_pair_max_clusters(bool in_fp8) {
-  const int a = in_fp8 ? max_pairs_for<true, false>() : max_pairs_for<false, false>();
-  const int b = in_fp8 ? max_pairs_for<true, true>() : max_pairs_for<false, true>();
-  return a < b ? a : b;
+  int n = 1 << 30;
+  const int v[4] = {in_fp8 ? max_pairs_for<true, false, 4>() : max_pairs_for<false, false, 4>(),
+                    in_fp8 ? max_pairs_for<true, true, 4>() : max_pairs_for<false, true, 4>(),
+                    in_fp8 ? max_pairs_for<true, false, 8>() : max_pairs_for<false, false, 8>(),
+                    in_fp8 ? max_pairs_for<true, true, 8>() : max_pairs_for<false, true, 8>()};
+  for (int x : v) n = x < n ? x : n;
+  return n;
 }
 
-cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, bool staged, const CUtensorMap& tmA,
-                                const CUtensorMap& tmB, const TcGemmParams& p, int clusters,
-                                cudaStream_t s) {
+cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, bool staged, int epi_warps,
+                                const CUtensorMap& tmA, const CUtensorMap& tmB,
+                                const TcGemmParams& p, int clusters, cudaStream_t s) {
   if (p.mode == 3 && (p.k_splits > 1 ? p.k_splits : 1) > (p.K + 63) / 64)
     return cudaErrorInvalidValue;  // every split needs a k-block
   if (p.mn_major && (in_fp8 || p.mode != 3)) return cudaErrorInvalidValue;
@@ -370,10 +390,9 @@ cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, bool staged, const CU
   // training modes, and the training forward that writes ReLU patterns
   if (p.mode >= 2 || p.relu_bits != nullptr)
     return launch_pair_one<false, false, true, true>(tmA, tmB, p, grid, s);
-  if (in_fp8) return staged ? launch_pair_io<true, true>(out_fp8, tmA, tmB, p, grid, s)
-                            : launch_pair_io<true, false>(out_fp8, tmA, tmB, p, grid, s);
-  return staged ? launch_pair_io<false, true>(out_fp8, tmA, tmB, p, grid, s)
-                : launch_pair_io<false, false>(out_fp8, tmA, tmB, p, grid, s);
+  if (epi_warps == 8) return launch_pair_epi<8>(in_fp8, out_fp8, staged, tmA, tmB, p, grid, s);
+  if (epi_warps != 4) return cudaErrorInvalidValue;
+  return launch_pair_epi<4>(in_fp8, out_fp8, staged, tmA, tmB, p, grid, s);
 }
 
 }  // namespace ddf

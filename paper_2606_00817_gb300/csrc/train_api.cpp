@@ -203,7 +203,7 @@ ddf_status tc_gemm_pair(ddf_s* h, const void* A, int M, int K, const CUtensorMap
   p.timeout_ns = h->timeout_ns;
   const int64_t tiles = ((M + 255) / 256) * static_cast<int64_t>(p.N / 256);
   const int clusters = static_cast<int>(std::min<int64_t>(tiles, h->pair_clusters));
-  DDF_CK(ddf::launch_tc_gemm_pair(false, false, staged, tmA, tmB, p, clusters, st));
+  DDF_CK(ddf::launch_tc_gemm_pair(false, false, staged, 4, tmA, tmB, p, clusters, st));
   return DDF_OK;
 }
 
@@ -341,7 +341,7 @@ ddf_status backward_from_dz(ddf_s* h, int B, cudaStream_t st) {
       ProfScope ps(h, kProfGemm, st);
       const int grid = static_cast<int>(std::min<int64_t>(splits * tiles1, slots));
       if (pair)
-        DDF_CK(ddf::launch_tc_gemm_pair(false, false, false, tmD, tmX, p, grid, st));
+        DDF_CK(ddf::launch_tc_gemm_pair(false, false, false, 4, tmD, tmX, p, grid, st));
       else
         DDF_CK(ddf::launch_tc_gemm(ddf::TcTile{bnw, 4}, false, false, tmD, tmX, p, grid, st));
     }

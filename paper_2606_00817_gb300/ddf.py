@@ -441,7 +441,8 @@ def ddf_get_tile(h, which: int = 0):
 
 # the autotuner's candidates, in its order; the last two are layer-1 only
 TILE_CANDIDATES = ((256, 4, 0, 0, 0), (256, 8, 0, 0, 0), (128, 4, 0, 0, 0), (128, 8, 0, 0, 0),
-                   (256, 4, 1, 0, 0), (256, 4, 1, 1, 0), (256, 4, 0, 1, 1), (256, 8, 0, 1, 1))
+                   (256, 4, 1, 0, 0), (256, 4, 1, 1, 0), (256, 8, 1, 1, 0), (256, 4, 0, 1, 1),
+                   (256, 8, 0, 1, 1))
 
 
 def ddf_autotune(h, rays, n, stream=None):

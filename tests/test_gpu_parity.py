@@ -213,7 +213,8 @@ def test_full_size_shadow_workload_sampled(torch_cuda):
 
 
 @pytest.mark.parametrize("tile", [(256, 4, 0, 0, 0), (256, 8, 0, 0, 0), (128, 4, 0, 0, 0),
-                                  (128, 8, 0, 0, 0), (256, 4, 1, 0, 0), (256, 4, 1, 1, 0)])
+                                  (128, 8, 0, 0, 0), (256, 4, 1, 0, 0), (256, 4, 1, 1, 0),
+                                  (256, 8, 1, 0, 0), (256, 8, 1, 1, 0)])
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
 def test_every_tile_matches_oracle(torch_cuda, tile, prec):
     from paper_2606_00817_gb300 import ddf
