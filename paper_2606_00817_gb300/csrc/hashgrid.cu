@@ -29,6 +29,7 @@ namespace {
 
 constexpr int kHgRows = 128;      // rays per tile (TMEM lanes)
 constexpr int kHgW = 64;          // MLP width
+constexpr int kHgLevels = 16;     // levels of HashGridParams
 constexpr int kHgCode = 59;       // 32 hash features + 27 direction values
 constexpr int kHgImage = kHgW * 128;  // one 64 x 64 bf16 swizzled operand: 8 KB
 constexpr uint32_t kPrimeY = 2654435761u;
@@ -430,28 +431,78 @@ __global__ void __launch_bounds__(kHgF32Rays)
   }
 }
 
-// part[s][n][k] = sum over the rays of split s of P[r][n] * A[r][k], for the
-// weight gradient dW = P^T A of a layer (P = dL/dpre [B x ldp], A = the
-// layer input [B x lda]); deterministic: every partial in a fixed order.
-__global__ void hg_outer_kernel(const float* __restrict__ P, int ldp, const float* __restrict__ A,
-                                int lda, int na, int64_t B, int64_t per_split,
-                                float* __restrict__ part) {
-  const int n = blockIdx.x, sp = blockIdx.y, np = gridDim.x;
-  const int k = threadIdx.x;
-  if (k >= na) return;
-  const int64_t r0 = sp * per_split;
+// Weight-gradient partials dW = P^T A of one MLP layer of the hash-grid
+// field (P = dL/dpre [B x ldp], A = the layer input [B x lda]): one
+// 256-thread block per split of the rays computes the whole [np x na]
+// partial (np, na <= 64) from 32-ray slices staged in shared memory, thread
+// (tn, tk) owning rows 4 tn .. 4 tn + 3 and columns 4 tk .. 4 tk + 3, and
+// bpart[s][n] = sum of P[r][n] over the split (the bias gradient's partial).
+// Every sum runs over the split's rays in order.
+__global__ void __launch_bounds__(256)
+hg_outer_tiled_kernel(const float* __restrict__ P, int ldp, int np, const float* __restrict__ A,
+                      int lda, int na, int64_t B, int64_t per_split, float* __restrict__ part,
+                      float* __restrict__ bpart) {
+  __shared__ float sP[32][65];
+  __shared__ float sA[32][65];
+  const int tid = threadIdx.x;
+  const int tn = tid >> 4, tk = tid & 15;
+  const int64_t r0 = blockIdx.x * per_split;
   const int64_t r1 = r0 + per_split < B ? r0 + per_split : B;
-  float s = 0.f;
-  for (int64_t r = r0; r < r1; ++r) s = fmaf(P[r * ldp + n], A[r * lda + k], s);
-  part[(static_cast<int64_t>(sp) * np + n) * na + k] = s;
+  float acc[4][4] = {};
+  float bs[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int64_t rb = r0; rb < r1; rb += 32) {
+    for (int i = tid; i < 32 * 64; i += 256) {
+      const int rr = i >> 6, c = i & 63;
+      const int64_t r = rb + rr;
+      const bool ok = r < r1;
+      sP[rr][c] = ok && c < np ? P[r * ldp + c] : 0.f;
+      sA[rr][c] = ok && c < na ? A[r * lda + c] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < 32; ++rr) {
+      float pv[4], av[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        pv[i] = sP[rr][4 * tn + i];
+        av[i] = sA[rr][4 * tk + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        bs[i] += pv[i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(pv[i], av[j], acc[i][j]);
+      }
+    }
+    __syncthreads();
+  }
+  float* ps = part + static_cast<int64_t>(blockIdx.x) * np * na;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int n = 4 * tn + i;
+    if (n >= np) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = 4 * tk + j;
+      if (k < na) ps[n * na + k] = acc[i][j];
+    }
+    if (tk == 0) bpart[static_cast<int64_t>(blockIdx.x) * np + n] = bs[i];
+  }
 }
 
 // ------------------------------------------------------------ packing
 
-// (f0, f1) FP32 entry pairs -> bf16x2 words (f0 in the low half).
-__global__ void hg_pack_table_kernel(const float* __restrict__ src, int64_t n, uint32_t* __restrict__ dst) {
+// (f0, f1) FP32 entry pairs -> bf16x2 words (f0 in the low half), every
+// level in one launch: source entry i of level l (blob layout `from`) goes
+// to entry i - from.offset[l] + to.offset[l] (the padded layout `to`).
+__global__ void hg_pack_table_kernel(const float* __restrict__ src, int64_t n, HashGridParams from,
+                                     HashGridParams to, uint32_t* __restrict__ dst) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i < n) dst[i] = pack2(src[2 * i], src[2 * i + 1]);
+  if (i >= n) return;
+  int l = 0;
+#pragma unroll
+  for (int k = 1; k < kHgLevels; ++k) l += i >= from.offset[k] ? 1 : 0;
+  dst[i - from.offset[l] + to.offset[l]] = pack2(src[2 * i], src[2 * i + 1]);
 }
 
 // W [64 x K] FP32 (K <= 64) -> the swizzled K-major bf16 image the MMA reads,
@@ -581,20 +632,19 @@ cudaError_t launch_hg_train_bwd(const HashGridParams& g, const float* mlp, int H
   return cudaGetLastError();
 }
 
-cudaError_t launch_hg_outer(const float* P, int ldp, int np, const float* A, int lda, int na,
-                            int64_t B, int splits, float* part, cudaStream_t s) {
-  if (np < 1 || na < 1 || na > 1024 || splits < 1) return cudaErrorInvalidValue;
-  const int64_t per = (B + splits - 1) / splits;
-  hg_outer_kernel<<<dim3(np, splits), ((na + 31) / 32) * 32, 0, s>>>(P, ldp, A, lda, na, B, per,
-                                                                      part);
+cudaError_t launch_hg_pack_table(const float* src, int64_t n_entries, const HashGridParams& from,
+                                 const HashGridParams& to, uint32_t* dst, cudaStream_t s) {
+  if (n_entries <= 0) return cudaSuccess;
+  hg_pack_table_kernel<<<static_cast<unsigned>((n_entries + 255) / 256), 256, 0, s>>>(
+      src, n_entries, from, to, dst);
   return cudaGetLastError();
 }
 
-cudaError_t launch_hg_pack_table(const float* src, int64_t n_entries, uint32_t* dst,
-                                 cudaStream_t s) {
-  if (n_entries <= 0) return cudaSuccess;
-  hg_pack_table_kernel<<<static_cast<unsigned>((n_entries + 255) / 256), 256, 0, s>>>(src, n_entries,
-                                                                                       dst);
+cudaError_t launch_hg_outer_tiled(const float* P, int ldp, int np, const float* A, int lda, int na,
+                                  int64_t B, int splits, float* part, float* bpart, cudaStream_t s) {
+  if (np < 1 || np > 64 || na < 1 || na > 64 || splits < 1) return cudaErrorInvalidValue;
+  const int64_t per = (B + splits - 1) / splits;
+  hg_outer_tiled_kernel<<<splits, 256, 0, s>>>(P, ldp, np, A, lda, na, B, per, part, bpart);
   return cudaGetLastError();
 }
 

@@ -59,11 +59,8 @@ ddf_status hg_refresh(ddf_s* h, cudaStream_t st) {
   const int H = h->cfg.hidden_layers;
   const float* tables = h->d_blob;
   uint32_t* tab = static_cast<uint32_t*>(h->hg_table);
-  for (int l = 0; l < kLevels; ++l) {  // level by level into the padded layout
-    const int64_t end = l + 1 < kLevels ? h->hg_blob.offset[l + 1] : h->hg_blob_entries;
-    DDF_CK(ddf::launch_hg_pack_table(tables + 2 * static_cast<int64_t>(h->hg_blob.offset[l]),
-                                     end - h->hg_blob.offset[l], tab + h->hg.offset[l], st));
-  }
+  // every level into the padded layout, one launch
+  DDF_CK(ddf::launch_hg_pack_table(tables, h->hg_blob_entries, h->hg_blob, h->hg, tab, st));
   // MLP part: W_1 [64 x 59], b_1, (W_l [64 x 64], b_l) ..., W_o [2 x 64], b_o
   const float* m = tables + 2 * h->hg_blob_entries;
   int K = kCode;
@@ -136,7 +133,7 @@ ddf_status hg_query(ddf_s* h, ddf::RaySoA rays, int64_t n, ddf::HeadOut out, cud
 
 namespace {
 
-constexpr int kGradSplits = 64;  // ray splits of the weight-gradient sums
+constexpr int kGradSplits = 128;  // ray splits of the weight-gradient sums
 
 struct MlpOffsets {
   int64_t w[4], b[4], wo, bo;
@@ -229,17 +226,16 @@ ddf_status hg_backward(ddf_s* h, ddf::RaySoA rays, int B, cudaStream_t st) {
     const float* P = h->hg_dpre + l * act;
     const float* A = l == 0 ? h->hg_code : h->hg_acts + (l - 1) * act;
     const int K = l == 0 ? kCode : kW;
-    DDF_CK(ddf::launch_hg_outer(P, kW, kW, A, kW, K, B, kGradSplits, h->tr_part, st));
+    DDF_CK(ddf::launch_hg_outer_tiled(P, kW, kW, A, kW, K, B, kGradSplits, h->tr_part,
+                                      h->tr_cpart, st));
     DDF_CK(ddf::launch_splitk_reduce(h->tr_part, kGradSplits, kW, K, static_cast<int64_t>(kW) * K, K,
                                      gmlp + o.w[l], K, st));
-    DDF_CK(ddf::launch_colsum_f32(P, B, kW, kW, kGradSplits, h->tr_cpart, st));
     DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart, kGradSplits, 1, kW, kW, kW, gmlp + o.b[l], kW, st));
   }
   const float* dz = reinterpret_cast<const float*>(h->tr_dz);
-  DDF_CK(ddf::launch_hg_outer(dz, 2, 2, h->hg_acts + (H - 1) * act, kW, kW, B, kGradSplits,
-                              h->tr_part, st));
+  DDF_CK(ddf::launch_hg_outer_tiled(dz, 2, 2, h->hg_acts + (H - 1) * act, kW, kW, B, kGradSplits,
+                                    h->tr_part, h->tr_cpart, st));
   DDF_CK(ddf::launch_splitk_reduce(h->tr_part, kGradSplits, 2, kW, 2 * kW, kW, gmlp + o.wo, kW, st));
-  DDF_CK(ddf::launch_colsum_f32(dz, B, 2, 2, kGradSplits, h->tr_cpart, st));
   DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart, kGradSplits, 1, 2, 2, 2, gmlp + o.bo, 2, st));
   h->grad_valid = true;
   return DDF_OK;
