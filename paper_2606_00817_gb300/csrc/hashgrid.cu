@@ -293,7 +293,9 @@ constexpr int kHgLd = kHgW + 1; // per-thread row stride in shared memory
 
 // Thread = ray: code and activations in a per-thread shared-memory row,
 // weights broadcast from shared memory, FFMA only. The training variant also
-// stores the code [B x 64], every hidden activation ([H x B x 64]) and z.
+// stores the code, every hidden activation and z; code and activations are
+// feature-major ([64 x B] and [H x 64 x B]) so that a warp's stores of one
+// feature cover 32 consecutive rays.
 template <bool TRAIN>
 __global__ void __launch_bounds__(kHgF32Rays)
     hashgrid_f32_kernel(const HashGridParams g, const float2* __restrict__ table,
@@ -322,7 +324,7 @@ __global__ void __launch_bounds__(kHgF32Rays)
 #pragma unroll
   for (int k = 0; k < 27; ++k) a[32 + k] = dcode[k];
   if constexpr (TRAIN) {
-    for (int k = 0; k < kHgW; ++k) code_out[row * kHgW + k] = k < kHgCode ? a[k] : 0.f;
+    for (int k = 0; k < kHgW; ++k) code_out[k * M + row] = k < kHgCode ? a[k] : 0.f;
   }
   const float* w = sw;
   int K = kHgCode;
@@ -334,8 +336,8 @@ __global__ void __launch_bounds__(kHgF32Rays)
       nb[n] = fmaxf(s + b[n], 0.f);
     }
     if constexpr (TRAIN) {
-      float* dst = acts + (static_cast<int64_t>(l) * M + row) * kHgW;
-      for (int n = 0; n < kHgW; ++n) dst[n] = nb[n];
+      float* dst = acts + static_cast<int64_t>(l) * kHgW * M + row;
+      for (int n = 0; n < kHgW; ++n) dst[n * M] = nb[n];
     }
     float* t = a;
     a = nb;
@@ -358,8 +360,8 @@ __global__ void __launch_bounds__(kHgF32Rays)
 }
 
 // Backward of one ray (FP32): from dL/dz through the head and the hidden
-// layers (ReLU masks from the stored activations), storing every dL/dpre for
-// the weight gradients, then the hash features' gradient scattered into the
+// layers (ReLU masks from the stored activations), storing every dL/dpre
+// (feature-major, [H x 64 x B]) for the weight gradients, then the hash features' gradient scattered into the
 // level tables' gradient (blob layout): each corner entry receives its
 // trilinear weight times the feature gradient (atomic adds; entries shared by
 // several rays or corners sum up).
@@ -389,12 +391,12 @@ __global__ void __launch_bounds__(kHgF32Rays)
   const float2 d = dz[row];
   for (int k = 0; k < kHgW; ++k) dh[k] = d.x * wo[k] + d.y * wo[kHgW + k];
   for (int l = H - 1; l >= 0; --l) {
-    const float* h = acts + (static_cast<int64_t>(l) * M + row) * kHgW;
-    float* dp = dpre + (static_cast<int64_t>(l) * M + row) * kHgW;
+    const float* h = acts + static_cast<int64_t>(l) * kHgW * M + row;
+    float* dp = dpre + static_cast<int64_t>(l) * kHgW * M + row;
     for (int k = 0; k < kHgW; ++k) {
-      const float v = h[k] > 0.f ? dh[k] : 0.f;
+      const float v = h[k * M] > 0.f ? dh[k] : 0.f;
       dh[k] = v;
-      dp[k] = v;
+      dp[k * M] = v;
     }
     const int K = l == 0 ? 2 * 16 : kHgW;  // layer 1: only the hash features need a gradient
     const int ldw = l == 0 ? kHgCode : kHgW;
@@ -432,16 +434,17 @@ __global__ void __launch_bounds__(kHgF32Rays)
 }
 
 // Weight-gradient partials dW = P^T A of one MLP layer of the hash-grid
-// field (P = dL/dpre [B x ldp], A = the layer input [B x lda]): one
-// 256-thread block per split of the rays computes the whole [np x na]
+// field (P = dL/dpre, A = the layer input; element (r, c) of P at
+// P[r prs + c pcs], of A at A[r ars + c acs]): one 256-thread block per
+// split of the rays computes the whole [np x na]
 // partial (np, na <= 64) from 32-ray slices staged in shared memory, thread
 // (tn, tk) owning rows 4 tn .. 4 tn + 3 and columns 4 tk .. 4 tk + 3, and
 // bpart[s][n] = sum of P[r][n] over the split (the bias gradient's partial).
 // Every sum runs over the split's rays in order.
 __global__ void __launch_bounds__(256)
-hg_outer_tiled_kernel(const float* __restrict__ P, int ldp, int np, const float* __restrict__ A,
-                      int lda, int na, int64_t B, int64_t per_split, float* __restrict__ part,
-                      float* __restrict__ bpart) {
+hg_outer_tiled_kernel(const float* __restrict__ P, int64_t prs, int64_t pcs, int np,
+                      const float* __restrict__ A, int64_t ars, int64_t acs, int na, int64_t B,
+                      int64_t per_split, float* __restrict__ part, float* __restrict__ bpart) {
   __shared__ float sP[32][65];
   __shared__ float sA[32][65];
   const int tid = threadIdx.x;
@@ -452,11 +455,11 @@ hg_outer_tiled_kernel(const float* __restrict__ P, int ldp, int np, const float*
   float bs[4] = {0.f, 0.f, 0.f, 0.f};
   for (int64_t rb = r0; rb < r1; rb += 32) {
     for (int i = tid; i < 32 * 64; i += 256) {
-      const int rr = i >> 6, c = i & 63;
+      const int rr = i & 31, c = i >> 5;  // a warp reads 32 rays of one feature
       const int64_t r = rb + rr;
       const bool ok = r < r1;
-      sP[rr][c] = ok && c < np ? P[r * ldp + c] : 0.f;
-      sA[rr][c] = ok && c < na ? A[r * lda + c] : 0.f;
+      sP[rr][c] = ok && c < np ? P[r * prs + c * pcs] : 0.f;
+      sA[rr][c] = ok && c < na ? A[r * ars + c * acs] : 0.f;
     }
     __syncthreads();
 #pragma unroll 4
@@ -640,11 +643,13 @@ cudaError_t launch_hg_pack_table(const float* src, int64_t n_entries, const Hash
   return cudaGetLastError();
 }
 
-cudaError_t launch_hg_outer_tiled(const float* P, int ldp, int np, const float* A, int lda, int na,
-                                  int64_t B, int splits, float* part, float* bpart, cudaStream_t s) {
+cudaError_t launch_hg_outer_tiled(const float* P, int64_t prs, int64_t pcs, int np, const float* A,
+                                  int64_t ars, int64_t acs, int na, int64_t B, int splits,
+                                  float* part, float* bpart, cudaStream_t s) {
   if (np < 1 || np > 64 || na < 1 || na > 64 || splits < 1) return cudaErrorInvalidValue;
   const int64_t per = (B + splits - 1) / splits;
-  hg_outer_tiled_kernel<<<splits, 256, 0, s>>>(P, ldp, np, A, lda, na, B, per, part, bpart);
+  hg_outer_tiled_kernel<<<splits, 256, 0, s>>>(P, prs, pcs, np, A, ars, acs, na, B, per, part,
+                                               bpart);
   return cudaGetLastError();
 }
 

@@ -226,15 +226,15 @@ ddf_status hg_backward(ddf_s* h, ddf::RaySoA rays, int B, cudaStream_t st) {
     const float* P = h->hg_dpre + l * act;
     const float* A = l == 0 ? h->hg_code : h->hg_acts + (l - 1) * act;
     const int K = l == 0 ? kCode : kW;
-    DDF_CK(ddf::launch_hg_outer_tiled(P, kW, kW, A, kW, K, B, kGradSplits, h->tr_part,
+    DDF_CK(ddf::launch_hg_outer_tiled(P, 1, B, kW, A, 1, B, K, B, kGradSplits, h->tr_part,
                                       h->tr_cpart, st));
     DDF_CK(ddf::launch_splitk_reduce(h->tr_part, kGradSplits, kW, K, static_cast<int64_t>(kW) * K, K,
                                      gmlp + o.w[l], K, st));
     DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart, kGradSplits, 1, kW, kW, kW, gmlp + o.b[l], kW, st));
   }
   const float* dz = reinterpret_cast<const float*>(h->tr_dz);
-  DDF_CK(ddf::launch_hg_outer_tiled(dz, 2, 2, h->hg_acts + (H - 1) * act, kW, kW, B, kGradSplits,
-                                    h->tr_part, h->tr_cpart, st));
+  DDF_CK(ddf::launch_hg_outer_tiled(dz, 2, 1, 2, h->hg_acts + (H - 1) * act, 1, B, kW, B,
+                                    kGradSplits, h->tr_part, h->tr_cpart, st));
   DDF_CK(ddf::launch_splitk_reduce(h->tr_part, kGradSplits, 2, kW, 2 * kW, kW, gmlp + o.wo, kW, st));
   DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart, kGradSplits, 1, 2, 2, 2, gmlp + o.bo, 2, st));
   h->grad_valid = true;

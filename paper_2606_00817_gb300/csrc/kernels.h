@@ -178,19 +178,21 @@ cudaError_t launch_hashgrid_f32(const HashGridParams& g, const float2* table, co
 // FP32 table (blob layout `from`) -> bf16x2 entries in the layout `to`.
 cudaError_t launch_hg_pack_table(const float* src, int64_t n_entries, const HashGridParams& from,
                                  const HashGridParams& to, uint32_t* dst, cudaStream_t s);
-// Training (FP32): forward storing code [B x 64], activations [H x B x 64]
-// and z; backward from dz storing dL/dpre [H x B x 64] and scattering the
-// hash features' gradient into grad_table (blob layout, atomic adds);
-// part[s][n][k] = sum over split s of P[r][n] A[r][k] and bpart[s][n] = sum
-// of P[r][n] (n < np <= 64, k < na <= 64).
+// Training (FP32): forward storing code [64 x B], activations [H x 64 x B]
+// (feature-major) and z; backward from dz storing dL/dpre [H x 64 x B] and
+// scattering the hash features' gradient into grad_table (blob layout,
+// atomic adds); part[s][n][k] = sum over split s of P(r, n) A(r, k) and
+// bpart[s][n] = sum of P(r, n) (n < np <= 64, k < na <= 64), with element
+// (r, c) of P at P[r prs + c pcs] and of A at A[r ars + c acs].
 cudaError_t launch_hg_train_fwd(const HashGridParams& g, const float2* table, const float* mlp,
                                 int H, RaySoA rays, int64_t B, float* code, float* acts,
                                 float2* z, cudaStream_t s);
 cudaError_t launch_hg_train_bwd(const HashGridParams& g, const float* mlp, int H, RaySoA rays,
                                 int64_t B, const float* acts, const float2* dz, float* dpre,
                                 float* grad_table, cudaStream_t s);
-cudaError_t launch_hg_outer_tiled(const float* P, int ldp, int np, const float* A, int lda, int na,
-                                  int64_t B, int splits, float* part, float* bpart, cudaStream_t s);
+cudaError_t launch_hg_outer_tiled(const float* P, int64_t prs, int64_t pcs, int np, const float* A,
+                                  int64_t ars, int64_t acs, int na, int64_t B, int splits,
+                                  float* part, float* bpart, cudaStream_t s);
 cudaError_t launch_hg_pack_image(const float* w, int K, uint8_t* img, cudaStream_t s);
 
 // Ambient occlusion (Sec. 3.3): for point p with rays [offsets[p], offsets[p+1])
