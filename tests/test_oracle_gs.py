@@ -100,3 +100,27 @@ def test_enter_box_invariants():
     t0, h0 = O.cast_scene(sc, o, d)
     t1, h1 = O.cast_scene(sc, o2, d)
     assert np.array_equal(h0, h1) and np.allclose(t1[h0], t0[h0] - e[h0])
+
+
+def test_anisotropic_and_off_axis_footprints():
+    """Closed forms of the EWA screen covariance for the camera at (0, 0, -4)
+    looking along +z (right = -x, up = +y, so pixel x grows with -X and pixel
+    y with -Y): a Gaussian at the origin rotated in the XY plane keeps the
+    sign of its XY covariance on screen, scaled by (f / 4)^2; a Gaussian at
+    (X0, 0, 0) stretched only along the view axis still has a horizontal
+    footprint, through the projection's depth derivative: S_xx = (f X0 / 16)^2
+    c^2 + 0.3."""
+    W = H = 64
+    fpx = H / (2 * np.tan(FOV / 2))
+    th = 0.6
+    R = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1.0]])
+    cov = R @ np.diag([0.2 ** 2, 0.05 ** 2, 0.01 ** 2]) @ R.T
+    _, S, _ = O.gs_project(np.zeros((1, 3)), cov[None], EYE, TGT, UP, FOV, W, H)
+    k = (fpx / 4.0) ** 2
+    assert np.allclose(S[0], k * cov[:2, :2] + 0.3 * np.eye(2), rtol=1e-12)
+    assert S[0, 0, 1] > 0                                  # the sign survives
+    X0, c = 0.5, 0.3
+    mu, S, z = O.gs_project(np.array([[X0, 0.0, 0.0]]), np.diag([0.0, 0.0, c ** 2])[None],
+                            EYE, TGT, UP, FOV, W, H)
+    assert abs(mu[0, 0] - ((W - 1) / 2 - X0 / 4.0 * fpx)) < 1e-9
+    assert np.allclose(S[0], np.diag([(fpx * X0 / 16.0) ** 2 * c ** 2 + 0.3, 0.3]), rtol=1e-12, atol=1e-15)
