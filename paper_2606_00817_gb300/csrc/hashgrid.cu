@@ -330,10 +330,20 @@ __global__ void __launch_bounds__(kHgF32Rays)
   int K = kHgCode;
   for (int l = 0; l < H; ++l) {
     const float* b = w + kHgW * K;
-    for (int n = 0; n < kHgW; ++n) {
-      float s = 0.f;
-      for (int k = 0; k < K; ++k) s = fmaf(a[k], w[n * K + k], s);
-      nb[n] = fmaxf(s + b[n], 0.f);
+    for (int n = 0; n < kHgW; n += 4) {  // 4 outputs at a time: 4 independent FMA chains
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      const float* w0 = w + n * K;
+      for (int k = 0; k < K; ++k) {
+        const float av = a[k];
+        s0 = fmaf(av, w0[k], s0);
+        s1 = fmaf(av, w0[K + k], s1);
+        s2 = fmaf(av, w0[2 * K + k], s2);
+        s3 = fmaf(av, w0[3 * K + k], s3);
+      }
+      nb[n] = fmaxf(s0 + b[n], 0.f);
+      nb[n + 1] = fmaxf(s1 + b[n + 1], 0.f);
+      nb[n + 2] = fmaxf(s2 + b[n + 2], 0.f);
+      nb[n + 3] = fmaxf(s3 + b[n + 3], 0.f);
     }
     if constexpr (TRAIN) {
       float* dst = acts + static_cast<int64_t>(l) * kHgW * M + row;
@@ -401,10 +411,20 @@ __global__ void __launch_bounds__(kHgF32Rays)
     const int K = l == 0 ? 2 * 16 : kHgW;  // layer 1: only the hash features need a gradient
     const int ldw = l == 0 ? kHgCode : kHgW;
     const float* w = sw + woff[l];
-    for (int j = 0; j < K; ++j) {
-      float s = 0.f;
-      for (int n = 0; n < kHgW; ++n) s = fmaf(dh[n], w[n * ldw + j], s);
-      dn[j] = s;
+    for (int j = 0; j < K; j += 4) {  // K is 32 or 64: 4 inputs at a time
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      for (int n = 0; n < kHgW; ++n) {
+        const float dv = dh[n];
+        const float* wr = w + n * ldw + j;
+        s0 = fmaf(dv, wr[0], s0);
+        s1 = fmaf(dv, wr[1], s1);
+        s2 = fmaf(dv, wr[2], s2);
+        s3 = fmaf(dv, wr[3], s3);
+      }
+      dn[j] = s0;
+      dn[j + 1] = s1;
+      dn[j + 2] = s2;
+      dn[j + 3] = s3;
     }
     float* t = dh;
     dh = dn;
