@@ -565,10 +565,18 @@ def _train_workload(torch, ddf, dev, local, stream, blob):
     reps = 20
     ms = _time_ms(torch, stream, lambda: [train_step() for _ in range(reps)], reps=1, warm=0) / reps
     res = {"batch": B, "ms_per_step": ms, "steps_per_s": 1e3 / ms,
-                           "rays_per_s": B / (ms / 1e3),
-                           "tflops_6_b_params": 6.0 * B * I.NetShape(*NET).n_params / (ms / 1e3) / 1e12,
-                           "loss_first": first, "loss_after": float(loss.item()),
-                           "steps_taken": it[0], "status": ddf.ddf_check_status(tr.h)}
+           "rays_per_s": B / (ms / 1e3),
+           "tflops_6_b_params": 6.0 * B * I.NetShape(*NET).n_params / (ms / 1e3) / 1e12,
+           "loss_first": first, "loss_after": float(loss.item()),
+           "activation_bytes": ddf.ddf_get_train_activation_bytes(tr.h)}
+    # activation checkpointing: keep every 3rd layer, recompute the rest
+    ddf.ddf_set_recompute(tr.h, 3)
+    train_step()
+    torch.cuda.synchronize()
+    ms3 = _time_ms(torch, stream, lambda: [train_step() for _ in range(reps)], reps=1, warm=0) / reps
+    res["recompute_segment_3"] = {"ms_per_step": ms3,
+                                  "activation_bytes": ddf.ddf_get_train_activation_bytes(tr.h)}
+    res.update({"steps_taken": it[0], "status": ddf.ddf_check_status(tr.h)})
     tr.close()
     return res
 

@@ -372,6 +372,24 @@ ddf_status ddf_distill_pool(ddf_handle h, const float* const pool[6], const floa
  * floats) to host memory. Synchronous. */
 ddf_status ddf_get_grad(ddf_handle h, float* host_grad, size_t n_floats);
 
+/* Activation checkpointing for training sinusoidal ray and SDF fields
+ * (the recomputation of activations "where memory asks for it"): segment
+ * <= 1 keeps every layer's output for the backward (the default). Segment
+ * k >= 2 keeps the outputs of layers k-1, 2k-1, ... and of the last layer.
+ * The backward then recomputes each run of dropped layers from the kept
+ * layer below it, just before it needs them. Gradients are bitwise those of
+ * segment 1: the forward GEMMs are deterministic. Activation memory falls
+ * from H buffers of batch x width bf16 to about H/k + k - 1 of them, at the
+ * cost of recomputing the dropped layers once per step. The training
+ * buffers are laid out anew by the next training call, and activations kept
+ * by ddf_forward_train are dropped. Synchronises the device.
+ * DDF_ERR_UNSUPPORTED on hash-grid fields. */
+ddf_status ddf_set_recompute(ddf_handle h, int32_t segment);
+
+/* Bytes of device memory the activation buffers of the last training batch
+ * occupy (0 before the first training call). */
+ddf_status ddf_get_train_activation_bytes(ddf_handle h, size_t* out);
+
 /* Zeroes the Adam moments and step count. */
 ddf_status ddf_reset_optimizer(ddf_handle h);
 

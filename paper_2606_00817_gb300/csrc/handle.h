@@ -97,7 +97,9 @@ struct ddf_s {
   // distillation step (train_api.cpp)
   int64_t tr_rows = 0;
   void* tr_enc = nullptr;                 // [B x kp16] bf16
-  std::vector<void*> tr_h;                // per layer [B x W] bf16 activations
+  std::vector<void*> tr_h;                // per layer [B x W] bf16 activations (views)
+  std::vector<void*> tr_store;            // the activation buffers tr_h points into
+  int tr_segment = 1;                     // checkpointing: keep every k-th layer (1: all)
   void* tr_dpre[2] = {nullptr, nullptr};  // [B x W] bf16 pre-activation gradients
   float* tr_part = nullptr;               // split-K partials of a weight gradient
   float* tr_cpart = nullptr;              // row-split partials of column sums

@@ -59,6 +59,14 @@ size_t n_params(const ddf_s* h) {
 
 bool is_hashgrid(const ddf_s* h) { return h->cfg.kind == DDF_KIND_HASHGRID; }
 
+// Whether layer l's output is kept through the backward (activation
+// checkpointing with segment k: the outputs of layers k-1, 2k-1, ... and of
+// the last layer; every output when k <= 1).
+bool kept_layer(const ddf_s* h, int l) {
+  const int k = h->tr_segment;
+  return k <= 1 || (l + 1) % k == 0 || l == h->cfg.hidden_layers - 1;
+}
+
 ddf_status train_alloc(ddf_s* h, void** p, size_t bytes) { return dev_alloc(h, p, bytes); }
 
 // Writes the bf16 query copies (W_l, and W_l^T for l >= 1), the biases and
@@ -134,7 +142,8 @@ ddf_status ensure_train(ddf_s* h, int64_t B) {
   if (B > h->tr_rows) {
     h->fwd_rows = 0;
     dev_free(h, h->tr_enc);
-    for (void* q : h->tr_h) dev_free(h, q);
+    for (void* q : h->tr_store) dev_free(h, q);
+    h->tr_store.clear();
     dev_free(h, h->tr_dpre[0]);
     dev_free(h, h->tr_dpre[1]);
     dev_free(h, h->tr_z);
@@ -148,8 +157,26 @@ ddf_status ensure_train(ddf_s* h, int64_t B) {
     h->tr_rows = 0;
     const size_t act = static_cast<size_t>(B) * W * 2;
     if ((s = train_alloc(h, &h->tr_enc, static_cast<size_t>(B) * h->kp16 * 2)) != DDF_OK) return s;
-    for (int l = 0; l < H; ++l)
-      if ((s = train_alloc(h, &h->tr_h[l], act)) != DDF_OK) return s;
+    // kept layers own a buffer; a dropped layer j shares scratch slot
+    // (j - first layer of its run) with the dropped layers of other runs
+    std::vector<void*> scratch;
+    for (int l = 0; l < H; ++l) {
+      if (kept_layer(h, l)) {
+        if ((s = train_alloc(h, &p, act)) != DDF_OK) return s;
+        h->tr_store.push_back(p);
+        h->tr_h[l] = p;
+        continue;
+      }
+      int s0 = l;
+      while (s0 > 0 && !kept_layer(h, s0 - 1)) --s0;
+      const size_t slot = static_cast<size_t>(l - s0);
+      if (slot >= scratch.size()) {
+        if ((s = train_alloc(h, &p, act)) != DDF_OK) return s;
+        h->tr_store.push_back(p);
+        scratch.push_back(p);
+      }
+      h->tr_h[l] = scratch[slot];
+    }
     for (int i = 0; i < 2; ++i)
       if ((s = train_alloc(h, &h->tr_dpre[i], act)) != DDF_OK) return s;
     if ((s = train_alloc(h, &p, B * sizeof(float2))) != DDF_OK) return s;
@@ -229,6 +256,29 @@ ddf_status check_train_args(ddf_s* h, const float* const rays[6], const float* t
 // Forward keeping every activation: encoding, the tensor-core layers, the
 // FP32 head into h->tr_z (float2 per row; .y unused for an SDF field).
 // rays: 6 SoA arrays (ray field) or 3 point arrays (SDF field, in rays[0..2]).
+// Forward of layer l over the batch: tr_h[l] = ReLU(tr_h[l-1] W_l^T + b_l)
+// (layer 0 reads the encoding), plus its ReLU bits on the pair path. The
+// GEMMs are deterministic, so a recomputed layer is bitwise the first one.
+ddf_status forward_layer(ddf_s* h, int l, int B, cudaStream_t st) {
+  const int W = h->cfg.width, H = h->cfg.hidden_layers;
+  ddf::TcGemmParams p{};
+  p.N = W;
+  p.bias = h->bias[l];
+  p.out_scale = 1.0f;
+  p.out = h->tr_h[l];
+  p.ldo = W;
+  p.mode = 0;
+  ProfScope ps(h, l == 0 ? kProfFirst : kProfGemm, st);
+  const void* A_in = l == 0 ? h->tr_enc : h->tr_h[l - 1];
+  const int K = l == 0 ? h->kp16 : W;
+  if (h->tr_pair && l < H - 1) {  // the input gradients will test this layer's ReLU pattern
+    p.relu_bits = h->tr_bits[l];
+    p.ldb = W / 32;
+  }
+  return h->tr_pair ? tc_gemm_pair(h, A_in, B, K, h->tmBpair[l], true, p, st)
+                    : tc_gemm(h, A_in, B, K, h->tmBtr[l], h->bn, p, st);
+}
+
 ddf_status forward_keep(ddf_s* h, const float* const rays[6], int B, cudaStream_t st) {
   const bool sdf = h->cfg.kind == DDF_KIND_SDF;
   const int W = h->cfg.width, H = h->cfg.hidden_layers;
@@ -244,22 +294,7 @@ ddf_status forward_keep(ddf_s* h, const float* const rays[6], int B, cudaStream_
       DDF_CK(ddf::launch_encode_bf16(r, B, h->cfg.octaves, h->kp16, bf(h->tr_enc), st));
   }
   for (int l = 0; l < H; ++l) {
-    ddf::TcGemmParams p{};
-    p.N = W;
-    p.bias = h->bias[l];
-    p.out_scale = 1.0f;
-    p.out = h->tr_h[l];
-    p.ldo = W;
-    p.mode = 0;
-    ProfScope ps(h, l == 0 ? kProfFirst : kProfGemm, st);
-    const void* A_in = l == 0 ? h->tr_enc : h->tr_h[l - 1];
-    const int K = l == 0 ? h->kp16 : W;
-    if (h->tr_pair && l < H - 1) {  // the input gradients will test this layer's ReLU pattern
-      p.relu_bits = h->tr_bits[l];
-      p.ldb = W / 32;
-    }
-    ddf_status s = h->tr_pair ? tc_gemm_pair(h, A_in, B, K, h->tmBpair[l], true, p, st)
-                              : tc_gemm(h, A_in, B, K, h->tmBtr[l], h->bn, p, st);
+    const ddf_status s = forward_layer(h, l, B, st);
     if (s != DDF_OK) return s;
   }
   DDF_CK(ddf::launch_head_train(bf(h->tr_h[H - 1]), B, W, h->head_w, h->head_b, h->tr_z, st));
@@ -315,6 +350,17 @@ ddf_status backward_from_dz(ddf_s* h, int B, cudaStream_t st) {
       if (cost < best - 1e-12) {
         best = cost;
         splits = static_cast<int>(c);
+      }
+    }
+    // with checkpointing, layer l's input may not have been kept: when it
+    // is the top of a run of dropped layers, recompute the run from the kept
+    // layer below it (the layers under it in the run follow in this loop)
+    if (l > 0 && !kept_layer(h, l - 1) && kept_layer(h, l)) {
+      int s0 = l - 1;
+      while (s0 > 0 && !kept_layer(h, s0 - 1)) --s0;
+      for (int j = s0; j <= l - 1; ++j) {
+        const ddf_status s = forward_layer(h, j, B, st);
+        if (s != DDF_OK) return s;
       }
     }
     const void* A_in = l == 0 ? h->tr_enc : h->tr_h[l - 1];
@@ -600,6 +646,26 @@ ddf_status ddf_get_grad(ddf_handle h, float* host_grad, size_t n_floats) {
   DeviceGuard g(h->cfg.device);
   DDF_CK(cudaDeviceSynchronize());
   DDF_CK(cudaMemcpy(host_grad, h->grad, n_floats * sizeof(float), cudaMemcpyDeviceToHost));
+  return DDF_OK;
+}
+
+ddf_status ddf_set_recompute(ddf_handle h, int32_t segment) {
+  if (h == nullptr) return fail(DDF_ERR_INVALID_ARG, "handle is NULL");
+  if (segment < 1) return fail(DDF_ERR_INVALID_ARG, "segment must be >= 1");
+  if (h->cfg.kind == DDF_KIND_HASHGRID)
+    return fail(DDF_ERR_UNSUPPORTED, "the hash-grid field keeps its 64-wide activations");
+  if (segment == h->tr_segment) return DDF_OK;
+  DeviceGuard g(h->cfg.device);
+  DDF_CK(cudaDeviceSynchronize());  // no launch may still use the buffers
+  h->tr_segment = segment;
+  h->tr_rows = 0;   // the next training call lays the activation buffers out anew
+  h->fwd_rows = 0;
+  return DDF_OK;
+}
+
+ddf_status ddf_get_train_activation_bytes(ddf_handle h, size_t* out) {
+  if (h == nullptr || out == nullptr) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+  *out = h->tr_store.size() * static_cast<size_t>(h->tr_rows) * h->cfg.width * 2;
   return DDF_OK;
 }
 

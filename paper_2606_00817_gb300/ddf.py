@@ -80,6 +80,8 @@ SIGNATURES = {
                                    _u64, _vp, _vp]),
     "ddf_get_grad": (C.c_int, [_vp, _vp, _sz]),
     "ddf_reset_optimizer": (C.c_int, [_vp]),
+    "ddf_set_recompute": (C.c_int, [_vp, _i32]),
+    "ddf_get_train_activation_bytes": (C.c_int, [_vp, C.POINTER(_sz)]),
     "ddf_cast_scene": (C.c_int, [_vp, _i32, _vp, _i32, _RAYS, _i64, _vp, _vp, _vp]),
     "ddf_sdf_eval": (C.c_int, [_vp, _RAYS, _i64, _vp, _vp]),
     "ddf_sphere_trace": (C.c_int, [_vp, _RAYS, _i64, _i32, C.c_float, C.c_float, _vp, _vp, _vp,
@@ -364,6 +366,16 @@ def ddf_get_grad(h, n: int) -> np.ndarray:
     out = np.empty(n, np.float32)
     _call("ddf_get_grad", h, out.ctypes.data, n)
     return out
+
+
+def ddf_set_recompute(h, segment: int) -> None:
+    _call("ddf_set_recompute", h, int(segment))
+
+
+def ddf_get_train_activation_bytes(h) -> int:
+    out = _sz()
+    _call("ddf_get_train_activation_bytes", h, C.byref(out))
+    return int(out.value)
 
 
 def ddf_reset_optimizer(h) -> None:

@@ -292,3 +292,52 @@ def test_autograd_function_sdf_and_misuse(torch_cuda):
         ddf.ddf_backward(m.h, dz, B - 8)
     ddf.ddf_backward(m.h, dz, B)
     assert ddf.ddf_check_status(m.h) == 0
+
+
+@pytest.mark.parametrize("net,B", [(SMALL, 4096), (PAPER, 4096), (PAPER, 1000)])
+def test_recompute_gives_the_same_gradient(torch_cuda, net, B):
+    """Activation checkpointing: keeping every k-th layer and recomputing the
+    rest in the backward gives the gradient of keeping them all, bit for bit
+    (the sums run in a fixed order, and the forward GEMMs are deterministic),
+    with fewer activation buffers. Also through DDFFunction."""
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    blob = I.xavier_blob(I.NetShape(*net))
+    rays, tt, y = _batch(net, B, seed=43)
+    m = ddf.DDF(*net, precision="bf16")
+    m.load(blob)
+    inputs = _dev(torch, rays.soa())
+    tt_d, y_d = torch.from_numpy(tt).cuda(), torch.from_numpy(y).cuda()
+
+    def grad():
+        loss = torch.zeros(1, device="cuda")
+        ddf.ddf_compute_grad(m.h, inputs, tt_d, y_d, B, loss)
+        return ddf.ddf_get_grad(m.h, blob.size), loss.item()
+
+    g1, l1 = grad()
+    g1b, _ = grad()
+    assert np.array_equal(g1, g1b)                       # deterministic to begin with
+    bytes_all = ddf.ddf_get_train_activation_bytes(m.h)
+    H, W = net[2], net[1]
+    assert bytes_all == H * B * W * 2
+    for seg, kept_plus_scratch in ((2, H // 2 + 1), (3, None), (H, H)):
+        ddf.ddf_set_recompute(m.h, seg)
+        g, l = grad()
+        assert np.array_equal(g, g1) and l == l1, seg
+        nb = ddf.ddf_get_train_activation_bytes(m.h)
+        if kept_plus_scratch is not None:
+            assert nb == kept_plus_scratch * B * W * 2, seg
+        assert nb <= bytes_all
+    # the autograd path with a checkpointed handle equals the one without
+    theta = torch.nn.Parameter(torch.from_numpy(blob).cuda())
+    outs = []
+    for seg in (1, 2):
+        ddf.ddf_set_recompute(m.h, seg)
+        theta.grad = None
+        z = ddf.ddf_function().apply(theta, m, inputs)
+        _torch_loss(torch, z, tt_d, y_d).backward()
+        outs.append(theta.grad.clone())
+    assert torch.equal(outs[0], outs[1])
+    with pytest.raises(ddf.DDFError):
+        ddf.ddf_set_recompute(m.h, 0)
+    assert ddf.ddf_check_status(m.h) == 0
