@@ -31,7 +31,8 @@ events on the launching stream, 3 timed repetitions after warm-up):
                  scene with thin legs, bars and a mug handle; 60,000 flat
                  surface Gaussians stand in for its 3DGS scene; 1,024
                  training views of 128 x 128 rendered to depth by the tile
-                 rasteriser and, on the same rays, cast exactly; one
+                 rasteriser, sphere traced through a neural SDF fitted to the
+                 scene (the paper's mesh-free source) and cast exactly; one
                  hash-grid field distilled from each source with the paper's
                  schedule (30,000 steps of 16,384 rays) and compared on 8
                  training and 8 held-out views with exact targets
@@ -434,6 +435,53 @@ def gs_workload(torch, ddf, dev, local, stream, V=1024, W=128, steps=30000, n_ga
     render_s = (time.perf_counter() - t0) / reps
     rays, t_ex, h_ex, on_thin, near_thin = views(cams, t_gs)
 
+    # the third source of Sec. 3.2: sphere tracing a neural surface fitted to
+    # the scene. Here the network is an SDF MLP (3D Fourier code, L = 8,
+    # 6 x 512) regressed on the closed-form union SDF, half on points uniform
+    # in [-1.2, 1.2]^3, half near the surface (the Gaussians' means plus
+    # N(0, 0.02^2) per axis), then sphere traced on the same camera rays
+    # (<= 128 steps, eps 1e-3, t_max 4)
+    SDF_NET = (8, 512, 6)
+    sdf_steps, SB = 2000, 65536
+    sm = ddf.DDF(*SDF_NET, precision="bf16", device=local, kind="sdf")
+    sm.load(I.xavier_blob_dims(I.sdf_layer_dims(*SDF_NET)))
+    npts = SB * 16
+    uni = I.uniform_points(npts // 2, seed=11)
+    near_idx = np.arange(npts - npts // 2) % len(means)
+    near = means[near_idx].astype(np.float64) + 0.02 * np.stack(
+        [I.gaussian(12, c, npts - npts // 2) for c in range(3)], 1)
+    pts_all = np.concatenate([uni, near])[I.splitmix64(13, 0, npts).argsort()]
+    pts = [torch.from_numpy(np.ascontiguousarray(pts_all[:, c], dtype=np.float32)).to(dev)
+           for c in range(3)]
+    s_t = torch.empty(SB, device=dev)
+    sl = torch.zeros(1, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(sdf_steps):
+        lo = (k % 16) * SB
+        pk = [c[lo:lo + SB] for c in pts]
+        ddf.ddf_union_sdf(sph, ns, box, nb, pk, SB, s_t, stream)
+        lr = 1e-3 * (0.05 + 0.95 * 0.5 * (1 + np.cos(np.pi * k / sdf_steps)))
+        ddf.ddf_sdf_train_step(sm.h, pk, s_t, SB, lr, sl, stream)
+    torch.cuda.synchronize()
+    sdf_train_s = time.perf_counter() - t0
+    t_sdf = torch.empty(n, device=dev)
+    h_sdf = torch.empty(n, dtype=torch.uint8, device=dev)
+    steps_sdf = torch.empty(n, dtype=torch.int32, device=dev)
+    chunk = 1 << 20
+    t0 = time.perf_counter()
+    for lo in range(0, n, chunk):
+        m_ = min(chunk, n - lo)
+        ddf.ddf_sphere_trace(sm.h, [r[lo:lo + m_] for r in rays], m_, 128, 1e-3, 4.0,
+                             t_sdf[lo:lo + m_], h_sdf[lo:lo + m_], steps_sdf[lo:lo + m_], stream)
+    torch.cuda.synchronize()
+    sdf_trace_s = time.perf_counter() - t0
+    sdf_info = {"net": list(SDF_NET), "train_steps": sdf_steps, "batch": SB,
+                "train_seconds": sdf_train_s, "loss_last": float(sl.item()),
+                "trace_seconds": sdf_trace_s,
+                "mean_steps": float(steps_sdf.double().mean().item())}
+    sm.close()
+
     def compare(t_p, hit_p, t_r, hit_r, cls):
         """Hit agreement and |dt| where both hit, per ray class."""
         out = {}
@@ -453,6 +501,10 @@ def gs_workload(torch, ddf, dev, local, stream, V=1024, W=128, steps=30000, n_ga
            "render_s": render_s, "render_pixels_per_s": n / render_s,
            "gs_depth_vs_exact_on_train_views": compare(
                t_gs, h_gs.bool(), t_ex, h_ex.bool(),
+               {"all": allm, "thin": on_thin, "near_thin": near_thin}),
+           "neural_sdf": sdf_info,
+           "neural_sdf_vs_exact_on_train_views": compare(
+               t_sdf, h_sdf.bool(), t_ex, h_ex.bool(),
                {"all": allm, "thin": on_thin, "near_thin": near_thin})}
     # evaluation sets: the first 8 training views (how well each field holds
     # the geometry its supervision showed) and held-out views; exact targets
@@ -465,7 +517,8 @@ def gs_workload(torch, ddf, dev, local, stream, V=1024, W=128, steps=30000, n_ga
     sets["held_out"] = (hrays, ht, hh.bool(), hthin, hnear)
     zone = lambda P: (P[:, 1] > -0.79) & (P[:, 1] < 0.09)      # legs and bars only
     fields = {}
-    for name, (tt, hh_t) in (("gs_depth", (t_gs, h_gs)), ("exact", (t_ex, h_ex))):
+    for name, (tt, hh_t) in (("gs_depth", (t_gs, h_gs)), ("neural_sdf_trace", (t_sdf, h_sdf)),
+                             ("exact", (t_ex, h_ex))):
         m = ddf.DDF(4, 64, 2, precision="bf16", device=local, kind="hashgrid")
         m.load(I.hashgrid_blob(m.n_params, hashgrid_mlp_dims(ddf), seed=0, table_scale=1e-4))
         torch.cuda.synchronize()
