@@ -225,6 +225,26 @@ cudaError_t launch_splitk_reduce(const float* part, int S, int rows, int ldp, in
                                  int cols_out, float* out, int ldo, cudaStream_t s);
 cudaError_t launch_adam(float* w, const float* g, float* m, float* v, int64_t n, float lr,
                         float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s);
+// Adam as above, and in the same pass every copy of the updated weights the
+// next step reads: block j of the blob covers [start, start + rows x cols);
+// a weight block also writes bf16 rows to wb (row stride ldb) and, when wt
+// is set, the bf16 transpose to wt ([cols x rows]); a vector block (rows 1)
+// copies to f32 (FP32). At most kAdamBlocks blocks.
+constexpr int kAdamBlocks = 24;
+struct AdamBlock {
+  int64_t start;
+  int rows, cols, ldb;
+  __nv_bfloat16* wb;
+  __nv_bfloat16* wt;
+  float* f32;
+};
+struct AdamBlocks {
+  int n;
+  AdamBlock b[kAdamBlocks];
+};
+cudaError_t launch_adam_refresh(float* w, const float* g, float* m, float* v, int64_t n, float lr,
+                                float b1, float b2, float eps, float bc1, float bc2,
+                                const AdamBlocks& blocks, cudaStream_t s);
 // dst [K x N] = bf16(src [N x K])^T
 cudaError_t launch_pack_bf16_t(const float* src, int N, int K, __nv_bfloat16* dst, cudaStream_t s);
 cudaError_t launch_cast_scene(const float* spheres, int ns, const float* boxes, int nb,

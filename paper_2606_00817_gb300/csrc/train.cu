@@ -225,6 +225,35 @@ __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, 
   w[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
 }
 
+// Adam plus the refresh of the weights' copies (see launch_adam_refresh).
+// The same arithmetic as adam_kernel, element by element.
+__global__ void adam_refresh_kernel(float* __restrict__ w, const float* __restrict__ g,
+                                    float* __restrict__ m, float* __restrict__ v, int64_t n,
+                                    float lr, float b1, float b2, float eps, float bc1, float bc2,
+                                    const AdamBlocks blocks) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const float wi = w[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+  w[i] = wi;
+  int j = 0;
+  while (j + 1 < blocks.n && i >= blocks.b[j + 1].start) ++j;
+  const AdamBlock& bk = blocks.b[j];
+  const int64_t e = i - bk.start;
+  if (e >= static_cast<int64_t>(bk.rows) * bk.cols) return;
+  if (bk.f32 != nullptr) bk.f32[e] = wi;
+  if (bk.wb != nullptr) {
+    const int64_t r = e / bk.cols, c = e - r * bk.cols;
+    const __nv_bfloat16 hb = __float2bfloat16_rn(wi);
+    bk.wb[r * bk.ldb + c] = hb;
+    if (bk.wt != nullptr) bk.wt[c * bk.rows + r] = hb;
+  }
+}
+
 // dst[k][n] = bf16(src[n][k]): the transposed weight of a [N x K] layer.
 __global__ void pack_bf16_t_kernel(const float* __restrict__ src, int N, int K,
                                    __nv_bfloat16* __restrict__ dst) {
@@ -310,6 +339,15 @@ cudaError_t launch_splitk_reduce(const float* part, int S, int rows, int ldp, in
   const int64_t total = static_cast<int64_t>(rows) * cols_out;
   splitk_reduce_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(
       part, S, rows, ldp, split_stride, cols_out, out, ldo);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam_refresh(float* w, const float* g, float* m, float* v, int64_t n, float lr,
+                                float b1, float b2, float eps, float bc1, float bc2,
+                                const AdamBlocks& blocks, cudaStream_t s) {
+  if (blocks.n < 1 || blocks.n > kAdamBlocks || blocks.b[0].start != 0) return cudaErrorInvalidValue;
+  adam_refresh_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(
+      w, g, m, v, n, lr, b1, b2, eps, bc1, bc2, blocks);
   return cudaGetLastError();
 }
 

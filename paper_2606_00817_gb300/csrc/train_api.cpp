@@ -547,9 +547,32 @@ ddf_status train_step(ddf_s* h, const float* const rays[6], const float* t_targe
   {
     ProfScope ps(h, kProfHead, st);
     h->fwd_rows = 0;  // the weights change
-    DDF_CK(ddf::launch_adam(h->d_blob, h->grad, h->adam_m, h->adam_v,
-                            static_cast<int64_t>(n_params(h)), lr, kB1, kB2, kEps, bc1, bc2, st));
-    if ((s = refresh_weights(h, st)) != DDF_OK) return s;
+    const int W = h->cfg.width, H = h->cfg.hidden_layers;
+    if (2 * H + 2 > ddf::kAdamBlocks) {  // deep nets: Adam, then the copies
+      DDF_CK(ddf::launch_adam(h->d_blob, h->grad, h->adam_m, h->adam_v,
+                              static_cast<int64_t>(n_params(h)), lr, kB1, kB2, kEps, bc1, bc2, st));
+      return refresh_weights(h, st);
+    }
+    // Adam and the refresh of the bf16 copies (W_l, W_l^T), biases and head
+    // in one pass over the blob
+    const BlobOffsets o = blob_offsets(h);
+    ddf::AdamBlocks bl{};
+    auto add = [&](size_t start, int rows, int cols, int ldb, __nv_bfloat16* wb,
+                   __nv_bfloat16* wt, float* f32) {
+      bl.b[bl.n++] = ddf::AdamBlock{static_cast<int64_t>(start), rows, cols, ldb, wb, wt, f32};
+    };
+    for (int l = 0; l < H; ++l) {
+      const int K = l == 0 ? h->d_in : W;
+      __nv_bfloat16* wt = (l > 0 && static_cast<int>(h->wt.size()) > l) ? h->wt[l] : nullptr;
+      add(o.w[l], W, K, l == 0 ? h->kp16 : W, h->wb[l], wt, nullptr);
+      add(o.b[l], 1, W, 0, nullptr, nullptr, h->bias[l]);
+    }
+    const int hr = static_cast<int>(head_rows(h));
+    add(o.wo, 1, hr * W, 0, nullptr, nullptr, h->head_w);
+    add(o.bo, 1, hr, 0, nullptr, nullptr, h->head_b);
+    DDF_CK(ddf::launch_adam_refresh(h->d_blob, h->grad, h->adam_m, h->adam_v,
+                                    static_cast<int64_t>(n_params(h)), lr, kB1, kB2, kEps, bc1, bc2,
+                                    bl, st));
   }
   return DDF_OK;
 }

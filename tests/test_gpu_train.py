@@ -341,3 +341,38 @@ def test_recompute_gives_the_same_gradient(torch_cuda, net, B):
     with pytest.raises(ddf.DDFError):
         ddf.ddf_set_recompute(m.h, 0)
     assert ddf.ddf_check_status(m.h) == 0
+
+
+@pytest.mark.parametrize("net", [SMALL, PAPER])
+def test_copies_after_a_step_match_a_fresh_load(torch_cuda, net):
+    """After an Adam step, every copy the library keeps of the weights (bf16
+    W and W^T, biases, head) equals what a fresh handle derives from the
+    stepped FP32 master weights: queries and the next gradient agree bit for
+    bit."""
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    blob = I.xavier_blob(I.NetShape(*net))
+    rays, tt, y = _batch(net, 2048, seed=44)
+    inputs = _dev(torch, rays.soa())
+    tt_d, y_d = torch.from_numpy(tt).cuda(), torch.from_numpy(y).cuda()
+    a = ddf.DDF(*net, precision="bf16")
+    a.load(blob)
+    for _ in range(2):
+        ddf.ddf_train_step(a.h, inputs, tt_d, y_d, 2048, 1e-3)
+    torch.cuda.synchronize()
+    stepped = ddf.ddf_get_weights(a.h, blob.size)
+    assert not np.array_equal(stepped, blob)
+    b = ddf.DDF(*net, precision="bf16")
+    b.load(stepped)
+    for m in (a, b):
+        ddf.ddf_set_tile(m.h, (256 if net[1] % 256 == 0 else 128, 4, 0, 0, 0), which=0)
+        ddf.ddf_set_tile(m.h, (256 if net[1] % 256 == 0 else 128, 4, 0, 0, 0), which=1)
+    ta, va = a.query(inputs)
+    tb, vb = b.query(inputs)
+    torch.cuda.synchronize()
+    assert torch.equal(ta, tb) and torch.equal(va, vb)
+    ddf.ddf_compute_grad(a.h, inputs, tt_d, y_d, 2048)
+    ga = ddf.ddf_get_grad(a.h, blob.size)
+    ddf.ddf_compute_grad(b.h, inputs, tt_d, y_d, 2048)
+    gb = ddf.ddf_get_grad(b.h, blob.size)
+    assert np.array_equal(ga, gb)
