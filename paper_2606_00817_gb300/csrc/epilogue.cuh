@@ -42,13 +42,14 @@ __device__ __forceinline__ EpiVectors stage_epi_vectors(const TcGemmParams& p, f
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     if (p.bias != nullptr) sb[i] = p.bias[i];
     if (p.col_scale != nullptr) ss[i] = p.col_scale[i];
-    if (p.mode == 1) {  // only the last query layer folds the head
+    if (p.mode == 1 || p.mode == 4) {  // only a last layer folds the head
       s0[i] = p.head_w[i];
       s1[i] = p.head_w[n + i];
     }
   }
-  return EpiVectors{sb, p.col_scale != nullptr ? ss : nullptr, p.mode == 1 ? s0 : nullptr,
-                    p.mode == 1 ? s1 : nullptr};
+  const bool head = p.mode == 1 || p.mode == 4;
+  return EpiVectors{sb, p.col_scale != nullptr ? ss : nullptr, head ? s0 : nullptr,
+                    head ? s1 : nullptr};
 }
 
 __device__ __forceinline__ uint32_t epi_pack_bf16x2(float lo, float hi) {
@@ -316,11 +317,13 @@ __device__ __forceinline__ void epi_row_staged(const TcGemmParams& p, const EpiV
 // staging buffer, as epi_row_staged, plus the layer's ReLU pattern: bit j of
 // relu_bits[row * ldb + column / 32] is set iff output column 32 (column / 32)
 // + j of the row is positive after rounding to bf16 (the test the input
-// gradients apply to this activation).
+// gradients apply to this activation); relu_bits may be null. Mode 4 (the
+// last layer) also folds the stored bf16 outputs into the two head dot
+// products over the thread's columns, in column order (h0, h1).
 __device__ __forceinline__ void epi_row_staged_bits(const TcGemmParams& p, const EpiVectors& ev,
                                                     uint32_t tbase, int warp_row0, int n0,
                                                     int c_begin, int c_end, uint8_t* stage,
-                                                    int lane) {
+                                                    int lane, float& h0, float& h1) {
   const size_t row_bytes = static_cast<size_t>(p.ldo) * 2;
   const int row = warp_row0 + lane;
   const int sw = lane & 7;
@@ -348,13 +351,21 @@ __device__ __forceinline__ void epi_row_staged_bits(const TcGemmParams& p, const
                                   fmaxf(__uint_as_float(v[j + 1]) + bias[j + 1], 0.f));
           m |= ((ow[q] & 0xFFFFu) != 0u ? 1u : 0u) << j;
           m |= ((ow[q] >> 16) != 0u ? 1u : 0u) << (j + 1);
+          if (ev.hw0 != nullptr) {
+            const int col = n0 + 32 * (c + h) + j;
+            const float x0 = __uint_as_float(ow[q] << 16), x1 = __uint_as_float(ow[q] & 0xFFFF0000u);
+            h0 = fmaf(x0, ev.hw0[col], h0);
+            h1 = fmaf(x0, ev.hw1[col], h1);
+            h0 = fmaf(x1, ev.hw0[col + 1], h0);
+            h1 = fmaf(x1, ev.hw1[col + 1], h1);
+          }
         }
         *reinterpret_cast<uint4*>(myrow + (((4 * h + k) ^ sw) << 4)) =
             make_uint4(ow[0], ow[1], ow[2], ow[3]);
       }
       bits[h] = m;
     }
-    if (row < p.M)
+    if (row < p.M && p.relu_bits != nullptr)
       *reinterpret_cast<uint2*>(p.relu_bits + static_cast<size_t>(row) * p.ldb + n0 / 32 + c) =
           make_uint2(bits[0], bits[1]);
     epi_flush_stage(p, stage, warp_row0, row_bytes, static_cast<size_t>(n0 + 32 * c) * 2, lane);

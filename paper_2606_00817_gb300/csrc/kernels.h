@@ -50,7 +50,9 @@ struct TcGemmParams {
   // [K x N] row-major (M / N index contiguous), their maps built with
   // 64 x 64 boxes; lets dW = dZ^T X read dZ [B x W] and X [B x K] as stored
   int mn_major;
-  // training on the pair kernel: mode 0 writes the output's ReLU pattern
+  // training on the pair kernel: mode 4 is mode 0 for the last layer, with
+  // the head partials of mode 1 taken from the stored bf16 outputs;
+  // mode 0 writes the output's ReLU pattern
   // (bit j of relu_bits[row * ldb + c]: column 32 c + j positive), mode 2
   // applies the previous layer's pattern from relu_bits instead of reading
   // `mask`, and writes per 32-row block column sums of its output into
@@ -225,6 +227,9 @@ cudaError_t launch_splitk_reduce(const float* part, int S, int rows, int ldp, in
                                  int cols_out, float* out, int ldo, cudaStream_t s);
 cudaError_t launch_adam(float* w, const float* g, float* m, float* v, int64_t n, float lr,
                         float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s);
+// z[r] = (sum over p < nparts of part[p][r]) + bo, for the two head rows.
+cudaError_t launch_head_sum(const float2* part, int nparts, int64_t M, const float* bo, float2* z,
+                            cudaStream_t s);
 // Adam as above, and in the same pass every copy of the updated weights the
 // next step reads: block j of the blob covers [start, start + rows x cols);
 // a weight block also writes bf16 rows to wb (row stride ldb) and, when wt

@@ -267,8 +267,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * EPI, 1)
                              static_cast<uint32_t>(b * S::BN);
       float h0 = 0.f, h1 = 0.f;
       if constexpr (TRAIN) {
-        if (p.mode == 0)
-          epi_row_staged_bits(p, ev, tbase, row - lane, n0, c0, c1, stage_w, lane);
+        if (p.mode == 0 || p.mode == 4)
+          epi_row_staged_bits(p, ev, tbase, row - lane, n0, c0, c1, stage_w, lane, h0, h1);
         else if (p.mode == 2)
           epi_row_masked_staged(p, tbase, row - lane, n0, c0, c1, stage_w, lane);
         else
@@ -281,7 +281,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * EPI, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(tempty_leader0 + 8u * b);
-      if (p.mode == 1 && row_ok)
+      if ((p.mode == 1 || p.mode == 4) && row_ok)
         p.head_part[(static_cast<size_t>(n_blk) * (EPI / 4) + half) * p.M + row] =
             make_float2(h0, h1);
     }
@@ -382,6 +382,7 @@ cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, bool staged, int epi_
     return cudaErrorInvalidValue;  // every split needs a k-block
   if (p.mn_major && (in_fp8 || p.mode != 3)) return cudaErrorInvalidValue;
   if (p.mode >= 2 && (in_fp8 || out_fp8)) return cudaErrorInvalidValue;
+  if (p.mode == 4 && (p.head_w == nullptr || p.head_part == nullptr)) return cudaErrorInvalidValue;
   if ((p.mode == 2 || p.relu_bits != nullptr) &&
       (p.relu_bits == nullptr || p.ldb < p.N / 32 || p.ldb % 2 != 0 || p.N % 64 != 0 || in_fp8 ||
        out_fp8))

@@ -42,6 +42,20 @@ __global__ void head_train_kernel(const __nv_bfloat16* __restrict__ H, int M, in
   if (lane == 0) z[row] = make_float2(s0 + bo[0], s1 + bo[1]);
 }
 
+// z of each row from the last layer's head partials (in partial order).
+__global__ void head_sum_kernel(const float2* __restrict__ part, int nparts, int64_t M,
+                                const float* __restrict__ bo, float2* __restrict__ z) {
+  const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= M) return;
+  float s0 = 0.f, s1 = 0.f;
+  for (int p = 0; p < nparts; ++p) {
+    const float2 v = part[p * M + r];
+    s0 += v.x;
+    s1 += v.y;
+  }
+  z[r] = make_float2(s0 + bo[0], s1 + bo[1]);
+}
+
 __global__ void count_hits_kernel(const uint8_t* __restrict__ y, int64_t B, unsigned* __restrict__ n) {
   __shared__ unsigned red[32];
   unsigned c = 0;
@@ -287,6 +301,13 @@ __global__ void cast_scene_kernel(const float* __restrict__ spheres, int ns,
 cudaError_t launch_head_train(const __nv_bfloat16* H, int M, int W, const float* wo,
                               const float* bo, float2* z, cudaStream_t s) {
   head_train_kernel<<<(M + 7) / 8, 256, 0, s>>>(H, M, W, wo, bo, z);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_head_sum(const float2* part, int nparts, int64_t M, const float* bo, float2* z,
+                            cudaStream_t s) {
+  if (M <= 0) return cudaSuccess;
+  head_sum_kernel<<<static_cast<unsigned>((M + 255) / 256), 256, 0, s>>>(part, nparts, M, bo, z);
   return cudaGetLastError();
 }
 

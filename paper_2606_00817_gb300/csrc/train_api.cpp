@@ -151,6 +151,8 @@ ddf_status ensure_train(ddf_s* h, int64_t B) {
     dev_free(h, h->tr_lpart);
     dev_free(h, h->tr_colpart);
     h->tr_colpart = nullptr;
+    dev_free(h, h->tr_hz);
+    h->tr_hz = nullptr;
     for (uint32_t* q : h->tr_bits) dev_free(h, q);
     h->tr_bits.assign(H > 1 ? H - 1 : 0, nullptr);
     h->tr_h.assign(H, nullptr);
@@ -189,6 +191,9 @@ ddf_status ensure_train(ddf_s* h, int64_t B) {
         DDF_OK)
       return s;
     h->tr_colpart = static_cast<float*>(p);
+    if ((s = train_alloc(h, &p, static_cast<size_t>(W / 256 + 1) * B * sizeof(float2))) != DDF_OK)
+      return s;
+    h->tr_hz = static_cast<float2*>(p);
     if (h->tr_pair)
       for (auto& q : h->tr_bits) {
         if ((s = train_alloc(h, &p, static_cast<size_t>(B) * (W / 32) * sizeof(uint32_t))) != DDF_OK)
@@ -256,6 +261,11 @@ ddf_status check_train_args(ddf_s* h, const float* const rays[6], const float* t
 // Forward keeping every activation: encoding, the tensor-core layers, the
 // FP32 head into h->tr_z (float2 per row; .y unused for an SDF field).
 // rays: 6 SoA arrays (ray field) or 3 point arrays (SDF field, in rays[0..2]).
+// Whether the last layer's epilogue computes the head (a ray field on the
+// pair path: two head rows from the stored bf16 outputs); otherwise
+// head_train reads the last activation back.
+bool head_in_last_layer(const ddf_s* h) { return h->tr_pair && h->cfg.kind == DDF_KIND_RAY; }
+
 // Forward of layer l over the batch: tr_h[l] = ReLU(tr_h[l-1] W_l^T + b_l)
 // (layer 0 reads the encoding), plus its ReLU bits on the pair path. The
 // GEMMs are deterministic, so a recomputed layer is bitwise the first one.
@@ -274,6 +284,11 @@ ddf_status forward_layer(ddf_s* h, int l, int B, cudaStream_t st) {
   if (h->tr_pair && l < H - 1) {  // the input gradients will test this layer's ReLU pattern
     p.relu_bits = h->tr_bits[l];
     p.ldb = W / 32;
+  }
+  if (head_in_last_layer(h) && l == H - 1) {  // z's partial dot products, per 256 columns
+    p.mode = 4;
+    p.head_w = h->head_w;
+    p.head_part = h->tr_hz;
   }
   return h->tr_pair ? tc_gemm_pair(h, A_in, B, K, h->tmBpair[l], true, p, st)
                     : tc_gemm(h, A_in, B, K, h->tmBtr[l], h->bn, p, st);
@@ -297,7 +312,10 @@ ddf_status forward_keep(ddf_s* h, const float* const rays[6], int B, cudaStream_
     const ddf_status s = forward_layer(h, l, B, st);
     if (s != DDF_OK) return s;
   }
-  DDF_CK(ddf::launch_head_train(bf(h->tr_h[H - 1]), B, W, h->head_w, h->head_b, h->tr_z, st));
+  if (head_in_last_layer(h))
+    DDF_CK(ddf::launch_head_sum(h->tr_hz, W / 256, B, h->head_b, h->tr_z, st));
+  else
+    DDF_CK(ddf::launch_head_train(bf(h->tr_h[H - 1]), B, W, h->head_w, h->head_b, h->tr_z, st));
   return DDF_OK;
 }
 
