@@ -390,6 +390,14 @@ ddf_status ddf_set_recompute(ddf_handle h, int32_t segment);
  * occupy (0 before the first training call). */
 ddf_status ddf_get_train_activation_bytes(ddf_handle h, size_t* out);
 
+/* Test hook for the out-of-memory paths: the (after + 1)-th device
+ * allocation the library makes for a handle from now on (weights,
+ * workspaces, training buffers; process-wide count) fails as if the device
+ * were full, and the hook switches itself off; after < 0 switches it off at
+ * once. The failing call returns DDF_ERR_OOM and releases what it had
+ * allocated, so the handle can repeat the call once memory is available. */
+ddf_status ddf_debug_fail_allocation(int64_t after);
+
 /* Zeroes the Adam moments and step count. */
 ddf_status ddf_reset_optimizer(ddf_handle h);
 

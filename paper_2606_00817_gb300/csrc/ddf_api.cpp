@@ -14,6 +14,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -76,9 +77,19 @@ bool make_tmap(CUtensorMap* m, const void* base, bool one_byte, uint64_t inner, 
 
 namespace ddfi {
 
+// Injected allocation failure (ddf_debug_fail_allocation): the allocation
+// that finds the counter at 0 fails and disables it; -1 = off.
+std::atomic<int64_t> g_fail_alloc_after{-1};
+
 ddf_status dev_alloc(ddf_s* h, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
+  int64_t k = g_fail_alloc_after.load();
+  while (k >= 0 && !g_fail_alloc_after.compare_exchange_weak(k, k - 1)) {
+  }
+  if (k == 0)
+    return fail(DDF_ERR_OOM, "device allocation of " + std::to_string(bytes) +
+                                 " bytes refused (injected failure)");
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -94,6 +105,26 @@ void dev_free(ddf_s* h, void* p) {
   auto it = std::find(h->owned.begin(), h->owned.end(), p);
   if (it != h->owned.end()) h->owned.erase(it);
   cudaFree(p);
+}
+
+// Frees every per-layer weight buffer and the master blob, so that a weight
+// load that failed half way starts from nothing on its next attempt.
+void release_weight_buffers(ddf_s* h) {
+  for (auto* v : {&h->wf, &h->bias, &h->wscale, &h->colscale}) {
+    for (float* q : *v) dev_free(h, q);
+    v->clear();
+  }
+  for (__nv_bfloat16* q : h->wb) dev_free(h, q);
+  for (__nv_bfloat16* q : h->wcal) dev_free(h, q);
+  for (uint8_t* q : h->wq) dev_free(h, q);
+  h->wb.clear();
+  h->wcal.clear();
+  h->wq.clear();
+  dev_free(h, h->head_w);
+  dev_free(h, h->head_b);
+  dev_free(h, h->d_blob);
+  h->head_w = h->head_b = h->d_blob = nullptr;
+  h->loaded = false;
 }
 
 bool valid_config(const ddf_config* c, std::string* why) {
@@ -588,6 +619,11 @@ size_t ddf_param_count(const ddf_config* cfg) {
 
 const char* ddf_last_error(void) { return g_last_error.c_str(); }
 
+ddf_status ddf_debug_fail_allocation(int64_t after) {
+  g_fail_alloc_after.store(after < 0 ? -1 : after);
+  return DDF_OK;
+}
+
 ddf_status ddf_create(const ddf_config* cfg, ddf_handle* out) {
   if (out == nullptr) return fail(DDF_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
@@ -680,7 +716,7 @@ ddf_status ddf_load_weights(ddf_handle h, const float* host_blob, size_t n_float
   const int prec = h->cfg.precision;
   cudaStream_t st = nullptr;
   ddf_status s;
-  if (h->d_blob == nullptr) {
+  auto alloc_buffers = [&]() -> ddf_status {
     void* p;
     if ((s = dev_alloc(h, &p, need * sizeof(float))) != DDF_OK) return s;
     h->d_blob = static_cast<float*>(p);
@@ -735,6 +771,11 @@ ddf_status ddf_load_weights(ddf_handle h, const float* host_blob, size_t n_float
     h->head_w = static_cast<float*>(p);
     if ((s = dev_alloc(h, &p, 4 * sizeof(float))) != DDF_OK) return s;
     h->head_b = static_cast<float*>(p);
+    return DDF_OK;
+  };
+  if (h->d_blob == nullptr && (s = alloc_buffers()) != DDF_OK) {
+    release_weight_buffers(h);  // the next load allocates again from nothing
+    return s;
   }
   DDF_CK(cudaMemcpy(h->d_blob, host_blob, need * sizeof(float), cudaMemcpyHostToDevice));
   size_t off = 0;

@@ -83,7 +83,7 @@ ddf_status hg_load(ddf_s* h, const float* host_blob) {
   const size_t need = hg_param_count(c);
   ddf_status s;
   void* p = nullptr;
-  if (h->d_blob == nullptr) {
+  auto alloc_buffers = [&]() -> ddf_status {
     // the FP32 path reads the blob's tables in place; the bf16 table starts
     // every level on an even entry (8-byte corner pairs)
     h->hg = hg_layout(&h->hg_entries, !f32);
@@ -103,6 +103,16 @@ ddf_status hg_load(ddf_s* h, const float* host_blob) {
       if (per_sm <= 0) return fail(DDF_ERR_UNSUPPORTED, "the hash-grid kernel does not fit an SM");
       h->hg_grid = per_sm * h->num_sms;
     }
+    return DDF_OK;
+  };
+  if (h->d_blob == nullptr && (s = alloc_buffers()) != DDF_OK) {
+    // a failure half way frees everything: the next load starts from nothing
+    for (void** q : {reinterpret_cast<void**>(&h->d_blob), &h->hg_table,
+                     reinterpret_cast<void**>(&h->hg_img), reinterpret_cast<void**>(&h->hg_bias)}) {
+      dev_free(h, *q);
+      *q = nullptr;
+    }
+    return s;
   }
   DDF_CK(cudaMemcpy(h->d_blob, host_blob, need * sizeof(float), cudaMemcpyHostToDevice));
   if (!f32 && (s = hg_refresh(h, nullptr)) != DDF_OK) return s;
@@ -161,7 +171,7 @@ ddf_status hg_ensure_train(ddf_s* h, int64_t B) {
   const size_t np = hg_param_count(h->cfg);
   ddf_status s;
   void* p = nullptr;
-  if (h->grad == nullptr) {
+  auto alloc_state = [&]() -> ddf_status {
     for (float** q : {&h->grad, &h->adam_m, &h->adam_v}) {
       if ((s = dev_alloc(h, &p, np * sizeof(float))) != DDF_OK) return s;
       *q = static_cast<float*>(p);
@@ -177,13 +187,26 @@ ddf_status hg_ensure_train(ddf_s* h, int64_t B) {
     h->tr_cpart = static_cast<float*>(p);
     if ((s = dev_alloc(h, &p, sizeof(unsigned))) != DDF_OK) return s;
     h->tr_nhit = static_cast<unsigned*>(p);
+    return DDF_OK;
+  };
+  if (h->grad == nullptr && (s = alloc_state()) != DDF_OK) {
+    // a failure half way frees everything: the next call starts from nothing
+    for (float** q : {&h->grad, &h->adam_m, &h->adam_v, &h->tr_part, &h->tr_cpart}) {
+      dev_free(h, *q);
+      *q = nullptr;
+    }
+    dev_free(h, h->tr_nhit);
+    h->tr_nhit = nullptr;
+    return s;
   }
   if (B > h->tr_rows) {
     h->fwd_rows = 0;
-    for (void* q : {static_cast<void*>(h->hg_code), static_cast<void*>(h->hg_acts),
-                    static_cast<void*>(h->hg_dpre), static_cast<void*>(h->tr_z),
-                    static_cast<void*>(h->tr_dz), static_cast<void*>(h->tr_lpart)})
-      dev_free(h, q);
+    for (void** q : {reinterpret_cast<void**>(&h->hg_code), reinterpret_cast<void**>(&h->hg_acts),
+                     reinterpret_cast<void**>(&h->hg_dpre), reinterpret_cast<void**>(&h->tr_z),
+                     reinterpret_cast<void**>(&h->tr_dz), reinterpret_cast<void**>(&h->tr_lpart)}) {
+      dev_free(h, *q);
+      *q = nullptr;
+    }
     h->tr_rows = 0;
     const size_t rows = static_cast<size_t>(B);
     if ((s = dev_alloc(h, &p, rows * kW * sizeof(float))) != DDF_OK) return s;

@@ -94,7 +94,9 @@ ddf_status ensure_train(ddf_s* h, int64_t B) {
   const int W = h->cfg.width, H = h->cfg.hidden_layers;
   ddf_status s;
   void* p;
-  if (h->grad == nullptr) {
+  // the optimizer state and the weight copies training needs; a failure
+  // half way frees all of it, so the next call starts from nothing
+  auto alloc_state = [&]() -> ddf_status {
     const size_t np = n_params(h);
     if ((s = train_alloc(h, &p, np * sizeof(float))) != DDF_OK) return s;
     h->grad = static_cast<float*>(p);
@@ -138,21 +140,31 @@ ddf_status ensure_train(ddf_s* h, int64_t B) {
     h->tr_nhit = static_cast<unsigned*>(p);
     if ((s = refresh_weights(h, nullptr)) != DDF_OK) return s;
     DDF_CK(cudaDeviceSynchronize());
+    return DDF_OK;
+  };
+  if (h->grad == nullptr && (s = alloc_state()) != DDF_OK) {
+    for (__nv_bfloat16* q : h->wt) dev_free(h, q);
+    h->wt.clear();
+    for (float** q : {&h->grad, &h->adam_m, &h->adam_v, &h->tr_part, &h->tr_cpart, &h->tr_hpart}) {
+      dev_free(h, *q);
+      *q = nullptr;
+    }
+    dev_free(h, h->tr_nhit);
+    h->tr_nhit = nullptr;
+    return s;
   }
   if (B > h->tr_rows) {
     h->fwd_rows = 0;
-    dev_free(h, h->tr_enc);
+    // every freed pointer is cleared, so a failure below leaves nothing to
+    // free twice on the next attempt
+    for (void** q : {&h->tr_enc, &h->tr_dpre[0], &h->tr_dpre[1], reinterpret_cast<void**>(&h->tr_z),
+                     reinterpret_cast<void**>(&h->tr_dz), reinterpret_cast<void**>(&h->tr_lpart),
+                     reinterpret_cast<void**>(&h->tr_colpart), reinterpret_cast<void**>(&h->tr_hz)}) {
+      dev_free(h, *q);
+      *q = nullptr;
+    }
     for (void* q : h->tr_store) dev_free(h, q);
     h->tr_store.clear();
-    dev_free(h, h->tr_dpre[0]);
-    dev_free(h, h->tr_dpre[1]);
-    dev_free(h, h->tr_z);
-    dev_free(h, h->tr_dz);
-    dev_free(h, h->tr_lpart);
-    dev_free(h, h->tr_colpart);
-    h->tr_colpart = nullptr;
-    dev_free(h, h->tr_hz);
-    h->tr_hz = nullptr;
     for (uint32_t* q : h->tr_bits) dev_free(h, q);
     h->tr_bits.assign(H > 1 ? H - 1 : 0, nullptr);
     h->tr_h.assign(H, nullptr);

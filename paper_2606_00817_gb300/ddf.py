@@ -81,6 +81,7 @@ SIGNATURES = {
     "ddf_get_grad": (C.c_int, [_vp, _vp, _sz]),
     "ddf_reset_optimizer": (C.c_int, [_vp]),
     "ddf_set_recompute": (C.c_int, [_vp, _i32]),
+    "ddf_debug_fail_allocation": (C.c_int, [_i64]),
     "ddf_get_train_activation_bytes": (C.c_int, [_vp, C.POINTER(_sz)]),
     "ddf_cast_scene": (C.c_int, [_vp, _i32, _vp, _i32, _RAYS, _i64, _vp, _vp, _vp]),
     "ddf_sdf_eval": (C.c_int, [_vp, _RAYS, _i64, _vp, _vp]),
@@ -366,6 +367,10 @@ def ddf_get_grad(h, n: int) -> np.ndarray:
     out = np.empty(n, np.float32)
     _call("ddf_get_grad", h, out.ctypes.data, n)
     return out
+
+
+def ddf_debug_fail_allocation(after: int) -> None:
+    _call("ddf_debug_fail_allocation", int(after))
 
 
 def ddf_set_recompute(h, segment: int) -> None:
