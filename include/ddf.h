@@ -390,6 +390,25 @@ ddf_status ddf_set_recompute(ddf_handle h, int32_t segment);
  * occupy (0 before the first training call). */
 ddf_status ddf_get_train_activation_bytes(ddf_handle h, size_t* out);
 
+/* Training checkpoints (resume a distillation run): ddf_save_checkpoint
+ * writes to `path` the field's configuration, its FP32 master weights and,
+ * once it has taken an Adam step, the Adam moments and step count, guarded
+ * by a CRC-32 (the ISO-HDLC / zlib definition) of everything after the
+ * 64-byte header. Layout, little-endian: "DDFCKPT\0", u32 version 1, u32
+ * flags (bit 0: optimizer state), the ddf_config, u64 parameter count, i64
+ * step, u32 CRC, u32 0, then the weights [, m, v] as float arrays in the
+ * blob layout. ddf_load_checkpoint reads one into a handle of the same
+ * configuration (the device field aside): the weights as ddf_load_weights
+ * would, then the optimizer state (or a reset one), so that k steps, a save,
+ * a load into a fresh handle and n - k more steps give the weights of n
+ * steps bit for bit (hash-grid fields: up to the atomics of their table
+ * gradient). Errors: DDF_ERR_INVALID_ARG for a file that cannot be opened,
+ * is not a checkpoint of this version or holds another configuration;
+ * DDF_ERR_BAD_WEIGHTS for a wrong size or CRC (the handle is left as it
+ * was). Synchronous. */
+ddf_status ddf_save_checkpoint(ddf_handle h, const char* path);
+ddf_status ddf_load_checkpoint(ddf_handle h, const char* path);
+
 /* Test hook for the out-of-memory paths: the (after + 1)-th device
  * allocation the library makes for a handle from now on (weights,
  * workspaces, training buffers; process-wide count) fails as if the device

@@ -13,6 +13,9 @@
 // that produces distillation targets lives here too (ddf_cast_scene).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
 
 #include "handle.h"
 #include "kernels.h"
@@ -719,6 +722,128 @@ ddf_status ddf_set_recompute(ddf_handle h, int32_t segment) {
 ddf_status ddf_get_train_activation_bytes(ddf_handle h, size_t* out) {
   if (h == nullptr || out == nullptr) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
   *out = h->tr_store.size() * static_cast<size_t>(h->tr_rows) * h->cfg.width * 2;
+  return DDF_OK;
+}
+
+}  // extern "C"
+
+// ---- training checkpoints -------------------------------------------------
+// File: magic "DDFCKPT" + NUL, u32 version (1), u32 flags (bit 0: optimizer
+// state present), the ddf_config (6 x i32), u64 parameter count, i64 Adam
+// step, u32 CRC-32 of the payload, u32 zero; then the payload: the FP32
+// master weights and, with bit 0, the Adam moments m and v (same layout).
+// Little-endian, as every target of this library is.
+
+namespace {
+
+constexpr char kCkptMagic[8] = {'D', 'D', 'F', 'C', 'K', 'P', 'T', '\0'};
+constexpr uint32_t kCkptVersion = 1;
+
+struct CkptHeader {
+  char magic[8];
+  uint32_t version, flags;
+  ddf_config cfg;
+  uint64_t n_params;
+  int64_t adam_step;
+  uint32_t crc, reserved;
+};
+static_assert(sizeof(CkptHeader) == 64, "checkpoint header layout");
+
+// CRC-32 of the ISO-HDLC / zlib definition: reflected polynomial 0xEDB88320,
+// initial value and final XOR 0xFFFFFFFF.
+uint32_t crc32_update(uint32_t crc, const void* data, size_t n) {
+  static uint32_t table[256];
+  static bool ready = false;
+  if (!ready) {
+    for (uint32_t i = 0; i < 256; ++i) {
+      uint32_t c = i;
+      for (int k = 0; k < 8; ++k) c = (c & 1u) ? (0xEDB88320u ^ (c >> 1)) : (c >> 1);
+      table[i] = c;
+    }
+    ready = true;
+  }
+  const uint8_t* b = static_cast<const uint8_t*>(data);
+  crc = ~crc;
+  for (size_t i = 0; i < n; ++i) crc = table[(crc ^ b[i]) & 0xFFu] ^ (crc >> 8);
+  return ~crc;
+}
+
+bool same_field(const ddf_config& a, const ddf_config& b) {
+  return a.octaves == b.octaves && a.width == b.width && a.hidden_layers == b.hidden_layers &&
+         a.precision == b.precision && a.kind == b.kind;
+}
+
+}  // namespace
+
+extern "C" {
+
+ddf_status ddf_save_checkpoint(ddf_handle h, const char* path) {
+  if (h == nullptr || path == nullptr) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+  if (!h->loaded || h->d_blob == nullptr) return fail(DDF_ERR_BAD_WEIGHTS, "no weights loaded");
+  DeviceGuard g(h->cfg.device);
+  const size_t n = n_params(h);
+  const bool opt = h->adam_m != nullptr && h->adam_v != nullptr && h->adam_step > 0;
+  std::vector<float> payload(n * (opt ? 3 : 1));
+  DDF_CK(cudaDeviceSynchronize());
+  DDF_CK(cudaMemcpy(payload.data(), h->d_blob, n * sizeof(float), cudaMemcpyDeviceToHost));
+  if (opt) {
+    DDF_CK(cudaMemcpy(payload.data() + n, h->adam_m, n * sizeof(float), cudaMemcpyDeviceToHost));
+    DDF_CK(cudaMemcpy(payload.data() + 2 * n, h->adam_v, n * sizeof(float), cudaMemcpyDeviceToHost));
+  }
+  CkptHeader hd{};
+  std::memcpy(hd.magic, kCkptMagic, 8);
+  hd.version = kCkptVersion;
+  hd.flags = opt ? 1u : 0u;
+  hd.cfg = h->cfg;
+  hd.n_params = n;
+  hd.adam_step = opt ? h->adam_step : 0;
+  hd.crc = crc32_update(0, payload.data(), payload.size() * sizeof(float));
+  FILE* f = std::fopen(path, "wb");
+  if (f == nullptr) return fail(DDF_ERR_INVALID_ARG, std::string("cannot open ") + path);
+  const bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1 &&
+                  std::fwrite(payload.data(), sizeof(float), payload.size(), f) == payload.size();
+  const bool closed = std::fclose(f) == 0;
+  if (!ok || !closed) return fail(DDF_ERR_INVALID_ARG, std::string("cannot write ") + path);
+  return DDF_OK;
+}
+
+ddf_status ddf_load_checkpoint(ddf_handle h, const char* path) {
+  if (h == nullptr || path == nullptr) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+  FILE* f = std::fopen(path, "rb");
+  if (f == nullptr) return fail(DDF_ERR_INVALID_ARG, std::string("cannot open ") + path);
+  CkptHeader hd{};
+  const bool got = std::fread(&hd, sizeof(hd), 1, f) == 1;
+  if (!got || std::memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != kCkptVersion) {
+    std::fclose(f);
+    return fail(DDF_ERR_INVALID_ARG, "not a checkpoint of this version");
+  }
+  const size_t n = n_params(h);
+  if (!same_field(hd.cfg, h->cfg) || hd.n_params != n || (hd.flags & ~1u) != 0) {
+    std::fclose(f);
+    return fail(DDF_ERR_INVALID_ARG, "the checkpoint is of another field configuration");
+  }
+  const bool opt = (hd.flags & 1u) != 0;
+  std::vector<float> payload(n * (opt ? 3 : 1));
+  const bool full = std::fread(payload.data(), sizeof(float), payload.size(), f) == payload.size();
+  const bool extra = full && std::fgetc(f) != EOF;
+  std::fclose(f);
+  if (!full || extra) return fail(DDF_ERR_BAD_WEIGHTS, "the checkpoint's size is wrong");
+  if (crc32_update(0, payload.data(), payload.size() * sizeof(float)) != hd.crc)
+    return fail(DDF_ERR_BAD_WEIGHTS, "the checkpoint's CRC-32 does not match");
+  ddf_status s = ddf_load_weights(h, payload.data(), n);
+  if (s != DDF_OK) return s;
+  DeviceGuard g(h->cfg.device);
+  if (opt) {  // the optimizer state, allocated if this handle has not trained yet
+    s = h->cfg.kind == DDF_KIND_HASHGRID ? hg_ensure_train(h, 8) : ensure_train(h, 8);
+    if (s != DDF_OK) return s;
+    DDF_CK(cudaMemcpy(h->adam_m, payload.data() + n, n * sizeof(float), cudaMemcpyHostToDevice));
+    DDF_CK(cudaMemcpy(h->adam_v, payload.data() + 2 * n, n * sizeof(float), cudaMemcpyHostToDevice));
+    h->adam_step = hd.adam_step;
+  } else if (h->adam_m != nullptr) {
+    DDF_CK(cudaMemset(h->adam_m, 0, n * sizeof(float)));
+    DDF_CK(cudaMemset(h->adam_v, 0, n * sizeof(float)));
+    h->adam_step = 0;
+  }
   return DDF_OK;
 }
 

@@ -82,6 +82,8 @@ SIGNATURES = {
     "ddf_reset_optimizer": (C.c_int, [_vp]),
     "ddf_set_recompute": (C.c_int, [_vp, _i32]),
     "ddf_debug_fail_allocation": (C.c_int, [_i64]),
+    "ddf_save_checkpoint": (C.c_int, [_vp, C.c_char_p]),
+    "ddf_load_checkpoint": (C.c_int, [_vp, C.c_char_p]),
     "ddf_get_train_activation_bytes": (C.c_int, [_vp, C.POINTER(_sz)]),
     "ddf_cast_scene": (C.c_int, [_vp, _i32, _vp, _i32, _RAYS, _i64, _vp, _vp, _vp]),
     "ddf_sdf_eval": (C.c_int, [_vp, _RAYS, _i64, _vp, _vp]),
@@ -367,6 +369,14 @@ def ddf_get_grad(h, n: int) -> np.ndarray:
     out = np.empty(n, np.float32)
     _call("ddf_get_grad", h, out.ctypes.data, n)
     return out
+
+
+def ddf_save_checkpoint(h, path) -> None:
+    _call("ddf_save_checkpoint", h, os.fsencode(path))
+
+
+def ddf_load_checkpoint(h, path) -> None:
+    _call("ddf_load_checkpoint", h, os.fsencode(path))
 
 
 def ddf_debug_fail_allocation(after: int) -> None:

@@ -80,3 +80,68 @@ def test_every_allocation_can_fail_and_the_handle_recovers(torch_cuda, kind):
         assert ddf.ddf_check_status(m.h) == 0
         m.close()
     assert failed >= 5
+
+
+@pytest.mark.parametrize("kind", ["ray", "hashgrid"])
+def test_checkpoint_resume_and_corruption(torch_cuda, tmp_path, kind):
+    """k steps, a checkpoint, a fresh handle loading it and n - k more steps
+    give the weights of n steps (bit for bit for the ray field; the hash
+    grid's table gradient sums by atomics). The file's CRC-32 is zlib's; a
+    flipped byte, a truncated file, a foreign magic or configuration are
+    refused with the handle untouched."""
+    import struct
+    import zlib
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    net, blob, inputs, tt, y = _case(torch, kind)
+
+    def steps(m, k):
+        for _ in range(k):
+            ddf.ddf_train_step(m.h, inputs, tt, y, 1000, 1e-3)
+        torch.cuda.synchronize()
+
+    a = ddf.DDF(*net, precision="bf16", kind=kind)
+    a.load(blob)
+    steps(a, 6)
+    w_a = ddf.ddf_get_weights(a.h, blob.size)
+    b = ddf.DDF(*net, precision="bf16", kind=kind)
+    b.load(blob)
+    steps(b, 3)
+    path = tmp_path / "run.ckpt"
+    ddf.ddf_save_checkpoint(b.h, path)
+    raw = path.read_bytes()
+    assert raw[:8] == b"DDFCKPT\0"
+    version, flags = struct.unpack_from("<II", raw, 8)
+    n_params, step = struct.unpack_from("<Qq", raw, 40)
+    crc = struct.unpack_from("<I", raw, 56)[0]
+    assert (version, flags, n_params, step) == (1, 1, blob.size, 3)
+    assert len(raw) == 64 + 3 * 4 * blob.size and zlib.crc32(raw[64:]) == crc
+    c = ddf.DDF(*net, precision="bf16", kind=kind)
+    ddf.ddf_load_checkpoint(c.h, path)
+    steps(c, 3)
+    w_c = ddf.ddf_get_weights(c.h, blob.size)
+    if kind == "ray":
+        assert np.array_equal(w_a, w_c)
+    else:
+        assert np.allclose(w_a, w_c, rtol=1e-5, atol=1e-6)
+    # refusals leave the handle as it was
+    t0, _ = c.query(inputs)
+    bad = bytearray(raw)
+    bad[64 + 4 * 17] ^= 0x40
+    (tmp_path / "flip.ckpt").write_bytes(bytes(bad))
+    (tmp_path / "short.ckpt").write_bytes(raw[:-4])
+    (tmp_path / "magic.ckpt").write_bytes(b"NOTACKPT" + raw[8:])
+    for name, status in (("flip.ckpt", 4), ("short.ckpt", 4), ("magic.ckpt", 1), ("none.ckpt", 1)):
+        with pytest.raises(ddf.DDFError) as e:
+            ddf.ddf_load_checkpoint(c.h, tmp_path / name)
+        assert e.value.status == status, name
+    other = ddf.DDF(4, 64, 3, precision="bf16", kind="hashgrid") if kind == "hashgrid" \
+        else ddf.DDF(6, 128, 3, precision="bf16")
+    with pytest.raises(ddf.DDFError) as e:
+        ddf.ddf_load_checkpoint(other.h, path)
+    assert e.value.status == 1
+    t1, _ = c.query(inputs)
+    torch.cuda.synchronize()
+    assert torch.equal(t0, t1)
+    for m in (a, b, c, other):
+        m.close()
