@@ -360,6 +360,9 @@ ddf_status check_ready(ddf_s* h, int kind = DDF_KIND_RAY) {
 
 ddf_status run_query(ddf_s* h, const float* const rays[6], int64_t n, ddf::HeadOut out,
                      cudaStream_t st) {
+  DDF_REQUIRE_ALIGNED(out.t, 4);
+  DDF_REQUIRE_ALIGNED(out.vis, 4);
+  DDF_REQUIRE_ALIGNED(out.z0, 4);
   const int64_t rows = std::min<int64_t>(n, h->chunk);
   ddf_status s = ensure_workspace(h, rows);
   if (s != DDF_OK) return s;
@@ -538,6 +541,8 @@ ddf_status ddf_sdf_eval(ddf_handle h, const float* const points[3], int64_t n, f
   if (points == nullptr || points[0] == nullptr || points[1] == nullptr || points[2] == nullptr ||
       out_s == nullptr)
     return fail(DDF_ERR_INVALID_ARG, "a pointer is NULL");
+  for (int c = 0; c < 3; ++c) DDF_REQUIRE_ALIGNED(points[c], 4);
+  DDF_REQUIRE_ALIGNED(out_s, 4);
   DeviceGuard g(h->cfg.device);
   const float* as_rays[6] = {points[0], points[1], points[2], points[0], points[1], points[2]};
   ddf::HeadOut o{};
@@ -557,6 +562,8 @@ ddf_status ddf_sphere_trace(ddf_handle h, const float* const rays[6], int64_t n,
       !std::isfinite(t_max))
     return fail(DDF_ERR_INVALID_ARG, "max_steps >= 1, finite eps > 0 and finite t_max >= 0 required");
   if (out_t == nullptr || out_hit == nullptr) return fail(DDF_ERR_INVALID_ARG, "output is NULL");
+  DDF_REQUIRE_ALIGNED(out_t, 4);
+  DDF_REQUIRE_ALIGNED(out_steps, 4);
   DeviceGuard g(h->cfg.device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int W = h->cfg.width, H = h->cfg.hidden_layers, cap = static_cast<int>(n);
@@ -857,6 +864,8 @@ ddf_status ddf_query_rays(ddf_handle h, const float* const rays[6], int64_t n, f
   if ((s = check_rays(rays, n)) != DDF_OK) return s;
   if (n > 0 && (out_t == nullptr || out_vis == nullptr))
     return fail(DDF_ERR_INVALID_ARG, "output pointer is NULL");
+  DDF_REQUIRE_ALIGNED(out_t, 4);
+  DDF_REQUIRE_ALIGNED(out_vis, 4);
   if (n == 0) return DDF_OK;
   DeviceGuard g(h->cfg.device);
   if ((s = ensure_workspace(h, std::min<int64_t>(n, h->chunk))) != DDF_OK) return s;
@@ -877,6 +886,8 @@ ddf_status ddf_query_shadow(ddf_handle h, const float* const rays[6], int64_t n,
   if (light == nullptr) return fail(DDF_ERR_INVALID_ARG, "light is NULL");
   if (n > 0 && (out_t == nullptr || out_vis == nullptr || out_occluded == nullptr))
     return fail(DDF_ERR_INVALID_ARG, "output pointer is NULL");
+  DDF_REQUIRE_ALIGNED(out_t, 4);
+  DDF_REQUIRE_ALIGNED(out_vis, 4);
   if (n == 0) return DDF_OK;
   DeviceGuard g(h->cfg.device);
   if ((s = ensure_workspace(h, std::min<int64_t>(n, h->chunk))) != DDF_OK) return s;
@@ -899,6 +910,9 @@ ddf_status ddf_query_ao(ddf_handle h, const float* const rays[6], int64_t n_rays
   if (n_points < 0) return fail(DDF_ERR_INVALID_ARG, "n_points must be >= 0");
   if (n_points > 0 && (offsets == nullptr || out_hard == nullptr))
     return fail(DDF_ERR_INVALID_ARG, "offsets or out_hard is NULL");
+  DDF_REQUIRE_ALIGNED(offsets, 4);
+  DDF_REQUIRE_ALIGNED(out_hard, 4);
+  DDF_REQUIRE_ALIGNED(out_soft, 4);
   if (n_rays >= (int64_t{1} << 31)) return fail(DDF_ERR_INVALID_ARG, "n_rays must fit int32 offsets");
   if (n_points == 0) return DDF_OK;
   DeviceGuard g(h->cfg.device);
@@ -1459,6 +1473,10 @@ extern "C" ddf_status ddf_render_gi(ddf_handle h, const float* spheres, int32_t 
     return fail(DDF_ERR_INVALID_ARG, "0..1024 spheres and 0..1024 boxes");
   if ((n_spheres > 0 && spheres == nullptr) || (n_boxes > 0 && boxes == nullptr))
     return fail(DDF_ERR_INVALID_ARG, "primitive array is NULL");
+  DDF_REQUIRE_ALIGNED(spheres, 4);
+  DDF_REQUIRE_ALIGNED(boxes, 4);
+  DDF_REQUIRE_ALIGNED(out_shadow, 4);
+  DDF_REQUIRE_ALIGNED(out_ao, 4);
   ddf_status s = DDF_OK;
   if (h != nullptr && (s = check_ready(h)) != DDF_OK) return s;
   ddf::GiCamera cam{};

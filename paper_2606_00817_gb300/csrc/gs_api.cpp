@@ -42,6 +42,10 @@ ddf_status ddf_render_gs_depth(const float* means, const float* covs, const floa
   if (n > 0 && (means == nullptr || covs == nullptr || opacities == nullptr))
     return fail(DDF_ERR_INVALID_ARG, "Gaussian arrays are NULL");
   if (out_t == nullptr || out_hit == nullptr) return fail(DDF_ERR_INVALID_ARG, "outputs are NULL");
+  DDF_REQUIRE_ALIGNED(means, 4);
+  DDF_REQUIRE_ALIGNED(covs, 4);
+  DDF_REQUIRE_ALIGNED(opacities, 4);
+  DDF_REQUIRE_ALIGNED(out_t, 4);
   std::vector<ddf::GiCamera> cams;
   ddf_status s = make_cameras(cameras, n_views, width, height, &cams);
   if (s != DDF_OK) return s;
@@ -91,8 +95,10 @@ ddf_status ddf_render_gs_depth(const float* means, const float* covs, const floa
 ddf_status ddf_camera_rays(const float* cameras, int32_t n_views, int32_t width, int32_t height,
                            float* const rays_out[6], void* stream) {
   if (rays_out == nullptr) return fail(DDF_ERR_INVALID_ARG, "rays_out is NULL");
-  for (int c = 0; c < 6; ++c)
+  for (int c = 0; c < 6; ++c) {
     if (rays_out[c] == nullptr) return fail(DDF_ERR_INVALID_ARG, "a ray array is NULL");
+    DDF_REQUIRE_ALIGNED(rays_out[c], 4);
+  }
   std::vector<ddf::GiCamera> cams;
   ddf_status s = make_cameras(cameras, n_views, width, height, &cams);
   if (s != DDF_OK) return s;
@@ -121,8 +127,11 @@ ddf_status ddf_enter_box(float* const rays[6], float* t, float* out_t_in, int64_
   ddf::RayOut r;
   for (int c = 0; c < 6; ++c) {
     if (rays[c] == nullptr && n > 0) return fail(DDF_ERR_INVALID_ARG, "a ray array is NULL");
+    DDF_REQUIRE_ALIGNED(rays[c], 4);
     r.p[c] = rays[c];
   }
+  DDF_REQUIRE_ALIGNED(t, 4);
+  DDF_REQUIRE_ALIGNED(out_t_in, 4);
   const cudaError_t e =
       ddf::launch_enter_box(r, t, out_t_in, n, half_extent, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "enter box");

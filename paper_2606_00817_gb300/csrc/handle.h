@@ -147,6 +147,14 @@ namespace ddfi {
 ddf_status fail(ddf_status s, const std::string& msg);
 ddf_status cuda_fail(cudaError_t e, const char* what);
 
+// A device pointer that the kernels access a bytes at a time must be a-byte
+// aligned: a misaligned one would fault the GPU, so it is refused here.
+#define DDF_REQUIRE_ALIGNED(ptr, a)                                                   \
+  do {                                                                                \
+    if ((ptr) != nullptr && reinterpret_cast<uintptr_t>(ptr) % (a) != 0)              \
+      return ::ddfi::fail(DDF_ERR_INVALID_ARG, #ptr " must be " #a "-byte aligned"); \
+  } while (0)
+
 // Restores the caller's current device when it goes out of scope.
 struct DeviceGuard {
   int prev = -1;

@@ -266,6 +266,7 @@ ddf_status check_train_args(ddf_s* h, const float* const rays[6], const float* t
     return fail(DDF_ERR_UNSUPPORTED, "training runs on bf16 handles");
   if (batch < 8 || batch % 8 != 0 || batch >= (int64_t{1} << 31))
     return fail(DDF_ERR_INVALID_ARG, "batch must be a positive multiple of 8 below 2^31");
+  DDF_REQUIRE_ALIGNED(t_target, 4);
   ddf_status s = check_rays(rays, batch);
   if (s != DDF_OK) return s;
   if (t_target == nullptr || (kind == DDF_KIND_RAY && hit_target == nullptr))
@@ -494,6 +495,7 @@ ddf_status ddf_compute_grad(ddf_handle h, const float* const rays[6], const floa
                             void* stream) {
   ddf_status s = check_train_args(h, rays, t_target, hit_target, batch);
   if (s != DDF_OK) return s;
+  DDF_REQUIRE_ALIGNED(out_loss, 4);
   DeviceGuard g(h->cfg.device);
   if (is_hashgrid(h)) {
     if ((s = hg_ensure_train(h, batch)) != DDF_OK) return s;
@@ -512,6 +514,7 @@ ddf_status ddf_train_step(ddf_handle h, const float* const rays[6], const float*
                           void* stream) {
   ddf_status s = check_train_args(h, rays, t_target, hit_target, batch);
   if (s != DDF_OK) return s;
+  DDF_REQUIRE_ALIGNED(out_loss, 4);
   return train_step(h, rays, t_target, hit_target, batch, lr, out_loss,
                     static_cast<cudaStream_t>(stream));
 }
@@ -549,6 +552,10 @@ ddf_status ddf_union_sdf(const float* spheres, int32_t n_spheres, const float* b
                 points[2] == nullptr || out_s == nullptr))
     return fail(DDF_ERR_INVALID_ARG, "a pointer is NULL");
   if (n == 0) return DDF_OK;
+  DDF_REQUIRE_ALIGNED(spheres, 4);
+  DDF_REQUIRE_ALIGNED(boxes, 4);
+  for (int c = 0; c < 3; ++c) DDF_REQUIRE_ALIGNED(points[c], 4);
+  DDF_REQUIRE_ALIGNED(out_s, 4);
   DDF_CK(ddf::launch_union_sdf(spheres, n_spheres, boxes, n_boxes, points[0], points[1], points[2],
                                n, out_s, static_cast<cudaStream_t>(stream)));
   return DDF_OK;
@@ -626,6 +633,7 @@ ddf_status ddf_forward_train(ddf_handle h, const float* const inputs[6], int64_t
   ddf_status s = check_train_args(h, p6, &dummy, &ydummy, batch, h->cfg.kind);
   if (s != DDF_OK) return s;
   if (out_z == nullptr) return fail(DDF_ERR_INVALID_ARG, "out_z is NULL");
+  DDF_REQUIRE_ALIGNED(out_z, 4);
   DeviceGuard g(h->cfg.device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (is_hashgrid(h)) {
@@ -652,6 +660,7 @@ ddf_status ddf_forward_train(ddf_handle h, const float* const inputs[6], int64_t
 
 ddf_status ddf_backward(ddf_handle h, const float* dz, int64_t batch, void* stream) {
   if (h == nullptr || dz == nullptr) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+  DDF_REQUIRE_ALIGNED(dz, 4);
   if (h->fwd_rows == 0 || h->fwd_rows != batch)
     return fail(DDF_ERR_INVALID_ARG,
                 "ddf_backward needs the activations of a ddf_forward_train of the same batch, "
@@ -671,6 +680,7 @@ ddf_status ddf_backward(ddf_handle h, const float* dz, int64_t batch, void* stre
 
 ddf_status ddf_copy_grad(ddf_handle h, float* dev_grad, size_t n_floats, void* stream) {
   if (h == nullptr || dev_grad == nullptr) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+  DDF_REQUIRE_ALIGNED(dev_grad, 4);
   if (!h->grad_valid) return fail(DDF_ERR_INVALID_ARG, "no gradient computed yet");
   if (n_floats != n_params(h)) return fail(DDF_ERR_INVALID_ARG, "wrong blob size");
   DeviceGuard g(h->cfg.device);
@@ -682,6 +692,7 @@ ddf_status ddf_copy_grad(ddf_handle h, float* dev_grad, size_t n_floats, void* s
 ddf_status ddf_load_weights_device(ddf_handle h, const float* dev_blob, size_t n_floats,
                                    void* stream) {
   if (h == nullptr || dev_blob == nullptr) return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+  DDF_REQUIRE_ALIGNED(dev_blob, 4);
   if (!h->loaded) return fail(DDF_ERR_BAD_WEIGHTS, "load weights once with ddf_load_weights first");
   if (h->cfg.precision != DDF_BF16 && !is_hashgrid(h))
     return fail(DDF_ERR_UNSUPPORTED, "device weight updates run on bf16 handles");
@@ -870,6 +881,9 @@ ddf_status ddf_cast_scene(const float* spheres, int32_t n_spheres, const float* 
   if (s != DDF_OK) return s;
   if (n > 0 && (out_t == nullptr || out_hit == nullptr))
     return fail(DDF_ERR_INVALID_ARG, "output pointer is NULL");
+  DDF_REQUIRE_ALIGNED(spheres, 4);
+  DDF_REQUIRE_ALIGNED(boxes, 4);
+  DDF_REQUIRE_ALIGNED(out_t, 4);
   ddf::RaySoA r;
   for (int c = 0; c < 6; ++c) r.p[c] = n > 0 ? rays[c] : nullptr;
   DDF_CK(ddf::launch_cast_scene(spheres, n_spheres, boxes, n_boxes, r, n, out_t, out_hit,
@@ -894,9 +908,12 @@ ddf_status ddf_sample_rays(const float* spheres, int32_t n_spheres, const float*
     return fail(DDF_ERR_INVALID_ARG, "surface_frac must be in [0, 1]");
   if (n == 0) return DDF_OK;
   if (rays_out == nullptr) return fail(DDF_ERR_INVALID_ARG, "rays_out is NULL");
+  DDF_REQUIRE_ALIGNED(spheres, 4);
+  DDF_REQUIRE_ALIGNED(boxes, 4);
   ddf::RayOut r;
   for (int c = 0; c < 6; ++c) {
     if (rays_out[c] == nullptr) return fail(DDF_ERR_INVALID_ARG, "a ray array is NULL");
+    DDF_REQUIRE_ALIGNED(rays_out[c], 4);
     r.p[c] = rays_out[c];
   }
   DDF_CK(ddf::launch_sample_rays(spheres, n_spheres, boxes, n_boxes, seed, step, n, surface_frac, r,
@@ -910,9 +927,11 @@ ddf_status ddf_shift_rays(float* const rays[6], float* t, const uint8_t* hit, in
   if (first >= n) return DDF_OK;
   if (rays == nullptr || t == nullptr || hit == nullptr)
     return fail(DDF_ERR_INVALID_ARG, "NULL argument");
+  DDF_REQUIRE_ALIGNED(t, 4);
   ddf::RayOut r;
   for (int c = 0; c < 6; ++c) {
     if (rays[c] == nullptr) return fail(DDF_ERR_INVALID_ARG, "a ray array is NULL");
+    DDF_REQUIRE_ALIGNED(rays[c], 4);
     r.p[c] = rays[c];
   }
   DDF_CK(ddf::launch_shift_rays(r, t, hit, n, first, seed, step, static_cast<cudaStream_t>(stream)));
@@ -928,6 +947,8 @@ ddf_status ddf_distill(ddf_handle h, const float* spheres, int32_t n_spheres, co
     return fail(DDF_ERR_INVALID_ARG, "steps >= 1, lr0 > 0, shift_frac in [0, 1]");
   if (n_spheres > 1024 || n_boxes > 1024)
     return fail(DDF_ERR_INVALID_ARG, "at most 1024 spheres and 1024 boxes");
+  DDF_REQUIRE_ALIGNED(spheres, 4);
+  DDF_REQUIRE_ALIGNED(boxes, 4);
   DeviceGuard g(h->cfg.device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   float* buf = nullptr;  // 6 ray arrays, targets, per-step losses
@@ -980,8 +1001,10 @@ ddf_status ddf_distill_pool(ddf_handle h, const float* const pool[6], const floa
   ddf::RaySoA ps;
   for (int c = 0; c < 6; ++c) {
     if (pool[c] == nullptr) return fail(DDF_ERR_INVALID_ARG, "a pool ray array is NULL");
+    DDF_REQUIRE_ALIGNED(pool[c], 4);
     ps.p[c] = pool[c];
   }
+  DDF_REQUIRE_ALIGNED(pool_t, 4);
   if (batch < 1) return fail(DDF_ERR_INVALID_ARG, "batch must be >= 1");
   DeviceGuard g(h->cfg.device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -145,3 +145,39 @@ def test_checkpoint_resume_and_corruption(torch_cuda, tmp_path, kind):
     assert torch.equal(t0, t1)
     for m in (a, b, c, other):
         m.close()
+
+
+def test_misaligned_device_pointers_are_refused(torch_cuda):
+    """A float array that does not start on a 4-byte boundary would make the
+    kernels fault: every entry point refuses it on the host, before any
+    launch, and the handle stays usable."""
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    net = (6, 128, 3)
+    blob = I.xavier_blob(I.NetShape(*net))
+    m = ddf.DDF(*net, precision="bf16")
+    m.load(blob)
+    n = 64
+    rays = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in I.uniform_rays(n, seed=1).soa()]
+    raw = torch.zeros(4 * n + 16, dtype=torch.uint8, device="cuda")
+    bad = raw.data_ptr() + 2                          # 2 bytes past a 16-byte boundary
+    good_t = torch.empty(n, device="cuda")
+    good_v = torch.empty(n, device="cuda")
+    hit = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    calls = [
+        lambda: ddf.ddf_query_rays(m.h, rays, n, bad, good_v),
+        lambda: ddf.ddf_query_rays(m.h, [bad] + rays[1:], n, good_t, good_v),
+        lambda: ddf.ddf_query_shadow(m.h, rays, n, (3.0, 3.0, 3.0), good_t, bad, hit),
+        lambda: ddf.ddf_train_step(m.h, rays, bad, hit, n, 1e-3),
+        lambda: ddf.ddf_cast_scene(good_t, 1, good_t, 0, rays, n, bad, hit),
+        lambda: ddf.ddf_enter_box(rays, bad, None, n, 1.0),
+        lambda: ddf.ddf_render_gs_depth(bad, good_t, good_t, 1, [[0, 0, -4, 0, 0, 0, 0, 1, 0, 0.7]],
+                                        8, 8, good_t, hit),
+    ]
+    for i, call in enumerate(calls):
+        with pytest.raises(ddf.DDFError) as e:
+            call()
+        assert e.value.status == 1, i
+    t, v = m.query(rays)
+    torch.cuda.synchronize()
+    assert torch.isfinite(t).all() and ddf.ddf_check_status(m.h) == 0
