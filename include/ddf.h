@@ -221,8 +221,11 @@ ddf_status ddf_calibrate_fp8(ddf_handle h, const float* const rays[6], int64_t n
  *       + 0.3 (1/B) sum_i [softplus(z1) - y z1],     t = softplus(z0).
  * Sinusoidal ray fields (bf16 handles only): bf16 activations, FP32 head and
  * loss, gradients from bf16 operands with FP32 accumulation; the handle keeps
- * every activation (2 W bytes per ray and layer, plus the same again for the
- * input gradients and transposes). Hash-grid fields (bf16 or FP32 handles):
+ * every hidden activation (2 W bytes per ray and layer, fewer with
+ * ddf_set_recompute), each layer's ReLU pattern as bits (W/8 bytes per ray
+ * and layer) and two input-gradient buffers (2 W bytes per ray each); the
+ * weight-gradient GEMMs read the stored activations as they lie, so no
+ * transposed copy is made. Hash-grid fields (bf16 or FP32 handles):
  * forward and backward in FP32 on the master weights; the level tables'
  * gradient is a scatter of each ray's feature gradient into its 8 corner
  * entries per level (atomic adds, so its last bits may vary from run to run);

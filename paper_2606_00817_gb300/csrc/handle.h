@@ -103,7 +103,8 @@ struct ddf_s {
   void* tr_dpre[2] = {nullptr, nullptr};  // [B x W] bf16 pre-activation gradients
   float* tr_part = nullptr;               // split-K partials of a weight gradient
   float* tr_cpart = nullptr;              // row-split partials of column sums
-  float* tr_hpart = nullptr;              // [512 x 3 x W] partials of the head's backward
+  float* tr_hpart = nullptr;              // [512 x (3 W + 4)] partials of the head's backward
+  unsigned* tr_ticket = nullptr;          // zeroed counters of the column-sum reductions
   float2* tr_z = nullptr;
   float2* tr_dz = nullptr;
   unsigned* tr_nhit = nullptr;

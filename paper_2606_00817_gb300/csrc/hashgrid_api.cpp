@@ -179,11 +179,12 @@ ddf_status hg_ensure_train(ddf_s* h, int64_t B) {
     DDF_CK(cudaMemset(h->adam_m, 0, np * sizeof(float)));
     DDF_CK(cudaMemset(h->adam_v, 0, np * sizeof(float)));
     h->adam_step = 0;
-    if ((s = dev_alloc(h, &p, static_cast<size_t>(kGradSplits) * kW * kW * sizeof(float))) != DDF_OK)
-      return s;
+    // one slice of partials per weight matrix (H layers and the head), so
+    // that every sum runs in one launch after the last outer product
+    const size_t slices = static_cast<size_t>(H) + 1;
+    if ((s = dev_alloc(h, &p, slices * kGradSplits * kW * kW * sizeof(float))) != DDF_OK) return s;
     h->tr_part = static_cast<float*>(p);
-    if ((s = dev_alloc(h, &p, static_cast<size_t>(kGradSplits) * kW * sizeof(float))) != DDF_OK)
-      return s;
+    if ((s = dev_alloc(h, &p, slices * kGradSplits * kW * sizeof(float))) != DDF_OK) return s;
     h->tr_cpart = static_cast<float*>(p);
     if ((s = dev_alloc(h, &p, sizeof(unsigned))) != DDF_OK) return s;
     h->tr_nhit = static_cast<unsigned*>(p);
@@ -245,21 +246,46 @@ ddf_status hg_backward(ddf_s* h, ddf::RaySoA rays, int B, cudaStream_t st) {
   DDF_CK(cudaMemsetAsync(h->grad, 0, tab * sizeof(float), st));
   DDF_CK(ddf::launch_hg_train_bwd(h->hg_blob, mlp, H, rays, B, h->hg_acts, h->tr_dz, h->hg_dpre,
                                   h->grad, st));
+  // the split partials of weight matrix l go to slice l; the weight and bias
+  // sums of all of them follow in launches of up to kRedJobs sums
+  const size_t pslice = static_cast<size_t>(kGradSplits) * kW * kW;
+  const size_t cslice = static_cast<size_t>(kGradSplits) * kW;
+  std::vector<ddf::RedSplit> sums;
+  auto add_sum = [&](const float* part, int rows, int cols, float* out) {
+    ddf::RedSplit a;
+    a.part = part;
+    a.split_stride = static_cast<int64_t>(rows) * cols;
+    a.S = kGradSplits;
+    a.rows = rows;
+    a.cols = cols;
+    a.ldp = cols;
+    a.ldo = cols;
+    a.out = out;
+    sums.push_back(a);
+  };
   for (int l = 0; l < H; ++l) {
     const float* P = h->hg_dpre + l * act;
     const float* A = l == 0 ? h->hg_code : h->hg_acts + (l - 1) * act;
     const int K = l == 0 ? kCode : kW;
-    DDF_CK(ddf::launch_hg_outer_tiled(P, 1, B, kW, A, 1, B, K, B, kGradSplits, h->tr_part,
-                                      h->tr_cpart, st));
-    DDF_CK(ddf::launch_splitk_reduce(h->tr_part, kGradSplits, kW, K, static_cast<int64_t>(kW) * K, K,
-                                     gmlp + o.w[l], K, st));
-    DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart, kGradSplits, 1, kW, kW, kW, gmlp + o.b[l], kW, st));
+    float* part = h->tr_part + l * pslice;
+    float* cpart = h->tr_cpart + l * cslice;
+    DDF_CK(ddf::launch_hg_outer_tiled(P, 1, B, kW, A, 1, B, K, B, kGradSplits, part, cpart, st));
+    add_sum(part, kW, K, gmlp + o.w[l]);
+    add_sum(cpart, 1, kW, gmlp + o.b[l]);
   }
   const float* dz = reinterpret_cast<const float*>(h->tr_dz);
+  float* part = h->tr_part + H * pslice;
+  float* cpart = h->tr_cpart + H * cslice;
   DDF_CK(ddf::launch_hg_outer_tiled(dz, 2, 1, 2, h->hg_acts + (H - 1) * act, 1, B, kW, B,
-                                    kGradSplits, h->tr_part, h->tr_cpart, st));
-  DDF_CK(ddf::launch_splitk_reduce(h->tr_part, kGradSplits, 2, kW, 2 * kW, kW, gmlp + o.wo, kW, st));
-  DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart, kGradSplits, 1, 2, 2, 2, gmlp + o.bo, 2, st));
+                                    kGradSplits, part, cpart, st));
+  add_sum(part, 2, kW, gmlp + o.wo);
+  add_sum(cpart, 1, 2, gmlp + o.bo);
+  for (size_t j0 = 0; j0 < sums.size(); j0 += ddf::kRedJobs) {
+    ddf::GradReduce g;
+    g.nsplit = static_cast<int>(std::min<size_t>(ddf::kRedJobs, sums.size() - j0));
+    for (int j = 0; j < g.nsplit; ++j) g.split[j] = sums[j0 + j];
+    DDF_CK(ddf::launch_grad_reduce(g, st));
+  }
   h->grad_valid = true;
   return DDF_OK;
 }

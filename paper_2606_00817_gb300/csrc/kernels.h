@@ -119,9 +119,12 @@ cudaError_t launch_tc_gemm(const TcTile& tile, bool in_fp8, bool out_fp8, const 
 int tc_gemm_smem_bytes(int bn, bool in_fp8);
 
 // CTA-pair variant: clusters of 2 CTAs, 256 x 256 output tiles, persistent
-// over `clusters` clusters, 4 or 8 epilogue warps per CTA (training modes:
-// 4). Mode 1 writes (N/256) (epi_warps/4) partials per row; modes 2
-// and 3 (bf16) as the 1-CTA kernel, mode 3 with K-major or MN-major operands.
+// over `clusters` clusters, 4 or 8 epilogue warps per CTA (training modes
+// and the training forward with ReLU bits: kTrainEpiWarps, whatever
+// epi_warps says). Modes 1 and 4 write (N/256) (epi_warps/4) head partials
+// per row; modes 2 and 3 (bf16) as the 1-CTA kernel, mode 3 with K-major or
+// MN-major operands.
+constexpr int kTrainEpiWarps = 4;
 cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, bool staged, int epi_warps,
                                 const CUtensorMap& tmA, const CUtensorMap& tmB,
                                 const TcGemmParams& p, int clusters, cudaStream_t s);
@@ -213,28 +216,65 @@ cudaError_t launch_loss(const float2* z, const float* t_tgt, const uint8_t* y, i
                         unsigned* nhit, float clamp, float lam, float2* dz, float* part,
                         float* loss_out, cudaStream_t s);
 // One pass over H [M x W]: dpre = bf16((dz wo) where H > 0), and per split
-// of rows part [splits x 3 x W]: partials of dz0 H, dz1 H and of dpre's
-// column sums.
+// of rows part [splits x (3 W + 4)]: partials of dz0 H, dz1 H, of dpre's
+// column sums and of dz0, dz1 (each summed over the split's rows in order;
+// the last two columns of a row are padding and are not written).
 cudaError_t launch_head_back_fused(const float2* dz, const __nv_bfloat16* H, int M, int W,
                                   const float* wo, int splits, __nv_bfloat16* dpre, float* part,
                                   cudaStream_t s);
-// part [splits x N]: row-split partial column sums
-cudaError_t launch_colsum_bf16(const __nv_bfloat16* X, int M, int N, int ld, int splits,
-                               float* part, cudaStream_t s);
-cudaError_t launch_colsum_f32(const float* X, int M, int N, int ld, int splits, float* part,
-                              cudaStream_t s);
-cudaError_t launch_splitk_reduce(const float* part, int S, int rows, int ldp, int64_t split_stride,
-                                 int cols_out, float* out, int ldo, cudaStream_t s);
+
+// Gradient reductions in one launch, every sum in a fixed order (the same
+// bits whichever block finishes first).
+// Split sum: out[r ldo + c] = part[0][r][c] + part[1][r][c] + ... (S terms,
+// in split order), r < rows, c < cols, part[q][r][c] at q split_stride +
+// r ldp + c.
+struct RedSplit {
+  const float* part = nullptr;
+  int64_t split_stride = 0;
+  int S = 0, rows = 0, cols = 0, ldp = 0, ldo = 0;
+  float* out = nullptr;
+  int vec = 0;  // set by the launcher: float4 loads and stores
+};
+// Column sums of X [M x N] (FP32, or bf16 with x_bf16), row stride ld: the
+// rows split R ways ([j rps, (j + 1) rps), rps = ceil(M / R)); split j's sum
+// of column c is ((S0 + S1) + S2) + S3 with S_p the sum, in row order, of
+// its rows r0 + p, r0 + p + 4, ...; it goes to cpart[j ldc + c] (ldc >= N
+// rounded up to 4, a multiple of 4; cpart 16-byte aligned); the column's sum
+// is the same phase split over the R partials. Column c is written to
+// out[k][c - c0[k]] for each segment k holding it. ticket: one counter per
+// 256 columns, zero before the launch and after it. X is read 4 columns at a
+// time: ld must be a multiple of 4 and at least N rounded up to 4 (the
+// padding is read, never written out), X 16-byte aligned (8 for bf16).
+constexpr int kRedSegs = 3;
+constexpr int kRedTickets = 128;
+struct RedCols {
+  const void* X = nullptr;  // null: no column sum
+  int x_bf16 = 0, M = 0, N = 0, ld = 0, R = 1, ldc = 0;
+  float* cpart = nullptr;
+  unsigned* ticket = nullptr;
+  int nseg = 0;
+  int c0[kRedSegs] = {}, cnt[kRedSegs] = {};
+  float* out[kRedSegs] = {};
+};
+constexpr int kRedJobs = 8;
+struct GradReduce {
+  int nsplit = 0;
+  RedSplit split[kRedJobs];
+  RedCols cols;
+  int blk0[kRedJobs + 1] = {};  // block offsets of the split jobs (set by the launcher)
+};
+cudaError_t launch_grad_reduce(const GradReduce& g, cudaStream_t s);
 cudaError_t launch_adam(float* w, const float* g, float* m, float* v, int64_t n, float lr,
                         float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s);
 // z[r] = (sum over p < nparts of part[p][r]) + bo, for the two head rows.
 cudaError_t launch_head_sum(const float2* part, int nparts, int64_t M, const float* bo, float2* z,
                             cudaStream_t s);
 // Adam as above, and in the same pass every copy of the updated weights the
-// next step reads: block j of the blob covers [start, start + rows x cols);
-// a weight block also writes bf16 rows to wb (row stride ldb) and, when wt
-// is set, the bf16 transpose to wt ([cols x rows]); a vector block (rows 1)
-// copies to f32 (FP32). At most kAdamBlocks blocks.
+// next step reads: block j of the blob covers [start, start + rows x cols)
+// (the blocks tile [0, n) in order); a weight block also writes bf16 rows to
+// wb (row stride ldb) and, when wt is set (16-byte aligned), the bf16
+// transpose to wt ([cols x rows]); a vector block (rows 1) copies to f32
+// (FP32). At most kAdamBlocks blocks.
 constexpr int kAdamBlocks = 24;
 struct AdamBlock {
   int64_t start;
@@ -242,6 +282,7 @@ struct AdamBlock {
   __nv_bfloat16* wb;
   __nv_bfloat16* wt;
   float* f32;
+  int cta0 = 0;  // first CTA of the block (set by the launcher)
 };
 struct AdamBlocks {
   int n;

@@ -225,8 +225,14 @@ __device__ __forceinline__ uint32_t map_to_cta(uint32_t addr, uint32_t rank) {
   return r;
 }
 
+// Relaxed arrive on a barrier of this cluster. It orders nothing in memory:
+// the callers signal that their tcgen05.ld reads of a TMEM buffer are done
+// (tcgen05.wait::ld has returned and tcgen05.fence::before_thread_sync was
+// issued), which holds by program order before the arrive is issued. A
+// release at cluster scope would also hold the warp until every global store
+// it issued earlier is acknowledged, which nothing on the waiting side reads.
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
                : "memory");
 }
 

@@ -39,8 +39,8 @@ constexpr uint64_t kPairDrainNs = 1000000000ull;
 
 // STAGED: mode-0 outputs go through per-warp shared staging buffers
 // (epi_row_staged); one pipeline stage fewer leaves room for them. EPI:
-// epilogue warps per CTA, 4 (one per TMEM lane quarter) or 8 (two per
-// quarter, each draining half of the tile's columns).
+// epilogue warps per CTA (warps 2..), 4 (one per TMEM lane quarter) or 8
+// (two per quarter, each draining half of the tile's columns).
 template <bool IN_FP8, bool STAGED, int EPI = 4>
 struct PairShape {
   static constexpr int BM = 256;                 // output rows per pair tile
@@ -53,7 +53,8 @@ struct PairShape {
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;  // per CTA
   static constexpr int STAGES = STAGED ? 5 : 6;
   static constexpr int OUT_STAGE_BYTES = STAGED ? EPI * kStageBytesPerWarp : 0;
-  static constexpr int THREADS = 64 + 32 * EPI;
+  static constexpr int EPI_WARP0 = 2;  // first epilogue warp
+  static constexpr int THREADS = 32 * (EPI_WARP0 + EPI);
   static constexpr int TMEM_COLS = 512;
   static constexpr int NUM_BARS = 2 * STAGES + 5;
   static constexpr int CTRL_BYTES = 256;  // barriers, TMEM slot, abort flag, issue counts
@@ -67,7 +68,7 @@ struct PairShape {
 // gradients with K-major or MN-major operands), bf16 only; the query
 // instantiations compile none of it.
 template <bool IN_FP8, bool OUT_FP8, bool STAGED, bool TRAIN, int EPI = 4>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * EPI, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EPI), 1)
     tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                         const __grid_constant__ CUtensorMap tmB, const TcGemmParams p) {
   using S = PairShape<IN_FP8, STAGED, EPI>;
@@ -164,6 +165,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * EPI, 1)
     }
   };
 
+  // Roles: warp 0 lane 0 produces, warp 1 lane 0 of the leader issues the
+  // MMAs, warps EPI_WARP0.. drain the accumulators.
+  if (warp < S::EPI_WARP0) {
   if (warp == 0 && lane == 0) {
     // ---------------------------------------------------------- producer
     uint32_t it = 0;
@@ -238,13 +242,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * EPI, 1)
     if (!ok) raise_abort();
     tc_commit_pair(mdone_bar);
     mbar_wait_bounded(mdone_bar, 0, nullptr, kPairDrainNs);
-  } else if (warp >= 2) {
+  }
+  } else {
     // ---------------------------------------------------------- epilogue (both CTAs)
     const int q = warp & 3;  // TMEM lane quarter this warp may access
-    const int half = EPI == 4 ? 0 : (warp - 2) / 4;
+    const int half = EPI == 4 ? 0 : (warp - S::EPI_WARP0) / 4;
     constexpr int kChunks = S::BN / 32 / (EPI / 4);  // 32-column chunks per warp
     const int c0 = half * kChunks, c1 = c0 + kChunks;
-    uint8_t* const stage_w = smem + S::VEC_OFFSET + epi_vector_bytes(p.N) + (warp - 2) * kStageBytesPerWarp;
+    uint8_t* const stage_w = smem + S::VEC_OFFSET + epi_vector_bytes(p.N) + (warp - S::EPI_WARP0) * kStageBytesPerWarp;
     const int r_local = q * 32 + lane;
     const uint32_t tempty_leader0 = map_to_cta(tempty_bar(0), 0);
     int local = 0;
@@ -390,7 +395,7 @@ cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, bool staged, int epi_
   const int grid = 2 * clusters;
   // training modes, and the training forward that writes ReLU patterns
   if (p.mode >= 2 || p.relu_bits != nullptr)
-    return launch_pair_one<false, false, true, true>(tmA, tmB, p, grid, s);
+    return launch_pair_one<false, false, true, true, kTrainEpiWarps>(tmA, tmB, p, grid, s);
   if (epi_warps == 8) return launch_pair_epi<8>(in_fp8, out_fp8, staged, tmA, tmB, p, grid, s);
   if (epi_warps != 4) return cudaErrorInvalidValue;
   return launch_pair_epi<4>(in_fp8, out_fp8, staged, tmA, tmB, p, grid, s);

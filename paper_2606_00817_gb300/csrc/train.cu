@@ -154,15 +154,18 @@ __global__ void head_back_fused_kernel(const float2* __restrict__ dz, const __nv
   const int s = blockIdx.x;
   const int r0 = s * rows_per_split, r1 = min(M, r0 + rows_per_split);
   float w0[8], w1[8], g0[8], g1[8], cs[8];
+  float zs0 = 0.f, zs1 = 0.f;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     w0[j] = wo[c + j];
     w1[j] = wo[W + c + j];
     g0[j] = g1[j] = cs[j] = 0.f;
   }
-#pragma unroll 4
+#pragma unroll 8
   for (int r = r0; r < r1; ++r) {
     const float2 d = dz[r];
+    zs0 += d.x;
+    zs1 += d.y;
     const uint4 hv = *reinterpret_cast<const uint4*>(H + static_cast<int64_t>(r) * W + c);
     const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
     uint32_t ow[4];
@@ -183,46 +186,130 @@ __global__ void head_back_fused_kernel(const float2* __restrict__ dz, const __nv
     }
     *reinterpret_cast<uint4*>(dpre + static_cast<int64_t>(r) * W + c) = make_uint4(ow[0], ow[1], ow[2], ow[3]);
   }
-  float* ps = part + static_cast<size_t>(s) * 3 * W + c;
+  float* ps = part + static_cast<size_t>(s) * (3 * W + 4) + c;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     ps[j] = g0[j];
     ps[W + j] = g1[j];
     ps[2 * W + j] = cs[j];
   }
+  if (c == 0) {
+    ps[3 * W] = zs0;
+    ps[3 * W + 1] = zs1;
+  }
 }
 
-// part[s][k] = sum over rows of split s of X[r][k] (bf16 or FP32 input).
-template <typename T>
-__device__ __forceinline__ float as_f(T v);
-template <>
-__device__ __forceinline__ float as_f<float>(float v) { return v; }
-template <>
-__device__ __forceinline__ float as_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
-
-template <typename T>
-__global__ void colsum_kernel(const T* __restrict__ X, int M, int N, int ld, int rows_per_split,
-                              float* __restrict__ part) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = blockIdx.y;
-  if (k >= N) return;
-  const int r0 = s * rows_per_split, r1 = min(M, r0 + rows_per_split);
-  float a = 0.f;
-  for (int r = r0; r < r1; ++r) a += as_f<T>(X[static_cast<int64_t>(r) * ld + k]);
-  part[static_cast<size_t>(s) * N + k] = a;
+// Gradient reductions of one launch (see GradReduce). Blocks [blk0[j],
+// blk0[j + 1]) do split-sum job j, four output elements per thread (one
+// float4 when the job is aligned for it); the blocks after them do the
+// column sum, R row splits of each 256-column block, and the last of the R
+// blocks of a column block to finish (an atomic ticket) adds the R partials.
+// A thread of a column block takes 4 columns and every 4th row (or partial)
+// from its phase (0-3); the 4 phase sums are then added in phase order.
+// Every sum runs in a fixed order, so the result does not depend on which
+// block finishes when.
+// Columns col .. col + 3 of one row of the column-sum input (4 aligned
+// columns: the launcher checks the row stride and the base address).
+__device__ __forceinline__ float4 red_cols_load4(const RedCols& cs, int64_t row_off, int col) {
+  if (cs.x_bf16) {
+    const uint2 u =
+        *reinterpret_cast<const uint2*>(static_cast<const __nv_bfloat16*>(cs.X) + row_off + col);
+    return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xFFFF0000u),
+                       __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xFFFF0000u));
+  }
+  return *reinterpret_cast<const float4*>(static_cast<const float*>(cs.X) + row_off + col);
 }
 
-// out[r * ldo + c] = sum_s part[s][r][c] (split order), c < cols_out, part row stride ldp.
-__global__ void splitk_reduce_kernel(const float* __restrict__ part, int S, int rows, int ldp,
-                                     int64_t split_stride, int cols_out, float* __restrict__ out,
-                                     int ldo) {
-  const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= static_cast<int64_t>(rows) * cols_out) return;
-  const int r = static_cast<int>(idx / cols_out);
-  const int c = static_cast<int>(idx - static_cast<int64_t>(r) * cols_out);
-  float a = 0.f;
-  for (int s = 0; s < S; ++s) a += part[s * split_stride + static_cast<int64_t>(r) * ldp + c];
-  out[static_cast<int64_t>(r) * ldo + c] = a;
+__device__ __forceinline__ void add4(float4& a, const float4 b) {
+  a.x += b.x;
+  a.y += b.y;
+  a.z += b.z;
+  a.w += b.w;
+}
+
+__global__ void __launch_bounds__(256) grad_reduce_kernel(const __grid_constant__ GradReduce g) {
+  const int b = blockIdx.x;
+  if (b < g.blk0[g.nsplit]) {
+    int j = 0;
+    while (b >= g.blk0[j + 1]) ++j;
+    const RedSplit& a = g.split[j];
+    const int64_t e0 = 4 * (static_cast<int64_t>(b - g.blk0[j]) * blockDim.x + threadIdx.x);
+    const int64_t total = static_cast<int64_t>(a.rows) * a.cols;
+    if (e0 >= total) return;
+    if (a.vec) {
+      const int r = static_cast<int>(e0 / a.cols);
+      const int c = static_cast<int>(e0 - static_cast<int64_t>(r) * a.cols);
+      const float* src = a.part + static_cast<int64_t>(r) * a.ldp + c;
+      float* dst = a.out + static_cast<int64_t>(r) * a.ldo + c;  // cols, ldp, ldo, split_stride multiples of 4; 16-byte aligned
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+      for (int q = 0; q < a.S; ++q) add4(acc, *reinterpret_cast<const float4*>(src + q * a.split_stride));
+      *reinterpret_cast<float4*>(dst) = acc;
+      return;
+    }
+    for (int k = 0; k < 4 && e0 + k < total; ++k) {  // the 4 elements may span rows
+      const int rk = static_cast<int>((e0 + k) / a.cols);
+      const int ck = static_cast<int>(e0 + k - static_cast<int64_t>(rk) * a.cols);
+      const float* sk = a.part + static_cast<int64_t>(rk) * a.ldp + ck;
+      float acc = 0.f;
+      for (int q = 0; q < a.S; ++q) acc += sk[q * a.split_stride];
+      a.out[static_cast<int64_t>(rk) * a.ldo + ck] = acc;
+    }
+    return;
+  }
+  const RedCols& cs = g.cols;
+  __shared__ float4 ph_sum[4][64];
+  __shared__ int last;
+  const int bb = b - g.blk0[g.nsplit];
+  const int ncb = (cs.N + 255) / 256;
+  const int cb = bb % ncb, j = bb / ncb;
+  const int quad = threadIdx.x & 63, phase = threadIdx.x >> 6;
+  const int col4 = cb * 256 + 4 * quad;  // first of this thread's 4 columns
+  const int col = cb * 256 + static_cast<int>(threadIdx.x);  // column of the phase sum
+  {
+    const int rps = (cs.M + cs.R - 1) / cs.R;
+    const int r0 = j * rps, r1 = min(cs.M, r0 + rps);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (col4 < cs.N) {
+#pragma unroll 4
+      for (int r = r0 + phase; r < r1; r += 4)
+        add4(acc, red_cols_load4(cs, static_cast<int64_t>(r) * cs.ld, col4));
+    }
+    ph_sum[phase][quad] = acc;
+    __syncthreads();
+    if (col < cs.N) {
+      const float* f0 = reinterpret_cast<const float*>(ph_sum[0]);
+      const float* f1 = reinterpret_cast<const float*>(ph_sum[1]);
+      const float* f2 = reinterpret_cast<const float*>(ph_sum[2]);
+      const float* f3 = reinterpret_cast<const float*>(ph_sum[3]);
+      const int t = threadIdx.x;
+      cs.cpart[static_cast<size_t>(j) * cs.ldc + col] = ((f0[t] + f1[t]) + f2[t]) + f3[t];
+    }
+  }
+  __threadfence();  // this thread's partial is visible before the ticket is taken
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&cs.ticket[cb], 1u) == static_cast<unsigned>(cs.R - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (col4 < cs.N) {
+#pragma unroll 4
+    for (int q = phase; q < cs.R; q += 4)
+      add4(acc, __ldcg(reinterpret_cast<const float4*>(cs.cpart + static_cast<size_t>(q) * cs.ldc + col4)));
+  }
+  ph_sum[phase][quad] = acc;
+  __syncthreads();
+  if (col < cs.N) {
+    const int t = threadIdx.x;
+    const float sum = ((reinterpret_cast<const float*>(ph_sum[0])[t] +
+                        reinterpret_cast<const float*>(ph_sum[1])[t]) +
+                       reinterpret_cast<const float*>(ph_sum[2])[t]) +
+                      reinterpret_cast<const float*>(ph_sum[3])[t];
+    for (int k = 0; k < cs.nseg; ++k)
+      if (col >= cs.c0[k] && col < cs.c0[k] + cs.cnt[k]) cs.out[k][col - cs.c0[k]] = sum;
+  }
+  if (threadIdx.x == 0) cs.ticket[cb] = 0u;  // ready for the next launch
 }
 
 // Adam (Kingma & Ba): bias-corrected, no weight decay. bc1 = 1 - b1^t, bc2 = 1 - b2^t.
@@ -239,14 +326,19 @@ __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, 
   w[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
 }
 
-// Adam plus the refresh of the weights' copies (see launch_adam_refresh).
-// The same arithmetic as adam_kernel, element by element.
-__global__ void adam_refresh_kernel(float* __restrict__ w, const float* __restrict__ g,
-                                    float* __restrict__ m, float* __restrict__ v, int64_t n,
-                                    float lr, float b1, float b2, float eps, float bc1, float bc2,
-                                    const AdamBlocks blocks) {
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+// Adam plus the refresh of the weights' copies (see launch_adam_refresh),
+// the same arithmetic as adam_kernel element by element. A CTA takes either
+// 2,048 consecutive elements of a block without a transposed copy, or a
+// tile of 32 rows x 64 columns of one with it: each thread updates 8
+// elements of one column (rows 4 apart), the tile's bf16 values are staged
+// in shared memory by column, and every thread writes 8 consecutive bf16 of
+// one row of the transposed copy, so all stores are whole runs.
+constexpr int kAdamTileR = 32, kAdamTileC = 64, kAdamLinear = 2048;
+
+__device__ __forceinline__ float adam_one(float* __restrict__ w, const float* __restrict__ g,
+                                          float* __restrict__ m, float* __restrict__ v, int64_t i,
+                                          float lr, float b1, float b2, float eps, float bc1,
+                                          float bc2) {
   const float gi = g[i];
   const float mi = b1 * m[i] + (1.f - b1) * gi;
   const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
@@ -254,17 +346,66 @@ __global__ void adam_refresh_kernel(float* __restrict__ w, const float* __restri
   v[i] = vi;
   const float wi = w[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
   w[i] = wi;
+  return wi;
+}
+
+__global__ void __launch_bounds__(256) adam_refresh_kernel(float* __restrict__ w,
+                                                           const float* __restrict__ g,
+                                                           float* __restrict__ m,
+                                                           float* __restrict__ v, float lr, float b1,
+                                                           float b2, float eps, float bc1, float bc2,
+                                                           const __grid_constant__ AdamBlocks blocks) {
+  __shared__ __align__(16) __nv_bfloat16 tile[kAdamTileC][kAdamTileR + 8];
   int j = 0;
-  while (j + 1 < blocks.n && i >= blocks.b[j + 1].start) ++j;
+  while (j + 1 < blocks.n && static_cast<int>(blockIdx.x) >= blocks.b[j + 1].cta0) ++j;
   const AdamBlock& bk = blocks.b[j];
-  const int64_t e = i - bk.start;
-  if (e >= static_cast<int64_t>(bk.rows) * bk.cols) return;
-  if (bk.f32 != nullptr) bk.f32[e] = wi;
-  if (bk.wb != nullptr) {
-    const int64_t r = e / bk.cols, c = e - r * bk.cols;
-    const __nv_bfloat16 hb = __float2bfloat16_rn(wi);
-    bk.wb[r * bk.ldb + c] = hb;
-    if (bk.wt != nullptr) bk.wt[c * bk.rows + r] = hb;
+  const int u = static_cast<int>(blockIdx.x) - bk.cta0;
+  const int64_t count = static_cast<int64_t>(bk.rows) * bk.cols;
+  if (bk.wt == nullptr) {
+    for (int k = 0; k < kAdamLinear / 256; ++k) {
+      const int64_t e = static_cast<int64_t>(u) * kAdamLinear + k * 256 + threadIdx.x;
+      if (e >= count) break;
+      const float wi = adam_one(w, g, m, v, bk.start + e, lr, b1, b2, eps, bc1, bc2);
+      if (bk.f32 != nullptr) bk.f32[e] = wi;
+      if (bk.wb != nullptr) {
+        const int64_t r = e / bk.cols, c = e - r * bk.cols;
+        bk.wb[r * bk.ldb + c] = __float2bfloat16_rn(wi);
+      }
+    }
+    return;
+  }
+  const int ntc = (bk.cols + kAdamTileC - 1) / kAdamTileC;
+  const int r0 = (u / ntc) * kAdamTileR, c0 = (u % ntc) * kAdamTileC;
+  const int cl = threadIdx.x & (kAdamTileC - 1);
+  const int c = c0 + cl;
+#pragma unroll
+  for (int k = 0; k < kAdamTileR / 4; ++k) {
+    const int rl = static_cast<int>(threadIdx.x >> 6) + 4 * k;
+    const int r = r0 + rl;
+    __nv_bfloat16 hb = __float2bfloat16_rn(0.f);
+    if (r < bk.rows && c < bk.cols) {
+      const int64_t e = static_cast<int64_t>(r) * bk.cols + c;
+      const float wi = adam_one(w, g, m, v, bk.start + e, lr, b1, b2, eps, bc1, bc2);
+      hb = __float2bfloat16_rn(wi);
+      if (bk.f32 != nullptr) bk.f32[e] = wi;
+      if (bk.wb != nullptr) bk.wb[static_cast<int64_t>(r) * bk.ldb + c] = hb;
+    }
+    tile[cl][rl] = hb;
+  }
+  __syncthreads();
+  // transposed copy wt [cols x rows]: thread -> column c0 + t / 4, rows
+  // r0 + 8 (t % 4) .. + 7
+  const int tc = c0 + static_cast<int>(threadIdx.x >> 2);
+  const int q = threadIdx.x & 3;
+  const int tr = r0 + 8 * q;
+  if (tc < bk.cols && tr < bk.rows) {
+    __nv_bfloat16* dst = bk.wt + static_cast<int64_t>(tc) * bk.rows + tr;
+    const __nv_bfloat16* src = &tile[threadIdx.x >> 2][8 * q];
+    if (bk.rows % 8 == 0) {  // tr + 8 <= rows, 16-byte aligned
+      *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
+    } else {
+      for (int k = 0; k < 8 && tr + k < bk.rows; ++k) dst[k] = src[k];
+    }
   }
 }
 
@@ -341,34 +482,68 @@ cudaError_t launch_head_back_fused(const float2* dz, const __nv_bfloat16* H, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_colsum_bf16(const __nv_bfloat16* X, int M, int N, int ld, int splits,
-                               float* part, cudaStream_t s) {
-  const int rps = (M + splits - 1) / splits;
-  colsum_kernel<__nv_bfloat16><<<dim3((N + 255) / 256, splits), 256, 0, s>>>(X, M, N, ld, rps, part);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_colsum_f32(const float* X, int M, int N, int ld, int splits, float* part,
-                              cudaStream_t s) {
-  const int rps = (M + splits - 1) / splits;
-  colsum_kernel<float><<<dim3((N + 255) / 256, splits), 256, 0, s>>>(X, M, N, ld, rps, part);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_splitk_reduce(const float* part, int S, int rows, int ldp, int64_t split_stride,
-                                 int cols_out, float* out, int ldo, cudaStream_t s) {
-  const int64_t total = static_cast<int64_t>(rows) * cols_out;
-  splitk_reduce_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(
-      part, S, rows, ldp, split_stride, cols_out, out, ldo);
+cudaError_t launch_grad_reduce(const GradReduce& g0, cudaStream_t s) {
+  GradReduce g = g0;
+  if (g.nsplit < 0 || g.nsplit > kRedJobs) return cudaErrorInvalidValue;
+  auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
+  g.blk0[0] = 0;
+  for (int j = 0; j < g.nsplit; ++j) {
+    RedSplit& a = g.split[j];
+    if (a.part == nullptr || a.out == nullptr || a.S < 1 || a.rows < 0 || a.cols < 1 ||
+        a.ldp < a.cols || a.ldo < a.cols)
+      return cudaErrorInvalidValue;
+    a.vec = a.cols % 4 == 0 && a.ldp % 4 == 0 && a.ldo % 4 == 0 && a.split_stride % 4 == 0 &&
+            al16(a.part) && al16(a.out);
+    const int64_t nb = (static_cast<int64_t>(a.rows) * a.cols + 1023) / 1024;
+    if (g.blk0[j] + nb > (1ll << 30)) return cudaErrorInvalidValue;
+    g.blk0[j + 1] = g.blk0[j] + static_cast<int>(nb);
+  }
+  for (int j = g.nsplit + 1; j <= kRedJobs; ++j) g.blk0[j] = g.blk0[g.nsplit];
+  int64_t blocks = g.blk0[g.nsplit];
+  RedCols& c = g.cols;
+  if (c.X != nullptr) {
+    const int ncb = (c.N + 255) / 256;
+    const int n4 = (c.N + 3) / 4 * 4;
+    if (c.N < 1 || c.M < 0 || c.R < 1 || ncb > kRedTickets || c.cpart == nullptr ||
+        c.ticket == nullptr || c.nseg < 0 || c.nseg > kRedSegs || c.ldc < n4 || c.ldc % 4 != 0 ||
+        !al16(c.cpart) || c.ld < c.N)
+      return cudaErrorInvalidValue;
+    for (int k = 0; k < c.nseg; ++k)
+      if (c.out[k] == nullptr || c.c0[k] < 0 || c.cnt[k] < 0 || c.c0[k] + c.cnt[k] > c.N)
+        return cudaErrorInvalidValue;
+    // whole 4-column loads: rows padded to a multiple of 4 columns, aligned
+    const uintptr_t xa = reinterpret_cast<uintptr_t>(c.X);
+    if (c.ld % 4 != 0 || c.ld < n4 || (xa & (c.x_bf16 ? 7u : 15u)) != 0) return cudaErrorInvalidValue;
+    blocks += static_cast<int64_t>(ncb) * c.R;
+  }
+  if (blocks == 0) return cudaSuccess;
+  if (blocks > (1ll << 31) - 1) return cudaErrorInvalidValue;
+  grad_reduce_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(g);
   return cudaGetLastError();
 }
 
 cudaError_t launch_adam_refresh(float* w, const float* g, float* m, float* v, int64_t n, float lr,
                                 float b1, float b2, float eps, float bc1, float bc2,
-                                const AdamBlocks& blocks, cudaStream_t s) {
-  if (blocks.n < 1 || blocks.n > kAdamBlocks || blocks.b[0].start != 0) return cudaErrorInvalidValue;
-  adam_refresh_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(
-      w, g, m, v, n, lr, b1, b2, eps, bc1, bc2, blocks);
+                                const AdamBlocks& blocks0, cudaStream_t s) {
+  AdamBlocks blocks = blocks0;
+  if (blocks.n < 1 || blocks.n > kAdamBlocks) return cudaErrorInvalidValue;
+  // the blocks tile [0, n) in order; each gets its CTAs
+  int64_t next = 0, ctas = 0;
+  for (int j = 0; j < blocks.n; ++j) {
+    AdamBlock& bk = blocks.b[j];
+    if (bk.start != next || bk.rows < 1 || bk.cols < 1) return cudaErrorInvalidValue;
+    if (bk.wt != nullptr && (reinterpret_cast<uintptr_t>(bk.wt) & 15u) != 0) return cudaErrorInvalidValue;
+    const int64_t count = static_cast<int64_t>(bk.rows) * bk.cols;
+    next += count;
+    bk.cta0 = static_cast<int>(ctas);
+    ctas += bk.wt != nullptr ? static_cast<int64_t>((bk.rows + kAdamTileR - 1) / kAdamTileR) *
+                                   ((bk.cols + kAdamTileC - 1) / kAdamTileC)
+                             : (count + kAdamLinear - 1) / kAdamLinear;
+    if (ctas > (1ll << 30)) return cudaErrorInvalidValue;
+  }
+  if (next != n) return cudaErrorInvalidValue;
+  adam_refresh_kernel<<<static_cast<unsigned>(ctas), 256, 0, s>>>(w, g, m, v, lr, b1, b2, eps, bc1,
+                                                                   bc2, blocks);
   return cudaGetLastError();
 }
 

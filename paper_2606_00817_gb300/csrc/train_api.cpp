@@ -72,6 +72,10 @@ bool kept_layer(const ddf_s* h, int l) {
 
 ddf_status train_alloc(ddf_s* h, void** p, size_t bytes) { return dev_alloc(h, p, bytes); }
 
+// Head partials per row the last training layer leaves (pair kernel, mode 4):
+// one per 256 columns and epilogue warp of a TMEM lane quarter.
+int train_head_parts(int W) { return std::max(1, W / 256) * (ddf::kTrainEpiWarps / 4); }
+
 // Writes the bf16 query copies (W_l, and W_l^T for l >= 1), the biases and
 // the head from the FP32 master blob.
 ddf_status refresh_weights(ddf_s* h, cudaStream_t st) {
@@ -133,14 +137,19 @@ ddf_status ensure_train(ddf_s* h, int64_t B) {
     if ((s = train_alloc(h, &p, kPartSplits * static_cast<size_t>(W) * nmax * sizeof(float))) != DDF_OK)
       return s;
     h->tr_part = static_cast<float*>(p);
-    if ((s = train_alloc(h, &p, kColSplits * 3 * static_cast<size_t>(W) * sizeof(float))) != DDF_OK)
+    if ((s = train_alloc(h, &p, kColSplits * (3 * static_cast<size_t>(W) + 4) * sizeof(float))) !=
+        DDF_OK)
       return s;
     h->tr_cpart = static_cast<float*>(p);
-    if ((s = train_alloc(h, &p, kHeadSplits * 3 * static_cast<size_t>(W) * sizeof(float))) != DDF_OK)
+    if ((s = train_alloc(h, &p, kHeadSplits * (3 * static_cast<size_t>(W) + 4) * sizeof(float))) !=
+        DDF_OK)
       return s;
     h->tr_hpart = static_cast<float*>(p);
     if ((s = train_alloc(h, &p, sizeof(unsigned))) != DDF_OK) return s;
     h->tr_nhit = static_cast<unsigned*>(p);
+    if ((s = train_alloc(h, &p, ddf::kRedTickets * sizeof(unsigned))) != DDF_OK) return s;
+    h->tr_ticket = static_cast<unsigned*>(p);
+    DDF_CK(cudaMemset(h->tr_ticket, 0, ddf::kRedTickets * sizeof(unsigned)));
     if ((s = refresh_weights(h, nullptr)) != DDF_OK) return s;
     DDF_CK(cudaDeviceSynchronize());
     return DDF_OK;
@@ -152,8 +161,10 @@ ddf_status ensure_train(ddf_s* h, int64_t B) {
       dev_free(h, *q);
       *q = nullptr;
     }
-    dev_free(h, h->tr_nhit);
-    h->tr_nhit = nullptr;
+    for (unsigned** q : {&h->tr_nhit, &h->tr_ticket}) {
+      dev_free(h, *q);
+      *q = nullptr;
+    }
     return s;
   }
   if (B > h->tr_rows) {
@@ -206,7 +217,8 @@ ddf_status ensure_train(ddf_s* h, int64_t B) {
         DDF_OK)
       return s;
     h->tr_colpart = static_cast<float*>(p);
-    if ((s = train_alloc(h, &p, static_cast<size_t>(W / 256 + 1) * B * sizeof(float2))) != DDF_OK)
+    if ((s = train_alloc(h, &p, static_cast<size_t>(train_head_parts(W)) * B * sizeof(float2))) !=
+        DDF_OK)
       return s;
     h->tr_hz = static_cast<float2*>(p);
     if (h->tr_pair)
@@ -329,7 +341,7 @@ ddf_status forward_keep(ddf_s* h, const float* const rays[6], int B, cudaStream_
     if (s != DDF_OK) return s;
   }
   if (head_in_last_layer(h))
-    DDF_CK(ddf::launch_head_sum(h->tr_hz, W / 256, B, h->head_b, h->tr_z, st));
+    DDF_CK(ddf::launch_head_sum(h->tr_hz, train_head_parts(W), B, h->head_b, h->tr_z, st));
   else
     DDF_CK(ddf::launch_head_train(bf(h->tr_h[H - 1]), B, W, h->head_w, h->head_b, h->tr_z, st));
   return DDF_OK;
@@ -345,17 +357,34 @@ ddf_status backward_from_dz(ddf_s* h, int B, cudaStream_t st) {
 
   // ---- head: dW_o = dz^T h_H, db_o = sum dz, dpre_H = (dz W_o) where h_H > 0
   // and its column sums (the last layer's bias gradient), in one pass over
-  // h_H; the row-split partials reduce in two deterministic steps
+  // h_H; its row-split partials [dz0 h | dz1 h | dpre | dz0 | dz1 | 2 padding] reduce in
+  // one deterministic launch
   const int hsplits = std::max(1, std::min(kHeadSplits, B / 64));
   DDF_CK(ddf::launch_head_back_fused(h->tr_dz, bf(h->tr_h[H - 1]), B, W, h->head_w, hsplits,
                                      bf(h->tr_dpre[0]), h->tr_hpart, st));
-  DDF_CK(ddf::launch_colsum_f32(h->tr_hpart, hsplits, 3 * W, 3 * W, kColSplits, h->tr_cpart, st));
-  DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart, kColSplits, hr, W, 3 * W, W, h->grad + o.wo, W, st));
-  DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart + 2 * W, kColSplits, 1, W, 3 * W, W,
-                                   h->grad + o.b[H - 1], W, st));
-  DDF_CK(ddf::launch_colsum_f32(reinterpret_cast<const float*>(h->tr_dz), B, 2, 2, kColSplits,
-                                h->tr_cpart, st));
-  DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart, kColSplits, 1, 2, 2, hr, h->grad + o.bo, hr, st));
+  {
+    ddf::GradReduce g;
+    ddf::RedCols& c = g.cols;
+    c.X = h->tr_hpart;
+    c.M = hsplits;
+    c.N = 3 * W + 2;
+    c.ld = 3 * W + 4;
+    c.ldc = 3 * W + 4;
+    c.R = kColSplits;
+    c.cpart = h->tr_cpart;
+    c.ticket = h->tr_ticket;
+    c.nseg = 3;
+    c.c0[0] = 0;          // dW_o rows (hr of them, row-major like the blob)
+    c.cnt[0] = hr * W;
+    c.out[0] = h->grad + o.wo;
+    c.c0[1] = 2 * W;      // the last layer's bias
+    c.cnt[1] = W;
+    c.out[1] = h->grad + o.b[H - 1];
+    c.c0[2] = 3 * W;      // db_o
+    c.cnt[2] = hr;
+    c.out[2] = h->grad + o.bo;
+    DDF_CK(ddf::launch_grad_reduce(g, st));
+  }
 
   // ---- layers, last to first
   int cur = 0;
@@ -425,19 +454,39 @@ ddf_status backward_from_dz(ddf_s* h, int B, cudaStream_t st) {
       else
         DDF_CK(ddf::launch_tc_gemm(ddf::TcTile{bnw, 4}, false, false, tmD, tmX, p, grid, st));
     }
-    DDF_CK(ddf::launch_splitk_reduce(h->tr_part, splits, W, N, static_cast<int64_t>(W) * N, K,
-                                     h->grad + o.w[l], K, st));
-    // bias gradient: column sums of dpre_l, from the 32-row partials the
-    // pair kernel's input-gradient epilogue left (below, one layer up), or
-    // read from dpre_l itself (the top layer, or without the pair kernel)
-    // (the top layer's came with the head's backward)
-    const int nblk = static_cast<int>(round_up(B, 256) / 32);
-    if (l < H - 1) {
-      if (h->tr_pair)
-        DDF_CK(ddf::launch_colsum_f32(h->tr_colpart, nblk, W, W, kColSplits, h->tr_cpart, st));
-      else
-        DDF_CK(ddf::launch_colsum_bf16(bf(h->tr_dpre[cur]), B, W, W, kColSplits, h->tr_cpart, st));
-      DDF_CK(ddf::launch_splitk_reduce(h->tr_cpart, kColSplits, 1, W, W, W, h->grad + o.b[l], W, st));
+    // one launch: dW_l from the split partials, and the bias gradient, the
+    // column sums of dpre_l, from the 32-row partials the pair kernel's
+    // input-gradient epilogue left (below, one layer up), or read from
+    // dpre_l itself without the pair kernel (the top layer's bias came with
+    // the head's backward)
+    {
+      ddf::GradReduce g;
+      g.nsplit = 1;
+      ddf::RedSplit& a = g.split[0];
+      a.part = h->tr_part;
+      a.split_stride = static_cast<int64_t>(W) * N;
+      a.S = splits;
+      a.rows = W;
+      a.cols = K;
+      a.ldp = N;
+      a.ldo = K;
+      a.out = h->grad + o.w[l];
+      if (l < H - 1) {
+        ddf::RedCols& c = g.cols;
+        c.X = h->tr_pair ? static_cast<const void*>(h->tr_colpart) : h->tr_dpre[cur];
+        c.x_bf16 = h->tr_pair ? 0 : 1;
+        c.M = h->tr_pair ? static_cast<int>(round_up(B, 256) / 32) : B;
+        c.N = W;
+        c.ld = W;
+        c.ldc = W;
+        c.R = kColSplits;
+        c.cpart = h->tr_cpart;
+        c.ticket = h->tr_ticket;
+        c.nseg = 1;
+        c.cnt[0] = W;
+        c.out[0] = h->grad + o.b[l];
+      }
+      DDF_CK(ddf::launch_grad_reduce(g, st));
     }
     if (l == 0) break;
     // dpre_{l-1} [B x W] = (dpre_l [B x W]) (W_l^T [W x W])^T masked by h_{l-1} > 0
