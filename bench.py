@@ -790,13 +790,13 @@ def main():
         peak, peak_src = 1700.0, "fallback (1.7 PFLOP/s sustained)"
     achieved = gemm_flops_step * args.steps / (g_ms / 1e3) / 1e12 if g_ms > 0 else None
     # DRAM bytes per activation row of the CTA-pair staged bf16 kernel, from
-    # one ncu capture of a 262,144-row 1280x1280 launch (674.6 MB read +
-    # 633.0 MB written, the summary kept under profiles/); traffic grows with
+    # one ncu capture of a 262,144-row 1280x1280 launch (674.4 MB read +
+    # 632.5 MB written, the summary kept under profiles/); traffic grows with
     # the rows, so a launch of R rows moves about R times this.
     traffic = None
     rows_per_launch = gemm_flops_step * args.steps / g_n / (2.0 * W_ * W_) if g_n else 0
     if tile["hidden"] == "256x4pairstaged" and args.precision == "bf16":
-        traffic = rows_per_launch * (1307.6e6 / 262144)
+        traffic = rows_per_launch * (1306.9e6 / 262144)
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "traffic_unit": "DRAM bytes per launch (ncu dram__bytes_read+write, scaled "
