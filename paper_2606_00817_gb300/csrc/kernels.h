@@ -264,6 +264,8 @@ struct GradReduce {
   int blk0[kRedJobs + 1] = {};  // block offsets of the split jobs (set by the launcher)
 };
 cudaError_t launch_grad_reduce(const GradReduce& g, cudaStream_t s);
+// Adam (Kingma & Ba, bias-corrected with bc1 = 1 - b1^t, bc2 = 1 - b2^t, no
+// weight decay) on n parameters: m, v and w updated in place.
 cudaError_t launch_adam(float* w, const float* g, float* m, float* v, int64_t n, float lr,
                         float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s);
 // z[r] = (sum over p < nparts of part[p][r]) + bo, for the two head rows.

@@ -312,18 +312,44 @@ __global__ void __launch_bounds__(256) grad_reduce_kernel(const __grid_constant_
   if (threadIdx.x == 0) cs.ticket[cb] = 0u;  // ready for the next launch
 }
 
-// Adam (Kingma & Ba): bias-corrected, no weight decay. bc1 = 1 - b1^t, bc2 = 1 - b2^t.
+// One Adam update (Kingma & Ba): bias-corrected, no weight decay,
+// bc1 = 1 - b1^t, bc2 = 1 - b2^t; m and v are updated in place, the new
+// weight is returned. The fused multiply-adds are written out, so every
+// kernel that calls this rounds the same way.
+__device__ __forceinline__ float adam_elem(float w, float g, float& m, float& v, float lr, float b1,
+                                           float b2, float eps, float bc1, float bc2) {
+  m = fmaf(b1, m, (1.f - b1) * g);
+  v = fmaf(b2, v, (1.f - b2) * g * g);
+  return w - lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+}
+
+// Adam over n parameters, 4 per thread (one float4 of each array when vec:
+// all four arrays 16-byte aligned).
 __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
                             float* __restrict__ v, int64_t n, float lr, float b1, float b2,
-                            float eps, float bc1, float bc2) {
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float gi = g[i];
-  const float mi = b1 * m[i] + (1.f - b1) * gi;
-  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-  m[i] = mi;
-  v[i] = vi;
-  w[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+                            float eps, float bc1, float bc2, int vec) {
+  const int64_t i4 = 4 * (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
+  if (i4 >= n) return;
+  if (vec && i4 + 4 <= n) {
+    float4 W = *reinterpret_cast<const float4*>(w + i4);
+    const float4 G = *reinterpret_cast<const float4*>(g + i4);
+    float4 M = *reinterpret_cast<const float4*>(m + i4);
+    float4 V = *reinterpret_cast<const float4*>(v + i4);
+    W.x = adam_elem(W.x, G.x, M.x, V.x, lr, b1, b2, eps, bc1, bc2);
+    W.y = adam_elem(W.y, G.y, M.y, V.y, lr, b1, b2, eps, bc1, bc2);
+    W.z = adam_elem(W.z, G.z, M.z, V.z, lr, b1, b2, eps, bc1, bc2);
+    W.w = adam_elem(W.w, G.w, M.w, V.w, lr, b1, b2, eps, bc1, bc2);
+    *reinterpret_cast<float4*>(m + i4) = M;
+    *reinterpret_cast<float4*>(v + i4) = V;
+    *reinterpret_cast<float4*>(w + i4) = W;
+    return;
+  }
+  for (int64_t i = i4; i < i4 + 4 && i < n; ++i) {
+    float mi = m[i], vi = v[i];
+    w[i] = adam_elem(w[i], g[i], mi, vi, lr, b1, b2, eps, bc1, bc2);
+    m[i] = mi;
+    v[i] = vi;
+  }
 }
 
 // Adam plus the refresh of the weights' copies (see launch_adam_refresh),
@@ -339,12 +365,10 @@ __device__ __forceinline__ float adam_one(float* __restrict__ w, const float* __
                                           float* __restrict__ m, float* __restrict__ v, int64_t i,
                                           float lr, float b1, float b2, float eps, float bc1,
                                           float bc2) {
-  const float gi = g[i];
-  const float mi = b1 * m[i] + (1.f - b1) * gi;
-  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  float mi = m[i], vi = v[i];
+  const float wi = adam_elem(w[i], g[i], mi, vi, lr, b1, b2, eps, bc1, bc2);
   m[i] = mi;
   v[i] = vi;
-  const float wi = w[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
   w[i] = wi;
   return wi;
 }
@@ -549,8 +573,12 @@ cudaError_t launch_adam_refresh(float* w, const float* g, float* m, float* v, in
 
 cudaError_t launch_adam(float* w, const float* g, float* m, float* v, int64_t n, float lr,
                         float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s) {
-  adam_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(w, g, m, v, n, lr, b1, b2, eps,
-                                                                    bc1, bc2);
+  if (n <= 0) return cudaSuccess;
+  const uintptr_t a = reinterpret_cast<uintptr_t>(w) | reinterpret_cast<uintptr_t>(g) |
+                      reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v);
+  const int64_t threads = (n + 3) / 4;
+  adam_kernel<<<static_cast<unsigned>((threads + 255) / 256), 256, 0, s>>>(
+      w, g, m, v, n, lr, b1, b2, eps, bc1, bc2, (a & 15u) == 0 ? 1 : 0);
   return cudaGetLastError();
 }
 
