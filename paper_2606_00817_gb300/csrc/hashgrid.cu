@@ -372,9 +372,9 @@ __global__ void __launch_bounds__(kHgF32Rays)
 // Backward of one ray (FP32): from dL/dz through the head and the hidden
 // layers (ReLU masks from the stored activations), storing every dL/dpre
 // (feature-major, [H x 64 x B]) for the weight gradients, then the hash features' gradient scattered into the
-// level tables' gradient (blob layout): each corner entry receives its
-// trilinear weight times the feature gradient (atomic adds; entries shared by
-// several rays or corners sum up).
+// level tables' gradient (blob layout, 8-byte aligned): each corner entry
+// receives its trilinear weight times the feature gradient (atomic adds;
+// entries shared by several rays or corners sum up).
 __global__ void __launch_bounds__(kHgF32Rays)
     hg_train_bwd_kernel(const HashGridParams g, const float* __restrict__ mlp, int H, RaySoA rays,
                         int64_t M, const float* __restrict__ acts, const float2* __restrict__ dz,
@@ -447,8 +447,8 @@ __global__ void __launch_bounds__(kHgF32Rays)
       const float w = ((c & 1) ? wx : 1.f - wx) * (((c >> 1) & 1) ? wy : 1.f - wy) *
                       ((c >> 2) ? wz : 1.f - wz);
       const uint32_t e = g.offset[l] + hg_index(g, l, ix + (c & 1), iy + ((c >> 1) & 1), iz + (c >> 2));
-      atomicAdd(grad_table + 2 * static_cast<int64_t>(e), w * g0);
-      atomicAdd(grad_table + 2 * static_cast<int64_t>(e) + 1, w * g1);
+      // one 8-byte vector add for the entry's two features
+      atomicAdd(reinterpret_cast<float2*>(grad_table) + e, make_float2(w * g0, w * g1));
     }
   }
 }
@@ -644,6 +644,7 @@ cudaError_t launch_hg_train_bwd(const HashGridParams& g, const float* mlp, int H
                                 float* grad_table, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
   if (H < 1 || H > 4) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(grad_table) & 7u) != 0) return cudaErrorInvalidValue;
   const size_t smem = hg_f32_smem(H);
   cudaError_t e = cudaFuncSetAttribute(hg_train_bwd_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
