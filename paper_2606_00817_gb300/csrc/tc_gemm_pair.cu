@@ -17,7 +17,8 @@
 //               leader's producer arms it with the bytes of both halves
 //   empty[s]    (each CTA) the leader's commit multicasts "stage s consumed"
 //   tfull[b]    (each CTA) the leader's commit multicasts "accumulator b ready"
-//   tempty[b]   (leader) 4 epilogue warps of each CTA arrive: "b drained"
+//   tempty[b]   (leader) every epilogue warp of both CTAs arrives (relaxed:
+//               its TMEM reads are complete): "b drained"
 // Every wait is bounded. A timeout raises the abort flag of both CTAs and a
 // status bit. At teardown both producers publish how many stages they issued;
 // after a cluster barrier the one that issued fewer copies the missing stage
