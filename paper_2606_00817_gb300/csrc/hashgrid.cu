@@ -291,17 +291,12 @@ __global__ void __launch_bounds__(kHgRows, 4)  // 4 CTAs per SM: 128 registers
 constexpr int kHgF32Rays = 64;  // rays per block
 constexpr int kHgLd = kHgW + 1; // per-thread row stride in shared memory
 
-// Thread = ray: code and activations in a per-thread shared-memory row,
-// weights broadcast from shared memory, FFMA only. The training variant also
-// stores the code, every hidden activation and z; code and activations are
-// feature-major ([64 x B] and [H x 64 x B]) so that a warp's stores of one
-// feature cover 32 consecutive rays.
-template <bool TRAIN>
+// Queries, thread = ray: code and activations in a per-thread shared-memory
+// row, weights broadcast from shared memory, FFMA only.
 __global__ void __launch_bounds__(kHgF32Rays)
     hashgrid_f32_kernel(const HashGridParams g, const float2* __restrict__ table,
                         const float* __restrict__ mlp, int H, RaySoA rays, int64_t M,
-                        HeadOut out, float* __restrict__ code_out, float* __restrict__ acts,
-                        float2* __restrict__ z_out) {
+                        HeadOut out) {
   extern __shared__ float fsm[];
   const int n_mlp = kHgW * kHgCode + kHgW + (H - 1) * (kHgW * kHgW + kHgW) + 2 * kHgW + 2;
   float* sw = fsm;
@@ -323,9 +318,6 @@ __global__ void __launch_bounds__(kHgF32Rays)
   hg_dir_code(rays.p[3][row], rays.p[4][row], rays.p[5][row], dcode);
 #pragma unroll
   for (int k = 0; k < 27; ++k) a[32 + k] = dcode[k];
-  if constexpr (TRAIN) {
-    for (int k = 0; k < kHgW; ++k) code_out[k * M + row] = k < kHgCode ? a[k] : 0.f;
-  }
   const float* w = sw;
   int K = kHgCode;
   for (int l = 0; l < H; ++l) {
@@ -345,10 +337,6 @@ __global__ void __launch_bounds__(kHgF32Rays)
       nb[n + 2] = fmaxf(s2 + b[n + 2], 0.f);
       nb[n + 3] = fmaxf(s3 + b[n + 3], 0.f);
     }
-    if constexpr (TRAIN) {
-      float* dst = acts + static_cast<int64_t>(l) * kHgW * M + row;
-      for (int n = 0; n < kHgW; ++n) dst[n * M] = nb[n];
-    }
     float* t = a;
     a = nb;
     nb = t;
@@ -362,20 +350,127 @@ __global__ void __launch_bounds__(kHgF32Rays)
   }
   z0 += w[2 * kHgW];
   z1 += w[2 * kHgW + 1];
-  if constexpr (TRAIN) {
+  write_heads(out, row, z0, z1);
+}
+
+// ---------------------------------------------------------------- training
+// Training forward and backward with 4 threads per ray (64 rays, 256
+// threads per block): at the batch sizes of a distillation step (16,384
+// rays) one thread per ray leaves 3-4 warps per SM, every table gather and
+// atomic waiting out its full latency. Thread t of a ray takes levels t,
+// t + 4, t + 8, t + 12 and outputs (or input gradients) t + 4 q; each output
+// is still summed over its inputs in order, so the values are those of one
+// thread per ray. The ray's rows live in shared memory as in the query
+// kernel; __syncwarp orders the 4 threads of a ray (same warp). Threads of
+// rays past the end stay to the end (they take part in __syncwarp) and skip
+// every load and store of their row.
+constexpr int kHgTrainT = 4;
+constexpr int kHgTrainThreads = kHgF32Rays * kHgTrainT;
+
+// Forward weight rows in shared memory: odd strides (59, 65), so that the
+// 4 threads of a ray, reading rows t + 4 q of one column, hit 4 banks.
+__host__ __device__ constexpr int hg_train_ldw(int l) { return l == 0 ? kHgCode : kHgW + 1; }
+__host__ __device__ constexpr int hg_train_wfloats(int H) {
+  return kHgW * hg_train_ldw(0) + kHgW + (H - 1) * (kHgW * hg_train_ldw(1) + kHgW) + 2 * kHgW + 2;
+}
+
+__global__ void __launch_bounds__(kHgTrainThreads)
+    hg_train_fwd_kernel(const HashGridParams g, const float2* __restrict__ table,
+                        const float* __restrict__ mlp, int H, RaySoA rays, int64_t M,
+                        float* __restrict__ code_out, float* __restrict__ acts,
+                        float2* __restrict__ z_out) {
+  extern __shared__ float fsm[];
+  float* sw = fsm;
+  float* bufA = fsm + ((hg_train_wfloats(H) + 3) & ~3);
+  float* bufB = bufA + kHgF32Rays * kHgLd;
+  {  // weights: blob layout (W_l [64 x K_l], b_l, ..., W_o [2 x 64], b_o) -> padded rows
+    int src = 0, dst = 0;
+    for (int l = 0; l < H; ++l) {
+      const int K = l == 0 ? kHgCode : kHgW, ldw = hg_train_ldw(l);
+      for (int i = threadIdx.x; i < kHgW * K; i += blockDim.x)
+        sw[dst + (i / K) * ldw + i % K] = mlp[src + i];
+      src += kHgW * K;
+      dst += kHgW * ldw;
+      for (int i = threadIdx.x; i < kHgW; i += blockDim.x) sw[dst + i] = mlp[src + i];
+      src += kHgW;
+      dst += kHgW;
+    }
+    for (int i = threadIdx.x; i < 2 * kHgW + 2; i += blockDim.x) sw[dst + i] = mlp[src + i];
+  }
+  __syncthreads();
+  const int r = threadIdx.x >> 2, t = threadIdx.x & 3;
+  const int64_t row = static_cast<int64_t>(blockIdx.x) * kHgF32Rays + r;
+  const bool valid = row < M;
+  float* a = bufA + r * kHgLd;
+  float* nb = bufB + r * kHgLd;
+  if (valid) {
+    const float x = box01(rays.p[0][row]), y = box01(rays.p[1][row]), z = box01(rays.p[2][row]);
+    auto fetch = [&](uint32_t e0, uint32_t e1, float2& v0, float2& v1) {
+      v0 = __ldg(table + e0);
+      v1 = __ldg(table + e1);
+    };
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int l = t + 4 * j;
+      hg_level(g, l, x, y, z, fetch, a[2 * l], a[2 * l + 1]);
+    }
+    if (t == 0) {
+      float dcode[27];
+      hg_dir_code(rays.p[3][row], rays.p[4][row], rays.p[5][row], dcode);
+#pragma unroll
+      for (int k = 0; k < 27; ++k) a[32 + k] = dcode[k];
+    }
+  }
+  __syncwarp();
+  if (valid)
+    for (int k = t; k < kHgW; k += kHgTrainT) code_out[k * M + row] = k < kHgCode ? a[k] : 0.f;
+  const float* w = sw;
+  int K = kHgCode;
+  for (int l = 0; l < H; ++l) {
+    const int ldw = hg_train_ldw(l);
+    const float* b = w + kHgW * ldw;
+    float sacc[kHgW / kHgTrainT];
+#pragma unroll
+    for (int q = 0; q < kHgW / kHgTrainT; ++q) sacc[q] = 0.f;
+    for (int k = 0; k < K; ++k) {
+      const float av = a[k];
+#pragma unroll
+      for (int q = 0; q < kHgW / kHgTrainT; ++q)
+        sacc[q] = fmaf(av, w[(t + kHgTrainT * q) * ldw + k], sacc[q]);
+    }
+    float* dst = acts + static_cast<int64_t>(l) * kHgW * M + row;
+#pragma unroll
+    for (int q = 0; q < kHgW / kHgTrainT; ++q) {
+      const int n = t + kHgTrainT * q;
+      const float hv = fmaxf(sacc[q] + b[n], 0.f);
+      nb[n] = hv;
+      if (valid) dst[n * M] = hv;
+    }
+    __syncwarp();
+    float* tmp = a;
+    a = nb;
+    nb = tmp;
+    w = b + kHgW;
+    K = kHgW;
+  }
+  if (valid && t == 0) {
+    float z0 = 0.f, z1 = 0.f;
+    for (int k = 0; k < kHgW; ++k) {
+      z0 = fmaf(a[k], w[k], z0);
+      z1 = fmaf(a[k], w[kHgW + k], z1);
+    }
+    z0 += w[2 * kHgW];
+    z1 += w[2 * kHgW + 1];
     z_out[row] = make_float2(z0, z1);
-  } else {
-    write_heads(out, row, z0, z1);
   }
 }
 
-// Backward of one ray (FP32): from dL/dz through the head and the hidden
-// layers (ReLU masks from the stored activations), storing every dL/dpre
-// (feature-major, [H x 64 x B]) for the weight gradients, then the hash features' gradient scattered into the
-// level tables' gradient (blob layout, 8-byte aligned): each corner entry
-// receives its trilinear weight times the feature gradient (atomic adds;
-// entries shared by several rays or corners sum up).
-__global__ void __launch_bounds__(kHgF32Rays)
+// Backward of the training forward above, 4 threads per ray: dL/dpre of
+// every layer (feature-major, [H x 64 x B]) and the hash features' gradient
+// scattered into the level tables' gradient (blob layout, 8-byte aligned):
+// each corner entry receives its trilinear weight times the feature
+// gradient (atomic adds; entries shared by several rays or corners sum up).
+__global__ void __launch_bounds__(kHgTrainThreads)
     hg_train_bwd_kernel(const HashGridParams g, const float* __restrict__ mlp, int H, RaySoA rays,
                         int64_t M, const float* __restrict__ acts, const float2* __restrict__ dz,
                         float* __restrict__ dpre, float* __restrict__ grad_table) {
@@ -386,10 +481,11 @@ __global__ void __launch_bounds__(kHgF32Rays)
   float* bufB = bufA + kHgF32Rays * kHgLd;
   for (int i = threadIdx.x; i < n_mlp; i += blockDim.x) sw[i] = mlp[i];
   __syncthreads();
-  const int64_t row = static_cast<int64_t>(blockIdx.x) * kHgF32Rays + threadIdx.x;
-  if (row >= M) return;
-  float* dh = bufA + threadIdx.x * kHgLd;
-  float* dn = bufB + threadIdx.x * kHgLd;
+  const int r = threadIdx.x >> 2, t = threadIdx.x & 3;
+  const int64_t row = static_cast<int64_t>(blockIdx.x) * kHgF32Rays + r;
+  const bool valid = row < M;
+  float* dh = bufA + r * kHgLd;
+  float* dn = bufB + r * kHgLd;
   // weight offsets: layer l's W [64 x K_l] and b, then the head W_o [2 x 64], b_o
   int woff[4];
   int off = 0;
@@ -398,41 +494,44 @@ __global__ void __launch_bounds__(kHgF32Rays)
     off += kHgW * (l == 0 ? kHgCode : kHgW) + kHgW;
   }
   const float* wo = sw + off;
-  const float2 d = dz[row];
-  for (int k = 0; k < kHgW; ++k) dh[k] = d.x * wo[k] + d.y * wo[kHgW + k];
+  const float2 d = valid ? dz[row] : make_float2(0.f, 0.f);
+  for (int k = t; k < kHgW; k += kHgTrainT) dh[k] = d.x * wo[k] + d.y * wo[kHgW + k];
+  __syncwarp();
   for (int l = H - 1; l >= 0; --l) {
     const float* h = acts + static_cast<int64_t>(l) * kHgW * M + row;
     float* dp = dpre + static_cast<int64_t>(l) * kHgW * M + row;
-    for (int k = 0; k < kHgW; ++k) {
-      const float v = h[k * M] > 0.f ? dh[k] : 0.f;
+    for (int k = t; k < kHgW; k += kHgTrainT) {
+      const float v = valid && h[k * M] > 0.f ? dh[k] : 0.f;
       dh[k] = v;
-      dp[k * M] = v;
+      if (valid) dp[k * M] = v;
     }
+    __syncwarp();
     const int K = l == 0 ? 2 * 16 : kHgW;  // layer 1: only the hash features need a gradient
     const int ldw = l == 0 ? kHgCode : kHgW;
     const float* w = sw + woff[l];
-    for (int j = 0; j < K; j += 4) {  // K is 32 or 64: 4 inputs at a time
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-      for (int n = 0; n < kHgW; ++n) {
-        const float dv = dh[n];
-        const float* wr = w + n * ldw + j;
-        s0 = fmaf(dv, wr[0], s0);
-        s1 = fmaf(dv, wr[1], s1);
-        s2 = fmaf(dv, wr[2], s2);
-        s3 = fmaf(dv, wr[3], s3);
-      }
-      dn[j] = s0;
-      dn[j + 1] = s1;
-      dn[j + 2] = s2;
-      dn[j + 3] = s3;
+    float sacc[kHgW / kHgTrainT];
+#pragma unroll
+    for (int q = 0; q < kHgW / kHgTrainT; ++q) sacc[q] = 0.f;
+    for (int n = 0; n < kHgW; ++n) {
+      const float dv = dh[n];
+      const float* wr = w + n * ldw + t;
+#pragma unroll
+      for (int q = 0; q < kHgW / kHgTrainT; ++q)
+        if (t + kHgTrainT * q < K) sacc[q] = fmaf(dv, wr[kHgTrainT * q], sacc[q]);
     }
-    float* t = dh;
+#pragma unroll
+    for (int q = 0; q < kHgW / kHgTrainT; ++q)
+      if (t + kHgTrainT * q < K) dn[t + kHgTrainT * q] = sacc[q];
+    __syncwarp();
+    float* tmp = dh;
     dh = dn;
-    dn = t;
+    dn = tmp;
   }
-  // dh now holds dL/d(hash features) [32]: scatter to the 8 corners per level
+  if (!valid) return;
+  // dh holds dL/d(hash features) [32]: this thread scatters levels t, t + 4, ...
   const float x = box01(rays.p[0][row]), y = box01(rays.p[1][row]), z = box01(rays.p[2][row]);
-  for (int l = 0; l < 16; ++l) {
+  for (int j = 0; j < 4; ++j) {
+    const int l = t + 4 * j;
     const int n = g.res[l];
     const float fn = static_cast<float>(n);
     const float ux = x * fn, uy = y * fn, uz = z * fn;
@@ -606,13 +705,13 @@ cudaError_t launch_hashgrid_f32(const HashGridParams& g, const float2* table, co
   if (H < 1 || H > 4) return cudaErrorInvalidValue;
   const int n_mlp = kHgW * kHgCode + kHgW + (H - 1) * (kHgW * kHgW + kHgW) + 2 * kHgW + 2;
   const size_t smem = (((n_mlp + 3) & ~3) + 2 * kHgF32Rays * kHgLd) * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(hashgrid_f32_kernel<false>,
+  cudaError_t e = cudaFuncSetAttribute(hashgrid_f32_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   const int64_t blocks = (M + kHgF32Rays - 1) / kHgF32Rays;
-  hashgrid_f32_kernel<false><<<static_cast<unsigned>(blocks), kHgF32Rays, smem, s>>>(
-      g, table, mlp, H, rays, M, out, nullptr, nullptr, nullptr);
+  hashgrid_f32_kernel<<<static_cast<unsigned>(blocks), kHgF32Rays, smem, s>>>(
+      g, table, mlp, H, rays, M, out);
   return cudaGetLastError();
 }
 
@@ -628,14 +727,14 @@ cudaError_t launch_hg_train_fwd(const HashGridParams& g, const float2* table, co
                                 float2* z, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
   if (H < 1 || H > 4) return cudaErrorInvalidValue;
-  const size_t smem = hg_f32_smem(H);
-  cudaError_t e = cudaFuncSetAttribute(hashgrid_f32_kernel<true>,
+  const size_t smem = (((hg_train_wfloats(H) + 3) & ~3) + 2 * kHgF32Rays * kHgLd) * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(hg_train_fwd_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   const int64_t blocks = (B + kHgF32Rays - 1) / kHgF32Rays;
-  hashgrid_f32_kernel<true><<<static_cast<unsigned>(blocks), kHgF32Rays, smem, s>>>(
-      g, table, mlp, H, rays, B, HeadOut{}, code, acts, z);
+  hg_train_fwd_kernel<<<static_cast<unsigned>(blocks), kHgTrainThreads, smem, s>>>(
+      g, table, mlp, H, rays, B, code, acts, z);
   return cudaGetLastError();
 }
 
@@ -651,7 +750,7 @@ cudaError_t launch_hg_train_bwd(const HashGridParams& g, const float* mlp, int H
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   const int64_t blocks = (B + kHgF32Rays - 1) / kHgF32Rays;
-  hg_train_bwd_kernel<<<static_cast<unsigned>(blocks), kHgF32Rays, smem, s>>>(
+  hg_train_bwd_kernel<<<static_cast<unsigned>(blocks), kHgTrainThreads, smem, s>>>(
       g, mlp, H, rays, B, acts, dz, dpre, grad_table);
   return cudaGetLastError();
 }
