@@ -86,8 +86,10 @@ typedef enum {
  *                  (N+1) k)) while (N+1)^3 <= 2^19, else 2^19 entries indexed
  *                  by (i xor j * 2654435761 xor k * 805459861) mod 2^19; a
  *                  point reads the trilinear interpolation of its cell's 8
- *                  corners. Ray queries (ddf_query_*) accept it; tiles,
- *                  FP8 and training do not. */
+ *                  corners. Ray queries (ddf_query_*) and the training
+ *                  calls (ddf_compute_grad, ddf_train_step, ddf_forward_train
+ *                  / ddf_backward, ddf_distill, ddf_distill_pool; FP32 on the
+ *                  master weights) accept it; tiles and FP8 do not. */
 typedef enum { DDF_KIND_RAY = 0, DDF_KIND_SDF = 1, DDF_KIND_HASHGRID = 2 } ddf_kind;
 
 typedef struct {
