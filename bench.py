@@ -373,8 +373,9 @@ def _dilate(torch, mask, V, W, r):
 
 
 def _chamfer(torch, P, Q, cap=20000, seed=0):
-    """Symmetric Chamfer distance: mean nearest distance P -> Q plus Q -> P,
-    on at most `cap` points of each (seeded subsample)."""
+    """Symmetric Chamfer distance: the average of the mean nearest-point
+    distance from P to Q and the one from Q to P, on at most `cap` points of
+    each (seeded subsample)."""
     if P.shape[0] == 0 or Q.shape[0] == 0:
         return float("nan")
     g = torch.Generator(device=P.device).manual_seed(seed)
