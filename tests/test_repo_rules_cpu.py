@@ -1,0 +1,64 @@
+"""Structural rules of the repository, checked on the sources:
+* the product (the package and its CUDA/C++ sources) never imports or
+  includes the oracle;
+* the oracle imports nothing but numpy and the standard library;
+* no committed file outside tests/ and bench.py runs the oracle;
+* no product, test or profile file refers to the scratch folder.
+"""
+import ast
+import glob
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PKG = os.path.join(ROOT, "paper_2606_00817_gb300")
+
+
+def _imports(path):
+    tree = ast.parse(open(path).read(), path)
+    for node in ast.walk(tree):
+        if isinstance(node, ast.Import):
+            for a in node.names:
+                yield a.name
+        elif isinstance(node, ast.ImportFrom):
+            yield (node.module or "") if node.level == 0 else "." + (node.module or "")
+
+
+def test_package_never_imports_the_oracle():
+    for path in glob.glob(os.path.join(PKG, "**", "*.py"), recursive=True):
+        for name in _imports(path):
+            assert not name.split(".")[0] == "oracle", (path, name)
+    for path in glob.glob(os.path.join(PKG, "csrc", "*")):
+        assert not re.search(r'#include\s*[<"][^>"]*oracle', open(path, errors="replace").read()), path
+
+
+def test_oracle_imports_only_numpy_and_the_standard_library():
+    allowed = {"__future__", "numpy", "math", "dataclasses", "typing", "functools", "itertools"}
+    for path in glob.glob(os.path.join(ROOT, "oracle", "*.py")):
+        for name in _imports(path):
+            assert name.split(".")[0] in allowed, (path, name)
+
+
+def test_only_tests_smoke_and_bench_run_the_oracle():
+    users = set()
+    for path in glob.glob(os.path.join(ROOT, "**", "*.py"), recursive=True):
+        rel = os.path.relpath(path, ROOT)
+        if rel.split(os.sep)[0] in ("_work", "gpurun_out", "baseline", "oracle"):
+            continue
+        if any(n.split(".")[0] == "oracle" for n in _imports(path)):
+            users.add(rel.split(os.sep)[0] if os.sep in rel else rel)
+    assert users <= {"tests", "bench.py", "__graft_entry__.py"}, users
+
+
+def test_no_committed_file_refers_to_the_scratch_folder():
+    roots = [PKG, os.path.join(ROOT, "tests"), os.path.join(ROOT, "profiles"),
+             os.path.join(ROOT, "include"), os.path.join(ROOT, "oracle")]
+    files = [os.path.join(ROOT, f) for f in ("bench.py", "__graft_entry__.py")]
+    for r in roots:
+        files += [p for p in glob.glob(os.path.join(r, "**", "*"), recursive=True) if os.path.isfile(p)]
+    pat = re.compile(r"(^|[^A-Za-z0-9_])_work/")
+    for path in files:
+        if path.endswith((".so", ".o", ".pyc")) or path == os.path.abspath(__file__):
+            continue
+        text = open(path, errors="replace").read()
+        assert not pat.search(text), path
