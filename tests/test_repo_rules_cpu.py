@@ -62,3 +62,16 @@ def test_no_committed_file_refers_to_the_scratch_folder():
             continue
         text = open(path, errors="replace").read()
         assert not pat.search(text), path
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """With no compiled library the binding raises; it has nothing to fall
+    back on."""
+    import pytest
+    from paper_2606_00817_gb300 import ddf
+    monkeypatch.setattr(ddf, "LIB_PATH", str(tmp_path / "libddf.so"))
+    monkeypatch.setattr(ddf, "_LIB", None)
+    with pytest.raises(RuntimeError, match="is missing"):
+        ddf.lib()
+    with pytest.raises(RuntimeError):
+        ddf.ddf_param_count(ddf.make_config(6, 128, 4, "bf16"))
