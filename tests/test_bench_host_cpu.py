@@ -1,9 +1,12 @@
 """Host-side logic of bench.py that decides whether a measurement stands: the
 clock summary built from nvidia-smi samples (median SM clock under load,
-throttle reasons seen under load). A fake sample file stands in for
-nvidia-smi; no process is started."""
+throttle reasons seen under load; a fake sample file stands in for
+nvidia-smi, no process is started), the default command line, the per-rank
+split and the bounded oracle sample of the cpu_baseline leg."""
 import os
 import sys
+
+import numpy as np
 
 sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 import bench  # noqa: E402
@@ -51,3 +54,31 @@ def test_whole_job_rate_and_rank_shards():
     assert bench.whole_job_rate(1000, 4, 3, 2.0) == 6000.0
     a, b = bench.rank_rays(32, 0), bench.rank_rays(32, 1)
     assert a.n == b.n == 32 and not (a.soa()[0] == b.soa()[0]).all()
+
+
+def test_default_command_line_keeps_the_contract(monkeypatch):
+    """No flags: one GPU, the full headline workload, bf16, at least 3
+    warm-up steps."""
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    a = bench.parse()
+    assert a.gpus == 1 and a.impl == "ours" and a.precision == "bf16"
+    assert a.warmup >= 3 and a.steps >= 1 and a.rays == 4_194_304
+
+
+def test_oracle_sample_is_bounded_and_exact():
+    """The cpu_baseline leg: consecutive chunks until the time budget is
+    spent, never more than the cap, with the FP64 outputs of the rays it did."""
+    from oracle import ddf_oracle as O
+    from paper_2606_00817_gb300 import inputs as I
+    rays = I.uniform_rays(600, seed=9)
+    blob = I.xavier_blob(I.NetShape(*bench.NET), seed=0)
+    rate, n, el, ref = bench.oracle_sample(rays, blob, seconds=0.0, chunk=100, cap=400)
+    assert n == 100 and rate > 0 and el > 0                 # one chunk when the budget is 0
+    rate, n, el, ref = bench.oracle_sample(rays, blob, seconds=1e9, chunk=100, cap=400)
+    assert n == 400 and ref["t"].shape == (400,)            # capped
+    sub = rays.slice(0, 400)
+    want = O.ddf_forward(sub.origins(), sub.dirs(), blob, *bench.NET)
+    # the same FP64 values up to the matrix products' summation order, which
+    # depends on the batch size
+    assert np.allclose(ref["t"], want["t"], rtol=1e-12, atol=1e-13)
+    assert np.allclose(ref["vis"], want["vis"], rtol=1e-12, atol=1e-13)
