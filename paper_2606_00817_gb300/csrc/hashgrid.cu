@@ -1,7 +1,10 @@
-// hashgrid.cu -- query kernels of the hash-grid DDF, the paper's final field
+// hashgrid.cu -- kernels of the hash-grid DDF, the paper's final field
 // (Sec. 3.4): the ray origin is encoded by a multiresolution hash grid, the
 // direction by four sinusoidal bands, and a small MLP of width 64 maps the
-// joined code to (t, xi).
+// joined code to (t, xi). Queries are described below; training (FP32 on the
+// master weights) has its own forward and backward with 4 threads per ray,
+// the weight gradients as batch-split outer products, and the refresh of the
+// bf16 table.
 //
 // Per ray the code costs 16 levels x 8 corner reads of the level table (the
 // 26 MB bf16 table stays in the 129 MB L2), so the kernel is a gather kernel;

@@ -1,10 +1,12 @@
 // train.cu -- CUDA-core kernels of the distillation step (Sec. 3.2 / 3.4):
-// the FP32 head and its gradient, the clamped-L1 + cross-entropy loss, column
-// sums and split-K reduction, Adam, transposed weight packing (the weight
-// gradients themselves read their operands MN-major on the tensor cores, so
-// no activation is transposed), and the exact ray caster against a union of
-// spheres and boxes that supplies the distillation targets (Sec. 3.2, exact
-// cast supervision with analytic primitives in place of a mesh).
+// the FP32 head and its gradient, the clamped-L1 + cross-entropy loss, the
+// gradient reductions (one fixed-order launch per layer: split-K sums of the
+// weight gradients and column sums for the biases), Adam (plain, and fused
+// with the refresh of every weight copy, the transposed one included; the
+// weight gradients themselves read their operands MN-major on the tensor
+// cores, so no activation is transposed), and the exact ray caster against a
+// union of spheres and boxes that supplies the distillation targets (Sec.
+// 3.2, exact cast supervision with analytic primitives in place of a mesh).
 #include <cuda_bf16.h>
 
 #include "kernels.h"
