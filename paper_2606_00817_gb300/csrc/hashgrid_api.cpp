@@ -1,8 +1,11 @@
 // hashgrid_api.cpp -- host side of the hash-grid field (kind
 // DDF_KIND_HASHGRID), the paper's final DDF (Sec. 3.4): the level layout of
 // the multiresolution hash grid, weight loading (bf16 or FP32 level tables,
-// swizzled MLP operand images) and the query launch. The public entry points
-// (ddf_create, ddf_load_weights, the ray queries) dispatch here by kind.
+// swizzled MLP operand images), the query launch, and training (FP32
+// forward and backward, the table gradient's scatter, every weight and bias
+// sum in one reduction launch, Adam, the bf16 refresh). The public entry
+// points (ddf_create, ddf_load_weights, the ray queries, the training calls)
+// dispatch here by kind.
 #include <algorithm>
 #include <cmath>
 

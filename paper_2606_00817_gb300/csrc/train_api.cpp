@@ -6,10 +6,11 @@
 // head and every layer:
 //   dW_l = dpre_l^T A_l   (tensor cores, split-K over the batch, FP32 partials
 //                          reduced in a fixed order)
-//   db_l = column sums of dpre_l
+//   db_l = column sums of dpre_l (from 32-row sums the input-gradient
+//          epilogue leaves, reduced with dW_l in the same launch)
 //   dpre_{l-1} = (dpre_l W_l) masked by h_{l-1} > 0   (tensor cores, bf16)
-// and, for ddf_train_step, Adam on the FP32 master weights followed by a
-// refresh of the bf16 copies the queries use. The exact analytic ray caster
+// and, for ddf_train_step, Adam on the FP32 master weights together with the
+// refresh of the bf16 copies the queries use (one pass over the blob). The exact analytic ray caster
 // that produces distillation targets lives here too (ddf_cast_scene).
 #include <algorithm>
 #include <cmath>
