@@ -75,3 +75,13 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
         ddf.lib()
     with pytest.raises(RuntimeError):
         ddf.ddf_param_count(ddf.make_config(6, 128, 4, "bf16"))
+
+
+def test_every_golden_fixture_states_its_source():
+    import json
+    files = glob.glob(os.path.join(ROOT, "tests", "golden", "*.json"))
+    assert files
+    for path in files:
+        with open(path) as f:
+            src = json.load(f).get("source", "")
+        assert isinstance(src, str) and len(src) > 40, path
