@@ -804,6 +804,133 @@ def gi_images(scene, eye, target, up, fov_y, width, height, light, ao_samples, s
     return shadow.reshape(height, width), ao.reshape(height, width)
 
 
+# --------------------------- distillation schedule (Sec. 3.2 / Sec. 3.4)
+#
+# Sec. 3.2 trains on camera rays and on rays that start on the surface and
+# point in all directions, adds copies of hitting rays moved forward along
+# themselves (a point moved forward by s reports t - s), and Sec. 3.4 decays
+# the learning rate by a cosine to 5 % of its start. The paper fixes neither
+# the ray distributions nor the draws; the readings taken here:
+#   * a fraction surface_frac of the rays is surface-anchored: a primitive
+#     chosen uniformly (not by area), a point uniform on its surface
+#     (sphere: c + r n with n uniform on the sphere; box: a face chosen
+#     uniformly, the two in-face coordinates uniform), the origin 1e-3 off
+#     the surface along the outward normal, the direction uniform on the
+#     sphere; the rest are camera rays: origin uniform on a face of [-1, 1]^3,
+#     aimed at a point uniform in [-0.9, 0.9]^3;
+#   * the rays from index `first` on that hit move to o + s d with s = u t,
+#     u uniform in [0, 1), and report t - s; misses stay as they are;
+#   * lr_k = lr0 (0.05 + 0.95 (1 + cos(pi k / steps)) / 2), k = 0..steps-1;
+#   * draws: uniform m of ray i at step k is the counter-based SplitMix64
+#     uniform of (seed, a = k, b = i) (the key of gi_uniform), with m = 0 the
+#     surface/camera choice, 1 the primitive or face, 2..6 the positions and
+#     directions (in the order below), 7 the shift, and for batches drawn from
+#     a fixed pool the top 32 bits of mix(key + 8) pick the row;
+#   * where a uniform picks an integer (a primitive, a face), the product u K
+#     is taken in float32, as the GPU takes it, and floored.
+
+DISTILL_SURFACE_OFFSET = 1e-3
+
+
+def distill_uniform(seed, step, i, m):
+    """Uniform m of ray i at distillation step `step` (24 bits, exact in
+    float32)."""
+    return gi_uniform(seed, step, i, m)
+
+
+def _pick(u, k):
+    """floor(u k) with the product rounded to float32, clamped to k - 1."""
+    prod = (np.asarray(u, np.float32) * np.float32(k)).astype(F64)
+    return np.minimum(np.floor(prod), k - 1).astype(np.int64)
+
+
+def uniform_sphere_dir(a, b):
+    """Unit vector uniform on the sphere from two uniforms (Archimedes:
+    z = 2a - 1 uniform, azimuth 2 pi b)."""
+    z = 2.0 * np.asarray(a, F64) - 1.0
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    phi = 2.0 * np.pi * np.asarray(b, F64)
+    return np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=-1)
+
+
+def distill_rays(scene, seed, step, n, surface_frac):
+    """The n training rays of one distillation step (readings above).
+    Returns (o, d) [n, 3] float64 and the surface-anchored mask."""
+    i = np.arange(n, dtype=np.int64)
+    u = [distill_uniform(seed, step, i, m) for m in range(7)]
+    ns, nb = len(scene.radii), len(scene.box_lo)
+    K = ns + nb
+    surf = (u[0] < np.float32(surface_frac)) & (K > 0)
+    o = np.zeros((n, 3))
+    d = np.zeros((n, 3))
+    # surface-anchored rays
+    if K > 0:
+        p = _pick(u[1], K)
+        pt = np.zeros((n, 3))
+        nrm = np.zeros((n, 3))
+        sph = surf & (p < ns)
+        if np.any(sph):
+            js = p[sph]
+            nv = uniform_sphere_dir(u[2][sph], u[3][sph])
+            pt[sph] = np.asarray(scene.centers, F64)[js] + np.asarray(scene.radii, F64)[js, None] * nv
+            nrm[sph] = nv
+        bx = surf & (p >= ns)
+        for r in np.nonzero(bx)[0]:
+            lo = np.asarray(scene.box_lo[p[r] - ns], F64)
+            hi = np.asarray(scene.box_hi[p[r] - ns], F64)
+            face = int(_pick(u[2][r], 6))
+            axis, plus = face // 2, face % 2 == 1
+            a, c = (axis + 1) % 3, (axis + 2) % 3
+            pt[r, a] = lo[a] + u[3][r] * (hi[a] - lo[a])
+            pt[r, c] = lo[c] + u[4][r] * (hi[c] - lo[c])
+            pt[r, axis] = hi[axis] if plus else lo[axis]
+            nrm[r, axis] = 1.0 if plus else -1.0
+        o[surf] = pt[surf] + DISTILL_SURFACE_OFFSET * nrm[surf]
+        d[surf] = uniform_sphere_dir(u[5][surf], u[6][surf])
+    # camera rays
+    cam = ~surf
+    face = _pick(u[1], 6)
+    for r in np.nonzero(cam)[0]:
+        axis, plus = int(face[r]) // 2, int(face[r]) % 2 == 1
+        o[r, (axis + 1) % 3] = 2.0 * u[2][r] - 1.0
+        o[r, (axis + 2) % 3] = 2.0 * u[3][r] - 1.0
+        o[r, axis] = 1.0 if plus else -1.0
+    tgt = np.stack([1.8 * u[4] - 0.9, 1.8 * u[5] - 0.9, 1.8 * u[6] - 0.9], axis=1)
+    v = tgt[cam] - o[cam]
+    d[cam] = v / np.linalg.norm(v, axis=1, keepdims=True)
+    return o, d, surf
+
+
+def distill_shift(o, d, t, hit, first, seed, step):
+    """Ray-march shifted points: rays i >= first that hit move to o + s d with
+    s = u t (u = draw 7 of (seed, step, i)) and report t - s. Returns new
+    (o, t); misses and rays before `first` are unchanged."""
+    o = np.array(o, F64)
+    t = np.array(t, F64)
+    d = np.asarray(d, F64)
+    i = np.arange(first, o.shape[0], dtype=np.int64)
+    sel = i[np.asarray(hit, bool)[first:] & np.isfinite(t[first:])]
+    s = distill_uniform(seed, step, sel, 7) * t[sel]
+    o[sel] += s[:, None] * d[sel]
+    t[sel] -= s
+    return o, t
+
+
+def distill_lr(lr0, k, steps):
+    """Learning rate of step k of `steps`: a cosine from lr0 down to 5 % of it."""
+    return lr0 * (0.05 + 0.95 * 0.5 * (1.0 + np.cos(np.pi * np.asarray(k, F64) / steps)))
+
+
+def distill_pool_index(seed, step, i, n_pool):
+    """Pool row of batch row i at `step`: floor(u32 n_pool / 2^32) with u32
+    the top 32 bits of mix(key + 8) (integer arithmetic)."""
+    with np.errstate(over="ignore"):
+        key = splitmix64(splitmix64(_U64(seed) ^ _U64(0x5DEECE66D)) + _U64(step)) \
+            ^ (np.asarray(i, _U64) * _U64(0x2545F4914F6CDD1D))
+        u32 = splitmix64(key + _U64(8)) >> _U64(32)
+    return np.array([(int(x) * int(n_pool)) >> 32 for x in np.atleast_1d(u32)], np.int64)
+
+
 # ----------------------- Gaussian-rendered depth (Sec. 3.2, Sec. 4.2)
 #
 # The supervision source the paper finds too blurry for thin parts: depth

@@ -250,6 +250,101 @@ def test_reduced_precision_error_scales_with_format():
     assert e_bf < e_f8 < 0.2
 
 
+def _reduced(name):
+    """A hand-worked net of reduced_nets.json: (spec, blob, o, d)."""
+    net = _gold("reduced_nets.json")[name]
+    names = ["W1", "W2", "W3"][:net["hidden"]]
+    parts = []
+    for w in names + ["Wo"]:
+        b = "bo" if w == "Wo" else "b" + w[1:]
+        parts += [np.array(net[w], np.float32).ravel(), np.array(net[b], np.float32)]
+    blob = np.concatenate(parts)
+    o = np.array([net["ray"]["o"]], float)
+    d = np.array([net["ray"]["d"]], float)
+    return net, blob, o, d
+
+
+def _fp8_cases_hold():
+    net, blob, o, d = _reduced("fp8")
+    return all(O.ddf_forward(o, d, blob, 0, 2, 3, "fp8", c["act_scales"])["z"][0].tolist() == c["z"]
+               for c in net["cases"])
+
+
+def test_fp8_mode_hand_worked_network():
+    """e4m3 mode on a 3-layer net worked by hand (tests/golden/reduced_nets.json):
+    bf16 layer 1, activation codes with each layer's own input scale (one case
+    saturates at 448), weight codes that round, dequantisation by s_in s_n."""
+    net, blob, o, d = _reduced("fp8")
+    for c in net["cases"]:
+        z = O.ddf_forward(o, d, blob, 0, 2, 3, "fp8", c["act_scales"])["z"][0]
+        assert z.tolist() == c["z"], (c["act_scales"], z)
+    # the scale of layer l is the one of its own input: swapping them moves z
+    sw = O.ddf_forward(o, d, blob, 0, 2, 3, "fp8", net["cases"][0]["act_scales"][::-1])["z"][0]
+    assert sw.tolist() != net["cases"][0]["z"]
+
+
+@pytest.mark.parametrize("mistake", ["weights_unrounded", "no_saturation", "acts_unrounded",
+                                     "layer1_in_e4m3"])
+def test_fp8_pin_catches_planted_mistakes(monkeypatch, mistake):
+    """A plausible mistake planted in the oracle makes the hand-worked e4m3
+    pin fail."""
+    if mistake == "weights_unrounded":
+        scales = O.fp8_weight_scales
+        monkeypatch.setattr(O, "fp8_quantise_weights", lambda w: (
+            (np.asarray(w, np.float32) / scales(w).astype(np.float32)[:, None]).astype(float), scales(w)))
+    elif mistake == "no_saturation":
+        monkeypatch.setattr(O, "E4M3_MAX", np.inf)
+    elif mistake == "acts_unrounded":
+        orig = O.round_e4m3
+        monkeypatch.setattr(O, "round_e4m3", lambda x: np.asarray(x, float) if np.ndim(x) == 2
+                            and np.asarray(x).shape[0] == 1 else orig(x))
+    elif mistake == "layer1_in_e4m3":
+        monkeypatch.setattr(O, "round_bf16", lambda x: O.round_e4m3(x))
+    assert not _fp8_cases_hold()
+
+
+def test_fp8_calibration_hand_worked():
+    """Calibration takes max |h_l| after the ReLU of layers 1..H-1 over the
+    batch and rounds each up to a power of two: [0.125, 0.25] here, where the
+    encoded input, the pre-activations or the layer after would give 1, 1 or
+    0.125 (tests/golden/reduced_nets.json)."""
+    net, blob, _, _ = _reduced("fp8")
+    cal = net["calibration"]
+    o = np.array([r["o"] for r in cal["rays"]], float)
+    d = np.array([r["d"] for r in cal["rays"]], float)
+    assert O.calibrate_act_scales(o, d, blob, 0, 2, 3) == cal["scales"]
+    # the batch maximum: the first ray alone gives the same scales, the
+    # second alone a smaller first-layer maximum
+    assert O.calibrate_act_scales(o[:1], d[:1], blob, 0, 2, 3) == cal["scales"]
+    assert O.calibrate_act_scales(o[1:2], d[1:2], blob, 0, 2, 3)[0] == O.pow2_scale(1.0)
+
+
+def test_bf16_mode_hand_worked_network():
+    """bf16 mode on a 2-layer net worked by hand: the input, a weight and a
+    hidden activation (a tie, to even) round, the last hidden activation and
+    the head weights do not (tests/golden/reduced_nets.json)."""
+    net, blob, o, d = _reduced("bf16")
+    z = O.ddf_forward(o, d, blob, 0, 2, 2, "bf16")["z"][0]
+    assert z.tolist() == net["z"]
+    ex = O.ddf_forward(o, d, blob, 0, 2, 2, "exact")["z"][0]
+    assert ex.tolist() != net["z"]
+
+
+@pytest.mark.parametrize("mistake", ["no_rounding", "round_last_activation"])
+def test_bf16_pin_catches_planted_mistakes(monkeypatch, mistake):
+    net, blob, o, d = _reduced("bf16")
+    if mistake == "no_rounding":
+        monkeypatch.setattr(O, "round_bf16", lambda x: np.asarray(x, float))
+        z = O.ddf_forward(o, d, blob, 0, 2, 2, "bf16")["z"][0]
+    else:
+        # the last hidden activation rounded before the head (what R11 rules out)
+        layers = O.split_blob(blob, O.ddf_dims(0, 2, 2))
+        _, _, acts = O.mlp_forward(O.encode(o, d, 0), layers, "bf16", keep=True)
+        wo, bo = layers[-1]
+        z = (O.round_bf16(acts[-1]) @ wo.T + bo)[0]
+    assert z.tolist() != net["z"]
+
+
 def test_fp8_weight_quantiser():
     w = np.array([[0.5, -1.0, 0.25], [448.0 * 3, 1.0, 0.0], [0.0, 0.0, 0.0]], np.float32)
     q, s = O.fp8_quantise_weights(w)
