@@ -175,7 +175,9 @@ ddf_status ddf_query_shadow_host(ddf_handle h, const float* const rays[6], int64
  * a renderer's per-frame callback (cudaMalloc may synchronise the device and
  * stall the frame) or a host framework whose pool owns all device memory.
  *  - n must fit the scratch in one pass (about 6,190 rays for 126->1280x8
- *    bf16); larger n returns DDF_ERR_INVALID_ARG with the limit in the message.
+ *    bf16, about 49,300 for 78->128x4); larger n returns DDF_ERR_INVALID_ARG
+ *    with the limit in the message. Hash-grid fields run one fused kernel
+ *    with no scratch, so their batches have no such limit.
  *  - The first call on a device looks up the scratch address there; make it
  *    before any stream capture.
  *  - All calls (all handles) share the array and leave their data in it; no

@@ -1349,6 +1349,7 @@ ddf_status ddf_autotune(ddf_handle h, const float* const rays[6], int64_t n, voi
 // noalloc.cu). Not part of the public header.
 
 size_t ddf_internal_workspace_bytes(ddf_handle h, int64_t rows) {
+  if (h->cfg.kind == DDF_KIND_HASHGRID) return 0;  // one fused kernel, no scratch
   const int W = h->cfg.width;
   const bool f32 = h->cfg.precision == DDF_FP32;
   const size_t act_elem = f32 ? 4 : (h->cfg.precision == DDF_BF16 ? 2 : 1);
