@@ -198,8 +198,29 @@ ddf_status ddf_query_ao(ddf_handle h, const float* const rays[6], int64_t n_rays
                         const int32_t* offsets, int64_t n_points, float* out_hard,
                         float* out_soft, void* stream);
 
-/* Graph mode. When on, ddf_query_rays, ddf_query_shadow and ddf_query_ao
- * record their whole launch sequence (all chunks and layers) into a CUDA
+/* Mixed batch (Sec. 3.3: a frame of the application asks, per shading
+ * point, one shadow ray and a ragged set of hemisphere rays; both are single
+ * field evaluations). Evaluates n_shadow shadow rays (SoA shadow_rays, light
+ * and outputs as ddf_query_shadow) and a ragged AO batch (ao_rays, offsets,
+ * n_points, out_hard, out_soft as ddf_query_ao) as ONE batch of
+ * n_shadow + n_ao_rays rows: rows below n_shadow come from shadow_rays, the
+ * rest from ao_rays, and every layer launch covers both kinds, so the ragged
+ * sets share the persistent tiles with the shadow rays instead of running a
+ * second pass. The results equal those of the two separate queries. In
+ * graph mode the whole sequence (all chunks, all layers, the shadow decision
+ * and the segmented AO reduce) is one graph replay. Either part may be
+ * empty (its pointers may then be NULL); n_ao_rays < 2^31. Device pointers,
+ * asynchronous on stream; keeps 5 bytes x n_ao_rays of scratch inside the
+ * handle, like ddf_query_ao. */
+ddf_status ddf_query_mixed(ddf_handle h, const float* const shadow_rays[6], int64_t n_shadow,
+                           const float light[3], float* out_t, float* out_vis,
+                           uint8_t* out_occluded, const float* const ao_rays[6], int64_t n_ao_rays,
+                           const int32_t* offsets, int64_t n_points, float* out_hard,
+                           float* out_soft, void* stream);
+
+/* Graph mode. When on, ddf_query_rays, ddf_query_shadow, ddf_query_ao and
+ * ddf_query_mixed record their whole launch sequence (all chunks and layers)
+ * into a CUDA
  * graph the first time they see a given set of pointers, sizes and light,
  * and afterwards replay that graph with one cudaGraphLaunch on the caller's
  * stream; the data behind the pointers may change between calls. Up to 8

@@ -211,18 +211,48 @@ ddf_status ensure_workspace(ddf_s* h, int64_t rows) {
   return DDF_OK;
 }
 
+constexpr int64_t kNoSplit = INT64_MAX;
+
+// The rays from row `off` on. A batch that joins two sets of arrays keeps
+// its split relative to the new first row; once `off` is past the split the
+// second set becomes the only one.
 ddf::RaySoA shift_rays(ddf::RaySoA r, int64_t off) {
+  if (r.split != kNoSplit && off >= r.split) {
+    for (int c = 0; c < 6; ++c) {
+      r.p[c] = r.q[c] + (off - r.split);
+      r.q[c] = nullptr;
+    }
+    r.split = kNoSplit;
+    return r;
+  }
   for (int c = 0; c < 6; ++c) r.p[c] += off;
+  if (r.split != kNoSplit) r.split -= off;
   return r;
 }
 
-// Advances every output that is present (null outputs stay null).
+// Advances every output that is present (null outputs stay null); past the
+// split of a mixed batch only the second part's visibility and hit flags
+// remain.
 ddf::HeadOut shift_out(ddf::HeadOut o, int64_t off) {
+  if (o.split != kNoSplit && off >= o.split) {
+    const int64_t k = off - o.split;
+    o.t = nullptr;
+    o.z0 = nullptr;
+    o.occluded = nullptr;
+    o.vis = o.vis2 != nullptr ? o.vis2 + k : nullptr;
+    o.hit = o.hit2 != nullptr ? o.hit2 + k : nullptr;
+    o.vis2 = nullptr;
+    o.hit2 = nullptr;
+    o.split = kNoSplit;
+    o.rays = shift_rays(o.rays, off);
+    return o;
+  }
   if (o.t != nullptr) o.t += off;
   if (o.vis != nullptr) o.vis += off;
   if (o.hit != nullptr) o.hit += off;
   if (o.z0 != nullptr) o.z0 += off;
   if (o.occluded != nullptr) o.occluded += off;
+  if (o.split != kNoSplit) o.split -= off;
   o.rays = shift_rays(o.rays, off);
   return o;
 }
@@ -358,18 +388,28 @@ ddf_status check_ready(ddf_s* h, int kind = DDF_KIND_RAY) {
   return DDF_OK;
 }
 
-ddf_status run_query(ddf_s* h, const float* const rays[6], int64_t n, ddf::HeadOut out,
-                     cudaStream_t st) {
+ddf_status run_query_soa(ddf_s* h, ddf::RaySoA r, int64_t n, ddf::HeadOut out, cudaStream_t st) {
   DDF_REQUIRE_ALIGNED(out.t, 4);
   DDF_REQUIRE_ALIGNED(out.vis, 4);
   DDF_REQUIRE_ALIGNED(out.z0, 4);
+  DDF_REQUIRE_ALIGNED(out.vis2, 4);
   const int64_t rows = std::min<int64_t>(n, h->chunk);
   ddf_status s = ensure_workspace(h, rows);
   if (s != DDF_OK) return s;
-  ddf::RaySoA r;
-  for (int c = 0; c < 6; ++c) r.p[c] = rays[c];
   out.rays = r;
-  if (h->cfg.kind == DDF_KIND_HASHGRID) return hg_query(h, r, n, out, st);  // no chunks needed
+  if (h->cfg.kind == DDF_KIND_HASHGRID) {  // one fused kernel per part, no chunks needed
+    if (r.split == kNoSplit || r.split >= n) return hg_query(h, r, n, out, st);
+    const int64_t n1 = r.split;
+    ddf::RaySoA r1 = r;
+    r1.split = kNoSplit;
+    ddf::HeadOut o1 = out;
+    o1.split = kNoSplit;
+    o1.vis2 = nullptr;
+    o1.hit2 = nullptr;
+    o1.rays = r1;
+    if (n1 > 0 && (s = hg_query(h, r1, n1, o1, st)) != DDF_OK) return s;
+    return hg_query(h, shift_rays(r, n1), n - n1, shift_out(out, n1), st);
+  }
   for (int64_t off = 0; off < n; off += h->chunk) {
     const int m = static_cast<int>(std::min<int64_t>(h->chunk, n - off));
     const ddf::RaySoA rc = shift_rays(r, off);
@@ -378,6 +418,13 @@ ddf_status run_query(ddf_s* h, const float* const rays[6], int64_t n, ddf::HeadO
     if (s != DDF_OK) return s;
   }
   return DDF_OK;
+}
+
+ddf_status run_query(ddf_s* h, const float* const rays[6], int64_t n, ddf::HeadOut out,
+                     cudaStream_t st) {
+  ddf::RaySoA r;
+  for (int c = 0; c < 6; ++c) r.p[c] = rays[c];
+  return run_query_soa(h, r, n, out, st);
 }
 
 void clear_graphs(ddf_s* h) {
@@ -930,6 +977,63 @@ ddf_status ddf_query_ao(ddf_handle h, const float* const rays[6], int64_t n_rays
                                                 out_soft, st));
                    return DDF_OK;
                  });
+}
+
+ddf_status ddf_query_mixed(ddf_handle h, const float* const shadow_rays[6], int64_t n_shadow,
+                           const float light[3], float* out_t, float* out_vis,
+                           uint8_t* out_occluded, const float* const ao_rays[6], int64_t n_ao_rays,
+                           const int32_t* offsets, int64_t n_points, float* out_hard,
+                           float* out_soft, void* stream) {
+  ddf_status s = check_ready(h);
+  if (s != DDF_OK) return s;
+  if ((s = check_rays(shadow_rays, n_shadow)) != DDF_OK) return s;
+  if ((s = check_rays(ao_rays, n_ao_rays)) != DDF_OK) return s;
+  if (n_shadow > 0 && (light == nullptr || out_t == nullptr || out_vis == nullptr ||
+                       out_occluded == nullptr))
+    return fail(DDF_ERR_INVALID_ARG, "light or a shadow output is NULL");
+  if (n_points < 0) return fail(DDF_ERR_INVALID_ARG, "n_points must be >= 0");
+  if (n_points > 0 && (offsets == nullptr || out_hard == nullptr))
+    return fail(DDF_ERR_INVALID_ARG, "offsets or out_hard is NULL");
+  if (n_points == 0 && n_ao_rays > 0)
+    return fail(DDF_ERR_INVALID_ARG, "ambient-occlusion rays without shading points");
+  DDF_REQUIRE_ALIGNED(out_t, 4);
+  DDF_REQUIRE_ALIGNED(out_vis, 4);
+  DDF_REQUIRE_ALIGNED(offsets, 4);
+  DDF_REQUIRE_ALIGNED(out_hard, 4);
+  DDF_REQUIRE_ALIGNED(out_soft, 4);
+  if (n_ao_rays >= (int64_t{1} << 31)) return fail(DDF_ERR_INVALID_ARG, "n_ao_rays must fit int32 offsets");
+  const int64_t n = n_shadow + n_ao_rays;
+  if (n == 0 && n_points == 0) return DDF_OK;
+  DeviceGuard g(h->cfg.device);
+  if ((s = ensure_workspace(h, std::max<int64_t>(1, std::min<int64_t>(n, h->chunk)))) != DDF_OK)
+    return s;
+  if ((s = ensure_ao_buffers(h, std::max<int64_t>(1, n_ao_rays))) != DDF_OK) return s;
+  ddf::RaySoA r;
+  for (int c = 0; c < 6; ++c) {
+    r.p[c] = n_shadow > 0 ? shadow_rays[c] : nullptr;
+    r.q[c] = n_ao_rays > 0 ? ao_rays[c] : nullptr;
+  }
+  r.split = n_shadow;
+  ddf::HeadOut o{};
+  o.t = out_t;
+  o.vis = out_vis;
+  o.occluded = out_occluded;
+  for (int i = 0; n_shadow > 0 && i < 3; ++i) o.light[i] = light[i];
+  o.vis2 = h->ao_vis;
+  o.hit2 = h->ao_hit;
+  o.split = n_shadow;
+  std::vector<uint64_t> key = query_key(
+      3, r.p, n,
+      {out_t, out_vis, out_occluded, offsets, out_hard, out_soft, r.q[0], r.q[1], r.q[2], r.q[3],
+       r.q[4], r.q[5]},
+      n_shadow > 0 ? light : nullptr, n_points);
+  key.push_back(static_cast<uint64_t>(n_shadow));
+  return enqueue(h, key, static_cast<cudaStream_t>(stream), [&](cudaStream_t st) {
+    ddf_status q = n > 0 ? run_query_soa(h, r, n, o, st) : DDF_OK;
+    if (q != DDF_OK) return q;
+    DDF_CK(ddf::launch_ao_reduce(h->ao_hit, h->ao_vis, offsets, n_points, out_hard, out_soft, st));
+    return DDF_OK;
+  });
 }
 
 ddf_status ddf_set_graph_mode(ddf_handle h, int32_t on) {

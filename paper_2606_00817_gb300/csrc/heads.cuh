@@ -15,7 +15,18 @@ __device__ __forceinline__ float sigmoid_f(float z) {
   return z >= 0.f ? 1.f / (1.f + e) : e / (1.f + e);
 }
 
+// Component c of ray `row` of a batch that may join two sets of arrays.
+__device__ __forceinline__ float ray_ld(const RaySoA& r, int c, int64_t row) {
+  return row < r.split ? __ldg(r.p[c] + row) : __ldg(r.q[c] + (row - r.split));
+}
+
 __device__ __forceinline__ void write_heads(const HeadOut& o, int64_t i, float z0, float z1) {
+  if (i >= o.split) {  // the second part of a mixed batch: hit flag and visibility only
+    const int64_t k = i - o.split;
+    if (o.vis2 != nullptr) o.vis2[k] = sigmoid_f(z1);
+    if (o.hit2 != nullptr) o.hit2[k] = z1 > 0.f ? 1 : 0;
+    return;
+  }
   const float t = softplus_f(z0);
   if (o.t != nullptr) o.t[i] = t;
   if (o.vis != nullptr) o.vis[i] = sigmoid_f(z1);

@@ -8,9 +8,15 @@
 
 namespace ddf {
 
-// Structure-of-arrays ray pointers (ox, oy, oz, dx, dy, dz).
+// Structure-of-arrays ray pointers (ox, oy, oz, dx, dy, dz). One batch may
+// join two sets of arrays (the mixed shadow + ambient-occlusion query): rows
+// below `split` read p at the row, rows from `split` on read q at row - split.
+// The default split (INT64_MAX) reads p only; kernels that take rays from q
+// read them through ray_ld (heads.cuh).
 struct RaySoA {
   const float* p[6];
+  const float* q[6] = {};
+  int64_t split = INT64_MAX;
 };
 struct RayOut {
   float* p[6];
@@ -150,6 +156,11 @@ struct HeadOut {
   uint8_t* occluded;  // nullptr unless a shadow query
   float light[3];
   RaySoA rays;        // origins for the shadow distance
+  // Rows from `split` on (the ambient-occlusion part of a mixed query) write
+  // only vis2 / hit2 (nullable), at row - split, instead of the outputs above.
+  float* vis2 = nullptr;
+  uint8_t* hit2 = nullptr;
+  int64_t split = INT64_MAX;
 };
 // From FP32 activations H [M x W] (FP32 path).
 cudaError_t launch_head_f32(const float* H, int M, int W, const float* wo, const float* bo,

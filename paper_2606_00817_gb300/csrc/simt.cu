@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kEncRays) encode_kernel(RaySoA rays, int64_t M
     float* row = enc_smem + i * sld;
     float e[6];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) e[c] = __ldg(rays.p[c] + r0 + i);
+    for (int c = 0; c < 6; ++c) e[c] = ray_ld(rays, c, r0 + i);
 #pragma unroll
     for (int c = 0; c < 6; ++c) row[c] = e[c];
     int col = 6;

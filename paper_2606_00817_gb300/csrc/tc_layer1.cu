@@ -23,6 +23,7 @@
 
 #include "kernels.h"
 #include "epilogue.cuh"
+#include "heads.cuh"
 #include "ptx_sm103.cuh"
 
 namespace ddf {
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(64 + 32 * EPI + 128, 1)
       const int64_t row = static_cast<int64_t>(mb) * S::BM + r;
       float e[6];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) e[c] = row < p.M ? __ldg(rays.p[c] + row) : 0.f;
+      for (int c = 0; c < 6; ++c) e[c] = row < p.M ? ray_ld(rays, c, row) : 0.f;
       bool ok = mbar_wait_bounded(aempty_bar(a), ((blk >> 1) & 1) ^ 1u, abort_flag, p.timeout_ns);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) {

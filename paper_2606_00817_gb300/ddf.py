@@ -59,6 +59,8 @@ SIGNATURES = {
     "ddf_query_shadow_host": (C.c_int, [_vp, _RAYS, _i64, _vp, _vp, _vp, _vp]),
     "ddf_query_rays_noalloc": (C.c_int, [_vp, _RAYS, _i64, _vp, _vp, _vp]),
     "ddf_query_ao": (C.c_int, [_vp, _RAYS, _i64, _vp, _i64, _vp, _vp, _vp]),
+    "ddf_query_mixed": (C.c_int, [_vp, _RAYS, _i64, _vp, _vp, _vp, _vp, _RAYS, _i64, _vp, _i64,
+                                  _vp, _vp, _vp]),
     "ddf_set_graph_mode": (C.c_int, [_vp, _i32]),
     "ddf_calibrate_fp8": (C.c_int, [_vp, _RAYS, _i64, _vp, _vp, _vp]),
     "ddf_compute_grad": (C.c_int, [_vp, _RAYS, _vp, _vp, _i64, _vp, _vp]),
@@ -247,6 +249,18 @@ def ddf_query_rays_noalloc(h, rays, n, out_t, out_vis, stream=None) -> None:
 def ddf_query_ao(h, rays, n_rays, offsets, n_points, out_hard, out_soft=None, stream=None) -> None:
     rp, keep = _rays(rays)
     _call("ddf_query_ao", h, rp, int(n_rays), _ptr(offsets), int(n_points), _ptr(out_hard),
+          _ptr(out_soft), _stream(stream))
+
+
+def ddf_query_mixed(h, shadow_rays, n_shadow, light, out_t, out_vis, out_occluded, ao_rays,
+                    n_ao_rays, offsets, n_points, out_hard, out_soft=None, stream=None) -> None:
+    """Shadow rays and a ragged AO batch as one query; either part may be
+    None (with a count of 0)."""
+    sp, keep_s = _rays(shadow_rays if shadow_rays is not None else [None] * 6)
+    ap, keep_a = _rays(ao_rays if ao_rays is not None else [None] * 6)
+    lt = (C.c_float * 3)(*[float(v) for v in (light if light is not None else (0, 0, 0))])
+    _call("ddf_query_mixed", h, sp, int(n_shadow), C.addressof(lt), _ptr(out_t), _ptr(out_vis),
+          _ptr(out_occluded), ap, int(n_ao_rays), _ptr(offsets), int(n_points), _ptr(out_hard),
           _ptr(out_soft), _stream(stream))
 
 

@@ -178,3 +178,121 @@ def test_full_size_ragged_ao_fp8_graph(torch_cuda):
     assert np.all(np.abs(g_h - h_ref) <= tie + 1e-6)
     assert np.abs(g_s - s_ref).max() <= 1e-2
     assert ddf.ddf_check_status(m.h) == 0
+
+
+# ------------------------------------------- mixed shadow + ragged AO batch
+
+def _ao_set(scene, P, seed, empty=(0,)):
+    """A ragged AO batch of P points with the listed points given no rays."""
+    rays, offsets = I.ao_rays(scene, P, seed=seed)
+    cnt = np.diff(offsets.astype(np.int64))
+    keep = np.ones(rays.n, bool)
+    for p in empty:
+        keep[offsets[p]:offsets[p + 1]] = False
+        cnt[p] = 0
+    offsets = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int32)
+    return I.Rays(*[a[keep] for a in rays.soa()]), offsets
+
+
+def _outs(torch, ns, P):
+    return (torch.full((max(ns, 1),), -7.0, device="cuda"), torch.full((max(ns, 1),), -7.0, device="cuda"),
+            torch.full((max(ns, 1),), 9, dtype=torch.uint8, device="cuda"),
+            torch.full((P,), -7.0, device="cuda"), torch.full((P,), -7.0, device="cuda"))
+
+
+def _separate(torch, ddf, m, sdev, ns, light, adev, na, d_off, P):
+    t, v, occ, hard, soft = _outs(torch, ns, P)
+    if ns:
+        ddf.ddf_query_shadow(m.h, sdev, ns, light, t, v, occ)
+    ddf.ddf_query_ao(m.h, adev, na, d_off, P, hard, soft)
+    torch.cuda.synchronize()
+    return t[:ns].clone(), v[:ns].clone(), occ[:ns].clone(), hard.clone(), soft.clone()
+
+
+def _mixed(torch, ddf, m, sdev, ns, light, adev, na, d_off, P, outs):
+    t, v, occ, hard, soft = outs
+    for x in outs:
+        x.fill_(7)
+    ddf.ddf_query_mixed(m.h, sdev if ns else None, ns, light, t, v, occ, adev if na else None, na,
+                        d_off, P, hard, soft)
+    torch.cuda.synchronize()
+    return t[:ns].clone(), v[:ns].clone(), occ[:ns].clone(), hard.clone(), soft.clone()
+
+
+@pytest.mark.parametrize("net,prec,kind", [(SMALL, "bf16", "ray"), (PAPER, "fp8", "ray"),
+                                           (SMALL, "fp32", "ray"), (None, "bf16", "hashgrid")])
+@pytest.mark.parametrize("ns", [3001, 1024, 0])
+def test_mixed_query_equals_the_separate_queries(torch_cuda, net, prec, kind, ns):
+    """Shadow rays and a ragged AO batch in one query: 1024-ray chunks put the
+    join inside a chunk (3001 shadow rays), on a chunk boundary (1024) or at
+    the start (no shadow rays); every output equals, bit for bit, the one of
+    the separate ddf_query_shadow and ddf_query_ao calls, in eager mode and in
+    graph mode (one capture, then replays with new data behind the same
+    pointers)."""
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    light = (3.0, 3.0, 3.0)
+    scene = I.random_scene(64, 0, seed=0)
+    P = 200
+    data = []
+    for k in range(3):
+        sr = I.shadow_rays(scene, max(ns, 1), light, seed=36 + 2 * k)
+        ar, offsets = _ao_set(scene, P, seed=37, empty=(0, 99))      # one layout of the sets
+        if k:
+            ar = I.Rays(*[a + np.float32(1e-3 * k) for a in ar.soa()])  # new data, same sizes
+        data.append((sr, ar))
+    na = data[0][1].n
+    if kind == "hashgrid":
+        m = ddf.DDF(4, 64, 2, precision=prec, kind="hashgrid")
+        m.load(I.hashgrid_blob(m.n_params, O.hashgrid_mlp_dims(), seed=0))
+    else:
+        blob = I.xavier_blob(I.NetShape(*net))
+        ar0 = data[0][1]
+        sc = O.calibrate_act_scales(ar0.origins(), ar0.dirs(), blob, *net) if prec == "fp8" else None
+        m = _model(net, prec, blob, sc)
+        ddf.ddf_set_chunk_rays(m.h, 1024)
+    sdev, adev = _dev(torch, data[0][0].soa()), _dev(torch, data[0][1].soa())
+    d_off = torch.from_numpy(offsets).cuda()
+
+    def load(k):
+        for a, b in zip(sdev, _dev(torch, data[k][0].soa())):
+            a.copy_(b)
+        for a, b in zip(adev, _dev(torch, data[k][1].soa())):
+            a.copy_(b)
+
+    refs = []
+    for k in range(3):
+        load(k)
+        refs.append(_separate(torch, ddf, m, sdev, ns, light, adev, na, d_off, P))
+    outs = _outs(torch, ns, P)
+    load(0)
+    got = _mixed(torch, ddf, m, sdev, ns, light, adev, na, d_off, P, outs)
+    assert all(torch.equal(a, b) for a, b in zip(got, refs[0]))
+    assert got[3][0] == 1.0 and got[3][99] == 1.0
+    ddf.ddf_set_graph_mode(m.h, True)
+    for k in (0, 1, 2, 1):
+        load(k)
+        got = _mixed(torch, ddf, m, sdev, ns, light, adev, na, d_off, P, outs)
+        assert all(torch.equal(a, b) for a, b in zip(got, refs[k])), k
+    assert ddf.ddf_check_status(m.h) == 0
+
+
+def test_mixed_query_argument_errors(torch_cuda):
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    m = _model(SMALL, "bf16", I.xavier_blob(I.NetShape(*SMALL)))
+    r = [torch.zeros(8, device="cuda") for _ in range(6)]
+    off = torch.tensor([0, 4, 8], dtype=torch.int32, device="cuda")
+    out = torch.empty(8, device="cuda")
+    occ = torch.empty(8, dtype=torch.uint8, device="cuda")
+    with pytest.raises(ddf.DDFError):       # shadow rays without outputs
+        ddf.ddf_query_mixed(m.h, r, 8, (3, 3, 3), None, None, None, r, 8, off, 2, out, None)
+    with pytest.raises(ddf.DDFError):       # AO rays without shading points
+        ddf.ddf_query_mixed(m.h, r, 8, (3, 3, 3), out, out, occ, r, 8, off, 0, None, None)
+    # nothing at all is a no-op; points with no rays read 1
+    ddf.ddf_query_mixed(m.h, None, 0, None, None, None, None, None, 0, None, 0, None, None)
+    zero = torch.zeros(3, dtype=torch.int32, device="cuda")
+    hard = torch.empty(2, device="cuda")
+    ddf.ddf_query_mixed(m.h, None, 0, None, None, None, None, None, 0, zero, 2, hard, None)
+    torch.cuda.synchronize()
+    assert hard.tolist() == [1.0, 1.0]
