@@ -65,20 +65,37 @@ def test_default_command_line_keeps_the_contract(monkeypatch):
     assert a.warmup >= 3 and a.steps >= 1 and a.rays == 4_194_304
 
 
-def test_oracle_sample_is_bounded_and_exact():
-    """The cpu_baseline leg: consecutive chunks until the time budget is
-    spent, never more than the cap, with the FP64 outputs of the rays it did."""
+def test_oracle_sample_is_bounded_spread_and_exact():
+    """The cpu_baseline leg: blocks taken round-robin from every chunk of the
+    query until the time budget is spent (one round at least), never more than
+    the cap, with the FP64 outputs of exactly the rays it sampled."""
     from oracle import ddf_oracle as O
     from paper_2606_00817_gb300 import inputs as I
-    rays = I.uniform_rays(600, seed=9)
+    rays = I.uniform_rays(1000, seed=9)
     blob = I.xavier_blob(I.NetShape(*bench.NET), seed=0)
-    rate, n, el, ref = bench.oracle_sample(rays, blob, seconds=0.0, chunk=100, cap=400)
-    assert n == 100 and rate > 0 and el > 0                 # one chunk when the budget is 0
-    rate, n, el, ref = bench.oracle_sample(rays, blob, seconds=1e9, chunk=100, cap=400)
-    assert n == 400 and ref["t"].shape == (400,)            # capped
-    sub = rays.slice(0, 400)
+    # chunks of 400, 400 and 200 rays; blocks of 50
+    rate, idx, el, ref = bench.oracle_sample(rays, blob, seconds=0.0, block=50, cap=600, chunk=400)
+    assert rate > 0 and el > 0
+    assert sorted(set(idx // 400)) == [0, 1, 2] and idx.size == 150   # one block per chunk
+    rate, idx, el, ref = bench.oracle_sample(rays, blob, seconds=1e9, block=50, cap=600, chunk=400)
+    assert idx.size == 600 and ref["t"].shape == (600,) and np.unique(idx).size == 600
+    for c in range(3):
+        assert np.sum(idx // 400 == c) == 200                   # the same share of every chunk
+    sub = I.Rays(*[a[idx] for a in rays.soa()])
     want = O.ddf_forward(sub.origins(), sub.dirs(), blob, *bench.NET)
     # the same FP64 values up to the matrix products' summation order, which
     # depends on the batch size
     assert np.allclose(ref["t"], want["t"], rtol=1e-12, atol=1e-13)
     assert np.allclose(ref["vis"], want["vis"], rtol=1e-12, atol=1e-13)
+
+
+def test_tensor_pipe_figures_come_from_the_cited_profile():
+    """The tensor-pipe activity the bench line reports is copied from a
+    committed ncu summary; each figure must still appear in it."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        bench.TENSOR_PIPE["source"])
+    text = open(path).read()
+    assert "sm__pipe_tensor_cycles_active" in text
+    for v in bench.TENSOR_PIPE["active_pct_of_peak"]:
+        assert f"{v} %" in text, v

@@ -155,3 +155,149 @@ def test_distill_sinusoidal_field(torch_cuda):
     ev, tr, hr = _held_out(torch, ddf, sph, box)
     acc, _ = _quality(torch, m, ev, tr, hr)
     assert acc > max(hr.mean(), 1 - hr.mean()) + 0.003, acc
+
+
+# ------------------------------------------- against the oracle's schedule
+
+def _dir_tol(z):
+    """Bound on |x|, |y| of a float32 uniform_sphere_dir whose z is given:
+    r = sqrt(1 - z^2) with 1 - z^2 off by at most 2^-23 (z^2 rounded once,
+    allowing two roundings), so |dr| <= 2^-23 / (sqrt(v) + sqrt(v + 2^-23));
+    plus a few float32 ulps of the sine, cosine and product."""
+    v = np.maximum(0.0, 1.0 - z * z)
+    return 2e-6 + 2.0 ** -23 / (np.sqrt(v) + 2.0 ** -11.5)
+
+
+def test_sample_rays_match_oracle(torch_cuda):
+    """ddf_sample_rays against the oracle's sampler (the same counter-based
+    draws) ray by ray: which primitive, face or camera face a ray takes is
+    decided alike, and positions and directions agree to float32 rounding."""
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    scene, sph, box = _scene(torch)
+    n, seed, step = 30_000, 5, 17
+    g = [a.double().cpu().numpy() for a in _sample(torch, ddf, sph, box, n, seed, step)]
+    og, dg = np.stack(g[:3], 1), np.stack(g[3:], 1)
+    o, d, surf = O.distill_rays(scene, seed, step, n, 0.5)
+    i = np.arange(n)
+    u2, u5 = (O.distill_uniform(seed, step, i, m) for m in (2, 5))
+    # surface origins c + (r + 1e-3) n carry the normal's error times r + 1e-3 <= 0.301
+    tol_o = 2e-6 + np.where(surf, 0.301 * _dir_tol(2 * u2 - 1), 0.0)
+    tol_d = np.where(surf, _dir_tol(2 * u5 - 1), 2e-6)
+    eo = np.abs(og - o)
+    ed = np.abs(dg - d)
+    assert np.all(eo <= tol_o[:, None]), np.max(eo - tol_o[:, None])
+    assert np.all(ed <= tol_d[:, None]), np.max(ed - tol_d[:, None])
+    assert np.median(eo) < 1e-7 and np.median(ed) < 1e-7
+    assert 0.45 < surf.mean() < 0.55
+
+
+def test_shift_rays_match_oracle(torch_cuda):
+    """ddf_shift_rays on oracle-made rays and oracle targets against the
+    oracle's shift rule, ray by ray."""
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    scene, _, _ = _scene(torch)
+    n, first, seed, step = 20_000, 14_000, 9, 4
+    o, d, _ = O.distill_rays(scene, 3, 1, n, 0.5)
+    o32, d32 = o.astype(np.float32), d.astype(np.float32)
+    t, hit = O.cast_scene(scene, o32.astype(np.float64), d32.astype(np.float64))
+    t32 = np.where(hit, t, np.inf).astype(np.float32)
+    rays = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in
+            (o32[:, 0], o32[:, 1], o32[:, 2], d32[:, 0], d32[:, 1], d32[:, 2])]
+    tg = torch.from_numpy(t32).cuda()
+    hg = torch.from_numpy(hit.astype(np.uint8)).cuda()
+    ddf.ddf_shift_rays(rays, tg, hg, n, first, seed, step)
+    torch.cuda.synchronize()
+    og = np.stack([a.double().cpu().numpy() for a in rays[:3]], 1)
+    tgn = tg.double().cpu().numpy()
+    o2, t2 = O.distill_shift(o32.astype(np.float64), d32.astype(np.float64), t32.astype(np.float64),
+                             hit, first, seed, step)
+    h = hit.astype(bool)
+    scale = 1.0 + np.where(h, t32, 0.0)
+    assert np.all(np.abs(og - o2) <= 2e-6 * scale[:, None])
+    assert np.all(np.abs(tgn[h] - t2[h]) <= 2e-6 * scale[h])
+    assert np.array_equal(tgn[~h], t2[~h]) and np.array_equal(og[:first], o2[:first])
+    assert np.sum(h[first:]) > 1000
+
+
+def _manual_distill(torch, ddf, sph, box, blob, net, steps, batch, lrs, frac, shift, seed):
+    """The steps of ddf_distill taken one call at a time, with given rates."""
+    m = ddf.DDF(*net, precision="bf16")
+    m.load(blob)
+    first = batch - int(round(float(np.float32(shift)) * batch))
+    loss = torch.zeros(1, device="cuda")
+    for k in range(steps):
+        rays = _sample(torch, ddf, sph, box, batch, seed, k, frac)
+        t = torch.empty(batch, device="cuda")
+        hit = torch.empty(batch, dtype=torch.uint8, device="cuda")
+        ddf.ddf_cast_scene(sph, 32, box, 32, rays, batch, t, hit)
+        ddf.ddf_shift_rays(rays, t, hit, batch, first, seed, k)
+        ddf.ddf_train_step(m.h, rays, t, hit, batch, float(lrs[k]), loss)
+    torch.cuda.synchronize()
+    w = ddf.ddf_get_weights(m.h, blob.size)
+    m.close()
+    return w
+
+
+def test_distill_follows_the_oracle_schedule(torch_cuda):
+    """ddf_distill over 6 steps leaves the weights bit for bit where the same
+    steps taken one call at a time leave them when each step's rate is the
+    oracle's cosine schedule from the float32 lr0 the library receives
+    (rounded to float32); a constant rate, or the
+    schedule shifted by one step, does not."""
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    _, sph, box = _scene(torch)
+    net, steps, batch, lr0, frac, shift, seed = (6, 128, 4), 6, 4096, 1e-3, 0.5, 0.3, 3
+    blob = I.xavier_blob(I.NetShape(*net))
+    a = ddf.DDF(*net, precision="bf16")
+    a.load(blob)
+    ddf.ddf_distill(a.h, sph, 32, box, 32, steps, batch, lr0, frac, shift, seed=seed)
+    wa = ddf.ddf_get_weights(a.h, blob.size)
+    a.close()
+    # the library receives lr0 as a float32, so the schedule starts from that value
+    lr0_32 = float(np.float32(lr0))
+    lrs = O.distill_lr(lr0_32, np.arange(steps), steps).astype(np.float32)
+    run = lambda r: _manual_distill(torch, ddf, sph, box, blob, net, steps, batch, r, frac, shift,
+                                    seed)
+    assert np.array_equal(run(lrs), wa)
+    assert not np.array_equal(run(np.full(steps, lr0, np.float32)), wa)
+    assert not np.array_equal(run(O.distill_lr(lr0_32, np.arange(1, steps + 1), steps)
+                                  .astype(np.float32)), wa)
+
+
+def test_distill_pool_draws_the_oracle_rows(torch_cuda):
+    """ddf_distill_pool over 4 steps equals, bit for bit, the steps taken one
+    call at a time with each batch gathered from the pool at the rows the
+    oracle's pool draw picks, the shift applied and the oracle's rate."""
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    _, sph, box = _scene(torch)
+    net, steps, batch, lr0, shift, seed = (6, 128, 4), 4, 4096, 1e-3, 0.3, 11
+    n_pool = 50_000
+    pool = _sample(torch, ddf, sph, box, n_pool, 77, 0)
+    pt = torch.empty(n_pool, device="cuda")
+    ph = torch.empty(n_pool, dtype=torch.uint8, device="cuda")
+    ddf.ddf_cast_scene(sph, 32, box, 32, pool, n_pool, pt, ph)
+    blob = I.xavier_blob(I.NetShape(*net))
+    a = ddf.DDF(*net, precision="bf16")
+    a.load(blob)
+    ddf.ddf_distill_pool(a.h, pool, pt, ph, n_pool, steps, batch, lr0, shift, seed=seed)
+    wa = ddf.ddf_get_weights(a.h, blob.size)
+    a.close()
+    b = ddf.DDF(*net, precision="bf16")
+    b.load(blob)
+    first = batch - int(round(float(np.float32(shift)) * batch))
+    loss = torch.zeros(1, device="cuda")
+    lrs = O.distill_lr(float(np.float32(lr0)), np.arange(steps), steps).astype(np.float32)
+    for k in range(steps):
+        j = torch.from_numpy(O.distill_pool_index(seed, k, np.arange(batch), n_pool)).cuda()
+        rays = [p[j].contiguous() for p in pool]
+        t = pt[j].contiguous()
+        hit = ph[j].contiguous()
+        ddf.ddf_shift_rays(rays, t, hit, batch, first, seed, k)
+        ddf.ddf_train_step(b.h, rays, t, hit, batch, float(lrs[k]), loss)
+    torch.cuda.synchronize()
+    assert np.array_equal(ddf.ddf_get_weights(b.h, blob.size), wa)
+    b.close()
