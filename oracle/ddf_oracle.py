@@ -26,6 +26,9 @@ What the paper fixes and what this module reads into it:
     directions.
   * Sec. 3.2: supervision from an exact ray cast of the geometry; here the
     geometry is a union of spheres and boxes with closed-form intersections.
+  * Sec. 3.2 / 3.4: the distillation schedule (training-ray sampler, the
+    ray-march shifted points, the cosine learning rate; readings in its
+    section below).
   * Sec. 4.4: sphere tracing an SDF is the sequential baseline.
   * Sec. 3.4: the hash-grid field (readings in its section below).
   * Sec. 3.3 / the application: shadow and AO images (readings below).
@@ -777,9 +780,16 @@ def cosine_dirs(n, u1, u2):
     return (r * np.cos(phi))[:, None] * t1 + (r * np.sin(phi))[:, None] * t2 + z[:, None] * n
 
 
-def gi_images(scene, eye, target, up, fov_y, width, height, light, ao_samples, seed):
-    """Shadow (1 lit, 0 shadowed) and ambient-occlusion images of the scene
-    from exact casts; background -1. Returns (shadow, ao) [height, width]."""
+def gi_images(scene, eye, target, up, fov_y, width, height, light, ao_samples, seed,
+              field_blob=None, field_precision="exact", detail=False):
+    """Shadow (1 lit, 0 shadowed) and ambient-occlusion images of the scene;
+    background -1. The secondary rays are answered by exact casts, or, with
+    field_blob (a hash-grid field's blob), by that field (hashgrid_forward
+    in field_precision): a ray counts as a hit when z1 > 0, and a shadow ray
+    occludes when it hits closer than the light. Returns (shadow, ao)
+    [height, width], and with detail also, per foreground pixel (in pixel
+    order), the shadow rays' t, z1 (exact casts: +-1) and light distance and
+    the hemisphere rays' z1 [pixels, ao_samples]."""
     o, d = camera_rays(eye, target, up, fov_y, width, height)
     t, hit = cast_scene(scene, o, d)
     npx = width * height
@@ -790,18 +800,33 @@ def gi_images(scene, eye, target, up, fov_y, width, height, light, ao_samples, s
     nrm = surface_normal(scene, p)
     nrm = np.where(np.sum(nrm * d[idx], axis=1, keepdims=True) > 0, -nrm, nrm)
     sp = p + 1e-3 * nrm
+
+    def answer(org, dirs):
+        """(t, z1) of secondary rays: exact casts or the field."""
+        if field_blob is None:
+            ts, hs = cast_scene(scene, org, dirs)
+            return ts, np.where(hs, 1.0, -1.0)
+        f = hashgrid_forward(org, dirs, field_blob, precision=field_precision)
+        return f["t"], f["z"][:, 1]
+
     to_l = np.asarray(light, F64)[None, :] - sp
     dist = np.linalg.norm(to_l, axis=1)
-    ts, hs = cast_scene(scene, sp, to_l / dist[:, None])
-    shadow[idx] = np.where(hs & (ts < dist), 0.0, 1.0)
+    ts, zs = answer(sp, to_l / dist[:, None])
+    shadow[idx] = np.where((zs > 0) & (ts < dist), 0.0, 1.0)
     hits = np.zeros(idx.size)
+    z_ao = np.zeros((idx.size, ao_samples))
     for j in range(ao_samples):
         u1 = gi_uniform(seed, idx, j, 0)
         u2 = gi_uniform(seed, idx, j, 1)
-        _, ha = cast_scene(scene, sp, cosine_dirs(nrm, u1, u2))
-        hits += ha
+        _, za = answer(sp, cosine_dirs(nrm, u1, u2))
+        z_ao[:, j] = za
+        hits += za > 0
     ao[idx] = 1.0 - hits / ao_samples
-    return shadow.reshape(height, width), ao.reshape(height, width)
+    images = (shadow.reshape(height, width), ao.reshape(height, width))
+    if detail:
+        return images + ({"pixels": idx, "shadow_t": ts, "shadow_z1": zs, "shadow_dist": dist,
+                          "ao_z1": z_ao},)
+    return images
 
 
 # --------------------------- distillation schedule (Sec. 3.2 / Sec. 3.4)
@@ -874,27 +899,27 @@ def distill_rays(scene, seed, step, n, surface_frac):
             nv = uniform_sphere_dir(u[2][sph], u[3][sph])
             pt[sph] = np.asarray(scene.centers, F64)[js] + np.asarray(scene.radii, F64)[js, None] * nv
             nrm[sph] = nv
-        bx = surf & (p >= ns)
-        for r in np.nonzero(bx)[0]:
-            lo = np.asarray(scene.box_lo[p[r] - ns], F64)
-            hi = np.asarray(scene.box_hi[p[r] - ns], F64)
-            face = int(_pick(u[2][r], 6))
-            axis, plus = face // 2, face % 2 == 1
-            a, c = (axis + 1) % 3, (axis + 2) % 3
-            pt[r, a] = lo[a] + u[3][r] * (hi[a] - lo[a])
-            pt[r, c] = lo[c] + u[4][r] * (hi[c] - lo[c])
-            pt[r, axis] = hi[axis] if plus else lo[axis]
-            nrm[r, axis] = 1.0 if plus else -1.0
+        r = np.nonzero(surf & (p >= ns))[0]           # box faces
+        lo = np.asarray(scene.box_lo, F64)[p[r] - ns]
+        hi = np.asarray(scene.box_hi, F64)[p[r] - ns]
+        face = _pick(u[2][r], 6)
+        axis, plus = face // 2, face % 2 == 1
+        a, c = (axis + 1) % 3, (axis + 2) % 3
+        k = np.arange(r.size)
+        pt[r, a] = lo[k, a] + u[3][r] * (hi[k, a] - lo[k, a])
+        pt[r, c] = lo[k, c] + u[4][r] * (hi[k, c] - lo[k, c])
+        pt[r, axis] = np.where(plus, hi[k, axis], lo[k, axis])
+        nrm[r, axis] = np.where(plus, 1.0, -1.0)
         o[surf] = pt[surf] + DISTILL_SURFACE_OFFSET * nrm[surf]
         d[surf] = uniform_sphere_dir(u[5][surf], u[6][surf])
     # camera rays
+    r = np.nonzero(~surf)[0]
+    face = _pick(u[1][r], 6)
+    axis, plus = face // 2, face % 2 == 1
+    o[r, (axis + 1) % 3] = 2.0 * u[2][r] - 1.0
+    o[r, (axis + 2) % 3] = 2.0 * u[3][r] - 1.0
+    o[r, axis] = np.where(plus, 1.0, -1.0)
     cam = ~surf
-    face = _pick(u[1], 6)
-    for r in np.nonzero(cam)[0]:
-        axis, plus = int(face[r]) // 2, int(face[r]) % 2 == 1
-        o[r, (axis + 1) % 3] = 2.0 * u[2][r] - 1.0
-        o[r, (axis + 2) % 3] = 2.0 * u[3][r] - 1.0
-        o[r, axis] = 1.0 if plus else -1.0
     tgt = np.stack([1.8 * u[4] - 0.9, 1.8 * u[5] - 0.9, 1.8 * u[6] - 0.9], axis=1)
     v = tgt[cam] - o[cam]
     d[cam] = v / np.linalg.norm(v, axis=1, keepdims=True)

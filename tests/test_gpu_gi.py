@@ -90,3 +90,42 @@ def test_field_render_approaches_exact(torch_cuda):
     ps, pa = _psnr(fs, es, fg), _psnr(fa, ea, fg)
     assert ps > 10.0 and pa > 14.5, (ps, pa)
     assert ddf.ddf_check_status(m.h) == 0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_field_render_matches_oracle(torch_cuda, prec):
+    """The images with every secondary ray answered by a hash-grid field (a
+    seeded random field, so that hits, misses and distances vary) against
+    the oracle answering the same rays with the same blob
+    (gi_images(field_blob=...)), pixel by pixel. Decisions within reach of
+    float32 and bf16 rounding (|z1| or |t - light distance| below the
+    margin) may differ; so may pixels whose primary hit is decided
+    differently in float32 (silhouettes, box edges), as in the exact render."""
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    scene, sph, box = _scene(torch)
+    m = ddf.DDF(4, 64, 2, precision=prec, kind="hashgrid")
+    blob = I.hashgrid_blob(m.n_params, O.hashgrid_mlp_dims(), seed=3, table_scale=0.5)
+    W, H, k = 96, 72, 6
+    args = (scene, CAM[0:3], CAM[3:6], CAM[6:9], CAM[9], W, H, LIGHT, k, 5)
+    fp = "exact" if prec == "fp32" else "bf16"
+    # centre the visibility logit: the head bias b1 moves every z1 alike, so
+    # shifting it by the median z1 of the shadow rays makes half of them hit
+    _, _, det = O.gi_images(*args, field_blob=blob, field_precision=fp, detail=True)
+    blob[-1] -= np.float32(np.median(det["shadow_z1"]))
+    m.load(blob)
+    sh, ao = _render(torch, ddf, m.h, sph, box, W, H, k)
+    rs, ra, det = O.gi_images(*args, field_blob=blob, field_precision=fp, detail=True)
+    margin = 1e-2 if prec == "fp32" else 5e-2
+    px = det["pixels"]
+    sh_g, ao_g = sh.ravel()[px], ao.ravel()[px]
+    assert np.mean(sh_g >= 0) > 0.995                          # the same foreground
+    clear = (np.abs(det["shadow_z1"]) > margin) & \
+            (np.abs(det["shadow_t"] - det["shadow_dist"]) > margin * det["shadow_dist"])
+    assert clear.mean() > 0.7
+    assert 0.2 < np.mean(rs.ravel()[px] == 0) < 0.8             # the field shadows some pixels
+    assert np.mean(sh_g[clear] == rs.ravel()[px][clear]) >= 0.995
+    ties = np.sum(np.abs(det["ao_z1"]) <= margin, axis=1)
+    ok = np.abs(ao_g - ra.ravel()[px]) <= ties / k + 1e-6
+    assert np.mean(ok) >= 0.99
+    assert ddf.ddf_check_status(m.h) == 0

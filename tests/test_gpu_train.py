@@ -1,18 +1,24 @@
 """GPU tests of the distillation step: the exact analytic caster, the
 gradient, Adam, and a full-size (65,536-ray, 8 x 1280) training run.
 
-Gradient bounds, per weight/bias block, in L2 norm. Let
-  noise = |g_emu - g_exact|  (what bf16 rounding alone costs: the oracle
-          emulating the step's bf16 roundings against exact float64)
-Then the GPU gradient must satisfy
-  |g_gpu - g_emu|   <= 0.4 noise + 1e-3 |g_emu|
-  |g_gpu - g_exact| <= 1.2 noise + 1e-3 |g_exact|
-i.e. it is as good as the emulated arithmetic and tracks its particular
-rounding pattern. It cannot track it exactly: the tensor cores accumulate in
-FP32 and the oracle in float64, so a bf16 rounding of an activation or of a
-back-propagated gradient can fall the other way, and such differences
-compound through the layers (measured on GB300: the ratio stays near 0.25-0.29
-for 8 x 1280, and below 0.01 for 4 x 128)."""
+The gradient is compared element by element. Let, per weight or bias block,
+  n_i   = |g_emu,i - g_exact,i|  what bf16 rounding alone costs element i
+          (the oracle emulating the step's bf16 roundings, against exact
+          float64), and sigma = the root mean square of those over the block.
+The GPU and the emulating oracle round the same values at the same places;
+they differ only where FP32 accumulation (against float64) moves a value
+across a bf16 rounding boundary, which changes that value by one bf16 ulp and
+carries through the later layers. Such flips are a small fraction of all
+roundings, so their effect on an element is bounded by that element's own
+rounding cost plus a few times the block's typical one:
+  |g_gpu,i - g_emu,i| <= n_i + 3 sigma   for >= 99.99 % of every block,
+  |g_gpu,i - g_emu,i| <= n_i + 12 sigma  for every element.
+(Measured on GB300, 8 x 1280: the largest gap is 8.3 sigma at a batch of
+4,096 and 2.4 sigma at 65,536; at 3 sigma at most 2e-5 of a block is
+outside; for 4 x 128 every gap is below 0.4 sigma.) With sigma at 0.3-10 %
+of the block's gradient scale, an element that is wrong by its own size
+fails. The norm-wise comparison with the exact gradient is kept beside it:
+  |g_gpu - g_exact| <= 1.2 |g_emu - g_exact| + 1e-3 |g_exact|  per block."""
 import numpy as np
 import pytest
 
@@ -81,8 +87,42 @@ def _batch(net, B, seed):
     return rays, t_ref.astype(np.float32), hit_ref.astype(np.uint8)
 
 
-@pytest.mark.parametrize("net,B", [(SMALL, 4096), (PAPER, 4096)])
-def test_gradient_matches_oracle(torch_cuda, net, B):
+def _elementwise(g, g_emu, g_ex, net):
+    """Checks the element-wise bounds of the module docstring on every block
+    and returns the per-element bound n_i + 12 sigma (flat, blob layout)."""
+    bound = []
+    for i, (a, b, c) in enumerate(zip(_blocks(g, net), _blocks(g_emu, net), _blocks(g_ex, net))):
+        n = np.abs(b - c)
+        sigma = np.sqrt(np.mean(n * n))
+        d = np.abs(a - b)
+        assert np.mean(d <= n + 3 * sigma) >= 0.9999, (i, np.mean(d <= n + 3 * sigma))
+        assert np.all(d <= n + 12 * sigma), (i, np.max((d - n) / sigma))
+        assert np.linalg.norm(a - c) <= 1.2 * np.linalg.norm(b - c) + 1e-3 * np.linalg.norm(c), i
+        bound.append(n + 12 * sigma)
+    return np.concatenate(bound)
+
+
+def _oracle_grads(rays, blob, net, tt, y):
+    L_emu, g_emu = O.train_grad(rays.origins(), rays.dirs(), blob, *net, tt, y, precision="bf16")
+    _, g_ex = O.ddf_loss_grad(rays.origins(), rays.dirs(), blob, *net, tt, y)
+    return L_emu, g_emu, g_ex
+
+
+def _adam_interval(w0, g_emu, bound, lr, eps=1e-8):
+    """The first Adam step from zero moments moves w by -lr g / (|g| + eps),
+    which grows with g; for every gradient inside [g_emu - bound, g_emu +
+    bound] the new weight lies in the returned [lo, hi]."""
+    phi = lambda x: x / (np.abs(x) + eps)
+    return w0 - lr * phi(g_emu + bound), w0 - lr * phi(g_emu - bound)
+
+
+@pytest.mark.parametrize("net,B", [(SMALL, 4096), (PAPER, 4096), (PAPER, 65536)])
+def test_gradient_and_adam_match_oracle(torch_cuda, net, B):
+    """The gradient of one distillation batch, element by element (module
+    docstring), at the small field, the paper-sized field and the 65,536-ray
+    batch the benchmark trains on; then the first Adam step: every updated
+    weight lies where the oracle's Adam puts it for some gradient within the
+    element's bound (up to two float32 ulps of the weight)."""
     torch = torch_cuda
     from paper_2606_00817_gb300 import ddf
     blob = I.xavier_blob(I.NetShape(*net))
@@ -90,44 +130,30 @@ def test_gradient_matches_oracle(torch_cuda, net, B):
     m = ddf.DDF(*net, precision="bf16")
     m.load(blob)
     loss = torch.zeros(1, device="cuda")
-    ddf.ddf_compute_grad(m.h, _dev(torch, rays.soa()), torch.from_numpy(tt).cuda(),
-                         torch.from_numpy(y).cuda(), B, loss)
+    dev = _dev(torch, rays.soa())
+    tt_d, y_d = torch.from_numpy(tt).cuda(), torch.from_numpy(y).cuda()
+    ddf.ddf_compute_grad(m.h, dev, tt_d, y_d, B, loss)
     g = ddf.ddf_get_grad(m.h, blob.size).astype(np.float64)
-    L_emu, g_emu = O.train_grad(rays.origins(), rays.dirs(), blob, *net, tt, y, precision="bf16")
-    L_ex, g_ex = O.ddf_loss_grad(rays.origins(), rays.dirs(), blob, *net, tt, y)
-    assert abs(loss.item() - L_emu) <= 1e-4 * abs(L_emu)
-    for i, (a, b, c) in enumerate(zip(_blocks(g, net), _blocks(g_emu, net), _blocks(g_ex, net))):
-        noise = np.linalg.norm(b - c)
-        assert np.linalg.norm(a - b) <= 0.4 * noise + 1e-3 * np.linalg.norm(b), i
-        assert np.linalg.norm(a - c) <= 1.2 * noise + 1e-3 * np.linalg.norm(c), i
-    assert ddf.ddf_check_status(m.h) == 0
-
-
-def test_adam_step_matches_oracle_update(torch_cuda):
-    """First Adam step from zero moments: w1 = w0 - lr g / (|g| + eps) per
-    parameter, with g the oracle's own gradient, wherever |g| is not tiny."""
-    torch = torch_cuda
-    from paper_2606_00817_gb300 import ddf
-    net, B, lr = SMALL, 4096, 1e-3
-    blob = I.xavier_blob(I.NetShape(*net))
-    rays, tt, y = _batch(net, B, seed=43)
-    m = ddf.DDF(*net, precision="bf16")
-    m.load(blob)
-    ddf.ddf_train_step(m.h, _dev(torch, rays.soa()), torch.from_numpy(tt).cuda(),
-                       torch.from_numpy(y).cuda(), B, lr)
+    lr = 1e-3
+    ddf.ddf_train_step(m.h, dev, tt_d, y_d, B, lr)
     w1 = ddf.ddf_get_weights(m.h, blob.size).astype(np.float64)
-    _, g = O.train_grad(rays.origins(), rays.dirs(), blob, *net, tt, y, precision="bf16")
-    w_ref, _, _ = O.adam_step(blob.astype(np.float64), g, np.zeros_like(g), np.zeros_like(g), 1, lr)
-    big = np.abs(g) > 1e-4 * np.abs(g).max()
-    agree = np.abs(w1 - w_ref) <= 2e-6
-    assert big.mean() > 0.2
-    assert agree[big].mean() > 0.99
-    # queries now use the updated weights
-    t_after, _ = m.query(_dev(torch, rays.slice(0, 256).soa()))
-    emu = O.ddf_forward(rays.origins()[:256], rays.dirs()[:256], w_ref.astype(np.float32), *net,
-                        precision="bf16")
-    err = np.abs(t_after.double().cpu().numpy() - emu["t"])
-    assert np.median(err) < 5e-3
+    assert ddf.ddf_check_status(m.h) == 0
+    m.close()
+    L_emu, g_emu, g_ex = _oracle_grads(rays, blob, net, tt, y)
+    assert abs(loss.item() - L_emu) <= 1e-4 * abs(L_emu)
+    bound = _elementwise(g, g_emu, g_ex, net)
+    w0 = blob.astype(np.float64)
+    lo, hi = _adam_interval(w0, g_emu, bound, float(np.float32(lr)))
+    # float32 Adam: the constants 0.9f and 0.999f (1 - 0.999f is 1.3e-5 off
+    # 0.001) and the float32 moments move the step by up to about 1e-5 lr;
+    # the new weight is then rounded once
+    tol = 2 * np.spacing(np.abs(blob)).astype(np.float64) + 2e-5 * lr
+    excess = np.maximum(lo - tol - w1, w1 - hi - tol)
+    assert np.all(excess <= 0), (np.max(excess) / lr, int(np.argmax(excess)), np.mean(excess > 0))
+    # where the bound leaves the gradient's sign in no doubt the interval
+    # lies on one side of w0: the step's direction is fixed
+    sure = np.sign(g_emu - bound) == np.sign(g_emu + bound)
+    assert np.all(np.sign(w0 - w1)[sure & (np.abs(w1 - w0) > tol)] == np.sign(g_emu)[sure & (np.abs(w1 - w0) > tol)])
 
 
 def test_full_size_distillation_lowers_the_loss(torch_cuda):

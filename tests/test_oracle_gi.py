@@ -77,3 +77,39 @@ def test_one_sphere_silhouette_and_shadow():
     assert np.all(sh.ravel()[fg] == 1.0) and np.all(ao.ravel()[fg] == 1.0)
     sh2, _ = O.gi_images(sc, [0, 0, -4], [0, 0, 0], [0, 1, 0], fov, W, H, [0, 0, 10], 2, 1)
     assert np.all(sh2.ravel()[fg] == 0.0)
+
+
+def test_field_answered_images_of_constant_fields():
+    """With every table entry and weight zero the field answers every ray
+    with its head biases: z1 = b1 and t = softplus(b0). So the images are
+    closed forms: all foreground shadowed and fully occluded when b1 > 0 and
+    t is below every light distance; all lit and open when b1 < 0; lit but
+    fully occluded when t exceeds every light distance."""
+    scene = I.random_scene(32, 32, seed=0)
+    dims = O.hashgrid_mlp_dims()
+    n_tab = int(sum(O.hashgrid_table_sizes())) * 2
+    n_mlp = sum(fo * fi + fo for fo, fi in dims)
+    cam = ([2.5, 1.8, -3.0], [0, 0, 0], [0, 1, 0], np.radians(50.0))
+    ex_s, _ = O.gi_images(scene, *cam, 24, 16, (3.0, 3.0, 3.0), 4, 5)
+    fg = ex_s >= 0
+    assert 0.05 < fg.mean() < 0.95
+
+    def field(b0, b1):
+        blob = np.zeros(n_tab + n_mlp, np.float32)
+        blob[-2:] = [b0, b1]
+        return blob
+
+    def images(blob):
+        return O.gi_images(scene, *cam, 24, 16, (3.0, 3.0, 3.0), 4, 5, field_blob=blob)
+
+    s, a = images(field(np.log(np.expm1(0.5)), 1.0))        # t = 0.5, hit
+    assert np.all(s[fg] == 0) and np.all(a[fg] == 0) and np.all(s[~fg] == -1) and np.all(a[~fg] == -1)
+    s, a = images(field(0.0, -1.0))                         # misses
+    assert np.all(s[fg] == 1) and np.all(a[fg] == 1)
+    s, a = images(field(40.0, 1.0))                         # hits beyond the light
+    assert np.all(s[fg] == 1) and np.all(a[fg] == 0)
+    # detail: the shadow rays' distances to the light are those of the exact path
+    s, a, det = O.gi_images(scene, *cam, 24, 16, (3.0, 3.0, 3.0), 4, 5,
+                            field_blob=field(0.0, 1.0), detail=True)
+    assert det["pixels"].size == fg.sum() and det["ao_z1"].shape == (fg.sum(), 4)
+    assert np.allclose(det["shadow_z1"], 1.0) and np.allclose(det["shadow_t"], np.log(2.0))
