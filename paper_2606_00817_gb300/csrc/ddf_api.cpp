@@ -330,8 +330,15 @@ ddf_status forward_tc(ddf_s* h, ddf::RaySoA rays, int m, ddf::HeadOut out, cudaS
     if (t.pair) {
       const int64_t tiles = ((m + 255) / 256) * static_cast<int64_t>(W / 256);
       const int clusters = static_cast<int>(std::min<int64_t>(tiles, h->pair_clusters));
+      CUtensorMap tmO;  // staged outputs leave shared memory by TMA stores of 32-row boxes
+      const bool tma_out = t.staged && !last;
+      if (tma_out) {
+        if (!make_tmap(&tmO, p.out, out_fp8, W, m, static_cast<uint64_t>(W) * (out_fp8 ? 1 : 2), 32))
+          return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for an output map");
+        p.tma_out = 1;
+      }
       DDF_CK(ddf::launch_tc_gemm_pair(in_fp8, out_fp8, t.staged, t.epi_warps, tmA, h->tmB[l], p,
-                                      clusters, st));
+                                      clusters, st, tma_out ? &tmO : nullptr));
     } else {
       const int64_t tiles = ((m + 127) / 128) * static_cast<int64_t>(W / t.bn);
       const int grid = static_cast<int>(std::min<int64_t>(tiles, h->num_sms));

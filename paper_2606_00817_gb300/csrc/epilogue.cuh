@@ -23,6 +23,7 @@ struct EpiVectors {
   const float* scale;  // [N] or nullptr
   const float* hw0;    // [N] or nullptr (mode 1)
   const float* hw1;    // [N] or nullptr (mode 1)
+  float uscale;        // the scale of every column when `scale` is nullptr
 };
 
 // Widest layer whose vectors the tensor-core kernels stage (4 x 2048 floats
@@ -33,15 +34,20 @@ constexpr int kMaxStagedColumns = 2048;
 __host__ __device__ constexpr int epi_vector_bytes(int n) { return 4 * n * 4; }
 
 // Cooperative copy of the layer's vectors into shared memory (all threads).
+// An e4m3 output's scale (out_scale = 1 / s_out, a power of two) is folded
+// into them: ReLU(acc scale + bias) out_scale = ReLU(acc (scale out_scale) +
+// bias out_scale) exactly, since multiplying by a power of two commutes with
+// float32 rounding, so the epilogue saves one multiply per element.
 __device__ __forceinline__ EpiVectors stage_epi_vectors(const TcGemmParams& p, float* smem) {
   const int n = p.N;
   float* sb = smem;
   float* ss = smem + n;
   float* s0 = smem + 2 * n;
   float* s1 = smem + 3 * n;
+  const float os = p.out_scale;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    if (p.bias != nullptr) sb[i] = p.bias[i];
-    if (p.col_scale != nullptr) ss[i] = p.col_scale[i];
+    if (p.bias != nullptr) sb[i] = p.bias[i] * os;
+    if (p.col_scale != nullptr) ss[i] = p.col_scale[i] * os;
     if (p.mode == 1 || p.mode == 4) {  // only a last layer folds the head
       s0[i] = p.head_w[i];
       s1[i] = p.head_w[n + i];
@@ -49,7 +55,7 @@ __device__ __forceinline__ EpiVectors stage_epi_vectors(const TcGemmParams& p, f
   }
   const bool head = p.mode == 1 || p.mode == 4;
   return EpiVectors{sb, p.col_scale != nullptr ? ss : nullptr, head ? s0 : nullptr,
-                    head ? s1 : nullptr};
+                    head ? s1 : nullptr, os};
 }
 
 __device__ __forceinline__ uint32_t epi_pack_bf16x2(float lo, float hi) {
@@ -63,26 +69,42 @@ __device__ __forceinline__ uint32_t epi_pack_e4m3x4(float a, float b, float c, f
   return (lo & 0xFFFFu) | (hi << 16);
 }
 
+// ReLU in the conversion: max(x, 0) rounded, with lo in the low half.
+__device__ __forceinline__ uint32_t epi_pack_bf16x2_relu(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
+// ReLU in the conversion: four e4m3 codes of max(x, 0) (saturating at
+// 448), a in the lowest byte.
+__device__ __forceinline__ uint32_t epi_pack_e4m3x4_relu(float a, float b, float c, float d) {
+  uint16_t lo, hi;
+  asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(b), "f"(a));
+  asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(d), "f"(c));
+  return static_cast<uint32_t>(lo) | (static_cast<uint32_t>(hi) << 16);
+}
+
 // Processes the 32 accumulator values v of columns [nc, nc + 32) of `row`.
 template <bool OUT_FP8>
 __device__ __forceinline__ void epi_chunk(const TcGemmParams& p, const EpiVectors& ev,
                                           const uint32_t (&v)[32], int row, bool row_ok, int nc,
                                           float& h0, float& h1) {
-  float x[32];
+  float x[32];  // before the ReLU, which the packing conversions (or the head) apply
   const float4* b4 = reinterpret_cast<const float4*>(ev.bias + nc);
 #pragma unroll
   for (int j4 = 0; j4 < 8; ++j4) {
     const float4 bb = b4[j4];
-    float4 cs = make_float4(1.f, 1.f, 1.f, 1.f);
+    float4 cs = make_float4(ev.uscale, ev.uscale, ev.uscale, ev.uscale);
     if (ev.scale != nullptr) cs = reinterpret_cast<const float4*>(ev.scale + nc)[j4];
-    x[4 * j4 + 0] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 0]), cs.x, bb.x), 0.f);
-    x[4 * j4 + 1] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 1]), cs.y, bb.y), 0.f);
-    x[4 * j4 + 2] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 2]), cs.z, bb.z), 0.f);
-    x[4 * j4 + 3] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 3]), cs.w, bb.w), 0.f);
+    x[4 * j4 + 0] = fmaf(__uint_as_float(v[4 * j4 + 0]), cs.x, bb.x);
+    x[4 * j4 + 1] = fmaf(__uint_as_float(v[4 * j4 + 1]), cs.y, bb.y);
+    x[4 * j4 + 2] = fmaf(__uint_as_float(v[4 * j4 + 2]), cs.z, bb.z);
+    x[4 * j4 + 3] = fmaf(__uint_as_float(v[4 * j4 + 3]), cs.w, bb.w);
   }
   if (p.mode == 0) {
     if (p.amax != nullptr) {  // calibration: the warp's largest output of valid rows
-      float m = 0.f;
+      float m = 0.f;          // max(0, max x) = the largest output after the ReLU
       if (row_ok) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) m = fmaxf(m, x[j]);
@@ -95,16 +117,15 @@ __device__ __forceinline__ void epi_chunk(const TcGemmParams& p, const EpiVector
     if (!row_ok) return;
     if constexpr (OUT_FP8) {
       uint8_t* dst = static_cast<uint8_t*>(p.out) + static_cast<size_t>(row) * p.ldo + nc;
-      const float os = p.out_scale;
-      uint4 w0, w1;
-      w0.x = epi_pack_e4m3x4(x[0] * os, x[1] * os, x[2] * os, x[3] * os);
-      w0.y = epi_pack_e4m3x4(x[4] * os, x[5] * os, x[6] * os, x[7] * os);
-      w0.z = epi_pack_e4m3x4(x[8] * os, x[9] * os, x[10] * os, x[11] * os);
-      w0.w = epi_pack_e4m3x4(x[12] * os, x[13] * os, x[14] * os, x[15] * os);
-      w1.x = epi_pack_e4m3x4(x[16] * os, x[17] * os, x[18] * os, x[19] * os);
-      w1.y = epi_pack_e4m3x4(x[20] * os, x[21] * os, x[22] * os, x[23] * os);
-      w1.z = epi_pack_e4m3x4(x[24] * os, x[25] * os, x[26] * os, x[27] * os);
-      w1.w = epi_pack_e4m3x4(x[28] * os, x[29] * os, x[30] * os, x[31] * os);
+      uint4 w0, w1;  // the output scale is already in the vectors
+      w0.x = epi_pack_e4m3x4_relu(x[0], x[1], x[2], x[3]);
+      w0.y = epi_pack_e4m3x4_relu(x[4], x[5], x[6], x[7]);
+      w0.z = epi_pack_e4m3x4_relu(x[8], x[9], x[10], x[11]);
+      w0.w = epi_pack_e4m3x4_relu(x[12], x[13], x[14], x[15]);
+      w1.x = epi_pack_e4m3x4_relu(x[16], x[17], x[18], x[19]);
+      w1.y = epi_pack_e4m3x4_relu(x[20], x[21], x[22], x[23]);
+      w1.z = epi_pack_e4m3x4_relu(x[24], x[25], x[26], x[27]);
+      w1.w = epi_pack_e4m3x4_relu(x[28], x[29], x[30], x[31]);
       reinterpret_cast<uint4*>(dst)[0] = w0;
       reinterpret_cast<uint4*>(dst)[1] = w1;
     } else {
@@ -113,14 +134,16 @@ __device__ __forceinline__ void epi_chunk(const TcGemmParams& p, const EpiVector
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         uint4 w;
-        w.x = epi_pack_bf16x2(x[8 * k + 0], x[8 * k + 1]);
-        w.y = epi_pack_bf16x2(x[8 * k + 2], x[8 * k + 3]);
-        w.z = epi_pack_bf16x2(x[8 * k + 4], x[8 * k + 5]);
-        w.w = epi_pack_bf16x2(x[8 * k + 6], x[8 * k + 7]);
+        w.x = epi_pack_bf16x2_relu(x[8 * k + 0], x[8 * k + 1]);
+        w.y = epi_pack_bf16x2_relu(x[8 * k + 2], x[8 * k + 3]);
+        w.z = epi_pack_bf16x2_relu(x[8 * k + 4], x[8 * k + 5]);
+        w.w = epi_pack_bf16x2_relu(x[8 * k + 6], x[8 * k + 7]);
         reinterpret_cast<uint4*>(dst)[k] = w;
       }
     }
   } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) x[j] = fmaxf(x[j], 0.f);
     const float4* w0 = reinterpret_cast<const float4*>(ev.hw0 + nc);
     const float4* w1 = reinterpret_cast<const float4*>(ev.hw1 + nc);
 #pragma unroll
@@ -225,30 +248,29 @@ template <bool OUT_FP8>
 __device__ __forceinline__ void epi_chunk_stage(const TcGemmParams& p, const EpiVectors& ev,
                                                 const uint32_t (&v)[32], int nc, int c,
                                                 uint8_t* stage, int lane) {
-  float x[32];
+  float x[32];  // before the ReLU, which the packing conversions apply
   const float4* b4 = reinterpret_cast<const float4*>(ev.bias + nc);
 #pragma unroll
   for (int j4 = 0; j4 < 8; ++j4) {
     const float4 bb = b4[j4];
-    float4 cs = make_float4(1.f, 1.f, 1.f, 1.f);
+    float4 cs = make_float4(ev.uscale, ev.uscale, ev.uscale, ev.uscale);
     if (ev.scale != nullptr) cs = reinterpret_cast<const float4*>(ev.scale + nc)[j4];
-    x[4 * j4 + 0] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 0]), cs.x, bb.x), 0.f);
-    x[4 * j4 + 1] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 1]), cs.y, bb.y), 0.f);
-    x[4 * j4 + 2] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 2]), cs.z, bb.z), 0.f);
-    x[4 * j4 + 3] = fmaxf(fmaf(__uint_as_float(v[4 * j4 + 3]), cs.w, bb.w), 0.f);
+    x[4 * j4 + 0] = fmaf(__uint_as_float(v[4 * j4 + 0]), cs.x, bb.x);
+    x[4 * j4 + 1] = fmaf(__uint_as_float(v[4 * j4 + 1]), cs.y, bb.y);
+    x[4 * j4 + 2] = fmaf(__uint_as_float(v[4 * j4 + 2]), cs.z, bb.z);
+    x[4 * j4 + 3] = fmaf(__uint_as_float(v[4 * j4 + 3]), cs.w, bb.w);
   }
   uint8_t* row = stage + lane * 128;
   const int sw = lane & 7;
   if constexpr (OUT_FP8) {
-    const float os = p.out_scale;
     const int piece0 = 2 * (c & 3);  // 4 chunks of 32 bytes per 128-byte row
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 2; ++k) {  // the output scale is already in the vectors
       uint4 w;
-      w.x = epi_pack_e4m3x4(x[16 * k + 0] * os, x[16 * k + 1] * os, x[16 * k + 2] * os, x[16 * k + 3] * os);
-      w.y = epi_pack_e4m3x4(x[16 * k + 4] * os, x[16 * k + 5] * os, x[16 * k + 6] * os, x[16 * k + 7] * os);
-      w.z = epi_pack_e4m3x4(x[16 * k + 8] * os, x[16 * k + 9] * os, x[16 * k + 10] * os, x[16 * k + 11] * os);
-      w.w = epi_pack_e4m3x4(x[16 * k + 12] * os, x[16 * k + 13] * os, x[16 * k + 14] * os, x[16 * k + 15] * os);
+      w.x = epi_pack_e4m3x4_relu(x[16 * k + 0], x[16 * k + 1], x[16 * k + 2], x[16 * k + 3]);
+      w.y = epi_pack_e4m3x4_relu(x[16 * k + 4], x[16 * k + 5], x[16 * k + 6], x[16 * k + 7]);
+      w.z = epi_pack_e4m3x4_relu(x[16 * k + 8], x[16 * k + 9], x[16 * k + 10], x[16 * k + 11]);
+      w.w = epi_pack_e4m3x4_relu(x[16 * k + 12], x[16 * k + 13], x[16 * k + 14], x[16 * k + 15]);
       *reinterpret_cast<uint4*>(row + (((piece0 + k) ^ sw) << 4)) = w;
     }
   } else {
@@ -256,10 +278,10 @@ __device__ __forceinline__ void epi_chunk_stage(const TcGemmParams& p, const Epi
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       uint4 w;
-      w.x = epi_pack_bf16x2(x[8 * k + 0], x[8 * k + 1]);
-      w.y = epi_pack_bf16x2(x[8 * k + 2], x[8 * k + 3]);
-      w.z = epi_pack_bf16x2(x[8 * k + 4], x[8 * k + 5]);
-      w.w = epi_pack_bf16x2(x[8 * k + 6], x[8 * k + 7]);
+      w.x = epi_pack_bf16x2_relu(x[8 * k + 0], x[8 * k + 1]);
+      w.y = epi_pack_bf16x2_relu(x[8 * k + 2], x[8 * k + 3]);
+      w.z = epi_pack_bf16x2_relu(x[8 * k + 4], x[8 * k + 5]);
+      w.w = epi_pack_bf16x2_relu(x[8 * k + 6], x[8 * k + 7]);
       *reinterpret_cast<uint4*>(row + (((piece0 + k) ^ sw) << 4)) = w;
     }
   }
@@ -308,6 +330,49 @@ __device__ __forceinline__ void epi_row_staged(const TcGemmParams& p, const EpiV
       const int g0 = c + 2 - kGroup;  // first chunk of the staged group
       epi_flush_stage(p, stage, warp_row0, row_bytes,
                       static_cast<size_t>(n0 + 32 * g0) * kElem, lane);
+    }
+    if (next2) tmem_wait_ld_regs(va);
+  }
+}
+
+// Mode-0 drain by TMA stores (the fused layer 1, the staged pair tile): one
+// warp's chunks [c_begin, c_end) of its TMEM rows chunks [c_begin, c_end) of its TMEM rows
+// (bias + ReLU, bf16 or e4m3), packed group by group (128 bytes of each row)
+// into the warp's output boxes and written by TMA stores at
+// (column n0 + 32 c, row row0). `issued` counts the warp's stores so far.
+template <bool OUT_FP8, int DEPTH>
+__device__ __forceinline__ void epi_tile_tma(const TcGemmParams& p, const EpiVectors& ev,
+                                             const CUtensorMap* tmO, uint32_t tbase, int row0,
+                                             int n0, int c_begin, int c_end, uint8_t* boxes,
+                                             int lane, uint32_t& issued) {
+  constexpr int kGroup = OUT_FP8 ? 4 : 2;  // 32-column chunks per 128-byte row piece
+  uint32_t va[32], vb[32];
+  uint8_t* box = boxes;
+  tmem_ld32(tbase + 32u * c_begin, va);
+  tmem_wait_ld_regs(va);
+#pragma unroll 1
+  for (int c = c_begin; c < c_end; c += 2) {
+    if (((c - c_begin) % kGroup) == 0) {  // a new group: take the next box once it is free
+      box = boxes + (issued % DEPTH) * (32 * 128);
+      if (lane == 0) bulk_wait_group_read<DEPTH - 1>();
+      __syncwarp();
+    }
+    tmem_ld32(tbase + 32u * (c + 1), vb);
+    epi_chunk_stage<OUT_FP8>(p, ev, va, n0 + 32 * c, c, box, lane);
+    tmem_wait_ld_regs(vb);
+    const bool next2 = c + 2 < c_end;
+    if (next2) tmem_ld32(tbase + 32u * (c + 2), va);
+    epi_chunk_stage<OUT_FP8>(p, ev, vb, n0 + 32 * (c + 1), c + 1, box, lane);
+    if (((c + 2 - c_begin) % kGroup) == 0) {
+      const int g0 = c + 2 - kGroup;  // first chunk of the finished group
+      fence_proxy_async_smem();       // the TMA store reads the box through the async proxy
+      __syncwarp();
+      if (lane == 0) {
+        // element coordinates: 32 columns per chunk; e4m3 elements are bytes
+        tma_store_2d(tmO, smem_u32(box), n0 + 32 * g0, row0);
+        bulk_commit_group();
+      }
+      ++issued;
     }
     if (next2) tmem_wait_ld_regs(va);
   }

@@ -66,6 +66,10 @@ struct TcGemmParams {
   uint32_t* relu_bits;
   int ldb;
   float* col_part;
+  // pair kernel, staged query tile (mode 0): 1 = the outputs leave shared
+  // memory by TMA tensor stores through the output map the launcher takes
+  // (box 32 rows x 128 bytes), 0 = by 16-byte stores of the epilogue threads
+  int tma_out;
 };
 
 // ---- sphere tracing of an SDF field (trace.cu) ----
@@ -131,9 +135,12 @@ int tc_gemm_smem_bytes(int bn, bool in_fp8);
 // per row; modes 2 and 3 (bf16) as the 1-CTA kernel, mode 3 with K-major or
 // MN-major operands.
 constexpr int kTrainEpiWarps = 4;
+// tmO: the output map when p.tma_out is set (the staged mode-0 tile), else
+// nullptr.
 cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, bool staged, int epi_warps,
                                 const CUtensorMap& tmA, const CUtensorMap& tmB,
-                                const TcGemmParams& p, int clusters, cudaStream_t s);
+                                const TcGemmParams& p, int clusters, cudaStream_t s,
+                                const CUtensorMap* tmO = nullptr);
 // Clusters of the pair kernel that fit on the current device at once.
 int tc_gemm_pair_max_clusters(bool in_fp8);
 

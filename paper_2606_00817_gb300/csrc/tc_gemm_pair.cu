@@ -53,15 +53,25 @@ struct PairShape {
   static constexpr int B_BYTES = HALF * ROW_BYTES;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;  // per CTA
   static constexpr int STAGES = STAGED ? 5 : 6;
-  static constexpr int OUT_STAGE_BYTES = STAGED ? EPI * kStageBytesPerWarp : 0;
+  // staged outputs: per epilogue warp OUT_DEPTH boxes of 32 rows x 128 bytes
+  // (two with 4 warps, so a warp packs the next box while the TMA store of
+  // the last one still reads it; one with 8)
+  static constexpr int OUT_DEPTH = EPI == 4 ? 2 : 1;
+  static constexpr int OUT_STAGE_BYTES = STAGED ? EPI * OUT_DEPTH * kStageBytesPerWarp : 0;
   static constexpr int EPI_WARP0 = 2;  // first epilogue warp
   static constexpr int THREADS = 32 * (EPI_WARP0 + EPI);
   static constexpr int TMEM_COLS = 512;
   static constexpr int NUM_BARS = 2 * STAGES + 5;
   static constexpr int CTRL_BYTES = 256;  // barriers, TMEM slot, abort flag, issue counts
   static constexpr int VEC_OFFSET = STAGES * STAGE_BYTES + CTRL_BYTES;
-  // plus epi_vector_bytes(N) for the staged per-column vectors
-  static constexpr int SMEM_BYTES = VEC_OFFSET + 1024;
+  // then epi_vector_bytes(N) for the staged per-column vectors, then the
+  // output boxes on a 1024-byte boundary (the 128-byte swizzle atom)
+  __host__ __device__ static constexpr int out_off(int n) {
+    return (VEC_OFFSET + epi_vector_bytes(n) + 1023) & ~1023;
+  }
+  __host__ __device__ static constexpr int smem_bytes(int n) {
+    return out_off(n) + OUT_STAGE_BYTES + 1024;  // + 1024: base alignment
+  }
   static_assert(NUM_BARS * 8 + 16 <= CTRL_BYTES, "control block overflow");
 };
 
@@ -71,7 +81,8 @@ struct PairShape {
 template <bool IN_FP8, bool OUT_FP8, bool STAGED, bool TRAIN, int EPI = 4>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EPI), 1)
     tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
-                        const __grid_constant__ CUtensorMap tmB, const TcGemmParams p) {
+                        const __grid_constant__ CUtensorMap tmB,
+                        const __grid_constant__ CUtensorMap tmO, const TcGemmParams p) {
   using S = PairShape<IN_FP8, STAGED, EPI>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -250,9 +261,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EPI), 1)
     const int half = EPI == 4 ? 0 : (warp - S::EPI_WARP0) / 4;
     constexpr int kChunks = S::BN / 32 / (EPI / 4);  // 32-column chunks per warp
     const int c0 = half * kChunks, c1 = c0 + kChunks;
-    uint8_t* const stage_w = smem + S::VEC_OFFSET + epi_vector_bytes(p.N) + (warp - S::EPI_WARP0) * kStageBytesPerWarp;
+    uint8_t* const stage_w =
+        smem + S::out_off(p.N) + (warp - S::EPI_WARP0) * S::OUT_DEPTH * kStageBytesPerWarp;
     const int r_local = q * 32 + lane;
     const uint32_t tempty_leader0 = map_to_cta(tempty_bar(0), 0);
+    uint32_t stores = 0;  // TMA stores this warp issued
     int local = 0;
     for (int tile = pair; tile < num_tiles; tile += npairs, ++local) {
       const int b = local & 1;
@@ -279,6 +292,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EPI), 1)
           epi_row_masked_staged(p, tbase, row - lane, n0, c0, c1, stage_w, lane);
         else
           epi_row_train(p, tbase, row, row_ok, n0, c0, c1, split);
+      } else if (STAGED && p.mode == 0 && p.tma_out) {
+        epi_tile_tma<OUT_FP8, S::OUT_DEPTH>(p, ev, &tmO, tbase, row - lane, n0, c0, c1, stage_w,
+                                            lane, stores);
       } else if (STAGED && p.mode == 0) {
         epi_row_staged<OUT_FP8>(p, ev, tbase, row - lane, n0, c0, c1, stage_w, lane);
       } else {
@@ -291,6 +307,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EPI), 1)
         p.head_part[(static_cast<size_t>(n_blk) * (EPI / 4) + half) * p.M + row] =
             make_float2(h0, h1);
     }
+    // the boxes must stay untouched until every store has read them, and the
+    // outputs be written before the kernel ends
+    if (!TRAIN && STAGED && lane == 0) bulk_wait_group<0>();
+    __syncwarp();
   }
 
   // ---------------------------------------------------------- teardown
@@ -322,14 +342,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EPI), 1)
 }
 
 template <bool IN_FP8, bool OUT_FP8, bool STAGED, bool TRAIN = false, int EPI = 4>
-cudaError_t launch_pair_one(const CUtensorMap& tmA, const CUtensorMap& tmB,
+cudaError_t launch_pair_one(const CUtensorMap& tmA, const CUtensorMap& tmB, const CUtensorMap& tmO,
                             const TcGemmParams& p, int grid, cudaStream_t s) {
   using S = PairShape<IN_FP8, STAGED, EPI>;
   auto kern = tc_gemm_pair_kernel<IN_FP8, OUT_FP8, STAGED, TRAIN, EPI>;
-  const int smem = S::SMEM_BYTES + epi_vector_bytes(p.N) + S::OUT_STAGE_BYTES;
+  const int smem = S::smem_bytes(p.N);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, S::THREADS, smem, s>>>(tmA, tmB, p);
+  kern<<<grid, S::THREADS, smem, s>>>(tmA, tmB, tmO, p);
   return cudaGetLastError();
 }
 
@@ -337,7 +357,7 @@ template <bool IN_FP8, bool STAGED, int EPI>
 int max_pairs_for() {
   using S = PairShape<IN_FP8, STAGED, EPI>;
   auto kern = tc_gemm_pair_kernel<IN_FP8, false, STAGED, false, EPI>;
-  const int smem = S::SMEM_BYTES + epi_vector_bytes(kMaxStagedColumns) + S::OUT_STAGE_BYTES;
+  const int smem = S::smem_bytes(kMaxStagedColumns);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
     return 0;
   cudaLaunchConfig_t cfg = {};
@@ -354,19 +374,20 @@ int max_pairs_for() {
 
 template <bool IN_FP8, bool STAGED, int EPI>
 cudaError_t launch_pair_io(bool out_fp8, const CUtensorMap& tmA, const CUtensorMap& tmB,
-                           const TcGemmParams& p, int grid, cudaStream_t s) {
-  return out_fp8 ? launch_pair_one<IN_FP8, true, STAGED, false, EPI>(tmA, tmB, p, grid, s)
-                 : launch_pair_one<IN_FP8, false, STAGED, false, EPI>(tmA, tmB, p, grid, s);
+                           const CUtensorMap& tmO, const TcGemmParams& p, int grid,
+                           cudaStream_t s) {
+  return out_fp8 ? launch_pair_one<IN_FP8, true, STAGED, false, EPI>(tmA, tmB, tmO, p, grid, s)
+                 : launch_pair_one<IN_FP8, false, STAGED, false, EPI>(tmA, tmB, tmO, p, grid, s);
 }
 
 template <int EPI>
 cudaError_t launch_pair_epi(bool in_fp8, bool out_fp8, bool staged, const CUtensorMap& tmA,
-                            const CUtensorMap& tmB, const TcGemmParams& p, int grid,
-                            cudaStream_t s) {
-  if (in_fp8) return staged ? launch_pair_io<true, true, EPI>(out_fp8, tmA, tmB, p, grid, s)
-                            : launch_pair_io<true, false, EPI>(out_fp8, tmA, tmB, p, grid, s);
-  return staged ? launch_pair_io<false, true, EPI>(out_fp8, tmA, tmB, p, grid, s)
-                : launch_pair_io<false, false, EPI>(out_fp8, tmA, tmB, p, grid, s);
+                            const CUtensorMap& tmB, const CUtensorMap& tmO,
+                            const TcGemmParams& p, int grid, cudaStream_t s) {
+  if (in_fp8) return staged ? launch_pair_io<true, true, EPI>(out_fp8, tmA, tmB, tmO, p, grid, s)
+                            : launch_pair_io<true, false, EPI>(out_fp8, tmA, tmB, tmO, p, grid, s);
+  return staged ? launch_pair_io<false, true, EPI>(out_fp8, tmA, tmB, tmO, p, grid, s)
+                : launch_pair_io<false, false, EPI>(out_fp8, tmA, tmB, tmO, p, grid, s);
 }
 
 }  // namespace
@@ -383,7 +404,12 @@ int tc_gemm_pair_max_clusters(bool in_fp8) {
 
 cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, bool staged, int epi_warps,
                                 const CUtensorMap& tmA, const CUtensorMap& tmB,
-                                const TcGemmParams& p, int clusters, cudaStream_t s) {
+                                const TcGemmParams& p, int clusters, cudaStream_t s,
+                                const CUtensorMap* tmO) {
+  if (p.tma_out && (tmO == nullptr || !staged || p.mode != 0 || p.relu_bits != nullptr ||
+                    p.amax != nullptr))
+    return cudaErrorInvalidValue;  // TMA stores: the staged query tile, with its output map
+  const CUtensorMap& to = tmO != nullptr ? *tmO : tmA;  // not read unless p.tma_out
   if (p.mode == 3 && (p.k_splits > 1 ? p.k_splits : 1) > (p.K + 63) / 64)
     return cudaErrorInvalidValue;  // every split needs a k-block
   if (p.mn_major && (in_fp8 || p.mode != 3)) return cudaErrorInvalidValue;
@@ -396,10 +422,10 @@ cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, bool staged, int epi_
   const int grid = 2 * clusters;
   // training modes, and the training forward that writes ReLU patterns
   if (p.mode >= 2 || p.relu_bits != nullptr)
-    return launch_pair_one<false, false, true, true, kTrainEpiWarps>(tmA, tmB, p, grid, s);
-  if (epi_warps == 8) return launch_pair_epi<8>(in_fp8, out_fp8, staged, tmA, tmB, p, grid, s);
+    return launch_pair_one<false, false, true, true, kTrainEpiWarps>(tmA, tmB, to, p, grid, s);
+  if (epi_warps == 8) return launch_pair_epi<8>(in_fp8, out_fp8, staged, tmA, tmB, to, p, grid, s);
   if (epi_warps != 4) return cudaErrorInvalidValue;
-  return launch_pair_epi<4>(in_fp8, out_fp8, staged, tmA, tmB, p, grid, s);
+  return launch_pair_epi<4>(in_fp8, out_fp8, staged, tmA, tmB, to, p, grid, s);
 }
 
 }  // namespace ddf

@@ -77,48 +77,6 @@ __device__ __forceinline__ uint32_t next_pair(const float (&e)[6], int L, int& c
   return epi_pack_bf16x2(sn, cs);
 }
 
-// Epilogue of one tile for one warp: chunks [c_begin, c_end) of its TMEM rows
-// (bias + ReLU, bf16 or e4m3), packed group by group (128 bytes of each row)
-// into the warp's output boxes and written by TMA stores at
-// (column n0 + 32 c, row row0). `issued` counts the warp's stores so far.
-template <bool OUT_FP8, int DEPTH>
-__device__ __forceinline__ void epi_tile_tma(const TcGemmParams& p, const EpiVectors& ev,
-                                             const CUtensorMap* tmO, uint32_t tbase, int row0,
-                                             int n0, int c_begin, int c_end, uint8_t* boxes,
-                                             int lane, uint32_t& issued) {
-  constexpr int kGroup = OUT_FP8 ? 4 : 2;  // 32-column chunks per 128-byte row piece
-  uint32_t va[32], vb[32];
-  uint8_t* box = boxes;
-  tmem_ld32(tbase + 32u * c_begin, va);
-  tmem_wait_ld_regs(va);
-#pragma unroll 1
-  for (int c = c_begin; c < c_end; c += 2) {
-    if (((c - c_begin) % kGroup) == 0) {  // a new group: take the next box once it is free
-      box = boxes + (issued % DEPTH) * (32 * 128);
-      if (lane == 0) bulk_wait_group_read<DEPTH - 1>();
-      __syncwarp();
-    }
-    tmem_ld32(tbase + 32u * (c + 1), vb);
-    epi_chunk_stage<OUT_FP8>(p, ev, va, n0 + 32 * c, c, box, lane);
-    tmem_wait_ld_regs(vb);
-    const bool next2 = c + 2 < c_end;
-    if (next2) tmem_ld32(tbase + 32u * (c + 2), va);
-    epi_chunk_stage<OUT_FP8>(p, ev, vb, n0 + 32 * (c + 1), c + 1, box, lane);
-    if (((c + 2 - c_begin) % kGroup) == 0) {
-      const int g0 = c + 2 - kGroup;  // first chunk of the finished group
-      fence_proxy_async_smem();       // the TMA store reads the box through the async proxy
-      __syncwarp();
-      if (lane == 0) {
-        // element coordinates: 32 columns per chunk; e4m3 elements are bytes
-        tma_store_2d(tmO, smem_u32(box), n0 + 32 * g0, row0);
-        bulk_commit_group();
-      }
-      ++issued;
-    }
-    if (next2) tmem_wait_ld_regs(va);
-  }
-}
-
 template <bool OUT_FP8, int EPI>
 __global__ void __launch_bounds__(64 + 32 * EPI + 128, 1)
     tc_layer1_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmO,
@@ -170,10 +128,11 @@ __global__ void __launch_bounds__(64 + 32 * EPI + 128, 1)
     tmem_alloc(smem_u32(tmem_slot), S::TMEM_COLS);
     tmem_relinquish();
   }
-  // layer 1 has no column scale and no head: only the bias is staged
+  // layer 1 has no column scale and no head: only the bias is staged, with an
+  // e4m3 output's scale (a power of two) folded in as stage_epi_vectors does
   float* sbias = reinterpret_cast<float*>(smem + S::VEC_OFF);
-  for (int i = threadIdx.x; i < p.N; i += blockDim.x) sbias[i] = p.bias[i];
-  const EpiVectors ev{sbias, nullptr, nullptr, nullptr};
+  for (int i = threadIdx.x; i < p.N; i += blockDim.x) sbias[i] = p.bias[i] * p.out_scale;
+  const EpiVectors ev{sbias, nullptr, nullptr, nullptr, p.out_scale};
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
