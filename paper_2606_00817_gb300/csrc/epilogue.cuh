@@ -398,10 +398,12 @@ __device__ __forceinline__ uint32_t epi_chunk_stage_bits(const EpiVectors& ev, c
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int j = 8 * k + 2 * q;
-      ow[q] = epi_pack_bf16x2(fmaxf(__uint_as_float(v[j]) + bias[j], 0.f),
-                              fmaxf(__uint_as_float(v[j + 1]) + bias[j + 1], 0.f));
-      m |= ((ow[q] & 0xFFFFu) != 0u ? 1u : 0u) << j;
-      m |= ((ow[q] >> 16) != 0u ? 1u : 0u) << (j + 1);
+      ow[q] = epi_pack_bf16x2_relu(__uint_as_float(v[j]) + bias[j],
+                                   __uint_as_float(v[j + 1]) + bias[j + 1]);
+      // positive after rounding: a nonzero magnitude (a zero of either sign
+      // passes no gradient)
+      m |= ((ow[q] & 0x7FFFu) != 0u ? 1u : 0u) << j;
+      m |= ((ow[q] & 0x7FFF0000u) != 0u ? 1u : 0u) << (j + 1);
       if (ev.hw0 != nullptr) {
         const int col = col0 + j;
         const float x0 = __uint_as_float(ow[q] << 16), x1 = __uint_as_float(ow[q] & 0xFFFF0000u);
