@@ -228,6 +228,6 @@ ddf_status hg_train(ddf_s* h, ddf::RaySoA rays, const float* t_target, const uin
                     int B, float lr, float* out_loss, cudaStream_t st);
 ddf_status hg_ensure_train(ddf_s* h, int64_t B);
 // Rewrites a bf16 field's query copies from the FP32 master blob (on st).
-ddf_status hg_refresh(ddf_s* h, cudaStream_t st);
+ddf_status hg_refresh(ddf_s* h, cudaStream_t st, bool tables_too = true);
 
 }  // namespace ddfi

@@ -555,20 +555,24 @@ __global__ void __launch_bounds__(kHgTrainThreads)
   }
 }
 
-// Weight-gradient partials dW = P^T A of one MLP layer of the hash-grid
-// field (P = dL/dpre, A = the layer input; element (r, c) of P at
-// P[r prs + c pcs], of A at A[r ars + c acs]): one 256-thread block per
-// split of the rays computes the whole [np x na]
-// partial (np, na <= 64) from 32-ray slices staged in shared memory, thread
-// (tn, tk) owning rows 4 tn .. 4 tn + 3 and columns 4 tk .. 4 tk + 3, and
-// bpart[s][n] = sum of P[r][n] over the split (the bias gradient's partial).
-// Every sum runs over the split's rays in order.
+// Weight-gradient partials dW = P^T A of the MLP layers of the hash-grid
+// field, every layer in one launch (blockIdx.y = the layer's job; P =
+// dL/dpre, A = the layer input; element (r, c) of P at P[r prs + c pcs], of
+// A at A[r ars + c acs]): one 256-thread block per split of the rays and
+// layer computes the whole [np x na] partial (np, na <= 64) from 32-ray
+// slices staged in shared memory, thread (tn, tk) owning rows 4 tn .. 4 tn +
+// 3 and columns 4 tk .. 4 tk + 3, and bpart[s][n] = sum of P[r][n] over the
+// split (the bias gradient's partial). Every sum runs over the split's rays
+// in order.
 __global__ void __launch_bounds__(256)
-hg_outer_tiled_kernel(const float* __restrict__ P, int64_t prs, int64_t pcs, int np,
-                      const float* __restrict__ A, int64_t ars, int64_t acs, int na, int64_t B,
-                      int64_t per_split, float* __restrict__ part, float* __restrict__ bpart) {
+hg_outer_tiled_kernel(const HgOuterJobs jobs, int64_t B, int64_t per_split) {
   __shared__ float sP[32][65];
   __shared__ float sA[32][65];
+  const HgOuterJob& jb = jobs.job[blockIdx.y];
+  const float* __restrict__ P = jb.P;
+  const float* __restrict__ A = jb.A;
+  const int64_t prs = jb.prs, pcs = jb.pcs, ars = jb.ars, acs = jb.acs;
+  const int np = jb.np, na = jb.na;
   const int tid = threadIdx.x;
   const int tn = tid >> 4, tk = tid & 15;
   const int64_t r0 = blockIdx.x * per_split;
@@ -601,7 +605,7 @@ hg_outer_tiled_kernel(const float* __restrict__ P, int64_t prs, int64_t pcs, int
     }
     __syncthreads();
   }
-  float* ps = part + static_cast<int64_t>(blockIdx.x) * np * na;
+  float* ps = jb.part + static_cast<int64_t>(blockIdx.x) * np * na;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int n = 4 * tn + i;
@@ -611,7 +615,7 @@ hg_outer_tiled_kernel(const float* __restrict__ P, int64_t prs, int64_t pcs, int
       const int k = 4 * tk + j;
       if (k < na) ps[n * na + k] = acc[i][j];
     }
-    if (tk == 0) bpart[static_cast<int64_t>(blockIdx.x) * np + n] = bs[i];
+    if (tk == 0) jb.bpart[static_cast<int64_t>(blockIdx.x) * np + n] = bs[i];
   }
 }
 
@@ -766,13 +770,13 @@ cudaError_t launch_hg_pack_table(const float* src, int64_t n_entries, const Hash
   return cudaGetLastError();
 }
 
-cudaError_t launch_hg_outer_tiled(const float* P, int64_t prs, int64_t pcs, int np, const float* A,
-                                  int64_t ars, int64_t acs, int na, int64_t B, int splits,
-                                  float* part, float* bpart, cudaStream_t s) {
-  if (np < 1 || np > 64 || na < 1 || na > 64 || splits < 1) return cudaErrorInvalidValue;
+cudaError_t launch_hg_outer_tiled(const HgOuterJobs& jobs, int64_t B, int splits, cudaStream_t s) {
+  if (jobs.n < 1 || jobs.n > kHgOuterJobs || splits < 1) return cudaErrorInvalidValue;
+  for (int j = 0; j < jobs.n; ++j)
+    if (jobs.job[j].np < 1 || jobs.job[j].np > 64 || jobs.job[j].na < 1 || jobs.job[j].na > 64)
+      return cudaErrorInvalidValue;
   const int64_t per = (B + splits - 1) / splits;
-  hg_outer_tiled_kernel<<<splits, 256, 0, s>>>(P, prs, pcs, np, A, ars, acs, na, B, per, part,
-                                               bpart);
+  hg_outer_tiled_kernel<<<dim3(splits, jobs.n), 256, 0, s>>>(jobs, B, per);
   return cudaGetLastError();
 }
 

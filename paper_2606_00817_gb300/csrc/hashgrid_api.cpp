@@ -57,13 +57,16 @@ size_t hg_param_count(const ddf_config& c) {
 }
 
 // Writes the query copies of a bf16 field (padded bf16 table, swizzled MLP
-// operand images, FP32 biases and head) from the FP32 master blob, on st.
-ddf_status hg_refresh(ddf_s* h, cudaStream_t st) {
+// operand images, FP32 biases and head) from the FP32 master blob, on st;
+// with tables = false only those of the MLP (the training step's Adam pass
+// writes the table's copy itself).
+ddf_status hg_refresh(ddf_s* h, cudaStream_t st, bool tables_too) {
   const int H = h->cfg.hidden_layers;
   const float* tables = h->d_blob;
   uint32_t* tab = static_cast<uint32_t*>(h->hg_table);
   // every level into the padded layout, one launch
-  DDF_CK(ddf::launch_hg_pack_table(tables, h->hg_blob_entries, h->hg_blob, h->hg, tab, st));
+  if (tables_too)
+    DDF_CK(ddf::launch_hg_pack_table(tables, h->hg_blob_entries, h->hg_blob, h->hg, tab, st));
   // MLP part: W_1 [64 x 59], b_1, (W_l [64 x 64], b_l) ..., W_o [2 x 64], b_o
   const float* m = tables + 2 * h->hg_blob_entries;
   int K = kCode;
@@ -266,21 +269,22 @@ ddf_status hg_backward(ddf_s* h, ddf::RaySoA rays, int B, cudaStream_t st) {
     a.out = out;
     sums.push_back(a);
   };
+  ddf::HgOuterJobs jobs{};
   for (int l = 0; l < H; ++l) {
     const float* P = h->hg_dpre + l * act;
     const float* A = l == 0 ? h->hg_code : h->hg_acts + (l - 1) * act;
     const int K = l == 0 ? kCode : kW;
     float* part = h->tr_part + l * pslice;
     float* cpart = h->tr_cpart + l * cslice;
-    DDF_CK(ddf::launch_hg_outer_tiled(P, 1, B, kW, A, 1, B, K, B, kGradSplits, part, cpart, st));
+    jobs.job[jobs.n++] = ddf::HgOuterJob{P, 1, B, kW, A, 1, B, K, part, cpart};
     add_sum(part, kW, K, gmlp + o.w[l]);
     add_sum(cpart, 1, kW, gmlp + o.b[l]);
   }
   const float* dz = reinterpret_cast<const float*>(h->tr_dz);
   float* part = h->tr_part + H * pslice;
   float* cpart = h->tr_cpart + H * cslice;
-  DDF_CK(ddf::launch_hg_outer_tiled(dz, 2, 1, 2, h->hg_acts + (H - 1) * act, 1, B, kW, B,
-                                    kGradSplits, part, cpart, st));
+  jobs.job[jobs.n++] = ddf::HgOuterJob{dz, 2, 1, 2, h->hg_acts + (H - 1) * act, 1, B, kW, part, cpart};
+  DDF_CK(ddf::launch_hg_outer_tiled(jobs, B, kGradSplits, st));  // every layer, one launch
   add_sum(part, 2, kW, gmlp + o.wo);
   add_sum(cpart, 1, 2, gmlp + o.bo);
   for (size_t j0 = 0; j0 < sums.size(); j0 += ddf::kRedJobs) {
@@ -306,10 +310,20 @@ ddf_status hg_train(ddf_s* h, ddf::RaySoA rays, const float* t_target, const uin
     const double t = static_cast<double>(h->adam_step);
     const float bc1 = static_cast<float>(1.0 - std::pow(0.9, t));
     const float bc2 = static_cast<float>(1.0 - std::pow(0.999, t));
-    DDF_CK(ddf::launch_adam(h->d_blob, h->grad, h->adam_m, h->adam_v,
-                            static_cast<int64_t>(hg_param_count(h->cfg)), lr, kAdamB1, kAdamB2,
-                            kAdamEps, bc1, bc2, st));
-    if (h->cfg.precision != DDF_FP32 && (s = hg_refresh(h, st)) != DDF_OK) return s;
+    const int64_t n = static_cast<int64_t>(hg_param_count(h->cfg));
+    if (h->cfg.precision == DDF_FP32) {
+      DDF_CK(ddf::launch_adam(h->d_blob, h->grad, h->adam_m, h->adam_v, n, lr, kAdamB1, kAdamB2,
+                              kAdamEps, bc1, bc2, st));
+    } else {
+      // the tables' Adam and their bf16 copy in one pass, then the MLP's
+      const int64_t t = 2 * h->hg_blob_entries;
+      DDF_CK(ddf::launch_hg_adam_pack(h->d_blob, h->grad, h->adam_m, h->adam_v, h->hg_blob_entries,
+                                      lr, kAdamB1, kAdamB2, kAdamEps, bc1, bc2, h->hg_blob, h->hg,
+                                      static_cast<uint32_t*>(h->hg_table), st));
+      DDF_CK(ddf::launch_adam(h->d_blob + t, h->grad + t, h->adam_m + t, h->adam_v + t, n - t, lr,
+                              kAdamB1, kAdamB2, kAdamEps, bc1, bc2, st));
+      if ((s = hg_refresh(h, st, false)) != DDF_OK) return s;
+    }
   }
   return DDF_OK;
 }

@@ -213,9 +213,23 @@ cudaError_t launch_hg_train_fwd(const HashGridParams& g, const float2* table, co
 cudaError_t launch_hg_train_bwd(const HashGridParams& g, const float* mlp, int H, RaySoA rays,
                                 int64_t B, const float* acts, const float2* dz, float* dpre,
                                 float* grad_table, cudaStream_t s);
-cudaError_t launch_hg_outer_tiled(const float* P, int64_t prs, int64_t pcs, int np, const float* A,
-                                  int64_t ars, int64_t acs, int na, int64_t B, int splits,
-                                  float* part, float* bpart, cudaStream_t s);
+struct HgOuterJob {
+  const float* P;
+  int64_t prs, pcs;
+  int np;
+  const float* A;
+  int64_t ars, acs;
+  int na;
+  float* part;
+  float* bpart;
+};
+constexpr int kHgOuterJobs = 5;  // up to 4 hidden layers and the head
+struct HgOuterJobs {
+  HgOuterJob job[kHgOuterJobs];
+  int n;
+};
+// Every job of `jobs` in one launch (splits blocks per job).
+cudaError_t launch_hg_outer_tiled(const HgOuterJobs& jobs, int64_t B, int splits, cudaStream_t s);
 cudaError_t launch_hg_pack_image(const float* w, int K, uint8_t* img, cudaStream_t s);
 
 // Ambient occlusion (Sec. 3.3): for point p with rays [offsets[p], offsets[p+1])
@@ -286,6 +300,13 @@ cudaError_t launch_grad_reduce(const GradReduce& g, cudaStream_t s);
 // weight decay) on n parameters: m, v and w updated in place.
 cudaError_t launch_adam(float* w, const float* g, float* m, float* v, int64_t n, float lr,
                         float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s);
+// Adam over the first `entries` feature pairs of a hash-grid blob (its level
+// tables, layout `from`) and their bf16x2 copy in the padded layout `to`
+// (dst), in one pass; the same arithmetic as launch_adam.
+cudaError_t launch_hg_adam_pack(float* w, const float* g, float* m, float* v, int64_t entries,
+                                float lr, float b1, float b2, float eps, float bc1, float bc2,
+                                const HashGridParams& from, const HashGridParams& to,
+                                uint32_t* dst, cudaStream_t s);
 // z[r] = (sum over p < nparts of part[p][r]) + bo, for the two head rows.
 cudaError_t launch_head_sum(const float2* part, int nparts, int64_t M, const float* bo, float2* z,
                             cudaStream_t s);

@@ -354,6 +354,59 @@ __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, 
   }
 }
 
+// Adam over the level tables of a hash-grid field (entry i of the blob is
+// the feature pair 2 i, 2 i + 1) and, in the same pass, their bf16x2 query
+// copy: source entry i of level l goes to word i - from.offset[l] +
+// to.offset[l] (f0 in the low half). The arithmetic of adam_kernel, element
+// by element; two entries (one float4 of each array) per thread when vec.
+__global__ void hg_adam_pack_kernel(float* __restrict__ w, const float* __restrict__ g,
+                                    float* __restrict__ m, float* __restrict__ v, int64_t entries,
+                                    float lr, float b1, float b2, float eps, float bc1, float bc2,
+                                    HashGridParams from, HashGridParams to,
+                                    uint32_t* __restrict__ dst, int vec) {
+  const int64_t e0 = 2 * (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
+  if (e0 >= entries) return;
+  auto word = [&](int64_t e) {
+    int l = 0;
+#pragma unroll
+    for (int k = 1; k < 16; ++k) l += e >= from.offset[k] ? 1 : 0;
+    return e - from.offset[l] + to.offset[l];
+  };
+  auto pack = [](float lo, float hi) {
+    __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&b);
+  };
+  const int64_t i4 = 2 * e0;
+  if (vec && e0 + 2 <= entries) {
+    float4 W = *reinterpret_cast<const float4*>(w + i4);
+    const float4 G = *reinterpret_cast<const float4*>(g + i4);
+    float4 M = *reinterpret_cast<const float4*>(m + i4);
+    float4 V = *reinterpret_cast<const float4*>(v + i4);
+    W.x = adam_elem(W.x, G.x, M.x, V.x, lr, b1, b2, eps, bc1, bc2);
+    W.y = adam_elem(W.y, G.y, M.y, V.y, lr, b1, b2, eps, bc1, bc2);
+    W.z = adam_elem(W.z, G.z, M.z, V.z, lr, b1, b2, eps, bc1, bc2);
+    W.w = adam_elem(W.w, G.w, M.w, V.w, lr, b1, b2, eps, bc1, bc2);
+    *reinterpret_cast<float4*>(m + i4) = M;
+    *reinterpret_cast<float4*>(v + i4) = V;
+    *reinterpret_cast<float4*>(w + i4) = W;
+    dst[word(e0)] = pack(W.x, W.y);
+    dst[word(e0 + 1)] = pack(W.z, W.w);
+    return;
+  }
+  for (int64_t e = e0; e < e0 + 2 && e < entries; ++e) {
+    float nw[2];
+    for (int f = 0; f < 2; ++f) {
+      const int64_t i = 2 * e + f;
+      float mi = m[i], vi = v[i];
+      nw[f] = adam_elem(w[i], g[i], mi, vi, lr, b1, b2, eps, bc1, bc2);
+      w[i] = nw[f];
+      m[i] = mi;
+      v[i] = vi;
+    }
+    dst[word(e)] = pack(nw[0], nw[1]);
+  }
+}
+
 // Adam plus the refresh of the weights' copies (see launch_adam_refresh),
 // the same arithmetic as adam_kernel element by element. A CTA takes either
 // 2,048 consecutive elements of a block without a transposed copy, or a
@@ -581,6 +634,19 @@ cudaError_t launch_adam(float* w, const float* g, float* m, float* v, int64_t n,
   const int64_t threads = (n + 3) / 4;
   adam_kernel<<<static_cast<unsigned>((threads + 255) / 256), 256, 0, s>>>(
       w, g, m, v, n, lr, b1, b2, eps, bc1, bc2, (a & 15u) == 0 ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hg_adam_pack(float* w, const float* g, float* m, float* v, int64_t entries,
+                                float lr, float b1, float b2, float eps, float bc1, float bc2,
+                                const HashGridParams& from, const HashGridParams& to,
+                                uint32_t* dst, cudaStream_t s) {
+  if (entries <= 0) return cudaSuccess;
+  const uintptr_t a = reinterpret_cast<uintptr_t>(w) | reinterpret_cast<uintptr_t>(g) |
+                      reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v);
+  const int64_t threads = (entries + 1) / 2;
+  hg_adam_pack_kernel<<<static_cast<unsigned>((threads + 255) / 256), 256, 0, s>>>(
+      w, g, m, v, entries, lr, b1, b2, eps, bc1, bc2, from, to, dst, (a & 15u) == 0 ? 1 : 0);
   return cudaGetLastError();
 }
 
