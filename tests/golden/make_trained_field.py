@@ -8,9 +8,12 @@ half surface-anchored rays, Sec. 3.2), takes exact targets from the oracle's
 closed-form caster, moves the last 30 % by the ray-march shift, and takes one
 exact-gradient Adam step (Sec. 3.2 / 3.4 loss; Adam 1e-3 with the cosine
 decay to 5 %). The weights stay float64 during training and are rounded to
-float32 once at the end.
+float32 once at the end. The file also holds the exact outputs of the
+field on seeded uniform rays and its e4m3 scales (the "evaluation" block),
+so that the benchmark can report flip rates on trained weights without
+running the oracle.
 
-    python tests/golden/make_trained_field.py [--steps N]
+    python tests/golden/make_trained_field.py [--steps N] [--eval-only]
 """
 import argparse
 import base64
@@ -71,10 +74,40 @@ def train(steps):
     return blob, stats
 
 
+EVAL_RAYS = 16384
+EVAL_SEED = 77
+
+
+def evaluation(blob):
+    """Exact outputs of the field on EVAL_RAYS seeded uniform rays (origins
+    in [-1, 1]^3, directions uniform on the sphere; the generator of the
+    package's inputs module) and the e4m3 activation scales calibrated on
+    4,096 of them, for a benchmark that must not run the oracle itself."""
+    rays = I.uniform_rays(EVAL_RAYS, seed=EVAL_SEED)
+    out = O.ddf_forward(rays.origins(), rays.dirs(), blob, *NET)
+    cal = I.uniform_rays(4096, seed=EVAL_SEED + 1)
+    scales = O.calibrate_act_scales(cal.origins(), cal.dirs(), blob, *NET)
+    enc = lambda a: base64.b64encode(np.asarray(a, "<f4").tobytes()).decode()
+    return {"rays": f"inputs.uniform_rays({EVAL_RAYS}, seed={EVAL_SEED})",
+            "t_exact_f32_le_base64": enc(out["t"]), "z1_exact_f32_le_base64": enc(out["z"][:, 1]),
+            "fp8_act_scales": [float(x) for x in scales],
+            "fp8_scales_from": f"calibrate_act_scales on inputs.uniform_rays(4096, seed={EVAL_SEED + 1})"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--steps", type=int, default=1500)
+    ap.add_argument("--eval-only", action="store_true",
+                    help="keep the stored weights and only (re)write the evaluation block")
     a = ap.parse_args()
+    if a.eval_only:
+        with open(OUT) as f:
+            doc = json.load(f)
+        blob = np.frombuffer(base64.b64decode(doc["blob_f32_le_base64"]), dtype="<f4").astype(np.float32)
+        doc["evaluation"] = evaluation(blob)
+        with open(OUT, "w") as f:
+            json.dump(doc, f, indent=1)
+        return
     blob, stats = train(a.steps)
     doc = {
         "source": "Written by tests/golden/make_trained_field.py, which calls only the FP64 oracle "
@@ -86,6 +119,7 @@ def main():
         "octaves": NET[0], "width": NET[1], "hidden": NET[2], "steps": a.steps, "batch": BATCH,
         "lr0": LR0, "seed": SEED, "scene": "random_scene(32, 32, seed=0)",
         "stats": stats,
+        "evaluation": evaluation(blob),
         "blob_f32_le_base64": base64.b64encode(blob.astype("<f4").tobytes()).decode(),
     }
     with open(OUT, "w") as f:

@@ -269,6 +269,21 @@ def test_mixed_query_equals_the_separate_queries(torch_cuda, net, prec, kind, ns
     got = _mixed(torch, ddf, m, sdev, ns, light, adev, na, d_off, P, outs)
     assert all(torch.equal(a, b) for a, b in zip(got, refs[0]))
     assert got[3][0] == 1.0 and got[3][99] == 1.0
+    if kind == "ray" and net == SMALL:
+        # and directly against the oracle's shadow decision and AO
+        sr, ar = data[0]
+        emu_prec = "exact" if prec == "fp32" else prec
+        h_ref, s_ref, tie = _ao_reference(ar, offsets, blob, net, emu_prec, sc)
+        assert np.all(np.abs(got[3].double().cpu().numpy() - h_ref) <= tie + 1e-6)
+        assert np.abs(got[4].double().cpu().numpy() - s_ref).max() <= 2e-3
+        if ns:
+            emu = O.ddf_forward(sr.origins(), sr.dirs(), blob, *net, precision=emu_prec)
+            occ_ref = O.shadow(emu["t"], emu["z"][:, 1], sr.origins(), light)
+            dist = np.linalg.norm(np.array(light) - sr.origins().astype(np.float64), axis=1)
+            clear = (np.abs(emu["z"][:, 1]) > 1e-2) & (np.abs(emu["t"] - dist) > 1e-2)
+            assert clear.mean() > 0.8
+            occ = got[2].cpu().numpy().astype(bool)
+            assert np.array_equal(occ[clear], occ_ref[clear])
     ddf.ddf_set_graph_mode(m.h, True)
     for k in (0, 1, 2, 1):
         load(k)

@@ -48,3 +48,21 @@ def test_trained_field_is_trained():
     assert np.mean(np.abs(z1) < 0.1) < 0.05
     dt = np.abs(np.minimum(out["t"], 4) - np.minimum(t_ref, 4))[hit]
     assert np.median(dt) < 0.1
+
+
+def test_stored_evaluation_is_the_oracles():
+    """The evaluation block the benchmark reads (exact outputs on seeded
+    uniform rays, e4m3 scales) is what the oracle computes for the stored
+    weights, to float32 rounding."""
+    with open(GOLD) as f:
+        ev = json.load(f)["evaluation"]
+    net, blob = trained_field()
+    dec = lambda k: np.frombuffer(base64.b64decode(ev[k]), dtype="<f4").astype(np.float64)
+    t, z1 = dec("t_exact_f32_le_base64"), dec("z1_exact_f32_le_base64")
+    rays = I.uniform_rays(t.size, seed=77)
+    out = O.ddf_forward(rays.origins(), rays.dirs(), blob, *net)
+    assert np.allclose(t, out["t"], rtol=2 ** -23, atol=1e-30)
+    assert np.allclose(z1, out["z"][:, 1], rtol=2 ** -23, atol=1e-30)
+    cal = I.uniform_rays(4096, seed=78)
+    assert ev["fp8_act_scales"] == O.calibrate_act_scales(cal.origins(), cal.dirs(), blob, *net)
+    assert np.mean(np.abs(z1) < 0.1) < 0.05                 # a trained field: few near-ties
