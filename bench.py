@@ -574,6 +574,48 @@ def gs_workload(torch, ddf, dev, local, stream, V=1024, W=128, steps=30000, n_ga
     return res
 
 
+TRAINED_FIELD = os.path.join(ROOT, "tests", "golden", "trained_small_field.json")
+
+
+def trained_field_accuracy(torch, ddf, dev, local, stream):
+    """Flip rate and |dt| of the bf16 and e4m3 paths on weights that the FP64
+    oracle distilled by itself (78 -> 128 x 4 -> 2, stored with the oracle's
+    exact outputs on seeded uniform rays and its e4m3 scales), against those
+    stored outputs; the frozen bounds beside them."""
+    import base64
+    with open(TRAINED_FIELD) as fh:
+        doc = json.load(fh)
+    net = (doc["octaves"], doc["width"], doc["hidden"])
+    blob = np.frombuffer(base64.b64decode(doc["blob_f32_le_base64"]), dtype="<f4").astype(np.float32)
+    ev = doc["evaluation"]
+    dec = lambda k: np.frombuffer(base64.b64decode(ev[k]), dtype="<f4").astype(np.float64)
+    t_ex, z1_ex = dec("t_exact_f32_le_base64"), dec("z1_exact_f32_le_base64")
+    rays = I.uniform_rays(t_ex.size, seed=77)
+    d_rays = [torch.from_numpy(a).to(dev) for a in rays.soa()]
+    out = {"net": list(net), "rays": ev["rays"], "distilled_steps": doc["steps"],
+           "reference": "exact FP64 outputs stored by the oracle-only training script"}
+    bounds = {"bf16": (5e-3, 5e-2, 5e-3), "fp8": (2e-2, 0.2, 2e-2)}
+    for prec in ("bf16", "fp8"):
+        m = ddf.DDF(*net, precision=prec, device=local)
+        m.load(blob)
+        if prec == "fp8":
+            ddf.ddf_set_act_scales(m.h, ev["fp8_act_scales"])
+        t, v = m.query(d_rays, stream)
+        torch.cuda.synchronize()
+        t = t.double().cpu().numpy()
+        v = v.double().cpu().numpy()
+        dt = np.abs(t - t_ex)
+        b = bounds[prec]
+        out[prec] = {"mean_abs_dt": float(dt.mean()), "max_abs_dt": float(dt.max()),
+                     "frac_abs_dt_above_max_bound": float(np.mean(dt > b[1])),
+                     "flip_rate": float(np.mean((v > 0.5) != (z1_ex > 0))),
+                     "near_tie_frac": float(np.mean(np.abs(z1_ex) < 1e-3)),
+                     "bounds": {"mean_abs_dt": b[0], "max_abs_dt": b[1], "flip_rate": b[2]},
+                     "status": ddf.ddf_check_status(m.h)}
+        m.close()
+    return out
+
+
 def workloads(torch, ddf, dev, local, stream, flush, blob, which):
     """The ragged AO, distillation and sphere-tracing measurements (those
     named in `which`)."""
@@ -1041,6 +1083,7 @@ def main():
                "near_tie_frac": float(np.mean(np.abs(z1) < 1e-3)),
                "bounds": {"mean_abs_dt": 5e-3, "max_abs_dt": 5e-2, "flip_rate": 5e-3},
                "reference": "FP64 oracle, exact arithmetic"}
+        acc["trained_field"] = trained_field_accuracy(torch, ddf, dev, local, stream)
         if fp8_out is not None:
             t8n = fp8_out[0][sel].double().cpu().numpy()
             v8n = fp8_out[1][sel].double().cpu().numpy()
