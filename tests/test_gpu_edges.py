@@ -238,3 +238,40 @@ def test_sphere_trace_degenerate_settings(torch_cuda):
         assert np.all(t.cpu().numpy()[inside] == 0.0)
         assert g_steps.max() <= max_steps
     assert ddf.ddf_check_status(m.h) == 0
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+@pytest.mark.parametrize("tiles", [((256, 4, 1, 1, 0), (256, 4, 0, 1, 1)),
+                                   ((256, 8, 1, 1, 0), (256, 8, 0, 1, 1)),
+                                   ((256, 4, 1, 0, 0), (256, 4, 1, 0, 0))])
+def test_widest_field_on_the_pair_tiles(torch_cuda, prec, tiles):
+    """Width 2048, the widest field the tensor-core path takes: the staged
+    pair tile then holds 5 pipeline stages, 32 KB of per-column vectors and
+    the output boxes within the 227 KB of shared memory per CTA. 300 rays
+    (a ragged second row tile), against the emulating oracle."""
+    from paper_2606_00817_gb300 import ddf
+    net = (6, 2048, 3)
+    blob = I.xavier_blob(I.NetShape(*net))
+    sc = _scales(blob, net) if prec == "fp8" else None
+    m = _make(net, prec, blob, sc)
+    ddf.ddf_set_tile(m.h, tiles[0], 0)
+    ddf.ddf_set_tile(m.h, tiles[1], 1)
+    rays = I.uniform_rays(300, seed=60)
+    t, v = _query(torch_cuda, m, rays)
+    _check(t, v, rays, blob, net, prec, sc)
+    assert ddf.ddf_check_status(m.h) == 0
+
+
+def test_widest_and_deepest_configurations_are_the_limits(torch_cuda):
+    """The deepest field (64 hidden layers) runs and matches the oracle; one
+    column or layer more is refused at creation, before any launch."""
+    from paper_2606_00817_gb300 import ddf
+    net = (6, 128, 64)
+    blob = I.xavier_blob(I.NetShape(*net))
+    m = _make(net, "bf16", blob)
+    rays = I.uniform_rays(129, seed=61)
+    t, v = _query(torch_cuda, m, rays)
+    _check(t, v, rays, blob, net, "bf16", None)
+    for bad in ((6, 2176, 2), (6, 128, 65)):
+        with pytest.raises(ddf.DDFError):
+            ddf.DDF(*bad, precision="bf16")
