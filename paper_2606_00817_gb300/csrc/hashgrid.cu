@@ -109,7 +109,8 @@ __device__ __forceinline__ void hg_dir_code(float dx, float dy, float dz, float 
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       float s, co;
-      sincospif(ldexpf(dc[c], k), &s, &co);  // pi 2^k d, the 2^k scaling is exact
+      // pi 2^k d: the product by 2^k (exponent bits) is exact
+      sincospif(dc[c] * __int_as_float((127 + k) << 23), &s, &co);
       out[3 + 8 * c + 2 * k] = s;
       out[4 + 8 * c + 2 * k] = co;
     }

@@ -68,7 +68,8 @@ __global__ void __launch_bounds__(kEncRays) encode_kernel(RaySoA rays, int64_t M
     for (int c = 0; c < 6; ++c) {
       for (int k = 0; k < L; ++k) {
         float s, co;
-        sincospif(ldexpf(e[c], k), &s, &co);  // pi * 2^k * e, the 2^k scaling is exact
+        // pi 2^k e: the product by 2^k (exponent bits; k <= 15) is exact
+        sincospif(e[c] * __int_as_float((127 + k) << 23), &s, &co);
         row[col] = s;
         row[col + 1] = co;
         col += 2;

@@ -69,7 +69,9 @@ __device__ __forceinline__ uint32_t next_pair(const float (&e)[6], int L, int& c
   if (c >= 6) return 0u;
   const float ec = c == 0 ? e[0] : c == 1 ? e[1] : c == 2 ? e[2] : c == 3 ? e[3] : c == 4 ? e[4] : e[5];
   float sn, cs;
-  sincospif(ldexpf(ec, k), &sn, &cs);  // pi 2^k e, the 2^k scaling is exact
+  // pi 2^k e: the product by 2^k (built from its exponent bits; k <= 15) is
+  // exact, the value ldexpf(e, k) gives, without ldexpf's general path
+  sincospif(ec * __int_as_float((127 + k) << 23), &sn, &cs);
   if (++k == L) {
     k = 0;
     ++c;

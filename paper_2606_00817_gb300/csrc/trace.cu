@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kPtRows)
     for (int c = 0; c < 3; ++c)
       for (int k = 0; k < L; ++k) {
         float s, co;
-        sincospif(ldexpf(e[c], k), &s, &co);
+        sincospif(e[c] * __int_as_float((127 + k) << 23), &s, &co);  // 2^k exactly
         row[col] = s;
         row[col + 1] = co;
         col += 2;
