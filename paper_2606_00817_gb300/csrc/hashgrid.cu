@@ -358,17 +358,19 @@ __global__ void __launch_bounds__(kHgF32Rays)
 }
 
 // ---------------------------------------------------------------- training
-// Training forward and backward with 4 threads per ray (64 rays, 256
-// threads per block): at the batch sizes of a distillation step (16,384
+// Training forward and backward with kHgTrainT = 4 threads per ray (64 rays,
+// 256 threads per block): at the batch sizes of a distillation step (16,384
 // rays) one thread per ray leaves 3-4 warps per SM, every table gather and
 // atomic waiting out its full latency. Thread t of a ray takes levels t,
 // t + 4, t + 8, t + 12 and outputs (or input gradients) t + 4 q; each output
 // is still summed over its inputs in order, so the values are those of one
-// thread per ray. The ray's rows live in shared memory as in the query
-// kernel; __syncwarp orders the 4 threads of a ray (same warp). Threads of
-// rays past the end stay to the end (they take part in __syncwarp) and skip
-// every load and store of their row.
+// thread per ray (8 threads per ray were measured too, and were no faster). The ray's rows live in shared memory as in the query kernel;
+// __syncwarp orders the threads of a ray (same warp). Threads of rays past
+// the end stay to the end (they take part in __syncwarp) and skip every
+// load and store of their row.
 constexpr int kHgTrainT = 4;
+static_assert(kHgLevels % kHgTrainT == 0 && kHgW % kHgTrainT == 0 && 32 % kHgTrainT == 0,
+              "a ray's threads share a warp and split the levels and outputs evenly");
 constexpr int kHgTrainThreads = kHgF32Rays * kHgTrainT;
 
 // Forward weight rows in shared memory: odd strides (59, 65), so that the
@@ -402,7 +404,7 @@ __global__ void __launch_bounds__(kHgTrainThreads)
     for (int i = threadIdx.x; i < 2 * kHgW + 2; i += blockDim.x) sw[dst + i] = mlp[src + i];
   }
   __syncthreads();
-  const int r = threadIdx.x >> 2, t = threadIdx.x & 3;
+  const int r = threadIdx.x / kHgTrainT, t = threadIdx.x % kHgTrainT;
   const int64_t row = static_cast<int64_t>(blockIdx.x) * kHgF32Rays + r;
   const bool valid = row < M;
   float* a = bufA + r * kHgLd;
@@ -414,8 +416,8 @@ __global__ void __launch_bounds__(kHgTrainThreads)
       v1 = __ldg(table + e1);
     };
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int l = t + 4 * j;
+    for (int j = 0; j < kHgLevels / kHgTrainT; ++j) {
+      const int l = t + kHgTrainT * j;
       hg_level(g, l, x, y, z, fetch, a[2 * l], a[2 * l + 1]);
     }
     if (t == 0) {
@@ -469,7 +471,7 @@ __global__ void __launch_bounds__(kHgTrainThreads)
   }
 }
 
-// Backward of the training forward above, 4 threads per ray: dL/dpre of
+// Backward of the training forward above, kHgTrainT threads per ray: dL/dpre of
 // every layer (feature-major, [H x 64 x B]) and the hash features' gradient
 // scattered into the level tables' gradient (blob layout, 8-byte aligned):
 // each corner entry receives its trilinear weight times the feature
@@ -485,7 +487,7 @@ __global__ void __launch_bounds__(kHgTrainThreads)
   float* bufB = bufA + kHgF32Rays * kHgLd;
   for (int i = threadIdx.x; i < n_mlp; i += blockDim.x) sw[i] = mlp[i];
   __syncthreads();
-  const int r = threadIdx.x >> 2, t = threadIdx.x & 3;
+  const int r = threadIdx.x / kHgTrainT, t = threadIdx.x % kHgTrainT;
   const int64_t row = static_cast<int64_t>(blockIdx.x) * kHgF32Rays + r;
   const bool valid = row < M;
   float* dh = bufA + r * kHgLd;
@@ -532,10 +534,11 @@ __global__ void __launch_bounds__(kHgTrainThreads)
     dn = tmp;
   }
   if (!valid) return;
-  // dh holds dL/d(hash features) [32]: this thread scatters levels t, t + 4, ...
+  // dh holds dL/d(hash features) [32]: this thread scatters levels t,
+  // t + kHgTrainT, ...
   const float x = box01(rays.p[0][row]), y = box01(rays.p[1][row]), z = box01(rays.p[2][row]);
-  for (int j = 0; j < 4; ++j) {
-    const int l = t + 4 * j;
+  for (int j = 0; j < kHgLevels / kHgTrainT; ++j) {
+    const int l = t + kHgTrainT * j;
     const int n = g.res[l];
     const float fn = static_cast<float>(n);
     const float ux = x * fn, uy = y * fn, uz = z * fn;
