@@ -378,20 +378,16 @@ __device__ __forceinline__ void epi_tile_tma(const TcGemmParams& p, const EpiVec
   }
 }
 
-// Training forward (mode 0, bf16, no column scale) through the warp's
-// staging buffer, as epi_row_staged, plus the layer's ReLU pattern: bit j of
-// relu_bits[row * ldb + column / 32] is set iff output column 32 (column / 32)
-// + j of the row is positive after rounding to bf16 (the test the input
-// gradients apply to this activation); relu_bits may be null. Mode 4 (the
-// last layer) also folds the stored bf16 outputs into the two head dot
-// products over the thread's columns, in column order (h0, h1).
+// Training forward of the last layer (mode 4, bf16, no column scale) through
+// the warp's staging buffer, as epi_row_staged, folding the stored bf16
+// outputs into the two head dot products over the thread's columns, in
+// column order (h0, h1).
 // One chunk (32 columns, chunk index c of the tile, half h of its 128-byte
-// staging row): bias, ReLU, bf16, staged; returns the chunk's ReLU bits.
-__device__ __forceinline__ uint32_t epi_chunk_stage_bits(const EpiVectors& ev, const uint32_t (&v)[32],
-                                                         int col0, int h, uint8_t* myrow, int sw,
-                                                         float& h0, float& h1) {
+// staging row): bias, ReLU, bf16, staged, and the head's partial sums.
+__device__ __forceinline__ void epi_chunk_stage_head(const EpiVectors& ev, const uint32_t (&v)[32],
+                                                     int col0, int h, uint8_t* myrow, int sw,
+                                                     float& h0, float& h1) {
   const float* bias = ev.bias + col0;
-  uint32_t m = 0;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     uint32_t ow[4];
@@ -400,32 +396,24 @@ __device__ __forceinline__ uint32_t epi_chunk_stage_bits(const EpiVectors& ev, c
       const int j = 8 * k + 2 * q;
       ow[q] = epi_pack_bf16x2_relu(__uint_as_float(v[j]) + bias[j],
                                    __uint_as_float(v[j + 1]) + bias[j + 1]);
-      // positive after rounding: a nonzero magnitude (a zero of either sign
-      // passes no gradient)
-      m |= ((ow[q] & 0x7FFFu) != 0u ? 1u : 0u) << j;
-      m |= ((ow[q] & 0x7FFF0000u) != 0u ? 1u : 0u) << (j + 1);
-      if (ev.hw0 != nullptr) {
-        const int col = col0 + j;
-        const float x0 = __uint_as_float(ow[q] << 16), x1 = __uint_as_float(ow[q] & 0xFFFF0000u);
-        h0 = fmaf(x0, ev.hw0[col], h0);
-        h1 = fmaf(x0, ev.hw1[col], h1);
-        h0 = fmaf(x1, ev.hw0[col + 1], h0);
-        h1 = fmaf(x1, ev.hw1[col + 1], h1);
-      }
+      const int col = col0 + j;
+      const float x0 = __uint_as_float(ow[q] << 16), x1 = __uint_as_float(ow[q] & 0xFFFF0000u);
+      h0 = fmaf(x0, ev.hw0[col], h0);
+      h1 = fmaf(x0, ev.hw1[col], h1);
+      h0 = fmaf(x1, ev.hw0[col + 1], h0);
+      h1 = fmaf(x1, ev.hw1[col + 1], h1);
     }
     *reinterpret_cast<uint4*>(myrow + (((4 * h + k) ^ sw) << 4)) = make_uint4(ow[0], ow[1], ow[2], ow[3]);
   }
-  return m;
 }
 
 // The TMEM loads run one chunk ahead of the arithmetic (chunk c + 1 is in
 // flight while chunk c is converted), as in epi_row_staged.
-__device__ __forceinline__ void epi_row_staged_bits(const TcGemmParams& p, const EpiVectors& ev,
+__device__ __forceinline__ void epi_row_staged_head(const TcGemmParams& p, const EpiVectors& ev,
                                                     uint32_t tbase, int warp_row0, int n0,
                                                     int c_begin, int c_end, uint8_t* stage,
                                                     int lane, float& h0, float& h1) {
   const size_t row_bytes = static_cast<size_t>(p.ldo) * 2;
-  const int row = warp_row0 + lane;
   const int sw = lane & 7;
   uint8_t* myrow = stage + lane * 128;
   uint32_t va[32], vb[32];
@@ -434,67 +422,72 @@ __device__ __forceinline__ void epi_row_staged_bits(const TcGemmParams& p, const
 #pragma unroll 1
   for (int c = c_begin; c < c_end; c += 2) {  // c_end - c_begin is even
     tmem_ld32(tbase + 32u * (c + 1), vb);
-    const uint32_t b0 = epi_chunk_stage_bits(ev, va, n0 + 32 * c, 0, myrow, sw, h0, h1);
+    epi_chunk_stage_head(ev, va, n0 + 32 * c, 0, myrow, sw, h0, h1);
     tmem_wait_ld_regs(vb);
     const bool next2 = c + 2 < c_end;
     if (next2) tmem_ld32(tbase + 32u * (c + 2), va);
-    const uint32_t b1 = epi_chunk_stage_bits(ev, vb, n0 + 32 * (c + 1), 1, myrow, sw, h0, h1);
-    if (row < p.M && p.relu_bits != nullptr)
-      *reinterpret_cast<uint2*>(p.relu_bits + static_cast<size_t>(row) * p.ldb + n0 / 32 + c) =
-          make_uint2(b0, b1);
+    epi_chunk_stage_head(ev, vb, n0 + 32 * (c + 1), 1, myrow, sw, h0, h1);
     epi_flush_stage(p, stage, warp_row0, row_bytes, static_cast<size_t>(n0 + 32 * c) * 2, lane);
     if (next2) tmem_wait_ld_regs(va);
   }
 }
 
-// One chunk of the input gradient: the accumulator where ReLU bit j of m is
-// set, else 0, as bf16 into half h of the staging row.
-__device__ __forceinline__ void epi_chunk_stage_masked(const uint32_t (&v)[32], uint32_t m, int h,
-                                                       uint8_t* myrow, int sw) {
+// One chunk of the input gradient: the accumulator where the activation is
+// positive, else 0, as bf16 into half h of the staging row. mk holds the
+// chunk's 32 bf16 activations of this lane's row; one bf16x2 comparison
+// gives the mask of both halves of a packed pair (a zero of either sign
+// passes no gradient), so the result is bf16(acc) or +0.
+__device__ __forceinline__ void epi_chunk_stage_masked(const uint32_t (&v)[32], const uint4* mk,
+                                                       int h, uint8_t* myrow, int sw) {
+  const __nv_bfloat162 zero = __float2bfloat162_rn(0.f);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
+    const __nv_bfloat162* a = reinterpret_cast<const __nv_bfloat162*>(mk + k);
     uint32_t ow[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int j = 8 * k + 2 * q;
-      const float x0 = (m >> j) & 1u ? __uint_as_float(v[j]) : 0.f;
-      const float x1 = (m >> (j + 1)) & 1u ? __uint_as_float(v[j + 1]) : 0.f;
-      ow[q] = epi_pack_bf16x2(x0, x1);
+      ow[q] = epi_pack_bf16x2(__uint_as_float(v[j]), __uint_as_float(v[j + 1])) &
+              __hgt2_mask(a[q], zero);
     }
     *reinterpret_cast<uint4*>(myrow + (((4 * h + k) ^ sw) << 4)) = make_uint4(ow[0], ow[1], ow[2], ow[3]);
   }
 }
 
 // Input gradient (mode 2, bf16) through the warp's staging buffer: the
-// accumulator where the previous layer's ReLU pattern (relu_bits, as written
-// by epi_row_staged_bits) is set, else 0, leaving as 128-byte lines. With
+// accumulator where the previous layer's activation (p.mask, bf16
+// [M x ldm]) is positive, else 0, leaving as 128-byte lines. With
 // p.col_part, lane l also sums columns 2l and 2l + 1 of each 64-column group
 // over the warp's 32 rows (the bias gradient's share of these rows) into
-// col_part[warp_row0 / 32][column]. The TMEM loads and the ReLU bits of the
-// next chunk are in flight while a chunk is converted.
+// col_part[warp_row0 / 32][column]. The TMEM loads of the next chunk, and
+// the activations of the next two chunks, are in flight while a chunk is
+// converted. c_end - c_begin is a multiple of 4.
 __device__ __forceinline__ void epi_row_masked_staged(const TcGemmParams& p, uint32_t tbase,
                                                       int warp_row0, int n0, int c_begin,
                                                       int c_end, uint8_t* stage, int lane) {
   const size_t row_bytes = static_cast<size_t>(p.ldo) * 2;
   const int row = warp_row0 + lane;
+  const bool row_ok = row < p.M;
   const int sw = lane & 7;
   uint8_t* myrow = stage + lane * 128;
-  const uint32_t* bits_row = p.relu_bits + static_cast<size_t>(row) * p.ldb + n0 / 32;
+  // 8 bf16 per uint4: chunk c of the tile starts at uint4 4 c of the row
+  const uint4* mrow = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(p.mask) +
+                                                     static_cast<size_t>(row_ok ? row : 0) * p.ldm + n0);
+  auto load_pair = [&](int c, uint4 (&m)[8]) {  // the activations of chunks c, c + 1
+#pragma unroll
+    for (int i = 0; i < 8; ++i) m[i] = row_ok ? __ldg(mrow + 4 * c + i) : make_uint4(0u, 0u, 0u, 0u);
+  };
   uint32_t va[32], vb[32];
-  uint2 mb = make_uint2(0u, 0u);
-  if (row < p.M) mb = *reinterpret_cast<const uint2*>(bits_row + c_begin);
-  tmem_ld32(tbase + 32u * c_begin, va);
-  tmem_wait_ld_regs(va);
-#pragma unroll 1
-  for (int c = c_begin; c < c_end; c += 2) {  // c_end - c_begin is even
+  // one step: chunks c and c + 1 with their activations in cur, those of
+  // c + 2 and c + 3 loaded into nxt
+  auto step = [&](int c, const uint4 (&cur)[8], uint4 (&nxt)[8]) {
     tmem_ld32(tbase + 32u * (c + 1), vb);
     const bool next2 = c + 2 < c_end;
-    uint2 mb_next = make_uint2(0u, 0u);
-    if (next2 && row < p.M) mb_next = *reinterpret_cast<const uint2*>(bits_row + c + 2);
-    epi_chunk_stage_masked(va, mb.x, 0, myrow, sw);
+    if (next2) load_pair(c + 2, nxt);
+    epi_chunk_stage_masked(va, cur, 0, myrow, sw);
     tmem_wait_ld_regs(vb);
     if (next2) tmem_ld32(tbase + 32u * (c + 2), va);
-    epi_chunk_stage_masked(vb, mb.y, 1, myrow, sw);
+    epi_chunk_stage_masked(vb, cur + 4, 1, myrow, sw);
     if (p.col_part != nullptr) {
       __syncwarp();
       // lane l: columns 2l, 2l + 1 of the group = 4-byte word (l & 3) of
@@ -512,8 +505,16 @@ __device__ __forceinline__ void epi_row_masked_staged(const TcGemmParams& p, uin
                                  32 * c + 2 * lane) = make_float2(s0, s1);
     }
     epi_flush_stage(p, stage, warp_row0, row_bytes, static_cast<size_t>(n0 + 32 * c) * 2, lane);
-    mb = mb_next;
     if (next2) tmem_wait_ld_regs(va);
+  };
+  uint4 m0[8], m1[8];
+  load_pair(c_begin, m0);
+  tmem_ld32(tbase + 32u * c_begin, va);
+  tmem_wait_ld_regs(va);
+#pragma unroll 1
+  for (int c = c_begin; c < c_end; c += 4) {
+    step(c, m0, m1);
+    step(c + 2, m1, m0);
   }
 }
 

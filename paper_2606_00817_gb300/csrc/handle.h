@@ -111,7 +111,6 @@ struct ddf_s {
   float* tr_lpart = nullptr;              // per-block loss partials
   float* tr_colpart = nullptr;            // [B / 32 x W] column sums of an input gradient
   float2* tr_hz = nullptr;                // [W / 256 x B] head partials of the last layer
-  std::vector<uint32_t*> tr_bits;         // layers 0..H-2: [B x W/32] ReLU patterns (pair path)
   float* grad = nullptr;                  // gradient blob (weight-blob layout)
   float* adam_m = nullptr;
   float* adam_v = nullptr;

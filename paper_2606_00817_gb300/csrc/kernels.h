@@ -41,8 +41,9 @@ struct TcGemmParams {
   uint64_t timeout_ns;
   float* amax;             // mode 0, nullable: running max of the layer's outputs
                            // (rows < M), for activation-scale calibration
-  // training modes (1-CTA kernel only):
+  // training modes:
   //   mode 2: out = bf16(acc masked by mask > 0), mask bf16 [M x ldm]
+  //           (the activation whose ReLU the gradient passes back through)
   //   mode 3: out_f32[split][M x ldo] = acc, k_splits splits of the K range
   const void* mask;
   int ldm;
@@ -57,14 +58,9 @@ struct TcGemmParams {
   // 64 x 64 boxes; lets dW = dZ^T X read dZ [B x W] and X [B x K] as stored
   int mn_major;
   // training on the pair kernel: mode 4 is mode 0 for the last layer, with
-  // the head partials of mode 1 taken from the stored bf16 outputs;
-  // mode 0 writes the output's ReLU pattern
-  // (bit j of relu_bits[row * ldb + c]: column 32 c + j positive), mode 2
-  // applies the previous layer's pattern from relu_bits instead of reading
-  // `mask`, and writes per 32-row block column sums of its output into
+  // the head partials of mode 1 taken from the stored bf16 outputs; mode 2
+  // also writes per 32-row block column sums of its output into
   // col_part [ceil(M / 32) x ldo] FP32 (nullable)
-  uint32_t* relu_bits;
-  int ldb;
   float* col_part;
   // pair kernel, staged query tile (mode 0): 1 = the outputs leave shared
   // memory by TMA tensor stores through the output map the launcher takes
@@ -130,9 +126,9 @@ int tc_gemm_smem_bytes(int bn, bool in_fp8);
 
 // CTA-pair variant: clusters of 2 CTAs, 256 x 256 output tiles, persistent
 // over `clusters` clusters, 4 or 8 epilogue warps per CTA (training modes
-// and the training forward with ReLU bits: kTrainEpiWarps, whatever
-// epi_warps says). Modes 1 and 4 write (N/256) (epi_warps/4) head partials
-// per row; modes 2 and 3 (bf16) as the 1-CTA kernel, mode 3 with K-major or
+// 2-4: kTrainEpiWarps, whatever epi_warps says). Modes 1 and 4 write
+// (N/256) (epi_warps/4) head partials per row; modes 2 and 3 (bf16) as the
+// 1-CTA kernel, mode 2 through the staging buffers, mode 3 with K-major or
 // MN-major operands.
 constexpr int kTrainEpiWarps = 4;
 // tmO: the output map when p.tma_out is set (the staged mode-0 tile), else

@@ -75,8 +75,9 @@ struct PairShape {
   static_assert(NUM_BARS * 8 + 16 <= CTRL_BYTES, "control block overflow");
 };
 
-// TRAIN: the training modes (2, 3: masked input gradients, split-K weight
-// gradients with K-major or MN-major operands), bf16 only; the query
+// TRAIN: the training modes (2: input gradients masked by the stored
+// activation; 3: split-K weight gradients with K-major or MN-major operands;
+// 4: the last layer's forward with the head partials), bf16 only; the query
 // instantiations compile none of it.
 template <bool IN_FP8, bool OUT_FP8, bool STAGED, bool TRAIN, int EPI = 4>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EPI), 1)
@@ -286,8 +287,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EPI), 1)
                              static_cast<uint32_t>(b * S::BN);
       float h0 = 0.f, h1 = 0.f;
       if constexpr (TRAIN) {
-        if (p.mode == 0 || p.mode == 4)
-          epi_row_staged_bits(p, ev, tbase, row - lane, n0, c0, c1, stage_w, lane, h0, h1);
+        static_assert(kChunks % 4 == 0, "the masked epilogue steps over 4 chunks");
+        if (p.mode == 4)
+          epi_row_staged_head(p, ev, tbase, row - lane, n0, c0, c1, stage_w, lane, h0, h1);
         else if (p.mode == 2)
           epi_row_masked_staged(p, tbase, row - lane, n0, c0, c1, stage_w, lane);
         else
@@ -406,8 +408,7 @@ cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, bool staged, int epi_
                                 const CUtensorMap& tmA, const CUtensorMap& tmB,
                                 const TcGemmParams& p, int clusters, cudaStream_t s,
                                 const CUtensorMap* tmO) {
-  if (p.tma_out && (tmO == nullptr || !staged || p.mode != 0 || p.relu_bits != nullptr ||
-                    p.amax != nullptr))
+  if (p.tma_out && (tmO == nullptr || !staged || p.mode != 0 || p.amax != nullptr))
     return cudaErrorInvalidValue;  // TMA stores: the staged query tile, with its output map
   const CUtensorMap& to = tmO != nullptr ? *tmO : tmA;  // not read unless p.tma_out
   if (p.mode == 3 && (p.k_splits > 1 ? p.k_splits : 1) > (p.K + 63) / 64)
@@ -415,13 +416,11 @@ cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, bool staged, int epi_
   if (p.mn_major && (in_fp8 || p.mode != 3)) return cudaErrorInvalidValue;
   if (p.mode >= 2 && (in_fp8 || out_fp8)) return cudaErrorInvalidValue;
   if (p.mode == 4 && (p.head_w == nullptr || p.head_part == nullptr)) return cudaErrorInvalidValue;
-  if ((p.mode == 2 || p.relu_bits != nullptr) &&
-      (p.relu_bits == nullptr || p.ldb < p.N / 32 || p.ldb % 2 != 0 || p.N % 64 != 0 || in_fp8 ||
-       out_fp8))
-    return cudaErrorInvalidValue;  // ReLU patterns: bf16, whole 64-column groups
+  if (p.mode == 2 && (p.mask == nullptr || reinterpret_cast<uintptr_t>(p.mask) % 16 != 0 ||
+                      p.ldm < p.N || p.ldm % 8 != 0))
+    return cudaErrorInvalidValue;  // the activation is read as 16-byte pieces of its rows
   const int grid = 2 * clusters;
-  // training modes, and the training forward that writes ReLU patterns
-  if (p.mode >= 2 || p.relu_bits != nullptr)
+  if (p.mode >= 2)  // training modes
     return launch_pair_one<false, false, true, true, kTrainEpiWarps>(tmA, tmB, to, p, grid, s);
   if (epi_warps == 8) return launch_pair_epi<8>(in_fp8, out_fp8, staged, tmA, tmB, to, p, grid, s);
   if (epi_warps != 4) return cudaErrorInvalidValue;

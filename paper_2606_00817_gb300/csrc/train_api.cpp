@@ -180,8 +180,6 @@ ddf_status ensure_train(ddf_s* h, int64_t B) {
     }
     for (void* q : h->tr_store) dev_free(h, q);
     h->tr_store.clear();
-    for (uint32_t* q : h->tr_bits) dev_free(h, q);
-    h->tr_bits.assign(H > 1 ? H - 1 : 0, nullptr);
     h->tr_h.assign(H, nullptr);
     h->tr_rows = 0;
     const size_t act = static_cast<size_t>(B) * W * 2;
@@ -222,12 +220,6 @@ ddf_status ensure_train(ddf_s* h, int64_t B) {
         DDF_OK)
       return s;
     h->tr_hz = static_cast<float2*>(p);
-    if (h->tr_pair)
-      for (auto& q : h->tr_bits) {
-        if ((s = train_alloc(h, &p, static_cast<size_t>(B) * (W / 32) * sizeof(uint32_t))) != DDF_OK)
-          return s;
-        q = static_cast<uint32_t*>(p);
-      }
     h->tr_rows = B;
   }
   return DDF_OK;
@@ -263,7 +255,15 @@ ddf_status tc_gemm_pair(ddf_s* h, const void* A, int M, int K, const CUtensorMap
   p.timeout_ns = h->timeout_ns;
   const int64_t tiles = ((M + 255) / 256) * static_cast<int64_t>(p.N / 256);
   const int clusters = static_cast<int>(std::min<int64_t>(tiles, h->pair_clusters));
-  DDF_CK(ddf::launch_tc_gemm_pair(false, false, staged, 4, tmA, tmB, p, clusters, st));
+  CUtensorMap tmO;  // a staged forward's output leaves shared memory by TMA stores
+  const bool tma_out = staged && p.mode == 0;
+  if (tma_out) {
+    if (!make_tmap(&tmO, p.out, false, p.N, M, static_cast<uint64_t>(p.ldo) * 2, 32))
+      return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for an output map");
+    p.tma_out = 1;
+  }
+  DDF_CK(ddf::launch_tc_gemm_pair(false, false, staged, 4, tmA, tmB, p, clusters, st,
+                                  tma_out ? &tmO : nullptr));
   return DDF_OK;
 }
 
@@ -296,8 +296,8 @@ ddf_status check_train_args(ddf_s* h, const float* const rays[6], const float* t
 bool head_in_last_layer(const ddf_s* h) { return h->tr_pair && h->cfg.kind == DDF_KIND_RAY; }
 
 // Forward of layer l over the batch: tr_h[l] = ReLU(tr_h[l-1] W_l^T + b_l)
-// (layer 0 reads the encoding), plus its ReLU bits on the pair path. The
-// GEMMs are deterministic, so a recomputed layer is bitwise the first one.
+// (layer 0 reads the encoding). The GEMMs are deterministic, so a
+// recomputed layer is bitwise the first one.
 ddf_status forward_layer(ddf_s* h, int l, int B, cudaStream_t st) {
   const int W = h->cfg.width, H = h->cfg.hidden_layers;
   ddf::TcGemmParams p{};
@@ -310,10 +310,6 @@ ddf_status forward_layer(ddf_s* h, int l, int B, cudaStream_t st) {
   ProfScope ps(h, l == 0 ? kProfFirst : kProfGemm, st);
   const void* A_in = l == 0 ? h->tr_enc : h->tr_h[l - 1];
   const int K = l == 0 ? h->kp16 : W;
-  if (h->tr_pair && l < H - 1) {  // the input gradients will test this layer's ReLU pattern
-    p.relu_bits = h->tr_bits[l];
-    p.ldb = W / 32;
-  }
   if (head_in_last_layer(h) && l == H - 1) {  // z's partial dot products, per 256 columns
     p.mode = 4;
     p.head_w = h->head_w;
@@ -498,11 +494,7 @@ ddf_status backward_from_dz(ddf_s* h, int B, cudaStream_t st) {
     q.ldo = W;
     q.mask = h->tr_h[l - 1];
     q.ldm = W;
-    if (h->tr_pair) {
-      q.relu_bits = h->tr_bits[l - 1];
-      q.ldb = W / 32;
-      q.col_part = h->tr_colpart;
-    }
+    if (h->tr_pair) q.col_part = h->tr_colpart;
     {
       ProfScope ps(h, kProfGemm, st);
       ddf_status s = h->tr_pair ? tc_gemm_pair(h, h->tr_dpre[cur], B, W, h->tmWTpair[l], false, q, st)
