@@ -85,23 +85,51 @@ __device__ __forceinline__ uint32_t epi_pack_e4m3x4_relu(float a, float b, float
   return static_cast<uint32_t>(lo) | (static_cast<uint32_t>(hi) << 16);
 }
 
-// Processes the 32 accumulator values v of columns [nc, nc + 32) of `row`.
-template <bool OUT_FP8>
-__device__ __forceinline__ void epi_chunk(const TcGemmParams& p, const EpiVectors& ev,
-                                          const uint32_t (&v)[32], int row, bool row_ok, int nc,
-                                          float& h0, float& h1) {
-  float x[32];  // before the ReLU, which the packing conversions (or the head) apply
+// One 32-byte (256-bit) global store of w[0..7] at p (32-byte aligned): a
+// whole sector from one thread, so rows written by different lanes of a warp
+// still reach L2 as full sectors.
+__device__ __forceinline__ void st_global_256(void* p, const uint32_t* w) {
+  asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(w[0]),
+               "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+               : "memory");
+}
+
+// Host check of what the mode-0 thread stores assume: the output and its
+// row stride 32-byte aligned.
+inline bool epi_out_aligned(const TcGemmParams& p, bool out_fp8) {
+  if (p.mode != 0 || p.out == nullptr) return true;
+  const size_t row_bytes = static_cast<size_t>(p.ldo) * (out_fp8 ? 1 : 2);
+  return reinterpret_cast<uintptr_t>(p.out) % 32 == 0 && row_bytes % 32 == 0;
+}
+
+// x[j] = v[j] cs[j] + bias[j] over the chunk's 32 columns [nc, nc + 32),
+// two columns per packed FP32 FMA (each lane rounds once, as fmaf does).
+__device__ __forceinline__ void epi_affine32(const EpiVectors& ev, const uint32_t (&v)[32], int nc,
+                                             float (&x)[32]) {
   const float4* b4 = reinterpret_cast<const float4*>(ev.bias + nc);
 #pragma unroll
   for (int j4 = 0; j4 < 8; ++j4) {
     const float4 bb = b4[j4];
     float4 cs = make_float4(ev.uscale, ev.uscale, ev.uscale, ev.uscale);
     if (ev.scale != nullptr) cs = reinterpret_cast<const float4*>(ev.scale + nc)[j4];
-    x[4 * j4 + 0] = fmaf(__uint_as_float(v[4 * j4 + 0]), cs.x, bb.x);
-    x[4 * j4 + 1] = fmaf(__uint_as_float(v[4 * j4 + 1]), cs.y, bb.y);
-    x[4 * j4 + 2] = fmaf(__uint_as_float(v[4 * j4 + 2]), cs.z, bb.z);
-    x[4 * j4 + 3] = fmaf(__uint_as_float(v[4 * j4 + 3]), cs.w, bb.w);
+    const float2 lo = __ffma2_rn(make_float2(__uint_as_float(v[4 * j4 + 0]), __uint_as_float(v[4 * j4 + 1])),
+                                 make_float2(cs.x, cs.y), make_float2(bb.x, bb.y));
+    const float2 hi = __ffma2_rn(make_float2(__uint_as_float(v[4 * j4 + 2]), __uint_as_float(v[4 * j4 + 3])),
+                                 make_float2(cs.z, cs.w), make_float2(bb.z, bb.w));
+    x[4 * j4 + 0] = lo.x;
+    x[4 * j4 + 1] = lo.y;
+    x[4 * j4 + 2] = hi.x;
+    x[4 * j4 + 3] = hi.y;
   }
+}
+
+// Processes the 32 accumulator values v of columns [nc, nc + 32) of `row`.
+template <bool OUT_FP8>
+__device__ __forceinline__ void epi_chunk(const TcGemmParams& p, const EpiVectors& ev,
+                                          const uint32_t (&v)[32], int row, bool row_ok, int nc,
+                                          float& h0, float& h1) {
+  float x[32];  // before the ReLU, which the packing conversions (or the head) apply
+  epi_affine32(ev, v, nc, x);
   if (p.mode == 0) {
     if (p.amax != nullptr) {  // calibration: the warp's largest output of valid rows
       float m = 0.f;          // max(0, max x) = the largest output after the ReLU
@@ -115,50 +143,41 @@ __device__ __forceinline__ void epi_chunk(const TcGemmParams& p, const EpiVector
       if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(p.amax), __float_as_int(m));
     }
     if (!row_ok) return;
+    // 32-byte stores: the output rows start 32-byte aligned (launchers check
+    // the base and the row stride) and nc is a multiple of 32
     if constexpr (OUT_FP8) {
       uint8_t* dst = static_cast<uint8_t*>(p.out) + static_cast<size_t>(row) * p.ldo + nc;
-      uint4 w0, w1;  // the output scale is already in the vectors
-      w0.x = epi_pack_e4m3x4_relu(x[0], x[1], x[2], x[3]);
-      w0.y = epi_pack_e4m3x4_relu(x[4], x[5], x[6], x[7]);
-      w0.z = epi_pack_e4m3x4_relu(x[8], x[9], x[10], x[11]);
-      w0.w = epi_pack_e4m3x4_relu(x[12], x[13], x[14], x[15]);
-      w1.x = epi_pack_e4m3x4_relu(x[16], x[17], x[18], x[19]);
-      w1.y = epi_pack_e4m3x4_relu(x[20], x[21], x[22], x[23]);
-      w1.z = epi_pack_e4m3x4_relu(x[24], x[25], x[26], x[27]);
-      w1.w = epi_pack_e4m3x4_relu(x[28], x[29], x[30], x[31]);
-      reinterpret_cast<uint4*>(dst)[0] = w0;
-      reinterpret_cast<uint4*>(dst)[1] = w1;
+      uint32_t w[8];  // the output scale is already in the vectors
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        w[k] = epi_pack_e4m3x4_relu(x[4 * k], x[4 * k + 1], x[4 * k + 2], x[4 * k + 3]);
+      st_global_256(dst, w);
     } else {
       __nv_bfloat16* dst =
           static_cast<__nv_bfloat16*>(p.out) + static_cast<size_t>(row) * p.ldo + nc;
+      uint32_t w[16];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        uint4 w;
-        w.x = epi_pack_bf16x2_relu(x[8 * k + 0], x[8 * k + 1]);
-        w.y = epi_pack_bf16x2_relu(x[8 * k + 2], x[8 * k + 3]);
-        w.z = epi_pack_bf16x2_relu(x[8 * k + 4], x[8 * k + 5]);
-        w.w = epi_pack_bf16x2_relu(x[8 * k + 6], x[8 * k + 7]);
-        reinterpret_cast<uint4*>(dst)[k] = w;
-      }
+      for (int k = 0; k < 16; ++k) w[k] = epi_pack_bf16x2_relu(x[2 * k], x[2 * k + 1]);
+      st_global_256(dst, w);
+      st_global_256(dst + 16, w + 8);
     }
   } else {
 #pragma unroll
     for (int j = 0; j < 32; ++j) x[j] = fmaxf(x[j], 0.f);
     const float4* w0 = reinterpret_cast<const float4*>(ev.hw0 + nc);
     const float4* w1 = reinterpret_cast<const float4*>(ev.hw1 + nc);
+    float2 hh = make_float2(h0, h1);  // both head sums, one packed FMA per column
 #pragma unroll
     for (int j4 = 0; j4 < 8; ++j4) {
       const float4 a = w0[j4];
       const float4 bb = w1[j4];
-      h0 = fmaf(x[4 * j4 + 0], a.x, h0);
-      h0 = fmaf(x[4 * j4 + 1], a.y, h0);
-      h0 = fmaf(x[4 * j4 + 2], a.z, h0);
-      h0 = fmaf(x[4 * j4 + 3], a.w, h0);
-      h1 = fmaf(x[4 * j4 + 0], bb.x, h1);
-      h1 = fmaf(x[4 * j4 + 1], bb.y, h1);
-      h1 = fmaf(x[4 * j4 + 2], bb.z, h1);
-      h1 = fmaf(x[4 * j4 + 3], bb.w, h1);
+      hh = __ffma2_rn(make_float2(x[4 * j4 + 0], x[4 * j4 + 0]), make_float2(a.x, bb.x), hh);
+      hh = __ffma2_rn(make_float2(x[4 * j4 + 1], x[4 * j4 + 1]), make_float2(a.y, bb.y), hh);
+      hh = __ffma2_rn(make_float2(x[4 * j4 + 2], x[4 * j4 + 2]), make_float2(a.z, bb.z), hh);
+      hh = __ffma2_rn(make_float2(x[4 * j4 + 3], x[4 * j4 + 3]), make_float2(a.w, bb.w), hh);
     }
+    h0 = hh.x;
+    h1 = hh.y;
   }
 }
 
@@ -249,17 +268,7 @@ __device__ __forceinline__ void epi_chunk_stage(const TcGemmParams& p, const Epi
                                                 const uint32_t (&v)[32], int nc, int c,
                                                 uint8_t* stage, int lane) {
   float x[32];  // before the ReLU, which the packing conversions apply
-  const float4* b4 = reinterpret_cast<const float4*>(ev.bias + nc);
-#pragma unroll
-  for (int j4 = 0; j4 < 8; ++j4) {
-    const float4 bb = b4[j4];
-    float4 cs = make_float4(ev.uscale, ev.uscale, ev.uscale, ev.uscale);
-    if (ev.scale != nullptr) cs = reinterpret_cast<const float4*>(ev.scale + nc)[j4];
-    x[4 * j4 + 0] = fmaf(__uint_as_float(v[4 * j4 + 0]), cs.x, bb.x);
-    x[4 * j4 + 1] = fmaf(__uint_as_float(v[4 * j4 + 1]), cs.y, bb.y);
-    x[4 * j4 + 2] = fmaf(__uint_as_float(v[4 * j4 + 2]), cs.z, bb.z);
-    x[4 * j4 + 3] = fmaf(__uint_as_float(v[4 * j4 + 3]), cs.w, bb.w);
-  }
+  epi_affine32(ev, v, nc, x);
   uint8_t* row = stage + lane * 128;
   const int sw = lane & 7;
   if constexpr (OUT_FP8) {
@@ -336,8 +345,7 @@ __device__ __forceinline__ void epi_row_staged(const TcGemmParams& p, const EpiV
 }
 
 // Mode-0 drain by TMA stores (the fused layer 1, the staged pair tile): one
-// warp's chunks [c_begin, c_end) of its TMEM rows chunks [c_begin, c_end) of its TMEM rows
-// (bias + ReLU, bf16 or e4m3), packed group by group (128 bytes of each row)
+// warp's chunks [c_begin, c_end) of its TMEM rows (bias + ReLU, bf16 or e4m3), packed group by group (128 bytes of each row)
 // into the warp's output boxes and written by TMA stores at
 // (column n0 + 32 c, row row0). `issued` counts the warp's stores so far.
 template <bool OUT_FP8, int DEPTH>
@@ -492,17 +500,16 @@ __device__ __forceinline__ void epi_row_masked_staged(const TcGemmParams& p, uin
       __syncwarp();
       // lane l: columns 2l, 2l + 1 of the group = 4-byte word (l & 3) of
       // 16-byte piece l >> 2 in every row
-      float s0 = 0.f, s1 = 0.f;
+      float2 cs = make_float2(0.f, 0.f);  // both columns, one packed add per row
       const int piece = lane >> 2, word = lane & 3;
 #pragma unroll 8
       for (int r = 0; r < 32; ++r) {
         const uint32_t w = *reinterpret_cast<const uint32_t*>(stage + r * 128 +
                                                               ((piece ^ (r & 7)) << 4) + 4 * word);
-        s0 += __uint_as_float(w << 16);
-        s1 += __uint_as_float(w & 0xFFFF0000u);
+        cs = __fadd2_rn(cs, make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u)));
       }
       *reinterpret_cast<float2*>(p.col_part + static_cast<size_t>(warp_row0 / 32) * p.ldo + n0 +
-                                 32 * c + 2 * lane) = make_float2(s0, s1);
+                                 32 * c + 2 * lane) = cs;
     }
     epi_flush_stage(p, stage, warp_row0, row_bytes, static_cast<size_t>(n0 + 32 * c) * 2, lane);
     if (next2) tmem_wait_ld_regs(va);

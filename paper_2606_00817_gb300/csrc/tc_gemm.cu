@@ -298,6 +298,7 @@ int tc_gemm_smem_bytes(int bn, bool in_fp8) {
 cudaError_t launch_tc_gemm(const TcTile& tile, bool in_fp8, bool out_fp8, const CUtensorMap& tmA,
                            const CUtensorMap& tmB, const TcGemmParams& p, int grid,
                            cudaStream_t s) {
+  if (!epi_out_aligned(p, out_fp8)) return cudaErrorInvalidValue;
   if (tile.bn == 256 && tile.epi_warps == 4) return launch_bn<256, 4>(in_fp8, out_fp8, tmA, tmB, p, grid, s);
   if (tile.bn == 256 && tile.epi_warps == 8) return launch_bn<256, 8>(in_fp8, out_fp8, tmA, tmB, p, grid, s);
   if (tile.bn == 128 && tile.epi_warps == 4) return launch_bn<128, 4>(in_fp8, out_fp8, tmA, tmB, p, grid, s);

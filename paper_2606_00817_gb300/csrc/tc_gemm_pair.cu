@@ -410,6 +410,7 @@ cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, bool staged, int epi_
                                 const CUtensorMap* tmO) {
   if (p.tma_out && (tmO == nullptr || !staged || p.mode != 0 || p.amax != nullptr))
     return cudaErrorInvalidValue;  // TMA stores: the staged query tile, with its output map
+  if (!p.tma_out && !epi_out_aligned(p, out_fp8)) return cudaErrorInvalidValue;
   const CUtensorMap& to = tmO != nullptr ? *tmO : tmA;  // not read unless p.tma_out
   if (p.mode == 3 && (p.k_splits > 1 ? p.k_splits : 1) > (p.K + 63) / 64)
     return cudaErrorInvalidValue;  // every split needs a k-block

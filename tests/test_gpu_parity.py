@@ -178,19 +178,22 @@ def test_weights_round_trip_and_argument_errors(torch_cuda):
 def test_timeout_path_gives_up_cleanly_and_recovers(torch_cuda):
     """A zero wait limit makes the pipelined kernel give up at its first wait
     that is not already satisfied: the status word reports it, nothing traps,
-    and the next launch with the normal limit is correct."""
+    and the next launch with the normal limit is correct. A wait gives up
+    only once it has outlasted a tick of the global timer, so the field is
+    the paper-sized one: its first accumulator takes 20 k-blocks of MMAs
+    (microseconds) before the epilogue's first wait can succeed."""
     torch = torch_cuda
     from paper_2606_00817_gb300 import ddf
-    blob = I.xavier_blob(I.NetShape(*SMALL))
+    blob = I.xavier_blob(I.NetShape(*PAPER))
     rays = I.uniform_rays(65536, seed=7)
-    m = _make(SMALL, "bf16", blob)
+    m = _make(PAPER, "bf16", blob)
     ddf.ddf_set_timeout_ns(m.h, 0)
     m.query(_dev(torch, rays))
     assert ddf.ddf_check_status(m.h) & 1
     ddf.ddf_set_timeout_ns(m.h, 2_000_000_000)
-    t, v = _query(torch, m, rays.slice(0, 2048))
+    t, v = _query(torch, m, rays.slice(0, 512))
     assert ddf.ddf_check_status(m.h) == 0
-    _check_reduced(t, v, rays.slice(0, 2048), blob, SMALL, "bf16", None)
+    _check_reduced(t, v, rays.slice(0, 512), blob, PAPER, "bf16", None)
 
 
 @pytest.fixture(scope="module")
