@@ -353,33 +353,24 @@ def hashgrid_workload(torch, ddf, dev, local, stream, flush, d_rays, R, steps=30
                       "status": ddf.ddf_check_status(m.h)}
     # the application (Sec. 3.3): shadow and AO images, 512 x 512, 16 AO
     # rays, secondary rays answered by the distilled field vs the exact caster
-    W = H = 512
-    k = 16
     cam = (2.5, 1.8, -3.0, 0.0, 0.0, 0.0, 0.0, 1.0, 0.0, float(np.radians(50.0)))
-    imgs = {}
-    for name, hh_ in (("field", m.h), ("exact", None)):
-        sh_i = torch.empty(W * H, device=dev)
-        ao_i = torch.empty(W * H, device=dev)
-        ddf.ddf_render_gi(hh_, sph, ns, box, nb, cam, W, H, LIGHT, k, 5, sh_i, ao_i, stream)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ddf.ddf_render_gi(hh_, sph, ns, box, nb, cam, W, H, LIGHT, k, 5, sh_i, ao_i, stream)
-        imgs[name] = (time.perf_counter() - t0, sh_i.cpu().numpy(), ao_i.cpu().numpy())
-    fg = imgs["exact"][1] >= 0
-    psnr = lambda a, b, msk: float(10 * np.log10(1.0 / max(np.mean((a[msk] - b[msk]) ** 2), 1e-12)))
-    full = np.ones_like(fg)
-    res["gi"] = {"width": W, "height": H, "ao_rays_per_pixel": k,
-                 "foreground_frac": float(fg.mean()),
-                 "field_render_s": imgs["field"][0], "exact_render_s": imgs["exact"][0],
-                 "secondary_rays": int(W * H * (1 + k)),
-                 "shadow_psnr_foreground_db": psnr(imgs["field"][1], imgs["exact"][1], fg),
-                 "ao_psnr_foreground_db": psnr(imgs["field"][2], imgs["exact"][2], fg),
-                 "shadow_psnr_image_db": psnr(np.where(fg, imgs["field"][1], 1.0),
-                                              np.where(fg, imgs["exact"][1], 1.0), full),
-                 "ao_psnr_image_db": psnr(np.where(fg, imgs["field"][2], 1.0),
-                                          np.where(fg, imgs["exact"][2], 1.0), full),
-                 "paper_context": "shadow 30.3 dB, AO 21.3 dB over 142 scanned objects (Table e4)"}
+    res["gi"] = _gi_compare(ddf, torch, dev, stream, m.h, (sph, ns, box, nb), cam)
     m.close()
+    # the same on one object, as the paper's images are (Sec. 4.6: objects
+    # shadowing themselves, no ground): the table scene without its floor
+    # slab, a field distilled on it with the same recipe
+    tsc, _ = I.table_scene()
+    tsc = I.Scene(tsc.centers, tsc.radii, tsc.box_lo[1:], tsc.box_hi[1:])
+    tb = _scene_buffers(torch, dev, tsc)
+    mt = ddf.DDF(4, 64, 2, precision="bf16", device=local, kind="hashgrid")
+    mt.load(I.hashgrid_blob(n, mlp_dims, seed=0, table_scale=1e-4))
+    ddf.ddf_distill(mt.h, *tb, steps, batch, 3e-3, 0.5, 0.3, seed=1, stream=stream)
+    cam_t = (2.0, 1.2, -2.0, 0.0, -0.2, 0.0, 0.0, 1.0, 0.0, float(np.radians(45.0)))
+    res["gi_one_object"] = {"scene": "table_scene without the floor: table with legs and bars, mug "
+                                     "with handle, ball (12 primitives)",
+                            **_gi_compare(ddf, torch, dev, stream, mt.h, tb, cam_t),
+                            "status": ddf.ddf_check_status(mt.h)}
+    mt.close()
     # gather traffic: 16 levels x 8 corners x one 4-byte bf16 entry pair per
     # ray, plus 24 B of ray and 9 B of outputs; the 26 MB bf16 table stays in L2
     per_ray = 16 * 8 * 4 + 24 + 9
@@ -387,6 +378,38 @@ def hashgrid_workload(torch, ddf, dev, local, stream, flush, d_rays, R, steps=30
     res["achieved_gbs_algorithmic"] = per_ray * res["bf16"]["rays_per_s"] / 1e9
     res["speedup_bf16_vs_fp32"] = res["fp32"]["ms_per_step"] / res["bf16"]["ms_per_step"]
     return res
+
+
+def _gi_compare(ddf, torch, dev, stream, h, scene_bufs, cam, W=512, k=16):
+    """Shadow and AO images with the secondary rays answered by the field h
+    and by the exact caster; PSNR of the field's images over foreground
+    pixels and over the whole image (background pixels set to 1 in both)."""
+    sph, ns, box, nb = scene_bufs
+    imgs = {}
+    for name, hh_ in (("field", h), ("exact", None)):
+        sh_i = torch.empty(W * W, device=dev)
+        ao_i = torch.empty(W * W, device=dev)
+        ddf.ddf_render_gi(hh_, sph, ns, box, nb, cam, W, W, LIGHT, k, 5, sh_i, ao_i, stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ddf.ddf_render_gi(hh_, sph, ns, box, nb, cam, W, W, LIGHT, k, 5, sh_i, ao_i, stream)
+        torch.cuda.synchronize()
+        imgs[name] = (time.perf_counter() - t0, sh_i.cpu().numpy(), ao_i.cpu().numpy())
+    fg = imgs["exact"][1] >= 0
+    psnr = lambda a, b, msk: float(10 * np.log10(1.0 / max(np.mean((a[msk] - b[msk]) ** 2), 1e-12)))
+    full = np.ones_like(fg)
+    return {"width": W, "height": W, "ao_rays_per_pixel": k,
+            "foreground_frac": float(fg.mean()),
+            "field_render_s": imgs["field"][0], "exact_render_s": imgs["exact"][0],
+            "secondary_rays": int(W * W * (1 + k)),
+            "shadowed_frac_exact": float(np.mean(imgs["exact"][1][fg] == 0)),
+            "shadow_psnr_foreground_db": psnr(imgs["field"][1], imgs["exact"][1], fg),
+            "ao_psnr_foreground_db": psnr(imgs["field"][2], imgs["exact"][2], fg),
+            "shadow_psnr_image_db": psnr(np.where(fg, imgs["field"][1], 1.0),
+                                         np.where(fg, imgs["exact"][1], 1.0), full),
+            "ao_psnr_image_db": psnr(np.where(fg, imgs["field"][2], 1.0),
+                                     np.where(fg, imgs["exact"][2], 1.0), full),
+            "paper_context": "shadow 30.3 dB, AO 21.3 dB over 142 scanned objects (Table e4)"}
 
 
 def _dilate(torch, mask, V, W, r):
@@ -581,7 +604,8 @@ def trained_field_accuracy(torch, ddf, dev, local, stream):
     """Flip rate and |dt| of the bf16 and e4m3 paths on weights that the FP64
     oracle distilled by itself (78 -> 128 x 4 -> 2, stored with the oracle's
     exact outputs on seeded uniform rays and its e4m3 scales), against those
-    stored outputs; the frozen bounds beside them."""
+    stored outputs; the frozen bounds beside them, and what the emulated
+    rounding scheme gives on the same rays (stored by the same script)."""
     import base64
     with open(TRAINED_FIELD) as fh:
         doc = json.load(fh)
@@ -611,6 +635,9 @@ def trained_field_accuracy(torch, ddf, dev, local, stream):
                      "flip_rate": float(np.mean((v > 0.5) != (z1_ex > 0))),
                      "near_tie_frac": float(np.mean(np.abs(z1_ex) < 1e-3)),
                      "bounds": {"mean_abs_dt": b[0], "max_abs_dt": b[1], "flip_rate": b[2]},
+                     # the scheme itself on the same rays: the oracle's float64
+                     # emulation of the same roundings, stored by the script
+                     "scheme_oracle_emulation": ev.get("scheme", {}).get(prec),
                      "status": ddf.ddf_check_status(m.h)}
         m.close()
     return out

@@ -301,13 +301,17 @@ ddf_status ddf_load_weights_device(ddf_handle h, const float* dev_blob, size_t n
 
 /* ---- the distillation schedule (Sec. 3.2 / 3.4) ----
  * ddf_sample_rays: n training rays into rays_out (6 device float arrays): a
- * fraction surface_frac anchored on the scene (a primitive chosen uniformly,
- * a point on its surface offset 1e-3 along the normal, a direction uniform
- * on the sphere: the "rays that start on the surface and point in all
- * directions" of Sec. 3.2), the rest camera rays (origin uniform on a face
- * of the box [-1,1]^3, aimed at a point uniform in [-0.9,0.9]^3). Counter-
- * based SplitMix64: (seed, step, i) fixes ray i. Primitive arrays as
- * ddf_cast_scene. Asynchronous.
+ * fraction surface_frac anchored on the scene (a point uniform by area over
+ * the primitives' surfaces, offset 1e-3 along the normal, a direction
+ * uniform on the sphere: the "rays that start on the surface and point in
+ * all directions" of Sec. 3.2), the rest camera rays (origin uniform on a
+ * face of the box [-1,1]^3, aimed at a point uniform in [-0.9,0.9]^3). The
+ * surface element (a sphere or one box face) is drawn with an integer weight
+ * floor(area 2^24), the area a float32 product clamped to [0, 2^16]; a
+ * scene of zero total area gives camera rays only. Counter-based
+ * SplitMix64: (seed, step, i) fixes ray i. Primitive arrays as
+ * ddf_cast_scene, at most 1024 spheres and 1024 boxes (else
+ * DDF_ERR_INVALID_ARG). Asynchronous.
  * ddf_shift_rays: the ray-march shifted points of Sec. 3.2: every ray
  * i in [first, n) with hit[i] moves forward by s = u t[i] (u uniform in
  * [0, 1), from (seed, step, i)) and t[i] becomes t[i] - s. Asynchronous.

@@ -836,25 +836,35 @@ def gi_images(scene, eye, target, up, fov_y, width, height, light, ao_samples, s
 # themselves (a point moved forward by s reports t - s), and Sec. 3.4 decays
 # the learning rate by a cosine to 5 % of its start. The paper fixes neither
 # the ray distributions nor the draws; the readings taken here:
-#   * a fraction surface_frac of the rays is surface-anchored: a primitive
-#     chosen uniformly (not by area), a point uniform on its surface
-#     (sphere: c + r n with n uniform on the sphere; box: a face chosen
-#     uniformly, the two in-face coordinates uniform), the origin 1e-3 off
-#     the surface along the outward normal, the direction uniform on the
-#     sphere; the rest are camera rays: origin uniform on a face of [-1, 1]^3,
-#     aimed at a point uniform in [-0.9, 0.9]^3;
+#   * a fraction surface_frac of the rays is surface-anchored: a point
+#     uniform by area over the primitives' surfaces (a surface element, a
+#     sphere or one face of a box, chosen with probability proportional to
+#     its area, then a point uniform on it: sphere c + r n with n uniform on
+#     the sphere; box face: the two in-face coordinates uniform), the origin
+#     1e-3 off the surface along the outward normal, the direction uniform on
+#     the sphere; points of one primitive that lie inside another are kept;
+#     the rest are camera rays: origin uniform on a face of [-1, 1]^3, aimed
+#     at a point uniform in [-0.9, 0.9]^3;
+#   * the element's area weight is an integer, floor(A 2^24) with A the
+#     float32 product (4 pi r) r or (hi_u - lo_u)(hi_v - lo_v) clamped to
+#     [0, 2^16]; the weights' prefix sums are exact integers, each rounded
+#     once to float32, and the element is the first whose rounded prefix sum
+#     exceeds the float32 product u W (W the rounded total), so that any
+#     summation order gives the same choice;
 #   * the rays from index `first` on that hit move to o + s d with s = u t,
 #     u uniform in [0, 1), and report t - s; misses stay as they are;
 #   * lr_k = lr0 (0.05 + 0.95 (1 + cos(pi k / steps)) / 2), k = 0..steps-1;
 #   * draws: uniform m of ray i at step k is the counter-based SplitMix64
 #     uniform of (seed, a = k, b = i) (the key of gi_uniform), with m = 0 the
-#     surface/camera choice, 1 the primitive or face, 2..6 the positions and
+#     surface/camera choice, 1 the surface element or camera face, 2..6 the positions and
 #     directions (in the order below), 7 the shift, and for batches drawn from
 #     a fixed pool the top 32 bits of mix(key + 8) pick the row;
-#   * where a uniform picks an integer (a primitive, a face), the product u K
-#     is taken in float32, as the GPU takes it, and floored.
+#   * where a uniform picks one of K camera faces, the product u K is taken
+#     in float32, as the GPU takes it, and floored.
 
 DISTILL_SURFACE_OFFSET = 1e-3
+DISTILL_AREA_SCALE = 2.0 ** 24   # area weights are floor(A 2^24)
+DISTILL_AREA_MAX = 2.0 ** 16     # element areas are clamped to [0, 2^16]
 
 
 def distill_uniform(seed, step, i, m):
@@ -867,6 +877,42 @@ def _pick(u, k):
     """floor(u k) with the product rounded to float32, clamped to k - 1."""
     prod = (np.asarray(u, np.float32) * np.float32(k)).astype(F64)
     return np.minimum(np.floor(prod), k - 1).astype(np.int64)
+
+
+def distill_surface_weights(scene):
+    """Integer area weight of every surface element: the spheres in order,
+    then the six faces of each box (face f: axis f // 2, the upper side if f
+    is odd). The area is the float32 product (4 pi r) r for a sphere and
+    (hi_u - lo_u)(hi_v - lo_v) over the face's two in-face axes u, v,
+    clamped to [0, 2^16] (a NaN to 0); the weight is floor(A 2^24)."""
+    r = np.asarray(scene.radii, np.float32).reshape(-1)
+    a_s = (np.float32(4.0 * np.pi) * r) * r
+    lo = np.asarray(scene.box_lo, np.float32).reshape(-1, 3)
+    hi = np.asarray(scene.box_hi, np.float32).reshape(-1, 3)
+    e = hi - lo
+    a_f = np.zeros((lo.shape[0], 6), np.float32)
+    for axis in range(3):
+        u, v = (axis + 1) % 3, (axis + 2) % 3
+        a_f[:, 2 * axis] = a_f[:, 2 * axis + 1] = e[:, u] * e[:, v]
+    a = np.concatenate([a_s, a_f.reshape(-1)]).astype(np.float32)
+    a = np.fmin(np.fmax(a, np.float32(0.0)), np.float32(DISTILL_AREA_MAX))
+    return np.floor(a * np.float32(DISTILL_AREA_SCALE)).astype(np.int64)
+
+
+def distill_pick_surface(scene, u):
+    """The surface element each uniform u picks (readings above): the first
+    element whose exact prefix sum of weights, rounded to float32, exceeds
+    the float32 product u W, W the rounded total; clamped to the last
+    element. Returns (element index array, W > 0)."""
+    w = distill_surface_weights(scene)
+    cum = np.cumsum(w)                         # exact: every sum below 2^53
+    if cum.size == 0 or cum[-1] == 0:
+        return np.zeros(np.shape(u), np.int64), False
+    cum32 = cum.astype(F64).astype(np.float32)  # exact in float64, one rounding
+    total = cum32[-1]
+    x = np.asarray(u, np.float32) * total
+    j = np.searchsorted(cum32, x, side="right")
+    return np.minimum(j, cum.size - 1).astype(np.int64), True
 
 
 def uniform_sphere_dir(a, b):
@@ -883,14 +929,13 @@ def distill_rays(scene, seed, step, n, surface_frac):
     Returns (o, d) [n, 3] float64 and the surface-anchored mask."""
     i = np.arange(n, dtype=np.int64)
     u = [distill_uniform(seed, step, i, m) for m in range(7)]
-    ns, nb = len(scene.radii), len(scene.box_lo)
-    K = ns + nb
-    surf = (u[0] < np.float32(surface_frac)) & (K > 0)
+    ns = len(scene.radii)
+    p, any_area = distill_pick_surface(scene, u[1])
+    surf = (u[0] < np.float32(surface_frac)) & any_area
     o = np.zeros((n, 3))
     d = np.zeros((n, 3))
     # surface-anchored rays
-    if K > 0:
-        p = _pick(u[1], K)
+    if any_area:
         pt = np.zeros((n, 3))
         nrm = np.zeros((n, 3))
         sph = surf & (p < ns)
@@ -900,9 +945,9 @@ def distill_rays(scene, seed, step, n, surface_frac):
             pt[sph] = np.asarray(scene.centers, F64)[js] + np.asarray(scene.radii, F64)[js, None] * nv
             nrm[sph] = nv
         r = np.nonzero(surf & (p >= ns))[0]           # box faces
-        lo = np.asarray(scene.box_lo, F64)[p[r] - ns]
-        hi = np.asarray(scene.box_hi, F64)[p[r] - ns]
-        face = _pick(u[2][r], 6)
+        lo = np.asarray(scene.box_lo, F64)[(p[r] - ns) // 6]
+        hi = np.asarray(scene.box_hi, F64)[(p[r] - ns) // 6]
+        face = (p[r] - ns) % 6
         axis, plus = face // 2, face % 2 == 1
         a, c = (axis + 1) % 3, (axis + 2) % 3
         k = np.arange(r.size)

@@ -10,6 +10,7 @@
 #include <cstdint>
 
 #include "kernels.h"
+#include "caster.cuh"
 #include "rng.cuh"
 
 namespace ddf {
@@ -33,19 +34,83 @@ __device__ __forceinline__ void sphere_dir(float a, float b, float& x, float& y,
 }
 
 constexpr float kSurfaceOffset = 1e-3f;  // origins sit this far off the surface
+constexpr int kMaxSurfaceElems = kMaxPrims + 6 * kMaxPrims;
+constexpr int kSampleThreads = 256;
 
-__global__ void sample_rays_kernel(const float* __restrict__ spheres, int ns,
-                                   const float* __restrict__ boxes, int nb, uint64_t seed,
-                                   uint64_t step, int64_t n, float surface_frac,
-                                   RayOut r) {
+// Integer area weight of surface element e (the spheres, then six faces per
+// box; face f is axis f / 2, the upper side if f is odd): floor(A 2^24),
+// with A the float32 product (4 pi r) r or (hi_u - lo_u)(hi_v - lo_v),
+// clamped to [0, 2^16] (a NaN to 0). Rounded products, no contraction.
+__device__ __forceinline__ uint64_t surface_weight(const float* spheres, int ns,
+                                                   const float* boxes, int e) {
+  float a;
+  if (e < ns) {
+    const float rad = spheres[4 * e + 3];
+    a = __fmul_rn(__fmul_rn(12.566370964050293f, rad), rad);  // 4 pi rounded to float32
+  } else {
+    const float* b = boxes + 6 * ((e - ns) / 6);
+    const int axis = ((e - ns) % 6) >> 1;
+    const int u = (axis + 1) % 3, v = (axis + 2) % 3;
+    a = __fmul_rn(__fsub_rn(b[u + 3], b[u]), __fsub_rn(b[v + 3], b[v]));
+  }
+  a = fminf(fmaxf(a, 0.f), 65536.f);
+  return static_cast<uint64_t>(__fmul_rn(a, 16777216.f));
+}
+
+__global__ void __launch_bounds__(kSampleThreads)
+    sample_rays_kernel(const float* __restrict__ spheres, int ns,
+                       const float* __restrict__ boxes, int nb, uint64_t seed,
+                       uint64_t step, int64_t n, float surface_frac, RayOut r) {
+  // The block's copy of the area distribution: exact integer prefix sums of
+  // the weights (each thread a contiguous run of elements, the runs' totals
+  // scanned in order), each rounded once to float32, so the choice below
+  // does not depend on how the sums were split.
+  __shared__ float s_cum[kMaxSurfaceElems];
+  __shared__ unsigned long long s_run[kSampleThreads];
+  __shared__ unsigned long long s_total;
+  const int E = ns + 6 * nb;
+  const int per = (E + kSampleThreads - 1) / kSampleThreads;
+  const int e0 = static_cast<int>(threadIdx.x) * per, e1 = min(E, e0 + per);
+  unsigned long long run = 0;
+  for (int e = e0; e < e1; ++e) run += surface_weight(spheres, ns, boxes, e);
+  s_run[threadIdx.x] = run;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long acc = 0;
+    for (int t = 0; t < kSampleThreads; ++t) {
+      const unsigned long long v = s_run[t];
+      s_run[t] = acc;
+      acc += v;
+    }
+    s_total = acc;
+  }
+  __syncthreads();
+  run = s_run[threadIdx.x];
+  for (int e = e0; e < e1; ++e) {
+    run += surface_weight(spheres, ns, boxes, e);
+    s_cum[e] = __ull2float_rn(run);
+  }
+  __syncthreads();
+  const float total = __ull2float_rn(s_total);
+
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint64_t key = ray_key(seed, step, i);
   float ox, oy, oz, dx, dy, dz;
-  if (u01(key, 0) < surface_frac && ns + nb > 0) {
-    // a surface point of a primitive chosen uniformly, its normal, and a
-    // direction uniform over the whole sphere
-    const int p = min(static_cast<int>(u01(key, 1) * static_cast<float>(ns + nb)), ns + nb - 1);
+  if (u01(key, 0) < surface_frac && total > 0.f) {
+    // a surface point uniform by area, its normal, and a direction uniform
+    // over the whole sphere; the element: the first whose rounded prefix
+    // sum exceeds u W
+    const float x = __fmul_rn(u01(key, 1), total);
+    int lo = 0, hi = E;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (s_cum[mid] > x)
+        hi = mid;
+      else
+        lo = mid + 1;
+    }
+    const int p = min(lo, E - 1);
     float px, py, pz, nx, ny, nz;
     if (p < ns) {
       const float* s = spheres + 4 * p;
@@ -54,8 +119,8 @@ __global__ void sample_rays_kernel(const float* __restrict__ spheres, int ns,
       py = s[1] + s[3] * ny;
       pz = s[2] + s[3] * nz;
     } else {
-      const float* b = boxes + 6 * (p - ns);
-      const int face = min(static_cast<int>(u01(key, 2) * 6.f), 5);
+      const float* b = boxes + 6 * ((p - ns) / 6);
+      const int face = (p - ns) % 6;
       const int axis = face >> 1;
       const float sg = (face & 1) ? 1.f : -1.f;
       const float a = u01(key, 3), c = u01(key, 4);
@@ -190,8 +255,10 @@ cudaError_t launch_sample_rays(const float* spheres, int ns, const float* boxes,
                                uint64_t seed, uint64_t step, int64_t n, float surface_frac,
                                RayOut r, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  sample_rays_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(
-      spheres, ns, boxes, nb, seed, step, n, surface_frac, r);
+  if (ns < 0 || nb < 0 || ns > kMaxPrims || nb > kMaxPrims) return cudaErrorInvalidValue;
+  sample_rays_kernel<<<static_cast<unsigned>((n + kSampleThreads - 1) / kSampleThreads),
+                       kSampleThreads, 0, s>>>(spheres, ns, boxes, nb, seed, step, n,
+                                               surface_frac, r);
   return cudaGetLastError();
 }
 

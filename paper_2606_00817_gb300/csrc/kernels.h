@@ -346,10 +346,11 @@ cudaError_t launch_quant_e4m3(const float* src, int N, int K, int ldd, uint8_t* 
 cudaError_t launch_scale_vec(const float* v, float a, int n, float* out, cudaStream_t s);
 
 // ---- distillation sampling (distill.cu) ----
-// n rays: a fraction surface_frac anchored on a primitive's surface (1e-3 off
-// it along the normal, direction uniform on the sphere), the rest camera rays
-// from a face of [-1,1]^3 toward a point of [-0.9,0.9]^3. Counter-based:
-// (seed, step, i) fixes ray i.
+// n rays: a fraction surface_frac anchored on the scene's surface (a point
+// uniform by area, 1e-3 off it along the normal, direction uniform on the
+// sphere), the rest camera rays from a face of [-1,1]^3 toward a point of
+// [-0.9,0.9]^3. Counter-based: (seed, step, i) fixes ray i. At most
+// kMaxPrims spheres and kMaxPrims boxes.
 cudaError_t launch_sample_rays(const float* spheres, int ns, const float* boxes, int nb,
                                uint64_t seed, uint64_t step, int64_t n, float surface_frac,
                                RayOut r, cudaStream_t s);

@@ -944,6 +944,8 @@ ddf_status ddf_sample_rays(const float* spheres, int32_t n_spheres, const float*
                            int32_t n_boxes, uint64_t seed, uint64_t step, int64_t n,
                            float surface_frac, float* const rays_out[6], void* stream) {
   if (n_spheres < 0 || n_boxes < 0 || n < 0) return fail(DDF_ERR_INVALID_ARG, "negative count");
+  if (n_spheres > 1024 || n_boxes > 1024)
+    return fail(DDF_ERR_INVALID_ARG, "at most 1024 spheres and 1024 boxes");
   if ((n_spheres > 0 && spheres == nullptr) || (n_boxes > 0 && boxes == nullptr))
     return fail(DDF_ERR_INVALID_ARG, "primitive array is NULL");
   if (!(surface_frac >= 0.f && surface_frac <= 1.f))

@@ -91,12 +91,26 @@ def evaluation(blob):
     return {"rays": f"inputs.uniform_rays({EVAL_RAYS}, seed={EVAL_SEED})",
             "t_exact_f32_le_base64": enc(out["t"]), "z1_exact_f32_le_base64": enc(out["z"][:, 1]),
             "fp8_act_scales": [float(x) for x in scales],
-            "fp8_scales_from": f"calibrate_act_scales on inputs.uniform_rays(4096, seed={EVAL_SEED + 1})"}
+            "fp8_scales_from": f"calibrate_act_scales on inputs.uniform_rays(4096, seed={EVAL_SEED + 1})",
+            "scheme": scheme_accuracy(rays, blob, out, scales)}
+
+
+def scheme_accuracy(rays, blob, exact, scales):
+    """What the reduced-precision schemes themselves give on these rays: the
+    oracle's float64 emulation of the bf16 and e4m3 roundings (the e4m3 one
+    with the stored scales) against the exact outputs."""
+    res = {}
+    for prec, sc in (("bf16", None), ("fp8", scales)):
+        emu = O.ddf_forward(rays.origins(), rays.dirs(), blob, *NET, precision=prec, act_scales=sc)
+        dt = np.abs(emu["t"] - exact["t"])
+        res[prec] = {"mean_abs_dt": float(dt.mean()), "max_abs_dt": float(dt.max()),
+                     "flip_rate": float(np.mean((emu["z"][:, 1] > 0) != (exact["z"][:, 1] > 0)))}
+    return res
 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--steps", type=int, default=1500)
+    ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--eval-only", action="store_true",
                     help="keep the stored weights and only (re)write the evaluation block")
     a = ap.parse_args()

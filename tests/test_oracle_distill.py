@@ -75,6 +75,65 @@ def _surface_gap(scene, p):
     return np.stack(gaps, 1)
 
 
+def _area_counts_match(scene, o):
+    """Counts of surface origins per primitive (the one whose surface the
+    origin is 1e-3 off) against the closed-form area fractions, 4 pi r^2 and
+    2 (ab + bc + ca), within 5 binomial sigma + 3."""
+    near = np.argmin(np.abs(_surface_gap(scene, o) - 1e-3), axis=1)
+    r = np.asarray(scene.radii, np.float64)
+    e = np.asarray(scene.box_hi, np.float64) - np.asarray(scene.box_lo, np.float64)
+    area = np.concatenate([4 * np.pi * r ** 2,
+                           2 * (e[:, 0] * e[:, 1] + e[:, 1] * e[:, 2] + e[:, 2] * e[:, 0])])
+    frac = area / area.sum()
+    cnt = np.bincount(near, minlength=frac.size)
+    want = len(o) * frac
+    return bool(np.all(np.abs(cnt - want) <= 5 * np.sqrt(want * (1 - frac)) + 3))
+
+
+def test_surface_weights_and_pick_by_hand():
+    """A sphere of radius 0.5 and a 1 x 0.5 x 0.25 box: the weights are
+    floor(A 2^24) with float32(4 pi) (1/2) (1/2) = float32(pi) =
+    13176795 / 2^22 for the sphere and 0.125, 0.25, 0.5 for the box's face
+    pairs across x, y and z; a uniform picks the element whose share of the
+    cumulative weight it falls in."""
+    sc = I.Scene(np.array([[0.0, 0.0, 0.0]]), np.array([0.5]), np.array([[2.0, 0.0, 0.0]]),
+                 np.array([[3.0, 0.5, 0.25]]))
+    w = O.distill_surface_weights(sc)
+    assert w.tolist() == [52707180, 2097152, 2097152, 4194304, 4194304, 8388608, 8388608]
+    # cumulative: 52.7M, 54.8M, 56.9M, 61.1M, 65.3M, 73.7M, 82.1M
+    j, ok = O.distill_pick_surface(sc, np.array([0.0, 0.5, 0.65, 0.7, 0.85, 0.99]))
+    assert ok and j.tolist() == [0, 0, 1, 3, 5, 6]
+    # degenerate primitives weigh nothing; no area at all: camera rays only
+    flat = I.Scene(np.zeros((1, 3)), np.array([0.0]), np.array([[0.0, 0.0, 0.0]]),
+                   np.array([[1.0, 1.0, 0.0]]))
+    assert O.distill_surface_weights(flat).tolist() == [0, 0, 0, 0, 0, 16777216, 16777216]
+    none = I.Scene(np.zeros((1, 3)), np.array([0.0]), np.zeros((0, 3)), np.zeros((0, 3)))
+    assert not np.any(O.distill_rays(none, 1, 0, 100, 1.0)[2])
+
+
+def test_thin_box_caps_are_rarely_chosen():
+    """A 0.04 x 0.9 x 0.04 leg: its two end caps hold 2 (0.04^2) / (2 (0.036
+    + 0.0016 + 0.036)) = 2.17 % of its area, so of the surface origins about
+    that fraction sits beyond its y extent."""
+    leg = I.Scene(np.zeros((0, 3)), np.zeros(0), np.array([[0.0, -0.45, 0.0]]),
+                  np.array([[0.04, 0.45, 0.04]]))
+    o, _, surf = O.distill_rays(leg, 3, 0, 40000, 1.0)
+    assert surf.all()
+    cap = np.abs(o[:, 1]) > 0.45
+    p = 2 * 0.04 ** 2 / (2 * (0.036 + 0.0016 + 0.036))
+    assert abs(cap.mean() - p) < 4 * np.sqrt(p * (1 - p) / cap.size)
+
+
+def test_planted_uniform_pick_fails_the_area_check(monkeypatch):
+    """Planted in the oracle: surface elements drawn with equal weights (the
+    element, not its area). The area check catches it."""
+    scene = I.random_scene(32, 32, seed=0)
+    monkeypatch.setattr(O, "distill_surface_weights",
+                        lambda sc: np.ones(len(sc.radii) + 6 * len(sc.box_lo), np.int64))
+    o, _, surf = O.distill_rays(scene, 7, 3, 40000, 0.5)
+    assert not _area_counts_match(scene, o[surf])
+
+
 def test_sampler_invariants():
     scene = I.random_scene(32, 32, seed=0)
     n = 40000
@@ -84,10 +143,8 @@ def test_sampler_invariants():
     # surface rays start 1e-3 off some primitive's surface, outside it
     g = _surface_gap(scene, o[surf][:4000])
     assert np.all(np.abs(g - 1e-3).min(1) < 1e-12)
-    # every primitive is chosen about equally often (1/64 of the surface rays)
-    near = np.argmin(np.abs(_surface_gap(scene, o[surf]) - 1e-3), axis=1)
-    cnt = np.bincount(near, minlength=64)
-    assert cnt.min() > 200 and cnt.max() < 460                  # 312.5 expected
+    # each primitive is chosen in proportion to its surface area
+    assert _area_counts_match(scene, o[surf])
     assert np.abs(d[surf].mean(0)).max() < 0.02                 # directions cover the sphere
     # camera rays start on a face of [-1, 1]^3 and pass through [-0.9, 0.9]^3
     oc, dc = o[~surf], d[~surf]

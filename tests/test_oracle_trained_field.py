@@ -66,3 +66,9 @@ def test_stored_evaluation_is_the_oracles():
     cal = I.uniform_rays(4096, seed=78)
     assert ev["fp8_act_scales"] == O.calibrate_act_scales(cal.origins(), cal.dirs(), blob, *net)
     assert np.mean(np.abs(z1) < 0.1) < 0.05                 # a trained field: few near-ties
+    # the schemes' own accuracy: the emulating oracle against the exact one
+    for prec, sc in (("bf16", None), ("fp8", ev["fp8_act_scales"])):
+        emu = O.ddf_forward(rays.origins(), rays.dirs(), blob, *net, precision=prec, act_scales=sc)
+        want = ev["scheme"][prec]
+        assert np.isclose(want["flip_rate"], np.mean((emu["z"][:, 1] > 0) != (out["z"][:, 1] > 0)))
+        assert np.isclose(want["max_abs_dt"], np.abs(emu["t"] - out["t"]).max(), rtol=1e-12)
