@@ -337,7 +337,8 @@ def test_bf16_pin_catches_planted_mistakes(monkeypatch, mistake):
         monkeypatch.setattr(O, "round_bf16", lambda x: np.asarray(x, float))
         z = O.ddf_forward(o, d, blob, 0, 2, 2, "bf16")["z"][0]
     else:
-        # the last hidden activation rounded before the head (what R11 rules out)
+        # the last hidden activation rounded before the head (the head reads it
+        # in FP32, unrounded)
         layers = O.split_blob(blob, O.ddf_dims(0, 2, 2))
         _, _, acts = O.mlp_forward(O.encode(o, d, 0), layers, "bf16", keep=True)
         wo, bo = layers[-1]
