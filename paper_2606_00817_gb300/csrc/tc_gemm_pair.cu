@@ -75,16 +75,21 @@ struct PairShape {
   static_assert(NUM_BARS * 8 + 16 <= CTRL_BYTES, "control block overflow");
 };
 
-// TRAIN: the training modes (2: input gradients masked by the stored
-// activation; 3: split-K weight gradients with K-major or MN-major operands;
-// 4: the last layer's forward with the head partials), bf16 only; the query
-// instantiations compile none of it.
-template <bool IN_FP8, bool OUT_FP8, bool STAGED, bool TRAIN, int EPI = 4>
+// TM: 0 for the query modes (0, 1), else the one training mode the
+// instantiation serves (2: input gradients masked by the stored activation;
+// 3: split-K weight gradients with K-major or MN-major operands; 4: the last
+// layer's forward with the head partials), bf16 only. Each compiles only its
+// own epilogue and operand paths, so no mode's loop shares registers or
+// schedule with another's (one instantiation for all three ran a plain
+// forward epilogue 20 % slower).
+template <bool IN_FP8, bool OUT_FP8, bool STAGED, int TM, int EPI = 4>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EPI), 1)
     tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                         const __grid_constant__ CUtensorMap tmB,
                         const __grid_constant__ CUtensorMap tmO, const TcGemmParams p) {
   using S = PairShape<IN_FP8, STAGED, EPI>;
+  constexpr bool TRAIN = TM != 0;
+  static_assert(TM == 0 || TM == 2 || TM == 3 || TM == 4, "training mode");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -147,9 +152,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EPI), 1)
   const int num_kb = (p.K + S::BK - 1) / S::BK;
   // split-K (mode 3): tile = (split, m block, n block); split s covers the
   // k-blocks [s num_kb / splits, (s+1) num_kb / splits)
-  const int splits = (TRAIN && p.k_splits > 1) ? p.k_splits : 1;
+  const int splits = (TM == 3 && p.k_splits > 1) ? p.k_splits : 1;
   auto kb_lo = [&](int split) {
-    if constexpr (!TRAIN) return split * num_kb;
+    if constexpr (TM != 3) return split * num_kb;
     return static_cast<int>((static_cast<int64_t>(split) * num_kb) / splits);
   };
   const int num_tiles = splits * num_m * num_n;
@@ -161,7 +166,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EPI), 1)
   };
   // MN-major operands (bf16): A as [K x M], B as [K x N] row-major, loaded as
   // 64-wide boxes of BK rows (8 KB each, two per operand half)
-  const bool mn = TRAIN && !IN_FP8 && p.mn_major != 0;
+  const bool mn = TM == 3 && !IN_FP8 && p.mn_major != 0;
   constexpr uint32_t kBoxBytes = 64 * S::BK * 2;
   auto load_stage = [&](int s, int m0, int nb, int kb, uint32_t bar) {
     if (mn) {
@@ -288,9 +293,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EPI), 1)
       float h0 = 0.f, h1 = 0.f;
       if constexpr (TRAIN) {
         static_assert(kChunks % 4 == 0, "the masked epilogue steps over 4 chunks");
-        if (p.mode == 4)
+        if constexpr (TM == 4)
           epi_row_staged_head(p, ev, tbase, row - lane, n0, c0, c1, stage_w, lane, h0, h1);
-        else if (p.mode == 2)
+        else if constexpr (TM == 2)
           epi_row_masked_staged(p, tbase, row - lane, n0, c0, c1, stage_w, lane);
         else
           epi_row_train(p, tbase, row, row_ok, n0, c0, c1, split);
@@ -343,11 +348,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EPI), 1)
   }
 }
 
-template <bool IN_FP8, bool OUT_FP8, bool STAGED, bool TRAIN = false, int EPI = 4>
+template <bool IN_FP8, bool OUT_FP8, bool STAGED, int TM = 0, int EPI = 4>
 cudaError_t launch_pair_one(const CUtensorMap& tmA, const CUtensorMap& tmB, const CUtensorMap& tmO,
                             const TcGemmParams& p, int grid, cudaStream_t s) {
   using S = PairShape<IN_FP8, STAGED, EPI>;
-  auto kern = tc_gemm_pair_kernel<IN_FP8, OUT_FP8, STAGED, TRAIN, EPI>;
+  auto kern = tc_gemm_pair_kernel<IN_FP8, OUT_FP8, STAGED, TM, EPI>;
   const int smem = S::smem_bytes(p.N);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
@@ -358,7 +363,7 @@ cudaError_t launch_pair_one(const CUtensorMap& tmA, const CUtensorMap& tmB, cons
 template <bool IN_FP8, bool STAGED, int EPI>
 int max_pairs_for() {
   using S = PairShape<IN_FP8, STAGED, EPI>;
-  auto kern = tc_gemm_pair_kernel<IN_FP8, false, STAGED, false, EPI>;
+  auto kern = tc_gemm_pair_kernel<IN_FP8, false, STAGED, 0, EPI>;
   const int smem = S::smem_bytes(kMaxStagedColumns);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
     return 0;
@@ -378,8 +383,8 @@ template <bool IN_FP8, bool STAGED, int EPI>
 cudaError_t launch_pair_io(bool out_fp8, const CUtensorMap& tmA, const CUtensorMap& tmB,
                            const CUtensorMap& tmO, const TcGemmParams& p, int grid,
                            cudaStream_t s) {
-  return out_fp8 ? launch_pair_one<IN_FP8, true, STAGED, false, EPI>(tmA, tmB, tmO, p, grid, s)
-                 : launch_pair_one<IN_FP8, false, STAGED, false, EPI>(tmA, tmB, tmO, p, grid, s);
+  return out_fp8 ? launch_pair_one<IN_FP8, true, STAGED, 0, EPI>(tmA, tmB, tmO, p, grid, s)
+                 : launch_pair_one<IN_FP8, false, STAGED, 0, EPI>(tmA, tmB, tmO, p, grid, s);
 }
 
 template <int EPI>
@@ -421,8 +426,10 @@ cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, bool staged, int epi_
                       p.ldm < p.N || p.ldm % 8 != 0))
     return cudaErrorInvalidValue;  // the activation is read as 16-byte pieces of its rows
   const int grid = 2 * clusters;
-  if (p.mode >= 2)  // training modes
-    return launch_pair_one<false, false, true, true, kTrainEpiWarps>(tmA, tmB, to, p, grid, s);
+  // training modes, one instantiation each
+  if (p.mode == 2) return launch_pair_one<false, false, true, 2, kTrainEpiWarps>(tmA, tmB, to, p, grid, s);
+  if (p.mode == 3) return launch_pair_one<false, false, true, 3, kTrainEpiWarps>(tmA, tmB, to, p, grid, s);
+  if (p.mode == 4) return launch_pair_one<false, false, true, 4, kTrainEpiWarps>(tmA, tmB, to, p, grid, s);
   if (epi_warps == 8) return launch_pair_epi<8>(in_fp8, out_fp8, staged, tmA, tmB, to, p, grid, s);
   if (epi_warps != 4) return cudaErrorInvalidValue;
   return launch_pair_epi<4>(in_fp8, out_fp8, staged, tmA, tmB, to, p, grid, s);
