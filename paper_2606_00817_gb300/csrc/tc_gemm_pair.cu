@@ -75,21 +75,23 @@ struct PairShape {
   static_assert(NUM_BARS * 8 + 16 <= CTRL_BYTES, "control block overflow");
 };
 
-// TM: 0 for the query modes (0, 1), else the one training mode the
-// instantiation serves (2: input gradients masked by the stored activation;
-// 3: split-K weight gradients with K-major or MN-major operands; 4: the last
-// layer's forward with the head partials), bf16 only. Each compiles only its
-// own epilogue and operand paths, so no mode's loop shares registers or
-// schedule with another's (one instantiation for all three ran a plain
-// forward epilogue 20 % slower).
+// TM: the work the instantiation serves. 0: the query modes (0, 1) with
+// thread stores; 1: mode 0 leaving by TMA stores (the staged hidden-layer
+// tile); else one training mode, bf16 only (2: input gradients masked by the
+// stored activation; 3: split-K weight gradients with K-major or MN-major
+// operands; 4: the last layer's forward with the head partials). Each
+// compiles only its own epilogue and operand paths, so no mode's loop shares
+// registers or schedule with another's (one instantiation for all three
+// training modes ran a plain forward epilogue 20 % slower).
 template <bool IN_FP8, bool OUT_FP8, bool STAGED, int TM, int EPI = 4>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EPI), 1)
     tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                         const __grid_constant__ CUtensorMap tmB,
                         const __grid_constant__ CUtensorMap tmO, const TcGemmParams p) {
   using S = PairShape<IN_FP8, STAGED, EPI>;
-  constexpr bool TRAIN = TM != 0;
-  static_assert(TM == 0 || TM == 2 || TM == 3 || TM == 4, "training mode");
+  constexpr bool TRAIN = TM >= 2;
+  static_assert(TM >= 0 && TM <= 4, "instantiation kind");
+  static_assert(TM != 1 || STAGED, "TMA stores leave through the staging boxes");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -299,7 +301,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EPI), 1)
           epi_row_masked_staged(p, tbase, row - lane, n0, c0, c1, stage_w, lane);
         else
           epi_row_train(p, tbase, row, row_ok, n0, c0, c1, split);
-      } else if (STAGED && p.mode == 0 && p.tma_out) {
+      } else if constexpr (TM == 1) {
         epi_tile_tma<OUT_FP8, S::OUT_DEPTH>(p, ev, &tmO, tbase, row - lane, n0, c0, c1, stage_w,
                                             lane, stores);
       } else if (STAGED && p.mode == 0) {
@@ -387,6 +389,17 @@ cudaError_t launch_pair_io(bool out_fp8, const CUtensorMap& tmA, const CUtensorM
                  : launch_pair_one<IN_FP8, false, STAGED, 0, EPI>(tmA, tmB, tmO, p, grid, s);
 }
 
+// The staged mode-0 tile whose outputs leave by TMA stores.
+template <int EPI>
+cudaError_t launch_pair_tma(bool in_fp8, bool out_fp8, const CUtensorMap& tmA,
+                            const CUtensorMap& tmB, const CUtensorMap& tmO,
+                            const TcGemmParams& p, int grid, cudaStream_t s) {
+  if (in_fp8) return out_fp8 ? launch_pair_one<true, true, true, 1, EPI>(tmA, tmB, tmO, p, grid, s)
+                             : launch_pair_one<true, false, true, 1, EPI>(tmA, tmB, tmO, p, grid, s);
+  return out_fp8 ? launch_pair_one<false, true, true, 1, EPI>(tmA, tmB, tmO, p, grid, s)
+                 : launch_pair_one<false, false, true, 1, EPI>(tmA, tmB, tmO, p, grid, s);
+}
+
 template <int EPI>
 cudaError_t launch_pair_epi(bool in_fp8, bool out_fp8, bool staged, const CUtensorMap& tmA,
                             const CUtensorMap& tmB, const CUtensorMap& tmO,
@@ -430,8 +443,11 @@ cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, bool staged, int epi_
   if (p.mode == 2) return launch_pair_one<false, false, true, 2, kTrainEpiWarps>(tmA, tmB, to, p, grid, s);
   if (p.mode == 3) return launch_pair_one<false, false, true, 3, kTrainEpiWarps>(tmA, tmB, to, p, grid, s);
   if (p.mode == 4) return launch_pair_one<false, false, true, 4, kTrainEpiWarps>(tmA, tmB, to, p, grid, s);
+  if (epi_warps != 4 && epi_warps != 8) return cudaErrorInvalidValue;
+  if (p.tma_out)
+    return epi_warps == 8 ? launch_pair_tma<8>(in_fp8, out_fp8, tmA, tmB, to, p, grid, s)
+                          : launch_pair_tma<4>(in_fp8, out_fp8, tmA, tmB, to, p, grid, s);
   if (epi_warps == 8) return launch_pair_epi<8>(in_fp8, out_fp8, staged, tmA, tmB, to, p, grid, s);
-  if (epi_warps != 4) return cudaErrorInvalidValue;
   return launch_pair_epi<4>(in_fp8, out_fp8, staged, tmA, tmB, to, p, grid, s);
 }
 
