@@ -752,6 +752,12 @@ ddf_status ddf_destroy(ddf_handle h) {
   }
   if (h->s_copy) cudaStreamDestroy(h->s_copy);
   if (h->s_comp) cudaStreamDestroy(h->s_comp);
+  for (int b = 0; b < 2; ++b) {
+    if (h->ev_gemm[b]) cudaEventDestroy(h->ev_gemm[b]);
+    if (h->ev_red[b]) cudaEventDestroy(h->ev_red[b]);
+  }
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->s_red) cudaStreamDestroy(h->s_red);
   clear_graphs(h);
   if (h->s_graph) cudaStreamDestroy(h->s_graph);
   delete h;

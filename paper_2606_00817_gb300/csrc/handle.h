@@ -101,7 +101,13 @@ struct ddf_s {
   std::vector<void*> tr_store;            // the activation buffers tr_h points into
   int tr_segment = 1;                     // checkpointing: keep every k-th layer (1: all)
   void* tr_dpre[2] = {nullptr, nullptr};  // [B x W] bf16 pre-activation gradients
-  float* tr_part = nullptr;               // split-K partials of a weight gradient
+  float* tr_part = nullptr;               // split-K partials of a weight gradient, two sets
+  size_t tr_part_set = 0;                 // floats per set of tr_part
+  size_t tr_colpart_set = 0;              // floats per set of tr_colpart
+  cudaStream_t s_red = nullptr;           // the gradient reductions, beside the GEMMs
+  cudaEvent_t ev_gemm[2] = {};            // a weight-gradient GEMM of buffer set b done
+  cudaEvent_t ev_red[2] = {};             // the reduction reading buffer set b done
+  cudaEvent_t ev_join = nullptr;          // every reduction of a backward pass done
   float* tr_cpart = nullptr;              // row-split partials of column sums
   float* tr_hpart = nullptr;              // [512 x (3 W + 4)] partials of the head's backward
   unsigned* tr_ticket = nullptr;          // zeroed counters of the column-sum reductions
@@ -109,7 +115,7 @@ struct ddf_s {
   float2* tr_dz = nullptr;
   unsigned* tr_nhit = nullptr;
   float* tr_lpart = nullptr;              // per-block loss partials
-  float* tr_colpart = nullptr;            // [B / 32 x W] column sums of an input gradient
+  float* tr_colpart = nullptr;            // 2 x [B / 32 x W] column sums of an input gradient
   float2* tr_hz = nullptr;                // [W / 256 x B] head partials of the last layer
   float* grad = nullptr;                  // gradient blob (weight-blob layout)
   float* adam_m = nullptr;

@@ -135,8 +135,10 @@ ddf_status ensure_train(ddf_s* h, int64_t B) {
         return fail(DDF_ERR_CUDA, "cuTensorMapEncodeTiled failed for a weight map");
     }
     const int nmax = std::max(W, 128);
-    if ((s = train_alloc(h, &p, kPartSplits * static_cast<size_t>(W) * nmax * sizeof(float))) != DDF_OK)
-      return s;
+    // two sets: layer l's reduction reads set l & 1 while the GEMMs of the
+    // layer below write the other
+    h->tr_part_set = kPartSplits * static_cast<size_t>(W) * nmax;
+    if ((s = train_alloc(h, &p, 2 * h->tr_part_set * sizeof(float))) != DDF_OK) return s;
     h->tr_part = static_cast<float*>(p);
     if ((s = train_alloc(h, &p, kColSplits * (3 * static_cast<size_t>(W) + 4) * sizeof(float))) !=
         DDF_OK)
@@ -212,9 +214,8 @@ ddf_status ensure_train(ddf_s* h, int64_t B) {
     h->tr_dz = static_cast<float2*>(p);
     if ((s = train_alloc(h, &p, ((B + 255) / 256) * sizeof(float))) != DDF_OK) return s;
     h->tr_lpart = static_cast<float*>(p);
-    if ((s = train_alloc(h, &p, static_cast<size_t>(round_up(B, 256) / 32) * W * sizeof(float))) !=
-        DDF_OK)
-      return s;
+    h->tr_colpart_set = static_cast<size_t>(round_up(B, 256) / 32) * W;  // two sets, as tr_part
+    if ((s = train_alloc(h, &p, 2 * h->tr_colpart_set * sizeof(float))) != DDF_OK) return s;
     h->tr_colpart = static_cast<float*>(p);
     if ((s = train_alloc(h, &p, static_cast<size_t>(train_head_parts(W)) * B * sizeof(float2))) !=
         DDF_OK)
@@ -344,6 +345,23 @@ ddf_status forward_keep(ddf_s* h, const float* const rays[6], int B, cudaStream_
   return DDF_OK;
 }
 
+// The stream the layers' gradient reductions run on and its events, made on
+// first use.
+ddf_status ensure_reduce_stream(ddf_s* h) {
+  if (h->s_red != nullptr) return DDF_OK;
+  for (int b = 0; b < 2; ++b) {
+    if (h->ev_gemm[b] == nullptr)
+      DDF_CK(cudaEventCreateWithFlags(&h->ev_gemm[b], cudaEventDisableTiming));
+    if (h->ev_red[b] == nullptr)
+      DDF_CK(cudaEventCreateWithFlags(&h->ev_red[b], cudaEventDisableTiming));
+  }
+  if (h->ev_join == nullptr) DDF_CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+  DDF_CK(cudaStreamCreateWithFlags(&h->s_red, cudaStreamNonBlocking));
+  return DDF_OK;
+}
+
+ddf_status backward_layers(ddf_s* h, int B, cudaStream_t st, cudaStream_t rs);
+
 // Backward from dL/dz in h->tr_dz through the head and every layer, using the
 // activations forward_keep left; the gradient goes to h->grad.
 ddf_status backward_from_dz(ddf_s* h, int B, cudaStream_t st) {
@@ -383,7 +401,34 @@ ddf_status backward_from_dz(ddf_s* h, int B, cudaStream_t st) {
     DDF_CK(ddf::launch_grad_reduce(g, st));
   }
 
-  // ---- layers, last to first
+  // ---- layers, last to first. Each layer's reduction runs on the side
+  // stream while the main stream goes on with the GEMMs below it; the
+  // caller's stream waits for all of them before it returns, failed or not.
+  ddf_status s = ensure_reduce_stream(h);
+  if (s != DDF_OK) return s;
+  DDF_CK(cudaEventRecord(h->ev_join, st));  // the head's reduction above, in order
+  DDF_CK(cudaStreamWaitEvent(h->s_red, h->ev_join, 0));
+  s = backward_layers(h, B, st, h->s_red);
+  const cudaError_t e1 = cudaEventRecord(h->ev_join, h->s_red);
+  const cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(st, h->ev_join, 0) : e1;
+  if (s != DDF_OK) return s;
+  if (e2 != cudaSuccess) return cuda_fail(e2, "joining the reduction stream");
+  h->grad_valid = true;
+  return DDF_OK;
+}
+
+// The layers of the backward pass. Layer l's weight-gradient partials and
+// its bias column partials live in buffer set l & 1 (tr_part, tr_colpart);
+// its reduction runs on rs after the GEMM that wrote the partials, and a GEMM
+// that is about to overwrite a set waits for the reduction that last read it.
+ddf_status backward_layers(ddf_s* h, int B, cudaStream_t st, cudaStream_t rs) {
+  const int W = h->cfg.width, H = h->cfg.hidden_layers;
+  const BlobOffsets o = blob_offsets(h);
+  auto part_set = [&](int l) { return h->tr_part + static_cast<size_t>(l & 1) * h->tr_part_set; };
+  auto colpart_set = [&](int l) {
+    return h->tr_colpart + static_cast<size_t>(l & 1) * h->tr_colpart_set;
+  };
+  bool pending[2] = {false, false};  // a reduction of set b was issued
   int cur = 0;
   const int num_kb = (B + 63) / 64;
   for (int l = H - 1; l >= 0; --l) {
@@ -437,12 +482,13 @@ ddf_status backward_from_dz(ddf_s* h, int B, cudaStream_t st) {
     p.K = B;
     p.mode = 3;
     p.mn_major = 1;
-    p.out_f32 = h->tr_part;
+    p.out_f32 = part_set(l);
     p.ldo = N;
     p.k_splits = splits;
     p.split_stride = static_cast<size_t>(W) * N;
     p.status = h->status_dev;
     p.timeout_ns = h->timeout_ns;
+    if (pending[l & 1]) DDF_CK(cudaStreamWaitEvent(st, h->ev_red[l & 1], 0));
     {
       ProfScope ps(h, kProfGemm, st);
       const int grid = static_cast<int>(std::min<int64_t>(splits * tiles1, slots));
@@ -460,7 +506,7 @@ ddf_status backward_from_dz(ddf_s* h, int B, cudaStream_t st) {
       ddf::GradReduce g;
       g.nsplit = 1;
       ddf::RedSplit& a = g.split[0];
-      a.part = h->tr_part;
+      a.part = part_set(l);
       a.split_stride = static_cast<int64_t>(W) * N;
       a.S = splits;
       a.rows = W;
@@ -470,7 +516,7 @@ ddf_status backward_from_dz(ddf_s* h, int B, cudaStream_t st) {
       a.out = h->grad + o.w[l];
       if (l < H - 1) {
         ddf::RedCols& c = g.cols;
-        c.X = h->tr_pair ? static_cast<const void*>(h->tr_colpart) : h->tr_dpre[cur];
+        c.X = h->tr_pair ? static_cast<const void*>(colpart_set(l)) : h->tr_dpre[cur];
         c.x_bf16 = h->tr_pair ? 0 : 1;
         c.M = h->tr_pair ? static_cast<int>(round_up(B, 256) / 32) : B;
         c.N = W;
@@ -483,9 +529,16 @@ ddf_status backward_from_dz(ddf_s* h, int B, cudaStream_t st) {
         c.cnt[0] = W;
         c.out[0] = h->grad + o.b[l];
       }
-      DDF_CK(ddf::launch_grad_reduce(g, st));
+      DDF_CK(cudaEventRecord(h->ev_gemm[l & 1], st));
+      DDF_CK(cudaStreamWaitEvent(rs, h->ev_gemm[l & 1], 0));
+      DDF_CK(ddf::launch_grad_reduce(g, rs));
+      DDF_CK(cudaEventRecord(h->ev_red[l & 1], rs));
+      pending[l & 1] = true;
     }
     if (l == 0) break;
+    // the input gradient writes set (l - 1) & 1 and dpre[cur ^ 1], which the
+    // reduction of layer l + 1 read
+    if (pending[(l + 1) & 1]) DDF_CK(cudaStreamWaitEvent(st, h->ev_red[(l + 1) & 1], 0));
     // dpre_{l-1} [B x W] = (dpre_l [B x W]) (W_l^T [W x W])^T masked by h_{l-1} > 0
     ddf::TcGemmParams q{};
     q.N = W;
@@ -494,7 +547,7 @@ ddf_status backward_from_dz(ddf_s* h, int B, cudaStream_t st) {
     q.ldo = W;
     q.mask = h->tr_h[l - 1];
     q.ldm = W;
-    if (h->tr_pair) q.col_part = h->tr_colpart;
+    if (h->tr_pair) q.col_part = colpart_set(l - 1);
     {
       ProfScope ps(h, kProfGemm, st);
       ddf_status s = h->tr_pair ? tc_gemm_pair(h, h->tr_dpre[cur], B, W, h->tmWTpair[l], false, q, st)
@@ -503,7 +556,6 @@ ddf_status backward_from_dz(ddf_s* h, int B, cudaStream_t st) {
     }
     cur ^= 1;
   }
-  h->grad_valid = true;
   return DDF_OK;
 }
 
