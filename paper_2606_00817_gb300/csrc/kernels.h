@@ -320,6 +320,7 @@ struct AdamBlock {
   __nv_bfloat16* wt;
   float* f32;
   int cta0 = 0;  // first CTA of the block (set by the launcher)
+  int vec = 0;   // set by the launcher: a weight block updated 4 columns at a time
 };
 struct AdamBlocks {
   int n;

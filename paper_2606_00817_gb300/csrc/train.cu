@@ -455,21 +455,61 @@ __global__ void __launch_bounds__(256) adam_refresh_kernel(float* __restrict__ w
   }
   const int ntc = (bk.cols + kAdamTileC - 1) / kAdamTileC;
   const int r0 = (u / ntc) * kAdamTileR, c0 = (u % ntc) * kAdamTileC;
-  const int cl = threadIdx.x & (kAdamTileC - 1);
-  const int c = c0 + cl;
+  if (bk.vec) {
+    // four adjacent columns per thread: one float4 of each array and one
+    // 8-byte piece of the bf16 rows (the launcher checked the alignment)
+    const int cq = static_cast<int>(threadIdx.x) & (kAdamTileC / 4 - 1);
+    const int c = c0 + 4 * cq;
 #pragma unroll
-  for (int k = 0; k < kAdamTileR / 4; ++k) {
-    const int rl = static_cast<int>(threadIdx.x >> 6) + 4 * k;
-    const int r = r0 + rl;
-    __nv_bfloat16 hb = __float2bfloat16_rn(0.f);
-    if (r < bk.rows && c < bk.cols) {
-      const int64_t e = static_cast<int64_t>(r) * bk.cols + c;
-      const float wi = adam_one(w, g, m, v, bk.start + e, lr, b1, b2, eps, bc1, bc2);
-      hb = __float2bfloat16_rn(wi);
-      if (bk.f32 != nullptr) bk.f32[e] = wi;
-      if (bk.wb != nullptr) bk.wb[static_cast<int64_t>(r) * bk.ldb + c] = hb;
+    for (int k = 0; k < kAdamTileR * kAdamTileC / 4 / 256; ++k) {
+      const int rl = static_cast<int>(threadIdx.x) / (kAdamTileC / 4) + (256 / (kAdamTileC / 4)) * k;
+      const int r = r0 + rl;
+      float4 W = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < bk.rows && c < bk.cols) {  // cols % 4 == 0: all four columns
+        const int64_t e = static_cast<int64_t>(r) * bk.cols + c;
+        const int64_t i = bk.start + e;
+        W = *reinterpret_cast<const float4*>(w + i);
+        const float4 G = *reinterpret_cast<const float4*>(g + i);
+        float4 M = *reinterpret_cast<const float4*>(m + i);
+        float4 V = *reinterpret_cast<const float4*>(v + i);
+        W.x = adam_elem(W.x, G.x, M.x, V.x, lr, b1, b2, eps, bc1, bc2);
+        W.y = adam_elem(W.y, G.y, M.y, V.y, lr, b1, b2, eps, bc1, bc2);
+        W.z = adam_elem(W.z, G.z, M.z, V.z, lr, b1, b2, eps, bc1, bc2);
+        W.w = adam_elem(W.w, G.w, M.w, V.w, lr, b1, b2, eps, bc1, bc2);
+        *reinterpret_cast<float4*>(w + i) = W;
+        *reinterpret_cast<float4*>(m + i) = M;
+        *reinterpret_cast<float4*>(v + i) = V;
+        if (bk.f32 != nullptr) *reinterpret_cast<float4*>(bk.f32 + e) = W;
+        if (bk.wb != nullptr) {
+          const __nv_bfloat162 lo = __floats2bfloat162_rn(W.x, W.y), hi = __floats2bfloat162_rn(W.z, W.w);
+          uint2 pk;
+          pk.x = *reinterpret_cast<const uint32_t*>(&lo);
+          pk.y = *reinterpret_cast<const uint32_t*>(&hi);
+          *reinterpret_cast<uint2*>(bk.wb + static_cast<int64_t>(r) * bk.ldb + c) = pk;
+        }
+      }
+      tile[4 * cq + 0][rl] = __float2bfloat16_rn(W.x);
+      tile[4 * cq + 1][rl] = __float2bfloat16_rn(W.y);
+      tile[4 * cq + 2][rl] = __float2bfloat16_rn(W.z);
+      tile[4 * cq + 3][rl] = __float2bfloat16_rn(W.w);
     }
-    tile[cl][rl] = hb;
+  } else {
+    const int cl = threadIdx.x & (kAdamTileC - 1);
+    const int c = c0 + cl;
+#pragma unroll
+    for (int k = 0; k < kAdamTileR / 4; ++k) {
+      const int rl = static_cast<int>(threadIdx.x >> 6) + 4 * k;
+      const int r = r0 + rl;
+      __nv_bfloat16 hb = __float2bfloat16_rn(0.f);
+      if (r < bk.rows && c < bk.cols) {
+        const int64_t e = static_cast<int64_t>(r) * bk.cols + c;
+        const float wi = adam_one(w, g, m, v, bk.start + e, lr, b1, b2, eps, bc1, bc2);
+        hb = __float2bfloat16_rn(wi);
+        if (bk.f32 != nullptr) bk.f32[e] = wi;
+        if (bk.wb != nullptr) bk.wb[static_cast<int64_t>(r) * bk.ldb + c] = hb;
+      }
+      tile[cl][rl] = hb;
+    }
   }
   __syncthreads();
   // transposed copy wt [cols x rows]: thread -> column c0 + t / 4, rows
@@ -612,6 +652,10 @@ cudaError_t launch_adam_refresh(float* w, const float* g, float* m, float* v, in
     AdamBlock& bk = blocks.b[j];
     if (bk.start != next || bk.rows < 1 || bk.cols < 1) return cudaErrorInvalidValue;
     if (bk.wt != nullptr && (reinterpret_cast<uintptr_t>(bk.wt) & 15u) != 0) return cudaErrorInvalidValue;
+    auto al = [](const void* q, uintptr_t a) { return (reinterpret_cast<uintptr_t>(q) & (a - 1)) == 0; };
+    bk.vec = bk.wt != nullptr && bk.cols % 4 == 0 && bk.start % 4 == 0 && al(w, 16) && al(g, 16) &&
+             al(m, 16) && al(v, 16) && (bk.f32 == nullptr || al(bk.f32, 16)) &&
+             (bk.wb == nullptr || (al(bk.wb, 8) && bk.ldb % 4 == 0));
     const int64_t count = static_cast<int64_t>(bk.rows) * bk.cols;
     next += count;
     bk.cta0 = static_cast<int>(ctas);
