@@ -163,30 +163,56 @@ __global__ void head_back_fused_kernel(const float2* __restrict__ dz, const __nv
     w1[j] = wo[W + c + j];
     g0[j] = g1[j] = cs[j] = 0.f;
   }
-#pragma unroll 8
-  for (int r = r0; r < r1; ++r) {
-    const float2 d = dz[r];
-    zs0 += d.x;
-    zs1 += d.y;
-    const uint4 hv = *reinterpret_cast<const uint4*>(H + static_cast<int64_t>(r) * W + c);
-    const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
-    uint32_t ow[4];
+  // rows in batches of kHeadRows, the next batch's loads in flight while a
+  // batch is computed; rows are taken in order, so the sums are the same
+  // bits as a plain loop over the rows
+  constexpr int kHeadRows = 4;
+  uint4 h0q[kHeadRows], h1q[kHeadRows];
+  float2 d0q[kHeadRows], d1q[kHeadRows];
+  auto load = [&](int rb, uint4 (&hq)[kHeadRows], float2 (&dq)[kHeadRows]) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float h0 = __uint_as_float(hw[q] << 16), h1 = __uint_as_float(hw[q] & 0xFFFF0000u);
-      const int j = 2 * q;
-      const float x0 = h0 > 0.f ? d.x * w0[j] + d.y * w1[j] : 0.f;
-      const float x1 = h1 > 0.f ? d.x * w0[j + 1] + d.y * w1[j + 1] : 0.f;
-      const __nv_bfloat162 o = __floats2bfloat162_rn(x0, x1);
-      ow[q] = *reinterpret_cast<const uint32_t*>(&o);
-      cs[j] += __low2float(o);
-      cs[j + 1] += __high2float(o);
-      g0[j] = fmaf(d.x, h0, g0[j]);
-      g1[j] = fmaf(d.y, h0, g1[j]);
-      g0[j + 1] = fmaf(d.x, h1, g0[j + 1]);
-      g1[j + 1] = fmaf(d.y, h1, g1[j + 1]);
+    for (int q = 0; q < kHeadRows; ++q) {
+      const int r = rb + q;
+      hq[q] = r < r1 ? __ldg(reinterpret_cast<const uint4*>(H + static_cast<int64_t>(r) * W + c))
+                     : make_uint4(0u, 0u, 0u, 0u);
+      dq[q] = r < r1 ? dz[r] : make_float2(0.f, 0.f);
     }
-    *reinterpret_cast<uint4*>(dpre + static_cast<int64_t>(r) * W + c) = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+  };
+  auto rows = [&](int rb, const uint4 (&hq)[kHeadRows], const float2 (&dq)[kHeadRows]) {
+#pragma unroll
+    for (int k = 0; k < kHeadRows; ++k) {
+      const int r = rb + k;
+      if (r >= r1) break;
+      const float2 d = dq[k];
+      zs0 += d.x;
+      zs1 += d.y;
+      const uint4 hv = hq[k];
+      const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+      uint32_t ow[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float h0 = __uint_as_float(hw[q] << 16), h1 = __uint_as_float(hw[q] & 0xFFFF0000u);
+        const int j = 2 * q;
+        const float x0 = h0 > 0.f ? d.x * w0[j] + d.y * w1[j] : 0.f;
+        const float x1 = h1 > 0.f ? d.x * w0[j + 1] + d.y * w1[j + 1] : 0.f;
+        const __nv_bfloat162 o = __floats2bfloat162_rn(x0, x1);
+        ow[q] = *reinterpret_cast<const uint32_t*>(&o);
+        cs[j] += __low2float(o);
+        cs[j + 1] += __high2float(o);
+        g0[j] = fmaf(d.x, h0, g0[j]);
+        g1[j] = fmaf(d.y, h0, g1[j]);
+        g0[j + 1] = fmaf(d.x, h1, g0[j + 1]);
+        g1[j + 1] = fmaf(d.y, h1, g1[j + 1]);
+      }
+      *reinterpret_cast<uint4*>(dpre + static_cast<int64_t>(r) * W + c) = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+    }
+  };
+  load(r0, h0q, d0q);
+  for (int rb = r0; rb < r1; rb += 2 * kHeadRows) {
+    if (rb + kHeadRows < r1) load(rb + kHeadRows, h1q, d1q);
+    rows(rb, h0q, d0q);
+    if (rb + 2 * kHeadRows < r1) load(rb + 2 * kHeadRows, h0q, d0q);
+    rows(rb + kHeadRows, h1q, d1q);
   }
   float* ps = part + static_cast<size_t>(s) * (3 * W + 4) + c;
 #pragma unroll
