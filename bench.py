@@ -70,8 +70,8 @@ WORKLOAD = ("shadow rays: 4,194,304 rays from a 64-sphere analytic scene toward 
 # (sm__pipe_tensor_cycles_active, percent of peak over the elapsed cycles, two
 # launches of a 262,144-row hidden layer); the figures are copied from the
 # summary named here, and a host test checks that they still appear in it.
-TENSOR_PIPE = {"kernel": "tc_gemm_pair_kernel<bf16, bf16, staged>",
-               "active_pct_of_peak": [81.8, 82.3],
+TENSOR_PIPE = {"kernel": "tc_gemm_pair_kernel<bf16, bf16, staged, TMA-store tile>",
+               "active_pct_of_peak": [80.9, 81.4],
                "source": "profiles/tc_gemm_pair_bf16_shadow_4M.md",
                "metric": "sm__pipe_tensor_cycles_active (pct of peak, elapsed)"}
 
@@ -942,14 +942,15 @@ def main():
     if peak is None:
         peak, peak_src = 1700.0, "fallback (1.7 PFLOP/s sustained)"
     achieved = gemm_flops_step * args.steps / (g_ms / 1e3) / 1e12 if g_ms > 0 else None
-    # DRAM bytes per activation row of the CTA-pair staged bf16 kernel, from
-    # one ncu capture of a 262,144-row 1280x1280 launch (674.7 MB read +
-    # 631.9 MB written, the summary kept under profiles/); traffic grows with
-    # the rows, so a launch of R rows moves about R times this.
+    # DRAM bytes per activation row of the CTA-pair staged bf16 kernel (its
+    # TMA-store instantiation), from one ncu capture of two 262,144-row
+    # 1280x1280 launches (674.4 MB read + 631.7 / 629.2 MB written, mean
+    # 1304.9 MB; the summary kept under profiles/); traffic grows with the
+    # rows, so a launch of R rows moves about R times this.
     traffic = None
     rows_per_launch = gemm_flops_step * args.steps / g_n / (2.0 * W_ * W_) if g_n else 0
     if tile["hidden"] == "256x4pairstaged" and args.precision == "bf16":
-        traffic = rows_per_launch * (1306.6e6 / 262144)
+        traffic = rows_per_launch * (1304.9e6 / 262144)
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "traffic_unit": "DRAM bytes per launch (ncu dram__bytes_read+write, scaled "
