@@ -301,3 +301,47 @@ def test_distill_pool_draws_the_oracle_rows(torch_cuda):
     torch.cuda.synchronize()
     assert np.array_equal(ddf.ddf_get_weights(b.h, blob.size), wa)
     b.close()
+
+
+def test_sampler_area_edge_cases(torch_cuda):
+    """A scene whose surfaces have no area gives camera rays only, as the
+    oracle's sampler does (ray by ray), and a scene past the 1,024-sphere or
+    1,024-box limit is refused as an argument error; a thin box's end caps
+    get the share of its surface rays their area gives (2.17 %)."""
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    flat = I.Scene(np.zeros((1, 3)), np.array([0.0]), np.array([[0.0, 0.0, 0.0]]),
+                   np.array([[0.5, 0.5, 0.0]]))
+    sph = torch.tensor([0.0, 0.0, 0.0, 0.0], device="cuda")
+    box = torch.tensor([0.0, 0.0, 0.0, 0.5, 0.5, 0.0], device="cuda")
+    n = 4096
+    out = [torch.empty(n, device="cuda") for _ in range(6)]
+    # the flat box has area on its two z faces: surface rays are drawn there
+    ddf.ddf_sample_rays(sph, 1, box, 1, 3, 0, n, 1.0, out)
+    torch.cuda.synchronize()
+    o, d, surf = O.distill_rays(flat, 3, 0, n, 1.0)
+    g = np.stack([a.double().cpu().numpy() for a in out[:3]], 1)
+    assert surf.all() and np.allclose(g, o, atol=2e-6)
+    assert np.allclose(np.abs(g[:, 2]), 1e-3, atol=1e-6)      # 1e-3 off the z faces
+    # no area at all: camera rays only
+    zero = torch.tensor([0.0, 0.0, 0.0, 0.0, 0.0, 0.0], device="cuda")
+    ddf.ddf_sample_rays(sph, 1, zero, 1, 3, 0, n, 1.0, out)
+    torch.cuda.synchronize()
+    none = I.Scene(np.zeros((1, 3)), np.array([0.0]), np.zeros((1, 3)), np.zeros((1, 3)))
+    o, d, surf = O.distill_rays(none, 3, 0, n, 1.0)
+    g = np.stack([a.double().cpu().numpy() for a in out[:3]], 1)
+    assert not surf.any() and np.allclose(g, o, atol=2e-6)
+    assert np.all(np.abs(g).max(axis=1) == 1.0)                # on a face of the box
+    # thin box: caps by area
+    leg = torch.tensor([0.0, -0.45, 0.0, 0.04, 0.45, 0.04], device="cuda")
+    n2 = 40000
+    out2 = [torch.empty(n2, device="cuda") for _ in range(6)]
+    ddf.ddf_sample_rays(sph, 0, leg, 1, 3, 0, n2, 1.0, out2)
+    torch.cuda.synchronize()
+    cap = np.abs(out2[1].double().cpu().numpy()) > 0.45
+    p = 2 * 0.04 ** 2 / (2 * (0.036 + 0.0016 + 0.036))
+    assert abs(cap.mean() - p) < 4 * np.sqrt(p * (1 - p) / n2)
+    with pytest.raises(ddf.DDFError) as e:
+        big = torch.zeros(4 * 1025, device="cuda")
+        ddf.ddf_sample_rays(big, 1025, box, 1, 3, 0, n, 1.0, out)
+    assert e.value.status == 1
