@@ -66,14 +66,20 @@ WORKLOAD = ("shadow rays: 4,194,304 rays from a 64-sphere analytic scene toward 
             "at (3,3,3); DDF 126 -> 1280x8 -> 2 (L=10, ~11.6M params, Xavier)")
 
 
-# Tensor-pipe activity of the dominant kernel from its last ncu capture
-# (sm__pipe_tensor_cycles_active, percent of peak over the elapsed cycles, two
-# launches of a 262,144-row hidden layer); the figures are copied from the
-# summary named here, and a host test checks that they still appear in it.
-TENSOR_PIPE = {"kernel": "tc_gemm_pair_kernel<bf16, bf16, staged, TMA-store tile>",
-               "active_pct_of_peak": [80.9, 81.4],
-               "source": "profiles/tc_gemm_pair_bf16_shadow_4M.md",
-               "metric": "sm__pipe_tensor_cycles_active (pct of peak, elapsed)"}
+# Tensor-pipe activity and DRAM traffic of the dominant kernel, per hidden
+# tile the autotuner may pick, from its last ncu capture (two launches of a
+# 262,144-row 1280x1280 hidden layer: sm__pipe_tensor_cycles_active, percent
+# of peak over the elapsed cycles; dram__bytes_read.sum + dram__bytes_write.sum,
+# mean of the launches); the figures are copied from the summary named here,
+# and a host test checks that they still appear in it.
+PROFILED_TILES = {
+    "256x4pairstaged": {"kernel": "tc_gemm_pair_kernel<bf16, bf16, staged, TMA-store tile, 4 epilogue warps>",
+                        "active_pct_of_peak": [80.9, 81.4], "traffic_per_262144_rows": 1304.9e6},
+    "256x8pairstaged": {"kernel": "tc_gemm_pair_kernel<bf16, bf16, staged, TMA-store tile, 8 epilogue warps>",
+                        "active_pct_of_peak": [80.9, 81.2], "traffic_per_262144_rows": 1304.6e6},
+}
+PROFILE_SOURCE = "profiles/tc_gemm_pair_bf16_shadow_4M.md"
+PROFILE_METRIC = "sm__pipe_tensor_cycles_active (pct of peak, elapsed)"
 
 
 def parse():
@@ -942,15 +948,14 @@ def main():
     if peak is None:
         peak, peak_src = 1700.0, "fallback (1.7 PFLOP/s sustained)"
     achieved = gemm_flops_step * args.steps / (g_ms / 1e3) / 1e12 if g_ms > 0 else None
-    # DRAM bytes per activation row of the CTA-pair staged bf16 kernel (its
-    # TMA-store instantiation), from one ncu capture of two 262,144-row
-    # 1280x1280 launches (674.4 MB read + 631.7 / 629.2 MB written, mean
-    # 1304.9 MB; the summary kept under profiles/); traffic grows with the
-    # rows, so a launch of R rows moves about R times this.
+    # DRAM bytes per activation row of the hidden tile that ran, from its
+    # ncu capture (PROFILED_TILES); traffic grows with the rows, so a launch
+    # of R rows moves about R / 262,144 times the captured bytes.
     traffic = None
     rows_per_launch = gemm_flops_step * args.steps / g_n / (2.0 * W_ * W_) if g_n else 0
-    if tile["hidden"] == "256x4pairstaged" and args.precision == "bf16":
-        traffic = rows_per_launch * (1304.9e6 / 262144)
+    prof = PROFILED_TILES.get(tile["hidden"]) if args.precision == "bf16" else None
+    if prof is not None:
+        traffic = rows_per_launch * (prof["traffic_per_262144_rows"] / 262144)
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "traffic_unit": "DRAM bytes per launch (ncu dram__bytes_read+write, scaled "
@@ -962,7 +967,9 @@ def main():
                 "kernel_time_share": g_ms / sum(v[0] for v in prof.values()),
                 "first_layer": {"achieved_tflops": first_flops_step * args.steps / (f_ms / 1e3) / 1e12
                                 if f_ms > 0 else None, "ms_per_step": f_ms / args.steps},
-                "tensor_pipe": TENSOR_PIPE}
+                "tensor_pipe": ({"kernel": prof["kernel"], "active_pct_of_peak": prof["active_pct_of_peak"],
+                                 "source": PROFILE_SOURCE, "metric": PROFILE_METRIC}
+                                if prof is not None else None)}
     launches = int(sum(v[1] for v in prof.values()))
 
     # end to end through the host-buffer entry point (pinned host memory)

@@ -94,8 +94,10 @@ def test_tensor_pipe_figures_come_from_the_cited_profile():
     committed ncu summary; each figure must still appear in it."""
     import os
     path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
-                        bench.TENSOR_PIPE["source"])
+                        bench.PROFILE_SOURCE)
     text = open(path).read()
     assert "sm__pipe_tensor_cycles_active" in text
-    for v in bench.TENSOR_PIPE["active_pct_of_peak"]:
-        assert f"{v} %" in text, v
+    for tile in bench.PROFILED_TILES.values():
+        for v in tile["active_pct_of_peak"]:
+            assert f"{v} %" in text, v
+        assert f"{tile['traffic_per_262144_rows'] / 1e6:.1f} MB" in text
