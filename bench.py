@@ -953,9 +953,9 @@ def main():
     # of R rows moves about R / 262,144 times the captured bytes.
     traffic = None
     rows_per_launch = gemm_flops_step * args.steps / g_n / (2.0 * W_ * W_) if g_n else 0
-    prof = PROFILED_TILES.get(tile["hidden"]) if args.precision == "bf16" else None
-    if prof is not None:
-        traffic = rows_per_launch * (prof["traffic_per_262144_rows"] / 262144)
+    tile_prof = PROFILED_TILES.get(tile["hidden"]) if args.precision == "bf16" else None
+    if tile_prof is not None:
+        traffic = rows_per_launch * (tile_prof["traffic_per_262144_rows"] / 262144)
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "traffic_unit": "DRAM bytes per launch (ncu dram__bytes_read+write, scaled "
@@ -967,9 +967,10 @@ def main():
                 "kernel_time_share": g_ms / sum(v[0] for v in prof.values()),
                 "first_layer": {"achieved_tflops": first_flops_step * args.steps / (f_ms / 1e3) / 1e12
                                 if f_ms > 0 else None, "ms_per_step": f_ms / args.steps},
-                "tensor_pipe": ({"kernel": prof["kernel"], "active_pct_of_peak": prof["active_pct_of_peak"],
+                "tensor_pipe": ({"kernel": tile_prof["kernel"],
+                                 "active_pct_of_peak": tile_prof["active_pct_of_peak"],
                                  "source": PROFILE_SOURCE, "metric": PROFILE_METRIC}
-                                if prof is not None else None)}
+                                if tile_prof is not None else None)}
     launches = int(sum(v[1] for v in prof.values()))
 
     # end to end through the host-buffer entry point (pinned host memory)
