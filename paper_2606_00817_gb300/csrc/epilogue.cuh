@@ -124,13 +124,14 @@ __device__ __forceinline__ void epi_affine32(const EpiVectors& ev, const uint32_
 }
 
 // Processes the 32 accumulator values v of columns [nc, nc + 32) of `row`.
-template <bool OUT_FP8>
+// HEAD_ONLY: mode 1 known at compile time (no stores are compiled).
+template <bool OUT_FP8, bool HEAD_ONLY = false>
 __device__ __forceinline__ void epi_chunk(const TcGemmParams& p, const EpiVectors& ev,
                                           const uint32_t (&v)[32], int row, bool row_ok, int nc,
                                           float& h0, float& h1) {
   float x[32];  // before the ReLU, which the packing conversions (or the head) apply
   epi_affine32(ev, v, nc, x);
-  if (p.mode == 0) {
+  if (!HEAD_ONLY && p.mode == 0) {
     if (p.amax != nullptr) {  // calibration: the warp's largest output of valid rows
       float m = 0.f;          // max(0, max x) = the largest output after the ReLU
       if (row_ok) {
@@ -183,7 +184,7 @@ __device__ __forceinline__ void epi_chunk(const TcGemmParams& p, const EpiVector
 
 // Drains chunks [c_begin, c_end) of this thread's TMEM row (tbase = lane
 // quarter + accumulator column base), columns n0 + 32 c.
-template <bool OUT_FP8>
+template <bool OUT_FP8, bool HEAD_ONLY = false>
 __device__ __forceinline__ void epi_row(const TcGemmParams& p, const EpiVectors& ev,
                                         uint32_t tbase, int row, bool row_ok, int n0, int c_begin,
                                         int c_end, float& h0, float& h1) {
@@ -194,12 +195,12 @@ __device__ __forceinline__ void epi_row(const TcGemmParams& p, const EpiVectors&
   for (int c = c_begin; c < c_end; c += 2) {
     const bool next = c + 1 < c_end;
     if (next) tmem_ld32(tbase + 32u * (c + 1), vb);  // in flight during chunk c
-    epi_chunk<OUT_FP8>(p, ev, va, row, row_ok, n0 + 32 * c, h0, h1);
+    epi_chunk<OUT_FP8, HEAD_ONLY>(p, ev, va, row, row_ok, n0 + 32 * c, h0, h1);
     if (!next) break;
     tmem_wait_ld_regs(vb);
     const bool next2 = c + 2 < c_end;
     if (next2) tmem_ld32(tbase + 32u * (c + 2), va);  // in flight during chunk c+1
-    epi_chunk<OUT_FP8>(p, ev, vb, row, row_ok, n0 + 32 * (c + 1), h0, h1);
+    epi_chunk<OUT_FP8, HEAD_ONLY>(p, ev, vb, row, row_ok, n0 + 32 * (c + 1), h0, h1);
     if (next2) tmem_wait_ld_regs(va);
   }
 }

@@ -77,7 +77,8 @@ struct PairShape {
 
 // TM: the work the instantiation serves. 0: the query modes (0, 1) with
 // thread stores; 1: mode 0 leaving by TMA stores (the staged hidden-layer
-// tile); else one training mode, bf16 only (2: input gradients masked by the
+// tile); 5: mode 1 alone (the last layer's head partials, nothing stored);
+// else one training mode, bf16 only (2: input gradients masked by the
 // stored activation; 3: split-K weight gradients with K-major or MN-major
 // operands; 4: the last layer's forward with the head partials). Each
 // compiles only its own epilogue and operand paths, so no mode's loop shares
@@ -89,8 +90,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EPI), 1)
                         const __grid_constant__ CUtensorMap tmB,
                         const __grid_constant__ CUtensorMap tmO, const TcGemmParams p) {
   using S = PairShape<IN_FP8, STAGED, EPI>;
-  constexpr bool TRAIN = TM >= 2;
-  static_assert(TM >= 0 && TM <= 4, "instantiation kind");
+  constexpr bool TRAIN = TM >= 2 && TM <= 4;
+  static_assert(TM >= 0 && TM <= 5, "instantiation kind");
   static_assert(TM != 1 || STAGED, "TMA stores leave through the staging boxes");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -304,6 +305,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EPI), 1)
       } else if constexpr (TM == 1) {
         epi_tile_tma<OUT_FP8, S::OUT_DEPTH>(p, ev, &tmO, tbase, row - lane, n0, c0, c1, stage_w,
                                             lane, stores);
+      } else if constexpr (TM == 5) {
+        epi_row<OUT_FP8, true>(p, ev, tbase, row, row_ok, n0, c0, c1, h0, h1);
       } else if (STAGED && p.mode == 0) {
         epi_row_staged<OUT_FP8>(p, ev, tbase, row - lane, n0, c0, c1, stage_w, lane);
       } else {
@@ -389,6 +392,16 @@ cudaError_t launch_pair_io(bool out_fp8, const CUtensorMap& tmA, const CUtensorM
                  : launch_pair_one<IN_FP8, false, STAGED, 0, EPI>(tmA, tmB, tmO, p, grid, s);
 }
 
+// The last layer (mode 1: head partials only): nothing is staged, so the
+// unstaged layout and its deeper operand ring serve every tile.
+template <int EPI>
+cudaError_t launch_pair_head(bool in_fp8, const CUtensorMap& tmA, const CUtensorMap& tmB,
+                             const CUtensorMap& tmO, const TcGemmParams& p, int grid,
+                             cudaStream_t s) {
+  return in_fp8 ? launch_pair_one<true, false, false, 5, EPI>(tmA, tmB, tmO, p, grid, s)
+                : launch_pair_one<false, false, false, 5, EPI>(tmA, tmB, tmO, p, grid, s);
+}
+
 // The staged mode-0 tile whose outputs leave by TMA stores.
 template <int EPI>
 cudaError_t launch_pair_tma(bool in_fp8, bool out_fp8, const CUtensorMap& tmA,
@@ -447,6 +460,9 @@ cudaError_t launch_tc_gemm_pair(bool in_fp8, bool out_fp8, bool staged, int epi_
   if (p.tma_out)
     return epi_warps == 8 ? launch_pair_tma<8>(in_fp8, out_fp8, tmA, tmB, to, p, grid, s)
                           : launch_pair_tma<4>(in_fp8, out_fp8, tmA, tmB, to, p, grid, s);
+  if (p.mode == 1)
+    return epi_warps == 8 ? launch_pair_head<8>(in_fp8, tmA, tmB, to, p, grid, s)
+                          : launch_pair_head<4>(in_fp8, tmA, tmB, to, p, grid, s);
   if (epi_warps == 8) return launch_pair_epi<8>(in_fp8, out_fp8, staged, tmA, tmB, to, p, grid, s);
   return launch_pair_epi<4>(in_fp8, out_fp8, staged, tmA, tmB, to, p, grid, s);
 }
