@@ -49,7 +49,7 @@ typedef enum {
   DDF_ERR_CUDA = 2,         /* a CUDA runtime call failed (message in ddf_last_error) */
   DDF_ERR_OOM = 3,          /* device or pinned allocation failed */
   DDF_ERR_BAD_WEIGHTS = 4,  /* blob size mismatch, non-finite values, no weights loaded */
-  DDF_ERR_UNSUPPORTED = 5,  /* valid request this build does not support (e.g. width) */
+  DDF_ERR_UNSUPPORTED = 5,  /* valid request the library does not support (e.g. width) */
   DDF_ERR_TIMEOUT = 6       /* a device-side bounded wait ran out (see header notes) */
 } ddf_status;
 

@@ -39,11 +39,23 @@ def test_oracle_imports_only_numpy_and_the_standard_library():
             assert name.split(".")[0] in allowed, (path, name)
 
 
+def _ignored_top_dirs():
+    """Top-level folders .gitignore keeps out of the repository."""
+    out = set()
+    with open(os.path.join(ROOT, ".gitignore")) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#") and line.endswith("/"):
+                out.add(line.strip("/").split("/")[0])
+    return out
+
+
 def test_only_tests_smoke_and_bench_run_the_oracle():
     users = set()
+    skip = _ignored_top_dirs() | {"oracle"}
     for path in glob.glob(os.path.join(ROOT, "**", "*.py"), recursive=True):
         rel = os.path.relpath(path, ROOT)
-        if rel.split(os.sep)[0] in ("_work", "gpurun_out", "baseline", "oracle"):
+        if rel.split(os.sep)[0] in skip:
             continue
         if any(n.split(".")[0] == "oracle" for n in _imports(path)):
             users.add(rel.split(os.sep)[0] if os.sep in rel else rel)
