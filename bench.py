@@ -82,6 +82,47 @@ PROFILE_SOURCE = "profiles/tc_gemm_pair_bf16_shadow_4M.md"
 PROFILE_METRIC = "sm__pipe_tensor_cycles_active (pct of peak, elapsed)"
 
 
+def roofline_block(prof, R, steps, hidden_tile, precision, peaks):
+    """The line's roofline object for the dominant kernel, the tensor-core
+    GEMM of the hidden layers 2..H (identical launches: chunk x 1280 x 1280
+    each), from the library's per-class kernel times prof = {class: (ms,
+    launches)} over `steps` steps of R rays."""
+    L_, W_, H_ = NET
+    d_in = 6 + 12 * L_
+    gemm_flops_step = 2.0 * R * (H_ - 1) * W_ * W_
+    first_flops_step = 2.0 * R * d_in * W_
+    g_ms, g_n = prof["gemm"]
+    f_ms, f_n = prof["gemm_first"]
+    peak = peaks.get("bf16_tflops_sustained")
+    peak_src = "measured (bf16_tflops_sustained)"
+    if peak is None:
+        peak, peak_src = 1700.0, "fallback (1.7 PFLOP/s sustained)"
+    achieved = gemm_flops_step * steps / (g_ms / 1e3) / 1e12 if g_ms > 0 else None
+    # DRAM bytes per activation row of the hidden tile that ran, from its
+    # ncu capture (PROFILED_TILES); traffic grows with the rows, so a launch
+    # of R rows moves about R / 262,144 times the captured bytes.
+    traffic = None
+    rows_per_launch = gemm_flops_step * steps / g_n / (2.0 * W_ * W_) if g_n else 0
+    tile_prof = PROFILED_TILES.get(hidden_tile) if precision == "bf16" else None
+    if tile_prof is not None:
+        traffic = rows_per_launch * (tile_prof["traffic_per_262144_rows"] / 262144)
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if achieved else None, "traffic": traffic,
+            "traffic_unit": "DRAM bytes per launch (ncu dram__bytes_read+write, scaled "
+                            "from a 262,144-row capture by rows per launch)",
+            "algorithmic_bytes_per_launch": rows_per_launch * 2 * 2 * W_ + 2 * W_ * W_,
+            "kernel": "tensor-core layer GEMM, hidden layers 2..8 (bf16, 1280x1280)",
+            "flops_per_launch": gemm_flops_step * steps / g_n if g_n else None,
+            "avg_launch_ms": g_ms / g_n if g_n else None, "peak_source": peak_src,
+            "kernel_time_share": g_ms / sum(v[0] for v in prof.values()),
+            "first_layer": {"achieved_tflops": first_flops_step * steps / (f_ms / 1e3) / 1e12
+                            if f_ms > 0 else None, "ms_per_step": f_ms / steps},
+            "tensor_pipe": ({"kernel": tile_prof["kernel"],
+                             "active_pct_of_peak": tile_prof["active_pct_of_peak"],
+                             "source": PROFILE_SOURCE, "metric": PROFILE_METRIC}
+                            if tile_prof is not None else None)}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -929,48 +970,17 @@ def main():
     value = whole_job_rate(R, ws, args.steps, total_ms / 1e3)
     status = ddf.ddf_check_status(m.h)
 
-    # roofline of the dominant kernel: the tensor-core GEMM of the hidden
-    # layers 2..H (identical launches: chunk x 1280 x 1280 each)
-    L_, W_, H_ = NET
-    d_in = 6 + 12 * L_
-    gemm_flops_step = 2.0 * R * (H_ - 1) * W_ * W_
-    first_flops_step = 2.0 * R * d_in * W_
-    g_ms, g_n = prof["gemm"]
-    f_ms, f_n = prof["gemm_first"]
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             peaks = json.load(fh)
     except OSError:
         pass
-    peak = peaks.get("bf16_tflops_sustained")
-    peak_src = "measured (bf16_tflops_sustained)"
-    if peak is None:
-        peak, peak_src = 1700.0, "fallback (1.7 PFLOP/s sustained)"
-    achieved = gemm_flops_step * args.steps / (g_ms / 1e3) / 1e12 if g_ms > 0 else None
-    # DRAM bytes per activation row of the hidden tile that ran, from its
-    # ncu capture (PROFILED_TILES); traffic grows with the rows, so a launch
-    # of R rows moves about R / 262,144 times the captured bytes.
-    traffic = None
-    rows_per_launch = gemm_flops_step * args.steps / g_n / (2.0 * W_ * W_) if g_n else 0
-    tile_prof = PROFILED_TILES.get(tile["hidden"]) if args.precision == "bf16" else None
-    if tile_prof is not None:
-        traffic = rows_per_launch * (tile_prof["traffic_per_262144_rows"] / 262144)
-    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if achieved else None, "traffic": traffic,
-                "traffic_unit": "DRAM bytes per launch (ncu dram__bytes_read+write, scaled "
-                                "from a 262,144-row capture by rows per launch)",
-                "algorithmic_bytes_per_launch": rows_per_launch * 2 * 2 * W_ + 2 * W_ * W_,
-                "kernel": "tensor-core layer GEMM, hidden layers 2..8 (bf16, 1280x1280)",
-                "flops_per_launch": gemm_flops_step * args.steps / g_n if g_n else None,
-                "avg_launch_ms": g_ms / g_n if g_n else None, "peak_source": peak_src,
-                "kernel_time_share": g_ms / sum(v[0] for v in prof.values()),
-                "first_layer": {"achieved_tflops": first_flops_step * args.steps / (f_ms / 1e3) / 1e12
-                                if f_ms > 0 else None, "ms_per_step": f_ms / args.steps},
-                "tensor_pipe": ({"kernel": tile_prof["kernel"],
-                                 "active_pct_of_peak": tile_prof["active_pct_of_peak"],
-                                 "source": PROFILE_SOURCE, "metric": PROFILE_METRIC}
-                                if tile_prof is not None else None)}
+    roofline = roofline_block(prof, R, args.steps, tile["hidden"], args.precision, peaks)
+    # what the comparison legs below rate against the same peak
+    L_, W_, H_ = NET
+    gemm_flops_step = 2.0 * R * (H_ - 1) * W_ * W_
+    peak, peak_src = roofline["peak"], roofline["peak_source"]
     launches = int(sum(v[1] for v in prof.values()))
 
     # end to end through the host-buffer entry point (pinned host memory)

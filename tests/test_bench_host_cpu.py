@@ -2,11 +2,14 @@
 clock summary built from nvidia-smi samples (median SM clock under load,
 throttle reasons seen under load; a fake sample file stands in for
 nvidia-smi, no process is started), the default command line, the per-rank
-split and the bounded oracle sample of the cpu_baseline leg."""
+split, the bounded oracle sample of the cpu_baseline leg, the roofline
+object built from fake kernel times, and a static check that every name a
+bench function reads is bound."""
 import os
 import sys
 
 import numpy as np
+import pytest
 
 sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 import bench  # noqa: E402
@@ -101,3 +104,58 @@ def test_tensor_pipe_figures_come_from_the_cited_profile():
         for v in tile["active_pct_of_peak"]:
             assert f"{v} %" in text, v
         assert f"{tile['traffic_per_262144_rows'] / 1e6:.1f} MB" in text
+
+
+def test_roofline_block_from_fake_counters():
+    """The line's roofline object from the library's per-class kernel times:
+    7 hidden-layer launches of 1,048,576 rows in 14 ms against a 1,707.7
+    TFLOP/s peak, the profiled tile's traffic scaled by rows."""
+    prof = {"gemm": (14.0, 7), "gemm_first": (0.5, 1), "head": (0.05, 1), "encode": (0.0, 0)}
+    R = 1 << 20
+    r = bench.roofline_block(prof, R, 1, "256x4pairstaged", "bf16", {"bf16_tflops_sustained": 1707.7})
+    flops = 2.0 * R * 7 * 1280 * 1280
+    assert r["achieved"] == pytest.approx(flops / 14e-3 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / 1707.7)
+    assert r["flops_per_launch"] == pytest.approx(flops / 7)
+    assert r["avg_launch_ms"] == pytest.approx(2.0)
+    assert r["traffic"] == pytest.approx(R * 1304.9e6 / 262144)
+    assert r["kernel_time_share"] == pytest.approx(14.0 / 14.55)
+    assert r["tensor_pipe"]["active_pct_of_peak"] == [80.9, 81.4]
+    # an unprofiled tile or precision reports no traffic; no measured peak: the fallback
+    r2 = bench.roofline_block(prof, R, 1, "128x4", "bf16", {})
+    assert r2["traffic"] is None and r2["tensor_pipe"] is None and r2["peak"] == 1700.0
+
+
+def test_bench_functions_bind_every_name_they_read():
+    """Every name a function of bench.py reads is bound in it, at module
+    level or as a builtin (a renamed or shadowed variable fails here instead
+    of on the GPU)."""
+    import ast
+    import builtins
+    import os
+    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "bench.py")).read()
+    tree = ast.parse(src)
+    module = set(dir(builtins))
+    for n in tree.body:
+        if isinstance(n, (ast.FunctionDef, ast.ClassDef)):
+            module.add(n.name)
+        elif isinstance(n, ast.Assign):
+            module |= {x.id for t in n.targets for x in ast.walk(t) if isinstance(x, ast.Name)}
+        elif isinstance(n, (ast.Import, ast.ImportFrom)):
+            module |= {(a.asname or a.name).split(".")[0] for a in n.names}
+    for fn in (n for n in tree.body if isinstance(n, ast.FunctionDef)):
+        bound = set()
+        for x in ast.walk(fn):
+            if isinstance(x, ast.Name) and isinstance(x.ctx, (ast.Store, ast.Del)):
+                bound.add(x.id)
+            elif isinstance(x, ast.arg):
+                bound.add(x.arg)
+            elif isinstance(x, ast.FunctionDef):
+                bound.add(x.name)
+            elif isinstance(x, (ast.Import, ast.ImportFrom)):
+                bound |= {(a.asname or a.name).split(".")[0] for a in x.names}
+            elif isinstance(x, ast.ExceptHandler) and x.name:
+                bound.add(x.name)
+        used = {x.id for x in ast.walk(fn) if isinstance(x, ast.Name) and isinstance(x.ctx, ast.Load)}
+        assert not (used - bound - module), (fn.name, sorted(used - bound - module))
