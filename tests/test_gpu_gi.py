@@ -72,10 +72,11 @@ def test_field_render_approaches_exact(torch_cuda):
     """A hash-grid field distilled for 3,000 steps (the paper's recipe)
     renders shadow and AO images whose PSNR against the exact images, over
     foreground pixels, is above 10 dB and 14.5 dB (measured on GB300 on this
-    64-primitive scene, 16 AO rays: 10.7-11.4 and 16.2-16.3 dB at 3,000
-    steps with surface rays drawn by primitive or by area, 12.3 and 19.0 dB
-    at 30,000), and its images use the exact primary hits (same
-    foreground)."""
+    64-primitive scene with 16 AO rays: at this 128 x 96 size, with surface
+    rays drawn by primitive, 11.1-11.4 and 16.2 dB at 3,000 steps and 12.3
+    and 19.0 dB at 30,000; the benchmark's 512 x 512 images with surface
+    rays drawn by area, 10.7-10.8 and 16.3 dB at 3,000), and its images use
+    the exact primary hits (same foreground)."""
     torch = torch_cuda
     from paper_2606_00817_gb300 import ddf
     scene, sph, box = _scene(torch)
