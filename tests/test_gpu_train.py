@@ -402,3 +402,33 @@ def test_copies_after_a_step_match_a_fresh_load(torch_cuda, net):
     ddf.ddf_compute_grad(b.h, inputs, tt_d, y_d, 2048)
     gb = ddf.ddf_get_grad(b.h, blob.size)
     assert np.array_equal(ga, gb)
+
+
+def test_gradient_is_complete_on_the_callers_stream(torch_cuda):
+    """The layer reductions run on a stream of the library's own beside the
+    GEMMs; the backward joins it into the caller's stream before it returns.
+    So a gradient computed and copied out on a user stream, with only that
+    stream synchronised, is the whole gradient: the buffer first holds
+    another batch's gradient, and the copy must show none of it."""
+    torch = torch_cuda
+    from paper_2606_00817_gb300 import ddf
+    net, B = PAPER, 16384
+    blob = I.xavier_blob(I.NetShape(*net))
+    m = ddf.DDF(*net, precision="bf16")
+    m.load(blob)
+    batches = []
+    for seed in (51, 52):
+        rays, tt, y = _batch(net, B, seed=seed)
+        batches.append((_dev(torch, rays.soa()), torch.from_numpy(tt).cuda(), torch.from_numpy(y).cuda()))
+    ddf.ddf_compute_grad(m.h, *batches[1], B)
+    want = ddf.ddf_get_grad(m.h, blob.size)               # device-synchronised reference
+    ddf.ddf_compute_grad(m.h, *batches[0], B)
+    other = ddf.ddf_get_grad(m.h, blob.size)
+    assert not np.array_equal(want, other)
+    s = torch.cuda.Stream()
+    out = torch.empty(blob.size, device="cuda")
+    ddf.ddf_compute_grad(m.h, *batches[1], B, stream=s)
+    ddf.ddf_copy_grad(m.h, out, stream=s)
+    s.synchronize()
+    assert np.array_equal(out.cpu().numpy(), want)
+    assert ddf.ddf_check_status(m.h) == 0
